@@ -1,0 +1,404 @@
+"""Seeded synthetic closed triangle meshes, emitted as FP32 triangle soups.
+
+This module only produces inputs. It holds none of the distance-field
+arithmetic: no closest-point, pseudonormal, classification or sign code lives
+here, so both the CUDA path and the CPU oracle can take their inputs from it.
+
+The meshes stand in for the paper's public STL models (Table 1: 5e4 to 2.9e6
+faces of near-uniform size, Section 11.2), which are not available here. Every
+mesh is built as an indexed mesh in float64, each unique vertex is rounded to
+float32 once, and the soup is gathered from those rounded vertices, so copies of
+a vertex in the soup are bitwise identical (the welding reading of Section 7.2).
+Triangles are shuffled and each triangle's corners are rotated cyclically
+(orientation preserved) so the soup carries no order (Section 7: "the order of
+triangles in an STL file can be arbitrary").
+
+Seeds follow the recipe `353_000 + config_index` (PCG64).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+CENTER = np.array([0.5, 0.5, 0.5])
+
+
+@dataclass
+class Mesh:
+    """Indexed closed mesh: float64 vertices [V,3], int32 triangles [T,3] (CCW seen from outside)."""
+    vertices: np.ndarray
+    triangles: np.ndarray
+
+    def soup(self, seed: int | None = None, shuffle: bool = True) -> np.ndarray:
+        """FP32 soup [T,3,3]; each unique vertex rounded once, then gathered."""
+        v32 = self.vertices.astype(np.float32)
+        tri = self.triangles
+        if shuffle:
+            rng = np.random.Generator(np.random.PCG64(0 if seed is None else seed))
+            perm = rng.permutation(tri.shape[0])
+            rot = rng.integers(0, 3, size=tri.shape[0])
+            tri = tri[perm]
+            idx = (np.arange(3)[None, :] + rot[:, None]) % 3
+            tri = np.take_along_axis(tri, idx, axis=1)
+        return np.ascontiguousarray(v32[tri])
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def _orient_outward(vertices: np.ndarray, triangles: np.ndarray) -> np.ndarray:
+    """Flip every triangle if the mesh's signed volume is negative."""
+    a, b, c = (vertices[triangles[:, k]] for k in range(3))
+    vol = np.einsum("ij,ij->i", a, np.cross(b, c)).sum() / 6.0
+    if vol < 0:
+        triangles = triangles[:, [0, 2, 1]]
+    return np.ascontiguousarray(triangles.astype(np.int32))
+
+
+def _grid_quads(nu: int, nv: int) -> np.ndarray:
+    """Two triangles per quad of a doubly periodic (nu x nv) vertex grid, index = i*nv + j."""
+    i, j = np.meshgrid(np.arange(nu), np.arange(nv), indexing="ij")
+    i, j = i.ravel(), j.ravel()
+    i1, j1 = (i + 1) % nu, (j + 1) % nv
+    v00, v10, v11, v01 = i * nv + j, i1 * nv + j, i1 * nv + j1, i * nv + j1
+    t1 = np.stack([v00, v10, v11], axis=1)
+    t2 = np.stack([v00, v11, v01], axis=1)
+    return np.concatenate([t1, t2], axis=0)
+
+
+# ----------------------------------------------------------------------------- icosphere
+
+_ICO_T = (1.0 + 5.0 ** 0.5) / 2.0
+_ICO_V = np.array([
+    (-1, _ICO_T, 0), (1, _ICO_T, 0), (-1, -_ICO_T, 0), (1, -_ICO_T, 0),
+    (0, -1, _ICO_T), (0, 1, _ICO_T), (0, -1, -_ICO_T), (0, 1, -_ICO_T),
+    (_ICO_T, 0, -1), (_ICO_T, 0, 1), (-_ICO_T, 0, -1), (-_ICO_T, 0, 1)], dtype=np.float64)
+_ICO_F = np.array([
+    (0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+    (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+    (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)], dtype=np.int64)
+
+
+def geodesic_directions(freq: int) -> tuple[np.ndarray, np.ndarray]:
+    """Class-I geodesic subdivision of the icosahedron: unit directions [10f^2+2,3], triangles [20f^2,3].
+
+    Each icosahedron face is split into freq^2 triangles on a barycentric lattice.
+    Lattice points on shared icosahedron edges are keyed canonically so the two
+    faces sharing an edge produce the same vertex index (and value).
+    """
+    keys: dict = {}
+    pos: list = []
+
+    def vid(a, b, c, i, j):
+        # point A + (B-A) i/f + (C-A) j/f on face (a,b,c); canonical key per location
+        f = freq
+        k = f - i - j
+        if i == f:
+            key = ("v", b)
+        elif j == f:
+            key = ("v", c)
+        elif k == f:
+            key = ("v", a)
+        elif k == 0:  # on edge b-c
+            key = ("e",) + ((b, c, j) if b < c else (c, b, i))
+        elif i == 0:  # on edge a-c
+            key = ("e",) + ((a, c, j) if a < c else (c, a, k))
+        elif j == 0:  # on edge a-b
+            key = ("e",) + ((a, b, i) if a < b else (b, a, k))
+        else:
+            key = ("f", a, b, c, i, j)
+        got = keys.get(key)
+        if got is not None:
+            return got
+        if key[0] == "v":
+            p = _ICO_V[key[1]]
+        elif key[0] == "e":
+            lo, hi, s = key[1], key[2], key[3]
+            p = _ICO_V[lo] + (_ICO_V[hi] - _ICO_V[lo]) * (s / f)
+        else:
+            p = _ICO_V[a] + (_ICO_V[b] - _ICO_V[a]) * (i / f) + (_ICO_V[c] - _ICO_V[a]) * (j / f)
+        keys[key] = len(pos)
+        pos.append(p)
+        return keys[key]
+
+    tris = []
+    for a, b, c in _ICO_F:
+        a, b, c = int(a), int(b), int(c)
+        for i in range(freq):
+            for j in range(freq - i):
+                p00 = vid(a, b, c, i, j)
+                p10 = vid(a, b, c, i + 1, j)
+                p01 = vid(a, b, c, i, j + 1)
+                tris.append((p00, p10, p01))
+                if i + j < freq - 1:
+                    p11 = vid(a, b, c, i + 1, j + 1)
+                    tris.append((p10, p11, p01))
+    d = np.array(pos)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return d, np.array(tris, dtype=np.int64)
+
+
+def _sinusoid_field(rng, dirs: np.ndarray, n_terms: int, max_freq: float) -> np.ndarray:
+    """Seeded smooth scalar field on unit directions, normalised to max |f| = 1."""
+    f = np.zeros(dirs.shape[0])
+    for _ in range(n_terms):
+        w = rng.normal(size=3)
+        w *= rng.uniform(1.0, max_freq) / np.linalg.norm(w)
+        f += rng.uniform(0.5, 1.0) * np.sin(dirs @ w + rng.uniform(0, 2 * math.pi))
+    return f / np.abs(f).max()
+
+
+def icosphere(freq: int, radius: float = 0.3, center=CENTER, displacement: float = 0.0,
+              seed: int = 0, n_terms: int = 6, max_freq: float = 3.0) -> Mesh:
+    """Geodesic icosphere (20 f^2 triangles, 10 f^2 + 2 vertices), optional seeded radial displacement."""
+    d, tri = geodesic_directions(freq)
+    r = np.full(d.shape[0], radius)
+    if displacement:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        r = r + displacement * _sinusoid_field(rng, d, n_terms, max_freq)
+    v = np.asarray(center) + d * r[:, None]
+    return Mesh(v, _orient_outward(v, tri))
+
+
+# ----------------------------------------------------------------------------- torus
+
+def torus(nu: int = 250, nv: int = 100, R: float = 0.3, r: float = 0.1, bump: float = 0.02,
+          jitter: float = 1e-3, seed: int = 353_001, center=CENTER) -> Mesh:
+    """Torus with minor radius r + bump*sin(5u)*sin(7v) along the minor-circle normal,
+    plus N(0, jitter^2) per-coordinate noise on the (welded) vertices."""
+    u = 2 * math.pi * np.arange(nu) / nu
+    v = 2 * math.pi * np.arange(nv) / nv
+    U, Vv = np.meshgrid(u, v, indexing="ij")
+    rr = r + bump * np.sin(5 * U) * np.sin(7 * Vv)
+    x = (R + rr * np.cos(Vv)) * np.cos(U)
+    y = (R + rr * np.cos(Vv)) * np.sin(U)
+    z = rr * np.sin(Vv)
+    verts = np.stack([x, y, z], axis=-1).reshape(-1, 3)
+    if jitter:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        verts = verts + rng.normal(0.0, jitter, size=verts.shape)
+    verts = verts + np.asarray(center)
+    return Mesh(verts, _orient_outward(verts, _grid_quads(nu, nv)))
+
+
+# ----------------------------------------------------------------------------- torus-knot tube
+
+def knot_curve(t: np.ndarray, p: int = 3, q: int = 7, R: float = 0.3, a: float = 0.12):
+    """(p,q) torus knot c(t) and its derivative, t in [0, 2pi)."""
+    rho = R + a * np.cos(q * t)
+    c = np.stack([rho * np.cos(p * t), rho * np.sin(p * t), a * np.sin(q * t)], axis=-1)
+    drho = -a * q * np.sin(q * t)
+    dc = np.stack([drho * np.cos(p * t) - rho * p * np.sin(p * t),
+                   drho * np.sin(p * t) + rho * p * np.cos(p * t),
+                   a * q * np.cos(q * t)], axis=-1)
+    return c, dc
+
+
+def _parallel_transport_frame(T: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Closed parallel-transport frame along unit tangents T[n,3]; closure twist spread uniformly."""
+    n = T.shape[0]
+    N = np.zeros_like(T)
+    a = np.cross(T[0], [0.0, 0.0, 1.0])
+    if np.linalg.norm(a) < 1e-6:
+        a = np.cross(T[0], [1.0, 0.0, 0.0])
+    N[0] = a / np.linalg.norm(a)
+    for i in range(n - 1):
+        # rotate N[i] by the minimal rotation taking T[i] to T[i+1] (double reflection)
+        v1 = T[i + 1] - T[i]
+        c1 = v1 @ v1
+        r = N[i] - (2.0 / c1) * (v1 @ N[i]) * v1 if c1 > 0 else N[i]
+        t = T[i] - (2.0 / c1) * (v1 @ T[i]) * v1 if c1 > 0 else T[i]
+        v2 = T[i + 1] - t
+        c2 = v2 @ v2
+        N[i + 1] = r - (2.0 / c2) * (v2 @ r) * v2 if c2 > 0 else r
+        N[i + 1] -= (N[i + 1] @ T[i + 1]) * T[i + 1]
+        N[i + 1] /= np.linalg.norm(N[i + 1])
+    # transport once more from the last sample back to the first to measure the twist
+    v1 = T[0] - T[-1]
+    c1 = v1 @ v1
+    r = N[-1] - (2.0 / c1) * (v1 @ N[-1]) * v1 if c1 > 0 else N[-1]
+    t = T[-1] - (2.0 / c1) * (v1 @ T[-1]) * v1 if c1 > 0 else T[-1]
+    v2 = T[0] - t
+    c2 = v2 @ v2
+    Nend = r - (2.0 / c2) * (v2 @ r) * v2 if c2 > 0 else r
+    B0 = np.cross(T[0], N[0])
+    phi = math.atan2(Nend @ B0, Nend @ N[0])
+    ang = -phi * np.arange(n) / n
+    B = np.cross(T, N)
+    Nc = np.cos(ang)[:, None] * N + np.sin(ang)[:, None] * B
+    Bc = np.cross(T, Nc)
+    return Nc, Bc
+
+
+def knot_tube(n_along: int = 8192, n_around: int = 128, radius: float = 0.04, noise: float = 0.005,
+              seed: int = 353_003, p: int = 3, q: int = 7, R: float = 0.3, a: float = 0.12,
+              center=CENTER) -> Mesh:
+    """Closed tube around the (p,q) torus knot with seeded periodic surface noise."""
+    t = 2 * math.pi * np.arange(n_along) / n_along
+    c, dc = knot_curve(t, p, q, R, a)
+    T = dc / np.linalg.norm(dc, axis=1, keepdims=True)
+    N, B = _parallel_transport_frame(T)
+    th = 2 * math.pi * np.arange(n_around) / n_around
+    rng = np.random.Generator(np.random.PCG64(seed))
+    S, TH = np.meshgrid(t, th, indexing="ij")
+    field = np.zeros_like(S)
+    for _ in range(8):
+        fs = int(rng.integers(1, 40))
+        ft = int(rng.integers(1, 9))
+        field += rng.uniform(0.5, 1.0) * np.sin(fs * S + ft * TH + rng.uniform(0, 2 * math.pi))
+    field /= np.abs(field).max()
+    rho = radius + noise * field
+    verts = (c[:, None, :] + rho[..., None] * (np.cos(TH)[..., None] * N[:, None, :]
+                                               + np.sin(TH)[..., None] * B[:, None, :]))
+    verts = verts.reshape(-1, 3) + np.asarray(center)
+    return Mesh(verts, _orient_outward(verts, _grid_quads(n_along, n_around)))
+
+
+def knot_min_strand_separation(n: int = 4096, p: int = 3, q: int = 7, R: float = 0.3, a: float = 0.12,
+                               exclude: float = 0.5) -> float:
+    """Smallest distance between knot-curve samples more than `exclude` apart in arc parameter."""
+    t = 2 * math.pi * np.arange(n) / n
+    c, _ = knot_curve(t, p, q, R, a)
+    best = np.inf
+    for i in range(0, n, 4):
+        dt = np.abs(t - t[i])
+        dt = np.minimum(dt, 2 * math.pi - dt)
+        far = dt > exclude
+        if far.any():
+            best = min(best, float(np.linalg.norm(c[far] - c[i], axis=1).min()))
+    return best
+
+
+# ----------------------------------------------------------------------------- small exact shapes
+
+def box(center=(0.5, 0.5, 0.5), half=(0.2, 0.15, 0.1), subdiv: int = 1) -> Mesh:
+    """Axis-aligned box; each face split into subdiv x subdiv quads (two triangles each)."""
+    c = np.asarray(center, dtype=np.float64)
+    hx = np.asarray(half, dtype=np.float64)
+    verts: dict = {}
+    pos: list = []
+
+    def vid(p):
+        key = tuple(p)
+        if key not in verts:
+            verts[key] = len(pos)
+            pos.append(p)
+        return verts[key]
+
+    tris = []
+    s = subdiv
+    for axis in range(3):
+        for sgn in (-1, 1):
+            u_ax, v_ax = [k for k in range(3) if k != axis]
+            for i in range(s):
+                for j in range(s):
+                    quad = []
+                    for di, dj in ((0, 0), (1, 0), (1, 1), (0, 1)):
+                        p = [0.0, 0.0, 0.0]
+                        p[axis] = sgn
+                        p[u_ax] = -1 + 2 * (i + di) / s
+                        p[v_ax] = -1 + 2 * (j + dj) / s
+                        quad.append(vid(tuple(p)))
+                    tris.append((quad[0], quad[1], quad[2]))
+                    tris.append((quad[0], quad[2], quad[3]))
+    unit = np.array(pos)
+    v = c + unit * hx
+    tri = np.array(tris, dtype=np.int64)
+    # orient each triangle so its normal points away from the box centre
+    a, b, cc = (v[tri[:, k]] for k in range(3))
+    nrm = np.cross(b - a, cc - a)
+    out = np.einsum("ij,ij->i", nrm, (a + b + cc) / 3 - c)
+    tri[out < 0] = tri[out < 0][:, [0, 2, 1]]
+    return Mesh(v, tri.astype(np.int32))
+
+
+def regular_tetrahedron(center=(0.5, 0.5, 0.5), size: float = 0.25) -> Mesh:
+    """Regular tetrahedron with vertices at center + size*(+-1,+-1,+-1) (even sign parity)."""
+    u = np.array([(1, 1, 1), (1, -1, -1), (-1, 1, -1), (-1, -1, 1)], dtype=np.float64)
+    v = np.asarray(center) + size * u
+    tri = np.array([(0, 1, 2), (0, 3, 1), (0, 2, 3), (1, 3, 2)], dtype=np.int64)
+    a, b, c = (v[tri[:, k]] for k in range(3))
+    nrm = np.cross(b - a, c - a)
+    out = np.einsum("ij,ij->i", nrm, (a + b + c) / 3 - np.asarray(center))
+    tri[out < 0] = tri[out < 0][:, [0, 2, 1]]
+    return Mesh(v, tri.astype(np.int32))
+
+
+def octahedron(center=(0.5, 0.5, 0.5), size: float = 0.3) -> Mesh:
+    u = np.array([(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)], dtype=np.float64)
+    v = np.asarray(center) + size * u
+    tri = []
+    for sx in (0, 1):
+        for sy in (2, 3):
+            for sz in (4, 5):
+                tri.append((sx, sy, sz))
+    tri = np.array(tri, dtype=np.int64)
+    a, b, c = (v[tri[:, k]] for k in range(3))
+    nrm = np.cross(b - a, c - a)
+    out = np.einsum("ij,ij->i", nrm, (a + b + c) / 3 - np.asarray(center))
+    tri[out < 0] = tri[out < 0][:, [0, 2, 1]]
+    return Mesh(v, tri.astype(np.int32))
+
+
+def star_fan_solid(n: int, heights, radius: float = 0.25, apex_h: float = 0.1, bottom: float = -0.2,
+                   center=(0.5, 0.5, 0.5)) -> Mesh:
+    """Closed solid: a top apex joined to a ring of n rim points with per-point heights, closed by a
+    bottom apex.  Alternating rim heights make the top apex a saddle; strongly folded rims give a
+    ruff-like apex whose face normals point to both sides of its pseudonormal plane (Section 3.3)."""
+    heights = np.asarray(heights, dtype=np.float64)
+    ang = 2 * math.pi * np.arange(n) / n
+    rim = np.stack([radius * np.cos(ang), radius * np.sin(ang), heights], axis=1)
+    v = np.concatenate([[[0.0, 0.0, apex_h]], rim, [[0.0, 0.0, bottom]]], axis=0) + np.asarray(center)
+    top, bot = 0, n + 1
+    tri = []
+    for i in range(n):
+        a, b = 1 + i, 1 + (i + 1) % n
+        tri.append((top, a, b))
+        tri.append((bot, b, a))
+    return Mesh(v, _orient_outward(v, np.array(tri, dtype=np.int64)))
+
+
+# ----------------------------------------------------------------------------- named workloads
+
+def config_mesh(index: int) -> Mesh:
+    """The meshes of the five workloads (index 1..5; 3 is the batch, see batch_meshes)."""
+    if index == 1:
+        return icosphere(4, radius=0.3)
+    if index == 2:
+        return torus(seed=353_002)
+    if index == 4:
+        return knot_tube(seed=353_004)
+    if index == 5:
+        return icosphere(100, radius=0.3, displacement=0.02, seed=353_005)
+    raise ValueError(index)
+
+
+def config_soup(index: int) -> np.ndarray:
+    return config_mesh(index).soup(seed=353_000 + index)
+
+
+CONFIG_GRID = {1: (64, 3), 2: (512, 4), 4: (1024, 3), 5: (512, 4)}   # N, band half-width in cells
+
+
+def batch_meshes(n: int = 64, seed: int = 353_003, t_min: float = 1e3, t_max: float = 2e5):
+    """Batch of uneven meshes: displaced icospheres and displaced tori, sizes log-uniform in triangles,
+    each paired with a grid size N in {64, 96, ..., 384}.  Returns a list of (Mesh, N)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for m in range(n):
+        target = math.exp(rng.uniform(math.log(t_min), math.log(t_max)))
+        kind = int(rng.integers(0, 2))
+        sub = 353_000 + 100 * 3 + m
+        if kind == 0:
+            f = max(2, int(round(math.sqrt(target / 20.0))))
+            mesh = icosphere(f, radius=float(rng.uniform(0.2, 0.35)),
+                             displacement=float(rng.uniform(0.0, 0.03)), seed=sub)
+        else:
+            nv = max(8, int(round(math.sqrt(target / 2.0 / 2.5))))
+            nu = max(8, int(round(target / 2.0 / nv)))
+            mesh = torus(nu=nu, nv=nv, R=float(rng.uniform(0.22, 0.3)), r=float(rng.uniform(0.06, 0.1)),
+                         bump=float(rng.uniform(0.0, 0.02)), jitter=0.0, seed=sub)
+        N = int(rng.choice(np.arange(64, 385, 32)))
+        out.append((mesh, N))
+    return out

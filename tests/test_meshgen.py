@@ -1,0 +1,90 @@
+"""Checks of the synthetic input meshes: closed, oriented 2-manifolds with the sizes the
+workloads name, no degenerate triangles, the expected Euler characteristic, and exact
+duplicate coordinates in the soup (Section 7 reading of "identical" vertices)."""
+import numpy as np
+import pytest
+
+import meshgen
+
+
+def _check_closed_oriented(mesh: meshgen.Mesh):
+    tri = mesh.triangles.astype(np.int64)
+    a = tri.ravel()
+    b = tri[:, [1, 2, 0]].ravel()
+    directed = set(zip(a.tolist(), b.tolist()))
+    assert len(directed) == a.size, "a directed edge appears twice (not oriented)"
+    for u, v in directed:
+        assert (v, u) in directed, "open edge"
+    X = mesh.vertices
+    cr = np.cross(X[tri[:, 1]] - X[tri[:, 0]], X[tri[:, 2]] - X[tri[:, 0]])
+    area2 = np.linalg.norm(cr, axis=1)
+    assert area2.min() > 1e-12
+    vol = np.einsum("ij,ij->i", X[tri[:, 0]], np.cross(X[tri[:, 1]], X[tri[:, 2]])).sum() / 6
+    assert vol > 0
+    return len(directed) // 2
+
+
+@pytest.mark.parametrize("freq", [1, 2, 4, 7])
+def test_icosphere_counts(freq):
+    m = meshgen.icosphere(freq)
+    assert m.triangles.shape[0] == 20 * freq * freq
+    assert m.vertices.shape[0] == 10 * freq * freq + 2
+    E = _check_closed_oriented(m)
+    assert m.vertices.shape[0] - E + m.triangles.shape[0] == 2
+
+
+def test_config1_sizes():
+    m = meshgen.config_mesh(1)
+    assert m.triangles.shape == (320, 3) and m.vertices.shape == (162, 3)
+    r = np.linalg.norm(m.vertices - 0.5, axis=1)
+    assert np.allclose(r, 0.3)
+
+
+def test_torus_small_and_config2_sizes():
+    m = meshgen.torus(nu=30, nv=12, seed=1)
+    E = _check_closed_oriented(m)
+    assert m.vertices.shape[0] - E + m.triangles.shape[0] == 0
+    m2 = meshgen.config_mesh(2)
+    assert m2.triangles.shape[0] == 50_000 and m2.vertices.shape[0] == 25_000
+
+
+def test_knot_tube_small():
+    m = meshgen.knot_tube(n_along=512, n_around=16, seed=3)
+    E = _check_closed_oriented(m)
+    assert m.vertices.shape[0] - E + m.triangles.shape[0] == 0
+
+
+def test_knot_strand_separation():
+    # strands must stay far apart compared with 2*(tube radius + noise) + 2*band
+    sep = meshgen.knot_min_strand_separation()
+    assert sep > 2 * 0.045 + 2 * 3 / 1024 + 0.02, sep
+
+
+def test_soup_duplicates_are_bitwise_equal():
+    m = meshgen.icosphere(3, displacement=0.02, seed=5)
+    s = m.soup(seed=9)
+    flat = s.reshape(-1, 3)
+    uniq = np.unique(flat.view(np.dtype((np.void, 12))))
+    assert uniq.shape[0] == m.vertices.shape[0]
+
+
+def test_soup_shuffle_preserves_orientation():
+    m = meshgen.icosphere(2)
+    s = m.soup(seed=1).astype(np.float64)
+    n = np.cross(s[:, 1] - s[:, 0], s[:, 2] - s[:, 0])
+    c = s.mean(axis=1) - 0.5
+    assert np.all(np.einsum("ij,ij->i", n, c) > 0)
+
+
+def test_box_and_tetra_closed():
+    for m in (meshgen.box(subdiv=2), meshgen.regular_tetrahedron(), meshgen.octahedron(),
+              meshgen.star_fan_solid(8, [0.05, -0.05] * 4)):
+        E = _check_closed_oriented(m)
+        assert m.vertices.shape[0] - E + m.triangles.shape[0] == 2
+
+
+def test_batch_meshes_sizes():
+    batch = meshgen.batch_meshes(n=8, t_max=2e4)
+    for mesh, N in batch:
+        _check_closed_oriented(mesh)
+        assert 64 <= N <= 384 and N % 32 == 0
