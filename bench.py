@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the narrow-band SDF path on one GB300 (one JSON line on stdout).
+
+Default workload (--workload c2): a 50,000-triangle displaced, jittered torus soup
+(R=0.3, r=0.1), grid 512^3 on [0,1]^3, band half-width 4h.  One step is the whole
+path: sdf_build_features (weld, pair, records) + sdf_narrow_band (bin, scan
+conversion + merge + dense write, FP64 re-decision) + sdf_narrow_band_backward
+(vertex adjoint of L = sum_band (d - 0.01)^2, its upstream gradient formed once from
+the first forward since the mesh is the same every step).  --workload c4 times the
+2,097,152-triangle knot tube on 1024^3, band 3h (forward only).
+
+value = band points produced per second (all ranks), device-timed with CUDA events;
+e2e = the same metric through the public API with host buffers (pinned H2D of the
+soup, D2H of the SDF and the vertex gradient inside the timed region).
+--impl reference times the FP64 CPU oracle on a bounded slab of the same workload.
+Multi-GPU (torchrun): every rank runs its own replica of the workload (independent
+problems, no data-path collective); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "narrow-band grid points/s and fwd+adjoint ms at 1 GB300 vs plain fwd; fraction of HBM roofline"
+UNIT = "band points/s"
+
+WORKLOADS = {
+    "c1": dict(index=1, adjoint=False, winner=False,
+               desc="icosphere nu=4 r=0.3 (320 triangles), grid 64^3 on [0,1]^3, band 3h, forward"),
+    "c2": dict(index=2, adjoint=True, winner=True,
+               desc="displaced jittered torus R=0.3 r=0.1 (50,000 triangles), grid 512^3 on [0,1]^3, band 4h, "
+                    "forward + vertex adjoint of sum_band (d - 0.01)^2"),
+    "c4": dict(index=4, adjoint=False, winner=False,
+               desc="(3,7) torus-knot tube r=0.04 + 0.005 noise (2,097,152 triangles), grid 1024^3 on [0,1]^3, "
+                    "band 3h, forward"),
+    "c5": dict(index=5, adjoint=True, winner=True,
+               desc="displaced icosphere nu=100 (200,000 triangles), grid 512^3 on [0,1]^3, band 4h, "
+                    "forward + vertex adjoint"),
+}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling in the background (200 ms period)."""
+    Q = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and parts[0] != self.uuid and ("GPU-" + self.uuid) != parts[0]:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def record_bytes(feats) -> int:
+    """Feature-record bytes the tile kernel reads once (face 4+2 float4, edge 5 float4 + class,
+    vertex 2 float4 + class + one float4 plane per corner)."""
+    T, E, V = feats.n_tri, feats.n_edge, feats.n_vert
+    return T * 96 + E * 81 + V * 33 + 3 * T * 16
+
+
+def cpu_baseline(soup, N, w, target_s: float = 12.0):
+    """The oracle as it stands on a z-slab of the workload grid: rate of band points produced."""
+    import oracle
+    t0 = time.perf_counter()
+    om = oracle.OracleMesh.from_soup(soup)
+    t_build = time.perf_counter() - t0
+    z = soup[..., 2].ravel()
+    kmid = int(np.clip(np.median(z) * N, 0, N - 1))
+    layers, band, spent = 1, 0, 0.0
+    while True:
+        k0 = max(0, kmid - layers // 2)
+        t1 = time.perf_counter()
+        d = om.narrow_band((N, N, layers), (0.0, 0.0, k0 / N), 1.0 / N, w)
+        dt = time.perf_counter() - t1
+        band, spent = int(np.isfinite(d).sum()), dt
+        if dt > target_s / 4 or layers * 2 > N:
+            break
+        layers *= 2
+    frac = layers / N
+    rate = band / (spent + t_build * frac)
+    return {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{layers} of {N} z-layers through the mesh middle ({band} band points, {spent:.1f} s) "
+                      f"plus the oracle's mesh build ({t_build:.2f} s) prorated by {frac:.4f}"}
+
+
+def run_reference(args, wl):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import meshgen
+    import oracle
+    soup = meshgen.config_soup(wl["index"])
+    N, cells = meshgen.CONFIG_GRID[wl["index"]]
+    w = cells / N
+    om = oracle.OracleMesh.from_soup(soup)
+    z = soup[..., 2].ravel()
+    kmid = int(np.clip(np.median(z) * N, 0, N - 1))
+    layers = 2
+    # each step evaluates a bounded slab of the workload (the oracle as it stands)
+    def step(i):
+        k0 = (kmid - layers * 4 + layers * (i % 8)) % max(1, N - layers)
+        d = om.narrow_band((N, N, layers), (0.0, 0.0, k0 / N), 1.0 / N, w)
+        return int(np.isfinite(d).sum())
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    band = sum(step(i) for i in range(args.steps))
+    dt = time.perf_counter() - t0
+    value = band / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl["desc"], "sample": f"{layers} z-layers per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{layers} of {N} z-layers per step near the mesh middle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+
+    import torch
+    import torch.distributed as tdist
+
+    import meshgen
+    import paper_1903_00353_gb300 as sdf
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        tdist.barrier()
+    sdf.load_library()
+
+    soup_np = meshgen.config_soup(wl["index"])
+    N, cells = meshgen.CONFIG_GRID[wl["index"]]
+    w = cells / N
+    grid = sdf.Grid.cube(N)
+    dev = torch.device("cuda", local)
+    soup = torch.from_numpy(soup_np).to(dev)
+    dist = torch.empty(grid.shape, dtype=torch.float32, device=dev)
+    win = torch.empty(grid.shape, dtype=torch.int32, device=dev) if wl["winner"] else None
+    gv = None
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    # upstream gradient of L = sum_band (d - 0.01)^2 from one forward (same mesh every step)
+    feats = sdf.sdf_build_features(soup)
+    sdf.sdf_narrow_band(feats, grid, w, out=dist, winner=win if win is not None else False)
+    band_points = int(torch.isfinite(dist).sum())
+    stats = feats.status()
+    rec_bytes = record_bytes(feats)
+    g = None
+    if wl["adjoint"]:
+        g = torch.where(torch.isfinite(dist), 2.0 * (dist - 0.01), torch.zeros_like(dist))
+        gv = torch.zeros(feats.n_vert, 3, dtype=torch.float32, device=dev)
+    feats.destroy()
+
+    def step(timed_events=None):
+        ev = timed_events
+        if ev:
+            ev[0].record()
+        f = sdf.sdf_build_features(soup)
+        if ev:
+            ev[1].record()
+        sdf.sdf_narrow_band(f, grid, w, out=dist, winner=win if win is not None else False, flags=sdf.FLAG_TIMING)
+        if ev:
+            ev[2].record()
+        if wl["adjoint"]:
+            gv.zero_()
+            sdf.sdf_narrow_band_backward(f, grid, w, g, winner=win, grad_vertices=gv, flags=sdf.FLAG_TIMING)
+        if ev:
+            ev[3].record()
+        return f
+
+    for _ in range(args.warmup):
+        step().destroy()
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    per = []
+    tile_ms, tile_calls = 0.0, 0
+    launches0 = sdf.kernel_launches()
+    with ClockSampler(uuid) as clk:
+        if world > 1:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.fill_(1.0)  # evict L2 between timed steps
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            f = step(evs)
+            torch.cuda.synchronize()
+            t = f.timing()
+            tile_ms += t["tile"][0]
+            tile_calls += t["tile"][1]
+            f.destroy()
+            per.append([evs[0].elapsed_time(evs[1]), evs[1].elapsed_time(evs[2]), evs[2].elapsed_time(evs[3])])
+        torch.cuda.synchronize()
+        if world > 1:
+            tdist.barrier()
+    launches = sdf.kernel_launches() - launches0
+    per = np.array(per)
+    total_ms = float(per.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = band_points * args.steps * world / (total_ms / 1e3)
+    build_ms, fwd_ms, adj_ms = (float(x) for x in per.mean(axis=0))
+
+    # end to end through the public API with host buffers
+    soup_host = torch.from_numpy(soup_np).pin_memory()
+    dist_host = torch.empty(grid.shape, dtype=torch.float32).pin_memory()
+    gv_host = torch.empty(max(1, gv.shape[0] if gv is not None else 1), 3, dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s_dev = soup_host.to(dev, non_blocking=True)
+        f = sdf.sdf_build_features(s_dev)
+        sdf.sdf_narrow_band(f, grid, w, out=dist, winner=win if win is not None else False)
+        if wl["adjoint"]:
+            ge = torch.where(torch.isfinite(dist), 2.0 * (dist - 0.01), torch.zeros_like(dist))
+            gv.zero_()
+            sdf.sdf_narrow_band_backward(f, grid, w, ge, winner=win, grad_vertices=gv)
+            gv_host.copy_(gv, non_blocking=True)
+        dist_host.copy_(dist, non_blocking=True)
+        torch.cuda.synchronize()
+        f.destroy()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": band_points * e2e_steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(soup_np.nbytes),
+           "d2h_bytes_per_step": int(dist.numel() * 4 + (gv.numel() * 4 if gv is not None else 0))}
+
+    hbm, peak_kind = peaks()
+    tile_avg_ms = tile_ms / max(1, tile_calls)
+    alg_bytes = 4 * N ** 3 + (4 * N ** 3 if wl["winner"] else 0) + rec_bytes
+    achieved = alg_bytes / (tile_avg_ms / 1e3) / 1e9
+    roofline = {"kernel": "k_tile (scan conversion + merge + dense write)", "bound": "hbm",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_source": peak_kind, "traffic": None, "algorithmic_bytes": int(alg_bytes),
+                "avg_ms": tile_avg_ms}
+
+    if rank != 0:
+        if world > 1:
+            tdist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(soup_np, N, w)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "triangles": int(soup_np.shape[0]), "grid": [N, N, N], "band_w": w,
+                   "band_points": band_points, "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "build_ms": build_ms, "fwd_ms": fwd_ms, "adjoint_ms": adj_ms if wl["adjoint"] else None,
+        "fwd_adjoint_ms": fwd_ms + adj_ms if wl["adjoint"] else None,
+        "fwd_adjoint_over_fwd": (fwd_ms + adj_ms) / fwd_ms if wl["adjoint"] else None,
+        "candidates_per_band_point": stats["candidates"] / max(1, stats["band_points"]),
+        "fp64_points": stats["fp64_points"],
+        "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(), "e2e": e2e,
+        "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

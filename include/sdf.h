@@ -1,0 +1,210 @@
+/*
+ * sdf.h -- C ABI of the GB300 narrow-band signed distance field library
+ * (Characteristic/Scan Conversion method, Roosing, Strickson & Nikiforakis,
+ * "Fast Distance Fields for Fluid Dynamics Mesh Generation on Graphics
+ * Hardware", arXiv:1903.00353).
+ *
+ * Problem statement (Section 6, Section 7): the input is a closed, oriented
+ * triangulated surface whose triangles list their vertices counter-clockwise
+ * seen from outside, with no gaps, overlaps or flipped faces.  The output is
+ * the signed distance (interior negative, Section 3.1) at every cell centre of
+ * a logically Cartesian grid that lies within a user-given distance w of the
+ * surface (Section 9, Section 10); every other cell holds +infinity
+ * (Algorithm 1 starts from d = infinity).
+ *
+ * Conventions for every call:
+ *   - Pointers are DEVICE pointers unless marked "host".  Float data is FP32.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream) unless stated otherwise; they may synchronise `stream`
+ *     once to read a device status word or a size.
+ *   - The caller owns every input and output buffer.  The library owns the
+ *     sdf_features handle and the scratch memory cached in it, released by
+ *     sdf_features_destroy.  No call keeps a pointer to caller memory after it
+ *     returns.
+ *   - Every call returns an sdf_status; no exception crosses the ABI.  On an
+ *     error the outputs are unspecified.
+ *   - Calls on one handle must not overlap in time (they share its scratch).
+ *
+ * Grid layout (Section 10, a row-major 1D float array): point (i,j,k) sits at
+ * origin + ((i+1/2) h, (j+1/2) h, (k+1/2) h) and is stored at
+ * i + nx*(j + ny*k) (x fastest).
+ *
+ * Feature ids (Section 2: faces, edges and vertices are the features):
+ *   face f in [0, T); edge e -> T + e; vertex v -> T + E + v,
+ * with T triangles, E = 3T/2 unique edges and V unique vertices.  Winner ids
+ * name the feature whose characteristic region produced the stored value;
+ * -1 outside the band.
+ */
+#ifndef GB300_SDF_H
+#define GB300_SDF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sdf_status {
+    SDF_OK = 0,
+    SDF_ERR_INVALID_ARG = 1,  /* null pointer, negative size, bad grid, w <= 0             */
+    SDF_ERR_NONMANIFOLD = 2,  /* an edge is not shared by exactly two oppositely directed
+                                 triangle edges: open, non-manifold or inconsistently
+                                 oriented surface (Section 6 assumes a closed surface)     */
+    SDF_ERR_DEGENERATE = 3,   /* zero-area triangle or zero-length edge (Section 4)        */
+    SDF_ERR_NONFINITE = 4,    /* NaN or infinite coordinate                               */
+    SDF_ERR_TOO_LARGE = 5,    /* sizes beyond the index ranges (2^31 features, 2^31 rows)  */
+    SDF_ERR_OOM = 6,          /* device allocation failed                                 */
+    SDF_ERR_CUDA = 7,         /* a CUDA runtime call failed                               */
+    SDF_ERR_TIMEOUT = 8       /* a bounded device wait gave up (reserved)                 */
+} sdf_status;
+
+/* Grid description (host struct, passed by pointer). */
+typedef struct sdf_grid {
+    int32_t nx, ny, nz;  /* points per axis, each >= 1                        */
+    float origin[3];     /* lower corner of the grid box                      */
+    float h;             /* cell size > 0                                     */
+} sdf_grid;
+
+/* Opaque, library-owned feature set of one mesh. */
+typedef struct sdf_features_s *sdf_features;
+
+/* Flags for sdf_build_features / sdf_narrow_band. */
+#define SDF_FLAG_DISABLE_SADDLE 0x1u /* debug ablation (Section 11.1, Fig. ear): give saddle
+                                        vertices no extrusion; the field then has gaps      */
+#define SDF_FLAG_NO_SYNC 0x2u        /* sdf_narrow_band: skip the final status read; call
+                                        sdf_features_status later (needed inside graphs)     */
+#define SDF_FLAG_TIMING 0x4u         /* record CUDA events on `stream` around the stages of
+                                        sdf_narrow_band / sdf_narrow_band_backward (adds one
+                                        host synchronisation per call); read them with
+                                        sdf_features_timing                                  */
+
+/*
+ * sdf_build_features -- mesh-connectivity stage (Section 7, Section 8).
+ *
+ * From an unordered triangle soup, welds equal vertices by sorting (Section
+ * 7.2; "identical" read as bitwise-equal FP32 coordinates, -0 == +0), pairs
+ * the two directed copies of every edge (Section 7.1), and builds the face,
+ * edge and vertex records: unit face normals, edge convexity
+ * d = (ab x n1) . n2 (Section 8.2), angle-weighted pseudonormals
+ * N_alpha = sum alpha_i n_i (Eq. 8) and the convex / concave / flat / saddle
+ * class of every vertex (Section 3.1, Section 3.2, Section 8.3).
+ *
+ *   soup   device float[n_tri][3][3], corners counter-clockwise seen from
+ *          outside; read only during the call.
+ *   n_tri  number of triangles, 1 <= n_tri < 2^28.
+ *   flags  0 or SDF_FLAG_DISABLE_SADDLE.
+ *   out    host pointer receiving the new handle (NULL on error).
+ *
+ * Synchronises `stream` once (sizes and the status word).  Errors:
+ * SDF_ERR_INVALID_ARG, SDF_ERR_NONFINITE, SDF_ERR_DEGENERATE,
+ * SDF_ERR_NONMANIFOLD, SDF_ERR_TOO_LARGE, SDF_ERR_OOM, SDF_ERR_CUDA.
+ */
+int sdf_build_features(const float *soup, int64_t n_tri, uint32_t flags, void *stream, sdf_features *out);
+
+/*
+ * sdf_features_update_positions -- re-evaluate the geometry of an existing
+ * handle for new welded vertex positions (same connectivity): normals,
+ * pseudonormals, classification and extrusion records (Section 8).  Used by
+ * shape optimisation, where only the positions change between steps.
+ *
+ *   vertices  device float[V][3] in the handle's vertex order (see
+ *             sdf_features_vertices / sdf_features_vertex_map).
+ * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_DEGENERATE (checked at the next
+ * synchronising call), SDF_ERR_CUDA.
+ */
+int sdf_features_update_positions(sdf_features f, const float *vertices, void *stream);
+
+/*
+ * sdf_narrow_band -- extrusion, scan conversion and merge (Sections 5, 8, 9,
+ * 10; Algorithm 1 and Algorithm 2).
+ *
+ * For every feature, builds its characteristic region clipped to distance w
+ * (face prism, edge wedge, vertex region), finds the grid points inside it
+ * row by row (half-space tests against the region's planes, Algorithm 2),
+ * computes the distance of each point to the feature and its sign, and keeps
+ * per point the value of smallest magnitude (Algorithm 1) through a packed
+ * 64-bit atomicMin of (|d| bits, feature id).  Distances and scan conversion
+ * run in FP32; points whose band membership or sign falls inside the FP32
+ * error window are re-decided in FP64 from the winner's neighbourhood.
+ *
+ *   feats       host array [n] of handles.
+ *   grids       host array [n] of grids.
+ *   band_w      host array [n] of band half-widths w > 0 (a point is in the
+ *               band iff |d| < w).
+ *   n           number of (mesh, grid) problems; n > 1 runs them as one batch.
+ *   out_dist    host array [n] of device float[nz][ny][nx] outputs.
+ *   out_winner  host array [n] of device int32[nz][ny][nx] (winner feature
+ *               id, -1 outside the band); the array or any entry may be NULL.
+ *   flags       0 or SDF_FLAG_NO_SYNC.
+ *
+ * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_TOO_LARGE, SDF_ERR_OOM, SDF_ERR_CUDA.
+ */
+int sdf_narrow_band(const sdf_features *feats, const sdf_grid *grids, const float *band_w, int32_t n,
+                    float *const *out_dist, int32_t *const *out_winner, uint32_t flags, void *stream);
+
+/*
+ * sdf_narrow_band_backward -- adjoint of the narrow band with respect to the
+ * welded vertex positions (a project addition; the paper has no adjoint).
+ *
+ * For L with upstream gradient g = dL/dd on the grid, every band point p with
+ * winner feature F and closest point q = sum_k lam_k x_k on F (barycentric on a
+ * face, (1-t, t) on an edge, 1 at a vertex) contributes
+ *     dL/dx_k += -g(p) * s(p) * lam_k * (p - q)/|p - q|,
+ * s = sign d(p): the envelope theorem applied to d = s * min |p - q| (Eq. 1).
+ *
+ *   grad_dist      host array [n] of device float[nz][ny][nx] (dL/dd).
+ *   winner         host array [n] of device int32 winners from the forward, or
+ *                  NULL (array or entry) to recompute them.
+ *   grad_vertices  host array [n] of device float[V][3]; ACCUMULATED into (the
+ *                  caller zeroes it first).
+ * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_OOM, SDF_ERR_CUDA.
+ */
+int sdf_narrow_band_backward(const sdf_features *feats, const sdf_grid *grids, const float *band_w, int32_t n,
+                             const float *const *grad_dist, const int32_t *const *winner,
+                             float *const *grad_vertices, uint32_t flags, void *stream);
+
+/*
+ * sdf_features_info -- sizes and classification counts (host outputs, any may
+ * be NULL).  Table 2 of the paper reports total, unique and saddle vertices.
+ *   counts[0..7] = V, E, convex vertices, concave vertices, flat vertices,
+ *                  saddle vertices, convex edges, concave edges.
+ */
+int sdf_features_info(sdf_features f, int64_t *n_tri, int64_t *counts /* host [8] */);
+
+/* Welded vertex id of every soup corner: device int32[3*n_tri]. */
+int sdf_features_vertex_map(sdf_features f, int32_t *soup_to_vertex, void *stream);
+
+/* Welded vertex positions: device float[V][3]. */
+int sdf_features_vertices(sdf_features f, float *out, void *stream);
+
+/*
+ * Status word and counters of the last sdf_narrow_band on this handle
+ * (synchronises `stream`).  stats (host, nullable) [4] = candidate (point,
+ * region) pairs merged by atomicMin, band points, points re-decided in FP64,
+ * (tile, region) pairs scheduled.
+ */
+int sdf_features_status(sdf_features f, int64_t *stats, void *stream);
+
+/*
+ * Accumulated device time (milliseconds, from CUDA events recorded on the calls' stream) of the
+ * stages of calls made with SDF_FLAG_TIMING, and the number of timed calls:
+ *   ms[0] binning (region boxes -> tiles), ms[1] tile kernel (scan conversion, merge and the
+ *   dense write), ms[2] FP64 re-decision, ms[3] adjoint kernel.  Host outputs [4], nullable.
+ * reset != 0 zeroes the accumulators after reading.
+ */
+int sdf_features_timing(sdf_features f, double *ms, int64_t *calls, int reset);
+
+/* Process-wide number of CUDA kernels this library has launched (diagnostics). */
+int64_t sdf_kernel_launches(void);
+
+/* Release the handle and its device memory (NULL is a no-op). */
+void sdf_features_destroy(sdf_features f);
+
+/* Static description of a status code. */
+const char *sdf_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_SDF_H */

@@ -1,0 +1,275 @@
+"""GB300 narrow-band signed distance fields of closed triangle meshes
+(Characteristic/Scan Conversion method, arXiv:1903.00353).
+
+Thin Python binding of the C ABI declared in include/sdf.h: it marshals torch
+tensors (device memory, the current CUDA stream) into the library's calls and
+does no computation of its own.  Every step of the method runs in the CUDA
+kernels of csrc/.  There is no CPU fallback: without the compiled library or a
+CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Sequence
+
+import torch
+
+from . import _buildlib
+
+__all__ = ["Grid", "Features", "sdf_build_features", "sdf_narrow_band", "sdf_narrow_band_backward",
+           "SDFFunction", "load_library", "kernel_launches", "SDFError", "FLAG_DISABLE_SADDLE", "FLAG_NO_SYNC",
+           "FLAG_TIMING"]
+
+FLAG_DISABLE_SADDLE = 0x1
+FLAG_NO_SYNC = 0x2
+FLAG_TIMING = 0x4
+
+
+class SDFError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {load_library().sdf_status_string(code).decode()} (status {code})")
+
+
+class _CGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("origin", ctypes.c_float * 3), ("h", ctypes.c_float)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load the compiled library (build it first with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _buildlib.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    P, I64, I32, U32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
+    L.sdf_build_features.argtypes = [P, I64, U32, P, ctypes.POINTER(P)]
+    L.sdf_features_update_positions.argtypes = [P, P, P]
+    L.sdf_narrow_band.argtypes = [ctypes.POINTER(P), ctypes.POINTER(_CGrid), ctypes.POINTER(ctypes.c_float), I32,
+                                  ctypes.POINTER(P), ctypes.POINTER(P), U32, P]
+    L.sdf_narrow_band_backward.argtypes = [ctypes.POINTER(P), ctypes.POINTER(_CGrid), ctypes.POINTER(ctypes.c_float),
+                                           I32, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), U32, P]
+    L.sdf_features_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    L.sdf_features_vertex_map.argtypes = [P, P, P]
+    L.sdf_features_vertices.argtypes = [P, P, P]
+    L.sdf_features_status.argtypes = [P, ctypes.POINTER(I64), P]
+    L.sdf_features_destroy.argtypes = [P]
+    L.sdf_features_destroy.restype = None
+    L.sdf_features_timing.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), ctypes.c_int]
+    L.sdf_features_timing.restype = ctypes.c_int
+    L.sdf_kernel_launches.argtypes = []
+    L.sdf_kernel_launches.restype = I64
+    L.sdf_status_string.argtypes = [ctypes.c_int]
+    L.sdf_status_string.restype = ctypes.c_char_p
+    for name in ("sdf_build_features", "sdf_features_update_positions", "sdf_narrow_band",
+                 "sdf_narrow_band_backward", "sdf_features_info", "sdf_features_vertex_map",
+                 "sdf_features_vertices", "sdf_features_status"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def kernel_launches() -> int:
+    """Process-wide number of kernels the library has launched."""
+    return int(load_library().sdf_kernel_launches())
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise SDFError(code, what)
+
+
+def _dev_f32(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    return t
+
+
+@dataclass(frozen=True)
+class Grid:
+    """Cell-centred grid: point (i,j,k) at origin + (i+1/2, j+1/2, k+1/2) h, stored x fastest."""
+    nx: int
+    ny: int
+    nz: int
+    origin: tuple = (0.0, 0.0, 0.0)
+    h: float = 1.0
+
+    @staticmethod
+    def cube(n: int, lo: float = 0.0, hi: float = 1.0) -> "Grid":
+        return Grid(n, n, n, (lo, lo, lo), (hi - lo) / n)
+
+    def c(self) -> _CGrid:
+        g = _CGrid()
+        g.nx, g.ny, g.nz = self.nx, self.ny, self.nz
+        for k in range(3):
+            g.origin[k] = float(self.origin[k])
+        g.h = float(self.h)
+        return g
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+class Features:
+    """Library-owned feature records of one closed mesh (sdf_build_features)."""
+
+    def __init__(self, handle: int, n_tri: int):
+        self._h = ctypes.c_void_p(handle)
+        self.n_tri = n_tri
+        n = ctypes.c_int64()
+        c = (ctypes.c_int64 * 8)()
+        _check(load_library().sdf_features_info(self._h, ctypes.byref(n), c), "sdf_features_info")
+        self.counts = [int(x) for x in c]
+        self.n_vert, self.n_edge = self.counts[0], self.counts[1]
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("features destroyed")
+        return self._h
+
+    def vertex_map(self) -> torch.Tensor:
+        out = torch.empty(3 * self.n_tri, dtype=torch.int32, device="cuda")
+        _check(load_library().sdf_features_vertex_map(self.handle, out.data_ptr(), _stream()), "vertex_map")
+        return out
+
+    def vertices(self) -> torch.Tensor:
+        out = torch.empty(self.n_vert, 3, dtype=torch.float32, device="cuda")
+        _check(load_library().sdf_features_vertices(self.handle, out.data_ptr(), _stream()), "vertices")
+        return out
+
+    def update_positions(self, vertices: torch.Tensor):
+        v = _dev_f32(vertices, "vertices")
+        if v.shape != (self.n_vert, 3):
+            raise ValueError("vertices must be [V, 3]")
+        _check(load_library().sdf_features_update_positions(self.handle, v.data_ptr(), _stream()),
+               "sdf_features_update_positions")
+
+    def status(self):
+        st = (ctypes.c_int64 * 4)()
+        code = load_library().sdf_features_status(self.handle, st, _stream())
+        _check(code, "sdf_features_status")
+        return {"candidates": int(st[0]), "band_points": int(st[1]), "fp64_points": int(st[2])}
+
+    def timing(self, reset: bool = False):
+        """Accumulated stage times (ms) of calls made with FLAG_TIMING: bin, tile, fp64, adjoint."""
+        ms = (ctypes.c_double * 4)()
+        calls = (ctypes.c_int64 * 4)()
+        _check(load_library().sdf_features_timing(self.handle, ms, calls, int(reset)), "sdf_features_timing")
+        names = ("bin", "tile", "fp64", "adjoint")
+        return {n: (float(ms[i]), int(calls[i])) for i, n in enumerate(names)}
+
+    def destroy(self):
+        if self._h is not None and _lib is not None:
+            _lib.sdf_features_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def sdf_build_features(soup: torch.Tensor, flags: int = 0, stream=None) -> Features:
+    """Weld, pair and build feature records from a float32 CUDA soup [T, 3, 3]."""
+    s = _dev_f32(soup, "soup")
+    if s.dim() != 3 or s.shape[1:] != (3, 3):
+        raise ValueError("soup must be [T, 3, 3]")
+    h = ctypes.c_void_p()
+    _check(load_library().sdf_build_features(s.data_ptr(), s.shape[0], flags, _stream(stream), ctypes.byref(h)),
+           "sdf_build_features")
+    return Features(h.value, s.shape[0])
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = None if t is None else t.data_ptr()
+    return arr
+
+
+def sdf_narrow_band(features: Features | Sequence[Features], grid: Grid | Sequence[Grid], w,
+                    out: torch.Tensor | Sequence[torch.Tensor] | None = None, winner: bool | Sequence = False,
+                    flags: int = 0, stream=None):
+    """Narrow-band SDF on one grid (or a batch when lists are given).
+
+    Returns dist [nz, ny, nx] (and winner ids when winner=True); lists for a batch."""
+    batch = isinstance(features, (list, tuple))
+    feats = list(features) if batch else [features]
+    grids = list(grid) if batch else [grid]
+    ws = list(w) if batch else [w]
+    n = len(feats)
+    if not (len(grids) == len(ws) == n):
+        raise ValueError("features, grid and w must have the same length")
+    if out is None:
+        outs = [torch.empty(g.shape, dtype=torch.float32, device="cuda") for g in grids]
+    else:
+        outs = list(out) if batch else [out]
+        for o, g in zip(outs, grids):
+            _dev_f32(o, "out")
+            if o.numel() != g.nx * g.ny * g.nz:
+                raise ValueError("out has the wrong size")
+    if isinstance(winner, (list, tuple)):
+        wins = list(winner)
+    elif winner:
+        wins = [torch.empty(g.shape, dtype=torch.int32, device="cuda") for g in grids]
+    else:
+        wins = [None] * n
+    fa = (ctypes.c_void_p * n)(*[f.handle.value for f in feats])
+    ga = (_CGrid * n)(*[g.c() for g in grids])
+    wa = (ctypes.c_float * n)(*[float(x) for x in ws])
+    _check(load_library().sdf_narrow_band(fa, ga, wa, n, _ptr_array(outs), _ptr_array(wins), flags,
+                                          _stream(stream)), "sdf_narrow_band")
+    res = [(o, wn) if wn is not None else o for o, wn in zip(outs, wins)]
+    return res if batch else res[0]
+
+
+def sdf_narrow_band_backward(features: Features, grid: Grid, w: float, grad_dist: torch.Tensor,
+                             winner: torch.Tensor | None = None, grad_vertices: torch.Tensor | None = None,
+                             flags: int = 0, stream=None) -> torch.Tensor:
+    """dL/d(welded vertices) [V, 3] for upstream dL/dd on the grid; accumulates into grad_vertices."""
+    g = _dev_f32(grad_dist, "grad_dist")
+    if grad_vertices is None:
+        grad_vertices = torch.zeros(features.n_vert, 3, dtype=torch.float32, device="cuda")
+    fa = (ctypes.c_void_p * 1)(features.handle.value)
+    ga = (_CGrid * 1)(grid.c())
+    wa = (ctypes.c_float * 1)(float(w))
+    _check(load_library().sdf_narrow_band_backward(fa, ga, wa, 1, _ptr_array([g]),
+                                                   _ptr_array([winner]) if winner is not None else None,
+                                                   _ptr_array([grad_vertices]), flags, _stream(stream)),
+           "sdf_narrow_band_backward")
+    return grad_vertices
+
+
+class SDFFunction(torch.autograd.Function):
+    """dist = SDFFunction.apply(vertices [V,3], features, grid, w): the narrow band of the mesh with
+    the features' connectivity at the given welded vertex positions; differentiable in vertices."""
+
+    @staticmethod
+    def forward(ctx, vertices, features: Features, grid: Grid, w: float):
+        features.update_positions(vertices.detach().contiguous())
+        dist, win = sdf_narrow_band(features, grid, w, winner=True)
+        ctx.features, ctx.grid, ctx.w = features, grid, w
+        ctx.save_for_backward(win)
+        return dist
+
+    @staticmethod
+    def backward(ctx, grad_dist):
+        (win,) = ctx.saved_tensors
+        gv = sdf_narrow_band_backward(ctx.features, ctx.grid, ctx.w, grad_dist.contiguous(), winner=win)
+        return gv, None, None, None

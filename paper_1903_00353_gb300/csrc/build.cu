@@ -1,0 +1,570 @@
+// Mesh-connectivity stage and feature records (Sections 7 and 8 of the paper).
+//
+//   soup --(bounds, weld keys)--> radix sort --> vertex runs --> welded vertices + CSR of corners
+//        --(edge keys)--> radix sort --> paired half-edges --> unique edges (va, vb, f1, f2)
+//        --> face / edge / vertex records (normals, side planes, pseudonormals, classes)
+//
+// Welding (Section 7.2).  The paper sorts 30-bit Morton codes and then groups identical
+// vertices serially inside each equal-code run.  Here the sort key is the 30-bit Morton
+// code of the quantised position (over the soup's bounding box, Section 7.1) in the high
+// bits and a 34-bit hash of the exact coordinate bits in the low bits, so equal vertices
+// always share a key and distinct vertices almost never do.  Runs of equal keys holding
+// different coordinates (hash collisions) are re-ordered by exact coordinates by one
+// thread per such run, the only serial step left of the paper's fix-up.
+//
+// Edge pairing (Section 7.1): each directed triangle edge gets the key
+// (min vid, max vid); after sorting, each key must occur exactly twice with opposite
+// directions, else the surface is not a closed oriented 2-manifold.
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <algorithm>
+
+#include "sdf_internal.cuh"
+
+namespace sdf {
+namespace {
+
+constexpr int BT = 256;
+
+__device__ __forceinline__ void atomic_min_f(float *a, float v) {
+    if (v >= 0.f) atomicMin(reinterpret_cast<int *>(a), __float_as_int(v));
+    else atomicMax(reinterpret_cast<unsigned *>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_f(float *a, float v) {
+    if (v >= 0.f) atomicMax(reinterpret_cast<int *>(a), __float_as_int(v));
+    else atomicMin(reinterpret_cast<unsigned *>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ float canon_zero(float x) { return x == 0.f ? 0.f : x; }  // -0 -> +0
+
+// ----------------------------------------------------------------------------- soup bounds + finiteness
+__global__ void k_soup_bounds(const float *soup, int64_t n3, float *bb, DevCounters *ctr) {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n3; s += (int64_t)gridDim.x * blockDim.x) {
+        for (int j = 0; j < 3; j++) {
+            float x = soup[3 * s + j];
+            if (!isfinite(x)) bad = true;
+            else { lo[j] = fminf(lo[j], x); hi[j] = fmaxf(hi[j], x); }
+        }
+    }
+    if (bad) atomicOr(&ctr->status, ST_NONFINITE);
+    for (int j = 0; j < 3; j++) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[j] = fminf(lo[j], __shfl_xor_sync(0xffffffffu, lo[j], o));
+            hi[j] = fmaxf(hi[j], __shfl_xor_sync(0xffffffffu, hi[j], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int j = 0; j < 3; j++) {
+            if (lo[j] <= hi[j]) { atomic_min_f(bb + j, lo[j]); atomic_max_f(bb + 3 + j, hi[j]); }
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t expand10(uint32_t x) {  // spread 10 bits to every third bit
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000ffu;
+    x = (x | (x << 8)) & 0x0300f00fu;
+    x = (x | (x << 4)) & 0x030c30c3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {  // SplitMix64 finaliser
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_weld_keys(const float *soup, int64_t n3, const float *bb, uint64_t *keys, uint32_t *vals) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n3) return;
+    float x = canon_zero(soup[3 * s]), y = canon_zero(soup[3 * s + 1]), z = canon_zero(soup[3 * s + 2]);
+    uint32_t q[3];
+    float c[3] = {x, y, z};
+    for (int j = 0; j < 3; j++) {
+        float ext = bb[3 + j] - bb[j];
+        float t = ext > 0.f ? (c[j] - bb[j]) / ext * 1024.f : 0.f;
+        int qi = (int)t;
+        q[j] = (uint32_t)min(max(qi, 0), 1023);
+    }
+    uint64_t morton = (uint64_t)(expand10(q[0]) | (expand10(q[1]) << 1) | (expand10(q[2]) << 2));
+    uint64_t hsh = mix64(((uint64_t)__float_as_uint(x) << 32 | __float_as_uint(y)) ^ mix64(__float_as_uint(z) + 0x9e3779b97f4a7c15ull));
+    keys[s] = (morton << 34) | (hsh & ((1ull << 34) - 1));
+    vals[s] = (uint32_t)s;
+}
+
+__device__ __forceinline__ bool same_xyz(const float *soup, uint32_t a, uint32_t b) {
+    return canon_zero(soup[3 * (int64_t)a]) == canon_zero(soup[3 * (int64_t)b]) &&
+           canon_zero(soup[3 * (int64_t)a + 1]) == canon_zero(soup[3 * (int64_t)b + 1]) &&
+           canon_zero(soup[3 * (int64_t)a + 2]) == canon_zero(soup[3 * (int64_t)b + 2]);
+}
+__device__ __forceinline__ bool less_xyz(const float *soup, uint32_t a, uint32_t b) {
+    for (int j = 0; j < 3; j++) {
+        uint32_t ua = __float_as_uint(canon_zero(soup[3 * (int64_t)a + j]));
+        uint32_t ub = __float_as_uint(canon_zero(soup[3 * (int64_t)b + j]));
+        if (ua != ub) return ua < ub;
+    }
+    return a < b;
+}
+
+// one thread per run of equal keys: if the run mixes distinct coordinates (hash collision),
+// insertion-sort it by (coordinate bits, soup index) so equal vertices become contiguous
+__global__ void k_weld_fix(const uint64_t *keys, uint32_t *vals, const float *soup, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || (i > 0 && keys[i] == keys[i - 1])) return;
+    int64_t e = i + 1;
+    bool mixed = false;
+    while (e < n && keys[e] == keys[i]) {
+        mixed |= !same_xyz(soup, vals[e], vals[i]);
+        e++;
+    }
+    if (!mixed) return;
+    for (int64_t a = i + 1; a < e; a++) {
+        uint32_t v = vals[a];
+        int64_t b = a - 1;
+        while (b >= i && less_xyz(soup, v, vals[b])) { vals[b + 1] = vals[b]; b--; }
+        vals[b + 1] = v;
+    }
+}
+
+__global__ void k_weld_heads(const uint64_t *keys, const uint32_t *vals, const float *soup, int64_t n,
+                             uint32_t *head) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    head[i] = (i == 0 || keys[i] != keys[i - 1] || !same_xyz(soup, vals[i], vals[i - 1])) ? 1u : 0u;
+}
+
+// head[] holds the exclusive scan of the run heads; vid = that + is_head - 1
+__global__ void k_weld_scatter(const uint32_t *vals, const uint32_t *hscan, const uint64_t *keys, const float *soup,
+                               int64_t n, int32_t *soup_vid, int32_t *vert_start, int32_t *vert_corner,
+                               float *vpos) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool is_head = hscan[i + 1] != hscan[i];
+    int32_t vid = (int32_t)hscan[i + 1] - 1;
+    uint32_t s = vals[i];
+    soup_vid[s] = vid;
+    vert_corner[i] = (int32_t)s;
+    if (is_head) {
+        vert_start[vid] = (int32_t)i;
+        for (int j = 0; j < 3; j++) vpos[3 * vid + j] = canon_zero(soup[3 * (int64_t)s + j]);
+    }
+    if (i == n - 1) vert_start[vid + 1] = (int32_t)n;
+}
+
+__global__ void k_edge_keys(const int32_t *soup_vid, int64_t n, int nb, uint64_t *keys, uint32_t *vals,
+                            DevCounters *ctr) {
+    int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (h >= n) return;
+    int64_t f = h / 3;
+    int k = (int)(h - 3 * f);
+    uint32_t a = (uint32_t)soup_vid[h], b = (uint32_t)soup_vid[3 * f + (k + 1) % 3];
+    if (a == b) atomicOr(&ctr->status, ST_DEGENERATE);
+    uint32_t lo = min(a, b), hi = max(a, b);
+    keys[h] = ((uint64_t)lo << nb) | hi;
+    vals[h] = (uint32_t)h;
+}
+
+__global__ void k_edge_pair(const uint64_t *keys, const uint32_t *vals, const int32_t *soup_vid, int64_t n,
+                            int4 *edge_vf, int32_t *face_edge, DevCounters *ctr) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n / 2) return;
+    int64_t i = 2 * e;
+    bool ok = keys[i] == keys[i + 1] && (i + 2 >= n || keys[i + 2] != keys[i]) && (i == 0 || keys[i - 1] != keys[i]);
+    uint32_t h0 = vals[i], h1 = vals[i + 1];
+    int32_t a0 = soup_vid[h0], a1 = soup_vid[h1];
+    ok = ok && a0 != a1;  // the two copies must run in opposite directions
+    if (!ok) {
+        atomicOr(&ctr->status, ST_NONMANIFOLD);
+        return;
+    }
+    // f1 holds the direction va -> vb with va < vb
+    uint32_t hf1 = a0 < a1 ? h0 : h1, hf2 = a0 < a1 ? h1 : h0;
+    int32_t va = min(a0, a1), vb = max(a0, a1);
+    edge_vf[e] = make_int4(va, vb, (int32_t)(hf1 / 3), (int32_t)(hf2 / 3));
+    face_edge[h0] = (int32_t)e;
+    face_edge[h1] = (int32_t)e;
+}
+
+// ----------------------------------------------------------------------------- records (geometry)
+// FP64 check of a (filtered) zero-area predicate
+__device__ bool degenerate_fp64(float3 a, float3 b, float3 c) {
+    double3 e1 = d3(b) - d3(a), e2 = d3(c) - d3(a);
+    double3 cr = dcross3(e1, e2);
+    double len = sqrt(ddot3(cr, cr));
+    return !(len > 1e-14 * (ddot3(e1, e1) + ddot3(e2, e2)));
+}
+
+__device__ __forceinline__ float4 plane_through(float3 m, float3 p) {  // (m, -m.p): value m.x + w
+    return make_float4(m.x, m.y, m.z, -dot3(m, p));
+}
+__device__ __forceinline__ float3 normalized(float3 v) {
+    float r = rsqrtf(dot3(v, v));
+    return r * v;
+}
+
+__global__ void k_face_records(const int32_t *face_vid, const float *vpos, int64_t T, float4 *face_rec,
+                               float4 *face_box, DevCounters *ctr) {
+    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= T) return;
+    float3 a = load_vpos(vpos, face_vid[3 * f]), b = load_vpos(vpos, face_vid[3 * f + 1]),
+           c = load_vpos(vpos, face_vid[3 * f + 2]);
+    float3 e1 = b - a, e2 = c - a;
+    float3 cr = cross3(e1, e2);
+    float len2 = dot3(cr, cr);
+    float scale = dot3(e1, e1) + dot3(e2, e2);
+    if (!(len2 > 1e-10f * scale * scale) && degenerate_fp64(a, b, c)) {
+        atomicOr(&ctr->status, ST_DEGENERATE);
+        len2 = fmaxf(len2, 1e-30f);
+    }
+    float3 n = rsqrtf(len2) * cr;
+    // plane of the face, and the three side planes with inward normals n x (edge) (Section 8.1)
+    face_rec[4 * f + 0] = make_float4(n.x, n.y, n.z, -dot3(n, a));
+    face_rec[4 * f + 1] = plane_through(normalized(cross3(n, b - a)), a);
+    face_rec[4 * f + 2] = plane_through(normalized(cross3(n, c - b)), b);
+    face_rec[4 * f + 3] = plane_through(normalized(cross3(n, a - c)), c);
+    face_box[2 * f + 0] = make_float4(fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)),
+                                      fminf(a.z, fminf(b.z, c.z)), 0.f);
+    face_box[2 * f + 1] = make_float4(fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)),
+                                      fmaxf(a.z, fmaxf(b.z, c.z)), 0.f);
+}
+
+__device__ double3 face_normal_fp64(const int32_t *face_vid, const float *vpos, int f) {
+    double3 a = d3(load_vpos(vpos, face_vid[3 * f])), b = d3(load_vpos(vpos, face_vid[3 * f + 1])),
+            c = d3(load_vpos(vpos, face_vid[3 * f + 2]));
+    double3 cr = dcross3(b - a, c - a);
+    return (1.0 / sqrt(ddot3(cr, cr))) * cr;
+}
+
+// edge wedge (Section 8.2): unit direction t (va -> vb, the direction in face f1), the planes
+// (p - a).m1 <= 0 and (p - a).m2 <= 0 with m1 = n1 x t into face 1 and m2 = n2 x (-t) into face 2,
+// and the edge pseudonormal n1 + n2.  Class from d = (ab x n1) . n2 (FP32, FP64 when near zero).
+__global__ void k_edge_records(const int4 *edge_vf, const int32_t *face_vid, const float *vpos,
+                               const float4 *face_rec, int64_t E, float4 *edge_rec, int8_t *edge_class,
+                               DevCounters *ctr) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    int4 q = edge_vf[e];
+    float3 a = load_vpos(vpos, q.x), b = load_vpos(vpos, q.y);
+    float3 n1 = f3(face_rec[4 * q.z]), n2 = f3(face_rec[4 * q.w]);
+    float3 ab = b - a;
+    float L = sqrtf(dot3(ab, ab));
+    float3 t = (1.f / L) * ab;
+    float3 m1 = normalized(cross3(n1, t));
+    float3 m2 = normalized(cross3(n2, make_float3(-t.x, -t.y, -t.z)));
+    float3 np = n1 + n2;
+    edge_rec[5 * e + 0] = make_float4(a.x, a.y, a.z, L);
+    edge_rec[5 * e + 1] = make_float4(t.x, t.y, t.z, dot3(t, a));
+    edge_rec[5 * e + 2] = make_float4(-m1.x, -m1.y, -m1.z, dot3(m1, a));
+    edge_rec[5 * e + 3] = make_float4(-m2.x, -m2.y, -m2.z, dot3(m2, a));
+    edge_rec[5 * e + 4] = make_float4(np.x, np.y, np.z, 0.f);
+    float d = dot3(cross3(t, n1), n2);
+    int8_t cls;
+    if (fabsf(d) > 1e-5f) {
+        cls = d > 0.f ? CLS_CONVEX : CLS_CONCAVE;
+    } else {  // filtered predicate: decide near-flat edges in FP64
+        double3 A = d3(a), B = d3(b);
+        double3 N1 = face_normal_fp64(face_vid, vpos, q.z), N2 = face_normal_fp64(face_vid, vpos, q.w);
+        double3 AB = B - A;
+        double dd = ddot3(dcross3(AB, N1), N2);
+        double tol = 1e-12 * sqrt(ddot3(AB, AB));
+        cls = dd > tol ? CLS_CONVEX : (dd < -tol ? CLS_CONCAVE : CLS_FLAT);
+    }
+    edge_class[e] = cls;
+    if (cls == CLS_CONVEX) atomicAdd(&ctr->cls[6], 1ull);
+    else if (cls == CLS_CONCAVE) atomicAdd(&ctr->cls[7], 1ull);
+}
+
+__device__ __forceinline__ float corner_angle(float3 e1, float3 e2) {
+    float3 cr = cross3(e1, e2);
+    return atan2f(sqrtf(dot3(cr, cr)), dot3(e1, e2));
+}
+
+// vertex records (Section 8.3): N_alpha = sum alpha_i n_i (Eq. 8), one plane (p - v).e_j <= 0 per
+// incident edge (the region where no incident edge leads closer than v), and the class from the
+// signs of (v_n - v).N_alpha over the neighbours (FP32 when clear, FP64 otherwise).
+__global__ void k_vertex_records(const int32_t *vert_start, const int32_t *vert_corner, const int32_t *face_vid,
+                                 const float *vpos, const float4 *face_rec, int64_t V, float4 *vert_rec,
+                                 float4 *vert_plane, int8_t *vert_class, DevCounters *ctr) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    int s0 = vert_start[v], s1 = vert_start[v + 1];
+    float3 p = load_vpos(vpos, (int)v);
+    float3 N = make_float3(0.f, 0.f, 0.f);
+    for (int i = s0; i < s1; i++) {
+        int c = vert_corner[i];
+        int f = c / 3, k = c - 3 * f;
+        float3 xn = load_vpos(vpos, face_vid[3 * f + (k + 1) % 3]);
+        float3 xp = load_vpos(vpos, face_vid[3 * f + (k + 2) % 3]);
+        float3 e1 = xn - p, e2 = xp - p;
+        N = N + corner_angle(e1, e2) * f3(face_rec[4 * f]);
+        float3 ej = normalized(e1);
+        vert_plane[i] = make_float4(-ej.x, -ej.y, -ej.z, dot3(ej, p));
+    }
+    float Nlen = sqrtf(dot3(N, N));
+    bool below = false, above = false, unsure = false;
+    for (int i = s0; i < s1; i++) {
+        int c = vert_corner[i];
+        int f = c / 3, k = c - 3 * f;
+        float3 dv = load_vpos(vpos, face_vid[3 * f + (k + 1) % 3]) - p;
+        float d = dot3(dv, N);
+        float bound = 1e-5f * sqrtf(dot3(dv, dv)) * Nlen;
+        if (d < -bound) below = true;
+        else if (d > bound) above = true;
+        else unsure = true;
+    }
+    if (unsure) {  // FP64 filtered predicate
+        below = above = false;
+        double3 P = d3(p), ND = make_double3(0, 0, 0);
+        for (int i = s0; i < s1; i++) {
+            int c = vert_corner[i];
+            int f = c / 3, k = c - 3 * f;
+            double3 e1 = d3(load_vpos(vpos, face_vid[3 * f + (k + 1) % 3])) - P;
+            double3 e2 = d3(load_vpos(vpos, face_vid[3 * f + (k + 2) % 3])) - P;
+            double3 cr = dcross3(e1, e2);
+            double alpha = atan2(sqrt(ddot3(cr, cr)), ddot3(e1, e2));
+            ND = ND + alpha * face_normal_fp64(face_vid, vpos, f);
+        }
+        double NL = sqrt(ddot3(ND, ND));
+        for (int i = s0; i < s1; i++) {
+            int c = vert_corner[i];
+            int f = c / 3, k = c - 3 * f;
+            double3 dv = d3(load_vpos(vpos, face_vid[3 * f + (k + 1) % 3])) - P;
+            double d = ddot3(dv, ND);
+            double tol = 1e-12 * sqrt(ddot3(dv, dv)) * NL;
+            if (d < -tol) below = true;
+            else if (d > tol) above = true;
+        }
+    }
+    int8_t cls = below && above ? CLS_SADDLE : (below ? CLS_CONVEX : (above ? CLS_CONCAVE : CLS_FLAT));
+    vert_class[v] = cls;
+    float3 Nu = (1.f / Nlen) * N;
+    vert_rec[2 * v + 0] = make_float4(p.x, p.y, p.z, __int_as_float(s0));
+    vert_rec[2 * v + 1] = make_float4(Nu.x, Nu.y, Nu.z, __int_as_float(s1 - s0));
+    atomicAdd(&ctr->cls[cls == CLS_CONVEX ? 2 : (cls == CLS_CONCAVE ? 3 : (cls == CLS_FLAT ? 4 : 5))], 1ull);
+}
+
+inline unsigned nblk(int64_t n) { return (unsigned)((n + BT - 1) / BT); }
+
+}  // namespace
+
+int build_records(sdf_features_s *f, cudaStream_t s) {
+    if (f->T > 0) {
+        k_face_records<<<nblk(f->T), BT, 0, s>>>(f->face_vid, f->vpos, f->T, f->face_rec, f->face_box, f->ctr);
+        SDF_LAUNCHED(1);
+        k_edge_records<<<nblk(f->E), BT, 0, s>>>(f->edge_vf, f->face_vid, f->vpos, f->face_rec, f->E, f->edge_rec,
+                                                f->edge_class, f->ctr);
+        SDF_LAUNCHED(1);
+        k_vertex_records<<<nblk(f->V), BT, 0, s>>>(f->vert_start, f->vert_corner, f->face_vid, f->vpos, f->face_rec,
+                                                  f->V, f->vert_rec, f->vert_plane, f->vert_class, f->ctr);
+        SDF_LAUNCHED(1);
+    }
+    SDF_TRY(cudaGetLastError());
+    return SDF_OK;
+}
+
+}  // namespace sdf
+
+using namespace sdf;
+
+static int status_to_code(unsigned st) {
+    if (st & ST_NONFINITE) return SDF_ERR_NONFINITE;
+    if (st & ST_DEGENERATE) return SDF_ERR_DEGENERATE;
+    if (st & ST_NONMANIFOLD) return SDF_ERR_NONMANIFOLD;
+    return SDF_OK;
+}
+
+static void free_handle(sdf_features_s *f) {
+    if (!f) return;
+    void *ptrs[] = {f->face_vid, f->face_edge, f->edge_vf, f->vert_start, f->vert_corner, f->vpos, f->face_rec,
+                    f->face_box, f->edge_rec, f->vert_rec, f->vert_plane, f->edge_class, f->vert_class, f->ctr};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    f->bins.release();
+    f->pairs.release();
+    f->patch.release();
+    f->scan_tmp.release();
+    f->fwd_winner.release();
+    for (cudaEvent_t e : f->ev)
+        if (e) cudaEventDestroy(e);
+    delete f;
+}
+
+template <class T> static cudaError_t dalloc(T **p, int64_t n) {
+    return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (size_t)(n > 0 ? n : 1));
+}
+
+#define B_TRY(expr)                                       \
+    do {                                                  \
+        cudaError_t e_ = (expr);                          \
+        if (e_ != cudaSuccess) {                          \
+            tmp.release();                                \
+            free_handle(f);                               \
+            return e_ == cudaErrorMemoryAllocation ? SDF_ERR_OOM : SDF_ERR_CUDA; \
+        }                                                 \
+    } while (0)
+
+extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t flags, void *stream, sdf_features *out) {
+    if (!out) return SDF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!soup || n_tri <= 0) return SDF_ERR_INVALID_ARG;
+    if (n_tri >= (int64_t(1) << 28)) return SDF_ERR_TOO_LARGE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t T = n_tri, n = 3 * T;
+    sdf_features_s *f = new sdf_features_s();
+    f->T = T;
+    f->flags = flags;
+    DevBuf tmp;
+    // scratch: keys, vals (+ alternates), heads/scan, sort and scan temporaries, bounds
+    size_t off_keys = 0, off_kalt = off_keys + 8 * n, off_vals = off_kalt + 8 * n, off_valt = off_vals + 4 * n,
+           off_head = off_valt + 4 * n, off_bb = off_head + 4 * (n + 1) + 64, off_rtmp = off_bb + 64;
+    size_t need = off_rtmp + radix_tmp_bytes(n) + scan_tmp_bytes(n + 1) + 1024;
+    B_TRY(tmp.reserve(need));
+    char *base = tmp.as<char>();
+    uint64_t *keys = reinterpret_cast<uint64_t *>(base + off_keys), *kalt = reinterpret_cast<uint64_t *>(base + off_kalt);
+    uint32_t *vals = reinterpret_cast<uint32_t *>(base + off_vals), *valt = reinterpret_cast<uint32_t *>(base + off_valt);
+    uint32_t *head = reinterpret_cast<uint32_t *>(base + off_head);
+    float *bb = reinterpret_cast<float *>(base + off_bb);
+    void *rtmp = base + off_rtmp;
+
+    B_TRY(dalloc(&f->ctr, 1));
+    B_TRY(cudaMemsetAsync(f->ctr, 0, sizeof(DevCounters), s));
+    float bb_init[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    B_TRY(cudaMemcpyAsync(bb, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
+    k_soup_bounds<<<(unsigned)std::min<int64_t>(nblk(n), 4 * 152), BT, 0, s>>>(soup, n, bb, f->ctr);
+    SDF_LAUNCHED(1);
+    k_weld_keys<<<nblk(n), BT, 0, s>>>(soup, n, bb, keys, vals);
+    SDF_LAUNCHED(1);
+    B_TRY(cudaGetLastError());
+    B_TRY(radix_sort_u64(keys, vals, kalt, valt, n, 64, rtmp, s));
+    k_weld_fix<<<nblk(n), BT, 0, s>>>(keys, vals, soup, n);
+    SDF_LAUNCHED(1);
+    k_weld_heads<<<nblk(n), BT, 0, s>>>(keys, vals, soup, n, valt);
+    SDF_LAUNCHED(1);
+    B_TRY(cudaGetLastError());
+    // head[i] = number of run heads before i, head[n] = V (so head[i+1] is the inclusive count at i)
+    B_TRY(scan_exclusive_u32(valt, head, n, true, rtmp, s));
+    uint32_t Vh = 0;
+    unsigned st_h = 0;
+    B_TRY(cudaMemcpyAsync(&Vh, head + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaMemcpyAsync(&st_h, &f->ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaStreamSynchronize(s));
+    if (st_h) {
+        tmp.release();
+        free_handle(f);
+        return status_to_code(st_h);
+    }
+    const int64_t V = Vh;
+    f->V = V;
+    B_TRY(dalloc(&f->face_vid, n));
+    B_TRY(dalloc(&f->face_edge, n));
+    B_TRY(dalloc(&f->vert_start, V + 1));
+    B_TRY(dalloc(&f->vert_corner, n));
+    B_TRY(dalloc(&f->vpos, 3 * V));
+    k_weld_scatter<<<nblk(n), BT, 0, s>>>(vals, head, keys, soup, n, f->face_vid, f->vert_start, f->vert_corner,
+                                          f->vpos);
+    SDF_LAUNCHED(1);
+    B_TRY(cudaGetLastError());
+    // edge pairing
+    if (n % 2) {
+        tmp.release();
+        free_handle(f);
+        return SDF_ERR_NONMANIFOLD;
+    }
+    int nb = 1;
+    while ((int64_t(1) << nb) < V) nb++;
+    const int64_t E = n / 2;
+    f->E = E;
+    k_edge_keys<<<nblk(n), BT, 0, s>>>(f->face_vid, n, nb, keys, vals, f->ctr);
+    SDF_LAUNCHED(1);
+    B_TRY(cudaGetLastError());
+    B_TRY(radix_sort_u64(keys, vals, kalt, valt, n, 2 * nb, rtmp, s));
+    B_TRY(dalloc(&f->edge_vf, E));
+    k_edge_pair<<<nblk(E), BT, 0, s>>>(keys, vals, f->face_vid, n, f->edge_vf, f->face_edge, f->ctr);
+    SDF_LAUNCHED(1);
+    B_TRY(cudaGetLastError());
+    // records
+    B_TRY(dalloc(&f->face_rec, 4 * T));
+    B_TRY(dalloc(&f->face_box, 2 * T));
+    B_TRY(dalloc(&f->edge_rec, 5 * E));
+    B_TRY(dalloc(&f->edge_class, E));
+    B_TRY(dalloc(&f->vert_rec, 2 * V));
+    B_TRY(dalloc(&f->vert_plane, n));
+    B_TRY(dalloc(&f->vert_class, V));
+    unsigned st = 0;
+    B_TRY(cudaMemcpyAsync(&st, &f->ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaStreamSynchronize(s));
+    if (st) {  // do not evaluate geometry on broken connectivity
+        tmp.release();
+        free_handle(f);
+        return status_to_code(st);
+    }
+    if (build_records(f, s) != SDF_OK) B_TRY(cudaErrorUnknown);
+    DevCounters c;
+    B_TRY(cudaMemcpyAsync(&c, f->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaStreamSynchronize(s));
+    tmp.release();
+    if (c.status) {
+        int code = status_to_code(c.status);
+        free_handle(f);
+        return code;
+    }
+    f->counts[0] = V;
+    f->counts[1] = E;
+    for (int i = 2; i < 8; i++) f->counts[i] = (int64_t)c.cls[i];
+    *out = f;
+    return SDF_OK;
+}
+
+extern "C" int sdf_features_update_positions(sdf_features f, const float *vertices, void *stream) {
+    if (!f || !vertices) return SDF_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    SDF_TRY(cudaMemcpyAsync(f->vpos, vertices, sizeof(float) * 3 * f->V, cudaMemcpyDeviceToDevice, s));
+    SDF_TRY(cudaMemsetAsync(f->ctr->cls, 0, sizeof(f->ctr->cls), s));
+    return build_records(f, s);
+}
+
+extern "C" void sdf_features_destroy(sdf_features f) {
+    if (!f) return;
+    cudaDeviceSynchronize();
+    free_handle(f);
+}
+
+extern "C" int sdf_features_info(sdf_features f, int64_t *n_tri, int64_t *counts) {
+    if (!f) return SDF_ERR_INVALID_ARG;
+    if (n_tri) *n_tri = f->T;
+    if (counts)
+        for (int i = 0; i < 8; i++) counts[i] = f->counts[i];
+    return SDF_OK;
+}
+
+extern "C" int sdf_features_vertex_map(sdf_features f, int32_t *soup_to_vertex, void *stream) {
+    if (!f || !soup_to_vertex) return SDF_ERR_INVALID_ARG;
+    SDF_TRY(cudaMemcpyAsync(soup_to_vertex, f->face_vid, sizeof(int32_t) * 3 * f->T, cudaMemcpyDeviceToDevice,
+                            reinterpret_cast<cudaStream_t>(stream)));
+    return SDF_OK;
+}
+
+extern "C" int sdf_features_vertices(sdf_features f, float *outp, void *stream) {
+    if (!f || !outp) return SDF_ERR_INVALID_ARG;
+    SDF_TRY(cudaMemcpyAsync(outp, f->vpos, sizeof(float) * 3 * f->V, cudaMemcpyDeviceToDevice,
+                            reinterpret_cast<cudaStream_t>(stream)));
+    return SDF_OK;
+}
+
+extern "C" const char *sdf_status_string(int status) {
+    switch (status) {
+    case SDF_OK: return "ok";
+    case SDF_ERR_INVALID_ARG: return "invalid argument";
+    case SDF_ERR_NONMANIFOLD: return "surface is not a closed, consistently oriented 2-manifold";
+    case SDF_ERR_DEGENERATE: return "degenerate triangle or edge";
+    case SDF_ERR_NONFINITE: return "non-finite coordinate";
+    case SDF_ERR_TOO_LARGE: return "size beyond the supported index range";
+    case SDF_ERR_OOM: return "device out of memory";
+    case SDF_ERR_CUDA: return "CUDA runtime error";
+    case SDF_ERR_TIMEOUT: return "bounded device wait gave up";
+    default: return "unknown status";
+    }
+}

@@ -1,0 +1,266 @@
+// Device-wide exclusive scan and stable LSD radix sort.
+//
+// The paper orders edge and vertex entries with a library sort_by_key followed by
+// a gather and a serial per-group fix-up (Section 7.1).  Here both steps are one
+// hand-written stable radix sort of (64-bit key, 32-bit payload) pairs: 8-bit
+// digits, a per-tile histogram pass, a device-wide scan of the digit offsets and a
+// scatter pass that ranks keys inside each warp with __match_any_sync and stages
+// the tile in shared memory so global writes of one digit run are contiguous.
+#include "sdf_internal.cuh"
+
+namespace sdf {
+
+// ============================================================================= scan
+namespace {
+constexpr int SC_THREADS = 256, SC_ITEMS = 16, SC_TILE = SC_THREADS * SC_ITEMS;
+
+__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// block-wide exclusive scan of one value per thread; returns the block total via *total
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t warp_tot[SC_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = warp_incl_scan_u32(v);
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < SC_THREADS / 32 ? warp_tot[lane] : 0u;
+        uint32_t ti = warp_incl_scan_u32(t);
+        if (lane < SC_THREADS / 32) warp_tot[lane] = ti - t;
+        if (lane == SC_THREADS / 32 - 1) *total = ti;
+    }
+    __syncthreads();
+    uint32_t r = warp_tot[warp] + inc - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *in, int64_t n, uint32_t *sums) {
+    int64_t base = (int64_t)blockIdx.x * SC_TILE;
+    uint32_t s = 0;
+    for (int i = 0; i < SC_ITEMS; i++) {
+        int64_t idx = base + (int64_t)i * SC_THREADS + threadIdx.x;
+        if (idx < n) s += in[idx];
+    }
+    __shared__ uint32_t tot;
+    block_excl_scan_u32(s, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// exclusive scan of each tile (blocked arrangement: thread t owns SC_ITEMS consecutive items),
+// offset by offs[blockIdx.x] (nullable)
+__global__ void __launch_bounds__(SC_THREADS) k_scan_apply(const uint32_t *in, uint32_t *out, int64_t n,
+                                                           const uint32_t *offs, uint32_t *total_out) {
+    int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+    uint32_t v[SC_ITEMS];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SC_ITEMS; i++) {
+        v[i] = (base + i < n) ? in[base + i] : 0u;
+        s += v[i];
+    }
+    __shared__ uint32_t tot;
+    uint32_t run = block_excl_scan_u32(s, &tot) + (offs ? offs[blockIdx.x] : 0u);
+#pragma unroll
+    for (int i = 0; i < SC_ITEMS; i++) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+    if (total_out && blockIdx.x == gridDim.x - 1 && threadIdx.x == SC_THREADS - 1) *total_out = run;
+}
+}  // namespace
+
+size_t scan_tmp_bytes(int64_t n) {
+    size_t bytes = 0;
+    int64_t m = n;
+    while (m > SC_TILE) {
+        m = (m + SC_TILE - 1) / SC_TILE;
+        bytes += ((size_t)m + 64) * sizeof(uint32_t);
+    }
+    return bytes + 256;
+}
+
+cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, bool write_total, void *tmp,
+                               cudaStream_t s) {
+    if (n <= 0) {
+        if (write_total) return cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
+        return cudaSuccess;
+    }
+    int64_t nb = (n + SC_TILE - 1) / SC_TILE;
+    if (nb == 1) {
+        k_scan_apply<<<1, SC_THREADS, 0, s>>>(in, out, n, nullptr, write_total ? out + n : nullptr);
+        SDF_LAUNCHED(1);
+        return cudaGetLastError();
+    }
+    uint32_t *sums = reinterpret_cast<uint32_t *>(tmp);
+    void *rest = sums + nb + 64;
+    k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, sums);
+    SDF_LAUNCHED(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = scan_exclusive_u32(sums, sums, nb, false, rest, s);
+    if (e != cudaSuccess) return e;
+    k_scan_apply<<<(unsigned)nb, SC_THREADS, 0, s>>>(in, out, n, sums, write_total ? out + n : nullptr);
+    SDF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+
+// ============================================================================= radix sort
+namespace {
+constexpr int RS_THREADS = 256, RS_WARPS = RS_THREADS / 32, RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS, RADIX = 256;
+constexpr size_t RS_SMEM = (size_t)RS_TILE * (sizeof(uint64_t) + sizeof(uint32_t)) +
+                           (size_t)RS_WARPS * RADIX * sizeof(uint32_t) + 2 * RADIX * sizeof(uint32_t);
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *keys, int64_t n, int shift,
+                                                        uint32_t *hist, int64_t nb) {
+    __shared__ uint32_t h[RADIX];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int i = 0; i < RS_ITEMS; i++) {
+        int64_t idx = base + (int64_t)i * RS_THREADS + threadIdx.x;
+        if (idx < n) atomicAdd(&h[(unsigned)(keys[idx] >> shift) & (RADIX - 1)], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];  // digit-major
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *kin, const uint32_t *vin,
+                                                           uint64_t *kout, uint32_t *vout, int64_t n, int shift,
+                                                           const uint32_t *offs, int64_t nb) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *skey = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *sval = reinterpret_cast<uint32_t *>(skey + RS_TILE);
+    uint32_t *wcnt = sval + RS_TILE;           // [RS_WARPS][RADIX]
+    uint32_t *bstart = wcnt + RS_WARPS * RADIX; // [RADIX]
+    uint32_t *btot = bstart + RADIX;           // [RADIX]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < RS_WARPS * RADIX; i += RS_THREADS) wcnt[i] = 0;
+    __syncthreads();
+
+    const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t wbase = tile0 + (int64_t)warp * (32 * RS_ITEMS);
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint64_t k[RS_ITEMS];
+    uint32_t v[RS_ITEMS], rank[RS_ITEMS];
+    uint32_t *mycnt = wcnt + warp * RADIX;
+#pragma unroll
+    for (int it = 0; it < RS_ITEMS; it++) {
+        int64_t idx = wbase + it * 32 + lane;
+        bool valid = idx < n;
+        k[it] = valid ? kin[idx] : 0ull;
+        v[it] = valid ? vin[idx] : 0u;
+        unsigned d = valid ? ((unsigned)(k[it] >> shift) & (RADIX - 1)) : (RADIX + lane);  // invalid: own group
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = valid ? mycnt[d] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt_mask) == 0u) mycnt[d] = before + __popc(peers);
+        __syncwarp();
+        rank[it] = before + __popc(peers & lt_mask);
+    }
+    __syncthreads();
+    {   // thread t owns digit t: prefix over warps, then block totals
+        uint32_t run = 0;
+        for (int w = 0; w < RS_WARPS; w++) {
+            uint32_t c = wcnt[w * RADIX + threadIdx.x];
+            wcnt[w * RADIX + threadIdx.x] = run;
+            run += c;
+        }
+        btot[threadIdx.x] = run;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scan of 256 digit totals by one warp (8 per lane)
+        uint32_t loc[8], s = 0;
+#pragma unroll
+        for (int i = 0; i < 8; i++) { loc[i] = btot[lane * 8 + i]; s += loc[i]; }
+        uint32_t inc = warp_incl_scan_u32(s);
+        uint32_t run = inc - s;
+#pragma unroll
+        for (int i = 0; i < 8; i++) { bstart[lane * 8 + i] = run; run += loc[i]; }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < RS_ITEMS; it++) {
+        int64_t idx = wbase + it * 32 + lane;
+        if (idx < n) {
+            unsigned d = (unsigned)(k[it] >> shift) & (RADIX - 1);
+            uint32_t lp = bstart[d] + mycnt[d] + rank[it];
+            skey[lp] = k[it];
+            sval[lp] = v[it];
+        }
+    }
+    __syncthreads();
+    int cnt = (n - tile0 < (int64_t)RS_TILE) ? (int)(n - tile0) : RS_TILE;
+    for (int i = threadIdx.x; i < cnt; i += RS_THREADS) {
+        uint64_t key = skey[i];
+        unsigned d = (unsigned)(key >> shift) & (RADIX - 1);
+        int64_t g = (int64_t)offs[(int64_t)d * nb + blockIdx.x] + (i - (int64_t)bstart[d]);
+        kout[g] = key;
+        vout[g] = sval[i];
+    }
+}
+}  // namespace
+
+size_t radix_tmp_bytes(int64_t n) {
+    int64_t nb = (n + RS_TILE - 1) / RS_TILE;
+    size_t hist = ((size_t)nb * RADIX + 64) * sizeof(uint32_t);
+    return hist + scan_tmp_bytes(nb * RADIX) + 256;
+}
+
+cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int64_t n,
+                           int bits, void *tmp, cudaStream_t s) {
+    if (n <= 1 || bits <= 0) return cudaSuccess;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int64_t nb = (n + RS_TILE - 1) / RS_TILE;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(tmp);
+    void *scan_tmp = hist + nb * RADIX + 64;
+    int passes = (bits + 7) / 8;
+    uint64_t *ki = keys, *ko = keys_alt;
+    uint32_t *vi = vals, *vo = vals_alt;
+    for (int p = 0; p < passes; p++) {
+        int shift = 8 * p;
+        k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, s>>>(ki, n, shift, hist, nb);
+        SDF_LAUNCHED(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = scan_exclusive_u32(hist, hist, nb * RADIX, false, scan_tmp, s);
+        if (e != cudaSuccess) return e;
+        k_rs_scatter<<<(unsigned)nb, RS_THREADS, RS_SMEM, s>>>(ki, vi, ko, vo, n, shift, hist, nb);
+        SDF_LAUNCHED(1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        uint64_t *tk = ki; ki = ko; ko = tk;
+        uint32_t *tv = vi; vi = vo; vo = tv;
+    }
+    if (ki != keys) {
+        cudaError_t e = cudaMemcpyAsync(keys, ki, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(vals, vi, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace sdf
+
+// ============================================================================= launch counter
+#include <atomic>
+namespace sdf {
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace sdf
+extern "C" int64_t sdf_kernel_launches(void) { return sdf::g_launches.load(); }

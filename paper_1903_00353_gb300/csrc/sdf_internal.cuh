@@ -1,0 +1,141 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Nothing here is part of the C ABI (include/sdf.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sdf.h"
+
+namespace sdf {
+
+// ----------------------------------------------------------------------------- status bits (device word)
+enum : unsigned {
+    ST_NONFINITE = 1u,
+    ST_DEGENERATE = 2u,
+    ST_NONMANIFOLD = 4u,
+    ST_PAIR_OVERFLOW = 8u,   // (tile, region) pair list too small: grow and rerun
+    ST_PATCH_OVERFLOW = 16u, // FP64 re-decision list too small: grow and rerun
+};
+
+// vertex / edge classes (Section 3.1, Section 3.2)
+enum : int8_t { CLS_FLAT = 0, CLS_CONVEX = 1, CLS_CONCAVE = -1, CLS_SADDLE = 2 };
+
+// tile of the narrow-band kernel: TX x TY x TZ grid points (x fastest)
+constexpr int TILE_X = 32, TILE_Y = 8, TILE_Z = 8;
+constexpr int TILE_PTS = TILE_X * TILE_Y * TILE_Z;
+
+// ----------------------------------------------------------------------------- device buffers
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t need) {
+        if (need <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        size_t want = need + need / 4 + 256;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) bytes = want;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// ----------------------------------------------------------------------------- device status / counters
+struct DevCounters {
+    unsigned status;
+    unsigned pad;
+    unsigned long long n_candidates;   // (point, region) pairs merged
+    unsigned long long n_band;         // band points written
+    unsigned long long n_patch;        // points re-decided in FP64
+    unsigned long long n_pairs;        // (tile, region) pairs scheduled
+    unsigned long long cls[8];         // classification counts
+};
+
+}  // namespace sdf
+
+// ----------------------------------------------------------------------------- the handle
+struct sdf_features_s {
+    int64_t T = 0, V = 0, E = 0;
+    uint32_t flags = 0;
+    // connectivity (fixed after the build)
+    int32_t *face_vid = nullptr;    // [3T] welded vertex of each soup corner
+    int32_t *face_edge = nullptr;   // [3T] edge id of the edge from corner k to corner k+1
+    int4 *edge_vf = nullptr;        // [E] (va < vb, f1 holding va->vb, f2 holding vb->va)
+    int32_t *vert_start = nullptr;  // [V+1] CSR into vert_corner
+    int32_t *vert_corner = nullptr; // [3T] soup corners grouped by vertex
+    // geometry (re-evaluated by sdf_features_update_positions)
+    float *vpos = nullptr;          // [V][3]
+    float4 *face_rec = nullptr;     // [T][4] (n, c0) and three inward side planes (m, c)
+    float4 *face_box = nullptr;     // [T][2] vertex bounding box lo, hi
+    float4 *edge_rec = nullptr;     // [E][5] (a, L) (t, t.a) (-m1, m1.a) (-m2, m2.a) (n1+n2, 0)
+    float4 *vert_rec = nullptr;     // [V][2] (v, start) (unit N_alpha, count)
+    float4 *vert_plane = nullptr;   // [3T] (-e_j, e_j.v) per incident edge, CSR by vert_start
+    int8_t *edge_class = nullptr;   // [E]
+    int8_t *vert_class = nullptr;   // [V]
+    int64_t counts[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    sdf::DevCounters *ctr = nullptr; // device counters
+    // narrow-band scratch, grown on demand
+    sdf::DevBuf bins, pairs, patch, scan_tmp, fwd_winner;
+    int64_t pair_cap = 0, patch_cap = 0;
+    // stage timing (SDF_FLAG_TIMING)
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double t_ms[4] = {0, 0, 0, 0};
+    int64_t t_calls[4] = {0, 0, 0, 0};
+};
+
+namespace sdf {
+
+// ----------------------------------------------------------------------------- launch counter
+void count_launches(int64_t n);
+#define SDF_LAUNCHED(n) ::sdf::count_launches(n)
+
+// ----------------------------------------------------------------------------- scans and sorts (scan_sort.cu)
+// Exclusive scan of n uint32 values (in may equal out); out[n] receives the total when
+// write_total is set.  tmp must hold scan_tmp_bytes(n) bytes.
+size_t scan_tmp_bytes(int64_t n);
+cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, bool write_total, void *tmp,
+                               cudaStream_t s);
+// Stable LSD radix sort of (keys, vals) on bits [0, bits).  Buffers *_alt are ping-pong
+// scratch of the same size; the result ends in keys/vals.
+size_t radix_tmp_bytes(int64_t n);
+cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int64_t n,
+                           int bits, void *tmp, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- geometry stage (build.cu)
+int build_records(sdf_features_s *f, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- small device helpers
+__device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double3 d3(float3 a) { return make_double3(a.x, a.y, a.z); }
+__device__ __forceinline__ double3 operator-(double3 a, double3 b) { return make_double3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ double3 operator+(double3 a, double3 b) { return make_double3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ double3 operator*(double s, double3 a) { return make_double3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ double ddot3(double3 a, double3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ double3 dcross3(double3 a, double3 b) {
+    return make_double3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 load_vpos(const float *vpos, int v) {
+    return make_float3(vpos[3 * v], vpos[3 * v + 1], vpos[3 * v + 2]);
+}
+
+}  // namespace sdf
+
+#define SDF_TRY(expr)                                  \
+    do {                                               \
+        cudaError_t e_ = (expr);                       \
+        if (e_ != cudaSuccess) return SDF_ERR_CUDA;    \
+    } while (0)
