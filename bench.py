@@ -196,6 +196,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=None, help="override the grid size N (same mesh, same band in cells)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.warmup < 3:
@@ -223,6 +224,9 @@ def main():
 
     soup_np = meshgen.config_soup(wl["index"])
     N, cells = meshgen.CONFIG_GRID[wl["index"]]
+    if args.grid:
+        N = args.grid
+        wl = dict(wl, desc=wl["desc"].replace(f"{meshgen.CONFIG_GRID[wl['index']][0]}^3", f"{N}^3"))
     w = cells / N
     grid = sdf.Grid.cube(N)
     dev = torch.device("cuda", local)
@@ -351,7 +355,8 @@ def main():
         "fwd_adjoint_ms": fwd_ms + adj_ms if wl["adjoint"] else None,
         "fwd_adjoint_over_fwd": (fwd_ms + adj_ms) / fwd_ms if wl["adjoint"] else None,
         "candidates_per_band_point": stats["candidates"] / max(1, stats["band_points"]),
-        "fp64_points": stats["fp64_points"],
+        "fp64_points": stats["fp64_points"], "tile_region_pairs": stats["pairs"], "rows": stats["rows"],
+        "rows_hit": stats["rows_hit"],
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(), "e2e": e2e,
         "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
     }

@@ -31,9 +31,11 @@
  *
  * Feature ids (Section 2: faces, edges and vertices are the features):
  *   face f in [0, T); edge e -> T + e; vertex v -> T + E + v,
- * with T triangles, E = 3T/2 unique edges and V unique vertices.  Winner ids
- * name the feature whose characteristic region produced the stored value;
- * -1 outside the band.
+ * with T triangles, E = 3T/2 unique edges and V unique vertices.  Faces,
+ * edges and vertices are numbered in a spatial (Morton) order chosen by the
+ * library; sdf_features_face_map and sdf_features_vertex_map relate them to
+ * the soup.  Winner ids name the feature whose characteristic region produced
+ * the stored value; -1 outside the band.
  */
 #ifndef GB300_SDF_H
 #define GB300_SDF_H
@@ -174,14 +176,18 @@ int sdf_features_info(sdf_features f, int64_t *n_tri, int64_t *counts /* host [8
 /* Welded vertex id of every soup corner: device int32[3*n_tri]. */
 int sdf_features_vertex_map(sdf_features f, int32_t *soup_to_vertex, void *stream);
 
+/* Soup triangle of every library face id: device int32[n_tri]. */
+int sdf_features_face_map(sdf_features f, int32_t *face_to_soup, void *stream);
+
 /* Welded vertex positions: device float[V][3]. */
 int sdf_features_vertices(sdf_features f, float *out, void *stream);
 
 /*
  * Status word and counters of the last sdf_narrow_band on this handle
- * (synchronises `stream`).  stats (host, nullable) [4] = candidate (point,
- * region) pairs merged by atomicMin, band points, points re-decided in FP64,
- * (tile, region) pairs scheduled.
+ * (synchronises `stream`).  stats (host, nullable) [6] = candidate (point,
+ * region) pairs merged by atomicMin, band points decided in FP32, points
+ * re-decided in FP64, (tile, region) pairs scheduled, grid rows intersected
+ * with a region, of which non-empty.
  */
 int sdf_features_status(sdf_features f, int64_t *stats, void *stream);
 

@@ -59,6 +59,8 @@ def load_library(path: str | None = None):
                                            I32, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), U32, P]
     L.sdf_features_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
     L.sdf_features_vertex_map.argtypes = [P, P, P]
+    L.sdf_features_face_map.argtypes = [P, P, P]
+    L.sdf_features_face_map.restype = ctypes.c_int
     L.sdf_features_vertices.argtypes = [P, P, P]
     L.sdf_features_status.argtypes = [P, ctypes.POINTER(I64), P]
     L.sdf_features_destroy.argtypes = [P]
@@ -147,6 +149,12 @@ class Features:
         _check(load_library().sdf_features_vertex_map(self.handle, out.data_ptr(), _stream()), "vertex_map")
         return out
 
+    def face_map(self) -> torch.Tensor:
+        """Soup triangle index of every library face id (faces are stored in a spatial order)."""
+        out = torch.empty(self.n_tri, dtype=torch.int32, device="cuda")
+        _check(load_library().sdf_features_face_map(self.handle, out.data_ptr(), _stream()), "face_map")
+        return out
+
     def vertices(self) -> torch.Tensor:
         out = torch.empty(self.n_vert, 3, dtype=torch.float32, device="cuda")
         _check(load_library().sdf_features_vertices(self.handle, out.data_ptr(), _stream()), "vertices")
@@ -160,10 +168,11 @@ class Features:
                "sdf_features_update_positions")
 
     def status(self):
-        st = (ctypes.c_int64 * 4)()
+        st = (ctypes.c_int64 * 6)()
         code = load_library().sdf_features_status(self.handle, st, _stream())
         _check(code, "sdf_features_status")
-        return {"candidates": int(st[0]), "band_points": int(st[1]), "fp64_points": int(st[2])}
+        return {"candidates": int(st[0]), "band_points": int(st[1]), "fp64_points": int(st[2]),
+                "pairs": int(st[3]), "rows": int(st[4]), "rows_hit": int(st[5])}
 
     def timing(self, reset: bool = False):
         """Accumulated stage times (ms) of calls made with FLAG_TIMING: bin, tile, fp64, adjoint."""
@@ -226,6 +235,12 @@ def sdf_narrow_band(features: Features | Sequence[Features], grid: Grid | Sequen
                 raise ValueError("out has the wrong size")
     if isinstance(winner, (list, tuple)):
         wins = list(winner)
+    elif isinstance(winner, torch.Tensor):
+        if batch:
+            raise ValueError("a batch takes a list of winner tensors")
+        if not winner.is_cuda or winner.dtype != torch.int32 or not winner.is_contiguous():
+            raise ValueError("winner must be a contiguous int32 CUDA tensor")
+        wins = [winner]
     elif winner:
         wins = [torch.empty(g.shape, dtype=torch.int32, device="cuda") for g in grids]
     else:

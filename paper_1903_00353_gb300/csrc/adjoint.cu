@@ -123,7 +123,7 @@ __global__ void k_adjoint(AdjArgs a) {
                 }
             } else {
                 const int v = wid - a.T - a.E;
-                float4 r0 = a.vert_rec[2 * v], r1 = a.vert_rec[2 * v + 1];
+                float4 r0 = a.vert_rec[3 * v], r1 = a.vert_rec[3 * v + 1];
                 float3 d = p - f3(r0);
                 float len = sqrtf(dot3(d, d));
                 if (len > 0.f) {

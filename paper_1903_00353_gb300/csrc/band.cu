@@ -27,6 +27,9 @@
 //      membership or sign lies inside the FP32 error window;
 //   3. patch kernel: re-decides the queued points in FP64 from the winner's neighbourhood.
 #include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
 
 #include "sdf_internal.cuh"
 
@@ -88,27 +91,71 @@ __device__ __forceinline__ bool to_index_box(float lx, float ly, float lz, float
     return i0 <= i1 && j0 <= j1 && k0 <= k1;
 }
 
-// integer box of the clipped region of feature `id` of type TYPE; false if the feature has none
+__device__ __forceinline__ void box_add(float3 &lo, float3 &hi, float3 p) {
+    lo.x = fminf(lo.x, p.x); lo.y = fminf(lo.y, p.y); lo.z = fminf(lo.z, p.z);
+    hi.x = fmaxf(hi.x, p.x); hi.y = fmaxf(hi.y, p.y); hi.z = fmaxf(hi.z, p.z);
+}
+
+// extent of the spherical cone {y : angle(y, axis) <= theta, |y| <= 1} along +e (unit axis comp. ca)
+__device__ __forceinline__ float cone_reach(float ca, float cth, float sth) {
+    if (ca >= cth) return 1.f;
+    float sa = sqrtf(fmaxf(0.f, 1.f - ca * ca));
+    return fmaxf(0.f, ca * cth + sa * sth);  // cos(angle(e, axis) - theta), or the apex
+}
+
+// integer box of the clipped region of feature `id` of type TYPE; false if the feature has none.
+//   face  : triangle box grown by W |n| per axis (the prism is the triangle swept along +-W n);
+//   edge  : segment box plus the box of the sector of radius W between the two face normals
+//           (u1, u2 on the region's side), which lies in the kite {0, u1, u2, m / cos(theta/2)};
+//   vertex: the spherical cone of the vertex region when one bounds it, else the ball of radius W.
 template <int TYPE>
 __device__ __forceinline__ bool feature_box(const Feat &F, const GridP &g, int id, int &i0, int &i1, int &j0,
                                             int &j1, int &k0, int &k1) {
     const float R = g.W + g.eps;
+    const float slack = R * 1e-5f + g.eps;
     if (TYPE == FACE) {
         float4 n = __ldg(F.face_rec + 4 * id), lo = __ldg(F.face_box + 2 * id), hi = __ldg(F.face_box + 2 * id + 1);
-        float ex = R * fabsf(n.x) + g.eps, ey = R * fabsf(n.y) + g.eps, ez = R * fabsf(n.z) + g.eps;
+        float ex = R * fabsf(n.x) + slack, ey = R * fabsf(n.y) + slack, ez = R * fabsf(n.z) + slack;
         return to_index_box(lo.x - ex, lo.y - ey, lo.z - ez, hi.x + ex, hi.y + ey, hi.z + ez, g, i0, i1, j0, j1, k0, k1);
     } else if (TYPE == EDGE) {
-        int8_t c = F.edge_class[id];
+        const int8_t c = F.edge_class[id];
         if (c == CLS_FLAT) return false;
-        float4 a = __ldg(F.edge_rec + 5 * id), t = __ldg(F.edge_rec + 5 * id + 1);
-        float bx = fmaf(a.w, t.x, a.x), by = fmaf(a.w, t.y, a.y), bz = fmaf(a.w, t.z, a.z);
-        return to_index_box(fminf(a.x, bx) - R, fminf(a.y, by) - R, fminf(a.z, bz) - R, fmaxf(a.x, bx) + R,
-                            fmaxf(a.y, by) + R, fmaxf(a.z, bz) + R, g, i0, i1, j0, j1, k0, k1);
+        const float4 a = __ldg(F.edge_rec + 5 * id), t = __ldg(F.edge_rec + 5 * id + 1);
+        const float4 r2 = __ldg(F.edge_rec + 5 * id + 2), r3 = __ldg(F.edge_rec + 5 * id + 3);
+        const float3 tt = f3(t);
+        // n1 = t x m1, n2 = (-t) x m2 with the stored planes holding -m1, -m2
+        float3 u1 = cross3(f3(r2), tt), u2 = cross3(tt, f3(r3));
+        if (c == CLS_CONCAVE) { u1 = -1.f * u1; u2 = -1.f * u2; }
+        const float3 ms = u1 + u2;
+        const float lm = sqrtf(dot3(ms, ms));
+        float3 slo = make_float3(0.f, 0.f, 0.f), shi = slo;
+        if (lm > 0.2f) {  // sector angle < ~168 degrees: kite bound
+            box_add(slo, shi, u1);
+            box_add(slo, shi, u2);
+            box_add(slo, shi, (2.f / (lm * lm)) * ms);  // m / cos(theta/2), |ms| = 2 cos(theta/2)
+        } else {
+            slo = make_float3(-1.f, -1.f, -1.f);
+            shi = make_float3(1.f, 1.f, 1.f);
+        }
+        const float bx = fmaf(a.w, t.x, a.x), by = fmaf(a.w, t.y, a.y), bz = fmaf(a.w, t.z, a.z);
+        return to_index_box(fminf(a.x, bx) + R * slo.x - slack, fminf(a.y, by) + R * slo.y - slack,
+                            fminf(a.z, bz) + R * slo.z - slack, fmaxf(a.x, bx) + R * shi.x + slack,
+                            fmaxf(a.y, by) + R * shi.y + slack, fmaxf(a.z, bz) + R * shi.z + slack, g, i0, i1, j0,
+                            j1, k0, k1);
     } else {
-        int8_t c = F.vert_class[id];
+        const int8_t c = F.vert_class[id];
         if (c == CLS_FLAT || (F.skip_saddle && c == CLS_SADDLE)) return false;
-        float4 v = __ldg(F.vert_rec + 2 * id);
-        return to_index_box(v.x - R, v.y - R, v.z - R, v.x + R, v.y + R, v.z + R, g, i0, i1, j0, j1, k0, k1);
+        const float4 v = __ldg(F.vert_rec + 3 * id), cone = __ldg(F.vert_rec + 3 * id + 2);
+        float3 lo = make_float3(-1.f, -1.f, -1.f), hi = make_float3(1.f, 1.f, 1.f);
+        if (cone.w > -1.f) {
+            const float cth = fminf(cone.w, 1.f), sth = sqrtf(fmaxf(0.f, 1.f - cth * cth));
+            hi = make_float3(cone_reach(cone.x, cth, sth), cone_reach(cone.y, cth, sth), cone_reach(cone.z, cth, sth));
+            lo = make_float3(-cone_reach(-cone.x, cth, sth), -cone_reach(-cone.y, cth, sth),
+                             -cone_reach(-cone.z, cth, sth));
+        }
+        return to_index_box(v.x + R * lo.x - slack, v.y + R * lo.y - slack, v.z + R * lo.z - slack,
+                            v.x + R * hi.x + slack, v.y + R * hi.y + slack, v.z + R * hi.z + slack, g, i0, i1, j0,
+                            j1, k0, k1);
     }
 }
 
@@ -163,51 +210,63 @@ __device__ __forceinline__ int warp_owner(int incl, int r) {
     return lo;
 }
 
-// half-space P.xyz . (X, Y, Z) + P.w >= -eps along the row (Y, Z): shrink [xa, xb]
-__device__ __forceinline__ void clip_plane(float4 P, float Y, float Z, float eps, float &xa, float &xb) {
-    float r = fmaf(P.y, Y, fmaf(P.z, Z, P.w)) + eps;
-    if (P.x > 0.f) xa = fmaxf(xa, -r / P.x);
-    else if (P.x < 0.f) xb = fminf(xb, -r / P.x);
+__device__ __forceinline__ float comp(float4 P, int ax) { return ax == 0 ? P.x : (ax == 1 ? P.y : P.z); }
+__device__ __forceinline__ float comp3(float3 P, int ax) { return ax == 0 ? P.x : (ax == 1 ? P.y : P.z); }
+
+// Half-space P.xyz . p + P.w >= -eps along the grid line parallel to axis `ax` through the
+// coordinates (B, C) on the other two axes (bx < cx): shrink the interval [xa, xb] of the
+// line coordinate (Algorithm 2 restricted to a line, with the tolerance of Section 10).
+__device__ __forceinline__ void clip_plane(float4 P, int ax, int bx, int cx, float B, float C, float eps, float &xa,
+                                           float &xb) {
+    const float pa = comp(P, ax);
+    const float r = fmaf(comp(P, bx), B, fmaf(comp(P, cx), C, P.w)) + eps;
+    if (pa > 0.f) xa = fmaxf(xa, -r / pa);
+    else if (pa < 0.f) xb = fminf(xb, -r / pa);
     else if (r < 0.f) xa = INFINITY;
 }
 
-// x-span of the region of feature `id` on the row (j, k), intersected with [bi0, bi1]
+// index span [ia, ib] within [lo, hi] along axis `ax` of the region of feature `id` on the grid
+// line with indices (rb, rc) on the other two axes
 template <int TYPE>
-__device__ __forceinline__ void row_span(const Feat &F, const GridP &g, int id, int j, int k, int bi0, int bi1,
+__device__ __forceinline__ void row_span(const Feat &F, const GridP &g, int id, int ax, int rb, int rc, int lo, int hi,
                                          int &ia, int &ib) {
-    const float Y = fmaf((float)j + 0.5f, g.h, g.oy), Z = fmaf((float)k + 0.5f, g.h, g.oz);
+    const int bx = ax == 0 ? 1 : 0, cx = ax == 2 ? 1 : 2;
+    const float3 org = make_float3(g.ox, g.oy, g.oz);
+    const float B = fmaf((float)rb + 0.5f, g.h, comp3(org, bx)), C = fmaf((float)rc + 0.5f, g.h, comp3(org, cx));
     float xa = -INFINITY, xb = INFINITY;
     const float e = g.eps;
     if (TYPE == FACE) {
         const float4 *r = F.face_rec + 4 * id;
-        float4 n = __ldg(r);
-        clip_plane(make_float4(n.x, n.y, n.z, n.w + g.W), Y, Z, e, xa, xb);      // n.p + c >= -W
-        clip_plane(make_float4(-n.x, -n.y, -n.z, g.W - n.w), Y, Z, e, xa, xb);   // n.p + c <= W
-        clip_plane(__ldg(r + 1), Y, Z, e, xa, xb);
-        clip_plane(__ldg(r + 2), Y, Z, e, xa, xb);
-        clip_plane(__ldg(r + 3), Y, Z, e, xa, xb);
+        const float4 n = __ldg(r);
+        clip_plane(make_float4(n.x, n.y, n.z, n.w + g.W), ax, bx, cx, B, C, e, xa, xb);      // n.p + c >= -W
+        clip_plane(make_float4(-n.x, -n.y, -n.z, g.W - n.w), ax, bx, cx, B, C, e, xa, xb);   // n.p + c <= W
+        clip_plane(__ldg(r + 1), ax, bx, cx, B, C, e, xa, xb);
+        clip_plane(__ldg(r + 2), ax, bx, cx, B, C, e, xa, xb);
+        clip_plane(__ldg(r + 3), ax, bx, cx, B, C, e, xa, xb);
     } else if (TYPE == EDGE) {
         const float4 *r = F.edge_rec + 5 * id;
-        float4 a = __ldg(r), t = __ldg(r + 1);
-        clip_plane(make_float4(t.x, t.y, t.z, -t.w), Y, Z, e, xa, xb);           // t.(p - a) >= 0
-        clip_plane(make_float4(-t.x, -t.y, -t.z, t.w + a.w), Y, Z, e, xa, xb);   // t.(p - a) <= L
-        clip_plane(__ldg(r + 2), Y, Z, e, xa, xb);                               // (p - a).m1 <= 0
-        clip_plane(__ldg(r + 3), Y, Z, e, xa, xb);                               // (p - a).m2 <= 0
+        const float4 a = __ldg(r), t = __ldg(r + 1);
+        clip_plane(make_float4(t.x, t.y, t.z, -t.w), ax, bx, cx, B, C, e, xa, xb);           // t.(p - a) >= 0
+        clip_plane(make_float4(-t.x, -t.y, -t.z, t.w + a.w), ax, bx, cx, B, C, e, xa, xb);   // t.(p - a) <= L
+        clip_plane(__ldg(r + 2), ax, bx, cx, B, C, e, xa, xb);                               // (p - a).m1 <= 0
+        clip_plane(__ldg(r + 3), ax, bx, cx, B, C, e, xa, xb);                               // (p - a).m2 <= 0
     } else {
-        float4 v = __ldg(F.vert_rec + 2 * id), nv = __ldg(F.vert_rec + 2 * id + 1);
-        float dy = Y - v.y, dz = Z - v.z;
-        float R = g.W + e;
-        float r2 = R * R - dy * dy - dz * dz;
+        const float4 v = __ldg(F.vert_rec + 3 * id), nv = __ldg(F.vert_rec + 3 * id + 1);
+        const float3 vv = f3(v);
+        const float db = B - comp3(vv, bx), dc = C - comp3(vv, cx);
+        const float R = g.W + e;
+        const float r2 = R * R - db * db - dc * dc;
         if (r2 < 0.f) { ia = 1; ib = 0; return; }
-        float sq = sqrtf(r2);
-        xa = v.x - sq;
-        xb = v.x + sq;
-        int s0 = __float_as_int(v.w), cnt = __float_as_int(nv.w);
-        for (int q = 0; q < cnt; q++) clip_plane(__ldg(F.vert_plane + s0 + q), Y, Z, e, xa, xb);
+        const float sq = sqrtf(r2);
+        xa = comp3(vv, ax) - sq;
+        xb = comp3(vv, ax) + sq;
+        const int s0 = __float_as_int(v.w), cnt = __float_as_int(nv.w);
+        for (int q = 0; q < cnt; q++) clip_plane(__ldg(F.vert_plane + s0 + q), ax, bx, cx, B, C, e, xa, xb);
     }
     const float sl = 1.f / 4096.f;
-    float fa = fminf(fmaxf((xa - g.ox) * g.inv_h - 0.5f - sl, (float)bi0), (float)bi1 + 1.f);
-    float fb = fmaxf(fminf((xb - g.ox) * g.inv_h - 0.5f + sl, (float)bi1), (float)bi0 - 1.f);
+    const float oa = comp3(org, ax);
+    const float fa = fminf(fmaxf((xa - oa) * g.inv_h - 0.5f - sl, (float)lo), (float)hi + 1.f);
+    const float fb = fmaxf(fminf((xb - oa) * g.inv_h - 0.5f + sl, (float)hi), (float)lo - 1.f);
     ia = (int)ceilf(fa);
     ib = (int)floorf(fb);
 }
@@ -251,149 +310,291 @@ __device__ __forceinline__ float eval_point(const Feat &F, const GridP &g, int i
         neg = dot3(d, f3(np)) < 0.f;
         return sqrtf(dot3(d, d));
     } else {
-        float4 v = __ldg(F.vert_rec + 2 * id), nv = __ldg(F.vert_rec + 2 * id + 1);
+        float4 v = __ldg(F.vert_rec + 3 * id), nv = __ldg(F.vert_rec + 3 * id + 1);
         float3 u = p - f3(v);
         neg = dot3(u, f3(nv)) < 0.f;
         return sqrtf(dot3(u, u));
     }
 }
 
-template <int TYPE>
-__device__ __forceinline__ void process_regions(const Feat &F, const GridP &g, const int32_t *pairs, int64_t q_begin,
-                                                int64_t q_end, int tx0, int ty0, int tz0, int cx1, int cy1, int cz1,
-                                                unsigned long long *skey, unsigned &cand) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int id_base = TYPE == FACE ? 0 : (TYPE == EDGE ? F.T : F.T + F.E);
-    for (int64_t qb = q_begin + (int64_t)warp * 32; qb < q_end; qb += (int64_t)nw * 32) {
-        int64_t q = qb + lane;
-        int id = 0, bi0 = 0, bi1 = -1, bj0 = 0, bj1 = -1, bk0 = 0, bk1 = -1;
-        if (q < q_end) {
-            id = __ldg(pairs + q) - id_base;
-            if (feature_box<TYPE>(F, g, id, bi0, bi1, bj0, bj1, bk0, bk1)) {
-                bi0 = max(bi0, tx0); bi1 = min(bi1, cx1);
-                bj0 = max(bj0, ty0); bj1 = min(bj1, cy1);
-                bk0 = max(bk0, tz0); bk1 = min(bk1, cz1);
-            } else {
-                bi1 = -1;
+// ----------------------------------------------------------------------------- type dispatch
+__device__ __forceinline__ int feat_type(const Feat &F, int fid) { return fid < F.T ? FACE : (fid < F.T + F.E ? EDGE : VERT); }
+__device__ __forceinline__ int feat_local(const Feat &F, int fid, int type) {
+    return type == FACE ? fid : (type == EDGE ? fid - F.T : fid - F.T - F.E);
+}
+__device__ __forceinline__ bool box_any(const Feat &F, const GridP &g, int type, int id, int *lo, int *hi) {
+    if (type == FACE) return feature_box<FACE>(F, g, id, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
+    if (type == EDGE) return feature_box<EDGE>(F, g, id, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
+    return feature_box<VERT>(F, g, id, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
+}
+__device__ __forceinline__ void span_any(const Feat &F, const GridP &g, int type, int id, int ax, int rb, int rc,
+                                         int lo, int hi, int &ia, int &ib) {
+    if (type == FACE) row_span<FACE>(F, g, id, ax, rb, rc, lo, hi, ia, ib);
+    else if (type == EDGE) row_span<EDGE>(F, g, id, ax, rb, rc, lo, hi, ia, ib);
+    else row_span<VERT>(F, g, id, ax, rb, rc, lo, hi, ia, ib);
+}
+__device__ __forceinline__ float eval_any(const Feat &F, const GridP &g, int type, int id, int i, int j, int k,
+                                          bool &neg) {
+    if (type == FACE) return eval_point<FACE>(F, g, id, i, j, k, neg);
+    if (type == EDGE) return eval_point<EDGE>(F, g, id, i, j, k, neg);
+    return eval_point<VERT>(F, g, id, i, j, k, neg);
+}
+
+// per-tile shared state of the tile kernel
+struct TileSmem {
+    unsigned long long key[TILE_PTS];  // packed (|d| bits << 32 | id << 1 | sign), one per tile point
+    int fid[NT];                       // regions of the current pass
+    int row0[NT + 1];                  // exclusive prefix of their row counts
+    int lo_a[NT], hi_a[NT], lo_b[NT], lo_c[NT];
+    unsigned char ax[NT], nb[NT];
+    int wtot[NT / 32];
+    long long work;
+};
+
+// All regions of one band tile, with the rows of every region flattened over all 8 warps of
+// the CTA: (1) one thread per region computes its box clipped to the tile, its scan axis (the
+// longest side) and its row count; (2) a block scan numbers the rows; (3) each lane takes one
+// row, finds its region by binary search, and intersects the row with the region's half-spaces
+// (Algorithm 2) to get a span; (4) the span points of a warp are flattened over its lanes and
+// merged into the tile's keys with a shared-memory atomicMin (Algorithm 1).
+__device__ void process_band_tile(const Feat &F, const GridP &g, const int32_t *pairs, int64_t q0, int64_t q3,
+                                  int x0, int y0, int z0, int cx1, int cy1, int cz1, TileSmem &S, unsigned &cand,
+                                  unsigned &rows, unsigned &hits) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t base = q0; base < q3; base += NT) {
+        const int64_t q = base + threadIdx.x;
+        int nrows = 0;
+        {
+            int fid = 0, lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};
+            if (q < q3) {
+                fid = __ldg(pairs + q);
+                const int type = feat_type(F, fid);
+                if (box_any(F, g, type, feat_local(F, fid, type), lo, hi)) {
+                    lo[0] = max(lo[0], x0); hi[0] = min(hi[0], cx1);
+                    lo[1] = max(lo[1], y0); hi[1] = min(hi[1], cy1);
+                    lo[2] = max(lo[2], z0); hi[2] = min(hi[2], cz1);
+                } else {
+                    hi[0] = -1;
+                }
             }
+            const int n0 = hi[0] - lo[0] + 1, n1 = hi[1] - lo[1] + 1, n2 = hi[2] - lo[2] + 1;
+            const int ax = (n0 >= n1 && n0 >= n2) ? 0 : (n1 >= n2 ? 1 : 2);
+            const int bx = ax == 0 ? 1 : 0, cx = ax == 2 ? 1 : 2;
+            const int nb = bx == 0 ? n0 : n1, nc = cx == 1 ? n1 : n2;
+            nrows = (n0 > 0 && n1 > 0 && n2 > 0) ? nb * nc : 0;
+            S.fid[threadIdx.x] = fid;
+            S.ax[threadIdx.x] = (unsigned char)ax;
+            S.nb[threadIdx.x] = (unsigned char)max(nb, 1);
+            S.lo_a[threadIdx.x] = ax == 0 ? lo[0] : (ax == 1 ? lo[1] : lo[2]);
+            S.hi_a[threadIdx.x] = ax == 0 ? hi[0] : (ax == 1 ? hi[1] : hi[2]);
+            S.lo_b[threadIdx.x] = bx == 0 ? lo[0] : lo[1];
+            S.lo_c[threadIdx.x] = cx == 1 ? lo[1] : lo[2];
         }
-        const int nj = bj1 - bj0 + 1;
-        const int nrows = (bi0 <= bi1 && bj0 <= bj1 && bk0 <= bk1) ? nj * (bk1 - bk0 + 1) : 0;
+        // block exclusive scan of the row counts
         const int incl = warp_incl_scan(nrows);
-        const int total = __shfl_sync(FULL, incl, 31);
-        for (int r0 = 0; r0 < total; r0 += 32) {
-            const int r = r0 + lane;
-            const int o = min(warp_owner(incl, r), 31);
-            const int o_excl = __shfl_sync(FULL, incl - nrows, o);
-            const int o_id = __shfl_sync(FULL, id, o), o_nj = __shfl_sync(FULL, nj, o);
-            const int o_bj0 = __shfl_sync(FULL, bj0, o), o_bk0 = __shfl_sync(FULL, bk0, o);
-            const int o_bi0 = __shfl_sync(FULL, bi0, o), o_bi1 = __shfl_sync(FULL, bi1, o);
-            int rj = 0, rk = 0, ia = 0, len = 0;
-            if (r < total) {
-                const int local = r - o_excl;
-                rk = o_bk0 + local / o_nj;
-                rj = o_bj0 + (local - (rk - o_bk0) * o_nj);
+        if (lane == 31) S.wtot[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int t = lane < NT / 32 ? S.wtot[lane] : 0;
+            const int ti = warp_incl_scan(t);
+            if (lane < NT / 32) S.wtot[lane] = ti - t;
+            if (lane == NT / 32 - 1) S.row0[NT] = ti;
+        }
+        __syncthreads();
+        S.row0[threadIdx.x] = S.wtot[warp] + incl - nrows;
+        __syncthreads();
+        const int R = S.row0[NT];
+        for (int rbase = warp * 32; rbase < R; rbase += NT) {
+            const int r = rbase + lane;
+            int type = FACE, id = 0, rb = 0, rc = 0, ia = 0, len = 0, ax = 0;
+            if (r < R) {
+                int lo = 0, hi = NT - 1;  // last region whose first row is <= r
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (S.row0[mid] <= r) lo = mid; else hi = mid - 1;
+                }
+                const int fid = S.fid[lo];
+                type = feat_type(F, fid);
+                id = feat_local(F, fid, type);
+                ax = S.ax[lo];
+                const int nbv = S.nb[lo];
+                const int local = r - S.row0[lo];
+                const int qc = (int)(((float)local + 0.5f) * __frcp_rn((float)nbv));  // exact for these sizes
+                rc = S.lo_c[lo] + qc;
+                rb = S.lo_b[lo] + (local - qc * nbv);
                 int ib;
-                row_span<TYPE>(F, g, o_id, rj, rk, o_bi0, o_bi1, ia, ib);
+                span_any(F, g, type, id, ax, rb, rc, S.lo_a[lo], S.hi_a[lo], ia, ib);
                 len = max(ib - ia + 1, 0);
+                rows++;
+                hits += len > 0;
             }
+            // span points of this warp's 32 rows, flattened over the lanes
             const int pincl = warp_incl_scan(len);
             const int ptotal = __shfl_sync(FULL, pincl, 31);
             for (int p0 = 0; p0 < ptotal; p0 += 32) {
                 const int pp = p0 + lane;
                 const int ro = min(warp_owner(pincl, pp), 31);
                 const int r_start = __shfl_sync(FULL, ia - (pincl - len), ro);
-                const int r_j = __shfl_sync(FULL, rj, ro), r_k = __shfl_sync(FULL, rk, ro);
-                const int r_id = __shfl_sync(FULL, o_id, ro);
+                const int r_b = __shfl_sync(FULL, rb, ro), r_c = __shfl_sync(FULL, rc, ro);
+                const int r_id = __shfl_sync(FULL, id, ro), r_ax = __shfl_sync(FULL, ax, ro);
+                const int r_type = __shfl_sync(FULL, type, ro);
                 if (pp < ptotal) {
-                    const int pi = r_start + pp;
+                    const int pa = r_start + pp;
+                    const int pi = r_ax == 0 ? pa : r_b;
+                    const int pj = r_ax == 1 ? pa : (r_ax == 0 ? r_b : r_c);
+                    const int pk = r_ax == 2 ? pa : r_c;
                     bool neg;
-                    float d = eval_point<TYPE>(F, g, r_id, pi, r_j, r_k, neg);
+                    const float d = eval_any(F, g, r_type, r_id, pi, pj, pk, neg);
                     if (d < g.W) {
-                        unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) |
-                                                 ((unsigned long long)(unsigned)(r_id + id_base) << 1) |
-                                                 (unsigned long long)neg;
-                        int loc = ((r_k - tz0) * TILE_Y + (r_j - ty0)) * TILE_X + (pi - tx0);
-                        atomicMin(skey + loc, key);
+                        const int gid = r_type == FACE ? r_id : (r_type == EDGE ? r_id + F.T : r_id + F.T + F.E);
+                        const unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) |
+                                                       ((unsigned long long)(unsigned)gid << 1) |
+                                                       (unsigned long long)neg;
+                        const int loc = ((pk - z0) * TILE_Y + (pj - y0)) * TILE_X + (pi - x0);
+                        atomicMin(S.key + loc, key);
                         cand++;
                     }
                 }
             }
         }
+        __syncthreads();  // region descriptors are rewritten by the next pass
     }
 }
 
-__global__ void __launch_bounds__(NT) k_tile(Feat F, GridP g, Outputs o) {
-    __shared__ unsigned long long skey[TILE_PTS];
-    __shared__ unsigned s_cand, s_band, s_patch_overflow;
-    const int64_t tile = blockIdx.x;
-    const int tx = (int)(tile % g.ntx), ty = (int)((tile / g.ntx) % g.nty), tz = (int)(tile / ((int64_t)g.ntx * g.nty));
-    const int x0 = tx * TILE_X, y0 = ty * TILE_Y, z0 = tz * TILE_Z;
-    const uint32_t *st = o.bin_start + 3 * tile;
-    int64_t q0 = st[0], q1 = st[1], q2 = st[2], q3 = st[3];
-    q0 = min(q0, o.pair_cap); q1 = min(q1, o.pair_cap); q2 = min(q2, o.pair_cap); q3 = min(q3, o.pair_cap);
-    const int64_t plane = (int64_t)g.nx * g.ny;
-    if (q0 == q3) {  // no region meets this tile: +inf everywhere (Algorithm 1's initial value)
-        for (int e = threadIdx.x; e < TILE_PTS; e += NT) {
-            int x = e % TILE_X, y = (e / TILE_X) % TILE_Y, z = e / (TILE_X * TILE_Y);
-            int gi = x0 + x, gj = y0 + y, gk = z0 + z;
-            if (gi < g.nx && gj < g.ny && gk < g.nz) {
-                int64_t idx = (int64_t)gk * plane + (int64_t)gj * g.nx + gi;
-                o.dist[idx] = INFINITY;
-                if (o.winner) o.winner[idx] = -1;
-            }
-        }
-        return;
+// decode one merged key into the output value / winner, queueing FP64 re-decisions
+__device__ __forceinline__ float decode_key(unsigned long long key, const GridP &g, const Outputs &o, int64_t idx,
+                                            int &wid, unsigned &band, bool &overflow) {
+    wid = -1;
+    if (key == ~0ull) return INFINITY;
+    const float d = __uint_as_float((unsigned)(key >> 32));
+    const int fid = (int)((key >> 1) & 0x7fffffffu);
+    float val = INFINITY;
+    if (d < g.w) {
+        val = (key & 1ull) ? -d : d;
+        wid = fid;
+        band++;
     }
-    for (int e = threadIdx.x; e < TILE_PTS; e += NT) skey[e] = ~0ull;
-    if (threadIdx.x == 0) { s_cand = 0; s_band = 0; s_patch_overflow = 0; }
-    __syncthreads();
-    const int cx1 = min(x0 + TILE_X, g.nx) - 1, cy1 = min(y0 + TILE_Y, g.ny) - 1, cz1 = min(z0 + TILE_Z, g.nz) - 1;
-    unsigned cand = 0;
-    process_regions<FACE>(F, g, o.pairs, q0, q1, x0, y0, z0, cx1, cy1, cz1, skey, cand);
-    process_regions<EDGE>(F, g, o.pairs, q1, q2, x0, y0, z0, cx1, cy1, cz1, skey, cand);
-    process_regions<VERT>(F, g, o.pairs, q2, q3, x0, y0, z0, cx1, cy1, cz1, skey, cand);
-    __syncthreads();
-    unsigned band = 0;
-    for (int e = threadIdx.x; e < TILE_PTS; e += NT) {
-        int x = e % TILE_X, y = (e / TILE_X) % TILE_Y, z = e / (TILE_X * TILE_Y);
-        int gi = x0 + x, gj = y0 + y, gk = z0 + z;
-        if (gi >= g.nx || gj >= g.ny || gk >= g.nz) continue;
-        int64_t idx = (int64_t)gk * plane + (int64_t)gj * g.nx + gi;
-        unsigned long long key = skey[e];
-        float val = INFINITY;
-        int wid = -1;
-        if (key != ~0ull) {
-            float d = __uint_as_float((unsigned)(key >> 32));
-            int fid = (int)((key >> 1) & 0x7fffffffu);
-            if (d < g.w) {
-                val = (key & 1ull) ? -d : d;
-                wid = fid;
-                band++;
+    if (d < g.ds || d >= g.dlo) {  // inside the FP32 error window: re-decide in FP64
+        unsigned long long slot = atomicAdd(&o.ctr->n_patch, 1ull);
+        if ((int64_t)slot < o.patch_cap) {
+            PatchEntry pe;
+            pe.idx = idx;
+            pe.fid = fid;
+            pe.pad = 0;
+            o.patch[slot] = pe;
+        } else {
+            overflow = true;
+        }
+    }
+    return val;
+}
+
+__global__ void k_band_flags(const uint32_t *bin_start, int64_t n_tiles, uint32_t *flag) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n_tiles) flag[t] = bin_start[3 * t + 3] != bin_start[3 * t] ? 1u : 0u;
+}
+
+// Work list of the tile kernel: first the band tiles (tiles that some region meets), then chunks
+// of FILL_CHUNK empty tiles.  band_list / empty_list come from one scan of the band flags.
+constexpr int FILL_CHUNK = 32;
+
+__global__ void k_tile_lists(const uint32_t *bin_start, int64_t n_tiles, const uint32_t *band_pos,
+                             int32_t *band_list, int32_t *empty_list) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const bool band = bin_start[3 * t + 3] != bin_start[3 * t];
+    if (band) band_list[band_pos[t]] = (int32_t)t;
+    else empty_list[t - band_pos[t]] = (int32_t)t;
+}
+
+// Persistent tile kernel: CTAs take work items from one atomic ticket.  A band tile merges its
+// regions' candidates in shared memory and writes its 2048 points; an empty-tile chunk is written
+// +inf (Algorithm 1's initial value).  vec: rows are 16-byte aligned (nx % 4 == 0 and aligned
+// outputs), so a thread stores 4 consecutive x values at once.
+__global__ void __launch_bounds__(NT, 4) k_tile(Feat F, GridP g, Outputs o, int64_t n_tiles,
+                                                const int32_t *band_list, const int32_t *empty_list,
+                                                const uint32_t *n_band_ptr, unsigned long long *ticket, int vec) {
+    __shared__ TileSmem S;
+    __shared__ unsigned s_cand, s_band, s_ovf, s_rows, s_hits, s_pairs;
+    if (threadIdx.x == 0) { s_cand = 0; s_band = 0; s_ovf = 0; s_rows = 0; s_hits = 0; s_pairs = 0; }
+    unsigned cand = 0, band = 0, rows = 0, hits = 0, pairs = 0;
+    bool overflow = false;
+    const int64_t plane = (int64_t)g.nx * g.ny;
+    const int64_t n_band = *n_band_ptr, n_empty = n_tiles - n_band;
+    const int64_t n_work = n_band + (n_empty + FILL_CHUNK - 1) / FILL_CHUNK;
+    for (;;) {
+        if (threadIdx.x == 0) S.work = (long long)atomicAdd(ticket, 1ull);
+        __syncthreads();
+        const int64_t w = S.work;
+        __syncthreads();
+        if (w >= n_work) break;
+        const bool is_band = w < n_band;
+        const int64_t t_begin = is_band ? w : (w - n_band) * FILL_CHUNK;
+        const int64_t t_end = is_band ? w + 1 : min(t_begin + FILL_CHUNK, n_empty);
+        for (int64_t ti = t_begin; ti < t_end; ti++) {
+            const int64_t tile = is_band ? band_list[ti] : empty_list[ti];
+            const int tx = (int)(tile % g.ntx), ty = (int)((tile / g.ntx) % g.nty),
+                      tz = (int)(tile / ((int64_t)g.ntx * g.nty));
+            const int x0 = tx * TILE_X, y0 = ty * TILE_Y, z0 = tz * TILE_Z;
+            const int cx1 = min(x0 + TILE_X, g.nx) - 1, cy1 = min(y0 + TILE_Y, g.ny) - 1,
+                      cz1 = min(z0 + TILE_Z, g.nz) - 1;
+            if (is_band) {
+                const uint32_t *st = o.bin_start + 3 * tile;
+                const int64_t q0 = min((int64_t)st[0], o.pair_cap), q3 = min((int64_t)st[3], o.pair_cap);
+                for (int e = threadIdx.x; e < TILE_PTS; e += NT) S.key[e] = ~0ull;
+                __syncthreads();
+                process_band_tile(F, g, o.pairs, q0, q3, x0, y0, z0, cx1, cy1, cz1, S, cand, rows, hits);
+                if (threadIdx.x == 0) pairs += (unsigned)(q3 - q0);
             }
-            if (d < g.ds || d >= g.dlo) {  // inside the FP32 error window: re-decide in FP64
-                unsigned long long slot = atomicAdd(&o.ctr->n_patch, 1ull);
-                if ((int64_t)slot < o.patch_cap) {
-                    PatchEntry pe;
-                    pe.idx = idx;
-                    pe.fid = fid;
-                    pe.pad = 0;
-                    o.patch[slot] = pe;
-                } else {
-                    s_patch_overflow = 1;
+            if (vec && cx1 == x0 + TILE_X - 1) {
+                // 8 threads per 32-point row, 4 points each
+                for (int r = threadIdx.x >> 3; r < TILE_Y * TILE_Z; r += NT / 8) {
+                    const int y = r % TILE_Y, z = r / TILE_Y;
+                    const int gj = y0 + y, gk = z0 + z;
+                    if (gj > cy1 || gk > cz1) continue;
+                    const int x = (threadIdx.x & 7) * 4;
+                    const int64_t idx = (int64_t)gk * plane + (int64_t)gj * g.nx + x0 + x;
+                    float4 v = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+                    int4 wv = make_int4(-1, -1, -1, -1);
+                    if (is_band) {
+                        const unsigned long long *kp = S.key + r * TILE_X + x;
+                        v.x = decode_key(kp[0], g, o, idx, wv.x, band, overflow);
+                        v.y = decode_key(kp[1], g, o, idx + 1, wv.y, band, overflow);
+                        v.z = decode_key(kp[2], g, o, idx + 2, wv.z, band, overflow);
+                        v.w = decode_key(kp[3], g, o, idx + 3, wv.w, band, overflow);
+                    }
+                    *reinterpret_cast<float4 *>(o.dist + idx) = v;
+                    if (o.winner) *reinterpret_cast<int4 *>(o.winner + idx) = wv;
+                }
+            } else {
+                for (int e = threadIdx.x; e < TILE_PTS; e += NT) {
+                    const int x = e % TILE_X, y = (e / TILE_X) % TILE_Y, z = e / (TILE_X * TILE_Y);
+                    const int gi = x0 + x, gj = y0 + y, gk = z0 + z;
+                    if (gi > cx1 || gj > cy1 || gk > cz1) continue;
+                    const int64_t idx = (int64_t)gk * plane + (int64_t)gj * g.nx + gi;
+                    int wid = -1;
+                    const float val = is_band ? decode_key(S.key[e], g, o, idx, wid, band, overflow) : INFINITY;
+                    o.dist[idx] = val;
+                    if (o.winner) o.winner[idx] = wid;
                 }
             }
+            if (is_band) __syncthreads();  // keys are reused by the next band tile
         }
-        o.dist[idx] = val;
-        if (o.winner) o.winner[idx] = wid;
     }
     atomicAdd(&s_cand, cand);
     atomicAdd(&s_band, band);
+    atomicAdd(&s_rows, rows);
+    atomicAdd(&s_hits, hits);
+    atomicAdd(&s_pairs, pairs);
+    if (overflow) s_ovf = 1;
     __syncthreads();
     if (threadIdx.x == 0) {
         atomicAdd(&o.ctr->n_candidates, (unsigned long long)s_cand);
         atomicAdd(&o.ctr->n_band, (unsigned long long)s_band);
-        if (s_patch_overflow) atomicOr(&o.ctr->status, ST_PATCH_OVERFLOW);
+        atomicAdd(&o.ctr->n_rows, (unsigned long long)s_rows);
+        atomicAdd(&o.ctr->n_rows_hit, (unsigned long long)s_hits);
+        atomicAdd(&o.ctr->n_pairs, (unsigned long long)s_pairs);
+        if (s_ovf) atomicOr(&o.ctr->status, ST_PATCH_OVERFLOW);
     }
 }
 
@@ -599,6 +800,25 @@ static Feat make_feat(const sdf_features_s *f) {
 }
 
 // one (mesh, grid) problem; returns SDF_OK or an error; sets *retry when scratch was too small
+static int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 152;
+    }
+    return n;
+}
+static int tile_blocks_per_sm() {
+    static int b = 0;
+    if (!b) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tile, NT, 0);
+        if (b <= 0) b = 4;
+    }
+    return b;
+}
+
 int ensure_events(sdf_features_s *f) {
     for (int i = 0; i < 6; i++)
         if (!f->ev[i]) SDF_TRY(cudaEventCreate(&f->ev[i]));
@@ -617,6 +837,7 @@ static int narrow_band_one(sdf_features_s *f, const sdf_grid &gr, float w, float
     size_t bins_bytes = sizeof(uint32_t) * (size_t)(2 * n_bins + 64);
     SDF_TRY(f->bins.reserve(bins_bytes));
     SDF_TRY(f->scan_tmp.reserve(scan_tmp_bytes(n_bins)));
+    SDF_TRY(f->lists.reserve(16 + sizeof(uint32_t) * (size_t)(3 * n_tiles + 256)));
     if (f->pair_cap == 0) f->pair_cap = 8 * n_feat + 4096;
     if (f->patch_cap == 0) f->patch_cap = n_feat / 8 + 65536;
     SDF_TRY(f->pairs.reserve(sizeof(int32_t) * (size_t)f->pair_cap));
@@ -628,7 +849,7 @@ static int narrow_band_one(sdf_features_s *f, const sdf_grid &gr, float w, float
     }
     SDF_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n_bins, s));
     SDF_TRY(cudaMemsetAsync(&f->ctr->status, 0, sizeof(unsigned), s));
-    SDF_TRY(cudaMemsetAsync(&f->ctr->n_candidates, 0, 4 * sizeof(unsigned long long), s));
+    SDF_TRY(cudaMemsetAsync(&f->ctr->n_candidates, 0, 6 * sizeof(unsigned long long), s));
     k_bin<false><<<nblk(n_feat, 256), 256, 0, s>>>(F, g, cnt, nullptr, nullptr, 0, f->ctr);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
@@ -646,8 +867,25 @@ static int narrow_band_one(sdf_features_s *f, const sdf_grid &gr, float w, float
     o.patch = f->patch.as<PatchEntry>();
     o.patch_cap = f->patch_cap;
     o.ctr = f->ctr;
+    // band / empty tile lists for the persistent tile kernel (one scan of the band flags)
+    uint32_t *flags = cnt;  // the fill cursors are no longer needed
+    k_band_flags<<<nblk(n_tiles, 256), 256, 0, s>>>(start, n_tiles, flags);
+    SDF_LAUNCHED(1);
+    SDF_TRY(cudaGetLastError());
+    unsigned long long *ticket = f->lists.as<unsigned long long>();  // 8-byte aligned (allocation start)
+    uint32_t *band_pos = reinterpret_cast<uint32_t *>(ticket + 2);
+    int32_t *band_list = reinterpret_cast<int32_t *>(band_pos + n_tiles + 32);
+    int32_t *empty_list = band_list + n_tiles + 32;
+    SDF_TRY(scan_exclusive_u32(flags, band_pos, n_tiles, true, f->scan_tmp.p, s));
+    k_tile_lists<<<nblk(n_tiles, 256), 256, 0, s>>>(start, n_tiles, band_pos, band_list, empty_list);
+    SDF_LAUNCHED(1);
+    SDF_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
     if (timing) SDF_TRY(cudaEventRecord(f->ev[1], s));
-    k_tile<<<(unsigned)n_tiles, NT, 0, s>>>(F, g, o);
+    const int vec = ((g.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0) &&
+                    ((reinterpret_cast<uintptr_t>(win) & 15) == 0);
+    const int64_t tile_ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm() * num_sms());
+    k_tile<<<(unsigned)tile_ctas, NT, 0, s>>>(F, g, o, n_tiles, band_list, empty_list, band_pos + n_tiles, ticket,
+                                              vec);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
     if (timing) SDF_TRY(cudaEventRecord(f->ev[2], s));
@@ -691,7 +929,9 @@ int narrow_band_stats(sdf_features_s *f, int64_t *stats, cudaStream_t s) {
         stats[0] = (int64_t)c.n_candidates;
         stats[1] = (int64_t)c.n_band;
         stats[2] = (int64_t)c.n_patch;
-        stats[3] = 0;
+        stats[3] = (int64_t)c.n_pairs;
+        stats[4] = (int64_t)c.n_rows;
+        stats[5] = (int64_t)c.n_rows_hit;
     }
     if (c.status & (ST_PAIR_OVERFLOW | ST_PATCH_OVERFLOW)) return SDF_ERR_OOM;
     return SDF_OK;

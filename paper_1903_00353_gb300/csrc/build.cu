@@ -154,38 +154,90 @@ __global__ void k_weld_scatter(const uint32_t *vals, const uint32_t *hscan, cons
     if (i == n - 1) vert_start[vid + 1] = (int32_t)n;
 }
 
-__global__ void k_edge_keys(const int32_t *soup_vid, int64_t n, int nb, uint64_t *keys, uint32_t *vals,
-                            DevCounters *ctr) {
-    int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (h >= n) return;
-    int64_t f = h / 3;
-    int k = (int)(h - 3 * f);
-    uint32_t a = (uint32_t)soup_vid[h], b = (uint32_t)soup_vid[3 * f + (k + 1) % 3];
-    if (a == b) atomicOr(&ctr->status, ST_DEGENERATE);
-    uint32_t lo = min(a, b), hi = max(a, b);
-    keys[h] = ((uint64_t)lo << nb) | hi;
-    vals[h] = (uint32_t)h;
+// ----------------------------------------------------------------------------- spatial face order
+// key of a face: its smallest welded vertex id (vertex ids follow the Morton order of the weld),
+// so faces that are close in space get close ids and their records share cache lines
+__global__ void k_face_keys(const int32_t *soup_vid, int64_t T, uint64_t *keys, uint32_t *vals) {
+    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= T) return;
+    int32_t a = soup_vid[3 * f], b = soup_vid[3 * f + 1], c = soup_vid[3 * f + 2];
+    keys[f] = (uint64_t)(uint32_t)min(a, min(b, c));
+    vals[f] = (uint32_t)f;
 }
 
-__global__ void k_edge_pair(const uint64_t *keys, const uint32_t *vals, const int32_t *soup_vid, int64_t n,
-                            int4 *edge_vf, int32_t *face_edge, DevCounters *ctr) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n / 2) return;
-    int64_t i = 2 * e;
-    bool ok = keys[i] == keys[i + 1] && (i + 2 >= n || keys[i + 2] != keys[i]) && (i == 0 || keys[i - 1] != keys[i]);
-    uint32_t h0 = vals[i], h1 = vals[i + 1];
-    int32_t a0 = soup_vid[h0], a1 = soup_vid[h1];
-    ok = ok && a0 != a1;  // the two copies must run in opposite directions
-    if (!ok) {
-        atomicOr(&ctr->status, ST_NONMANIFOLD);
+// face_soup[f] = soup triangle of library face f; face_vid in library order; inv: soup -> library
+__global__ void k_face_perm(const uint32_t *order, const int32_t *soup_vid, int64_t T, int32_t *face_soup,
+                            int32_t *face_vid, uint32_t *inv) {
+    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= T) return;
+    uint32_t sf = order[f];
+    face_soup[f] = (int32_t)sf;
+    inv[sf] = (uint32_t)f;
+    for (int k = 0; k < 3; k++) face_vid[3 * f + k] = soup_vid[3 * (int64_t)sf + k];
+}
+
+__global__ void k_corner_remap(int32_t *vert_corner, const uint32_t *inv, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t c = vert_corner[i];
+    int32_t sf = c / 3;
+    vert_corner[i] = 3 * (int32_t)inv[sf] + (c - 3 * sf);
+}
+
+// ----------------------------------------------------------------------------- edge pairing
+// Directed edge h (corner k of face f, from vertex a to the next corner's vertex b) must meet
+// exactly one directed edge b -> a, found among the corners of b, and a -> b must occur once
+// among the corners of a (closed, consistently oriented 2-manifold).  Edges get ids in the
+// order of their smaller end point's corners, which keeps them spatially ordered too.
+__global__ void k_pair_fans(const int32_t *vert_start, const int32_t *vert_corner, const int32_t *face_vid, int64_t n,
+                            int32_t *twin, uint32_t *canon, DevCounters *ctr) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t h = vert_corner[i];
+    const int32_t f = h / 3, k = h - 3 * f;
+    const int32_t a = face_vid[h], b = face_vid[3 * f + (k + 1) % 3];
+    if (a == b) {
+        atomicOr(&ctr->status, ST_DEGENERATE);
+        canon[i] = 0;
         return;
     }
-    // f1 holds the direction va -> vb with va < vb
-    uint32_t hf1 = a0 < a1 ? h0 : h1, hf2 = a0 < a1 ? h1 : h0;
-    int32_t va = min(a0, a1), vb = max(a0, a1);
-    edge_vf[e] = make_int4(va, vb, (int32_t)(hf1 / 3), (int32_t)(hf2 / 3));
-    face_edge[h0] = (int32_t)e;
-    face_edge[h1] = (int32_t)e;
+    int32_t found = -1, nfound = 0;
+    for (int32_t q = vert_start[b]; q < vert_start[b + 1]; q++) {
+        const int32_t c = vert_corner[q];
+        const int32_t g = c / 3, kk = c - 3 * g;
+        if (face_vid[3 * g + (kk + 1) % 3] == a) {
+            found = c;
+            nfound++;
+        }
+    }
+    int32_t same = 0;
+    for (int32_t q = vert_start[a]; q < vert_start[a + 1]; q++) {
+        const int32_t c = vert_corner[q];
+        const int32_t g = c / 3, kk = c - 3 * g;
+        same += face_vid[3 * g + (kk + 1) % 3] == b;
+    }
+    if (nfound != 1 || same != 1) {
+        atomicOr(&ctr->status, ST_NONMANIFOLD);
+        canon[i] = 0;
+        return;
+    }
+    twin[h] = found;
+    canon[i] = a < b ? 1u : 0u;
+}
+
+// canonical directed edges (va < vb) create the edge records; eid = exclusive scan of canon
+__global__ void k_edge_emit(const int32_t *vert_corner, const int32_t *face_vid, const int32_t *twin,
+                            const uint32_t *canon, const uint32_t *eid, int64_t n, int4 *edge_vf,
+                            int32_t *face_edge) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || !canon[i]) return;
+    const int32_t h = vert_corner[i];
+    const int32_t f = h / 3, k = h - 3 * f;
+    const int32_t e = (int32_t)eid[i];
+    const int32_t t = twin[h];
+    edge_vf[e] = make_int4(face_vid[h], face_vid[3 * f + (k + 1) % 3], f, t / 3);
+    face_edge[h] = e;
+    face_edge[t] = e;
 }
 
 // ----------------------------------------------------------------------------- records (geometry)
@@ -341,8 +393,41 @@ __global__ void k_vertex_records(const int32_t *vert_start, const int32_t *vert_
     int8_t cls = below && above ? CLS_SADDLE : (below ? CLS_CONVEX : (above ? CLS_CONCAVE : CLS_FLAT));
     vert_class[v] = cls;
     float3 Nu = (1.f / Nlen) * N;
-    vert_rec[2 * v + 0] = make_float4(p.x, p.y, p.z, __int_as_float(s0));
-    vert_rec[2 * v + 1] = make_float4(Nu.x, Nu.y, Nu.z, __int_as_float(s1 - s0));
+    // Bound of the vertex region {y : y.e_j <= 0 for all incident edges}: a polyhedral cone whose
+    // extreme rays lie among +-(e_j x e_l).  If every extreme ray makes an angle < 90 degrees with
+    // +N_alpha (or every one with -N_alpha), the region lies in the cone of half-angle theta around
+    // that axis (used only to bound the grid rows to scan); otherwise the ball bound is used.
+    float4 cone = make_float4(0.f, 0.f, 0.f, -2.f);
+    const int deg = s1 - s0;
+    if (deg <= 24 && Nlen > 0.f) {
+        bool any = false, all_pos = true, all_neg = true;
+        float cpos = 1.f, cneg = 1.f;
+        for (int a = s0; a < s1; a++) {
+            const float3 ea = f3(vert_plane[a]);  // -e_a
+            for (int b = a + 1; b < s1; b++) {
+                const float3 eb = f3(vert_plane[b]);
+                float3 y = cross3(ea, eb);
+                const float ly = sqrtf(dot3(y, y));
+                if (!(ly > 1e-6f)) continue;
+                y = (1.f / ly) * y;
+                for (int sg = 0; sg < 2; sg++) {
+                    const float3 ys = sg ? make_float3(-y.x, -y.y, -y.z) : y;
+                    bool feas = true;
+                    for (int m = s0; m < s1 && feas; m++) feas = dot3(ys, f3(vert_plane[m])) >= -1e-4f;
+                    if (!feas) continue;
+                    any = true;
+                    const float c = dot3(ys, Nu);
+                    if (c > 0.02f) cpos = fminf(cpos, c); else all_pos = false;
+                    if (c < -0.02f) cneg = fminf(cneg, -c); else all_neg = false;
+                }
+            }
+        }
+        if (any && all_pos) cone = make_float4(Nu.x, Nu.y, Nu.z, cpos - 2e-3f);
+        else if (any && all_neg) cone = make_float4(-Nu.x, -Nu.y, -Nu.z, cneg - 2e-3f);
+    }
+    vert_rec[3 * v + 0] = make_float4(p.x, p.y, p.z, __int_as_float(s0));
+    vert_rec[3 * v + 1] = make_float4(Nu.x, Nu.y, Nu.z, __int_as_float(s1 - s0));
+    vert_rec[3 * v + 2] = cone;
     atomicAdd(&ctr->cls[cls == CLS_CONVEX ? 2 : (cls == CLS_CONCAVE ? 3 : (cls == CLS_FLAT ? 4 : 5))], 1ull);
 }
 
@@ -378,7 +463,7 @@ static int status_to_code(unsigned st) {
 
 static void free_handle(sdf_features_s *f) {
     if (!f) return;
-    void *ptrs[] = {f->face_vid, f->face_edge, f->edge_vf, f->vert_start, f->vert_corner, f->vpos, f->face_rec,
+    void *ptrs[] = {f->soup_vid, f->face_soup, f->face_vid, f->face_edge, f->edge_vf, f->vert_start, f->vert_corner, f->vpos, f->face_rec,
                     f->face_box, f->edge_rec, f->vert_rec, f->vert_plane, f->edge_class, f->vert_class, f->ctr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -387,6 +472,7 @@ static void free_handle(sdf_features_s *f) {
     f->patch.release();
     f->scan_tmp.release();
     f->fwd_winner.release();
+    f->lists.release();
     for (cudaEvent_t e : f->ev)
         if (e) cudaEventDestroy(e);
     delete f;
@@ -458,31 +544,45 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     }
     const int64_t V = Vh;
     f->V = V;
+    B_TRY(dalloc(&f->soup_vid, n));
     B_TRY(dalloc(&f->face_vid, n));
+    B_TRY(dalloc(&f->face_soup, T));
     B_TRY(dalloc(&f->face_edge, n));
     B_TRY(dalloc(&f->vert_start, V + 1));
     B_TRY(dalloc(&f->vert_corner, n));
     B_TRY(dalloc(&f->vpos, 3 * V));
-    k_weld_scatter<<<nblk(n), BT, 0, s>>>(vals, head, keys, soup, n, f->face_vid, f->vert_start, f->vert_corner,
+    k_weld_scatter<<<nblk(n), BT, 0, s>>>(vals, head, keys, soup, n, f->soup_vid, f->vert_start, f->vert_corner,
                                           f->vpos);
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
-    // edge pairing
+    // spatial face order: sort faces by their smallest (Morton-ordered) vertex id
+    int nb = 1;
+    while ((int64_t(1) << nb) < V) nb++;
+    k_face_keys<<<nblk(T), BT, 0, s>>>(f->soup_vid, T, keys, vals);
+    SDF_LAUNCHED(1);
+    B_TRY(cudaGetLastError());
+    B_TRY(radix_sort_u64(keys, vals, kalt, valt, T, nb, rtmp, s));
+    k_face_perm<<<nblk(T), BT, 0, s>>>(vals, f->soup_vid, T, f->face_soup, f->face_vid, valt);
+    SDF_LAUNCHED(1);
+    k_corner_remap<<<nblk(n), BT, 0, s>>>(f->vert_corner, valt, n);
+    SDF_LAUNCHED(1);
+    B_TRY(cudaGetLastError());
+    // edge pairing through the vertex fans
     if (n % 2) {
         tmp.release();
         free_handle(f);
         return SDF_ERR_NONMANIFOLD;
     }
-    int nb = 1;
-    while ((int64_t(1) << nb) < V) nb++;
     const int64_t E = n / 2;
     f->E = E;
-    k_edge_keys<<<nblk(n), BT, 0, s>>>(f->face_vid, n, nb, keys, vals, f->ctr);
+    int32_t *twin = reinterpret_cast<int32_t *>(kalt);  // kalt is free again
+    uint32_t *canon = valt;
+    k_pair_fans<<<nblk(n), BT, 0, s>>>(f->vert_start, f->vert_corner, f->face_vid, n, twin, canon, f->ctr);
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
-    B_TRY(radix_sort_u64(keys, vals, kalt, valt, n, 2 * nb, rtmp, s));
+    B_TRY(scan_exclusive_u32(canon, head, n, true, rtmp, s));
     B_TRY(dalloc(&f->edge_vf, E));
-    k_edge_pair<<<nblk(E), BT, 0, s>>>(keys, vals, f->face_vid, n, f->edge_vf, f->face_edge, f->ctr);
+    k_edge_emit<<<nblk(n), BT, 0, s>>>(f->vert_corner, f->face_vid, twin, canon, head, n, f->edge_vf, f->face_edge);
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
     // records
@@ -490,7 +590,7 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     B_TRY(dalloc(&f->face_box, 2 * T));
     B_TRY(dalloc(&f->edge_rec, 5 * E));
     B_TRY(dalloc(&f->edge_class, E));
-    B_TRY(dalloc(&f->vert_rec, 2 * V));
+    B_TRY(dalloc(&f->vert_rec, 3 * V));
     B_TRY(dalloc(&f->vert_plane, n));
     B_TRY(dalloc(&f->vert_class, V));
     unsigned st = 0;
@@ -503,9 +603,12 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     }
     if (build_records(f, s) != SDF_OK) B_TRY(cudaErrorUnknown);
     DevCounters c;
+    uint32_t n_canon = 0;
     B_TRY(cudaMemcpyAsync(&c, f->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaMemcpyAsync(&n_canon, head + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     B_TRY(cudaStreamSynchronize(s));
     tmp.release();
+    if (!c.status && (int64_t)n_canon != E) c.status |= ST_NONMANIFOLD;
     if (c.status) {
         int code = status_to_code(c.status);
         free_handle(f);
@@ -542,7 +645,14 @@ extern "C" int sdf_features_info(sdf_features f, int64_t *n_tri, int64_t *counts
 
 extern "C" int sdf_features_vertex_map(sdf_features f, int32_t *soup_to_vertex, void *stream) {
     if (!f || !soup_to_vertex) return SDF_ERR_INVALID_ARG;
-    SDF_TRY(cudaMemcpyAsync(soup_to_vertex, f->face_vid, sizeof(int32_t) * 3 * f->T, cudaMemcpyDeviceToDevice,
+    SDF_TRY(cudaMemcpyAsync(soup_to_vertex, f->soup_vid, sizeof(int32_t) * 3 * f->T, cudaMemcpyDeviceToDevice,
+                            reinterpret_cast<cudaStream_t>(stream)));
+    return SDF_OK;
+}
+
+extern "C" int sdf_features_face_map(sdf_features f, int32_t *face_to_soup, void *stream) {
+    if (!f || !face_to_soup) return SDF_ERR_INVALID_ARG;
+    SDF_TRY(cudaMemcpyAsync(face_to_soup, f->face_soup, sizeof(int32_t) * f->T, cudaMemcpyDeviceToDevice,
                             reinterpret_cast<cudaStream_t>(stream)));
     return SDF_OK;
 }

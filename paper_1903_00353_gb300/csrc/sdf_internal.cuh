@@ -55,6 +55,8 @@ struct DevCounters {
     unsigned long long n_band;         // band points written
     unsigned long long n_patch;        // points re-decided in FP64
     unsigned long long n_pairs;        // (tile, region) pairs scheduled
+    unsigned long long n_rows;         // grid rows intersected with a region
+    unsigned long long n_rows_hit;     // of which non-empty
     unsigned long long cls[8];         // classification counts
 };
 
@@ -64,25 +66,28 @@ struct DevCounters {
 struct sdf_features_s {
     int64_t T = 0, V = 0, E = 0;
     uint32_t flags = 0;
-    // connectivity (fixed after the build)
-    int32_t *face_vid = nullptr;    // [3T] welded vertex of each soup corner
+    // connectivity (fixed after the build); faces are stored in a spatial order (by smallest
+    // welded vertex id), face_soup maps them back to soup triangles
+    int32_t *soup_vid = nullptr;    // [3T] welded vertex of each soup corner (soup order)
+    int32_t *face_soup = nullptr;   // [T] soup triangle of each library face
+    int32_t *face_vid = nullptr;    // [3T] welded vertex of each library face corner
     int32_t *face_edge = nullptr;   // [3T] edge id of the edge from corner k to corner k+1
     int4 *edge_vf = nullptr;        // [E] (va < vb, f1 holding va->vb, f2 holding vb->va)
     int32_t *vert_start = nullptr;  // [V+1] CSR into vert_corner
-    int32_t *vert_corner = nullptr; // [3T] soup corners grouped by vertex
+    int32_t *vert_corner = nullptr; // [3T] face corners (3 f + k) grouped by vertex
     // geometry (re-evaluated by sdf_features_update_positions)
     float *vpos = nullptr;          // [V][3]
     float4 *face_rec = nullptr;     // [T][4] (n, c0) and three inward side planes (m, c)
     float4 *face_box = nullptr;     // [T][2] vertex bounding box lo, hi
     float4 *edge_rec = nullptr;     // [E][5] (a, L) (t, t.a) (-m1, m1.a) (-m2, m2.a) (n1+n2, 0)
-    float4 *vert_rec = nullptr;     // [V][2] (v, start) (unit N_alpha, count)
+    float4 *vert_rec = nullptr;     // [V][3] (v, start) (unit N_alpha, count) (cone axis, cos theta)
     float4 *vert_plane = nullptr;   // [3T] (-e_j, e_j.v) per incident edge, CSR by vert_start
     int8_t *edge_class = nullptr;   // [E]
     int8_t *vert_class = nullptr;   // [V]
     int64_t counts[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     sdf::DevCounters *ctr = nullptr; // device counters
     // narrow-band scratch, grown on demand
-    sdf::DevBuf bins, pairs, patch, scan_tmp, fwd_winner;
+    sdf::DevBuf bins, pairs, patch, scan_tmp, fwd_winner, lists;
     int64_t pair_cap = 0, patch_cap = 0;
     // stage timing (SDF_FLAG_TIMING)
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

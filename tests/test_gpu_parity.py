@@ -221,7 +221,8 @@ def test_adjoint_matches_oracle_adjoint():
         gv = sdf.sdf_narrow_band_backward(feats, grid, w, g, winner=win)
         gv2 = sdf.sdf_narrow_band_backward(feats, grid, w, g, winner=None)  # recomputed winners
         torch.cuda.synchronize()
-        assert torch.allclose(gv, gv2, rtol=1e-5, atol=1e-6)
+        # same winners, different atomicAdd order: equal up to FP32 summation rounding
+        assert float((gv - gv2).norm()) <= 1e-5 * float(gv.norm())
         band = torch.isfinite(dist).view(-1).cpu().numpy()
         idx = np.flatnonzero(band)
         pts = oracle.grid_points((N, N, N), (0, 0, 0), grid.h, idx)
