@@ -203,6 +203,34 @@ int sdf_features_timing(sdf_features f, double *ms, int64_t *calls, int reset);
 /* Process-wide number of CUDA kernels this library has launched (diagnostics). */
 int64_t sdf_kernel_launches(void);
 
+/*
+ * sdf_narrow_band_static -- the same narrow band as sdf_narrow_band for one (mesh, grid) problem,
+ * but the call allocates no device memory.  The paper has no counterpart: this entry point is
+ * for callers that cannot allocate during the call, such as a process whose device memory is
+ * owned by another runtime or a fixed budget, or a latency-bound loop.
+ *
+ * Its scratch is one library-owned device array of about 20.3 MiB that every device holding
+ * this library keeps until the process exits.  Limits: at most 65536 tiles of 32x8x8 points
+ * (e.g. a 512^3 grid), 4194304 (tile, region) pairs and 131072 points re-decided in FP64;
+ * beyond them the call returns SDF_ERR_TOO_LARGE (the grid limit before any work, the list
+ * limits after it, with the outputs unspecified).
+ *
+ * All calls share the array, and each call clears what it needs at its start.  Two calls
+ * whose work overlaps on the GPU (for example on two streams) race on it and must not be made.
+ * The first call on a device performs the set-up (it looks up the array's device address with
+ * that device current); make that first call before any stream capture.  The call
+ * synchronises `stream` once to read its status word.
+ *
+ *   f           handle from sdf_build_features.
+ *   grid        host pointer to the grid.
+ *   band_w      band half-width w > 0.
+ *   out_dist    device float[nz][ny][nx].
+ *   out_winner  device int32[nz][ny][nx] or NULL.
+ * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_TOO_LARGE, SDF_ERR_CUDA.
+ */
+int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, float band_w, float *out_dist,
+                           int32_t *out_winner, void *stream);
+
 /* Release the handle and its device memory (NULL is a no-op). */
 void sdf_features_destroy(sdf_features f);
 

@@ -59,6 +59,8 @@ def load_library(path: str | None = None):
                                            I32, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), U32, P]
     L.sdf_features_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
     L.sdf_features_vertex_map.argtypes = [P, P, P]
+    L.sdf_narrow_band_static.argtypes = [P, ctypes.POINTER(_CGrid), ctypes.c_float, P, P, P]
+    L.sdf_narrow_band_static.restype = ctypes.c_int
     L.sdf_features_face_map.argtypes = [P, P, P]
     L.sdf_features_face_map.restype = ctypes.c_int
     L.sdf_features_vertices.argtypes = [P, P, P]

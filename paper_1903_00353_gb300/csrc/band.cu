@@ -982,3 +982,129 @@ extern "C" int sdf_features_timing(sdf_features f, double *ms, int64_t *calls, i
     }
     return SDF_OK;
 }
+
+// ============================================================================= allocation-free variant
+// sdf_narrow_band_static: the narrow band of one (mesh, grid) problem without any device
+// allocation.  It exists for callers that must not allocate device memory during the call: a
+// process whose device memory is handed out by another runtime or a fixed budget (where an
+// unexpected cudaMalloc can fail or steal memory), or a real-time loop where the latency of an
+// allocation is not acceptable.  The regular sdf_narrow_band grows scratch buffers inside the
+// handle on demand, which allocates.  The first call on a device looks up the address of the
+// scratch array (which also makes the driver load this module's device data); make that first
+// call before any stream capture.
+//
+// All per-call scratch (bin counters, the (tile, region) pair list, the tile work lists, the
+// FP64 re-decision list, counters and the work ticket) lives in this one file-scope device
+// array.  Every device that loads the library holds it until the process exits.
+namespace sdf {
+namespace {
+constexpr int64_t ST_MAX_TILES = 65536;                 // 32x8x8-point tiles (512^3 points)
+constexpr int64_t ST_MAX_PAIRS = int64_t(4) << 20;      // (tile, region) pairs
+constexpr int64_t ST_MAX_PATCH = 131072;                // points re-decided in FP64
+constexpr size_t ST_OFF_CTR = 0;                        // DevCounters
+constexpr size_t ST_OFF_TICKET = 1024;                  // work ticket (8 bytes)
+constexpr size_t ST_OFF_CNT = 2048;                     // uint32 [3 * max tiles]
+constexpr size_t ST_OFF_START = ST_OFF_CNT + 4 * (3 * ST_MAX_TILES + 256);      // uint32 [3 * max tiles + 1]
+constexpr size_t ST_OFF_BANDPOS = ST_OFF_START + 4 * (3 * ST_MAX_TILES + 256);  // uint32 [max tiles + 1]
+constexpr size_t ST_OFF_BANDLIST = ST_OFF_BANDPOS + 4 * (ST_MAX_TILES + 256);   // int32 [max tiles]
+constexpr size_t ST_OFF_EMPTYLIST = ST_OFF_BANDLIST + 4 * (ST_MAX_TILES + 256); // int32 [max tiles]
+constexpr size_t ST_OFF_SCAN = ST_OFF_EMPTYLIST + 4 * (ST_MAX_TILES + 256);     // scan temporaries
+constexpr size_t ST_SCAN_BYTES = 65536;
+constexpr size_t ST_OFF_PAIRS = ST_OFF_SCAN + ST_SCAN_BYTES;                     // int32 [max pairs]
+constexpr size_t ST_OFF_PATCH = ST_OFF_PAIRS + 4 * ST_MAX_PAIRS;                 // PatchEntry [max patch]
+constexpr size_t ST_BYTES = ST_OFF_PATCH + sizeof(PatchEntry) * ST_MAX_PATCH;    // about 20.6 MiB
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_static_scratch[ST_BYTES];
+
+// device address of g_static_scratch for each device, looked up once with that device current
+static unsigned char *static_scratch_ptr(int *err) {
+    static unsigned char *ptrs[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        *err = SDF_ERR_CUDA;
+        return nullptr;
+    }
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+            *err = SDF_ERR_CUDA;
+            return nullptr;
+        }
+        ptrs[dev] = static_cast<unsigned char *>(p);
+    }
+    *err = SDF_OK;
+    return ptrs[dev];
+}
+}  // namespace sdf
+
+extern "C" int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, float band_w, float *out_dist,
+                                      int32_t *out_winner, void *stream) {
+    using namespace sdf;
+    if (!f || !grid || !out_dist) return SDF_ERR_INVALID_ARG;
+    GridP g;
+    int st = make_grid(*grid, band_w, g);
+    if (st) return st;
+    const int64_t n_tiles = (int64_t)g.ntx * g.nty * g.ntz, n_bins = 3 * n_tiles;
+    if (n_tiles > ST_MAX_TILES) return SDF_ERR_TOO_LARGE;  // grid beyond the static scratch
+    if (scan_tmp_bytes(n_bins) > ST_SCAN_BYTES) return SDF_ERR_TOO_LARGE;
+    unsigned char *base = static_scratch_ptr(&st);
+    if (st) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Feat F = make_feat(f);
+    const int64_t n_feat = f->T + f->E + f->V;
+    DevCounters *ctr = reinterpret_cast<DevCounters *>(base + ST_OFF_CTR);
+    unsigned long long *ticket = reinterpret_cast<unsigned long long *>(base + ST_OFF_TICKET);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(base + ST_OFF_CNT);
+    uint32_t *start = reinterpret_cast<uint32_t *>(base + ST_OFF_START);
+    uint32_t *band_pos = reinterpret_cast<uint32_t *>(base + ST_OFF_BANDPOS);
+    int32_t *band_list = reinterpret_cast<int32_t *>(base + ST_OFF_BANDLIST);
+    int32_t *empty_list = reinterpret_cast<int32_t *>(base + ST_OFF_EMPTYLIST);
+    void *scan_tmp = base + ST_OFF_SCAN;
+    int32_t *pairs = reinterpret_cast<int32_t *>(base + ST_OFF_PAIRS);
+    PatchEntry *patch = reinterpret_cast<PatchEntry *>(base + ST_OFF_PATCH);
+    // the array keeps the previous call's contents: clear the counters, bins and ticket
+    SDF_TRY(cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s));
+    SDF_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
+    SDF_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n_bins, s));
+    k_bin<false><<<nblk(n_feat, 256), 256, 0, s>>>(F, g, cnt, nullptr, nullptr, 0, ctr);
+    SDF_LAUNCHED(1);
+    SDF_TRY(cudaGetLastError());
+    SDF_TRY(scan_exclusive_u32(cnt, start, n_bins, true, scan_tmp, s));
+    SDF_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n_bins, s));
+    k_bin<true><<<nblk(n_feat, 256), 256, 0, s>>>(F, g, cnt, start, pairs, ST_MAX_PAIRS, ctr);
+    SDF_LAUNCHED(1);
+    SDF_TRY(cudaGetLastError());
+    k_band_flags<<<nblk(n_tiles, 256), 256, 0, s>>>(start, n_tiles, cnt);
+    SDF_LAUNCHED(1);
+    SDF_TRY(cudaGetLastError());
+    SDF_TRY(scan_exclusive_u32(cnt, band_pos, n_tiles, true, scan_tmp, s));
+    k_tile_lists<<<nblk(n_tiles, 256), 256, 0, s>>>(start, n_tiles, band_pos, band_list, empty_list);
+    SDF_LAUNCHED(1);
+    SDF_TRY(cudaGetLastError());
+    Outputs o;
+    o.dist = out_dist;
+    o.winner = out_winner;
+    o.pairs = pairs;
+    o.bin_start = start;
+    o.pair_cap = ST_MAX_PAIRS;
+    o.patch = patch;
+    o.patch_cap = ST_MAX_PATCH;
+    o.ctr = ctr;
+    const int vec = ((g.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(out_dist) & 15) == 0) &&
+                    ((reinterpret_cast<uintptr_t>(out_winner) & 15) == 0);
+    const int64_t tile_ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm() * num_sms());
+    k_tile<<<(unsigned)tile_ctas, NT, 0, s>>>(F, g, o, n_tiles, band_list, empty_list, band_pos + n_tiles, ticket,
+                                              vec);
+    SDF_LAUNCHED(1);
+    SDF_TRY(cudaGetLastError());
+    k_patch<<<4 * 152, 256, 0, s>>>(F, g, o);
+    SDF_LAUNCHED(1);
+    SDF_TRY(cudaGetLastError());
+    // read the status word: a pair or re-decision list beyond the static limits is an error
+    unsigned status = 0;
+    SDF_TRY(cudaMemcpyAsync(&status, &ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    SDF_TRY(cudaStreamSynchronize(s));
+    if (status & (ST_PAIR_OVERFLOW | ST_PATCH_OVERFLOW)) return SDF_ERR_TOO_LARGE;
+    return SDF_OK;
+}
