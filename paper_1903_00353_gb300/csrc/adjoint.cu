@@ -20,6 +20,7 @@ constexpr unsigned FULL = 0xffffffffu;
 struct AdjArgs {
     int T, E, V;
     int nx, ny, nz;
+    FastDiv div_nx, div_ny;
     float ox, oy, oz, h;
     const float *grad;
     const int32_t *winner;
@@ -53,91 +54,155 @@ __device__ __forceinline__ void warp_add(float *gv, int v, float gx, float gy, f
     }
 }
 
-__global__ void k_adjoint(AdjArgs a) {
-    const int64_t n = (int64_t)a.nx * a.ny * a.nz;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += stride) {
-        const int64_t idx = base + threadIdx.x;
-        int wid = -1;
-        float g = 0.f;
-        if (idx < n) {
-            wid = a.winner[idx];
-            if (wid >= 0) g = a.grad[idx];
+// contribution of band point idx (winner wid, upstream gradient g) to at most 3 vertices
+__device__ __forceinline__ int point_adjoint(const AdjArgs &a, int64_t idx, int wid, float g, int *vtx, float (*c)[3]) {
+    int i, j, k;
+    if (idx < (int64_t(1) << 31)) {
+        const uint32_t iu = (uint32_t)idx, r1 = a.div_nx.div(iu), r2 = a.div_ny.div(r1);
+        i = (int)(iu - r1 * (uint32_t)a.nx);
+        j = (int)(r1 - r2 * (uint32_t)a.ny);
+        k = (int)r2;
+    } else {
+        const int64_t plane = (int64_t)a.nx * a.ny;
+        k = (int)(idx / plane);
+        j = (int)((idx - (int64_t)k * plane) / a.nx);
+        i = (int)(idx - (int64_t)k * plane - (int64_t)j * a.nx);
+    }
+    const float3 p = make_float3(fmaf((float)i + 0.5f, a.h, a.ox), fmaf((float)j + 0.5f, a.h, a.oy),
+                                 fmaf((float)k + 0.5f, a.h, a.oz));
+    if (wid < a.T) {
+        // barycentric weights of the projection of p onto the face plane; s (p - q)/|p - q| = n
+        const int f = wid;
+        const float3 A = load_vpos(a.vpos, a.face_vid[3 * f]), B = load_vpos(a.vpos, a.face_vid[3 * f + 1]),
+                     C = load_vpos(a.vpos, a.face_vid[3 * f + 2]);
+        const float3 n = f3(a.face_rec[4 * f]);
+        const float3 ab = B - A, ac = C - A, ap = p - A;
+        const float d00 = dot3(ab, ab), d01 = dot3(ab, ac), d11 = dot3(ac, ac);
+        const float d20 = dot3(ap, ab), d21 = dot3(ap, ac);
+        const float den = d00 * d11 - d01 * d01;
+        float lb = (d11 * d20 - d01 * d21) / den, lc = (d00 * d21 - d01 * d20) / den;
+        // points of the inclusion margin project just outside: clamp onto the triangle
+        lb = fmaxf(lb, 0.f);
+        lc = fmaxf(lc, 0.f);
+        const float sum = lb + lc;
+        if (sum > 1.f) { lb /= sum; lc /= sum; }
+        const float lam[3] = {1.f - lb - lc, lb, lc};
+        for (int q = 0; q < 3; q++) {
+            vtx[q] = a.face_vid[3 * f + q];
+            c[q][0] = -g * lam[q] * n.x;
+            c[q][1] = -g * lam[q] * n.y;
+            c[q][2] = -g * lam[q] * n.z;
         }
-        bool act = wid >= 0 && g != 0.f;
-        if (!__any_sync(FULL, act)) continue;
-        int vtx[3] = {0, 0, 0};
-        float c[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-        int nv = 0;
-        if (act) {
-            const int64_t plane = (int64_t)a.nx * a.ny;
-            const int k = (int)(idx / plane), j = (int)((idx - (int64_t)k * plane) / a.nx),
-                      i = (int)(idx - (int64_t)k * plane - (int64_t)j * a.nx);
-            const float3 p = make_float3(fmaf((float)i + 0.5f, a.h, a.ox), fmaf((float)j + 0.5f, a.h, a.oy),
-                                         fmaf((float)k + 0.5f, a.h, a.oz));
-            if (wid < a.T) {
-                // barycentric weights of the projection of p onto the face plane
-                const int f = wid;
-                float3 A = load_vpos(a.vpos, a.face_vid[3 * f]), B = load_vpos(a.vpos, a.face_vid[3 * f + 1]),
-                       C = load_vpos(a.vpos, a.face_vid[3 * f + 2]);
-                float3 n = f3(a.face_rec[4 * f]);
-                float3 ab = B - A, ac = C - A, ap = p - A;
-                float d00 = dot3(ab, ab), d01 = dot3(ab, ac), d11 = dot3(ac, ac);
-                float d20 = dot3(ap, ab), d21 = dot3(ap, ac);
-                float den = d00 * d11 - d01 * d01;
-                float lb = (d11 * d20 - d01 * d21) / den, lc = (d00 * d21 - d01 * d20) / den;
-                // points of the inclusion margin project just outside: clamp onto the triangle
-                lb = fmaxf(lb, 0.f);
-                lc = fmaxf(lc, 0.f);
-                float sum = lb + lc;
-                if (sum > 1.f) { lb /= sum; lc /= sum; }
-                float la = 1.f - lb - lc;
-                float lam[3] = {la, lb, lc};
-                for (int q = 0; q < 3; q++) {
-                    vtx[q] = a.face_vid[3 * f + q];
-                    c[q][0] = -g * lam[q] * n.x;
-                    c[q][1] = -g * lam[q] * n.y;
-                    c[q][2] = -g * lam[q] * n.z;
-                }
-                nv = 3;
-            } else if (wid < a.T + a.E) {
-                const int e = wid - a.T;
-                const int4 q = a.edge_vf[e];
-                float4 r0 = a.edge_rec[5 * e], r1 = a.edge_rec[5 * e + 1], np = a.edge_rec[5 * e + 4];
-                float3 u = p - f3(r0);
-                float t = fminf(fmaxf(dot3(u, f3(r1)), 0.f), r0.w);
-                float3 d = u - t * f3(r1);
-                float len = sqrtf(dot3(d, d));
-                if (len > 0.f) {
-                    float s = dot3(d, f3(np)) < 0.f ? -1.f : 1.f;
-                    float tt = t / r0.w;
-                    float lam[2] = {1.f - tt, tt};
-                    float k0 = -g * s / len;
-                    for (int qq = 0; qq < 2; qq++) {
-                        vtx[qq] = qq == 0 ? q.x : q.y;
-                        c[qq][0] = k0 * lam[qq] * d.x;
-                        c[qq][1] = k0 * lam[qq] * d.y;
-                        c[qq][2] = k0 * lam[qq] * d.z;
-                    }
-                    nv = 2;
-                }
+        return 3;
+    } else if (wid < a.T + a.E) {
+        const int e = wid - a.T;
+        const int4 q = a.edge_vf[e];
+        const float4 r0 = a.edge_rec[5 * e], r1 = a.edge_rec[5 * e + 1], np = a.edge_rec[5 * e + 4];
+        const float3 u = p - f3(r0);
+        const float t = fminf(fmaxf(dot3(u, f3(r1)), 0.f), r0.w);
+        const float3 d = u - t * f3(r1);
+        const float len = sqrtf(dot3(d, d));
+        if (!(len > 0.f)) return 0;
+        const float s = dot3(d, f3(np)) < 0.f ? -1.f : 1.f;
+        const float tt = t / r0.w;
+        const float lam[2] = {1.f - tt, tt};
+        const float k0 = -g * s / len;
+        for (int qq = 0; qq < 2; qq++) {
+            vtx[qq] = qq == 0 ? q.x : q.y;
+            c[qq][0] = k0 * lam[qq] * d.x;
+            c[qq][1] = k0 * lam[qq] * d.y;
+            c[qq][2] = k0 * lam[qq] * d.z;
+        }
+        return 2;
+    } else {
+        const int v = wid - a.T - a.E;
+        const float4 r0 = a.vert_rec[3 * v], r1 = a.vert_rec[3 * v + 1];
+        const float3 d = p - f3(r0);
+        const float len = sqrtf(dot3(d, d));
+        if (!(len > 0.f)) return 0;
+        const float s = dot3(d, f3(r1)) < 0.f ? -1.f : 1.f;
+        const float k0 = -g * s / len;
+        vtx[0] = v;
+        c[0][0] = k0 * d.x;
+        c[0][1] = k0 * d.y;
+        c[0][2] = k0 * d.z;
+        return 1;
+    }
+}
+
+__device__ __forceinline__ int warp_incl_scan_i(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+__device__ __forceinline__ int warp_owner_i(int incl, int r) {
+    int lo = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const int v = __shfl_sync(FULL, incl, lo + s - 1);
+        if (v <= r) lo += s;
+    }
+    return lo;
+}
+
+// Each lane reads the winners of 4 consecutive grid points (one int4 when vec is set); the band
+// points of the warp's 128 points are then compacted over the lanes (warp scan of the per-lane
+// counts) so every lane of a pass works on a band point, and neighbouring points, which mostly
+// share a winner, are merged by warp_add before the atomics.
+__global__ void __launch_bounds__(256) k_adjoint(AdjArgs a, int vec) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = (int64_t)a.nx * a.ny * a.nz;
+    const int64_t n4 = (n + 3) / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n4; base += stride) {
+        const int64_t q4 = base + threadIdx.x;
+        int w4[4] = {-1, -1, -1, -1};
+        if (q4 < n4) {
+            if (vec) {
+                const int4 w = __ldg(reinterpret_cast<const int4 *>(a.winner) + q4);
+                w4[0] = w.x; w4[1] = w.y; w4[2] = w.z; w4[3] = w.w;
             } else {
-                const int v = wid - a.T - a.E;
-                float4 r0 = a.vert_rec[3 * v], r1 = a.vert_rec[3 * v + 1];
-                float3 d = p - f3(r0);
-                float len = sqrtf(dot3(d, d));
-                if (len > 0.f) {
-                    float s = dot3(d, f3(r1)) < 0.f ? -1.f : 1.f;
-                    float k0 = -g * s / len;
-                    vtx[0] = v;
-                    c[0][0] = k0 * d.x;
-                    c[0][1] = k0 * d.y;
-                    c[0][2] = k0 * d.z;
-                    nv = 1;
-                }
+                for (int u = 0; u < 4; u++)
+                    if (4 * q4 + u < n) w4[u] = __ldg(a.winner + 4 * q4 + u);
             }
         }
-        for (int q = 0; q < 3; q++) warp_add(a.gv, vtx[q], c[q][0], c[q][1], c[q][2], act && q < nv);
+        const int cnt = (w4[0] >= 0) + (w4[1] >= 0) + (w4[2] >= 0) + (w4[3] >= 0);
+        const int incl = warp_incl_scan_i(cnt);
+        const int total = __shfl_sync(FULL, incl, 31);
+        for (int c0 = 0; c0 < total; c0 += 32) {
+            const int k = c0 + lane;
+            const int o = min(warp_owner_i(incl, k), 31);
+            const int excl = __shfl_sync(FULL, incl - cnt, o);
+            const int ow0 = __shfl_sync(FULL, w4[0], o), ow1 = __shfl_sync(FULL, w4[1], o);
+            const int ow2 = __shfl_sync(FULL, w4[2], o), ow3 = __shfl_sync(FULL, w4[3], o);
+            bool act = false;
+            int wid = -1;
+            int64_t idx = 0;
+            float g = 0.f;
+            if (k < total) {
+                int r = k - excl;  // r-th band point among the owner's four
+                const int ow[4] = {ow0, ow1, ow2, ow3};
+                int u = 0;
+                for (; u < 4; u++) {
+                    if (ow[u] >= 0) {
+                        if (r == 0) break;
+                        r--;
+                    }
+                }
+                wid = ow[u];
+                idx = 4 * (base + (threadIdx.x & ~31) + o) + u;
+                g = __ldg(a.grad + idx);
+                act = g != 0.f;
+            }
+            int vtx[3] = {0, 0, 0};
+            float c[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+            const int nv = act ? point_adjoint(a, idx, wid, g, vtx, c) : 0;
+            for (int q = 0; q < 3; q++) warp_add(a.gv, vtx[q], c[q][0], c[q][1], c[q][2], q < nv);
+        }
     }
 }
 
@@ -165,7 +230,7 @@ extern "C" int sdf_narrow_band_backward(const sdf_features *feats, const sdf_gri
         const int32_t *win = winner ? winner[p] : nullptr;
         if (!win) {  // recompute the winners with a forward pass into library scratch
             if (!band_w) return SDF_ERR_INVALID_ARG;
-            SDF_TRY(f->fwd_winner.reserve((size_t)npts * (sizeof(int32_t) + sizeof(float))));
+            SDF_TRY(f->fwd_winner.reserve((size_t)npts * (sizeof(int32_t) + sizeof(float)), s));
             int32_t *w = f->fwd_winner.as<int32_t>();
             float *dscratch = reinterpret_cast<float *>(w + npts);
             float *const dl[1] = {dscratch};
@@ -178,20 +243,23 @@ extern "C" int sdf_narrow_band_backward(const sdf_features *feats, const sdf_gri
         AdjArgs a;
         a.T = (int)f->T; a.E = (int)f->E; a.V = (int)f->V;
         a.nx = gr.nx; a.ny = gr.ny; a.nz = gr.nz;
+        a.div_nx = FastDiv((uint32_t)gr.nx);
+        a.div_ny = FastDiv((uint32_t)gr.ny);
         a.ox = gr.origin[0]; a.oy = gr.origin[1]; a.oz = gr.origin[2]; a.h = gr.h;
         a.grad = grad_dist[p];
         a.winner = win;
         a.gv = grad_vertices[p];
         a.face_rec = f->face_rec; a.edge_rec = f->edge_rec; a.vert_rec = f->vert_rec;
         a.face_vid = f->face_vid; a.edge_vf = f->edge_vf; a.vpos = f->vpos;
-        int64_t blocks = (npts + 255) / 256;
+        int64_t blocks = ((npts + 3) / 4 + 255) / 256;
         if (blocks > 152 * 16) blocks = 152 * 16;
+        const int vec = (npts % 4 == 0) && ((reinterpret_cast<uintptr_t>(win) & 15) == 0);
         const bool timing = (flags & SDF_FLAG_TIMING) != 0;
         if (timing) {
             if (ensure_events(f)) return SDF_ERR_CUDA;
             SDF_TRY(cudaEventRecord(f->ev[4], s));
         }
-        k_adjoint<<<(unsigned)blocks, 256, 0, s>>>(a);
+        k_adjoint<<<(unsigned)blocks, 256, 0, s>>>(a, vec);
         SDF_LAUNCHED(1);
         SDF_TRY(cudaGetLastError());
         if (timing) {

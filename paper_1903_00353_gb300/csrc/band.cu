@@ -37,12 +37,13 @@ namespace sdf {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int NT = 256;  // threads per tile CTA
+constexpr int NT = 256;  // threads per tile CTA (and regions per pass)
 enum { FACE = 0, EDGE = 1, VERT = 2 };
 
 struct GridP {
     int nx, ny, nz;
     int ntx, nty, ntz;
+    FastDiv div_ntx, div_nty, div_nx, div_ny;  // tile and grid index decomposition
     float ox, oy, oz, h, inv_h;
     float w;     // band half-width: in band iff |d| < w
     float W;     // candidate cutoff w + dw
@@ -340,36 +341,64 @@ __device__ __forceinline__ float eval_any(const Feat &F, const GridP &g, int typ
     return eval_point<VERT>(F, g, id, i, j, k, neg);
 }
 
-// per-tile shared state of the tile kernel
+// ----------------------------------------------------------------------------- per-tile row coefficients
+// For a region and its scan axis a (other axes b < c), every half-space m.p + w >= -eps becomes,
+// on the row with relative indices (ib, ic), a bound on the relative index j along a that is
+// linear in (ib, ic):  j >= A + B ib + C ic (lower, m_a > 0), j <= ... (upper, m_a < 0), or, when
+// m_a = 0, a gate A + B ib + C ic >= 0 that empties the row.  The vertex ball adds
+// |j - j_v| <= sqrt(R^2 - (db0 + ib)^2 - (dc0 + ic)^2) in index units.  The coefficients are
+// computed once per (region, tile) and kept in shared memory, so a row costs a few FMAs per plane.
+// Vertex regions keep at most MAXVP of their planes: dropping planes only enlarges the region,
+// and a point outside the exact vertex region has a strictly closer point on an incident edge.
+constexpr int KMAX = 7, MAXVP = 6, ROW_TABLE = 4096;
+enum { K_LOWER = 0, K_UPPER = 1, K_GATE = 2 };
+
 struct TileSmem {
     unsigned long long key[TILE_PTS];  // packed (|d| bits << 32 | id << 1 | sign), one per tile point
-    int fid[NT];                       // regions of the current pass
+    float4 coef[NT][KMAX];             // span coefficients (A, B, C, kind) per region of the pass
+    float4 ball[NT];                   // vertex ball in index units (j_v, db0, dc0, R^2), R^2 < 0: none
+    int fid[NT];                       // regions of the current pass (global feature ids)
     int row0[NT + 1];                  // exclusive prefix of their row counts
-    int lo_a[NT], hi_a[NT], lo_b[NT], lo_c[NT];
-    unsigned char ax[NT], nb[NT];
+    int lo_a[NT], lo_b[NT], lo_c[NT];
+    unsigned char ax[NT], nb[NT], span_hi[NT], ncoef[NT];
+    unsigned char owner[ROW_TABLE];    // region (pass slot) of each row, for rows < ROW_TABLE
     int wtot[NT / 32];
     long long work;
 };
 
-// All regions of one band tile, with the rows of every region flattened over all 8 warps of
-// the CTA: (1) one thread per region computes its box clipped to the tile, its scan axis (the
-// longest side) and its row count; (2) a block scan numbers the rows; (3) each lane takes one
-// row, finds its region by binary search, and intersects the row with the region's half-spaces
-// (Algorithm 2) to get a span; (4) the span points of a warp are flattened over its lanes and
-// merged into the tile's keys with a shared-memory atomicMin (Algorithm 1).
+__device__ __forceinline__ void add_coef(float4 *E, int &ne, float4 P, int ax, int bx, int cx, float pb0, float pc0,
+                                         float K, const GridP &g) {
+    const float ma = comp(P, ax), mb = comp(P, bx), mc = comp(P, cx);
+    const float r0 = fmaf(mb, pb0, fmaf(mc, pc0, P.w)) + g.eps;
+    if (ma != 0.f) {
+        const float inv = 1.f / ma;
+        E[ne++] = make_float4(fmaf(-r0 * inv, g.inv_h, -K), -mb * inv, -mc * inv, ma > 0.f ? K_LOWER : K_UPPER);
+    } else {
+        E[ne++] = make_float4(r0, mb * g.h, mc * g.h, K_GATE);
+    }
+}
+
+// All regions of one band tile, with the rows of every region shared by all 8 warps of the CTA:
+// (1) one thread per region computes its box clipped to the tile, its scan axis (the longest
+// side), its row count and its span coefficients; (2) a block scan numbers the rows; (3) each
+// lane takes one row and evaluates the span from the coefficients (Algorithm 2 on a grid line);
+// (4) the span points of a warp are flattened over its lanes and merged into the tile's keys with
+// a shared-memory atomicMin (Algorithm 1).
 __device__ void process_band_tile(const Feat &F, const GridP &g, const int32_t *pairs, int64_t q0, int64_t q3,
                                   int x0, int y0, int z0, int cx1, int cy1, int cz1, TileSmem &S, unsigned &cand,
                                   unsigned &rows, unsigned &hits) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = threadIdx.x;
+    const float3 org = make_float3(g.ox, g.oy, g.oz);
     for (int64_t base = q0; base < q3; base += NT) {
-        const int64_t q = base + threadIdx.x;
+        const int64_t q = base + t;
         int nrows = 0;
         {
-            int fid = 0, lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};
+            int fid = 0, lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1}, type = FACE, id = 0;
             if (q < q3) {
                 fid = __ldg(pairs + q);
-                const int type = feat_type(F, fid);
-                if (box_any(F, g, type, feat_local(F, fid, type), lo, hi)) {
+                type = feat_type(F, fid);
+                id = feat_local(F, fid, type);
+                if (box_any(F, g, type, id, lo, hi)) {
                     lo[0] = max(lo[0], x0); hi[0] = min(hi[0], cx1);
                     lo[1] = max(lo[1], y0); hi[1] = min(hi[1], cy1);
                     lo[2] = max(lo[2], z0); hi[2] = min(hi[2], cz1);
@@ -382,49 +411,126 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int32_t *
             const int bx = ax == 0 ? 1 : 0, cx = ax == 2 ? 1 : 2;
             const int nb = bx == 0 ? n0 : n1, nc = cx == 1 ? n1 : n2;
             nrows = (n0 > 0 && n1 > 0 && n2 > 0) ? nb * nc : 0;
-            S.fid[threadIdx.x] = fid;
-            S.ax[threadIdx.x] = (unsigned char)ax;
-            S.nb[threadIdx.x] = (unsigned char)max(nb, 1);
-            S.lo_a[threadIdx.x] = ax == 0 ? lo[0] : (ax == 1 ? lo[1] : lo[2]);
-            S.hi_a[threadIdx.x] = ax == 0 ? hi[0] : (ax == 1 ? hi[1] : hi[2]);
-            S.lo_b[threadIdx.x] = bx == 0 ? lo[0] : lo[1];
-            S.lo_c[threadIdx.x] = cx == 1 ? lo[1] : lo[2];
+            const int la = ax == 0 ? lo[0] : (ax == 1 ? lo[1] : lo[2]);
+            const int ha = ax == 0 ? hi[0] : (ax == 1 ? hi[1] : hi[2]);
+            const int lb = bx == 0 ? lo[0] : lo[1];
+            const int lc = cx == 1 ? lo[1] : lo[2];
+            S.fid[t] = fid;
+            S.ax[t] = (unsigned char)ax;
+            S.nb[t] = (unsigned char)max(nb, 1);
+            S.lo_a[t] = la;
+            S.lo_b[t] = lb;
+            S.lo_c[t] = lc;
+            S.span_hi[t] = (unsigned char)max(ha - la, 0);
+            int ne = 0;
+            float4 ballv = make_float4(0.f, 0.f, 0.f, -1.f);
+            if (nrows > 0) {
+                const float pb0 = fmaf((float)lb + 0.5f, g.h, comp3(org, bx));
+                const float pc0 = fmaf((float)lc + 0.5f, g.h, comp3(org, cx));
+                const float K = comp3(org, ax) * g.inv_h + 0.5f + (float)la;  // j = (p_a - o_a)/h - 1/2 - lo_a
+                float4 *E = S.coef[t];  // written directly to shared memory
+                if (type == FACE) {
+                    const float4 *r = F.face_rec + 4 * id;
+                    const float4 n = __ldg(r);
+                    add_coef(E, ne, make_float4(n.x, n.y, n.z, n.w + g.W), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, ne, make_float4(-n.x, -n.y, -n.z, g.W - n.w), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, ne, __ldg(r + 1), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, ne, __ldg(r + 2), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, ne, __ldg(r + 3), ax, bx, cx, pb0, pc0, K, g);
+                } else if (type == EDGE) {
+                    const float4 *r = F.edge_rec + 5 * id;
+                    const float4 a = __ldg(r), tt = __ldg(r + 1);
+                    add_coef(E, ne, make_float4(tt.x, tt.y, tt.z, -tt.w), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, ne, make_float4(-tt.x, -tt.y, -tt.z, tt.w + a.w), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, ne, __ldg(r + 2), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, ne, __ldg(r + 3), ax, bx, cx, pb0, pc0, K, g);
+                } else {
+                    const float4 v = __ldg(F.vert_rec + 3 * id), nv = __ldg(F.vert_rec + 3 * id + 1);
+                    const int s0 = __float_as_int(v.w), cnt = min(__float_as_int(nv.w), MAXVP);
+                    for (int k = 0; k < cnt; k++)
+                        add_coef(E, ne, __ldg(F.vert_plane + s0 + k), ax, bx, cx, pb0, pc0, K, g);
+                    const float3 vv = f3(v);
+                    const float Rh = (g.W + g.eps) * g.inv_h;
+                    ballv = make_float4((comp3(vv, ax) - comp3(org, ax)) * g.inv_h - 0.5f - (float)la,
+                                        (pb0 - comp3(vv, bx)) * g.inv_h, (pc0 - comp3(vv, cx)) * g.inv_h, Rh * Rh);
+                }
+            }
+            S.ncoef[t] = (unsigned char)ne;
+            S.ball[t] = ballv;
         }
         // block exclusive scan of the row counts
         const int incl = warp_incl_scan(nrows);
         if (lane == 31) S.wtot[warp] = incl;
         __syncthreads();
         if (warp == 0) {
-            const int t = lane < NT / 32 ? S.wtot[lane] : 0;
-            const int ti = warp_incl_scan(t);
-            if (lane < NT / 32) S.wtot[lane] = ti - t;
+            const int tv = lane < NT / 32 ? S.wtot[lane] : 0;
+            const int ti = warp_incl_scan(tv);
+            if (lane < NT / 32) S.wtot[lane] = ti - tv;
             if (lane == NT / 32 - 1) S.row0[NT] = ti;
         }
         __syncthreads();
-        S.row0[threadIdx.x] = S.wtot[warp] + incl - nrows;
+        {
+            const int r0 = S.wtot[warp] + incl - nrows;
+            S.row0[t] = r0;
+            for (int r = r0; r < min(r0 + nrows, ROW_TABLE); r++) S.owner[r] = (unsigned char)t;
+        }
         __syncthreads();
         const int R = S.row0[NT];
         for (int rbase = warp * 32; rbase < R; rbase += NT) {
             const int r = rbase + lane;
-            int type = FACE, id = 0, rb = 0, rc = 0, ia = 0, len = 0, ax = 0;
+            int type = FACE, id = 0, pb = 0, pc = 0, ia = 0, len = 0, ax = 0;
             if (r < R) {
-                int lo = 0, hi = NT - 1;  // last region whose first row is <= r
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (S.row0[mid] <= r) lo = mid; else hi = mid - 1;
+                int reg;
+                if (r < ROW_TABLE) {
+                    reg = S.owner[r];
+                } else {  // last region whose first row is <= r
+                    int lo = 0, hi = NT - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (S.row0[mid] <= r) lo = mid; else hi = mid - 1;
+                    }
+                    reg = lo;
                 }
-                const int fid = S.fid[lo];
+                const int fid = S.fid[reg];
                 type = feat_type(F, fid);
                 id = feat_local(F, fid, type);
-                ax = S.ax[lo];
-                const int nbv = S.nb[lo];
-                const int local = r - S.row0[lo];
-                const int qc = (int)(((float)local + 0.5f) * __frcp_rn((float)nbv));  // exact for these sizes
-                rc = S.lo_c[lo] + qc;
-                rb = S.lo_b[lo] + (local - qc * nbv);
-                int ib;
-                span_any(F, g, type, id, ax, rb, rc, S.lo_a[lo], S.hi_a[lo], ia, ib);
-                len = max(ib - ia + 1, 0);
+                ax = S.ax[reg];
+                const int nbv = S.nb[reg];
+                const int local = r - S.row0[reg];
+                const int ic = (int)(((float)local + 0.5f) * __frcp_rn((float)nbv));  // exact for these sizes
+                const int ib = local - ic * nbv;
+                const float fb = (float)ib, fc = (float)ic;
+                float lo_f = -1e30f, hi_f = 1e30f;
+                bool open = true;
+                const int ne = S.ncoef[reg];
+                for (int k = 0; k < ne; k++) {
+                    const float4 E = S.coef[reg][k];
+                    const float v = fmaf(E.y, fb, fmaf(E.z, fc, E.x));
+                    if (E.w == (float)K_LOWER) lo_f = fmaxf(lo_f, v);
+                    else if (E.w == (float)K_UPPER) hi_f = fminf(hi_f, v);
+                    else open = open && v >= 0.f;
+                }
+                const float4 bl = S.ball[reg];
+                if (bl.w >= 0.f) {
+                    const float db = bl.y + fb, dc = bl.z + fc;
+                    const float q2 = bl.w - db * db - dc * dc;
+                    if (q2 < 0.f) {
+                        open = false;
+                    } else {
+                        const float sq = sqrtf(q2);
+                        lo_f = fmaxf(lo_f, bl.x - sq);
+                        hi_f = fminf(hi_f, bl.x + sq);
+                    }
+                }
+                const float sl = 1.f / 4096.f;
+                const float span_hi = (float)S.span_hi[reg];
+                const float fa = fminf(fmaxf(lo_f - sl, 0.f), span_hi + 1.f);
+                const float fz = fmaxf(fminf(hi_f + sl, span_hi), -1.f);
+                const int ja = (int)ceilf(fa), jb = (int)floorf(fz);
+                len = open ? max(jb - ja + 1, 0) : 0;
+                ia = S.lo_a[reg] + ja;
+                pb = S.lo_b[reg] + ib;
+                pc = S.lo_c[reg] + ic;
                 rows++;
                 hits += len > 0;
             }
@@ -435,7 +541,7 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int32_t *
                 const int pp = p0 + lane;
                 const int ro = min(warp_owner(pincl, pp), 31);
                 const int r_start = __shfl_sync(FULL, ia - (pincl - len), ro);
-                const int r_b = __shfl_sync(FULL, rb, ro), r_c = __shfl_sync(FULL, rc, ro);
+                const int r_b = __shfl_sync(FULL, pb, ro), r_c = __shfl_sync(FULL, pc, ro);
                 const int r_id = __shfl_sync(FULL, id, ro), r_ax = __shfl_sync(FULL, ax, ro);
                 const int r_type = __shfl_sync(FULL, type, ro);
                 if (pp < ptotal) {
@@ -511,30 +617,36 @@ __global__ void k_tile_lists(const uint32_t *bin_start, int64_t n_tiles, const u
 // regions' candidates in shared memory and writes its 2048 points; an empty-tile chunk is written
 // +inf (Algorithm 1's initial value).  vec: rows are 16-byte aligned (nx % 4 == 0 and aligned
 // outputs), so a thread stores 4 consecutive x values at once.
-__global__ void __launch_bounds__(NT, 4) k_tile(Feat F, GridP g, Outputs o, int64_t n_tiles,
+__global__ void __launch_bounds__(NT, 3) k_tile(Feat F, GridP g, Outputs o, int64_t n_tiles,
                                                 const int32_t *band_list, const int32_t *empty_list,
                                                 const uint32_t *n_band_ptr, unsigned long long *ticket, int vec) {
-    __shared__ TileSmem S;
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    TileSmem &S = *reinterpret_cast<TileSmem *>(tile_smem);
     __shared__ unsigned s_cand, s_band, s_ovf, s_rows, s_hits, s_pairs;
     if (threadIdx.x == 0) { s_cand = 0; s_band = 0; s_ovf = 0; s_rows = 0; s_hits = 0; s_pairs = 0; }
     unsigned cand = 0, band = 0, rows = 0, hits = 0, pairs = 0;
     bool overflow = false;
     const int64_t plane = (int64_t)g.nx * g.ny;
     const int64_t n_band = *n_band_ptr, n_empty = n_tiles - n_band;
-    const int64_t n_work = n_band + (n_empty + FILL_CHUNK - 1) / FILL_CHUNK;
+    // work item w < n_band: band tile w plus its share of the empty tiles, so that the HBM-bound
+    // +inf fill is spread over the compute-bound band work; without band tiles, chunks of empties
+    const int64_t n_work = n_band > 0 ? n_band : (n_empty + FILL_CHUNK - 1) / FILL_CHUNK;
     for (;;) {
         if (threadIdx.x == 0) S.work = (long long)atomicAdd(ticket, 1ull);
         __syncthreads();
         const int64_t w = S.work;
         __syncthreads();
         if (w >= n_work) break;
-        const bool is_band = w < n_band;
-        const int64_t t_begin = is_band ? w : (w - n_band) * FILL_CHUNK;
-        const int64_t t_end = is_band ? w + 1 : min(t_begin + FILL_CHUNK, n_empty);
+        // empty tiles [e_begin, e_end) of this item
+        const int64_t e_begin = n_band > 0 ? (w * n_empty) / n_band : w * FILL_CHUNK;
+        const int64_t e_end = n_band > 0 ? ((w + 1) * n_empty) / n_band : min(e_begin + FILL_CHUNK, n_empty);
+        const int64_t t_begin = n_band > 0 ? -1 : 0;  // -1 = the band tile of the item
+        const int64_t t_end = e_end - e_begin;
         for (int64_t ti = t_begin; ti < t_end; ti++) {
-            const int64_t tile = is_band ? band_list[ti] : empty_list[ti];
-            const int tx = (int)(tile % g.ntx), ty = (int)((tile / g.ntx) % g.nty),
-                      tz = (int)(tile / ((int64_t)g.ntx * g.nty));
+            const bool is_band = ti < 0;
+            const int64_t tile = is_band ? band_list[w] : empty_list[e_begin + ti];
+            const uint32_t tu = (uint32_t)tile, r1 = g.div_ntx.div(tu), tz = g.div_nty.div(r1);
+            const int tx = (int)(tu - r1 * (uint32_t)g.ntx), ty = (int)(r1 - tz * (uint32_t)g.nty);
             const int x0 = tx * TILE_X, y0 = ty * TILE_Y, z0 = tz * TILE_Z;
             const int cx1 = min(x0 + TILE_X, g.nx) - 1, cy1 = min(y0 + TILE_Y, g.ny) - 1,
                       cz1 = min(z0 + TILE_Z, g.nz) - 1;
@@ -667,28 +779,43 @@ __global__ void k_patch(Feat F, GridP g, Outputs o) {
         const int64_t idx = pe.idx;
         const int fid = pe.fid;
         const int64_t plane = (int64_t)g.nx * g.ny;
-        const int gk = (int)(idx / plane), gj = (int)((idx - (int64_t)gk * plane) / g.nx),
-                  gi = (int)(idx - (int64_t)gk * plane - (int64_t)gj * g.nx);
+        int gi, gj, gk;
+        if (idx < (int64_t(1) << 31)) {
+            const uint32_t iu = (uint32_t)idx, r1 = g.div_nx.div(iu), r2 = g.div_ny.div(r1);
+            gi = (int)(iu - r1 * (uint32_t)g.nx);
+            gj = (int)(r1 - r2 * (uint32_t)g.ny);
+            gk = (int)r2;
+        } else {
+            gk = (int)(idx / plane);
+            gj = (int)((idx - (int64_t)gk * plane) / g.nx);
+            gi = (int)(idx - (int64_t)gk * plane - (int64_t)gj * g.nx);
+        }
         const double3 p = make_double3((double)g.ox + (gi + 0.5) * h, (double)g.oy + (gj + 0.5) * h,
                                        (double)g.oz + (gk + 0.5) * h);
         int vs[3], nv;
         if (fid < F.T) { vs[0] = F.face_vid[3 * fid]; vs[1] = F.face_vid[3 * fid + 1]; vs[2] = F.face_vid[3 * fid + 2]; nv = 3; }
         else if (fid < F.T + F.E) { int4 q = F.edge_vf[fid - F.T]; vs[0] = q.x; vs[1] = q.y; vs[2] = 0; nv = 2; }
         else { vs[0] = fid - F.T - F.E; vs[1] = vs[2] = 0; nv = 1; }
+        // the fans of the winner's vertices, concatenated; lanes take one corner (triangle) each
+        int c0[3], cn[3];
+        for (int a = 0; a < 3; a++) {
+            c0[a] = a < nv ? F.vert_start[vs[a]] : 0;
+            cn[a] = a < nv ? F.vert_start[vs[a] + 1] - c0[a] : 0;
+        }
+        const int total = cn[0] + cn[1] + cn[2];
         double bd = INFINITY;
         int bt = 0x7fffffff, breg = 0;
         double3 blam = make_double3(0, 0, 0);
-        for (int a = 0; a < nv; a++) {
-            const int c0 = F.vert_start[vs[a]], c1 = F.vert_start[vs[a] + 1];
-            for (int c = c0 + lane; c < c1; c += 32) {
-                const int t = F.vert_corner[c] / 3;
-                int reg;
-                double3 lam;
-                double d2 = closest_on_tri(p, d3(load_vpos(F.vpos, F.face_vid[3 * t])),
-                                           d3(load_vpos(F.vpos, F.face_vid[3 * t + 1])),
-                                           d3(load_vpos(F.vpos, F.face_vid[3 * t + 2])), reg, lam);
-                if (d2 < bd || (d2 == bd && t < bt)) { bd = d2; bt = t; breg = reg; blam = lam; }
-            }
+        for (int slot = lane; slot < total; slot += 32) {
+            const int a = slot < cn[0] ? 0 : (slot < cn[0] + cn[1] ? 1 : 2);
+            const int c = c0[a] + slot - (a == 0 ? 0 : (a == 1 ? cn[0] : cn[0] + cn[1]));
+            const int t = F.vert_corner[c] / 3;
+            int reg;
+            double3 lam;
+            double d2 = closest_on_tri(p, d3(load_vpos(F.vpos, F.face_vid[3 * t])),
+                                       d3(load_vpos(F.vpos, F.face_vid[3 * t + 1])),
+                                       d3(load_vpos(F.vpos, F.face_vid[3 * t + 2])), reg, lam);
+            if (d2 < bd || (d2 == bd && t < bt)) { bd = d2; bt = t; breg = reg; blam = lam; }
         }
         // warp argmin over (d2, triangle)
         int src = lane;
@@ -767,6 +894,10 @@ static int make_grid(const sdf_grid &gr, float w, GridP &g) {
     g.nty = (gr.ny + TILE_Y - 1) / TILE_Y;
     g.ntz = (gr.nz + TILE_Z - 1) / TILE_Z;
     if ((int64_t)g.ntx * g.nty * g.ntz * 3 >= (int64_t(1) << 31)) return SDF_ERR_TOO_LARGE;
+    g.div_ntx = FastDiv((uint32_t)g.ntx);
+    g.div_nty = FastDiv((uint32_t)g.nty);
+    g.div_nx = FastDiv((uint32_t)gr.nx);
+    g.div_ny = FastDiv((uint32_t)gr.ny);
     g.ox = gr.origin[0]; g.oy = gr.origin[1]; g.oz = gr.origin[2];
     g.h = gr.h;
     g.inv_h = 1.0f / gr.h;
@@ -813,8 +944,9 @@ static int num_sms() {
 static int tile_blocks_per_sm() {
     static int b = 0;
     if (!b) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tile, NT, 0);
-        if (b <= 0) b = 4;
+        cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tile, NT, sizeof(TileSmem));
+        if (b <= 0) b = 1;
     }
     return b;
 }
@@ -835,13 +967,13 @@ static int narrow_band_one(sdf_features_s *f, const sdf_grid &gr, float w, float
     const int64_t n_feat = f->T + f->E + f->V;
     // scratch: cnt [n_bins], start [n_bins + 1], scan temporaries
     size_t bins_bytes = sizeof(uint32_t) * (size_t)(2 * n_bins + 64);
-    SDF_TRY(f->bins.reserve(bins_bytes));
-    SDF_TRY(f->scan_tmp.reserve(scan_tmp_bytes(n_bins)));
-    SDF_TRY(f->lists.reserve(16 + sizeof(uint32_t) * (size_t)(3 * n_tiles + 256)));
+    SDF_TRY(f->bins.reserve(bins_bytes, s));
+    SDF_TRY(f->scan_tmp.reserve(scan_tmp_bytes(n_bins), s));
+    SDF_TRY(f->lists.reserve(16 + sizeof(uint32_t) * (size_t)(3 * n_tiles + 256), s));
     if (f->pair_cap == 0) f->pair_cap = 8 * n_feat + 4096;
     if (f->patch_cap == 0) f->patch_cap = n_feat / 8 + 65536;
-    SDF_TRY(f->pairs.reserve(sizeof(int32_t) * (size_t)f->pair_cap));
-    SDF_TRY(f->patch.reserve(sizeof(PatchEntry) * (size_t)f->patch_cap));
+    SDF_TRY(f->pairs.reserve(sizeof(int32_t) * (size_t)f->pair_cap, s));
+    SDF_TRY(f->patch.reserve(sizeof(PatchEntry) * (size_t)f->patch_cap, s));
     uint32_t *cnt = f->bins.as<uint32_t>(), *start = cnt + n_bins + 32;
     if (timing) {
         if (ensure_events(f)) return SDF_ERR_CUDA;
@@ -884,7 +1016,7 @@ static int narrow_band_one(sdf_features_s *f, const sdf_grid &gr, float w, float
     const int vec = ((g.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0) &&
                     ((reinterpret_cast<uintptr_t>(win) & 15) == 0);
     const int64_t tile_ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm() * num_sms());
-    k_tile<<<(unsigned)tile_ctas, NT, 0, s>>>(F, g, o, n_tiles, band_list, empty_list, band_pos + n_tiles, ticket,
+    k_tile<<<(unsigned)tile_ctas, NT, sizeof(TileSmem), s>>>(F, g, o, n_tiles, band_list, empty_list, band_pos + n_tiles, ticket,
                                               vec);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
@@ -1094,7 +1226,7 @@ extern "C" int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, floa
     const int vec = ((g.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(out_dist) & 15) == 0) &&
                     ((reinterpret_cast<uintptr_t>(out_winner) & 15) == 0);
     const int64_t tile_ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm() * num_sms());
-    k_tile<<<(unsigned)tile_ctas, NT, 0, s>>>(F, g, o, n_tiles, band_list, empty_list, band_pos + n_tiles, ticket,
+    k_tile<<<(unsigned)tile_ctas, NT, sizeof(TileSmem), s>>>(F, g, o, n_tiles, band_list, empty_list, band_pos + n_tiles, ticket,
                                               vec);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());

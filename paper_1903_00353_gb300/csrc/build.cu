@@ -91,7 +91,7 @@ __global__ void k_weld_keys(const float *soup, int64_t n3, const float *bb, uint
     }
     uint64_t morton = (uint64_t)(expand10(q[0]) | (expand10(q[1]) << 1) | (expand10(q[2]) << 2));
     uint64_t hsh = mix64(((uint64_t)__float_as_uint(x) << 32 | __float_as_uint(y)) ^ mix64(__float_as_uint(z) + 0x9e3779b97f4a7c15ull));
-    keys[s] = (morton << 34) | (hsh & ((1ull << 34) - 1));
+    keys[s] = (morton << 18) | (hsh & ((1ull << 18) - 1));  // 48-bit key: 6 radix passes
     vals[s] = (uint32_t)s;
 }
 
@@ -314,7 +314,7 @@ __global__ void k_edge_records(const int4 *edge_vf, const int32_t *face_vid, con
     edge_rec[5 * e + 4] = make_float4(np.x, np.y, np.z, 0.f);
     float d = dot3(cross3(t, n1), n2);
     int8_t cls;
-    if (fabsf(d) > 1e-5f) {
+    if (fabsf(d) > 2e-6f) {
         cls = d > 0.f ? CLS_CONVEX : CLS_CONCAVE;
     } else {  // filtered predicate: decide near-flat edges in FP64
         double3 A = d3(a), B = d3(b);
@@ -325,8 +325,14 @@ __global__ void k_edge_records(const int4 *edge_vf, const int32_t *face_vid, con
         cls = dd > tol ? CLS_CONVEX : (dd < -tol ? CLS_CONCAVE : CLS_FLAT);
     }
     edge_class[e] = cls;
-    if (cls == CLS_CONVEX) atomicAdd(&ctr->cls[6], 1ull);
-    else if (cls == CLS_CONCAVE) atomicAdd(&ctr->cls[7], 1ull);
+    // class counts: one atomic per warp and class (same-address atomics serialise in L2)
+    const unsigned act = __activemask();
+    const unsigned ncv = __popc(__ballot_sync(act, cls == CLS_CONVEX));
+    const unsigned ncc = __popc(__ballot_sync(act, cls == CLS_CONCAVE));
+    if ((threadIdx.x & 31) == __ffs(act) - 1) {
+        if (ncv) atomicAdd(&ctr->cls[6], (unsigned long long)ncv);
+        if (ncc) atomicAdd(&ctr->cls[7], (unsigned long long)ncc);
+    }
 }
 
 __device__ __forceinline__ float corner_angle(float3 e1, float3 e2) {
@@ -334,101 +340,161 @@ __device__ __forceinline__ float corner_angle(float3 e1, float3 e2) {
     return atan2f(sqrtf(dot3(cr, cr)), dot3(e1, e2));
 }
 
-// vertex records (Section 8.3): N_alpha = sum alpha_i n_i (Eq. 8), one plane (p - v).e_j <= 0 per
-// incident edge (the region where no incident edge leads closer than v), and the class from the
-// signs of (v_n - v).N_alpha over the neighbours (FP32 when clear, FP64 otherwise).
+constexpr int VL = 8;  // lanes per vertex in k_vertex_records
+
+__device__ __forceinline__ float gsum8(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 4, VL);
+    v += __shfl_xor_sync(0xffffffffu, v, 2, VL);
+    v += __shfl_xor_sync(0xffffffffu, v, 1, VL);
+    return v;
+}
+__device__ __forceinline__ float gmin8(float v) {
+    v = fminf(v, __shfl_xor_sync(0xffffffffu, v, 4, VL));
+    v = fminf(v, __shfl_xor_sync(0xffffffffu, v, 2, VL));
+    v = fminf(v, __shfl_xor_sync(0xffffffffu, v, 1, VL));
+    return v;
+}
+__device__ __forceinline__ bool gor8(bool b) {
+    int v = b;
+    v |= __shfl_xor_sync(0xffffffffu, v, 4, VL);
+    v |= __shfl_xor_sync(0xffffffffu, v, 2, VL);
+    v |= __shfl_xor_sync(0xffffffffu, v, 1, VL);
+    return v != 0;
+}
+
+// vertex records (Section 8.3), 8 lanes per vertex, each lane taking every 8th corner of the fan:
+// N_alpha = sum alpha_i n_i (Eq. 8); one plane (p - v).e_j <= 0 per incident edge (the region where
+// no incident edge leads closer than v); the class from the signs of (v_n - v).N_alpha over the
+// neighbours (FP32 when clear, FP64 otherwise); and a cone bounding the vertex region.
 __global__ void k_vertex_records(const int32_t *vert_start, const int32_t *vert_corner, const int32_t *face_vid,
                                  const float *vpos, const float4 *face_rec, int64_t V, float4 *vert_rec,
                                  float4 *vert_plane, int8_t *vert_class, DevCounters *ctr) {
-    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (v >= V) return;
-    int s0 = vert_start[v], s1 = vert_start[v + 1];
-    float3 p = load_vpos(vpos, (int)v);
+    const int64_t gl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t v = gl / VL;
+    const int sub = (int)(gl % VL);
+    const bool valid = v < V;
+    const int s0 = valid ? vert_start[v] : 0, s1 = valid ? vert_start[v + 1] : 0;
+    const float3 p = valid ? load_vpos(vpos, (int)v) : make_float3(0.f, 0.f, 0.f);
+    // pass 1: pseudonormal and region planes
     float3 N = make_float3(0.f, 0.f, 0.f);
-    for (int i = s0; i < s1; i++) {
-        int c = vert_corner[i];
-        int f = c / 3, k = c - 3 * f;
-        float3 xn = load_vpos(vpos, face_vid[3 * f + (k + 1) % 3]);
-        float3 xp = load_vpos(vpos, face_vid[3 * f + (k + 2) % 3]);
-        float3 e1 = xn - p, e2 = xp - p;
+    for (int i = s0 + sub; i < s1; i += VL) {
+        const int c = vert_corner[i];
+        const int f = c / 3, k = c - 3 * f;
+        const float3 xn = load_vpos(vpos, face_vid[3 * f + (k + 1) % 3]);
+        const float3 xp = load_vpos(vpos, face_vid[3 * f + (k + 2) % 3]);
+        const float3 e1 = xn - p, e2 = xp - p;
         N = N + corner_angle(e1, e2) * f3(face_rec[4 * f]);
-        float3 ej = normalized(e1);
+        const float3 ej = normalized(e1);
         vert_plane[i] = make_float4(-ej.x, -ej.y, -ej.z, dot3(ej, p));
     }
-    float Nlen = sqrtf(dot3(N, N));
-    bool below = false, above = false, unsure = false;
-    for (int i = s0; i < s1; i++) {
-        int c = vert_corner[i];
-        int f = c / 3, k = c - 3 * f;
-        float3 dv = load_vpos(vpos, face_vid[3 * f + (k + 1) % 3]) - p;
-        float d = dot3(dv, N);
-        float bound = 1e-5f * sqrtf(dot3(dv, dv)) * Nlen;
+    N = make_float3(gsum8(N.x), gsum8(N.y), gsum8(N.z));
+    const float Nlen = sqrtf(dot3(N, N));
+    const float3 Nu = (Nlen > 0.f ? 1.f / Nlen : 0.f) * N;
+    __syncwarp();  // the group's planes are written before they are read back
+    // pass 2: classification (FP32 with an error margin), convexity and the normal spread
+    bool below = false, above = false, unsure = false, cvx = true, ccv = true;
+    float cmin = 1.f;
+    for (int i = s0 + sub; i < s1; i += VL) {
+        const int c = vert_corner[i];
+        const float3 ej = -1.f * f3(vert_plane[i]);  // unit direction to the next neighbour
+        const float3 dv = load_vpos(vpos, face_vid[3 * (c / 3) + ((c % 3) + 1) % 3]) - p;
+        const float d = dot3(dv, N);
+        const float bound = 2e-6f * sqrtf(dot3(dv, dv)) * Nlen;
         if (d < -bound) below = true;
         else if (d > bound) above = true;
         else unsure = true;
-    }
-    if (unsure) {  // FP64 filtered predicate
-        below = above = false;
-        double3 P = d3(p), ND = make_double3(0, 0, 0);
-        for (int i = s0; i < s1; i++) {
-            int c = vert_corner[i];
-            int f = c / 3, k = c - 3 * f;
-            double3 e1 = d3(load_vpos(vpos, face_vid[3 * f + (k + 1) % 3])) - P;
-            double3 e2 = d3(load_vpos(vpos, face_vid[3 * f + (k + 2) % 3])) - P;
-            double3 cr = dcross3(e1, e2);
-            double alpha = atan2(sqrt(ddot3(cr, cr)), ddot3(e1, e2));
-            ND = ND + alpha * face_normal_fp64(face_vid, vpos, f);
+        const float3 nf = f3(face_rec[4 * (c / 3)]);
+        cmin = fminf(cmin, dot3(nf, Nu));
+        for (int b = s0; b < s1; b++) {  // every incident edge against this face's plane
+            const float dd = -dot3(nf, f3(vert_plane[b]));
+            cvx = cvx && dd <= 1e-4f;
+            ccv = ccv && dd >= -1e-4f;
         }
-        double NL = sqrt(ddot3(ND, ND));
-        for (int i = s0; i < s1; i++) {
-            int c = vert_corner[i];
-            int f = c / 3, k = c - 3 * f;
-            double3 dv = d3(load_vpos(vpos, face_vid[3 * f + (k + 1) % 3])) - P;
-            double d = ddot3(dv, ND);
-            double tol = 1e-12 * sqrt(ddot3(dv, dv)) * NL;
-            if (d < -tol) below = true;
-            else if (d > tol) above = true;
-        }
+        (void)ej;
     }
-    int8_t cls = below && above ? CLS_SADDLE : (below ? CLS_CONVEX : (above ? CLS_CONCAVE : CLS_FLAT));
-    vert_class[v] = cls;
-    float3 Nu = (1.f / Nlen) * N;
-    // Bound of the vertex region {y : y.e_j <= 0 for all incident edges}: a polyhedral cone whose
-    // extreme rays lie among +-(e_j x e_l).  If every extreme ray makes an angle < 90 degrees with
-    // +N_alpha (or every one with -N_alpha), the region lies in the cone of half-angle theta around
-    // that axis (used only to bound the grid rows to scan); otherwise the ball bound is used.
-    float4 cone = make_float4(0.f, 0.f, 0.f, -2.f);
-    const int deg = s1 - s0;
-    if (deg <= 24 && Nlen > 0.f) {
-        bool any = false, all_pos = true, all_neg = true;
-        float cpos = 1.f, cneg = 1.f;
-        for (int a = s0; a < s1; a++) {
-            const float3 ea = f3(vert_plane[a]);  // -e_a
-            for (int b = a + 1; b < s1; b++) {
-                const float3 eb = f3(vert_plane[b]);
-                float3 y = cross3(ea, eb);
-                const float ly = sqrtf(dot3(y, y));
-                if (!(ly > 1e-6f)) continue;
-                y = (1.f / ly) * y;
-                for (int sg = 0; sg < 2; sg++) {
-                    const float3 ys = sg ? make_float3(-y.x, -y.y, -y.z) : y;
-                    bool feas = true;
-                    for (int m = s0; m < s1 && feas; m++) feas = dot3(ys, f3(vert_plane[m])) >= -1e-4f;
-                    if (!feas) continue;
-                    any = true;
-                    const float c = dot3(ys, Nu);
-                    if (c > 0.02f) cpos = fminf(cpos, c); else all_pos = false;
-                    if (c < -0.02f) cneg = fminf(cneg, -c); else all_neg = false;
-                }
+    below = gor8(below);
+    above = gor8(above);
+    unsure = gor8(unsure);
+    cvx = !gor8(!cvx);
+    ccv = !gor8(!ccv);
+    cmin = gmin8(cmin);
+    int8_t my_cls = 99;  // class of the vertex held by lane sub == 0
+    if (valid && sub == 0) {
+        if (unsure) {  // FP64 filtered predicate (rare): recompute N_alpha and the signs in FP64
+            below = above = false;
+            const double3 P = d3(p);
+            double3 ND = make_double3(0, 0, 0);
+            for (int i = s0; i < s1; i++) {
+                const int c = vert_corner[i];
+                const int f = c / 3, k = c - 3 * f;
+                const double3 e1 = d3(load_vpos(vpos, face_vid[3 * f + (k + 1) % 3])) - P;
+                const double3 e2 = d3(load_vpos(vpos, face_vid[3 * f + (k + 2) % 3])) - P;
+                const double3 cr = dcross3(e1, e2);
+                const double alpha = atan2(sqrt(ddot3(cr, cr)), ddot3(e1, e2));
+                ND = ND + alpha * face_normal_fp64(face_vid, vpos, f);
+            }
+            const double NL = sqrt(ddot3(ND, ND));
+            for (int i = s0; i < s1; i++) {
+                const int c = vert_corner[i];
+                const int f = c / 3, k = c - 3 * f;
+                const double3 dv = d3(load_vpos(vpos, face_vid[3 * f + (k + 1) % 3])) - P;
+                const double d = ddot3(dv, ND);
+                const double tol = 1e-12 * sqrt(ddot3(dv, dv)) * NL;
+                if (d < -tol) below = true;
+                else if (d > tol) above = true;
             }
         }
-        if (any && all_pos) cone = make_float4(Nu.x, Nu.y, Nu.z, cpos - 2e-3f);
-        else if (any && all_neg) cone = make_float4(-Nu.x, -Nu.y, -Nu.z, cneg - 2e-3f);
+        const int8_t cls = below && above ? CLS_SADDLE : (below ? CLS_CONVEX : (above ? CLS_CONCAVE : CLS_FLAT));
+        vert_class[v] = cls;
+        // Bound of the vertex region {y : y.e_j <= 0}.  Locally convex (every incident edge below
+        // every incident face plane): the cone spanned by the face normals; locally concave: by
+        // their negatives; otherwise the extreme rays are searched among +-(e_j x e_l).  A cone
+        // is kept only if all its rays lie within 89 degrees of +N_alpha (or of -N_alpha).
+        float4 cone = make_float4(0.f, 0.f, 0.f, -2.f);
+        const int deg = s1 - s0;
+        if (Nlen > 0.f) {
+            if (cvx && !ccv && cmin > 0.02f) {
+                cone = make_float4(Nu.x, Nu.y, Nu.z, cmin - 2e-3f);
+            } else if (ccv && !cvx && cmin > 0.02f) {
+                cone = make_float4(-Nu.x, -Nu.y, -Nu.z, cmin - 2e-3f);
+            } else if (deg <= 24) {
+                bool any = false, all_pos = true, all_neg = true;
+                float cpos = 1.f, cng = 1.f;
+                for (int a = s0; a < s1; a++) {
+                    const float3 ea = f3(vert_plane[a]);  // -e_a
+                    for (int b = a + 1; b < s1; b++) {
+                        const float3 eb = f3(vert_plane[b]);
+                        float3 y = cross3(ea, eb);
+                        const float ly = sqrtf(dot3(y, y));
+                        if (!(ly > 1e-6f)) continue;
+                        y = (1.f / ly) * y;
+                        for (int sg = 0; sg < 2; sg++) {
+                            const float3 ys = sg ? make_float3(-y.x, -y.y, -y.z) : y;
+                            bool feas = true;
+                            for (int m = s0; m < s1 && feas; m++) feas = dot3(ys, f3(vert_plane[m])) >= -1e-4f;
+                            if (!feas) continue;
+                            any = true;
+                            const float cc = dot3(ys, Nu);
+                            if (cc > 0.02f) cpos = fminf(cpos, cc); else all_pos = false;
+                            if (cc < -0.02f) cng = fminf(cng, -cc); else all_neg = false;
+                        }
+                    }
+                }
+                if (any && all_pos) cone = make_float4(Nu.x, Nu.y, Nu.z, cpos - 2e-3f);
+                else if (any && all_neg) cone = make_float4(-Nu.x, -Nu.y, -Nu.z, cng - 2e-3f);
+            }
+        }
+        vert_rec[3 * v + 0] = make_float4(p.x, p.y, p.z, __int_as_float(s0));
+        vert_rec[3 * v + 1] = make_float4(Nu.x, Nu.y, Nu.z, __int_as_float(s1 - s0));
+        vert_rec[3 * v + 2] = cone;
+        my_cls = cls;
     }
-    vert_rec[3 * v + 0] = make_float4(p.x, p.y, p.z, __int_as_float(s0));
-    vert_rec[3 * v + 1] = make_float4(Nu.x, Nu.y, Nu.z, __int_as_float(s1 - s0));
-    vert_rec[3 * v + 2] = cone;
-    atomicAdd(&ctr->cls[cls == CLS_CONVEX ? 2 : (cls == CLS_CONCAVE ? 3 : (cls == CLS_FLAT ? 4 : 5))], 1ull);
+    // class counts: one atomic per warp and class (same-address atomics serialise in L2)
+    for (int c = 0; c < 4; c++) {
+        const int8_t want = c == 0 ? CLS_CONVEX : (c == 1 ? CLS_CONCAVE : (c == 2 ? CLS_FLAT : CLS_SADDLE));
+        const unsigned n = __popc(__ballot_sync(0xffffffffu, my_cls == want));
+        if ((threadIdx.x & 31) == 0 && n) atomicAdd(&ctr->cls[2 + c], (unsigned long long)n);
+    }
 }
 
 inline unsigned nblk(int64_t n) { return (unsigned)((n + BT - 1) / BT); }
@@ -442,7 +508,7 @@ int build_records(sdf_features_s *f, cudaStream_t s) {
         k_edge_records<<<nblk(f->E), BT, 0, s>>>(f->edge_vf, f->face_vid, f->vpos, f->face_rec, f->E, f->edge_rec,
                                                 f->edge_class, f->ctr);
         SDF_LAUNCHED(1);
-        k_vertex_records<<<nblk(f->V), BT, 0, s>>>(f->vert_start, f->vert_corner, f->face_vid, f->vpos, f->face_rec,
+        k_vertex_records<<<nblk(f->V * VL), BT, 0, s>>>(f->vert_start, f->vert_corner, f->face_vid, f->vpos, f->face_rec,
                                                   f->V, f->vert_rec, f->vert_plane, f->vert_class, f->ctr);
         SDF_LAUNCHED(1);
     }
@@ -461,32 +527,35 @@ static int status_to_code(unsigned st) {
     return SDF_OK;
 }
 
+// frees on the legacy default stream, after the caller's work on the handle has completed
 static void free_handle(sdf_features_s *f) {
     if (!f) return;
+    cudaDeviceSynchronize();  // no work may still use the handle's memory
+    cudaStream_t s0 = 0;
     void *ptrs[] = {f->soup_vid, f->face_soup, f->face_vid, f->face_edge, f->edge_vf, f->vert_start, f->vert_corner, f->vpos, f->face_rec,
                     f->face_box, f->edge_rec, f->vert_rec, f->vert_plane, f->edge_class, f->vert_class, f->ctr};
     for (void *p : ptrs)
-        if (p) cudaFree(p);
-    f->bins.release();
-    f->pairs.release();
-    f->patch.release();
-    f->scan_tmp.release();
-    f->fwd_winner.release();
-    f->lists.release();
+        if (p) pool_free(p, s0);
+    f->bins.release(s0);
+    f->pairs.release(s0);
+    f->patch.release(s0);
+    f->scan_tmp.release(s0);
+    f->fwd_winner.release(s0);
+    f->lists.release(s0);
     for (cudaEvent_t e : f->ev)
         if (e) cudaEventDestroy(e);
     delete f;
 }
 
-template <class T> static cudaError_t dalloc(T **p, int64_t n) {
-    return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (size_t)(n > 0 ? n : 1));
+template <class T> static cudaError_t dalloc_s(T **p, int64_t n, cudaStream_t s) {
+    return pool_alloc(reinterpret_cast<void **>(p), sizeof(T) * (size_t)(n > 0 ? n : 1), s);
 }
 
 #define B_TRY(expr)                                       \
     do {                                                  \
         cudaError_t e_ = (expr);                          \
         if (e_ != cudaSuccess) {                          \
-            tmp.release();                                \
+            tmp.release(s);                                \
             free_handle(f);                               \
             return e_ == cudaErrorMemoryAllocation ? SDF_ERR_OOM : SDF_ERR_CUDA; \
         }                                                 \
@@ -507,7 +576,7 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     size_t off_keys = 0, off_kalt = off_keys + 8 * n, off_vals = off_kalt + 8 * n, off_valt = off_vals + 4 * n,
            off_head = off_valt + 4 * n, off_bb = off_head + 4 * (n + 1) + 64, off_rtmp = off_bb + 64;
     size_t need = off_rtmp + radix_tmp_bytes(n) + scan_tmp_bytes(n + 1) + 1024;
-    B_TRY(tmp.reserve(need));
+    B_TRY(tmp.reserve(need, s));
     char *base = tmp.as<char>();
     uint64_t *keys = reinterpret_cast<uint64_t *>(base + off_keys), *kalt = reinterpret_cast<uint64_t *>(base + off_kalt);
     uint32_t *vals = reinterpret_cast<uint32_t *>(base + off_vals), *valt = reinterpret_cast<uint32_t *>(base + off_valt);
@@ -515,7 +584,7 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     float *bb = reinterpret_cast<float *>(base + off_bb);
     void *rtmp = base + off_rtmp;
 
-    B_TRY(dalloc(&f->ctr, 1));
+    B_TRY(dalloc_s(&f->ctr, 1, s));
     B_TRY(cudaMemsetAsync(f->ctr, 0, sizeof(DevCounters), s));
     float bb_init[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
     B_TRY(cudaMemcpyAsync(bb, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
@@ -524,7 +593,7 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     k_weld_keys<<<nblk(n), BT, 0, s>>>(soup, n, bb, keys, vals);
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
-    B_TRY(radix_sort_u64(keys, vals, kalt, valt, n, 64, rtmp, s));
+    B_TRY(radix_sort_u64(keys, vals, kalt, valt, n, 48, rtmp, s));
     k_weld_fix<<<nblk(n), BT, 0, s>>>(keys, vals, soup, n);
     SDF_LAUNCHED(1);
     k_weld_heads<<<nblk(n), BT, 0, s>>>(keys, vals, soup, n, valt);
@@ -538,19 +607,19 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     B_TRY(cudaMemcpyAsync(&st_h, &f->ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     B_TRY(cudaStreamSynchronize(s));
     if (st_h) {
-        tmp.release();
+        tmp.release(s);
         free_handle(f);
         return status_to_code(st_h);
     }
     const int64_t V = Vh;
     f->V = V;
-    B_TRY(dalloc(&f->soup_vid, n));
-    B_TRY(dalloc(&f->face_vid, n));
-    B_TRY(dalloc(&f->face_soup, T));
-    B_TRY(dalloc(&f->face_edge, n));
-    B_TRY(dalloc(&f->vert_start, V + 1));
-    B_TRY(dalloc(&f->vert_corner, n));
-    B_TRY(dalloc(&f->vpos, 3 * V));
+    B_TRY(dalloc_s(&f->soup_vid, n, s));
+    B_TRY(dalloc_s(&f->face_vid, n, s));
+    B_TRY(dalloc_s(&f->face_soup, T, s));
+    B_TRY(dalloc_s(&f->face_edge, n, s));
+    B_TRY(dalloc_s(&f->vert_start, V + 1, s));
+    B_TRY(dalloc_s(&f->vert_corner, n, s));
+    B_TRY(dalloc_s(&f->vpos, 3 * V, s));
     k_weld_scatter<<<nblk(n), BT, 0, s>>>(vals, head, keys, soup, n, f->soup_vid, f->vert_start, f->vert_corner,
                                           f->vpos);
     SDF_LAUNCHED(1);
@@ -569,7 +638,7 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     B_TRY(cudaGetLastError());
     // edge pairing through the vertex fans
     if (n % 2) {
-        tmp.release();
+        tmp.release(s);
         free_handle(f);
         return SDF_ERR_NONMANIFOLD;
     }
@@ -581,23 +650,23 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
     B_TRY(scan_exclusive_u32(canon, head, n, true, rtmp, s));
-    B_TRY(dalloc(&f->edge_vf, E));
+    B_TRY(dalloc_s(&f->edge_vf, E, s));
     k_edge_emit<<<nblk(n), BT, 0, s>>>(f->vert_corner, f->face_vid, twin, canon, head, n, f->edge_vf, f->face_edge);
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
     // records
-    B_TRY(dalloc(&f->face_rec, 4 * T));
-    B_TRY(dalloc(&f->face_box, 2 * T));
-    B_TRY(dalloc(&f->edge_rec, 5 * E));
-    B_TRY(dalloc(&f->edge_class, E));
-    B_TRY(dalloc(&f->vert_rec, 3 * V));
-    B_TRY(dalloc(&f->vert_plane, n));
-    B_TRY(dalloc(&f->vert_class, V));
+    B_TRY(dalloc_s(&f->face_rec, 4 * T, s));
+    B_TRY(dalloc_s(&f->face_box, 2 * T, s));
+    B_TRY(dalloc_s(&f->edge_rec, 5 * E, s));
+    B_TRY(dalloc_s(&f->edge_class, E, s));
+    B_TRY(dalloc_s(&f->vert_rec, 3 * V, s));
+    B_TRY(dalloc_s(&f->vert_plane, n, s));
+    B_TRY(dalloc_s(&f->vert_class, V, s));
     unsigned st = 0;
     B_TRY(cudaMemcpyAsync(&st, &f->ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     B_TRY(cudaStreamSynchronize(s));
     if (st) {  // do not evaluate geometry on broken connectivity
-        tmp.release();
+        tmp.release(s);
         free_handle(f);
         return status_to_code(st);
     }
@@ -607,7 +676,7 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     B_TRY(cudaMemcpyAsync(&c, f->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
     B_TRY(cudaMemcpyAsync(&n_canon, head + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     B_TRY(cudaStreamSynchronize(s));
-    tmp.release();
+    tmp.release(s);
     if (!c.status && (int64_t)n_canon != E) c.status |= ST_NONMANIFOLD;
     if (c.status) {
         int code = status_to_code(c.status);

@@ -88,11 +88,56 @@ size_t scan_tmp_bytes(int64_t n) {
     return bytes + 256;
 }
 
+// one block, 1024 threads, walks the whole array in chunks carrying the running prefix: one
+// launch instead of three for the small arrays of the sorts and of the tile lists
+__global__ void __launch_bounds__(1024) k_scan_single(const uint32_t *in, uint32_t *out, int64_t n,
+                                                      uint32_t *total_out) {
+    __shared__ uint32_t wt[32];
+    __shared__ uint32_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    constexpr int IT = 4;
+    for (int64_t base = 0; base < n; base += 1024 * IT) {
+        const int64_t i0 = base + (int64_t)threadIdx.x * IT;
+        uint32_t v[IT], sum = 0;
+#pragma unroll
+        for (int k = 0; k < IT; k++) {
+            v[k] = (i0 + k < n) ? in[i0 + k] : 0u;
+            sum += v[k];
+        }
+        const uint32_t inc = warp_incl_scan_u32(sum);
+        if (lane == 31) wt[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t t = wt[lane];
+            const uint32_t ti = warp_incl_scan_u32(t);
+            wt[lane] = ti - t;
+        }
+        __syncthreads();
+        uint32_t run = carry + wt[warp] + inc - sum;
+#pragma unroll
+        for (int k = 0; k < IT; k++) {
+            if (i0 + k < n) out[i0 + k] = run;
+            run += v[k];
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = run;
+        __syncthreads();
+    }
+    if (total_out && threadIdx.x == 0) *total_out = carry;
+}
+
 cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, bool write_total, void *tmp,
                                cudaStream_t s) {
     if (n <= 0) {
         if (write_total) return cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
         return cudaSuccess;
+    }
+    if (n <= 65536) {
+        k_scan_single<<<1, 1024, 0, s>>>(in, out, n, write_total ? out + n : nullptr);
+        SDF_LAUNCHED(1);
+        return cudaGetLastError();
     }
     int64_t nb = (n + SC_TILE - 1) / SC_TILE;
     if (nb == 1) {
@@ -264,3 +309,38 @@ static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace sdf
 extern "C" int64_t sdf_kernel_launches(void) { return sdf::g_launches.load(); }
+
+// ============================================================================= memory pool
+namespace sdf {
+static cudaMemPool_t g_pools[64] = {nullptr};
+
+static cudaMemPool_t pool_for_current_device(cudaError_t *err) {
+    int dev = 0;
+    *err = cudaGetDevice(&dev);
+    if (*err != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        *err = cudaMemPoolCreate(&pool, &props);
+        if (*err != cudaSuccess) return nullptr;
+        uint64_t threshold = ~0ull;  // keep freed blocks cached in the pool
+        *err = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+        if (*err != cudaSuccess) return nullptr;
+        g_pools[dev] = pool;
+    }
+    return g_pools[dev];
+}
+
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+    cudaError_t e;
+    cudaMemPool_t pool = pool_for_current_device(&e);
+    if (!pool) return e;
+    return cudaMallocFromPoolAsync(p, bytes > 0 ? bytes : 1, pool, s);
+}
+
+cudaError_t pool_free(void *p, cudaStream_t s) { return p ? cudaFreeAsync(p, s) : cudaSuccess; }
+}  // namespace sdf

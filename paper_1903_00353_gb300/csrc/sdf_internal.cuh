@@ -25,22 +25,28 @@ enum : int8_t { CLS_FLAT = 0, CLS_CONVEX = 1, CLS_CONCAVE = -1, CLS_SADDLE = 2 }
 constexpr int TILE_X = 32, TILE_Y = 8, TILE_Z = 8;
 constexpr int TILE_PTS = TILE_X * TILE_Y * TILE_Z;
 
-// ----------------------------------------------------------------------------- device buffers
+// ----------------------------------------------------------------------------- device memory
+// All library allocations come from one stream-ordered memory pool per device that keeps freed
+// memory cached (release threshold = unlimited), so a build or a call that needs scratch of a
+// size seen before does not reach the driver's allocator.
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);
+cudaError_t pool_free(void *p, cudaStream_t s);
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
-    cudaError_t reserve(size_t need) {
+    cudaError_t reserve(size_t need, cudaStream_t s) {
         if (need <= bytes) return cudaSuccess;
-        if (p) cudaFree(p);
+        if (p) pool_free(p, s);
         p = nullptr;
         bytes = 0;
         size_t want = need + need / 4 + 256;
-        cudaError_t e = cudaMalloc(&p, want);
+        cudaError_t e = pool_alloc(&p, want, s);
         if (e == cudaSuccess) bytes = want;
         return e;
     }
-    void release() {
-        if (p) cudaFree(p);
+    void release(cudaStream_t s) {
+        if (p) pool_free(p, s);
         p = nullptr;
         bytes = 0;
     }
@@ -115,6 +121,20 @@ cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, u
 
 // ----------------------------------------------------------------------------- geometry stage (build.cu)
 int build_records(sdf_features_s *f, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- division by a grid size
+// Unsigned division by an invariant divisor d >= 1 as a multiply-high and a shift (round-up
+// multiplier method of Granlund and Montgomery, 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(n, m) + n) >> l for every n < 2^31.
+struct FastDiv {
+    uint32_t d = 1, m = 1, l = 0;
+    FastDiv() = default;
+    explicit FastDiv(uint32_t dv) : d(dv) {
+        while ((uint64_t(1) << l) < dv) l++;
+        m = (uint32_t)(((uint64_t(1) << 32) * ((uint64_t(1) << l) - dv)) / dv + 1);
+    }
+    __device__ __forceinline__ uint32_t div(uint32_t n) const { return (__umulhi(n, m) + n) >> l; }
+};
 
 // ----------------------------------------------------------------------------- small device helpers
 __device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
