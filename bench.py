@@ -46,7 +46,13 @@ WORKLOADS = {
     "c5": dict(index=5, adjoint=True, winner=True,
                desc="displaced icosphere nu=100 (200,000 triangles), grid 512^3 on [0,1]^3, band 4h, "
                     "forward + vertex adjoint"),
+    "c5fit": dict(index=5, adjoint=True, winner=True, fit=True,
+                  desc="shape fitting: displaced icosphere nu=100 (200,000 triangles), grid 512^3, band 4h; "
+                       "one plain gradient-descent step on the welded vertices of "
+                       "sum_band (d - d_ellipsoid(0.35, 0.25, 0.2))^2 (position update, forward with winner "
+                       "checkpoint, loss, adjoint)"),
 }
+FIT_LR = 1e-4  # fixed learning rate of the shape-fitting workload
 
 
 def peaks():
@@ -188,6 +194,110 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def ellipsoid_target(N, dev):
+    """Exact SDF of the ellipsoid (0.35, 0.25, 0.2) at the cell centres (float32), in z slabs."""
+    import torch
+    import meshgen
+    c = (torch.arange(N, device=dev, dtype=torch.float64) + 0.5) / N
+    out = torch.empty((N, N, N), dtype=torch.float32, device=dev)
+    Y, X = torch.meshgrid(c, c, indexing="ij")
+    for k0 in range(0, N, 32):
+        k1 = min(N, k0 + 32)
+        Z = c[k0:k1].view(-1, 1, 1).expand(k1 - k0, N, N)
+        P = torch.stack([X.expand(k1 - k0, N, N), Y.expand(k1 - k0, N, N), Z], dim=-1)
+        out[k0:k1] = meshgen.ellipsoid_sdf_torch(P).to(torch.float32)
+    return out
+
+
+def run_fit(args, wl, sdf, soup_np, soup, grid, w, N, dev, world, rank):
+    """Shape-fitting workload: every step is one plain gradient-descent step on the welded vertices."""
+    import torch
+    import torch.distributed as tdist
+    target = ellipsoid_target(N, dev)
+    feats = sdf.sdf_build_features(soup)
+    X = feats.vertices().clone().requires_grad_(True)
+
+    def fit_step(ev=None):
+        if ev:
+            ev[0].record()
+        dist = sdf.SDFFunction.apply(X, feats, grid, w)
+        if ev:
+            ev[1].record()
+        band = torch.isfinite(dist)
+        d = torch.where(band, dist, target)
+        loss = ((d - target) ** 2).sum()
+        X.grad = None
+        loss.backward()
+        with torch.no_grad():
+            X.sub_(FIT_LR * X.grad)
+        if ev:
+            ev[2].record()
+        return loss.detach(), band.sum()
+
+    losses = []
+    for _ in range(args.warmup):
+        losses.append(fit_step()[0])
+    torch.cuda.synchronize()
+    launches0 = sdf.kernel_launches()
+    per, bands = [], []
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    with ClockSampler(uuid) as clk:
+        if world > 1:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            l, b = fit_step(evs)
+            losses.append(l)
+            bands.append(b)
+            per.append(evs)
+        torch.cuda.synchronize()
+    launches = sdf.kernel_launches() - launches0
+    times = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])] for e in per])
+    total_ms = float(times.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    band_total = int(sum(int(b) for b in bands))
+    value = band_total * world / (total_ms / 1e3)
+    loss_curve = [float(x) for x in losses]
+    # end to end: vertex positions from pinned host memory each step, loss read back each step
+    Xh = X.detach().cpu().pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, min(args.steps, 10))
+    e2e_band = 0
+    for _ in range(e2e_steps):
+        with torch.no_grad():
+            X.copy_(Xh, non_blocking=True)
+        l, b = fit_step()
+        e2e_band += int(b)
+        float(l)
+    e2e_s = time.perf_counter() - t0
+    if rank != 0:
+        return
+    fwd_ms, rest_ms = (float(x) for x in times.mean(axis=0))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "triangles": int(soup_np.shape[0]), "grid": [N, N, N], "band_w": w,
+                   "lr": FIT_LR, "l2": "inputs of the dense loss (> L2) streamed every step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "fwd_ms": fwd_ms, "loss_and_adjoint_ms": rest_ms, "loss_curve": loss_curve,
+        "e2e": {"value": e2e_band * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(Xh.numel() * 4),
+                "d2h_bytes_per_step": 4},
+        "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
+        "cpu_baseline": None, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -235,6 +345,10 @@ def main():
     win = torch.empty(grid.shape, dtype=torch.int32, device=dev) if wl["winner"] else None
     gv = None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    if wl.get("fit"):
+        run_fit(args, wl, sdf, soup_np, soup, grid, w, N, dev, world, rank)
+        return
 
     # upstream gradient of L = sum_band (d - 0.01)^2 from one forward (same mesh every step)
     feats = sdf.sdf_build_features(soup)

@@ -111,8 +111,9 @@ int sdf_build_features(const float *soup, int64_t n_tri, uint32_t flags, void *s
  *
  *   vertices  device float[V][3] in the handle's vertex order (see
  *             sdf_features_vertices / sdf_features_vertex_map).
- * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_DEGENERATE (checked at the next
- * synchronising call), SDF_ERR_CUDA.
+ * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_CUDA; a zero-area triangle at the new
+ * positions is reported as SDF_ERR_DEGENERATE by the next synchronising
+ * sdf_narrow_band or sdf_features_status call.
  */
 int sdf_features_update_positions(sdf_features f, const float *vertices, void *stream);
 
@@ -139,7 +140,8 @@ int sdf_features_update_positions(sdf_features f, const float *vertices, void *s
  *               id, -1 outside the band); the array or any entry may be NULL.
  *   flags       0 or SDF_FLAG_NO_SYNC.
  *
- * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_TOO_LARGE, SDF_ERR_OOM, SDF_ERR_CUDA.
+ * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_TOO_LARGE, SDF_ERR_OOM, SDF_ERR_CUDA,
+ * SDF_ERR_DEGENERATE (positions set by sdf_features_update_positions).
  */
 int sdf_narrow_band(const sdf_features *feats, const sdf_grid *grids, const float *band_w, int32_t n,
                     float *const *out_dist, int32_t *const *out_winner, uint32_t flags, void *stream);

@@ -402,3 +402,73 @@ def batch_meshes(n: int = 64, seed: int = 353_003, t_min: float = 1e3, t_max: fl
         N = int(rng.choice(np.arange(64, 385, 32)))
         out.append((mesh, N))
     return out
+
+
+# ----------------------------------------------------------------------------- analytic target field
+
+def ellipsoid_sdf(points, axes=(0.35, 0.25, 0.2), center=CENTER, iters: int = 200):
+    """Exact signed distance to an axis-aligned ellipsoid (negative inside), float64 numpy.
+
+    For q = |p - c| (first octant by symmetry) the closest surface point is
+    x_i = e_i^2 q_i / (t + e_i^2) with t the largest root of
+    F(t) = sum_i (e_i q_i / (t + e_i^2))^2 - 1, monotone on (-e_m^2, inf) with e_m the
+    smallest semi-axis; the root is bracketed by (-e_m^2, e_max |q|] and found by bisection
+    (the monotone 1-D root find of Eberly's formulation).  When q_m = 0 and the other terms of
+    F at t = -e_m^2 sum to less than 1, t = -e_m^2 and x_m follows from the surface equation."""
+    p = np.asarray(points, dtype=np.float64).reshape(-1, 3) - np.asarray(center, dtype=np.float64)
+    e = np.asarray(axes, dtype=np.float64)
+    q = np.abs(p)
+    e2 = e * e
+    m = int(np.argmin(e))
+    lo = np.full(q.shape[0], -e2[m])
+    hi = e.max() * np.linalg.norm(q, axis=1) + 1e-300
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for _ in range(iters):
+            mid = 0.5 * (lo + hi)
+            den = mid[:, None] + e2
+            F = np.where(q > 0, (e * q / np.where(den > 0, den, 1.0)) ** 2, 0.0)
+            F = np.where((q > 0) & (den <= 0), np.inf, F)
+            pos = F.sum(axis=1) - 1.0 > 0
+            lo = np.where(pos, mid, lo)
+            hi = np.where(pos, hi, mid)
+        t = 0.5 * (lo + hi)
+        x = np.where(q > 0, e2 * q / (t[:, None] + e2), 0.0)
+        # degenerate case: q_m = 0 and the root sits at t = -e_m^2
+        others = [k for k in range(3) if k != m]
+        xo = np.stack([e2[k] * q[:, k] / (e2[k] - e2[m]) for k in others], axis=1)
+        G = sum((xo[:, j] / e[k]) ** 2 for j, k in enumerate(others))
+        deg = (q[:, m] == 0) & (G < 1.0)
+        if np.any(deg):
+            xd = np.zeros((int(deg.sum()), 3))
+            for j, k in enumerate(others):
+                xd[:, k] = xo[deg, j]
+            xd[:, m] = e[m] * np.sqrt(1.0 - G[deg])
+            x[deg] = xd
+    d = np.linalg.norm(q - x, axis=1)
+    inside = ((q / e) ** 2).sum(axis=1) < 1.0
+    return np.where(inside, -d, d)
+
+
+def ellipsoid_sdf_torch(points, axes=(0.35, 0.25, 0.2), center=CENTER, iters: int = 100):
+    """The same as ellipsoid_sdf for a torch tensor [..., 3] (float64 on its device) for points with
+    no zero offset along the smallest semi-axis (always true for cell centres of an even grid
+    around the centre)."""
+    import torch
+    p = points.to(torch.float64) - torch.tensor(center, dtype=torch.float64, device=points.device)
+    e = torch.tensor(axes, dtype=torch.float64, device=points.device)
+    q = p.abs()
+    e2 = e * e
+    lo = torch.full(q.shape[:-1], float(-e2.min()), dtype=torch.float64, device=points.device)
+    hi = float(e.max()) * q.norm(dim=-1) + 1e-300
+    eq = e * q
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        F = ((eq / (mid[..., None] + e2)) ** 2).sum(dim=-1) - 1.0
+        pos = F > 0
+        lo = torch.where(pos, mid, lo)
+        hi = torch.where(pos, hi, mid)
+    t = 0.5 * (lo + hi)
+    x = e2 * q / (t[..., None] + e2)
+    d = (q - x).norm(dim=-1)
+    inside = ((q / e) ** 2).sum(dim=-1) < 1.0
+    return torch.where(inside, -d, d)

@@ -185,7 +185,7 @@ __global__ void k_bin(Feat F, GridP g, uint32_t *cnt, const uint32_t *start, int
                 } else {
                     int64_t pos = (int64_t)start[bin] + atomicAdd(cnt + bin, 1u);
                     if (pos < pair_cap) pairs[pos] = fid;
-                    else atomicOr(&ctr->status, ST_PAIR_OVERFLOW);
+                    else atomicOr(&ctr->nb_status, ST_PAIR_OVERFLOW);
                 }
             }
 }
@@ -706,7 +706,7 @@ __global__ void __launch_bounds__(NT, 3) k_tile(Feat F, GridP g, Outputs o, int6
         atomicAdd(&o.ctr->n_rows, (unsigned long long)s_rows);
         atomicAdd(&o.ctr->n_rows_hit, (unsigned long long)s_hits);
         atomicAdd(&o.ctr->n_pairs, (unsigned long long)s_pairs);
-        if (s_ovf) atomicOr(&o.ctr->status, ST_PATCH_OVERFLOW);
+        if (s_ovf) atomicOr(&o.ctr->nb_status, ST_PATCH_OVERFLOW);
     }
 }
 
@@ -980,7 +980,7 @@ static int narrow_band_one(sdf_features_s *f, const sdf_grid &gr, float w, float
         SDF_TRY(cudaEventRecord(f->ev[0], s));
     }
     SDF_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n_bins, s));
-    SDF_TRY(cudaMemsetAsync(&f->ctr->status, 0, sizeof(unsigned), s));
+    SDF_TRY(cudaMemsetAsync(&f->ctr->nb_status, 0, sizeof(unsigned), s));
     SDF_TRY(cudaMemsetAsync(&f->ctr->n_candidates, 0, 6 * sizeof(unsigned long long), s));
     k_bin<false><<<nblk(n_feat, 256), 256, 0, s>>>(F, g, cnt, nullptr, nullptr, 0, f->ctr);
     SDF_LAUNCHED(1);
@@ -1041,11 +1041,12 @@ static int narrow_band_one(sdf_features_s *f, const sdf_grid &gr, float w, float
     SDF_TRY(cudaMemcpyAsync(&total_pairs, start + n_bins, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     SDF_TRY(cudaStreamSynchronize(s));
     *retry = false;
-    if (c.status & ST_PAIR_OVERFLOW) {
+    if (c.status & ST_DEGENERATE) return SDF_ERR_DEGENERATE;  // from sdf_features_update_positions
+    if (c.nb_status & ST_PAIR_OVERFLOW) {
         f->pair_cap = (int64_t)total_pairs + total_pairs / 4 + 4096;
         *retry = true;
     }
-    if (c.status & ST_PATCH_OVERFLOW) {
+    if (c.nb_status & ST_PATCH_OVERFLOW) {
         f->patch_cap = (int64_t)c.n_patch + c.n_patch / 2 + 4096;
         *retry = true;
     }
@@ -1065,7 +1066,8 @@ int narrow_band_stats(sdf_features_s *f, int64_t *stats, cudaStream_t s) {
         stats[4] = (int64_t)c.n_rows;
         stats[5] = (int64_t)c.n_rows_hit;
     }
-    if (c.status & (ST_PAIR_OVERFLOW | ST_PATCH_OVERFLOW)) return SDF_ERR_OOM;
+    if (c.status & ST_DEGENERATE) return SDF_ERR_DEGENERATE;
+    if (c.nb_status & (ST_PAIR_OVERFLOW | ST_PATCH_OVERFLOW)) return SDF_ERR_OOM;
     return SDF_OK;
 }
 
@@ -1235,7 +1237,7 @@ extern "C" int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, floa
     SDF_TRY(cudaGetLastError());
     // read the status word: a pair or re-decision list beyond the static limits is an error
     unsigned status = 0;
-    SDF_TRY(cudaMemcpyAsync(&status, &ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    SDF_TRY(cudaMemcpyAsync(&status, &ctr->nb_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     SDF_TRY(cudaStreamSynchronize(s));
     if (status & (ST_PAIR_OVERFLOW | ST_PATCH_OVERFLOW)) return SDF_ERR_TOO_LARGE;
     return SDF_OK;

@@ -695,6 +695,7 @@ extern "C" int sdf_features_update_positions(sdf_features f, const float *vertic
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     SDF_TRY(cudaMemcpyAsync(f->vpos, vertices, sizeof(float) * 3 * f->V, cudaMemcpyDeviceToDevice, s));
     SDF_TRY(cudaMemsetAsync(f->ctr->cls, 0, sizeof(f->ctr->cls), s));
+    SDF_TRY(cudaMemsetAsync(&f->ctr->status, 0, sizeof(unsigned), s));  // re-evaluated below
     return build_records(f, s);
 }
 

@@ -55,8 +55,8 @@ struct DevBuf {
 
 // ----------------------------------------------------------------------------- device status / counters
 struct DevCounters {
-    unsigned status;
-    unsigned pad;
+    unsigned status;     // build / position-update errors (ST_NONFINITE, ST_DEGENERATE, ST_NONMANIFOLD)
+    unsigned nb_status;  // narrow-band scratch overflows (ST_PAIR_OVERFLOW, ST_PATCH_OVERFLOW)
     unsigned long long n_candidates;   // (point, region) pairs merged
     unsigned long long n_band;         // band points written
     unsigned long long n_patch;        // points re-decided in FP64

@@ -1,0 +1,72 @@
+"""Differentiable shape fitting through SDFFunction (autograd over the C ABI).  GPU only.
+
+A displaced icosphere's welded vertices follow plain gradient descent on
+L = sum over the band of (d - d_ellipsoid)^2, with d the narrow band of the current mesh and
+d_ellipsoid the exact SDF of the ellipsoid with semi-axes (0.35, 0.25, 0.2).  Checked: the loss
+decreases at every step, the first gradient matches the FP64 oracle's adjoint at the same band
+points, and checkpointed winners give the same gradient as recomputed ones.
+"""
+import numpy as np
+import pytest
+import torch
+
+import meshgen
+import oracle
+import paper_1903_00353_gb300 as sdf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _target(grid):
+    n = grid.nx
+    c = (torch.arange(n, device="cuda", dtype=torch.float64) + 0.5) * grid.h
+    Z, Y, X = torch.meshgrid(c, c, c, indexing="ij")
+    return meshgen.ellipsoid_sdf_torch(torch.stack([X, Y, Z], dim=-1)).to(torch.float32)
+
+
+def _loss(dist, target):
+    band = torch.isfinite(dist)
+    d = torch.where(band, dist, target)
+    return ((d - target) ** 2).sum(), band
+
+
+def test_fit_loss_decreases_and_gradient_matches_oracle():
+    mesh = meshgen.icosphere(12, radius=0.3, displacement=0.02, seed=5)
+    soup = mesh.soup(seed=7)
+    feats = sdf.sdf_build_features(torch.from_numpy(soup).cuda())
+    grid, w = sdf.Grid.cube(128), 4 / 128
+    target = _target(grid)
+    X = feats.vertices().clone().requires_grad_(True)
+    lr = 2e-4
+    losses = []
+    for step in range(8):
+        dist = sdf.SDFFunction.apply(X, feats, grid, w)
+        loss, band = _loss(dist, target)
+        X.grad = None
+        loss.backward()
+        if step == 0:
+            # FP64 oracle adjoint of the same loss at the same band points
+            idx = torch.nonzero(band.view(-1)).view(-1).cpu().numpy()
+            g = (2.0 * (dist.detach() - target)).view(-1)[torch.from_numpy(idx).cuda()].cpu().double().numpy()
+            pts = oracle.grid_points((128, 128, 128), (0, 0, 0), grid.h, idx)
+            om = oracle.OracleMesh.from_soup(soup)
+            go = om.adjoint_points(pts, g, w + 1e-9)
+            a = X.grad.cpu().numpy()[feats.vertex_map().cpu().numpy()]
+            b = go[om.soup_vid()]
+            rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+            assert rel < 1e-3, rel
+            # winners recomputed by the backward instead of checkpointed by the forward
+            g_full = torch.where(band, 2.0 * (dist.detach() - target), torch.zeros_like(target)).contiguous()
+            gv = sdf.sdf_narrow_band_backward(feats, grid, w, g_full, winner=None)
+            assert float((gv - X.grad).norm()) <= 1e-5 * float(X.grad.norm())
+        losses.append(float(loss.detach()))
+        with torch.no_grad():
+            X -= lr * X.grad
+    assert all(b <= a for a, b in zip(losses, losses[1:])), losses
+    assert losses[-1] < 0.95 * losses[0], losses
