@@ -40,6 +40,11 @@ WORKLOADS = {
     "c2": dict(index=2, adjoint=True, winner=True,
                desc="displaced jittered torus R=0.3 r=0.1 (50,000 triangles), grid 512^3 on [0,1]^3, band 4h, "
                     "forward + vertex adjoint of sum_band (d - 0.01)^2"),
+    "c3": dict(index=3, adjoint=False, winner=False, batch=True,
+               desc="batch of 64 seeded uneven meshes (log-uniform 1e3..2e5 triangles; displaced icospheres, "
+                    "displaced tori, clusters of 2-4 rotated boxes), per-mesh grids N in {64, 96, ..., 384} "
+                    "on [0,1]^3, band 3h; forward of all 64 problems as one launch sequence replayed from a "
+                    "CUDA graph, autotuned tile shape"),
     "c4": dict(index=4, adjoint=False, winner=False,
                desc="(3,7) torus-knot tube r=0.04 + 0.005 noise (2,097,152 triangles), grid 1024^3 on [0,1]^3, "
                     "band 3h, forward"),
@@ -160,15 +165,30 @@ def cpu_baseline(soup, N, w, target_s: float = 12.0):
                       f"plus the oracle's mesh build ({t_build:.2f} s) prorated by {frac:.4f}"}
 
 
+def batch_problems():
+    """The 64 (soup, N, w) problems of the batch workload (band 3h)."""
+    import meshgen
+    return [(m.soup(seed=353_300 + i), N, 3.0 / N) for i, (m, N) in enumerate(meshgen.batch_meshes())]
+
+
+def median_problem(problems):
+    """The batch problem whose grid size times triangle count is the median (a sample for the oracle)."""
+    order = sorted(range(len(problems)), key=lambda i: problems[i][0].shape[0] * problems[i][1] ** 3)
+    return problems[order[len(order) // 2]]
+
+
 def run_reference(args, wl):
     world, rank, _ = dist_setup()
     if rank != 0:
         return
     import meshgen
     import oracle
-    soup = meshgen.config_soup(wl["index"])
-    N, cells = meshgen.CONFIG_GRID[wl["index"]]
-    w = cells / N
+    if wl.get("batch"):
+        soup, N, w = median_problem(batch_problems())
+    else:
+        soup = meshgen.config_soup(wl["index"])
+        N, cells = meshgen.CONFIG_GRID[wl["index"]]
+        w = cells / N
     om = oracle.OracleMesh.from_soup(soup)
     z = soup[..., 2].ravel()
     kmid = int(np.clip(np.median(z) * N, 0, N - 1))
@@ -298,6 +318,144 @@ def run_fit(args, wl, sdf, soup_np, soup, grid, w, N, dev, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, wl, sdf, local, world, rank):
+    """Batch workload: all 64 problems in one launch sequence (one persistent tile kernel) captured
+    in a CUDA graph; one step = one replay.  Also times the plain path (64 single-problem calls)."""
+    import torch
+    import torch.distributed as tdist
+    dev = torch.device("cuda", local)
+    problems = batch_problems()
+    soups = [torch.from_numpy(s).to(dev) for s, _, _ in problems]
+    grids = [sdf.Grid.cube(N) for _, N, _ in problems]
+    ws = [w for _, _, w in problems]
+    t0 = time.perf_counter()
+    feats = [sdf.sdf_build_features(s) for s in soups]
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    outs = [torch.empty(g.shape, dtype=torch.float32, device=dev) for g in grids]
+    t0 = time.perf_counter()
+    batch = sdf.sdf_batch_create(feats, grids, ws, out=outs, autotune=True, timing=True)
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    band_points = sum(int(torch.isfinite(o).sum()) for o in outs)
+    stats = batch.status()
+    info = batch.info()
+    rec_bytes = sum(record_bytes(f) for f in feats)
+    grid_points = sum(g.nx * g.ny * g.nz for g in grids)
+
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    launches0 = sdf.kernel_launches()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            batch.run()
+    torch.cuda.synchronize()
+    per_replay = sdf.kernel_launches() - launches0
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    per, tile_ms = [], []
+    with ClockSampler(uuid) as clk:
+        if world > 1:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            e1.synchronize()
+            per.append(e0.elapsed_time(e1))
+            tile_ms.append(batch.timing()["tile"])
+        torch.cuda.synchronize()
+        if world > 1:
+            tdist.barrier()
+    launches = per_replay * args.steps
+    total_ms = float(sum(per))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = band_points * args.steps * world / (total_ms / 1e3)
+
+    # the plain path on the same problems: 64 single-problem calls (each synchronises once)
+    for f, g, w, o in zip(feats, grids, ws, outs):
+        sdf.sdf_narrow_band(f, g, w, out=o)
+    torch.cuda.synchronize()
+    plain = []
+    for _ in range(max(3, min(args.steps, 5))):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for f, g, w, o in zip(feats, grids, ws, outs):
+            sdf.sdf_narrow_band(f, g, w, out=o)
+        e1.record(stream)
+        e1.synchronize()
+        plain.append(e0.elapsed_time(e1))
+    plain_ms = float(np.mean(plain))
+
+    # end to end: soups from pinned host memory, 64 builds, one batched list call, all fields read back
+    soups_host = [torch.from_numpy(s).pin_memory() for s, _, _ in problems]
+    outs_host = [torch.empty(g.shape, dtype=torch.float32).pin_memory() for g in grids]
+    e2e_steps = 3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        fl = [sdf.sdf_build_features(sh.to(dev, non_blocking=True)) for sh in soups_host]
+        sdf.sdf_narrow_band(fl, grids, ws, out=outs)
+        for oh, o in zip(outs_host, outs):
+            oh.copy_(o, non_blocking=True)
+        torch.cuda.synchronize()
+        for f in fl:
+            f.destroy()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": band_points * e2e_steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(s.nbytes for s, _, _ in problems)),
+           "d2h_bytes_per_step": int(4 * grid_points)}
+
+    hbm, peak_kind = peaks()
+    tile_avg_ms = float(np.mean(tile_ms))
+    alg_bytes = 4 * grid_points + rec_bytes
+    achieved = alg_bytes / (tile_avg_ms / 1e3) / 1e9
+    roofline = {"kernel": "k_tile (all 64 problems in one persistent launch)", "bound": "hbm",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind,
+                "traffic": None, "algorithmic_bytes": int(alg_bytes), "avg_ms": tile_avg_ms}
+    del graph
+    batch.destroy()
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        s_np, N, w = median_problem(problems)
+        cpu = cpu_baseline(s_np, N, w)
+        cpu["sample"] = f"median problem of the batch ({s_np.shape[0]} triangles, {N}^3): " + cpu["sample"]
+    tris = [s.shape[0] for s, _, _ in problems]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "meshes": len(problems), "triangles_total": int(sum(tris)),
+                   "triangles_min_max": [int(min(tris)), int(max(tris))], "grid_points_total": int(grid_points),
+                   "band_points": band_points, "tile_shape": list(info["tile"]),
+                   "l2": "outputs (%.1f GB) larger than L2" % (4 * grid_points / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "batch_ms": total_ms / args.steps, "plain_ms": plain_ms, "plain_over_batch": plain_ms / (total_ms / args.steps),
+        "autotune_ms_per_run": info["tuned_ms"], "build_all_s": build_s, "batch_create_s": create_s,
+        "candidates_per_band_point": stats["candidates"] / max(1, stats["band_points"]),
+        "fp64_points": stats["fp64_points"], "tile_region_pairs": stats["pairs"],
+        "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(), "e2e": e2e,
+        "gpu_launches": int(launches), "gpu_launches_per_step": per_replay,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -331,6 +489,11 @@ def main():
     if world > 1:
         tdist.barrier()
     sdf.load_library()
+    if wl.get("batch"):
+        run_batch(args, wl, sdf, local, world, rank)
+        if world > 1:
+            tdist.destroy_process_group()
+        return
 
     soup_np = meshgen.config_soup(wl["index"])
     N, cells = meshgen.CONFIG_GRID[wl["index"]]

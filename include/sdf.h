@@ -79,6 +79,9 @@ typedef struct sdf_features_s *sdf_features;
                                         sdf_narrow_band / sdf_narrow_band_backward (adds one
                                         host synchronisation per call); read them with
                                         sdf_features_timing                                  */
+#define SDF_FLAG_AUTOTUNE 0x8u       /* sdf_batch_create: time every tile shape on the batch
+                                        and keep the fastest (also remembered for later
+                                        sdf_narrow_band calls with n > 1 of the same sizes)  */
 
 /*
  * sdf_build_features -- mesh-connectivity stage (Section 7, Section 8).
@@ -185,7 +188,7 @@ int sdf_features_face_map(sdf_features f, int32_t *face_to_soup, void *stream);
 int sdf_features_vertices(sdf_features f, float *out, void *stream);
 
 /*
- * Status word and counters of the last sdf_narrow_band on this handle
+ * Status word and counters of the last single-problem (n = 1) sdf_narrow_band on this handle
  * (synchronises `stream`).  stats (host, nullable) [6] = candidate (point,
  * region) pairs merged by atomicMin, band points decided in FP32, points
  * re-decided in FP64, (tile, region) pairs scheduled, grid rows intersected
@@ -232,6 +235,51 @@ int64_t sdf_kernel_launches(void);
  */
 int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, float band_w, float *out_dist,
                            int32_t *out_winner, void *stream);
+
+/*
+ * Batches for repeated evaluation -- the same computation as sdf_narrow_band with n problems,
+ * split into a set-up call and a replayable launch (a project addition; the paper evaluates one
+ * mesh at a time).
+ *
+ * sdf_batch_create describes the n (mesh, grid, output) problems, sizes and allocates all scratch
+ * (the problem table, bins, the (tile, region) pair list, tile work lists and the FP64
+ * re-decision list), runs the batch once (so the outputs hold the result on return) and, with
+ * SDF_FLAG_AUTOTUNE, times the tile shapes 32x8x8, 32x4x4 and 32x16x8 and keeps the fastest.
+ * It synchronises `stream`.  The handles, grids, widths and output pointers are fixed for the
+ * batch's lifetime; the handles' positions may change (sdf_features_update_positions) as long
+ * as the band stays within the scratch sized at creation.
+ *
+ * sdf_batch_run enqueues the whole batch on `stream`: a fixed sequence of kernels and memsets,
+ * with no allocation, no host synchronisation and no host-to-device copy, so it may be captured
+ * in a CUDA graph and replayed.  All problems share one persistent tile-kernel launch.
+ *
+ * sdf_batch_status (synchronises `stream`) returns the counters of the last run (layout of
+ * sdf_features_status) and SDF_ERR_OOM if the band of that run outgrew the scratch sized at
+ * creation (the outputs of that run are then unspecified; create a new batch).
+ *
+ * sdf_batch_info returns the tile shape in use (host int32[3], points per tile along x, y, z)
+ * and the per-run time measured while autotuning (ms; 0 without SDF_FLAG_AUTOTUNE).
+ *
+ * sdf_batch_timing (batches created with SDF_FLAG_TIMING, which then record four CUDA events on
+ * every run, as event nodes when captured in a graph) waits for the last run and returns its
+ * stage times in ms (host float[3]): binning, tile kernel, FP64 re-decision.  Without the flag
+ * it returns SDF_ERR_INVALID_ARG.
+ *
+ * Arguments of sdf_batch_create are those of sdf_narrow_band; flags 0, SDF_FLAG_AUTOTUNE,
+ * SDF_FLAG_TIMING or both.
+ * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_TOO_LARGE, SDF_ERR_OOM, SDF_ERR_CUDA, SDF_ERR_DEGENERATE.
+ * sdf_batch_destroy synchronises the device and releases the batch (NULL is a no-op); the
+ * handles outlive the batch and are not released by it.
+ */
+typedef struct sdf_batch_s *sdf_batch;
+int sdf_batch_create(const sdf_features *feats, const sdf_grid *grids, const float *band_w, int32_t n,
+                     float *const *out_dist, int32_t *const *out_winner, uint32_t flags, void *stream,
+                     sdf_batch *out);
+int sdf_batch_run(sdf_batch b, void *stream);
+int sdf_batch_status(sdf_batch b, int64_t *stats, void *stream);
+int sdf_batch_info(sdf_batch b, int32_t *tile_shape, double *tuned_ms);
+int sdf_batch_timing(sdf_batch b, float *ms);
+void sdf_batch_destroy(sdf_batch b);
 
 /* Release the handle and its device memory (NULL is a no-op). */
 void sdf_features_destroy(sdf_features f);

@@ -381,16 +381,57 @@ def config_soup(index: int) -> np.ndarray:
 CONFIG_GRID = {1: (64, 3), 2: (512, 4), 4: (1024, 3), 5: (512, 4)}   # N, band half-width in cells
 
 
+def random_rotation(rng) -> np.ndarray:
+    """Uniformly distributed rotation matrix (QR of a Gaussian matrix, signs fixed, det +1)."""
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    q = q * np.sign(np.diag(r))[None, :]
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def box_cluster(n_boxes: int, target_tris: float, seed: int, half_range=(0.06, 0.16)) -> Mesh:
+    """2-4 randomly rotated boxes with pairwise disjoint bounding spheres inside [0.05, 0.95]^3,
+    one closed mesh with several components; each box face is split into s x s quads so that the
+    whole has about target_tris triangles.  Mostly flat edges and vertices, with sharp convex
+    edges and corners: the opposite of a smooth surface for the feature classification."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    s = max(1, int(round(math.sqrt(target_tris / (12.0 * n_boxes)))))
+    placed: list = []  # (centre, radius)
+    verts, tris = [], []
+    off = 0
+    for _ in range(n_boxes):
+        for _attempt in range(200):
+            half = rng.uniform(*half_range, size=3)
+            rad = float(np.linalg.norm(half))
+            c = rng.uniform(0.05 + rad, 0.95 - rad, size=3) if rad < 0.45 else CENTER.copy()
+            if all(np.linalg.norm(c - c2) > rad + r2 + 0.02 for c2, r2 in placed):
+                break
+            half_range = (half_range[0] * 0.9, half_range[1] * 0.9)
+        else:
+            raise RuntimeError("could not place disjoint boxes")
+        placed.append((c, rad))
+        b = box(center=(0.0, 0.0, 0.0), half=tuple(half), subdiv=s)
+        R = random_rotation(rng)
+        verts.append(b.vertices @ R.T + c)
+        tris.append(b.triangles.astype(np.int64) + off)
+        off += b.vertices.shape[0]
+    return Mesh(np.concatenate(verts), np.concatenate(tris).astype(np.int32))
+
+
 def batch_meshes(n: int = 64, seed: int = 353_003, t_min: float = 1e3, t_max: float = 2e5):
-    """Batch of uneven meshes: displaced icospheres and displaced tori, sizes log-uniform in triangles,
-    each paired with a grid size N in {64, 96, ..., 384}.  Returns a list of (Mesh, N)."""
+    """Batch of uneven meshes: displaced icospheres, displaced tori and clusters of 2-4 rotated
+    boxes (type uniform), sizes log-uniform in triangles, each paired with a grid size N in
+    {64, 96, ..., 384}.  Returns a list of (Mesh, N)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for m in range(n):
         target = math.exp(rng.uniform(math.log(t_min), math.log(t_max)))
-        kind = int(rng.integers(0, 2))
+        kind = int(rng.integers(0, 3))
         sub = 353_000 + 100 * 3 + m
-        if kind == 0:
+        if kind == 2:
+            mesh = box_cluster(int(rng.integers(2, 5)), target, seed=sub)
+        elif kind == 0:
             f = max(2, int(round(math.sqrt(target / 20.0))))
             mesh = icosphere(f, radius=float(rng.uniform(0.2, 0.35)),
                              displacement=float(rng.uniform(0.0, 0.03)), seed=sub)

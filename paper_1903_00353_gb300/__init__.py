@@ -19,12 +19,16 @@ import torch
 from . import _buildlib
 
 __all__ = ["Grid", "Features", "sdf_build_features", "sdf_narrow_band", "sdf_narrow_band_backward",
-           "SDFFunction", "load_library", "kernel_launches", "SDFError", "FLAG_DISABLE_SADDLE", "FLAG_NO_SYNC",
-           "FLAG_TIMING"]
+           "SDFFunction", "Batch", "sdf_batch_create", "load_library", "kernel_launches", "SDFError",
+           "FLAG_DISABLE_SADDLE", "FLAG_NO_SYNC", "FLAG_TIMING", "FLAG_AUTOTUNE"]
 
 FLAG_DISABLE_SADDLE = 0x1
 FLAG_NO_SYNC = 0x2
 FLAG_TIMING = 0x4
+FLAG_AUTOTUNE = 0x8
+
+
+_STATUS_KEYS = ("candidates", "band_points", "fp64_points", "pairs", "rows", "rows_hit")
 
 
 class SDFError(RuntimeError):
@@ -73,9 +77,18 @@ def load_library(path: str | None = None):
     L.sdf_kernel_launches.restype = I64
     L.sdf_status_string.argtypes = [ctypes.c_int]
     L.sdf_status_string.restype = ctypes.c_char_p
+    L.sdf_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(_CGrid), ctypes.POINTER(ctypes.c_float), I32,
+                                   ctypes.POINTER(P), ctypes.POINTER(P), U32, P, ctypes.POINTER(P)]
+    L.sdf_batch_run.argtypes = [P, P]
+    L.sdf_batch_status.argtypes = [P, ctypes.POINTER(I64), P]
+    L.sdf_batch_info.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_double)]
+    L.sdf_batch_timing.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+    L.sdf_batch_destroy.argtypes = [P]
+    L.sdf_batch_destroy.restype = None
     for name in ("sdf_build_features", "sdf_features_update_positions", "sdf_narrow_band",
                  "sdf_narrow_band_backward", "sdf_features_info", "sdf_features_vertex_map",
-                 "sdf_features_vertices", "sdf_features_status"):
+                 "sdf_features_vertices", "sdf_features_status", "sdf_batch_create", "sdf_batch_run",
+                 "sdf_batch_status", "sdf_batch_info", "sdf_batch_timing"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -173,8 +186,7 @@ class Features:
         st = (ctypes.c_int64 * 6)()
         code = load_library().sdf_features_status(self.handle, st, _stream())
         _check(code, "sdf_features_status")
-        return {"candidates": int(st[0]), "band_points": int(st[1]), "fp64_points": int(st[2]),
-                "pairs": int(st[3]), "rows": int(st[4]), "rows_hit": int(st[5])}
+        return dict(zip(_STATUS_KEYS, [int(x) for x in st]))
 
     def timing(self, reset: bool = False):
         """Accumulated stage times (ms) of calls made with FLAG_TIMING: bin, tile, fp64, adjoint."""
@@ -254,6 +266,79 @@ def sdf_narrow_band(features: Features | Sequence[Features], grid: Grid | Sequen
                                           _stream(stream)), "sdf_narrow_band")
     res = [(o, wn) if wn is not None else o for o, wn in zip(outs, wins)]
     return res if batch else res[0]
+
+
+class Batch:
+    """A fixed batch of (mesh, grid, output) problems whose run() is a replayable launch sequence
+    (no allocation, no synchronisation), suitable for CUDA-graph capture."""
+
+    def __init__(self, handle: int, feats, outs, wins):
+        self._h = ctypes.c_void_p(handle)
+        self.features, self.outs, self.winners = list(feats), outs, wins
+
+    def run(self, stream=None):
+        _check(load_library().sdf_batch_run(self._h, _stream(stream)), "sdf_batch_run")
+
+    def status(self, stream=None):
+        st = (ctypes.c_int64 * 6)()
+        _check(load_library().sdf_batch_status(self._h, st, _stream(stream)), "sdf_batch_status")
+        return dict(zip(_STATUS_KEYS, [int(x) for x in st]))
+
+    def info(self):
+        shape = (ctypes.c_int32 * 3)()
+        ms = ctypes.c_double()
+        _check(load_library().sdf_batch_info(self._h, shape, ctypes.byref(ms)), "sdf_batch_info")
+        return {"tile": tuple(int(x) for x in shape), "tuned_ms": float(ms.value)}
+
+    def timing(self):
+        """Stage times (ms) of the last run of a batch created with timing=True: bin, tile, fp64."""
+        ms = (ctypes.c_float * 3)()
+        _check(load_library().sdf_batch_timing(self._h, ms), "sdf_batch_timing")
+        return {"bin": float(ms[0]), "tile": float(ms[1]), "fp64": float(ms[2])}
+
+    def destroy(self):
+        if self._h is not None and self._h.value:
+            load_library().sdf_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def sdf_batch_create(features: Sequence[Features], grids: Sequence[Grid], w: Sequence[float],
+                     out: Sequence[torch.Tensor] | None = None, winner: bool | Sequence = False,
+                     autotune: bool = False, timing: bool = False, stream=None) -> Batch:
+    """Create a batch; its outputs hold the result on return.  Keep the Features alive meanwhile."""
+    feats, grids, ws = list(features), list(grids), list(w)
+    n = len(feats)
+    if not (len(grids) == len(ws) == n) or n < 1:
+        raise ValueError("features, grids and w must be non-empty and of the same length")
+    if out is None:
+        outs = [torch.empty(g.shape, dtype=torch.float32, device="cuda") for g in grids]
+    else:
+        outs = list(out)
+        for o, g in zip(outs, grids):
+            _dev_f32(o, "out")
+            if o.numel() != g.nx * g.ny * g.nz:
+                raise ValueError("out has the wrong size")
+    if isinstance(winner, (list, tuple)):
+        wins = list(winner)
+    elif winner:
+        wins = [torch.empty(g.shape, dtype=torch.int32, device="cuda") for g in grids]
+    else:
+        wins = [None] * n
+    fa = (ctypes.c_void_p * n)(*[f.handle.value for f in feats])
+    ga = (_CGrid * n)(*[g.c() for g in grids])
+    wa = (ctypes.c_float * n)(*[float(x) for x in ws])
+    h = ctypes.c_void_p()
+    _check(load_library().sdf_batch_create(fa, ga, wa, n, _ptr_array(outs), _ptr_array(wins),
+                                           (FLAG_AUTOTUNE if autotune else 0) | (FLAG_TIMING if timing else 0),
+                                           _stream(stream), ctypes.byref(h)),
+           "sdf_batch_create")
+    return Batch(h.value, feats, outs, wins)
 
 
 def sdf_narrow_band_backward(features: Features, grid: Grid, w: float, grad_dist: torch.Tensor,

@@ -28,8 +28,13 @@
 //   3. patch kernel: re-decides the queued points in FP64 from the winner's neighbourhood.
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "sdf_internal.cuh"
 
@@ -63,14 +68,31 @@ struct Feat {
 };
 
 struct PatchEntry {
-    long long idx;
-    int fid;
-    int pad;
+    long long idx;  // linear grid index inside its problem
+    int fid;        // FP32 winner feature
+    int prob;       // problem of the batch
 };
 
-struct Outputs {
+// one (mesh, grid, outputs) problem of a batch; the single-problem call is a batch of one
+struct Prob {
+    Feat F;
+    GridP g;
     float *dist;
     int32_t *winner;
+    int vec;  // rows 16-byte aligned: x-rows of 4 points are stored with one vector store
+};
+
+// largest p in [0, n) with base[p] <= x (base ascending, base[0] = 0)
+__device__ __forceinline__ int find_prob(const long long *base, int n, long long x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct Outputs {
     const int32_t *pairs;
     const uint32_t *bin_start;
     int64_t pair_cap;
@@ -161,29 +183,33 @@ __device__ __forceinline__ bool feature_box(const Feat &F, const GridP &g, int i
 }
 
 // ----------------------------------------------------------------------------- binning
-template <bool FILL>
-__global__ void k_bin(Feat F, GridP g, uint32_t *cnt, const uint32_t *start, int32_t *pairs, int64_t pair_cap,
-                      DevCounters *ctr) {
-    int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t total = (int64_t)F.T + F.E + F.V;
-    if (gid >= total) return;
+template <bool FILL, int TY, int TZ>
+__global__ void k_bin(const Prob *P, const long long *feat_base, const long long *tile_base, int n, long long f_tot,
+                      uint32_t *cnt, const uint32_t *start, int32_t *pairs, int64_t pair_cap, DevCounters *ctr) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= f_tot) return;
+    const int p = find_prob(feat_base, n, gid);
+    const Feat &F = P[p].F;
+    const GridP &g = P[p].g;
+    const int64_t lid = gid - feat_base[p];
     int type, id;
     bool ok;
     int i0, i1, j0, j1, k0, k1;
-    if (gid < F.T) { type = FACE; id = (int)gid; ok = feature_box<FACE>(F, g, id, i0, i1, j0, j1, k0, k1); }
-    else if (gid < (int64_t)F.T + F.E) { type = EDGE; id = (int)(gid - F.T); ok = feature_box<EDGE>(F, g, id, i0, i1, j0, j1, k0, k1); }
-    else { type = VERT; id = (int)(gid - F.T - F.E); ok = feature_box<VERT>(F, g, id, i0, i1, j0, j1, k0, k1); }
+    if (lid < F.T) { type = FACE; id = (int)lid; ok = feature_box<FACE>(F, g, id, i0, i1, j0, j1, k0, k1); }
+    else if (lid < (int64_t)F.T + F.E) { type = EDGE; id = (int)(lid - F.T); ok = feature_box<EDGE>(F, g, id, i0, i1, j0, j1, k0, k1); }
+    else { type = VERT; id = (int)(lid - F.T - F.E); ok = feature_box<VERT>(F, g, id, i0, i1, j0, j1, k0, k1); }
     if (!ok) return;
-    int fid = (int)gid;  // face f -> f, edge e -> T + e, vertex v -> T + E + v
-    for (int tz = k0 / TILE_Z; tz <= k1 / TILE_Z; tz++)
-        for (int ty = j0 / TILE_Y; ty <= j1 / TILE_Y; ty++)
+    const int fid = (int)lid;  // face f -> f, edge e -> T + e, vertex v -> T + E + v (within its problem)
+    const int64_t tb = tile_base[p];
+    for (int tz = k0 / TZ; tz <= k1 / TZ; tz++)
+        for (int ty = j0 / TY; ty <= j1 / TY; ty++)
             for (int tx = i0 / TILE_X; tx <= i1 / TILE_X; tx++) {
-                int64_t tile = ((int64_t)tz * g.nty + ty) * g.ntx + tx;
-                int64_t bin = 3 * tile + type;
+                const int64_t tile = tb + ((int64_t)tz * g.nty + ty) * g.ntx + tx;
+                const int64_t bin = 3 * tile + type;
                 if (!FILL) {
                     atomicAdd(cnt + bin, 1u);
                 } else {
-                    int64_t pos = (int64_t)start[bin] + atomicAdd(cnt + bin, 1u);
+                    const int64_t pos = (int64_t)start[bin] + atomicAdd(cnt + bin, 1u);
                     if (pos < pair_cap) pairs[pos] = fid;
                     else atomicOr(&ctr->nb_status, ST_PAIR_OVERFLOW);
                 }
@@ -213,64 +239,6 @@ __device__ __forceinline__ int warp_owner(int incl, int r) {
 
 __device__ __forceinline__ float comp(float4 P, int ax) { return ax == 0 ? P.x : (ax == 1 ? P.y : P.z); }
 __device__ __forceinline__ float comp3(float3 P, int ax) { return ax == 0 ? P.x : (ax == 1 ? P.y : P.z); }
-
-// Half-space P.xyz . p + P.w >= -eps along the grid line parallel to axis `ax` through the
-// coordinates (B, C) on the other two axes (bx < cx): shrink the interval [xa, xb] of the
-// line coordinate (Algorithm 2 restricted to a line, with the tolerance of Section 10).
-__device__ __forceinline__ void clip_plane(float4 P, int ax, int bx, int cx, float B, float C, float eps, float &xa,
-                                           float &xb) {
-    const float pa = comp(P, ax);
-    const float r = fmaf(comp(P, bx), B, fmaf(comp(P, cx), C, P.w)) + eps;
-    if (pa > 0.f) xa = fmaxf(xa, -r / pa);
-    else if (pa < 0.f) xb = fminf(xb, -r / pa);
-    else if (r < 0.f) xa = INFINITY;
-}
-
-// index span [ia, ib] within [lo, hi] along axis `ax` of the region of feature `id` on the grid
-// line with indices (rb, rc) on the other two axes
-template <int TYPE>
-__device__ __forceinline__ void row_span(const Feat &F, const GridP &g, int id, int ax, int rb, int rc, int lo, int hi,
-                                         int &ia, int &ib) {
-    const int bx = ax == 0 ? 1 : 0, cx = ax == 2 ? 1 : 2;
-    const float3 org = make_float3(g.ox, g.oy, g.oz);
-    const float B = fmaf((float)rb + 0.5f, g.h, comp3(org, bx)), C = fmaf((float)rc + 0.5f, g.h, comp3(org, cx));
-    float xa = -INFINITY, xb = INFINITY;
-    const float e = g.eps;
-    if (TYPE == FACE) {
-        const float4 *r = F.face_rec + 4 * id;
-        const float4 n = __ldg(r);
-        clip_plane(make_float4(n.x, n.y, n.z, n.w + g.W), ax, bx, cx, B, C, e, xa, xb);      // n.p + c >= -W
-        clip_plane(make_float4(-n.x, -n.y, -n.z, g.W - n.w), ax, bx, cx, B, C, e, xa, xb);   // n.p + c <= W
-        clip_plane(__ldg(r + 1), ax, bx, cx, B, C, e, xa, xb);
-        clip_plane(__ldg(r + 2), ax, bx, cx, B, C, e, xa, xb);
-        clip_plane(__ldg(r + 3), ax, bx, cx, B, C, e, xa, xb);
-    } else if (TYPE == EDGE) {
-        const float4 *r = F.edge_rec + 5 * id;
-        const float4 a = __ldg(r), t = __ldg(r + 1);
-        clip_plane(make_float4(t.x, t.y, t.z, -t.w), ax, bx, cx, B, C, e, xa, xb);           // t.(p - a) >= 0
-        clip_plane(make_float4(-t.x, -t.y, -t.z, t.w + a.w), ax, bx, cx, B, C, e, xa, xb);   // t.(p - a) <= L
-        clip_plane(__ldg(r + 2), ax, bx, cx, B, C, e, xa, xb);                               // (p - a).m1 <= 0
-        clip_plane(__ldg(r + 3), ax, bx, cx, B, C, e, xa, xb);                               // (p - a).m2 <= 0
-    } else {
-        const float4 v = __ldg(F.vert_rec + 3 * id), nv = __ldg(F.vert_rec + 3 * id + 1);
-        const float3 vv = f3(v);
-        const float db = B - comp3(vv, bx), dc = C - comp3(vv, cx);
-        const float R = g.W + e;
-        const float r2 = R * R - db * db - dc * dc;
-        if (r2 < 0.f) { ia = 1; ib = 0; return; }
-        const float sq = sqrtf(r2);
-        xa = comp3(vv, ax) - sq;
-        xb = comp3(vv, ax) + sq;
-        const int s0 = __float_as_int(v.w), cnt = __float_as_int(nv.w);
-        for (int q = 0; q < cnt; q++) clip_plane(__ldg(F.vert_plane + s0 + q), ax, bx, cx, B, C, e, xa, xb);
-    }
-    const float sl = 1.f / 4096.f;
-    const float oa = comp3(org, ax);
-    const float fa = fminf(fmaxf((xa - oa) * g.inv_h - 0.5f - sl, (float)lo), (float)hi + 1.f);
-    const float fb = fmaxf(fminf((xb - oa) * g.inv_h - 0.5f + sl, (float)hi), (float)lo - 1.f);
-    ia = (int)ceilf(fa);
-    ib = (int)floorf(fb);
-}
 
 // FP32 distance to the triangle boundary (three clamped segments); used for points of the face
 // prism's tolerance margin, whose closest triangle point lies on the boundary
@@ -328,12 +296,6 @@ __device__ __forceinline__ bool box_any(const Feat &F, const GridP &g, int type,
     if (type == EDGE) return feature_box<EDGE>(F, g, id, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
     return feature_box<VERT>(F, g, id, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
 }
-__device__ __forceinline__ void span_any(const Feat &F, const GridP &g, int type, int id, int ax, int rb, int rc,
-                                         int lo, int hi, int &ia, int &ib) {
-    if (type == FACE) row_span<FACE>(F, g, id, ax, rb, rc, lo, hi, ia, ib);
-    else if (type == EDGE) row_span<EDGE>(F, g, id, ax, rb, rc, lo, hi, ia, ib);
-    else row_span<VERT>(F, g, id, ax, rb, rc, lo, hi, ia, ib);
-}
 __device__ __forceinline__ float eval_any(const Feat &F, const GridP &g, int type, int id, int i, int j, int k,
                                           bool &neg) {
     if (type == FACE) return eval_point<FACE>(F, g, id, i, j, k, neg);
@@ -353,8 +315,9 @@ __device__ __forceinline__ float eval_any(const Feat &F, const GridP &g, int typ
 constexpr int KMAX = 7, MAXVP = 6, ROW_TABLE = 4096;
 enum { K_LOWER = 0, K_UPPER = 1, K_GATE = 2 };
 
+template <int TY, int TZ>
 struct TileSmem {
-    unsigned long long key[TILE_PTS];  // packed (|d| bits << 32 | id << 1 | sign), one per tile point
+    unsigned long long key[TILE_X * TY * TZ];  // packed (|d| bits << 32 | id << 1 | sign) per tile point
     float4 coef[NT][KMAX];             // span coefficients (A, B, C, kind) per region of the pass
     float4 ball[NT];                   // vertex ball in index units (j_v, db0, dc0, R^2), R^2 < 0: none
     int fid[NT];                       // regions of the current pass (global feature ids)
@@ -384,9 +347,10 @@ __device__ __forceinline__ void add_coef(float4 *E, int &ne, float4 P, int ax, i
 // lane takes one row and evaluates the span from the coefficients (Algorithm 2 on a grid line);
 // (4) the span points of a warp are flattened over its lanes and merged into the tile's keys with
 // a shared-memory atomicMin (Algorithm 1).
+template <int TY, int TZ>
 __device__ void process_band_tile(const Feat &F, const GridP &g, const int32_t *pairs, int64_t q0, int64_t q3,
-                                  int x0, int y0, int z0, int cx1, int cy1, int cz1, TileSmem &S, unsigned &cand,
-                                  unsigned &rows, unsigned &hits) {
+                                  int x0, int y0, int z0, int cx1, int cy1, int cz1, TileSmem<TY, TZ> &S,
+                                  unsigned &cand, unsigned &rows, unsigned &hits) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = threadIdx.x;
     const float3 org = make_float3(g.ox, g.oy, g.oz);
     for (int64_t base = q0; base < q3; base += NT) {
@@ -556,7 +520,7 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int32_t *
                         const unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) |
                                                        ((unsigned long long)(unsigned)gid << 1) |
                                                        (unsigned long long)neg;
-                        const int loc = ((pk - z0) * TILE_Y + (pj - y0)) * TILE_X + (pi - x0);
+                        const int loc = ((pk - z0) * TY + (pj - y0)) * TILE_X + (pi - x0);
                         atomicMin(S.key + loc, key);
                         cand++;
                     }
@@ -569,7 +533,7 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int32_t *
 
 // decode one merged key into the output value / winner, queueing FP64 re-decisions
 __device__ __forceinline__ float decode_key(unsigned long long key, const GridP &g, const Outputs &o, int64_t idx,
-                                            int &wid, unsigned &band, bool &overflow) {
+                                            int prob, int &wid, unsigned &band, bool &overflow) {
     wid = -1;
     if (key == ~0ull) return INFINITY;
     const float d = __uint_as_float((unsigned)(key >> 32));
@@ -586,7 +550,7 @@ __device__ __forceinline__ float decode_key(unsigned long long key, const GridP 
             PatchEntry pe;
             pe.idx = idx;
             pe.fid = fid;
-            pe.pad = 0;
+            pe.prob = prob;
             o.patch[slot] = pe;
         } else {
             overflow = true;
@@ -613,23 +577,24 @@ __global__ void k_tile_lists(const uint32_t *bin_start, int64_t n_tiles, const u
     else empty_list[t - band_pos[t]] = (int32_t)t;
 }
 
-// Persistent tile kernel: CTAs take work items from one atomic ticket.  A band tile merges its
-// regions' candidates in shared memory and writes its 2048 points; an empty-tile chunk is written
-// +inf (Algorithm 1's initial value).  vec: rows are 16-byte aligned (nx % 4 == 0 and aligned
-// outputs), so a thread stores 4 consecutive x values at once.
-__global__ void __launch_bounds__(NT, 3) k_tile(Feat F, GridP g, Outputs o, int64_t n_tiles,
-                                                const int32_t *band_list, const int32_t *empty_list,
-                                                const uint32_t *n_band_ptr, unsigned long long *ticket, int vec) {
+// Persistent tile kernel over all tiles of all problems of a batch: CTAs take work items from one
+// atomic ticket.  Work item w < n_band is band tile w plus its share of the empty tiles (so the
+// HBM-bound +inf fill is spread over the compute-bound band work); without band tiles, items are
+// chunks of FILL_CHUNK empty tiles.  A band tile merges its regions' candidates in shared memory
+// and writes its points; an empty tile is written +inf (Algorithm 1's initial value).
+template <int TY, int TZ>
+__global__ void __launch_bounds__(NT, 3) k_tile(const Prob *P, const long long *tile_base, int n, Outputs o,
+                                                int64_t n_tiles, const int32_t *band_list,
+                                                const int32_t *empty_list, const uint32_t *n_band_ptr,
+                                                unsigned long long *ticket) {
+    constexpr int TP = TILE_X * TY * TZ;
     extern __shared__ __align__(16) unsigned char tile_smem[];
-    TileSmem &S = *reinterpret_cast<TileSmem *>(tile_smem);
+    TileSmem<TY, TZ> &S = *reinterpret_cast<TileSmem<TY, TZ> *>(tile_smem);
     __shared__ unsigned s_cand, s_band, s_ovf, s_rows, s_hits, s_pairs;
     if (threadIdx.x == 0) { s_cand = 0; s_band = 0; s_ovf = 0; s_rows = 0; s_hits = 0; s_pairs = 0; }
     unsigned cand = 0, band = 0, rows = 0, hits = 0, pairs = 0;
     bool overflow = false;
-    const int64_t plane = (int64_t)g.nx * g.ny;
     const int64_t n_band = *n_band_ptr, n_empty = n_tiles - n_band;
-    // work item w < n_band: band tile w plus its share of the empty tiles, so that the HBM-bound
-    // +inf fill is spread over the compute-bound band work; without band tiles, chunks of empties
     const int64_t n_work = n_band > 0 ? n_band : (n_empty + FILL_CHUNK - 1) / FILL_CHUNK;
     for (;;) {
         if (threadIdx.x == 0) S.work = (long long)atomicAdd(ticket, 1ull);
@@ -637,7 +602,6 @@ __global__ void __launch_bounds__(NT, 3) k_tile(Feat F, GridP g, Outputs o, int6
         const int64_t w = S.work;
         __syncthreads();
         if (w >= n_work) break;
-        // empty tiles [e_begin, e_end) of this item
         const int64_t e_begin = n_band > 0 ? (w * n_empty) / n_band : w * FILL_CHUNK;
         const int64_t e_end = n_band > 0 ? ((w + 1) * n_empty) / n_band : min(e_begin + FILL_CHUNK, n_empty);
         const int64_t t_begin = n_band > 0 ? -1 : 0;  // -1 = the band tile of the item
@@ -645,23 +609,28 @@ __global__ void __launch_bounds__(NT, 3) k_tile(Feat F, GridP g, Outputs o, int6
         for (int64_t ti = t_begin; ti < t_end; ti++) {
             const bool is_band = ti < 0;
             const int64_t tile = is_band ? band_list[w] : empty_list[e_begin + ti];
-            const uint32_t tu = (uint32_t)tile, r1 = g.div_ntx.div(tu), tz = g.div_nty.div(r1);
+            const int p = find_prob(tile_base, n, tile);
+            const Prob &pr = P[p];
+            const GridP &g = pr.g;
+            const uint32_t tu = (uint32_t)(tile - tile_base[p]), r1 = g.div_ntx.div(tu), tz = g.div_nty.div(r1);
             const int tx = (int)(tu - r1 * (uint32_t)g.ntx), ty = (int)(r1 - tz * (uint32_t)g.nty);
-            const int x0 = tx * TILE_X, y0 = ty * TILE_Y, z0 = tz * TILE_Z;
-            const int cx1 = min(x0 + TILE_X, g.nx) - 1, cy1 = min(y0 + TILE_Y, g.ny) - 1,
-                      cz1 = min(z0 + TILE_Z, g.nz) - 1;
+            const int x0 = tx * TILE_X, y0 = ty * TY, z0 = (int)tz * TZ;
+            const int cx1 = min(x0 + TILE_X, g.nx) - 1, cy1 = min(y0 + TY, g.ny) - 1, cz1 = min(z0 + TZ, g.nz) - 1;
+            const int64_t plane = (int64_t)g.nx * g.ny;
+            float *dist = pr.dist;
+            int32_t *winner = pr.winner;
             if (is_band) {
                 const uint32_t *st = o.bin_start + 3 * tile;
                 const int64_t q0 = min((int64_t)st[0], o.pair_cap), q3 = min((int64_t)st[3], o.pair_cap);
-                for (int e = threadIdx.x; e < TILE_PTS; e += NT) S.key[e] = ~0ull;
+                for (int e = threadIdx.x; e < TP; e += NT) S.key[e] = ~0ull;
                 __syncthreads();
-                process_band_tile(F, g, o.pairs, q0, q3, x0, y0, z0, cx1, cy1, cz1, S, cand, rows, hits);
+                process_band_tile<TY, TZ>(pr.F, g, o.pairs, q0, q3, x0, y0, z0, cx1, cy1, cz1, S, cand, rows, hits);
                 if (threadIdx.x == 0) pairs += (unsigned)(q3 - q0);
             }
-            if (vec && cx1 == x0 + TILE_X - 1) {
+            if (pr.vec && cx1 == x0 + TILE_X - 1) {
                 // 8 threads per 32-point row, 4 points each
-                for (int r = threadIdx.x >> 3; r < TILE_Y * TILE_Z; r += NT / 8) {
-                    const int y = r % TILE_Y, z = r / TILE_Y;
+                for (int r = threadIdx.x >> 3; r < TY * TZ; r += NT / 8) {
+                    const int y = r % TY, z = r / TY;
                     const int gj = y0 + y, gk = z0 + z;
                     if (gj > cy1 || gk > cz1) continue;
                     const int x = (threadIdx.x & 7) * 4;
@@ -670,24 +639,24 @@ __global__ void __launch_bounds__(NT, 3) k_tile(Feat F, GridP g, Outputs o, int6
                     int4 wv = make_int4(-1, -1, -1, -1);
                     if (is_band) {
                         const unsigned long long *kp = S.key + r * TILE_X + x;
-                        v.x = decode_key(kp[0], g, o, idx, wv.x, band, overflow);
-                        v.y = decode_key(kp[1], g, o, idx + 1, wv.y, band, overflow);
-                        v.z = decode_key(kp[2], g, o, idx + 2, wv.z, band, overflow);
-                        v.w = decode_key(kp[3], g, o, idx + 3, wv.w, band, overflow);
+                        v.x = decode_key(kp[0], g, o, idx, p, wv.x, band, overflow);
+                        v.y = decode_key(kp[1], g, o, idx + 1, p, wv.y, band, overflow);
+                        v.z = decode_key(kp[2], g, o, idx + 2, p, wv.z, band, overflow);
+                        v.w = decode_key(kp[3], g, o, idx + 3, p, wv.w, band, overflow);
                     }
-                    *reinterpret_cast<float4 *>(o.dist + idx) = v;
-                    if (o.winner) *reinterpret_cast<int4 *>(o.winner + idx) = wv;
+                    *reinterpret_cast<float4 *>(dist + idx) = v;
+                    if (winner) *reinterpret_cast<int4 *>(winner + idx) = wv;
                 }
             } else {
-                for (int e = threadIdx.x; e < TILE_PTS; e += NT) {
-                    const int x = e % TILE_X, y = (e / TILE_X) % TILE_Y, z = e / (TILE_X * TILE_Y);
+                for (int e = threadIdx.x; e < TP; e += NT) {
+                    const int x = e % TILE_X, y = (e / TILE_X) % TY, z = e / (TILE_X * TY);
                     const int gi = x0 + x, gj = y0 + y, gk = z0 + z;
                     if (gi > cx1 || gj > cy1 || gk > cz1) continue;
                     const int64_t idx = (int64_t)gk * plane + (int64_t)gj * g.nx + gi;
                     int wid = -1;
-                    const float val = is_band ? decode_key(S.key[e], g, o, idx, wid, band, overflow) : INFINITY;
-                    o.dist[idx] = val;
-                    if (o.winner) o.winner[idx] = wid;
+                    const float val = is_band ? decode_key(S.key[e], g, o, idx, p, wid, band, overflow) : INFINITY;
+                    dist[idx] = val;
+                    if (winner) winner[idx] = wid;
                 }
             }
             if (is_band) __syncthreads();  // keys are reused by the next band tile
@@ -768,16 +737,19 @@ __device__ __forceinline__ double wsum(double v) {
 
 // one warp per queued point: FP64 minimum over the triangles around the winner's vertices, sign
 // from the pseudonormal of the closest feature (face normal, n1 + n2, or N_alpha, Eq. 8)
-__global__ void k_patch(Feat F, GridP g, Outputs o) {
+__global__ void k_patch(const Prob *P, Outputs o) {
     const int lane = threadIdx.x & 31;
     const int64_t wid0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t n = min((int64_t)o.ctr->n_patch, o.patch_cap);
-    const double h = g.h;
     for (int64_t e = wid0; e < n; e += nwarps) {
         PatchEntry pe = o.patch[e];
         const int64_t idx = pe.idx;
         const int fid = pe.fid;
+        const Feat &F = P[pe.prob].F;
+        const GridP &g = P[pe.prob].g;
+        float *const dist = P[pe.prob].dist;
+        int32_t *const winner = P[pe.prob].winner;
         const int64_t plane = (int64_t)g.nx * g.ny;
         int gi, gj, gk;
         if (idx < (int64_t(1) << 31)) {
@@ -790,6 +762,7 @@ __global__ void k_patch(Feat F, GridP g, Outputs o) {
             gj = (int)((idx - (int64_t)gk * plane) / g.nx);
             gi = (int)(idx - (int64_t)gk * plane - (int64_t)gj * g.nx);
         }
+        const double h = g.h;
         const double3 p = make_double3((double)g.ox + (gi + 0.5) * h, (double)g.oy + (gj + 0.5) * h,
                                        (double)g.oz + (gk + 0.5) * h);
         int vs[3], nv;
@@ -873,8 +846,8 @@ __global__ void k_patch(Feat F, GridP g, Outputs o) {
                 val = (float)(s < 0.0 ? -d : d);
                 w = out_id;
             }
-            o.dist[idx] = val;
-            if (o.winner) o.winner[idx] = w;
+            dist[idx] = val;
+            if (winner) winner[idx] = w;
         }
     }
 }
@@ -884,15 +857,22 @@ inline unsigned nblk(int64_t n, int bt) { return (unsigned)((n + bt - 1) / bt); 
 }  // namespace
 
 // ----------------------------------------------------------------------------- host side
-static int make_grid(const sdf_grid &gr, float w, GridP &g) {
+// Tile shapes the kernels are instantiated for: 32 x TY x TZ points.  8 x 8 is the default; a
+// batch created with SDF_FLAG_AUTOTUNE times all of them on its own problems and keeps the fastest.
+constexpr int N_SHAPES = 3;
+static const int SHAPE_TY[N_SHAPES] = {8, 4, 16};
+static const int SHAPE_TZ[N_SHAPES] = {8, 4, 8};
+
+static int make_grid(const sdf_grid &gr, float w, int shape, GridP &g) {
     if (gr.nx < 1 || gr.ny < 1 || gr.nz < 1 || !(gr.h > 0.f) || !isfinite(gr.h) || !(w > 0.f) || !isfinite(w))
         return SDF_ERR_INVALID_ARG;
     for (int j = 0; j < 3; j++)
         if (!isfinite(gr.origin[j])) return SDF_ERR_INVALID_ARG;
+    if ((int64_t)gr.nx * gr.ny >= (int64_t(1) << 40)) return SDF_ERR_TOO_LARGE;
     g.nx = gr.nx; g.ny = gr.ny; g.nz = gr.nz;
     g.ntx = (gr.nx + TILE_X - 1) / TILE_X;
-    g.nty = (gr.ny + TILE_Y - 1) / TILE_Y;
-    g.ntz = (gr.nz + TILE_Z - 1) / TILE_Z;
+    g.nty = (gr.ny + SHAPE_TY[shape] - 1) / SHAPE_TY[shape];
+    g.ntz = (gr.nz + SHAPE_TZ[shape] - 1) / SHAPE_TZ[shape];
     if ((int64_t)g.ntx * g.nty * g.ntz * 3 >= (int64_t(1) << 31)) return SDF_ERR_TOO_LARGE;
     g.div_ntx = FastDiv((uint32_t)g.ntx);
     g.div_nty = FastDiv((uint32_t)g.nty);
@@ -930,7 +910,6 @@ static Feat make_feat(const sdf_features_s *f) {
     return F;
 }
 
-// one (mesh, grid) problem; returns SDF_OK or an error; sets *retry when scratch was too small
 static int num_sms() {
     static int n = 0;
     if (!n) {
@@ -941,14 +920,25 @@ static int num_sms() {
     }
     return n;
 }
-static int tile_blocks_per_sm() {
+
+template <int TY, int TZ> static int tile_blocks_per_sm() {
     static int b = 0;
     if (!b) {
-        cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tile, NT, sizeof(TileSmem));
+        cudaFuncSetAttribute(k_tile<TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(TileSmem<TY, TZ>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tile<TY, TZ>, NT, sizeof(TileSmem<TY, TZ>));
         if (b <= 0) b = 1;
     }
     return b;
+}
+
+// an event record that becomes an event node (with its timestamp) when the stream is being captured
+static cudaError_t record_event(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t err = cudaStreamIsCapturing(s, &cs);
+    if (err != cudaSuccess) return err;
+    return cudaEventRecordWithFlags(e, s, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                             : cudaEventRecordDefault);
 }
 
 int ensure_events(sdf_features_s *f) {
@@ -957,75 +947,232 @@ int ensure_events(sdf_features_s *f) {
     return SDF_OK;
 }
 
-static int narrow_band_one(sdf_features_s *f, const sdf_grid &gr, float w, float *out, int32_t *win,
-                           cudaStream_t s, bool sync, bool timing, bool *retry) {
-    GridP g;
-    int st = make_grid(gr, w, g);
-    if (st) return st;
-    Feat F = make_feat(f);
-    const int64_t n_tiles = (int64_t)g.ntx * g.nty * g.ntz, n_bins = 3 * n_tiles;
-    const int64_t n_feat = f->T + f->E + f->V;
-    // scratch: cnt [n_bins], start [n_bins + 1], scan temporaries
-    size_t bins_bytes = sizeof(uint32_t) * (size_t)(2 * n_bins + 64);
-    SDF_TRY(f->bins.reserve(bins_bytes, s));
-    SDF_TRY(f->scan_tmp.reserve(scan_tmp_bytes(n_bins), s));
-    SDF_TRY(f->lists.reserve(16 + sizeof(uint32_t) * (size_t)(3 * n_tiles + 256), s));
-    if (f->pair_cap == 0) f->pair_cap = 8 * n_feat + 4096;
-    if (f->patch_cap == 0) f->patch_cap = n_feat / 8 + 65536;
-    SDF_TRY(f->pairs.reserve(sizeof(int32_t) * (size_t)f->pair_cap, s));
-    SDF_TRY(f->patch.reserve(sizeof(PatchEntry) * (size_t)f->patch_cap, s));
-    uint32_t *cnt = f->bins.as<uint32_t>(), *start = cnt + n_bins + 32;
-    if (timing) {
-        if (ensure_events(f)) return SDF_ERR_CUDA;
-        SDF_TRY(cudaEventRecord(f->ev[0], s));
+// A batch of (mesh, grid, outputs) problems: host description, device tables and scratch.
+struct Plan {
+    int n = 0, shape = 0;
+    std::vector<Prob> probs;
+    std::vector<long long> fbase, tbase;  // prefix sums of features and tiles over the problems
+    long long f_tot = 0, n_tiles = 0;
+    DevBuf tables, bins, pairs, patch, scan_tmp, lists;
+    DevCounters *ctr = nullptr;
+    bool own_ctr = false;
+    int64_t pair_cap = 0, patch_cap = 0;
+    double tuned_ms = 0.0;
+    sdf_features_s *events = nullptr;  // handle whose events time the stages (SDF_FLAG_TIMING)
+    // the last uploaded table (host copy), the device address it went to, and a pinned staging
+    // buffer with an event marking the end of its last copy
+    std::vector<char> uploaded;
+    const void *uploaded_to = nullptr;
+    char *pinned = nullptr;
+    size_t pinned_bytes = 0;
+    cudaEvent_t pinned_ev = nullptr;
+    bool pageable = false;  // one-shot plans copy the table from pageable memory
+    bool batch_timing = false;  // record bev[0..3] around the stages of every launch
+    cudaEvent_t bev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+void plan_free(Plan *pl, cudaStream_t s) {
+    if (!pl) return;
+    pl->tables.release(s);
+    pl->bins.release(s);
+    pl->pairs.release(s);
+    pl->patch.release(s);
+    pl->scan_tmp.release(s);
+    pl->lists.release(s);
+    if (pl->own_ctr && pl->ctr) pool_free(pl->ctr, s);
+    if (pl->pinned_ev) {
+        cudaEventSynchronize(pl->pinned_ev);
+        cudaEventDestroy(pl->pinned_ev);
     }
-    SDF_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n_bins, s));
-    SDF_TRY(cudaMemsetAsync(&f->ctr->nb_status, 0, sizeof(unsigned), s));
-    SDF_TRY(cudaMemsetAsync(&f->ctr->n_candidates, 0, 6 * sizeof(unsigned long long), s));
-    k_bin<false><<<nblk(n_feat, 256), 256, 0, s>>>(F, g, cnt, nullptr, nullptr, 0, f->ctr);
+    if (pl->pinned) cudaFreeHost(pl->pinned);
+    for (cudaEvent_t e : pl->bev)
+        if (e) cudaEventDestroy(e);
+    delete pl;
+}
+
+static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *grids, const float *band_w, int n,
+                         float *const *out_dist, int32_t *const *out_winner, int shape) {
+    if (!feats || !grids || !band_w || n < 1 || !out_dist) return SDF_ERR_INVALID_ARG;
+    pl.n = n;
+    pl.shape = shape;
+    pl.probs.resize(n);
+    pl.fbase.assign(n + 1, 0);
+    pl.tbase.assign(n + 1, 0);
+    for (int p = 0; p < n; p++) {
+        if (!feats[p] || !out_dist[p]) return SDF_ERR_INVALID_ARG;
+        Prob &pr = pl.probs[p];
+        int st = make_grid(grids[p], band_w[p], shape, pr.g);
+        if (st) return st;
+        pr.F = make_feat(feats[p]);
+        pr.dist = out_dist[p];
+        pr.winner = out_winner ? out_winner[p] : nullptr;
+        pr.vec = ((pr.g.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(pr.dist) & 15) == 0) &&
+                 ((reinterpret_cast<uintptr_t>(pr.winner) & 15) == 0);
+        pl.fbase[p + 1] = pl.fbase[p] + feats[p]->T + feats[p]->E + feats[p]->V;
+        pl.tbase[p + 1] = pl.tbase[p] + (long long)pr.g.ntx * pr.g.nty * pr.g.ntz;
+    }
+    pl.f_tot = pl.fbase[n];
+    pl.n_tiles = pl.tbase[n];
+    if (3 * pl.n_tiles >= (int64_t(1) << 31) || pl.f_tot >= (int64_t(1) << 31)) return SDF_ERR_TOO_LARGE;
+    return SDF_OK;
+}
+
+// allocate scratch for the current capacities and upload the tables (not allowed while capturing)
+static int plan_reserve(Plan &pl, cudaStream_t s) {
+    const int64_t n_bins = 3 * pl.n_tiles;
+    const size_t tb = sizeof(Prob) * pl.n + 2 * sizeof(long long) * (pl.n + 1) + 256;
+    SDF_TRY(pl.tables.reserve(tb, s));
+    SDF_TRY(pl.bins.reserve(sizeof(uint32_t) * (size_t)(2 * n_bins + 64), s));
+    SDF_TRY(pl.scan_tmp.reserve(scan_tmp_bytes(n_bins), s));
+    SDF_TRY(pl.lists.reserve(16 + sizeof(uint32_t) * (size_t)(3 * pl.n_tiles + 256), s));
+    if (pl.pair_cap == 0) pl.pair_cap = 8 * pl.f_tot + 4096;
+    if (pl.patch_cap == 0) pl.patch_cap = pl.f_tot / 8 + 65536;
+    SDF_TRY(pl.pairs.reserve(sizeof(int32_t) * (size_t)pl.pair_cap, s));
+    SDF_TRY(pl.patch.reserve(sizeof(PatchEntry) * (size_t)pl.patch_cap, s));
+    if (!pl.ctr) {
+        SDF_TRY(pool_alloc(reinterpret_cast<void **>(&pl.ctr), sizeof(DevCounters), s));
+        SDF_TRY(cudaMemsetAsync(pl.ctr, 0, sizeof(DevCounters), s));
+        pl.own_ctr = true;
+    }
+    // the table: Prob[n], then feature and tile prefix sums; uploaded only when it changed
+    const size_t pb = sizeof(Prob) * pl.n, lb = sizeof(long long) * (pl.n + 1);
+    std::vector<char> tab(pb + 2 * lb);
+    memcpy(tab.data(), pl.probs.data(), pb);
+    memcpy(tab.data() + pb, pl.fbase.data(), lb);
+    memcpy(tab.data() + pb + lb, pl.tbase.data(), lb);
+    if (pl.uploaded_to == pl.tables.p && pl.uploaded == tab) return SDF_OK;
+    if (pl.pageable) {
+        pl.uploaded.swap(tab);
+        pl.uploaded_to = pl.tables.p;
+        SDF_TRY(cudaMemcpyAsync(pl.tables.p, pl.uploaded.data(), pl.uploaded.size(), cudaMemcpyHostToDevice, s));
+        return SDF_OK;
+    }
+    if (!pl.pinned_ev) SDF_TRY(cudaEventCreateWithFlags(&pl.pinned_ev, cudaEventDisableTiming));
+    SDF_TRY(cudaEventSynchronize(pl.pinned_ev));  // the previous copy out of the staging buffer
+    if (pl.pinned_bytes < tab.size()) {
+        if (pl.pinned) cudaFreeHost(pl.pinned);
+        pl.pinned = nullptr;
+        pl.pinned_bytes = 0;
+        SDF_TRY(cudaMallocHost(reinterpret_cast<void **>(&pl.pinned), tab.size() + 1024));
+        pl.pinned_bytes = tab.size() + 1024;
+    }
+    memcpy(pl.pinned, tab.data(), tab.size());
+    SDF_TRY(cudaMemcpyAsync(pl.tables.p, pl.pinned, tab.size(), cudaMemcpyHostToDevice, s));
+    SDF_TRY(cudaEventRecord(pl.pinned_ev, s));
+    pl.uploaded.swap(tab);
+    pl.uploaded_to = pl.tables.p;
+    return SDF_OK;
+}
+
+struct Scratch {  // device pointers used by one launch of the pipeline
+    const Prob *probs;
+    const long long *fbase, *tbase;
+    uint32_t *cnt, *start;
+    void *scan_tmp;
+    unsigned long long *ticket;
+    uint32_t *band_pos;
+    int32_t *band_list, *empty_list;
+    int32_t *pairs;
+    int64_t pair_cap;
+    PatchEntry *patch;
+    int64_t patch_cap;
+    DevCounters *ctr;
+};
+
+static Scratch plan_scratch(const Plan &pl) {
+    Scratch sc;
+    const char *t = pl.tables.as<char>();
+    sc.probs = reinterpret_cast<const Prob *>(t);
+    sc.fbase = reinterpret_cast<const long long *>(t + sizeof(Prob) * pl.n);
+    sc.tbase = sc.fbase + pl.n + 1;
+    sc.cnt = pl.bins.as<uint32_t>();
+    sc.start = sc.cnt + 3 * pl.n_tiles + 32;
+    sc.scan_tmp = pl.scan_tmp.p;
+    sc.ticket = pl.lists.as<unsigned long long>();  // 8-byte aligned (allocation start)
+    sc.band_pos = reinterpret_cast<uint32_t *>(sc.ticket + 2);
+    sc.band_list = reinterpret_cast<int32_t *>(sc.band_pos + pl.n_tiles + 32);
+    sc.empty_list = sc.band_list + pl.n_tiles + 32;
+    sc.pairs = pl.pairs.as<int32_t>();
+    sc.pair_cap = pl.pair_cap;
+    sc.patch = pl.patch.as<PatchEntry>();
+    sc.patch_cap = pl.patch_cap;
+    sc.ctr = pl.ctr;
+    return sc;
+}
+
+// the whole pipeline of one batch: kernels and memsets only (no allocation, no synchronisation)
+template <int TY, int TZ>
+static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &sc, cudaStream_t s,
+                        cudaEvent_t *ev) {
+    const int64_t n_bins = 3 * n_tiles;
+    if (ev) SDF_TRY(record_event(ev[0], s));
+    SDF_TRY(cudaMemsetAsync(sc.cnt, 0, sizeof(uint32_t) * n_bins, s));
+    SDF_TRY(cudaMemsetAsync(&sc.ctr->nb_status, 0, sizeof(unsigned), s));
+    SDF_TRY(cudaMemsetAsync(&sc.ctr->n_candidates, 0, 6 * sizeof(unsigned long long), s));
+    k_bin<false, TY, TZ><<<nblk(f_tot, 256), 256, 0, s>>>(sc.probs, sc.fbase, sc.tbase, n, f_tot, sc.cnt, nullptr,
+                                                          nullptr, 0, sc.ctr);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
-    SDF_TRY(scan_exclusive_u32(cnt, start, n_bins, true, f->scan_tmp.p, s));
-    SDF_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n_bins, s));
-    k_bin<true><<<nblk(n_feat, 256), 256, 0, s>>>(F, g, cnt, start, f->pairs.as<int32_t>(), f->pair_cap, f->ctr);
+    SDF_TRY(scan_exclusive_u32(sc.cnt, sc.start, n_bins, true, sc.scan_tmp, s));
+    SDF_TRY(cudaMemsetAsync(sc.cnt, 0, sizeof(uint32_t) * n_bins, s));
+    k_bin<true, TY, TZ><<<nblk(f_tot, 256), 256, 0, s>>>(sc.probs, sc.fbase, sc.tbase, n, f_tot, sc.cnt, sc.start,
+                                                         sc.pairs, sc.pair_cap, sc.ctr);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
-    Outputs o;
-    o.dist = out;
-    o.winner = win;
-    o.pairs = f->pairs.as<int32_t>();
-    o.bin_start = start;
-    o.pair_cap = f->pair_cap;
-    o.patch = f->patch.as<PatchEntry>();
-    o.patch_cap = f->patch_cap;
-    o.ctr = f->ctr;
     // band / empty tile lists for the persistent tile kernel (one scan of the band flags)
-    uint32_t *flags = cnt;  // the fill cursors are no longer needed
-    k_band_flags<<<nblk(n_tiles, 256), 256, 0, s>>>(start, n_tiles, flags);
+    uint32_t *flags = sc.cnt;  // the fill cursors are no longer needed
+    k_band_flags<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, flags);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
-    unsigned long long *ticket = f->lists.as<unsigned long long>();  // 8-byte aligned (allocation start)
-    uint32_t *band_pos = reinterpret_cast<uint32_t *>(ticket + 2);
-    int32_t *band_list = reinterpret_cast<int32_t *>(band_pos + n_tiles + 32);
-    int32_t *empty_list = band_list + n_tiles + 32;
-    SDF_TRY(scan_exclusive_u32(flags, band_pos, n_tiles, true, f->scan_tmp.p, s));
-    k_tile_lists<<<nblk(n_tiles, 256), 256, 0, s>>>(start, n_tiles, band_pos, band_list, empty_list);
+    SDF_TRY(scan_exclusive_u32(flags, sc.band_pos, n_tiles, true, sc.scan_tmp, s));
+    k_tile_lists<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, sc.band_pos, sc.band_list, sc.empty_list);
     SDF_LAUNCHED(1);
-    SDF_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
-    if (timing) SDF_TRY(cudaEventRecord(f->ev[1], s));
-    const int vec = ((g.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0) &&
-                    ((reinterpret_cast<uintptr_t>(win) & 15) == 0);
-    const int64_t tile_ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm() * num_sms());
-    k_tile<<<(unsigned)tile_ctas, NT, sizeof(TileSmem), s>>>(F, g, o, n_tiles, band_list, empty_list, band_pos + n_tiles, ticket,
-                                              vec);
-    SDF_LAUNCHED(1);
-    SDF_TRY(cudaGetLastError());
-    if (timing) SDF_TRY(cudaEventRecord(f->ev[2], s));
-    k_patch<<<4 * 152, 256, 0, s>>>(F, g, o);
+    SDF_TRY(cudaMemsetAsync(sc.ticket, 0, sizeof(unsigned long long), s));
+    Outputs o;
+    o.pairs = sc.pairs;
+    o.bin_start = sc.start;
+    o.pair_cap = sc.pair_cap;
+    o.patch = sc.patch;
+    o.patch_cap = sc.patch_cap;
+    o.ctr = sc.ctr;
+    if (ev) SDF_TRY(record_event(ev[1], s));
+    const int64_t ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm<TY, TZ>() * num_sms());
+    k_tile<TY, TZ><<<(unsigned)ctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
+        sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
-    if (timing) {
-        SDF_TRY(cudaEventRecord(f->ev[3], s));
+    if (ev) SDF_TRY(record_event(ev[2], s));
+    k_patch<<<4 * num_sms(), 256, 0, s>>>(sc.probs, o);
+    SDF_LAUNCHED(1);
+    SDF_TRY(cudaGetLastError());
+    if (ev) SDF_TRY(record_event(ev[3], s));
+    return SDF_OK;
+}
+
+static int launch_any(int shape, int n, long long f_tot, int64_t n_tiles, const Scratch &sc, cudaStream_t s,
+                      cudaEvent_t *ev) {
+    switch (shape) {
+    case 1: return launch_shape<4, 4>(n, f_tot, n_tiles, sc, s, ev);
+    case 2: return launch_shape<16, 8>(n, f_tot, n_tiles, sc, s, ev);
+    default: return launch_shape<8, 8>(n, f_tot, n_tiles, sc, s, ev);
+    }
+}
+
+// Single-problem calls with SDF_FLAG_TIMING time the stages with the handle's events and wait for
+// them; a batch created with SDF_FLAG_TIMING records its own events on every run (also inside a
+// graph capture, as event nodes) and leaves the reading to sdf_batch_timing.
+static int plan_launch(Plan &pl, cudaStream_t s, bool timing) {
+    cudaEvent_t *ev = nullptr;
+    if (pl.batch_timing) {
+        ev = pl.bev;
+    } else if (timing && pl.events) {
+        if (ensure_events(pl.events)) return SDF_ERR_CUDA;
+        ev = pl.events->ev;
+    }
+    int st = launch_any(pl.shape, pl.n, pl.f_tot, pl.n_tiles, plan_scratch(pl), s, ev);
+    if (st) return st;
+    if (ev && !pl.batch_timing) {
+        sdf_features_s *f = pl.events;
         SDF_TRY(cudaEventSynchronize(f->ev[3]));
         for (int i = 0; i < 3; i++) {
             float ms = 0.f;
@@ -1034,23 +1181,48 @@ static int narrow_band_one(sdf_features_s *f, const sdf_grid &gr, float w, float
             f->t_calls[i]++;
         }
     }
-    if (!sync) return SDF_OK;
+    return SDF_OK;
+}
+
+// synchronise, read the counters, and grow the capacities that overflowed (retry set)
+static int plan_check(Plan &pl, const sdf_features *feats, cudaStream_t s, bool *retry) {
     DevCounters c;
     uint32_t total_pairs = 0;
-    SDF_TRY(cudaMemcpyAsync(&c, f->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
-    SDF_TRY(cudaMemcpyAsync(&total_pairs, start + n_bins, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    SDF_TRY(cudaMemcpyAsync(&c, pl.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    SDF_TRY(cudaMemcpyAsync(&total_pairs, plan_scratch(pl).start + 3 * pl.n_tiles, sizeof(uint32_t),
+                            cudaMemcpyDeviceToHost, s));
     SDF_TRY(cudaStreamSynchronize(s));
     *retry = false;
-    if (c.status & ST_DEGENERATE) return SDF_ERR_DEGENERATE;  // from sdf_features_update_positions
+    for (int p = 0; p < pl.n; p++) {
+        if (feats[p]->ctr != pl.ctr) {  // degenerate positions flagged in the handle's own word
+            unsigned st = 0;
+            SDF_TRY(cudaMemcpy(&st, &feats[p]->ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+            if (st & ST_DEGENERATE) return SDF_ERR_DEGENERATE;
+        }
+    }
+    if (c.status & ST_DEGENERATE) return SDF_ERR_DEGENERATE;
     if (c.nb_status & ST_PAIR_OVERFLOW) {
-        f->pair_cap = (int64_t)total_pairs + total_pairs / 4 + 4096;
+        pl.pair_cap = (int64_t)total_pairs + total_pairs / 4 + 4096;
         *retry = true;
     }
     if (c.nb_status & ST_PATCH_OVERFLOW) {
-        f->patch_cap = (int64_t)c.n_patch + c.n_patch / 2 + 4096;
+        pl.patch_cap = (int64_t)c.n_patch + c.n_patch / 2 + 4096;
         *retry = true;
     }
     return SDF_OK;
+}
+
+// describe (already done), reserve, launch and, when synchronising, retry with grown scratch
+static int plan_execute(Plan &pl, const sdf_features *feats, cudaStream_t s, bool sync, bool timing) {
+    for (int attempt = 0; attempt < 4; attempt++) {
+        SDF_TRY_ST(plan_reserve(pl, s));
+        SDF_TRY_ST(plan_launch(pl, s, timing));
+        if (!sync) return SDF_OK;
+        bool retry = false;
+        SDF_TRY_ST(plan_check(pl, feats, s, &retry));
+        if (!retry) return SDF_OK;
+    }
+    return SDF_ERR_OOM;
 }
 
 // stats of the last call (host), used by sdf_features_status
@@ -1071,24 +1243,48 @@ int narrow_band_stats(sdf_features_s *f, int64_t *stats, cudaStream_t s) {
     return SDF_OK;
 }
 
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, long long, long long>, int> g_tuned;  // (n, features, grid points) -> shape
+
+static std::tuple<int, long long, long long> tune_key(const sdf_features *feats, const sdf_grid *grids, int n) {
+    long long nf = 0, np = 0;
+    for (int p = 0; p < n; p++) {
+        nf += feats[p]->T + feats[p]->E + feats[p]->V;
+        np += (long long)grids[p].nx * grids[p].ny * grids[p].nz;
+    }
+    return std::make_tuple(n, nf, np);
+}
+
 int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const float *band_w, int32_t n,
                     float *const *out_dist, int32_t *const *out_winner, uint32_t flags, cudaStream_t s) {
     if (!feats || !grids || !band_w || n < 1 || !out_dist) return SDF_ERR_INVALID_ARG;
     for (int p = 0; p < n; p++)
         if (!feats[p] || !out_dist[p]) return SDF_ERR_INVALID_ARG;
     const bool sync = !(flags & SDF_FLAG_NO_SYNC), timing = (flags & SDF_FLAG_TIMING) != 0;
-    for (int p = 0; p < n; p++) {
-        int32_t *win = out_winner ? out_winner[p] : nullptr;
-        bool retry = false;
-        int st = narrow_band_one(feats[p], grids[p], band_w[p], out_dist[p], win, s, sync, timing, &retry);
-        if (st) return st;
-        for (int attempt = 0; retry && attempt < 3; attempt++) {
-            st = narrow_band_one(feats[p], grids[p], band_w[p], out_dist[p], win, s, sync, timing, &retry);
-            if (st) return st;
+    if (n == 1) {  // a batch of one, with the plan (and its scratch) cached in the handle
+        sdf_features_s *f = feats[0];
+        if (!f->plan) {
+            f->plan = new Plan();
+            f->plan->ctr = f->ctr;
+            f->plan->events = f;
         }
-        if (retry) return SDF_ERR_OOM;
+        Plan &pl = *f->plan;
+        SDF_TRY_ST(plan_describe(pl, feats, grids, band_w, 1, out_dist, out_winner, 0));
+        return plan_execute(pl, feats, s, sync, timing);
     }
-    return SDF_OK;
+    int shape = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(tune_key(feats, grids, n));
+        if (it != g_tuned.end()) shape = it->second;
+    }
+    Plan pl;
+    pl.pageable = true;
+    int st = plan_describe(pl, feats, grids, band_w, n, out_dist, out_winner, shape);
+    if (!st) st = plan_execute(pl, feats, s, true, false);
+    // the temporary plan's memory returns to the pool in stream order
+    plan_free(new Plan(std::move(pl)), s);
+    return st;
 }
 
 }  // namespace sdf
@@ -1097,6 +1293,123 @@ extern "C" int sdf_narrow_band(const sdf_features *feats, const sdf_grid *grids,
                                float *const *out_dist, int32_t *const *out_winner, uint32_t flags, void *stream) {
     return sdf::narrow_band_all(feats, grids, band_w, n, out_dist, out_winner, flags,
                                 reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ----------------------------------------------------------------------------- batches for CUDA graphs
+struct sdf_batch_s {
+    sdf::Plan plan;
+    std::vector<sdf_features> feats;
+};
+
+extern "C" int sdf_batch_create(const sdf_features *feats, const sdf_grid *grids, const float *band_w, int32_t n,
+                                float *const *out_dist, int32_t *const *out_winner, uint32_t flags, void *stream,
+                                sdf_batch *out) {
+    using namespace sdf;
+    if (!out) return SDF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!feats || !grids || !band_w || n < 1 || !out_dist) return SDF_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    sdf_batch_s *b = new sdf_batch_s();
+    b->feats.assign(feats, feats + n);
+    int best = 0;
+    double best_ms = 0.0;
+    const int n_try = (flags & SDF_FLAG_AUTOTUNE) ? N_SHAPES : 1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int st = SDF_OK;
+    if (n_try > 1 && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = SDF_ERR_CUDA;
+    for (int shape = 0; shape < n_try && !st; shape++) {
+        st = plan_describe(b->plan, feats, grids, band_w, n, out_dist, out_winner, shape);
+        if (!st) st = plan_execute(b->plan, b->feats.data(), s, true, false);  // sizes the scratch
+        if (st || n_try == 1) break;
+        const int reps = 3;
+        if (cudaEventRecord(e0, s) != cudaSuccess) { st = SDF_ERR_CUDA; break; }
+        for (int r = 0; r < reps && !st; r++) st = plan_launch(b->plan, s, false);
+        float ms = 0.f;
+        if (!st && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            st = SDF_ERR_CUDA;
+        if (!st && (shape == 0 || ms / reps < best_ms)) {
+            best = shape;
+            best_ms = ms / reps;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (!st && (flags & SDF_FLAG_TIMING)) {
+        for (int i = 0; i < 4 && !st; i++)
+            if (cudaEventCreate(&b->plan.bev[i]) != cudaSuccess) st = SDF_ERR_CUDA;
+        b->plan.batch_timing = !st;
+    }
+    if (!st && n_try > 1) {  // rebuild the plan for the fastest shape and leave its outputs filled
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned[tune_key(feats, grids, n)] = best;
+        }
+        b->plan.pair_cap = 0;
+        b->plan.patch_cap = 0;
+        st = plan_describe(b->plan, feats, grids, band_w, n, out_dist, out_winner, best);
+        if (!st) st = plan_execute(b->plan, b->feats.data(), s, true, false);
+        b->plan.tuned_ms = best_ms;
+    }
+    if (st) {
+        plan_free(new Plan(std::move(b->plan)), s);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return SDF_OK;
+}
+
+extern "C" int sdf_batch_run(sdf_batch b, void *stream) {
+    if (!b) return SDF_ERR_INVALID_ARG;
+    return sdf::plan_launch(b->plan, reinterpret_cast<cudaStream_t>(stream), false);
+}
+
+extern "C" int sdf_batch_status(sdf_batch b, int64_t *stats, void *stream) {
+    using namespace sdf;
+    if (!b) return SDF_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DevCounters c;
+    SDF_TRY(cudaMemcpyAsync(&c, b->plan.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    SDF_TRY(cudaStreamSynchronize(s));
+    if (stats) {
+        stats[0] = (int64_t)c.n_candidates;
+        stats[1] = (int64_t)c.n_band;
+        stats[2] = (int64_t)c.n_patch;
+        stats[3] = (int64_t)c.n_pairs;
+        stats[4] = (int64_t)c.n_rows;
+        stats[5] = (int64_t)c.n_rows_hit;
+    }
+    if (c.nb_status & (ST_PAIR_OVERFLOW | ST_PATCH_OVERFLOW)) return SDF_ERR_OOM;
+    return SDF_OK;
+}
+
+extern "C" int sdf_batch_timing(sdf_batch b, float *ms) {
+    if (!b || !ms) return SDF_ERR_INVALID_ARG;
+    if (!b->plan.batch_timing) return SDF_ERR_INVALID_ARG;
+    for (int i = 0; i < 3; i++) {
+        SDF_TRY(cudaEventSynchronize(b->plan.bev[i + 1]));
+        SDF_TRY(cudaEventElapsedTime(&ms[i], b->plan.bev[i], b->plan.bev[i + 1]));
+    }
+    return SDF_OK;
+}
+
+extern "C" int sdf_batch_info(sdf_batch b, int32_t *tile_shape, double *tuned_ms) {
+    if (!b) return SDF_ERR_INVALID_ARG;
+    if (tile_shape) {
+        tile_shape[0] = sdf::TILE_X;
+        tile_shape[1] = sdf::SHAPE_TY[b->plan.shape];
+        tile_shape[2] = sdf::SHAPE_TZ[b->plan.shape];
+    }
+    if (tuned_ms) *tuned_ms = b->plan.tuned_ms;
+    return SDF_OK;
+}
+
+extern "C" void sdf_batch_destroy(sdf_batch b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    sdf::plan_free(new sdf::Plan(std::move(b->plan)), 0);
+    delete b;
 }
 
 extern "C" int sdf_features_status(sdf_features f, int64_t *stats, void *stream) {
@@ -1132,12 +1445,15 @@ extern "C" int sdf_features_timing(sdf_features f, double *ms, int64_t *calls, i
 // array.  Every device that loads the library holds it until the process exits.
 namespace sdf {
 namespace {
+static_assert(sizeof(Prob) + 16 * 4 <= 2048, "problem table slot");
 constexpr int64_t ST_MAX_TILES = 65536;                 // 32x8x8-point tiles (512^3 points)
 constexpr int64_t ST_MAX_PAIRS = int64_t(4) << 20;      // (tile, region) pairs
 constexpr int64_t ST_MAX_PATCH = 131072;                // points re-decided in FP64
 constexpr size_t ST_OFF_CTR = 0;                        // DevCounters
 constexpr size_t ST_OFF_TICKET = 1024;                  // work ticket (8 bytes)
-constexpr size_t ST_OFF_CNT = 2048;                     // uint32 [3 * max tiles]
+constexpr size_t ST_OFF_TABLE = 2048;                   // one Prob, then long long [4] prefix sums
+constexpr size_t ST_PROB_BYTES = (sizeof(Prob) + 15) / 16 * 16;
+constexpr size_t ST_OFF_CNT = ST_OFF_TABLE + 2048;      // uint32 [3 * max tiles]
 constexpr size_t ST_OFF_START = ST_OFF_CNT + 4 * (3 * ST_MAX_TILES + 256);      // uint32 [3 * max tiles + 1]
 constexpr size_t ST_OFF_BANDPOS = ST_OFF_START + 4 * (3 * ST_MAX_TILES + 256);  // uint32 [max tiles + 1]
 constexpr size_t ST_OFF_BANDLIST = ST_OFF_BANDPOS + 4 * (ST_MAX_TILES + 256);   // int32 [max tiles]
@@ -1146,7 +1462,7 @@ constexpr size_t ST_OFF_SCAN = ST_OFF_EMPTYLIST + 4 * (ST_MAX_TILES + 256);     
 constexpr size_t ST_SCAN_BYTES = 65536;
 constexpr size_t ST_OFF_PAIRS = ST_OFF_SCAN + ST_SCAN_BYTES;                     // int32 [max pairs]
 constexpr size_t ST_OFF_PATCH = ST_OFF_PAIRS + 4 * ST_MAX_PAIRS;                 // PatchEntry [max patch]
-constexpr size_t ST_BYTES = ST_OFF_PATCH + sizeof(PatchEntry) * ST_MAX_PATCH;    // about 20.6 MiB
+constexpr size_t ST_BYTES = ST_OFF_PATCH + sizeof(PatchEntry) * ST_MAX_PATCH;    // about 20.3 MiB
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_static_scratch[ST_BYTES];
@@ -1177,7 +1493,7 @@ extern "C" int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, floa
     using namespace sdf;
     if (!f || !grid || !out_dist) return SDF_ERR_INVALID_ARG;
     GridP g;
-    int st = make_grid(*grid, band_w, g);
+    int st = make_grid(*grid, band_w, 0, g);
     if (st) return st;
     const int64_t n_tiles = (int64_t)g.ntx * g.nty * g.ntz, n_bins = 3 * n_tiles;
     if (n_tiles > ST_MAX_TILES) return SDF_ERR_TOO_LARGE;  // grid beyond the static scratch
@@ -1187,54 +1503,38 @@ extern "C" int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, floa
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Feat F = make_feat(f);
     const int64_t n_feat = f->T + f->E + f->V;
-    DevCounters *ctr = reinterpret_cast<DevCounters *>(base + ST_OFF_CTR);
-    unsigned long long *ticket = reinterpret_cast<unsigned long long *>(base + ST_OFF_TICKET);
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(base + ST_OFF_CNT);
-    uint32_t *start = reinterpret_cast<uint32_t *>(base + ST_OFF_START);
-    uint32_t *band_pos = reinterpret_cast<uint32_t *>(base + ST_OFF_BANDPOS);
-    int32_t *band_list = reinterpret_cast<int32_t *>(base + ST_OFF_BANDLIST);
-    int32_t *empty_list = reinterpret_cast<int32_t *>(base + ST_OFF_EMPTYLIST);
-    void *scan_tmp = base + ST_OFF_SCAN;
-    int32_t *pairs = reinterpret_cast<int32_t *>(base + ST_OFF_PAIRS);
-    PatchEntry *patch = reinterpret_cast<PatchEntry *>(base + ST_OFF_PATCH);
-    // the array keeps the previous call's contents: clear the counters, bins and ticket
-    SDF_TRY(cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s));
-    SDF_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
-    SDF_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n_bins, s));
-    k_bin<false><<<nblk(n_feat, 256), 256, 0, s>>>(F, g, cnt, nullptr, nullptr, 0, ctr);
-    SDF_LAUNCHED(1);
-    SDF_TRY(cudaGetLastError());
-    SDF_TRY(scan_exclusive_u32(cnt, start, n_bins, true, scan_tmp, s));
-    SDF_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n_bins, s));
-    k_bin<true><<<nblk(n_feat, 256), 256, 0, s>>>(F, g, cnt, start, pairs, ST_MAX_PAIRS, ctr);
-    SDF_LAUNCHED(1);
-    SDF_TRY(cudaGetLastError());
-    k_band_flags<<<nblk(n_tiles, 256), 256, 0, s>>>(start, n_tiles, cnt);
-    SDF_LAUNCHED(1);
-    SDF_TRY(cudaGetLastError());
-    SDF_TRY(scan_exclusive_u32(cnt, band_pos, n_tiles, true, scan_tmp, s));
-    k_tile_lists<<<nblk(n_tiles, 256), 256, 0, s>>>(start, n_tiles, band_pos, band_list, empty_list);
-    SDF_LAUNCHED(1);
-    SDF_TRY(cudaGetLastError());
-    Outputs o;
-    o.dist = out_dist;
-    o.winner = out_winner;
-    o.pairs = pairs;
-    o.bin_start = start;
-    o.pair_cap = ST_MAX_PAIRS;
-    o.patch = patch;
-    o.patch_cap = ST_MAX_PATCH;
-    o.ctr = ctr;
-    const int vec = ((g.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(out_dist) & 15) == 0) &&
-                    ((reinterpret_cast<uintptr_t>(out_winner) & 15) == 0);
-    const int64_t tile_ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm() * num_sms());
-    k_tile<<<(unsigned)tile_ctas, NT, sizeof(TileSmem), s>>>(F, g, o, n_tiles, band_list, empty_list, band_pos + n_tiles, ticket,
-                                              vec);
-    SDF_LAUNCHED(1);
-    SDF_TRY(cudaGetLastError());
-    k_patch<<<4 * 152, 256, 0, s>>>(F, g, o);
-    SDF_LAUNCHED(1);
-    SDF_TRY(cudaGetLastError());
+    // the one-problem table: Prob, feature prefix sums {0, n_feat}, tile prefix sums {0, n_tiles}
+    Prob pr;
+    pr.F = make_feat(f);
+    pr.g = g;
+    pr.dist = out_dist;
+    pr.winner = out_winner;
+    pr.vec = ((g.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(out_dist) & 15) == 0) &&
+             ((reinterpret_cast<uintptr_t>(out_winner) & 15) == 0);
+    const long long bases[4] = {0, n_feat, 0, n_tiles};
+    Scratch sc;
+    sc.probs = reinterpret_cast<const Prob *>(base + ST_OFF_TABLE);
+    sc.fbase = reinterpret_cast<const long long *>(base + ST_OFF_TABLE + ST_PROB_BYTES);
+    sc.tbase = sc.fbase + 2;
+    sc.ctr = reinterpret_cast<DevCounters *>(base + ST_OFF_CTR);
+    sc.ticket = reinterpret_cast<unsigned long long *>(base + ST_OFF_TICKET);
+    sc.cnt = reinterpret_cast<uint32_t *>(base + ST_OFF_CNT);
+    sc.start = reinterpret_cast<uint32_t *>(base + ST_OFF_START);
+    sc.band_pos = reinterpret_cast<uint32_t *>(base + ST_OFF_BANDPOS);
+    sc.band_list = reinterpret_cast<int32_t *>(base + ST_OFF_BANDLIST);
+    sc.empty_list = reinterpret_cast<int32_t *>(base + ST_OFF_EMPTYLIST);
+    sc.scan_tmp = base + ST_OFF_SCAN;
+    sc.pairs = reinterpret_cast<int32_t *>(base + ST_OFF_PAIRS);
+    sc.pair_cap = ST_MAX_PAIRS;
+    sc.patch = reinterpret_cast<PatchEntry *>(base + ST_OFF_PATCH);
+    sc.patch_cap = ST_MAX_PATCH;
+    // host-to-device copies of a few hundred bytes (staged by the driver, no device allocation)
+    SDF_TRY(cudaMemcpyAsync(base + ST_OFF_TABLE, &pr, sizeof(Prob), cudaMemcpyHostToDevice, s));
+    SDF_TRY(cudaMemcpyAsync(base + ST_OFF_TABLE + ST_PROB_BYTES, bases, sizeof(bases), cudaMemcpyHostToDevice, s));
+    // the array keeps the previous call's contents: clear the counters (the pipeline clears the rest)
+    SDF_TRY(cudaMemsetAsync(sc.ctr, 0, sizeof(DevCounters), s));
+    SDF_TRY_ST((launch_shape<8, 8>(1, n_feat, n_tiles, sc, s, nullptr)));
+    DevCounters *ctr = sc.ctr;
     // read the status word: a pair or re-decision list beyond the static limits is an error
     unsigned status = 0;
     SDF_TRY(cudaMemcpyAsync(&status, &ctr->nb_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));

@@ -536,12 +536,9 @@ static void free_handle(sdf_features_s *f) {
                     f->face_box, f->edge_rec, f->vert_rec, f->vert_plane, f->edge_class, f->vert_class, f->ctr};
     for (void *p : ptrs)
         if (p) pool_free(p, s0);
-    f->bins.release(s0);
-    f->pairs.release(s0);
-    f->patch.release(s0);
-    f->scan_tmp.release(s0);
+    sdf::plan_free(f->plan, s0);
+    f->plan = nullptr;
     f->fwd_winner.release(s0);
-    f->lists.release(s0);
     for (cudaEvent_t e : f->ev)
         if (e) cudaEventDestroy(e);
     delete f;

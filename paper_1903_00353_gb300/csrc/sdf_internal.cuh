@@ -66,6 +66,9 @@ struct DevCounters {
     unsigned long long cls[8];         // classification counts
 };
 
+struct Plan;
+void plan_free(Plan *pl, cudaStream_t s);
+
 }  // namespace sdf
 
 // ----------------------------------------------------------------------------- the handle
@@ -92,9 +95,9 @@ struct sdf_features_s {
     int8_t *vert_class = nullptr;   // [V]
     int64_t counts[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     sdf::DevCounters *ctr = nullptr; // device counters
-    // narrow-band scratch, grown on demand
-    sdf::DevBuf bins, pairs, patch, scan_tmp, fwd_winner, lists;
-    int64_t pair_cap = 0, patch_cap = 0;
+    // narrow-band scratch of single-problem calls (problem table, bins, pairs), grown on demand
+    sdf::Plan *plan = nullptr;
+    sdf::DevBuf fwd_winner;  // winners recomputed by a backward call that was given none
     // stage timing (SDF_FLAG_TIMING)
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     double t_ms[4] = {0, 0, 0, 0};
@@ -162,5 +165,11 @@ __device__ __forceinline__ float3 load_vpos(const float *vpos, int v) {
 #define SDF_TRY(expr)                                  \
     do {                                               \
         cudaError_t e_ = (expr);                       \
-        if (e_ != cudaSuccess) return SDF_ERR_CUDA;    \
+        if (e_ != cudaSuccess) return e_ == cudaErrorMemoryAllocation ? SDF_ERR_OOM : SDF_ERR_CUDA; \
+    } while (0)
+// propagate a library status code
+#define SDF_TRY_ST(expr)                               \
+    do {                                               \
+        int st_ = (expr);                              \
+        if (st_ != SDF_OK) return st_;                 \
     } while (0)

@@ -47,6 +47,14 @@ def test_argument_validation_without_device(lib):
     assert lib.sdf_narrow_band(None, None, None, 1, None, None, 0, None) == 1
     assert lib.sdf_features_info(None, None, None) == 1
     lib.sdf_features_destroy(None)
+    batch = ctypes.c_void_p(1234)
+    assert lib.sdf_batch_create(None, None, None, 1, None, None, 0, None, ctypes.byref(batch)) == 1
+    assert batch.value is None
+    assert lib.sdf_batch_run(None, None) == 1
+    assert lib.sdf_batch_status(None, None, None) == 1
+    assert lib.sdf_batch_info(None, None, None) == 1
+    assert lib.sdf_batch_timing(None, None) == 1
+    lib.sdf_batch_destroy(None)
 
 
 def test_product_package_does_not_import_oracle():

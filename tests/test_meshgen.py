@@ -88,3 +88,20 @@ def test_batch_meshes_sizes():
     for mesh, N in batch:
         _check_closed_oriented(mesh)
         assert 64 <= N <= 384 and N % 32 == 0
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_box_cluster_components(k):
+    m = meshgen.box_cluster(k, 2000, seed=353_300 + k)
+    E = _check_closed_oriented(m)
+    # k disjoint spheres: Euler characteristic 2 per component
+    assert m.vertices.shape[0] - E + m.triangles.shape[0] == 2 * k
+    assert m.vertices.min() > 0.0 and m.vertices.max() < 1.0
+
+
+def test_random_rotation_is_proper():
+    rng = np.random.Generator(np.random.PCG64(5))
+    for _ in range(10):
+        R = meshgen.random_rotation(rng)
+        assert np.allclose(R @ R.T, np.eye(3), atol=1e-12)
+        assert abs(np.linalg.det(R) - 1.0) < 1e-12
