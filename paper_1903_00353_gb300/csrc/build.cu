@@ -1,20 +1,20 @@
 // Mesh-connectivity stage and feature records (Sections 7 and 8 of the paper).
 //
 //   soup --(bounds, weld keys)--> radix sort --> vertex runs --> welded vertices + CSR of corners
-//        --(edge keys)--> radix sort --> paired half-edges --> unique edges (va, vb, f1, f2)
+//        --(smallest vertex id)--> spatial face order --> edge twins found in the vertex fans
 //        --> face / edge / vertex records (normals, side planes, pseudonormals, classes)
 //
 // Welding (Section 7.2).  The paper sorts 30-bit Morton codes and then groups identical
-// vertices serially inside each equal-code run.  Here the sort key is the 30-bit Morton
-// code of the quantised position (over the soup's bounding box, Section 7.1) in the high
-// bits and a 34-bit hash of the exact coordinate bits in the low bits, so equal vertices
-// always share a key and distinct vertices almost never do.  Runs of equal keys holding
-// different coordinates (hash collisions) are re-ordered by exact coordinates by one
+// vertices serially inside each equal-code run.  Here the sort key is 48 bits: the 30-bit Morton
+// code of the quantised position (over the soup's bounding box, Section 7.1) in the high bits and
+// an 18-bit hash of the exact coordinate bits in the low bits, so equal vertices always share a
+// key and distinct vertices rarely do.  Runs of equal keys holding different coordinates (hash
+// collisions, or distinct vertices in one Morton cell) are re-ordered by exact coordinates by one
 // thread per such run, the only serial step left of the paper's fix-up.
 //
-// Edge pairing (Section 7.1): each directed triangle edge gets the key
-// (min vid, max vid); after sorting, each key must occur exactly twice with opposite
-// directions, else the surface is not a closed oriented 2-manifold.
+// Edge pairing (Section 7.1): the twin of the directed edge a->b is the corner of b whose next
+// vertex is a, found in b's fan of the vertex CSR; a->b must occur once around a and b->a once
+// around b, else the surface is not a closed oriented 2-manifold.  No second sort is needed.
 #include <stdio.h>
 #include <stdlib.h>
 
