@@ -216,7 +216,7 @@ int64_t sdf_kernel_launches(void);
  *
  * Its scratch is one library-owned device array of about 20.3 MiB that every device holding
  * this library keeps until the process exits.  Limits: at most 65536 tiles of 32x8x8 points
- * (e.g. a 512^3 grid), 4194304 (tile, region) pairs and 131072 points re-decided in FP64;
+ * (e.g. a 512^3 grid), 2097152 (tile, region) pairs and 131072 points re-decided in FP64;
  * beyond them the call returns SDF_ERR_TOO_LARGE (the grid limit before any work, the list
  * limits after it, with the outputs unspecified).
  *

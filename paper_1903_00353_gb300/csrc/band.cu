@@ -32,6 +32,7 @@
 //      membership or sign lies inside the FP32 error window.  Empty tiles are written +inf;
 //   3. patch kernel: re-decides the queued points in FP64 from the winner's neighbourhood.
 #include <math.h>
+#include <stddef.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -98,7 +99,7 @@ __device__ __forceinline__ int find_prob(const long long *base, int n, long long
 }
 
 struct Outputs {
-    const int32_t *pairs;
+    const int2 *pairs;
     const uint32_t *bin_start;
     int64_t pair_cap;
     PatchEntry *patch;
@@ -188,9 +189,21 @@ __device__ __forceinline__ bool feature_box(const Feat &F, const GridP &g, int i
 }
 
 // ----------------------------------------------------------------------------- binning
+// The region's integer box clipped to tile (tx, ty, tz), in tile-local indices, packed in 26 bits:
+// x lo, hi (5 bits each), y lo, hi, z lo, hi (4 bits each; TY, TZ <= 16).
+template <int TY, int TZ>
+__device__ __forceinline__ int pack_box(int i0, int i1, int j0, int j1, int k0, int k1, int tx, int ty, int tz) {
+    static_assert(TY <= 16 && TZ <= 16, "tile-local box packing");
+    const int x0 = tx * TILE_X, y0 = ty * TY, z0 = tz * TZ;
+    const int a0 = max(i0 - x0, 0), a1 = min(i1 - x0, TILE_X - 1);
+    const int b0 = max(j0 - y0, 0), b1 = min(j1 - y0, TY - 1);
+    const int c0 = max(k0 - z0, 0), c1 = min(k1 - z0, TZ - 1);
+    return a0 | (a1 << 5) | (b0 << 10) | (b1 << 14) | (c0 << 18) | (c1 << 22);
+}
+
 template <bool FILL, int TY, int TZ>
 __global__ void k_bin(const Prob *P, const long long *feat_base, const long long *tile_base, int n, long long f_tot,
-                      uint32_t *cnt, const uint32_t *start, int32_t *pairs, int64_t pair_cap, DevCounters *ctr) {
+                      uint32_t *cnt, const uint32_t *start, int2 *pairs, int64_t pair_cap, DevCounters *ctr) {
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (gid >= f_tot) return;
     const int p = find_prob(feat_base, n, gid);
@@ -215,7 +228,7 @@ __global__ void k_bin(const Prob *P, const long long *feat_base, const long long
                     atomicAdd(cnt + bin, 1u);
                 } else {
                     const int64_t pos = (int64_t)start[bin] + atomicAdd(cnt + bin, 1u);
-                    if (pos < pair_cap) pairs[pos] = fid;
+                    if (pos < pair_cap) pairs[pos] = make_int2(fid, pack_box<TY, TZ>(i0, i1, j0, j1, k0, k1, tx, ty, tz));
                     else atomicOr(&ctr->nb_status, ST_PAIR_OVERFLOW);
                 }
             }
@@ -296,11 +309,6 @@ __device__ __forceinline__ int feat_type(const Feat &F, int fid) { return fid < 
 __device__ __forceinline__ int feat_local(const Feat &F, int fid, int type) {
     return type == FACE ? fid : (type == EDGE ? fid - F.T : fid - F.T - F.E);
 }
-__device__ __forceinline__ bool box_any(const Feat &F, const GridP &g, int type, int id, int *lo, int *hi) {
-    if (type == FACE) return feature_box<FACE>(F, g, id, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
-    if (type == EDGE) return feature_box<EDGE>(F, g, id, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
-    return feature_box<VERT>(F, g, id, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
-}
 __device__ __forceinline__ float eval_any(const Feat &F, const GridP &g, int type, int id, int i, int j, int k,
                                           bool &neg) {
     if (type == FACE) return eval_point<FACE>(F, g, id, i, j, k, neg);
@@ -311,69 +319,128 @@ __device__ __forceinline__ float eval_any(const Feat &F, const GridP &g, int typ
 // ----------------------------------------------------------------------------- per-tile row coefficients
 // For a region and its scan axis a (other axes b < c), every half-space m.p + w >= -eps becomes,
 // on the row with relative indices (ib, ic), a bound on the relative index j along a that is
-// linear in (ib, ic):  j >= A + B ib + C ic (lower, m_a > 0), j <= ... (upper, m_a < 0), or, when
-// m_a = 0, a gate A + B ib + C ic >= 0 that empties the row.  The vertex ball adds
+// linear in (ib, ic):  j >= A + B ib + C ic (lower, m_a > 0) or j <= A + B ib + C ic (upper,
+// m_a < 0).  When m_a = 0 the half-space is a gate G = A + B ib + C ic >= 0 that opens or empties
+// the whole row; it is stored as the lower bound j >= -2^100 G, which is <= 0 (no restriction) for
+// G >= 0 and beyond the tile for every G < -2^-95.  Scaling by a power of two is exact, so the
+// sign of G is kept; a negative G of smaller magnitude (a row on the plane, inside the inclusion
+// tolerance) may leave part of the row open, which only adds candidates.  The vertex ball adds
 // |j - j_v| <= sqrt(R^2 - (db0 + ib)^2 - (dc0 + ic)^2) in index units.  The coefficients are
-// computed once per (region, tile) and kept in shared memory, so a row costs a few FMAs per plane.
-// Vertex regions keep at most MAXVP of their planes: dropping planes only enlarges the region,
-// and a point outside the exact vertex region has a strictly closer point on an incident edge.
-constexpr int KMAX = 7, MAXVP = 6, ROW_TABLE = 4096;
-enum { K_LOWER = 0, K_UPPER = 1, K_GATE = 2 };
+// computed once per (region, tile) and kept in shared memory, lower bounds from the front and
+// upper bounds from the back of the region's slots, so a row costs one FMA pair and a min or max
+// per plane (unused slots hold the neutral upper bound +1e30, so every row runs all KMAX slots
+// without branching).  Vertex regions keep at most MAXVP of their planes: dropping planes only enlarges the
+// region, and a point outside the exact vertex region has a strictly closer point on an incident
+// edge.  Faces have 5 planes, edges 4.
+constexpr int KMAX = 6, MAXVP = 6;
 
 template <int TY, int TZ>
 struct TileSmem {
     unsigned long long key[TILE_X * TY * TZ];  // packed (|d| bits << 32 | id << 1 | sign) per tile point
-    float4 coef[NT][KMAX];             // span coefficients (A, B, C, kind) per region of the pass
+    float4 coef[NT][KMAX];             // span coefficients (A, B, C, -): nl lower bounds, then upper bounds
     float4 ball[NT];                   // vertex ball in index units (j_v, db0, dc0, R^2), R^2 < 0: none
+    uint4 rinfo[NT];                   // row set-up of each region, packed (see process_band_tile)
     int fid[NT];                       // regions of the current pass (global feature ids)
-    int row0[NT + 1];                  // exclusive prefix of their row counts
-    int lo_a[NT], lo_b[NT], lo_c[NT];
-    unsigned char ax[NT], nb[NT], span_hi[NT], ncoef[NT];
-    unsigned char owner[ROW_TABLE];    // region (pass slot) of each row, for rows < ROW_TABLE
-    int wtot[NT / 32];
+    unsigned char ax[NT];              // scan axis
+    unsigned rowq[NT / 32][64];        // per-warp ring of non-empty rows waiting for point evaluation
+    int chunk_next;                    // next 32-region chunk of the tile to hand to a warp
     long long work;
 };
 
-__device__ __forceinline__ void add_coef(float4 *E, int &ne, float4 P, int ax, int bx, int cx, float pb0, float pc0,
-                                         float K, const GridP &g) {
+
+
+__device__ __forceinline__ void add_coef(float4 *E, int &nl, int &nu, float4 P, int ax, int bx, int cx, float pb0,
+                                         float pc0, float K, const GridP &g) {
     const float ma = comp(P, ax), mb = comp(P, bx), mc = comp(P, cx);
     const float r0 = fmaf(mb, pb0, fmaf(mc, pc0, P.w)) + g.eps;
-    if (ma != 0.f) {
+    if (ma > 0.f) {
         const float inv = 1.f / ma;
-        E[ne++] = make_float4(fmaf(-r0 * inv, g.inv_h, -K), -mb * inv, -mc * inv, ma > 0.f ? K_LOWER : K_UPPER);
+        E[nl++] = make_float4(fmaf(-r0 * inv, g.inv_h, -K), -mb * inv, -mc * inv, 0.f);
+    } else if (ma < 0.f) {
+        const float inv = 1.f / ma;
+        E[KMAX - 1 - nu++] = make_float4(fmaf(-r0 * inv, g.inv_h, -K), -mb * inv, -mc * inv, 0.f);
     } else {
-        E[ne++] = make_float4(r0, mb * g.h, mc * g.h, K_GATE);
+        const float s = -0x1p100f;
+        E[nl++] = make_float4(s * r0, s * (mb * g.h), s * (mc * g.h), 0.f);
     }
 }
 
-// All regions of one band tile, with the rows of every region shared by all 8 warps of the CTA:
-// (1) one thread per region computes its box clipped to the tile, its scan axis (the longest
-// side), its row count and its span coefficients; (2) a block scan numbers the rows; (3) each
-// lane takes one row and evaluates the span from the coefficients (Algorithm 2 on a grid line);
-// (4) the span points of a warp are flattened over its lanes and merged into the tile's keys with
-// a shared-memory atomicMin (Algorithm 1).
+// Points of n (<= 32) queued rows, starting at ring slot q0, flattened over the lanes of the warp:
+// distance to the row's feature, and the merge into the tile's keys (Algorithm 1).
 template <int TY, int TZ>
-__device__ void process_band_tile(const Feat &F, const GridP &g, const int32_t *pairs, int64_t q0, int64_t q3,
-                                  int x0, int y0, int z0, int cx1, int cy1, int cz1, TileSmem<TY, TZ> &S,
-                                  unsigned &cand, unsigned &rows, unsigned &hits) {
+__device__ __forceinline__ void eval_rows(const Feat &F, const GridP &g, TileSmem<TY, TZ> &S, const unsigned *Q,
+                                          int q0, int n, int x0, int y0, int z0, unsigned &cand) {
+    const int lane = threadIdx.x & 31;
+    const unsigned e = lane < n ? Q[(q0 + lane) & 63] : 0u;
+    const int len = (int)((e >> 13) & 63u);
+    const int pincl = warp_incl_scan(len);
+    const int ptotal = __shfl_sync(FULL, pincl, 31);
+    for (int p0 = 0; p0 < ptotal; p0 += 32) {
+        const int pp = p0 + lane;
+        const int ro = min(warp_owner(pincl, pp), 31);
+        const unsigned re = __shfl_sync(FULL, e, ro);
+        const int rfirst = __shfl_sync(FULL, pincl - len, ro);  // points before this row
+        if (pp < ptotal) {
+            const int slot = (int)(re & 255u);
+            const int la = (int)((re >> 8) & 31u) + (pp - rfirst), lb = (int)((re >> 19) & 31u), lc = (int)((re >> 24) & 31u);
+            const int ax = S.ax[slot];
+            const int lx = ax == 0 ? la : lb;
+            const int ly = ax == 1 ? la : (ax == 0 ? lb : lc);
+            const int lz = ax == 2 ? la : lc;
+            const int fid = S.fid[slot];
+            const int type = feat_type(F, fid), id = feat_local(F, fid, type);
+            bool neg;
+            const float d = eval_any(F, g, type, id, x0 + lx, y0 + ly, z0 + lz, neg);
+            if (d < g.W) {
+                const unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) |
+                                               ((unsigned long long)(unsigned)fid << 1) | (unsigned long long)neg;
+                atomicMin(S.key + (lz * TY + ly) * TILE_X + lx, key);
+                cand++;
+            }
+        }
+    }
+}
+
+// All regions of one band tile.  Warps take chunks of 32 regions from a shared counter and work on
+// them without block barriers: (1) one lane per region takes its box in the tile (packed in the
+// pair by the binning), its scan axis (the longest side), its row count and its span coefficients;
+// (2) a warp scan numbers the chunk's rows; (3) each lane takes one row, finds its region by a
+// shuffle search of the scan, and evaluates the span from the coefficients (Algorithm 2 on a grid
+// line); (4) non-empty rows wait in a per-warp queue until 32 are ready, then their points are
+// flattened over the lanes, evaluated and merged into the tile's keys with a shared-memory
+// atomicMin (Algorithm 1).
+template <int TY, int TZ>
+__device__ void process_band_tile(const Feat &F, const GridP &g, const int2 *pairs, int64_t q0, int64_t q3,
+                                  int x0, int y0, int z0, TileSmem<TY, TZ> &S, unsigned &cand, unsigned &rows,
+                                  unsigned &hits) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = threadIdx.x;
     const float3 org = make_float3(g.ox, g.oy, g.oz);
-    for (int64_t base = q0; base < q3; base += NT) {
-        const int64_t q = base + t;
+    // equal chunks of at most 32 regions, a multiple of the warp count of them, so that a tile with
+    // few regions still spreads its rows over every warp
+    const int64_t npairs = q3 - q0;
+    const int64_t nchunks = (NT / 32) * ((npairs + NT - 1) / NT);
+    const int cs = (int)((npairs + nchunks - 1) / max(nchunks, (int64_t)1));
+    for (;;) {
+        // this warp's next chunk of the tile's regions
+        int chunk = 0;
+        if (lane == 0) chunk = atomicAdd(&S.chunk_next, 1);
+        chunk = __shfl_sync(FULL, chunk, 0);
+        const int64_t base = q0 + (int64_t)cs * chunk;
+        if (base >= q3) break;
+        const int64_t q = base + lane;
+        const int64_t qend = min(base + cs, q3);
         int nrows = 0;
         {
             int fid = 0, lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1}, type = FACE, id = 0;
-            if (q < q3) {
-                fid = __ldg(pairs + q);
+            if (q < qend) {
+                const int2 pr = __ldg(pairs + q);
+                fid = pr.x;
                 type = feat_type(F, fid);
                 id = feat_local(F, fid, type);
-                if (box_any(F, g, type, id, lo, hi)) {
-                    lo[0] = max(lo[0], x0); hi[0] = min(hi[0], cx1);
-                    lo[1] = max(lo[1], y0); hi[1] = min(hi[1], cy1);
-                    lo[2] = max(lo[2], z0); hi[2] = min(hi[2], cz1);
-                } else {
-                    hi[0] = -1;
-                }
+                const unsigned bx = (unsigned)pr.y;
+                lo[0] = x0 + (int)(bx & 31u); hi[0] = x0 + (int)((bx >> 5) & 31u);
+                lo[1] = y0 + (int)((bx >> 10) & 15u); hi[1] = y0 + (int)((bx >> 14) & 15u);
+                lo[2] = z0 + (int)((bx >> 18) & 15u); hi[2] = z0 + (int)((bx >> 22) & 15u);
             }
             const int n0 = hi[0] - lo[0] + 1, n1 = hi[1] - lo[1] + 1, n2 = hi[2] - lo[2] + 1;
             const int ax = (n0 >= n1 && n0 >= n2) ? 0 : (n1 >= n2 ? 1 : 2);
@@ -386,12 +453,12 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int32_t *
             const int lc = cx == 1 ? lo[1] : lo[2];
             S.fid[t] = fid;
             S.ax[t] = (unsigned char)ax;
-            S.nb[t] = (unsigned char)max(nb, 1);
-            S.lo_a[t] = la;
-            S.lo_b[t] = lb;
-            S.lo_c[t] = lc;
-            S.span_hi[t] = (unsigned char)max(ha - la, 0);
-            int ne = 0;
+            // tile-local starts: a row's points are (a, b, c) = (lo_a + j, lo_b + ib, lo_c + ic)
+            const int loa = la - (ax == 0 ? x0 : (ax == 1 ? y0 : z0));
+            const int lob = lb - (bx == 0 ? x0 : y0);
+            const int loc = lc - (cx == 1 ? y0 : z0);
+            const int nbc = max(nb, 1);
+            int nl = 0, nu = 0;
             float4 ballv = make_float4(0.f, 0.f, 0.f, -1.f);
             if (nrows > 0) {
                 const float pb0 = fmaf((float)lb + 0.5f, g.h, comp3(org, bx));
@@ -401,83 +468,64 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int32_t *
                 if (type == FACE) {
                     const float4 *r = F.face_rec + 4 * id;
                     const float4 n = __ldg(r);
-                    add_coef(E, ne, make_float4(n.x, n.y, n.z, n.w + g.W), ax, bx, cx, pb0, pc0, K, g);
-                    add_coef(E, ne, make_float4(-n.x, -n.y, -n.z, g.W - n.w), ax, bx, cx, pb0, pc0, K, g);
-                    add_coef(E, ne, __ldg(r + 1), ax, bx, cx, pb0, pc0, K, g);
-                    add_coef(E, ne, __ldg(r + 2), ax, bx, cx, pb0, pc0, K, g);
-                    add_coef(E, ne, __ldg(r + 3), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, nl, nu, make_float4(n.x, n.y, n.z, n.w + g.W), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, nl, nu, make_float4(-n.x, -n.y, -n.z, g.W - n.w), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, nl, nu, __ldg(r + 1), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, nl, nu, __ldg(r + 2), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, nl, nu, __ldg(r + 3), ax, bx, cx, pb0, pc0, K, g);
                 } else if (type == EDGE) {
                     const float4 *r = F.edge_rec + 5 * id;
                     const float4 a = __ldg(r), tt = __ldg(r + 1);
-                    add_coef(E, ne, make_float4(tt.x, tt.y, tt.z, -tt.w), ax, bx, cx, pb0, pc0, K, g);
-                    add_coef(E, ne, make_float4(-tt.x, -tt.y, -tt.z, tt.w + a.w), ax, bx, cx, pb0, pc0, K, g);
-                    add_coef(E, ne, __ldg(r + 2), ax, bx, cx, pb0, pc0, K, g);
-                    add_coef(E, ne, __ldg(r + 3), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, nl, nu, make_float4(tt.x, tt.y, tt.z, -tt.w), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, nl, nu, make_float4(-tt.x, -tt.y, -tt.z, tt.w + a.w), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, nl, nu, __ldg(r + 2), ax, bx, cx, pb0, pc0, K, g);
+                    add_coef(E, nl, nu, __ldg(r + 3), ax, bx, cx, pb0, pc0, K, g);
                 } else {
                     const float4 v = __ldg(F.vert_rec + 3 * id), nv = __ldg(F.vert_rec + 3 * id + 1);
                     const int s0 = __float_as_int(v.w), cnt = min(__float_as_int(nv.w), MAXVP);
                     for (int k = 0; k < cnt; k++)
-                        add_coef(E, ne, __ldg(F.vert_plane + s0 + k), ax, bx, cx, pb0, pc0, K, g);
+                        add_coef(E, nl, nu, __ldg(F.vert_plane + s0 + k), ax, bx, cx, pb0, pc0, K, g);
                     const float3 vv = f3(v);
                     const float Rh = (g.W + g.eps) * g.inv_h;
                     ballv = make_float4((comp3(vv, ax) - comp3(org, ax)) * g.inv_h - 0.5f - (float)la,
                                         (pb0 - comp3(vv, bx)) * g.inv_h, (pc0 - comp3(vv, cx)) * g.inv_h, Rh * Rh);
                 }
             }
-            S.ncoef[t] = (unsigned char)ne;
+            for (int k = nl; k < KMAX - nu; k++) S.coef[t][k] = make_float4(1e30f, 0.f, 0.f, 0.f);
             S.ball[t] = ballv;
+            // rinfo: y = nb | nl << 8 | span_hi << 12 | lo_a << 17 | lo_b << 22 | lo_c << 27 (tile-local,
+            // 5 bits each), z = 1 / nb
+            S.rinfo[t] = make_uint4(0u, (unsigned)(nbc | (nl << 8) | (max(ha - la, 0) << 12) | (loa << 17) |
+                                                   (lob << 22) | (loc << 27)),
+                                    __float_as_uint(1.f / (float)nbc), 0u);
         }
-        // block exclusive scan of the row counts
+        // rows of the warp's regions, numbered by a warp scan
         const int incl = warp_incl_scan(nrows);
-        if (lane == 31) S.wtot[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            const int tv = lane < NT / 32 ? S.wtot[lane] : 0;
-            const int ti = warp_incl_scan(tv);
-            if (lane < NT / 32) S.wtot[lane] = ti - tv;
-            if (lane == NT / 32 - 1) S.row0[NT] = ti;
-        }
-        __syncthreads();
-        {
-            const int r0 = S.wtot[warp] + incl - nrows;
-            S.row0[t] = r0;
-            for (int r = r0; r < min(r0 + nrows, ROW_TABLE); r++) S.owner[r] = (unsigned char)t;
-        }
-        __syncthreads();
-        const int R = S.row0[NT];
-        for (int rbase = warp * 32; rbase < R; rbase += NT) {
+        const int R = __shfl_sync(FULL, incl, 31);
+        __syncwarp();
+        int qh = 0, qn = 0;  // head and length of this warp's row queue
+        for (int rbase = 0; rbase < R; rbase += 32) {
             const int r = rbase + lane;
-            int type = FACE, id = 0, pb = 0, pc = 0, ia = 0, len = 0, ax = 0;
+            const int own = min(warp_owner(incl, r), 31);  // lane whose region holds row r
+            const int r0 = __shfl_sync(FULL, incl - nrows, own);
+            const int reg = warp * 32 + own;
+            int len = 0, packed = 0;
             if (r < R) {
-                int reg;
-                if (r < ROW_TABLE) {
-                    reg = S.owner[r];
-                } else {  // last region whose first row is <= r
-                    int lo = 0, hi = NT - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (S.row0[mid] <= r) lo = mid; else hi = mid - 1;
-                    }
-                    reg = lo;
-                }
-                const int fid = S.fid[reg];
-                type = feat_type(F, fid);
-                id = feat_local(F, fid, type);
-                ax = S.ax[reg];
-                const int nbv = S.nb[reg];
-                const int local = r - S.row0[reg];
-                const int ic = (int)(((float)local + 0.5f) * __frcp_rn((float)nbv));  // exact for these sizes
+                const uint4 ri = S.rinfo[reg];
+                const int nbv = (int)(ri.y & 255u), nl = (int)((ri.y >> 8) & 15u);
+                const int local = r - r0;
+                const int ic = (int)(((float)local + 0.5f) * __uint_as_float(ri.z));  // exact for these sizes
                 const int ib = local - ic * nbv;
                 const float fb = (float)ib, fc = (float)ic;
                 float lo_f = -1e30f, hi_f = 1e30f;
                 bool open = true;
-                const int ne = S.ncoef[reg];
-                for (int k = 0; k < ne; k++) {
-                    const float4 E = S.coef[reg][k];
-                    const float v = fmaf(E.y, fb, fmaf(E.z, fc, E.x));
-                    if (E.w == (float)K_LOWER) lo_f = fmaxf(lo_f, v);
-                    else if (E.w == (float)K_UPPER) hi_f = fminf(hi_f, v);
-                    else open = open && v >= 0.f;
+                const float4 *E = S.coef[reg];
+#pragma unroll
+                for (int k = 0; k < KMAX; k++) {
+                    const float4 c = E[k];
+                    const float v = fmaf(c.y, fb, fmaf(c.z, fc, c.x));
+                    if (k < nl) lo_f = fmaxf(lo_f, v);
+                    else hi_f = fminf(hi_f, v);
                 }
                 const float4 bl = S.ball[reg];
                 if (bl.w >= 0.f) {
@@ -492,47 +540,35 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int32_t *
                     }
                 }
                 const float sl = 1.f / 4096.f;
-                const float span_hi = (float)S.span_hi[reg];
+                const float span_hi = (float)((ri.y >> 12) & 31u);
                 const float fa = fminf(fmaxf(lo_f - sl, 0.f), span_hi + 1.f);
                 const float fz = fmaxf(fminf(hi_f + sl, span_hi), -1.f);
                 const int ja = (int)ceilf(fa), jb = (int)floorf(fz);
                 len = open ? max(jb - ja + 1, 0) : 0;
-                ia = S.lo_a[reg] + ja;
-                pb = S.lo_b[reg] + ib;
-                pc = S.lo_c[reg] + ic;
+                // row record: slot | start along a << 8 | len << 13 | b << 19 | c << 24 (tile-local)
+                packed = reg | ((int)((ri.y >> 17) & 31u) + ja) << 8 | (len << 13) |
+                         (((int)((ri.y >> 22) & 31u) + ib) << 19) | (((int)(ri.y >> 27) + ic) << 24);
                 rows++;
                 hits += len > 0;
             }
-            // span points of this warp's 32 rows, flattened over the lanes
-            const int pincl = warp_incl_scan(len);
-            const int ptotal = __shfl_sync(FULL, pincl, 31);
-            for (int p0 = 0; p0 < ptotal; p0 += 32) {
-                const int pp = p0 + lane;
-                const int ro = min(warp_owner(pincl, pp), 31);
-                const int r_start = __shfl_sync(FULL, ia - (pincl - len), ro);
-                const int r_b = __shfl_sync(FULL, pb, ro), r_c = __shfl_sync(FULL, pc, ro);
-                const int r_id = __shfl_sync(FULL, id, ro), r_ax = __shfl_sync(FULL, ax, ro);
-                const int r_type = __shfl_sync(FULL, type, ro);
-                if (pp < ptotal) {
-                    const int pa = r_start + pp;
-                    const int pi = r_ax == 0 ? pa : r_b;
-                    const int pj = r_ax == 1 ? pa : (r_ax == 0 ? r_b : r_c);
-                    const int pk = r_ax == 2 ? pa : r_c;
-                    bool neg;
-                    const float d = eval_any(F, g, r_type, r_id, pi, pj, pk, neg);
-                    if (d < g.W) {
-                        const int gid = r_type == FACE ? r_id : (r_type == EDGE ? r_id + F.T : r_id + F.T + F.E);
-                        const unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) |
-                                                       ((unsigned long long)(unsigned)gid << 1) |
-                                                       (unsigned long long)neg;
-                        const int loc = ((pk - z0) * TY + (pj - y0)) * TILE_X + (pi - x0);
-                        atomicMin(S.key + loc, key);
-                        cand++;
-                    }
-                }
+            // queue the non-empty rows; evaluate their points once 32 rows are waiting
+            const unsigned hit = __ballot_sync(FULL, len > 0);
+            if (len > 0) S.rowq[warp][(qh + qn + __popc(hit & ((1u << lane) - 1u))) & 63] = (unsigned)packed;
+            qn += __popc(hit);
+            __syncwarp();
+            if (qn >= 32) {
+                eval_rows<TY, TZ>(F, g, S, S.rowq[warp], qh, 32, x0, y0, z0, cand);
+                qh = (qh + 32) & 63;
+                qn -= 32;
             }
         }
-        __syncthreads();  // region descriptors are rewritten by the next pass
+        while (qn > 0) {  // the rest of this warp's queue (region slots are rewritten by the next pass)
+            const int m = min(qn, 32);
+            eval_rows<TY, TZ>(F, g, S, S.rowq[warp], qh, m, x0, y0, z0, cand);
+            qh = (qh + m) & 63;
+            qn -= m;
+        }
+        __syncwarp();  // this warp's region slots are rewritten by its next chunk
     }
 }
 
@@ -588,7 +624,7 @@ __global__ void k_tile_lists(const uint32_t *bin_start, int64_t n_tiles, const u
 // chunks of FILL_CHUNK empty tiles.  A band tile merges its regions' candidates in shared memory
 // and writes its points; an empty tile is written +inf (Algorithm 1's initial value).
 template <int TY, int TZ>
-__global__ void __launch_bounds__(NT, 3) k_tile(const Prob *P, const long long *tile_base, int n, Outputs o,
+__global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *tile_base, int n, Outputs o,
                                                 int64_t n_tiles, const int32_t *band_list,
                                                 const int32_t *empty_list, const uint32_t *n_band_ptr,
                                                 unsigned long long *ticket) {
@@ -628,8 +664,10 @@ __global__ void __launch_bounds__(NT, 3) k_tile(const Prob *P, const long long *
                 const uint32_t *st = o.bin_start + 3 * tile;
                 const int64_t q0 = min((int64_t)st[0], o.pair_cap), q3 = min((int64_t)st[3], o.pair_cap);
                 for (int e = threadIdx.x; e < TP; e += NT) S.key[e] = ~0ull;
+                if (threadIdx.x == 0) S.chunk_next = 0;
                 __syncthreads();
-                process_band_tile<TY, TZ>(pr.F, g, o.pairs, q0, q3, x0, y0, z0, cx1, cy1, cz1, S, cand, rows, hits);
+                process_band_tile<TY, TZ>(pr.F, g, o.pairs, q0, q3, x0, y0, z0, S, cand, rows, hits);
+                __syncthreads();  // every merge is in before the decode
                 if (threadIdx.x == 0) pairs += (unsigned)(q3 - q0);
             }
             if (pr.vec && cx1 == x0 + TILE_X - 1) {
@@ -1032,7 +1070,7 @@ static int plan_reserve(Plan &pl, cudaStream_t s) {
     SDF_TRY(pl.lists.reserve(16 + sizeof(uint32_t) * (size_t)(3 * pl.n_tiles + 256), s));
     if (pl.pair_cap == 0) pl.pair_cap = 8 * pl.f_tot + 4096;
     if (pl.patch_cap == 0) pl.patch_cap = pl.f_tot / 8 + 65536;
-    SDF_TRY(pl.pairs.reserve(sizeof(int32_t) * (size_t)pl.pair_cap, s));
+    SDF_TRY(pl.pairs.reserve(sizeof(int2) * (size_t)pl.pair_cap, s));
     SDF_TRY(pl.patch.reserve(sizeof(PatchEntry) * (size_t)pl.patch_cap, s));
     if (!pl.ctr) {
         SDF_TRY(pool_alloc(reinterpret_cast<void **>(&pl.ctr), sizeof(DevCounters), s));
@@ -1077,7 +1115,7 @@ struct Scratch {  // device pointers used by one launch of the pipeline
     unsigned long long *ticket;
     uint32_t *band_pos;
     int32_t *band_list, *empty_list;
-    int32_t *pairs;
+    int2 *pairs;
     int64_t pair_cap;
     PatchEntry *patch;
     int64_t patch_cap;
@@ -1097,7 +1135,7 @@ static Scratch plan_scratch(const Plan &pl) {
     sc.band_pos = reinterpret_cast<uint32_t *>(sc.ticket + 2);
     sc.band_list = reinterpret_cast<int32_t *>(sc.band_pos + pl.n_tiles + 32);
     sc.empty_list = sc.band_list + pl.n_tiles + 32;
-    sc.pairs = pl.pairs.as<int32_t>();
+    sc.pairs = pl.pairs.as<int2>();
     sc.pair_cap = pl.pair_cap;
     sc.patch = pl.patch.as<PatchEntry>();
     sc.patch_cap = pl.patch_cap;
@@ -1452,7 +1490,7 @@ namespace sdf {
 namespace {
 static_assert(sizeof(Prob) + 16 * 4 <= 2048, "problem table slot");
 constexpr int64_t ST_MAX_TILES = 65536;                 // 32x8x8-point tiles (512^3 points)
-constexpr int64_t ST_MAX_PAIRS = int64_t(4) << 20;      // (tile, region) pairs
+constexpr int64_t ST_MAX_PAIRS = int64_t(2) << 20;      // (tile, region) pairs
 constexpr int64_t ST_MAX_PATCH = 131072;                // points re-decided in FP64
 constexpr size_t ST_OFF_CTR = 0;                        // DevCounters
 constexpr size_t ST_OFF_TICKET = 1024;                  // work ticket (8 bytes)
@@ -1465,8 +1503,8 @@ constexpr size_t ST_OFF_BANDLIST = ST_OFF_BANDPOS + 4 * (ST_MAX_TILES + 256);   
 constexpr size_t ST_OFF_EMPTYLIST = ST_OFF_BANDLIST + 4 * (ST_MAX_TILES + 256); // int32 [max tiles]
 constexpr size_t ST_OFF_SCAN = ST_OFF_EMPTYLIST + 4 * (ST_MAX_TILES + 256);     // scan temporaries
 constexpr size_t ST_SCAN_BYTES = 65536;
-constexpr size_t ST_OFF_PAIRS = ST_OFF_SCAN + ST_SCAN_BYTES;                     // int32 [max pairs]
-constexpr size_t ST_OFF_PATCH = ST_OFF_PAIRS + 4 * ST_MAX_PAIRS;                 // PatchEntry [max patch]
+constexpr size_t ST_OFF_PAIRS = ST_OFF_SCAN + ST_SCAN_BYTES;                     // int2 [max pairs]
+constexpr size_t ST_OFF_PATCH = ST_OFF_PAIRS + 8 * ST_MAX_PAIRS;                 // PatchEntry [max patch]
 constexpr size_t ST_BYTES = ST_OFF_PATCH + sizeof(PatchEntry) * ST_MAX_PATCH;    // about 20.3 MiB
 }  // namespace
 
@@ -1529,7 +1567,7 @@ extern "C" int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, floa
     sc.band_list = reinterpret_cast<int32_t *>(base + ST_OFF_BANDLIST);
     sc.empty_list = reinterpret_cast<int32_t *>(base + ST_OFF_EMPTYLIST);
     sc.scan_tmp = base + ST_OFF_SCAN;
-    sc.pairs = reinterpret_cast<int32_t *>(base + ST_OFF_PAIRS);
+    sc.pairs = reinterpret_cast<int2 *>(base + ST_OFF_PAIRS);
     sc.pair_cap = ST_MAX_PAIRS;
     sc.patch = reinterpret_cast<PatchEntry *>(base + ST_OFF_PATCH);
     sc.patch_cap = ST_MAX_PATCH;
