@@ -82,6 +82,10 @@ typedef struct sdf_features_s *sdf_features;
 #define SDF_FLAG_AUTOTUNE 0x8u       /* sdf_batch_create: time every tile shape on the batch
                                         and keep the fastest (also remembered for later
                                         sdf_narrow_band calls with n > 1 of the same sizes)  */
+#define SDF_FLAG_FILL_SIGN 0x10u     /* sdf_narrow_band / sdf_batch_create: points outside the
+                                        band get -inf inside the surface and +inf outside
+                                        (the sign fill beyond the band, Section 11.3);
+                                        requires w > h on every grid                         */
 
 /*
  * sdf_build_features -- mesh-connectivity stage (Section 7, Section 8).
@@ -141,10 +145,16 @@ int sdf_features_update_positions(sdf_features f, const float *vertices, void *s
  *   out_dist    host array [n] of device float[nz][ny][nx] outputs.
  *   out_winner  host array [n] of device int32[nz][ny][nx] (winner feature
  *               id, -1 outside the band); the array or any entry may be NULL.
- *   flags       0 or SDF_FLAG_NO_SYNC.
+ *   flags       0, SDF_FLAG_NO_SYNC, SDF_FLAG_TIMING, SDF_FLAG_FILL_SIGN (any combination).
+ *               With SDF_FLAG_FILL_SIGN, points outside the band hold -inf inside the
+ *               surface and +inf outside (Section 11.3's fill beyond the band): along each
+ *               x-row a run of points outside the band takes the sign of the band point
+ *               next to it, and a row without band points the sign of a neighbouring row
+ *               (exact whenever w > h; a grid without any band point is taken as outside).
  *
- * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_TOO_LARGE, SDF_ERR_OOM, SDF_ERR_CUDA,
- * SDF_ERR_DEGENERATE (positions set by sdf_features_update_positions).
+ * Errors: SDF_ERR_INVALID_ARG (also w <= h with SDF_FLAG_FILL_SIGN), SDF_ERR_TOO_LARGE,
+ * SDF_ERR_OOM, SDF_ERR_CUDA, SDF_ERR_DEGENERATE (positions set by
+ * sdf_features_update_positions).
  */
 int sdf_narrow_band(const sdf_features *feats, const sdf_grid *grids, const float *band_w, int32_t n,
                     float *const *out_dist, int32_t *const *out_winner, uint32_t flags, void *stream);
@@ -265,8 +275,8 @@ int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, float band_w, f
  * stage times in ms (host float[3]): binning, tile kernel, FP64 re-decision.  Without the flag
  * it returns SDF_ERR_INVALID_ARG.
  *
- * Arguments of sdf_batch_create are those of sdf_narrow_band; flags 0, SDF_FLAG_AUTOTUNE,
- * SDF_FLAG_TIMING or both.
+ * Arguments of sdf_batch_create are those of sdf_narrow_band; flags 0 or any of
+ * SDF_FLAG_AUTOTUNE, SDF_FLAG_TIMING, SDF_FLAG_FILL_SIGN.
  * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_TOO_LARGE, SDF_ERR_OOM, SDF_ERR_CUDA, SDF_ERR_DEGENERATE.
  * sdf_batch_destroy synchronises the device and releases the batch (NULL is a no-op); the
  * handles outlive the batch and are not released by it.

@@ -20,12 +20,13 @@ from . import _buildlib
 
 __all__ = ["Grid", "Features", "sdf_build_features", "sdf_narrow_band", "sdf_narrow_band_backward",
            "SDFFunction", "Batch", "sdf_batch_create", "load_library", "kernel_launches", "SDFError",
-           "FLAG_DISABLE_SADDLE", "FLAG_NO_SYNC", "FLAG_TIMING", "FLAG_AUTOTUNE"]
+           "FLAG_DISABLE_SADDLE", "FLAG_NO_SYNC", "FLAG_TIMING", "FLAG_AUTOTUNE", "FLAG_FILL_SIGN"]
 
 FLAG_DISABLE_SADDLE = 0x1
 FLAG_NO_SYNC = 0x2
 FLAG_TIMING = 0x4
 FLAG_AUTOTUNE = 0x8
+FLAG_FILL_SIGN = 0x10
 
 
 _STATUS_KEYS = ("candidates", "band_points", "fp64_points", "pairs", "rows", "rows_hit")
@@ -310,7 +311,8 @@ class Batch:
 
 def sdf_batch_create(features: Sequence[Features], grids: Sequence[Grid], w: Sequence[float],
                      out: Sequence[torch.Tensor] | None = None, winner: bool | Sequence = False,
-                     autotune: bool = False, timing: bool = False, stream=None) -> Batch:
+                     autotune: bool = False, timing: bool = False, fill_sign: bool = False,
+                     stream=None) -> Batch:
     """Create a batch; its outputs hold the result on return.  Keep the Features alive meanwhile."""
     feats, grids, ws = list(features), list(grids), list(w)
     n = len(feats)
@@ -335,7 +337,8 @@ def sdf_batch_create(features: Sequence[Features], grids: Sequence[Grid], w: Seq
     wa = (ctypes.c_float * n)(*[float(x) for x in ws])
     h = ctypes.c_void_p()
     _check(load_library().sdf_batch_create(fa, ga, wa, n, _ptr_array(outs), _ptr_array(wins),
-                                           (FLAG_AUTOTUNE if autotune else 0) | (FLAG_TIMING if timing else 0),
+                                           (FLAG_AUTOTUNE if autotune else 0) | (FLAG_TIMING if timing else 0) |
+                                           (FLAG_FILL_SIGN if fill_sign else 0),
                                            _stream(stream), ctypes.byref(h)),
            "sdf_batch_create")
     return Batch(h.value, feats, outs, wins)

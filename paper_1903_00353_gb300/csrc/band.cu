@@ -996,7 +996,12 @@ struct Plan {
     std::vector<Prob> probs;
     std::vector<long long> fbase, tbase;  // prefix sums of features and tiles over the problems
     long long f_tot = 0, n_tiles = 0;
-    DevBuf tables, bins, pairs, patch, scan_tmp, lists;
+    // sign beyond the band (SDF_FLAG_FILL_SIGN): output table, prefix sums of x-rows, z- and y-lines
+    bool fill = false;
+    std::vector<FillProb> fprobs;
+    std::vector<long long> rbase, zbase, ybase;
+    long long r_tot = 0, z_tot = 0, y_tot = 0;
+    DevBuf tables, bins, pairs, patch, scan_tmp, lists, rowsign;
     DevCounters *ctr = nullptr;
     bool own_ctr = false;
     int64_t pair_cap = 0, patch_cap = 0;
@@ -1022,6 +1027,7 @@ void plan_free(Plan *pl, cudaStream_t s) {
     pl->patch.release(s);
     pl->scan_tmp.release(s);
     pl->lists.release(s);
+    pl->rowsign.release(s);
     if (pl->own_ctr && pl->ctr) pool_free(pl->ctr, s);
     if (pl->pinned_ev) {
         cudaEventSynchronize(pl->pinned_ev);
@@ -1034,13 +1040,18 @@ void plan_free(Plan *pl, cudaStream_t s) {
 }
 
 static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *grids, const float *band_w, int n,
-                         float *const *out_dist, int32_t *const *out_winner, int shape) {
+                         float *const *out_dist, int32_t *const *out_winner, int shape, bool fill) {
     if (!feats || !grids || !band_w || n < 1 || !out_dist) return SDF_ERR_INVALID_ARG;
     pl.n = n;
     pl.shape = shape;
+    pl.fill = fill;
     pl.probs.resize(n);
     pl.fbase.assign(n + 1, 0);
     pl.tbase.assign(n + 1, 0);
+    pl.fprobs.resize(n);
+    pl.rbase.assign(n + 1, 0);
+    pl.zbase.assign(n + 1, 0);
+    pl.ybase.assign(n + 1, 0);
     for (int p = 0; p < n; p++) {
         if (!feats[p] || !out_dist[p]) return SDF_ERR_INVALID_ARG;
         Prob &pr = pl.probs[p];
@@ -1053,9 +1064,18 @@ static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *gr
                  ((reinterpret_cast<uintptr_t>(pr.winner) & 15) == 0);
         pl.fbase[p + 1] = pl.fbase[p] + feats[p]->T + feats[p]->E + feats[p]->V;
         pl.tbase[p + 1] = pl.tbase[p] + (long long)pr.g.ntx * pr.g.nty * pr.g.ntz;
+        // the fill's argument (rows outside the band run uncrossed) needs w > h
+        if (fill && !(band_w[p] > grids[p].h)) return SDF_ERR_INVALID_ARG;
+        pl.fprobs[p] = FillProb{out_dist[p], grids[p].nx, grids[p].ny, grids[p].nz};
+        pl.rbase[p + 1] = pl.rbase[p] + (long long)grids[p].ny * grids[p].nz;
+        pl.zbase[p + 1] = pl.zbase[p] + grids[p].nz;
+        pl.ybase[p + 1] = pl.ybase[p] + grids[p].ny;
     }
     pl.f_tot = pl.fbase[n];
     pl.n_tiles = pl.tbase[n];
+    pl.r_tot = pl.rbase[n];
+    pl.z_tot = pl.zbase[n];
+    pl.y_tot = pl.ybase[n];
     if (3 * pl.n_tiles >= (int64_t(1) << 31) || pl.f_tot >= (int64_t(1) << 31)) return SDF_ERR_TOO_LARGE;
     return SDF_OK;
 }
@@ -1063,8 +1083,10 @@ static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *gr
 // allocate scratch for the current capacities and upload the tables (not allowed while capturing)
 static int plan_reserve(Plan &pl, cudaStream_t s) {
     const int64_t n_bins = 3 * pl.n_tiles;
-    const size_t tb = sizeof(Prob) * pl.n + 2 * sizeof(long long) * (pl.n + 1) + 256;
+    const size_t tb = sizeof(Prob) * pl.n + 2 * sizeof(long long) * (pl.n + 1) + sizeof(FillProb) * pl.n +
+                      3 * sizeof(long long) * (pl.n + 1) + 256;
     SDF_TRY(pl.tables.reserve(tb, s));
+    if (pl.fill) SDF_TRY(pl.rowsign.reserve((size_t)pl.r_tot + 64, s));
     SDF_TRY(pl.bins.reserve(sizeof(uint32_t) * (size_t)(2 * n_bins + 64), s));
     SDF_TRY(pl.scan_tmp.reserve(scan_tmp_bytes(n_bins), s));
     SDF_TRY(pl.lists.reserve(16 + sizeof(uint32_t) * (size_t)(3 * pl.n_tiles + 256), s));
@@ -1077,12 +1099,17 @@ static int plan_reserve(Plan &pl, cudaStream_t s) {
         SDF_TRY(cudaMemsetAsync(pl.ctr, 0, sizeof(DevCounters), s));
         pl.own_ctr = true;
     }
-    // the table: Prob[n], then feature and tile prefix sums; uploaded only when it changed
-    const size_t pb = sizeof(Prob) * pl.n, lb = sizeof(long long) * (pl.n + 1);
-    std::vector<char> tab(pb + 2 * lb);
+    // the table: Prob[n], feature and tile prefix sums, FillProb[n], row / z-line / y-line prefix
+    // sums; uploaded only when it changed
+    const size_t pb = sizeof(Prob) * pl.n, lb = sizeof(long long) * (pl.n + 1), fb = sizeof(FillProb) * pl.n;
+    std::vector<char> tab(pb + 2 * lb + fb + 3 * lb);
     memcpy(tab.data(), pl.probs.data(), pb);
     memcpy(tab.data() + pb, pl.fbase.data(), lb);
     memcpy(tab.data() + pb + lb, pl.tbase.data(), lb);
+    memcpy(tab.data() + pb + 2 * lb, pl.fprobs.data(), fb);
+    memcpy(tab.data() + pb + 2 * lb + fb, pl.rbase.data(), lb);
+    memcpy(tab.data() + pb + 3 * lb + fb, pl.zbase.data(), lb);
+    memcpy(tab.data() + pb + 4 * lb + fb, pl.ybase.data(), lb);
     if (pl.uploaded_to == pl.tables.p && pl.uploaded == tab) return SDF_OK;
     if (pl.pageable) {
         pl.uploaded.swap(tab);
@@ -1120,6 +1147,11 @@ struct Scratch {  // device pointers used by one launch of the pipeline
     PatchEntry *patch;
     int64_t patch_cap;
     DevCounters *ctr;
+    // sign beyond the band (null fprobs: not requested)
+    const FillProb *fprobs = nullptr;
+    const long long *rbase = nullptr, *zbase = nullptr, *ybase = nullptr;
+    long long r_tot = 0, z_tot = 0, y_tot = 0;
+    int8_t *rowsign = nullptr;
 };
 
 static Scratch plan_scratch(const Plan &pl) {
@@ -1128,6 +1160,16 @@ static Scratch plan_scratch(const Plan &pl) {
     sc.probs = reinterpret_cast<const Prob *>(t);
     sc.fbase = reinterpret_cast<const long long *>(t + sizeof(Prob) * pl.n);
     sc.tbase = sc.fbase + pl.n + 1;
+    if (pl.fill) {
+        sc.fprobs = reinterpret_cast<const FillProb *>(sc.tbase + pl.n + 1);
+        sc.rbase = reinterpret_cast<const long long *>(sc.fprobs + pl.n);
+        sc.zbase = sc.rbase + pl.n + 1;
+        sc.ybase = sc.zbase + pl.n + 1;
+        sc.r_tot = pl.r_tot;
+        sc.z_tot = pl.z_tot;
+        sc.y_tot = pl.y_tot;
+        sc.rowsign = pl.rowsign.as<int8_t>();
+    }
     sc.cnt = pl.bins.as<uint32_t>();
     sc.start = sc.cnt + 3 * pl.n_tiles + 32;
     sc.scan_tmp = pl.scan_tmp.p;
@@ -1188,6 +1230,9 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
     k_patch<<<4 * num_sms(), 256, 0, s>>>(sc.probs, o);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
+    if (sc.fprobs)
+        SDF_TRY(fill_sign(sc.fprobs, sc.rbase, sc.zbase, sc.ybase, n, sc.r_tot, sc.z_tot, sc.y_tot, sc.rowsign,
+                          num_sms(), s));
     if (ev) SDF_TRY(record_event(ev[3], s));
     return SDF_OK;
 }
@@ -1304,6 +1349,7 @@ int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const floa
     for (int p = 0; p < n; p++)
         if (!feats[p] || !out_dist[p]) return SDF_ERR_INVALID_ARG;
     const bool sync = !(flags & SDF_FLAG_NO_SYNC), timing = (flags & SDF_FLAG_TIMING) != 0;
+    const bool fill = (flags & SDF_FLAG_FILL_SIGN) != 0;
     if (n == 1) {  // a batch of one, with the plan (and its scratch) cached in the handle
         sdf_features_s *f = feats[0];
         if (!f->plan) {
@@ -1312,7 +1358,7 @@ int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const floa
             f->plan->events = f;
         }
         Plan &pl = *f->plan;
-        SDF_TRY_ST(plan_describe(pl, feats, grids, band_w, 1, out_dist, out_winner, 0));
+        SDF_TRY_ST(plan_describe(pl, feats, grids, band_w, 1, out_dist, out_winner, 0, fill));
         return plan_execute(pl, feats, s, sync, timing);
     }
     int shape = 0;
@@ -1323,7 +1369,7 @@ int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const floa
     }
     Plan pl;
     pl.pageable = true;
-    int st = plan_describe(pl, feats, grids, band_w, n, out_dist, out_winner, shape);
+    int st = plan_describe(pl, feats, grids, band_w, n, out_dist, out_winner, shape, fill);
     if (!st) st = plan_execute(pl, feats, s, true, false);
     // the temporary plan's memory returns to the pool in stream order
     plan_free(new Plan(std::move(pl)), s);
@@ -1357,11 +1403,12 @@ extern "C" int sdf_batch_create(const sdf_features *feats, const sdf_grid *grids
     int best = 0;
     double best_ms = 0.0;
     const int n_try = (flags & SDF_FLAG_AUTOTUNE) ? N_SHAPES : 1;
+    const bool fill = (flags & SDF_FLAG_FILL_SIGN) != 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int st = SDF_OK;
     if (n_try > 1 && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = SDF_ERR_CUDA;
     for (int shape = 0; shape < n_try && !st; shape++) {
-        st = plan_describe(b->plan, feats, grids, band_w, n, out_dist, out_winner, shape);
+        st = plan_describe(b->plan, feats, grids, band_w, n, out_dist, out_winner, shape, fill);
         if (!st) st = plan_execute(b->plan, b->feats.data(), s, true, false);  // sizes the scratch
         if (st || n_try == 1) break;
         const int reps = 3;
@@ -1390,7 +1437,7 @@ extern "C" int sdf_batch_create(const sdf_features *feats, const sdf_grid *grids
         }
         b->plan.pair_cap = 0;
         b->plan.patch_cap = 0;
-        st = plan_describe(b->plan, feats, grids, band_w, n, out_dist, out_winner, best);
+        st = plan_describe(b->plan, feats, grids, band_w, n, out_dist, out_winner, best, fill);
         if (!st) st = plan_execute(b->plan, b->feats.data(), s, true, false);
         b->plan.tuned_ms = best_ms;
     }

@@ -122,6 +122,18 @@ size_t radix_tmp_bytes(int64_t n);
 cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int64_t n,
                            int bits, void *tmp, cudaStream_t s);
 
+// ----------------------------------------------------------------------------- sign beyond the band (fill.cu)
+// One problem's dense output, float[nz][ny][nx].
+struct FillProb {
+    float *dist;
+    int nx, ny, nz;
+};
+// Writes -inf to the points outside the band that lie inside the surface (points outside the band
+// hold +inf on entry).  rbase / zbase / ybase: prefix sums over the n problems of ny * nz (x-rows),
+// nz and ny, with totals r_tot, z_tot, y_tot; rowsign: int8 scratch of r_tot entries.
+cudaError_t fill_sign(const FillProb *P, const long long *rbase, const long long *zbase, const long long *ybase, int n,
+                      long long r_tot, long long z_tot, long long y_tot, int8_t *rowsign, int n_sm, cudaStream_t s);
+
 // ----------------------------------------------------------------------------- geometry stage (build.cu)
 int build_records(sdf_features_s *f, cudaStream_t s);
 
