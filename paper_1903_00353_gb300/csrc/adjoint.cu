@@ -7,9 +7,9 @@
 // vertices x_k: lam are the barycentric weights on a face, (1 - t, t) on an edge, 1 at a vertex.
 // Inside a face region s * (p - q)/|p - q| is the face normal n, so no sign is needed there.
 //
-// One thread per grid point; threads of a warp that hit the same vertex are merged with
-// __match_any_sync before the atomicAdd (warp-aggregated atomics), since neighbouring band
-// points usually share their winner.
+// Band points are compacted over the lanes of a warp in grid order; lanes that hit the same vertex
+// in a run are merged by a segmented warp scan before the atomicAdd (warp-aggregated atomics),
+// since neighbouring band points usually share their winner.
 #include "sdf_internal.cuh"
 
 namespace sdf {
@@ -31,26 +31,29 @@ struct AdjArgs {
     const float *vpos;
 };
 
-// add (gx, gy, gz) to vertex v, merged across the lanes of the warp that target the same vertex
+// add (gx, gy, gz) to vertex v, merged over runs of consecutive lanes that target the same vertex
+// (band points arrive in grid order, so neighbours with a common winner sit in adjacent lanes): a
+// segmented warp scan sums each run and its last lane issues the atomics
 __device__ __forceinline__ void warp_add(float *gv, int v, float gx, float gy, float gz, bool active) {
     const int lane = threadIdx.x & 31;
-    int key = active ? v : -1 - lane;  // inactive lanes form singleton groups
-    unsigned peers = __match_any_sync(FULL, key);
-    int leader = __ffs(peers) - 1;
-    // reduce within the peer group: each lane walks its group with shuffles
-    float sx = 0.f, sy = 0.f, sz = 0.f;
-    unsigned m = peers;
-    while (m) {
-        int src = __ffs(m) - 1;
-        m &= m - 1;
-        sx += __shfl_sync(peers, gx, src);
-        sy += __shfl_sync(peers, gy, src);
-        sz += __shfl_sync(peers, gz, src);
+    const int key = active ? v : -1;
+    const int prev = __shfl_up_sync(FULL, key, 1), next = __shfl_down_sync(FULL, key, 1);
+    const unsigned heads = __ballot_sync(FULL, lane == 0 || prev != key);
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // first lane of this run
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float tx = __shfl_up_sync(FULL, gx, o), ty = __shfl_up_sync(FULL, gy, o),
+                    tz = __shfl_up_sync(FULL, gz, o);
+        if (lane - o >= start) {
+            gx += tx;
+            gy += ty;
+            gz += tz;
+        }
     }
-    if (active && lane == leader) {
-        atomicAdd(gv + 3 * v, sx);
-        atomicAdd(gv + 3 * v + 1, sy);
-        atomicAdd(gv + 3 * v + 2, sz);
+    if (active && (lane == 31 || next != key)) {
+        atomicAdd(gv + 3 * v, gx);
+        atomicAdd(gv + 3 * v + 1, gy);
+        atomicAdd(gv + 3 * v + 2, gz);
     }
 }
 
@@ -139,25 +142,45 @@ __device__ __forceinline__ int warp_incl_scan_i(int v) {
     }
     return v;
 }
-__device__ __forceinline__ int warp_owner_i(int incl, int r) {
-    int lo = 0;
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-        const int v = __shfl_sync(FULL, incl, lo + s - 1);
-        if (v <= r) lo += s;
+
+// Each lane reads the winners of 4 consecutive grid points (one int4 when vec is set).  The band
+// points among a warp's 128 points are appended, in grid order, to a per-warp ring in shared
+// memory; whenever 32 are waiting, each lane takes one, computes its vertex contributions, and
+// neighbouring points, which mostly share a winner, are merged by warp_add before the atomics.
+// The band is a thin shell, so most passes hold only a few band points: the ring keeps the
+// contribution step on full warps.
+constexpr int ADJ_RING = 256;  // > 31 waiting + 128 appended per pass
+
+__device__ __forceinline__ void adjoint_batch(const AdjArgs &a, const long long *ridx, const int *rwid, int q0,
+                                              int m) {
+    const int lane = threadIdx.x & 31;
+    bool act = false;
+    int wid = -1;
+    int64_t idx = 0;
+    float g = 0.f;
+    if (lane < m) {
+        const int e = (q0 + lane) & (ADJ_RING - 1);
+        idx = ridx[e];
+        wid = rwid[e];
+        g = __ldg(a.grad + idx);
+        act = g != 0.f;
     }
-    return lo;
+    int vtx[3] = {0, 0, 0};
+    float c[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    const int nv = act ? point_adjoint(a, idx, wid, g, vtx, c) : 0;
+    for (int q = 0; q < 3; q++) warp_add(a.gv, vtx[q], c[q][0], c[q][1], c[q][2], q < nv);
 }
 
-// Each lane reads the winners of 4 consecutive grid points (one int4 when vec is set); the band
-// points of the warp's 128 points are then compacted over the lanes (warp scan of the per-lane
-// counts) so every lane of a pass works on a band point, and neighbouring points, which mostly
-// share a winner, are merged by warp_add before the atomics.
 __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a, int vec) {
-    const int lane = threadIdx.x & 31;
+    __shared__ long long s_idx[8][ADJ_RING];
+    __shared__ int s_wid[8][ADJ_RING];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long *ridx = s_idx[warp];
+    int *rwid = s_wid[warp];
     const int64_t n = (int64_t)a.nx * a.ny * a.nz;
     const int64_t n4 = (n + 3) / 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int qh = 0, qn = 0;  // ring head and length (warp-uniform)
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n4; base += stride) {
         const int64_t q4 = base + threadIdx.x;
         int w4[4] = {-1, -1, -1, -1};
@@ -173,37 +196,25 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a, int vec) {
         const int cnt = (w4[0] >= 0) + (w4[1] >= 0) + (w4[2] >= 0) + (w4[3] >= 0);
         const int incl = warp_incl_scan_i(cnt);
         const int total = __shfl_sync(FULL, incl, 31);
-        for (int c0 = 0; c0 < total; c0 += 32) {
-            const int k = c0 + lane;
-            const int o = min(warp_owner_i(incl, k), 31);
-            const int excl = __shfl_sync(FULL, incl - cnt, o);
-            const int ow0 = __shfl_sync(FULL, w4[0], o), ow1 = __shfl_sync(FULL, w4[1], o);
-            const int ow2 = __shfl_sync(FULL, w4[2], o), ow3 = __shfl_sync(FULL, w4[3], o);
-            bool act = false;
-            int wid = -1;
-            int64_t idx = 0;
-            float g = 0.f;
-            if (k < total) {
-                int r = k - excl;  // r-th band point among the owner's four
-                const int ow[4] = {ow0, ow1, ow2, ow3};
-                int u = 0;
-                for (; u < 4; u++) {
-                    if (ow[u] >= 0) {
-                        if (r == 0) break;
-                        r--;
-                    }
-                }
-                wid = ow[u];
-                idx = 4 * (base + (threadIdx.x & ~31) + o) + u;
-                g = __ldg(a.grad + idx);
-                act = g != 0.f;
+        if (total == 0) continue;
+        int pos = qh + qn + incl - cnt;
+        for (int u = 0; u < 4; u++) {
+            if (w4[u] >= 0) {
+                ridx[pos & (ADJ_RING - 1)] = 4 * q4 + u;
+                rwid[pos & (ADJ_RING - 1)] = w4[u];
+                pos++;
             }
-            int vtx[3] = {0, 0, 0};
-            float c[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-            const int nv = act ? point_adjoint(a, idx, wid, g, vtx, c) : 0;
-            for (int q = 0; q < 3; q++) warp_add(a.gv, vtx[q], c[q][0], c[q][1], c[q][2], q < nv);
         }
+        qn += total;
+        __syncwarp();
+        while (qn >= 32) {
+            adjoint_batch(a, ridx, rwid, qh, 32);
+            qh = (qh + 32) & (ADJ_RING - 1);
+            qn -= 32;
+        }
+        __syncwarp();  // ring slots are rewritten by the next pass
     }
+    if (qn > 0) adjoint_batch(a, ridx, rwid, qh, qn);
 }
 
 }  // namespace
