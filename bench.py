@@ -13,8 +13,10 @@ value = band points produced per second (all ranks), device-timed with CUDA even
 e2e = the same metric through the public API with host buffers (pinned H2D of the
 soup, D2H of the SDF and the vertex gradient inside the timed region).
 --impl reference times the FP64 CPU oracle on a bounded slab of the same workload.
-Multi-GPU (torchrun): every rank runs its own replica of the workload (independent
-problems, no data-path collective); timing is the max over ranks.
+Multi-GPU (torchrun): by default every rank runs its own replica of the workload (independent
+problems, no data-path collective, weak scaling); --shard slabs gives each rank one z-slab of the
+grid instead, with the vertex gradient summed over the ranks by one all-reduce (strong scaling).
+Timing is the max over ranks.
 """
 from __future__ import annotations
 
@@ -495,6 +497,9 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=None, help="override the grid size N (same mesh, same band in cells)")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "slabs"],
+                    help="N > 1: every rank runs the whole workload (replicas, weak scaling) or one z-slab of "
+                         "its grid with the vertex gradient summed over the ranks (slabs, strong scaling)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.warmup < 3:
@@ -531,7 +536,9 @@ def main():
         N = args.grid
         wl = dict(wl, desc=wl["desc"].replace(f"{meshgen.CONFIG_GRID[wl['index']][0]}^3", f"{N}^3"))
     w = cells / N
-    grid = sdf.Grid.cube(N)
+    from paper_1903_00353_gb300 import slabs
+    shard = args.shard == "slabs" and world > 1
+    grid = slabs.slab_grid(sdf.Grid.cube(N), world, rank) if shard else sdf.Grid.cube(N)
     dev = torch.device("cuda", local)
     soup = torch.from_numpy(soup_np).to(dev)
     dist = torch.empty(grid.shape, dtype=torch.float32, device=dev)
@@ -547,6 +554,11 @@ def main():
     feats = sdf.sdf_build_features(soup)
     sdf.sdf_narrow_band(feats, grid, w, out=dist, winner=win if win is not None else False)
     band_points = int(torch.isfinite(dist).sum())
+    band_total = band_points * world  # replicas: every rank produces the same band
+    if shard:  # slabs: the ranks' bands partition the whole grid's band
+        t = torch.tensor([band_points], dtype=torch.int64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.SUM)
+        band_total = int(t.item())
     stats = feats.status()
     rec_bytes = record_bytes(feats)
     g = None
@@ -568,6 +580,8 @@ def main():
         if wl["adjoint"]:
             gv.zero_()
             sdf.sdf_narrow_band_backward(f, grid, w, g, winner=win, grad_vertices=gv, flags=sdf.FLAG_TIMING)
+            if shard:
+                slabs.all_reduce_sum(gv)  # the one exchange: dL/dV summed over the slabs
         if ev:
             ev[3].record()
         return f
@@ -608,7 +622,7 @@ def main():
         t = torch.tensor([total_ms], device=dev)
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = band_points * args.steps * world / (total_ms / 1e3)
+    value = band_total * args.steps / (total_ms / 1e3)
     build_ms, fwd_ms, adj_ms = (float(x) for x in per.mean(axis=0))
 
     # end to end through the public API with host buffers
@@ -626,22 +640,25 @@ def main():
             ge = torch.where(torch.isfinite(dist), 2.0 * (dist - 0.01), torch.zeros_like(dist))
             gv.zero_()
             sdf.sdf_narrow_band_backward(f, grid, w, ge, winner=win, grad_vertices=gv)
+            if shard:
+                slabs.all_reduce_sum(gv)
             gv_host.copy_(gv, non_blocking=True)
         dist_host.copy_(dist, non_blocking=True)
         torch.cuda.synchronize()
         f.destroy()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": band_points * e2e_steps * world / e2e_s, "unit": UNIT,
+    e2e = {"value": band_total * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(soup_np.nbytes),
            "d2h_bytes_per_step": int(dist.numel() * 4 + (gv.numel() * 4 if gv is not None else 0))}
 
     hbm, peak_kind = peaks()
     tile_avg_ms = tile_ms / max(1, tile_calls)
-    alg_bytes = 4 * N ** 3 + (4 * N ** 3 if wl["winner"] else 0) + rec_bytes
+    npts = grid.nx * grid.ny * grid.nz
+    alg_bytes = 4 * npts + (4 * npts if wl["winner"] else 0) + rec_bytes
     achieved = alg_bytes / (tile_avg_ms / 1e3) / 1e9
     roofline = {"kernel": "k_tile (scan conversion + merge + dense write)", "bound": "hbm",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "peak_source": peak_kind, "traffic": tile_traffic(args.workload, not args.grid),
+                "peak_source": peak_kind, "traffic": tile_traffic(args.workload, not args.grid and not shard),
                 "algorithmic_bytes": int(alg_bytes),
                 "avg_ms": tile_avg_ms}
 
@@ -654,11 +671,11 @@ def main():
         cpu = cpu_baseline(soup_np, N, w)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "strong" if shard else "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["desc"], "triangles": int(soup_np.shape[0]), "grid": [N, N, N], "band_w": w,
                    "band_points": band_points, "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": (f"z-slabs x{world}" if shard else "replicas") if world > 1 else "single GPU"},
         "build_ms": build_ms, "fwd_ms": fwd_ms, "adjoint_ms": adj_ms if wl["adjoint"] else None,
         "fwd_adjoint_ms": fwd_ms + adj_ms if wl["adjoint"] else None,
         "fwd_adjoint_over_fwd": (fwd_ms + adj_ms) / fwd_ms if wl["adjoint"] else None,
