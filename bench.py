@@ -497,6 +497,9 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=None, help="override the grid size N (same mesh, same band in cells)")
+    ap.add_argument("--schedule", default="tile", choices=["tile", "cell"],
+                    help="forward schedule: the binned tile kernel, or the paper's thread-per-region cell loop "
+                         "(schedule comparison)")
     ap.add_argument("--shard", default="replicas", choices=["replicas", "slabs"],
                     help="N > 1: every rank runs the whole workload (replicas, weak scaling) or one z-slab of "
                          "its grid with the vertex gradient summed over the ranks (slabs, strong scaling)")
@@ -551,8 +554,9 @@ def main():
         return
 
     # upstream gradient of L = sum_band (d - 0.01)^2 from one forward (same mesh every step)
+    sched_flag = sdf.FLAG_CELL_LOOP if args.schedule == "cell" else 0
     feats = sdf.sdf_build_features(soup)
-    sdf.sdf_narrow_band(feats, grid, w, out=dist, winner=win if win is not None else False)
+    sdf.sdf_narrow_band(feats, grid, w, out=dist, winner=win if win is not None else False, flags=sched_flag)
     band_points = int(torch.isfinite(dist).sum())
     band_total = band_points * world  # replicas: every rank produces the same band
     if shard:  # slabs: the ranks' bands partition the whole grid's band
@@ -574,7 +578,8 @@ def main():
         f = sdf.sdf_build_features(soup)
         if ev:
             ev[1].record()
-        sdf.sdf_narrow_band(f, grid, w, out=dist, winner=win if win is not None else False, flags=sdf.FLAG_TIMING)
+        sdf.sdf_narrow_band(f, grid, w, out=dist, winner=win if win is not None else False,
+                            flags=sdf.FLAG_TIMING | sched_flag)
         if ev:
             ev[2].record()
         if wl["adjoint"]:
@@ -635,7 +640,7 @@ def main():
     for _ in range(e2e_steps):
         s_dev = soup_host.to(dev, non_blocking=True)
         f = sdf.sdf_build_features(s_dev)
-        sdf.sdf_narrow_band(f, grid, w, out=dist, winner=win if win is not None else False)
+        sdf.sdf_narrow_band(f, grid, w, out=dist, winner=win if win is not None else False, flags=sched_flag)
         if wl["adjoint"]:
             ge = torch.where(torch.isfinite(dist), 2.0 * (dist - 0.01), torch.zeros_like(dist))
             gv.zero_()
@@ -656,9 +661,12 @@ def main():
     npts = grid.nx * grid.ny * grid.nz
     alg_bytes = 4 * npts + (4 * npts if wl["winner"] else 0) + rec_bytes
     achieved = alg_bytes / (tile_avg_ms / 1e3) / 1e9
-    roofline = {"kernel": "k_tile (scan conversion + merge + dense write)", "bound": "hbm",
+    kname = ("k_cell_loop + k_decode_keys (the paper's schedule: region walk, global atomicMin, decode)"
+             if args.schedule == "cell" else "k_tile (scan conversion + merge + dense write)")
+    roofline = {"kernel": kname, "bound": "hbm",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "peak_source": peak_kind, "traffic": tile_traffic(args.workload, not args.grid and not shard),
+                "peak_source": peak_kind,
+                "traffic": tile_traffic(args.workload, not args.grid and not shard and args.schedule == "tile"),
                 "algorithmic_bytes": int(alg_bytes),
                 "avg_ms": tile_avg_ms}
 
@@ -675,6 +683,7 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["desc"], "triangles": int(soup_np.shape[0]), "grid": [N, N, N], "band_w": w,
                    "band_points": band_points, "l2": "flushed between timed steps (256 MiB write)",
+                   "schedule": args.schedule,
                    "parallelism": (f"z-slabs x{world}" if shard else "replicas") if world > 1 else "single GPU"},
         "build_ms": build_ms, "fwd_ms": fwd_ms, "adjoint_ms": adj_ms if wl["adjoint"] else None,
         "fwd_adjoint_ms": fwd_ms + adj_ms if wl["adjoint"] else None,

@@ -86,6 +86,13 @@ typedef struct sdf_features_s *sdf_features;
                                         band get -inf inside the surface and +inf outside
                                         (the sign fill beyond the band, Section 11.3);
                                         requires w > h on every grid                         */
+#define SDF_FLAG_CELL_LOOP 0x20u     /* sdf_narrow_band / sdf_batch_create: run the paper's own
+                                        schedule (Section 9: one thread per characteristic
+                                        region walking its box, a global 64-bit atomicMin per
+                                        grid point, then a decode pass) instead of the binned
+                                        tile kernel; same regions, distances and FP64
+                                        re-decision.  For the schedule comparison; needs
+                                        8 bytes of scratch per grid point                    */
 
 /*
  * sdf_build_features -- mesh-connectivity stage (Section 7, Section 8).
@@ -145,7 +152,8 @@ int sdf_features_update_positions(sdf_features f, const float *vertices, void *s
  *   out_dist    host array [n] of device float[nz][ny][nx] outputs.
  *   out_winner  host array [n] of device int32[nz][ny][nx] (winner feature
  *               id, -1 outside the band); the array or any entry may be NULL.
- *   flags       0, SDF_FLAG_NO_SYNC, SDF_FLAG_TIMING, SDF_FLAG_FILL_SIGN (any combination).
+ *   flags       0, SDF_FLAG_NO_SYNC, SDF_FLAG_TIMING, SDF_FLAG_FILL_SIGN, SDF_FLAG_CELL_LOOP
+ *               (any combination).
  *               With SDF_FLAG_FILL_SIGN, points outside the band hold -inf inside the
  *               surface and +inf outside (Section 11.3's fill beyond the band): along each
  *               x-row a run of points outside the band takes the sign of the band point

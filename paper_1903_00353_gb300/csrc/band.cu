@@ -418,8 +418,9 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int2 *pai
     // equal chunks of at most 32 regions, a multiple of the warp count of them, so that a tile with
     // few regions still spreads its rows over every warp
     const int64_t npairs = q3 - q0;
-    const int64_t nchunks = (NT / 32) * ((npairs + NT - 1) / NT);
-    const int cs = (int)((npairs + nchunks - 1) / max(nchunks, (int64_t)1));
+    if (npairs <= 0) return;  // (after a pair-list overflow a band tile may have no stored pairs)
+    const int64_t nchunks = (NT / 32) * ((npairs + NT - 1) / NT);  // >= NT / 32
+    const int cs = (int)((npairs + nchunks - 1) / nchunks);          // >= 1: every chunk advances
     for (;;) {
         // this warp's next chunk of the tile's regions
         int chunk = 0;
@@ -899,6 +900,103 @@ inline unsigned nblk(int64_t n, int bt) { return (unsigned)((n + bt - 1) / bt); 
 
 }  // namespace
 
+// ----------------------------------------------------------------------------- the paper's schedule
+// The schedule of Section 9, kept for the schedule ablation (SDF_FLAG_CELL_LOOP): one thread per
+// characteristic region walks every grid point of the region's box, tests it against the region's
+// half-spaces (and the vertex ball) with the inclusion tolerance, and merges the distance into a
+// 64-bit key per grid point with a global atomicMin (the paper's atomicCAS loop on a packed value);
+// a second kernel decodes every key into the dense output.  Same regions, distances, keys and
+// FP64 re-decision as the tile path; only the work decomposition differs.
+template <int TYPE>
+__device__ __forceinline__ bool region_contains(const Feat &F, const GridP &g, int id, float3 p) {
+    const float e = g.eps;
+    if (TYPE == FACE) {
+        const float4 *r = F.face_rec + 4 * id;
+        const float4 n = __ldg(r), s1 = __ldg(r + 1), s2 = __ldg(r + 2), s3 = __ldg(r + 3);
+        const float sd = dot3(f3(n), p) + n.w;
+        return sd + g.W >= -e && g.W - sd >= -e && dot3(f3(s1), p) + s1.w >= -e && dot3(f3(s2), p) + s2.w >= -e &&
+               dot3(f3(s3), p) + s3.w >= -e;
+    } else if (TYPE == EDGE) {
+        const float4 *r = F.edge_rec + 5 * id;
+        const float4 a = __ldg(r), t = __ldg(r + 1), p2 = __ldg(r + 2), p3 = __ldg(r + 3);
+        const float tp = dot3(f3(t), p);
+        return tp - t.w >= -e && t.w + a.w - tp >= -e && dot3(f3(p2), p) + p2.w >= -e &&
+               dot3(f3(p3), p) + p3.w >= -e;
+    } else {
+        const float4 v = __ldg(F.vert_rec + 3 * id), nv = __ldg(F.vert_rec + 3 * id + 1);
+        const float3 u = p - f3(v);
+        const float R = g.W + e;
+        if (dot3(u, u) > R * R) return false;
+        const int s0 = __float_as_int(v.w), cnt = min(__float_as_int(nv.w), MAXVP);
+        for (int k = 0; k < cnt; k++) {
+            const float4 P = __ldg(F.vert_plane + s0 + k);
+            if (dot3(f3(P), p) + P.w < -e) return false;
+        }
+        return true;
+    }
+}
+
+template <int TYPE>
+__device__ __forceinline__ unsigned walk_region(const Feat &F, const GridP &g, int id, int fid,
+                                                unsigned long long *keys) {
+    int i0, i1, j0, j1, k0, k1;
+    if (!feature_box<TYPE>(F, g, id, i0, i1, j0, j1, k0, k1)) return 0;
+    unsigned cand = 0;
+    for (int k = k0; k <= k1; k++)
+        for (int j = j0; j <= j1; j++)
+            for (int i = i0; i <= i1; i++) {
+                const float3 p = make_float3(fmaf((float)i + 0.5f, g.h, g.ox), fmaf((float)j + 0.5f, g.h, g.oy),
+                                             fmaf((float)k + 0.5f, g.h, g.oz));
+                if (!region_contains<TYPE>(F, g, id, p)) continue;
+                bool neg;
+                const float d = eval_point<TYPE>(F, g, id, i, j, k, neg);
+                if (d < g.W) {
+                    const unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) |
+                                                   ((unsigned long long)(unsigned)fid << 1) | (unsigned long long)neg;
+                    atomicMin(keys + ((int64_t)k * g.ny + j) * g.nx + i, key);
+                    cand++;
+                }
+            }
+    return cand;
+}
+
+__global__ void k_cell_loop(const Prob *P, const long long *feat_base, const long long *pbase, int n, long long f_tot,
+                            unsigned long long *keys, DevCounters *ctr) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned cand = 0;
+    if (gid < f_tot) {
+        const int p = find_prob(feat_base, n, gid);
+        const Feat &F = P[p].F;
+        const GridP &g = P[p].g;
+        const int64_t lid = gid - feat_base[p];
+        unsigned long long *kp = keys + pbase[p];
+        if (lid < F.T) cand = walk_region<FACE>(F, g, (int)lid, (int)lid, kp);
+        else if (lid < (int64_t)F.T + F.E) cand = walk_region<EDGE>(F, g, (int)(lid - F.T), (int)lid, kp);
+        else cand = walk_region<VERT>(F, g, (int)(lid - F.T - F.E), (int)lid, kp);
+    }
+    const unsigned c = __reduce_add_sync(0xffffffffu, cand);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&ctr->n_candidates, (unsigned long long)c);
+}
+
+// every grid point of every problem: its key to the dense output (and the FP64 queue)
+__global__ void k_decode_keys(const Prob *P, const long long *pbase, int n, long long p_tot,
+                              const unsigned long long *keys, Outputs o) {
+    unsigned band = 0;
+    bool overflow = false;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < p_tot; q += stride) {
+        const int p = find_prob(pbase, n, q);
+        const int64_t idx = q - pbase[p];
+        int wid = -1;
+        const float v = decode_key(__ldg(keys + q), P[p].g, o, idx, p, wid, band, overflow);
+        __stcs(P[p].dist + idx, v);
+        if (P[p].winner) __stcs(P[p].winner + idx, wid);
+    }
+    const unsigned b = __reduce_add_sync(0xffffffffu, band);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&o.ctr->n_band, (unsigned long long)b);
+    if (overflow) atomicOr(&o.ctr->nb_status, ST_PATCH_OVERFLOW);
+}
+
 // ----------------------------------------------------------------------------- host side
 // Tile shapes the kernels are instantiated for: 32 x TY x TZ points.  8 x 8 is the default; a
 // batch created with SDF_FLAG_AUTOTUNE times all of them on its own problems and keeps the fastest.
@@ -1001,7 +1099,11 @@ struct Plan {
     std::vector<FillProb> fprobs;
     std::vector<long long> rbase, zbase, ybase;
     long long r_tot = 0, z_tot = 0, y_tot = 0;
-    DevBuf tables, bins, pairs, patch, scan_tmp, lists, rowsign;
+    // the paper's schedule (SDF_FLAG_CELL_LOOP): prefix sums of grid points, one key per point
+    bool cell_loop = false;
+    std::vector<long long> pbase;
+    long long p_tot = 0;
+    DevBuf tables, bins, pairs, patch, scan_tmp, lists, rowsign, keys;
     DevCounters *ctr = nullptr;
     bool own_ctr = false;
     int64_t pair_cap = 0, patch_cap = 0;
@@ -1028,6 +1130,7 @@ void plan_free(Plan *pl, cudaStream_t s) {
     pl->scan_tmp.release(s);
     pl->lists.release(s);
     pl->rowsign.release(s);
+    pl->keys.release(s);
     if (pl->own_ctr && pl->ctr) pool_free(pl->ctr, s);
     if (pl->pinned_ev) {
         cudaEventSynchronize(pl->pinned_ev);
@@ -1052,6 +1155,7 @@ static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *gr
     pl.rbase.assign(n + 1, 0);
     pl.zbase.assign(n + 1, 0);
     pl.ybase.assign(n + 1, 0);
+    pl.pbase.assign(n + 1, 0);
     for (int p = 0; p < n; p++) {
         if (!feats[p] || !out_dist[p]) return SDF_ERR_INVALID_ARG;
         Prob &pr = pl.probs[p];
@@ -1070,12 +1174,14 @@ static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *gr
         pl.rbase[p + 1] = pl.rbase[p] + (long long)grids[p].ny * grids[p].nz;
         pl.zbase[p + 1] = pl.zbase[p] + grids[p].nz;
         pl.ybase[p + 1] = pl.ybase[p] + grids[p].ny;
+        pl.pbase[p + 1] = pl.pbase[p] + (long long)grids[p].nx * grids[p].ny * grids[p].nz;
     }
     pl.f_tot = pl.fbase[n];
     pl.n_tiles = pl.tbase[n];
     pl.r_tot = pl.rbase[n];
     pl.z_tot = pl.zbase[n];
     pl.y_tot = pl.ybase[n];
+    pl.p_tot = pl.pbase[n];
     if (3 * pl.n_tiles >= (int64_t(1) << 31) || pl.f_tot >= (int64_t(1) << 31)) return SDF_ERR_TOO_LARGE;
     return SDF_OK;
 }
@@ -1084,9 +1190,10 @@ static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *gr
 static int plan_reserve(Plan &pl, cudaStream_t s) {
     const int64_t n_bins = 3 * pl.n_tiles;
     const size_t tb = sizeof(Prob) * pl.n + 2 * sizeof(long long) * (pl.n + 1) + sizeof(FillProb) * pl.n +
-                      3 * sizeof(long long) * (pl.n + 1) + 256;
+                      4 * sizeof(long long) * (pl.n + 1) + 256;
     SDF_TRY(pl.tables.reserve(tb, s));
     if (pl.fill) SDF_TRY(pl.rowsign.reserve((size_t)pl.r_tot + 64, s));
+    if (pl.cell_loop) SDF_TRY(pl.keys.reserve(sizeof(unsigned long long) * (size_t)pl.p_tot, s));
     SDF_TRY(pl.bins.reserve(sizeof(uint32_t) * (size_t)(2 * n_bins + 64), s));
     SDF_TRY(pl.scan_tmp.reserve(scan_tmp_bytes(n_bins), s));
     SDF_TRY(pl.lists.reserve(16 + sizeof(uint32_t) * (size_t)(3 * pl.n_tiles + 256), s));
@@ -1102,7 +1209,7 @@ static int plan_reserve(Plan &pl, cudaStream_t s) {
     // the table: Prob[n], feature and tile prefix sums, FillProb[n], row / z-line / y-line prefix
     // sums; uploaded only when it changed
     const size_t pb = sizeof(Prob) * pl.n, lb = sizeof(long long) * (pl.n + 1), fb = sizeof(FillProb) * pl.n;
-    std::vector<char> tab(pb + 2 * lb + fb + 3 * lb);
+    std::vector<char> tab(pb + 2 * lb + fb + 4 * lb);
     memcpy(tab.data(), pl.probs.data(), pb);
     memcpy(tab.data() + pb, pl.fbase.data(), lb);
     memcpy(tab.data() + pb + lb, pl.tbase.data(), lb);
@@ -1110,6 +1217,7 @@ static int plan_reserve(Plan &pl, cudaStream_t s) {
     memcpy(tab.data() + pb + 2 * lb + fb, pl.rbase.data(), lb);
     memcpy(tab.data() + pb + 3 * lb + fb, pl.zbase.data(), lb);
     memcpy(tab.data() + pb + 4 * lb + fb, pl.ybase.data(), lb);
+    memcpy(tab.data() + pb + 5 * lb + fb, pl.pbase.data(), lb);
     if (pl.uploaded_to == pl.tables.p && pl.uploaded == tab) return SDF_OK;
     if (pl.pageable) {
         pl.uploaded.swap(tab);
@@ -1152,6 +1260,10 @@ struct Scratch {  // device pointers used by one launch of the pipeline
     const long long *rbase = nullptr, *zbase = nullptr, *ybase = nullptr;
     long long r_tot = 0, z_tot = 0, y_tot = 0;
     int8_t *rowsign = nullptr;
+    // the paper's schedule (null keys: the tile path)
+    const long long *pbase = nullptr;
+    long long p_tot = 0;
+    unsigned long long *keys = nullptr;
 };
 
 static Scratch plan_scratch(const Plan &pl) {
@@ -1160,6 +1272,12 @@ static Scratch plan_scratch(const Plan &pl) {
     sc.probs = reinterpret_cast<const Prob *>(t);
     sc.fbase = reinterpret_cast<const long long *>(t + sizeof(Prob) * pl.n);
     sc.tbase = sc.fbase + pl.n + 1;
+    if (pl.cell_loop) {
+        sc.pbase = reinterpret_cast<const long long *>(reinterpret_cast<const char *>(sc.tbase + pl.n + 1) +
+                                                       sizeof(FillProb) * pl.n) + 3 * (pl.n + 1);
+        sc.p_tot = pl.p_tot;
+        sc.keys = pl.keys.as<unsigned long long>();
+    }
     if (pl.fill) {
         sc.fprobs = reinterpret_cast<const FillProb *>(sc.tbase + pl.n + 1);
         sc.rbase = reinterpret_cast<const long long *>(sc.fprobs + pl.n);
@@ -1237,8 +1355,40 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
     return SDF_OK;
 }
 
+// the paper's schedule: clear the keys, one thread per region, decode, FP64 re-decision (and the fill)
+static int launch_cell_loop(int n, long long f_tot, const Scratch &sc, cudaStream_t s, cudaEvent_t *ev) {
+    if (ev) SDF_TRY(record_event(ev[0], s));
+    SDF_TRY(cudaMemsetAsync(sc.keys, 0xff, sizeof(unsigned long long) * (size_t)sc.p_tot, s));
+    SDF_TRY(cudaMemsetAsync(&sc.ctr->nb_status, 0, sizeof(unsigned), s));
+    SDF_TRY(cudaMemsetAsync(&sc.ctr->n_candidates, 0, 6 * sizeof(unsigned long long), s));
+    if (ev) SDF_TRY(record_event(ev[1], s));
+    k_cell_loop<<<nblk(f_tot, 128), 128, 0, s>>>(sc.probs, sc.fbase, sc.pbase, n, f_tot, sc.keys, sc.ctr);
+    SDF_LAUNCHED(1);
+    SDF_TRY(cudaGetLastError());
+    Outputs o;
+    o.pairs = nullptr;
+    o.bin_start = nullptr;
+    o.pair_cap = 0;
+    o.patch = sc.patch;
+    o.patch_cap = sc.patch_cap;
+    o.ctr = sc.ctr;
+    k_decode_keys<<<16 * num_sms(), 256, 0, s>>>(sc.probs, sc.pbase, n, sc.p_tot, sc.keys, o);
+    SDF_LAUNCHED(1);
+    SDF_TRY(cudaGetLastError());
+    if (ev) SDF_TRY(record_event(ev[2], s));
+    k_patch<<<4 * num_sms(), 256, 0, s>>>(sc.probs, o);
+    SDF_LAUNCHED(1);
+    SDF_TRY(cudaGetLastError());
+    if (sc.fprobs)
+        SDF_TRY(fill_sign(sc.fprobs, sc.rbase, sc.zbase, sc.ybase, n, sc.r_tot, sc.z_tot, sc.y_tot, sc.rowsign,
+                          num_sms(), s));
+    if (ev) SDF_TRY(record_event(ev[3], s));
+    return SDF_OK;
+}
+
 static int launch_any(int shape, int n, long long f_tot, int64_t n_tiles, const Scratch &sc, cudaStream_t s,
                       cudaEvent_t *ev) {
+    if (sc.keys) return launch_cell_loop(n, f_tot, sc, s, ev);
     switch (shape) {
     case 1: return launch_shape<4, 4>(n, f_tot, n_tiles, sc, s, ev);
     case 2: return launch_shape<16, 8>(n, f_tot, n_tiles, sc, s, ev);
@@ -1349,7 +1499,7 @@ int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const floa
     for (int p = 0; p < n; p++)
         if (!feats[p] || !out_dist[p]) return SDF_ERR_INVALID_ARG;
     const bool sync = !(flags & SDF_FLAG_NO_SYNC), timing = (flags & SDF_FLAG_TIMING) != 0;
-    const bool fill = (flags & SDF_FLAG_FILL_SIGN) != 0;
+    const bool fill = (flags & SDF_FLAG_FILL_SIGN) != 0, cell_loop = (flags & SDF_FLAG_CELL_LOOP) != 0;
     if (n == 1) {  // a batch of one, with the plan (and its scratch) cached in the handle
         sdf_features_s *f = feats[0];
         if (!f->plan) {
@@ -1358,6 +1508,7 @@ int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const floa
             f->plan->events = f;
         }
         Plan &pl = *f->plan;
+        pl.cell_loop = cell_loop;
         SDF_TRY_ST(plan_describe(pl, feats, grids, band_w, 1, out_dist, out_winner, 0, fill));
         return plan_execute(pl, feats, s, sync, timing);
     }
@@ -1369,6 +1520,7 @@ int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const floa
     }
     Plan pl;
     pl.pageable = true;
+    pl.cell_loop = cell_loop;
     int st = plan_describe(pl, feats, grids, band_w, n, out_dist, out_winner, shape, fill);
     if (!st) st = plan_execute(pl, feats, s, true, false);
     // the temporary plan's memory returns to the pool in stream order
@@ -1404,6 +1556,7 @@ extern "C" int sdf_batch_create(const sdf_features *feats, const sdf_grid *grids
     double best_ms = 0.0;
     const int n_try = (flags & SDF_FLAG_AUTOTUNE) ? N_SHAPES : 1;
     const bool fill = (flags & SDF_FLAG_FILL_SIGN) != 0;
+    b->plan.cell_loop = (flags & SDF_FLAG_CELL_LOOP) != 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int st = SDF_OK;
     if (n_try > 1 && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = SDF_ERR_CUDA;

@@ -232,3 +232,20 @@ def test_adjoint_matches_oracle_adjoint():
         b = go[om.soup_vid()]
         rel = np.linalg.norm(a - b) / np.linalg.norm(b)
         assert rel < 1e-3, rel
+
+
+def test_pair_list_overflow_is_retried():
+    """Few large triangles on a fine grid: the first launch overflows the initial (tile, region)
+    pair list (sized from the feature count), and the call grows it and runs again."""
+    soup = meshgen.config_soup(1)  # 320 triangles, each about 50 cells wide at 512^3
+    N = 384
+    grid, w = sdf.Grid.cube(N), 3 / N
+    feats = sdf.sdf_build_features(torch.from_numpy(soup).cuda())
+    dist = sdf.sdf_narrow_band(feats, grid, w)
+    st = feats.status()
+    assert st["pairs"] > 8 * (feats.n_tri + feats.n_edge + feats.n_vert) + 4096  # beyond the first capacity
+    idx = parity.near_surface_indices(soup, (N, N, N), (0, 0, 0), grid.h, w, 20_000, 353_384, n_uniform=2000)
+    d_gpu = dist.view(-1)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    om = oracle.OracleMesh.from_soup(soup)
+    d_or, _, _ = om.band_points((N, N, N), (0, 0, 0), grid.h, w + 2 * grid.h, idx)
+    parity.assert_parity(parity.compare(d_gpu, d_or, w, grid.h))
