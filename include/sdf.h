@@ -93,6 +93,15 @@ typedef struct sdf_features_s *sdf_features;
                                         tile kernel; same regions, distances and FP64
                                         re-decision.  For the schedule comparison; needs
                                         8 bytes of scratch per grid point                    */
+#define SDF_FLAG_VERTEX_CONE 0x40u   /* with SDF_FLAG_CELL_LOOP: the paper's vertex extrusions
+                                        (Sections 3.3, 8.3): a cone of height w around N_alpha
+                                        opening to the most diverging face normal on the
+                                        positive side; convex vertices the positive cone,
+                                        concave the negative one, saddles both.  For the
+                                        coverage comparison: the paper leaves its correctness
+                                        open (Section 11.1), so gaps are possible            */
+#define SDF_FLAG_VERTEX_HEMISPHERE 0x80u /* with SDF_FLAG_CELL_LOOP: half-balls on the N_alpha
+                                        and -N_alpha sides (Section 4.3), same class rule    */
 
 /*
  * sdf_build_features -- mesh-connectivity stage (Section 7, Section 8).
@@ -153,7 +162,8 @@ int sdf_features_update_positions(sdf_features f, const float *vertices, void *s
  *   out_winner  host array [n] of device int32[nz][ny][nx] (winner feature
  *               id, -1 outside the band); the array or any entry may be NULL.
  *   flags       0, SDF_FLAG_NO_SYNC, SDF_FLAG_TIMING, SDF_FLAG_FILL_SIGN, SDF_FLAG_CELL_LOOP
- *               (any combination).
+ *               (any combination), and with SDF_FLAG_CELL_LOOP one of SDF_FLAG_VERTEX_CONE,
+ *               SDF_FLAG_VERTEX_HEMISPHERE.
  *               With SDF_FLAG_FILL_SIGN, points outside the band hold -inf inside the
  *               surface and +inf outside (Section 11.3's fill beyond the band): along each
  *               x-row a run of points outside the band takes the sign of the band point

@@ -21,7 +21,7 @@ from . import _buildlib
 __all__ = ["Grid", "Features", "sdf_build_features", "sdf_narrow_band", "sdf_narrow_band_backward",
            "SDFFunction", "Batch", "sdf_batch_create", "load_library", "kernel_launches", "SDFError",
            "FLAG_DISABLE_SADDLE", "FLAG_NO_SYNC", "FLAG_TIMING", "FLAG_AUTOTUNE", "FLAG_FILL_SIGN",
-           "FLAG_CELL_LOOP"]
+           "FLAG_CELL_LOOP", "FLAG_VERTEX_CONE", "FLAG_VERTEX_HEMISPHERE"]
 
 FLAG_DISABLE_SADDLE = 0x1
 FLAG_NO_SYNC = 0x2
@@ -29,6 +29,8 @@ FLAG_TIMING = 0x4
 FLAG_AUTOTUNE = 0x8
 FLAG_FILL_SIGN = 0x10
 FLAG_CELL_LOOP = 0x20
+FLAG_VERTEX_CONE = 0x40
+FLAG_VERTEX_HEMISPHERE = 0x80
 
 
 _STATUS_KEYS = ("candidates", "band_points", "fp64_points", "pairs", "rows", "rows_hit")

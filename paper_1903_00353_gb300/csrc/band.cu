@@ -71,7 +71,16 @@ struct Feat {
     const int4 *edge_vf;
     const float *vpos;
     int skip_saddle;
+    int vmode;  // vertex regions of the cell-loop schedule: VM_EXACT, VM_CONE or VM_HEMISPHERE
 };
+
+// Vertex extrusions (cell-loop schedule only).  VM_EXACT: the exact vertex region of the tile path.
+// VM_CONE: the paper's cone (Sections 3.3, 8.3): axis N_alpha, half-angle to the most diverging
+// face normal on the positive side of the pseudonormal plane, height w; convex vertices get the
+// positive cone, concave ones the negative cone (axis -N_alpha), saddles both (the negative one the
+// reflection of the positive one).  VM_HEMISPHERE: the half-balls on the N_alpha side and on the
+// -N_alpha side (Section 4.3), by the same class rule.
+enum { VM_EXACT = 0, VM_CONE = 1, VM_HEMISPHERE = 2 };
 
 struct PatchEntry {
     long long idx;  // linear grid index inside its problem
@@ -936,18 +945,57 @@ __device__ __forceinline__ bool region_contains(const Feat &F, const GridP &g, i
     }
 }
 
+// the paper's vertex extrusions: which sides the vertex gets, and the cone's cos(half-angle)
+__device__ __forceinline__ bool paper_vertex(const Feat &F, int id, bool &pos, bool &neg, float &cth, float3 &axis) {
+    const int8_t c = F.vert_class[id];
+    if (c == CLS_FLAT || (F.skip_saddle && c == CLS_SADDLE)) return false;
+    pos = c == CLS_CONVEX || c == CLS_SADDLE;
+    neg = c == CLS_CONCAVE || c == CLS_SADDLE;
+    axis = f3(__ldg(F.vert_rec + 3 * id + 1));  // unit N_alpha
+    cth = 1.f;
+    if (F.vmode == VM_CONE) {  // most diverging face normal among those on the positive side
+        const int s0 = F.vert_start[id], s1 = F.vert_start[id + 1];
+        for (int i = s0; i < s1; i++) {
+            const float cn = dot3(f3(__ldg(F.face_rec + 4 * (F.vert_corner[i] / 3))), axis);
+            if (cn > 0.f) cth = fminf(cth, cn);
+        }
+    } else {
+        cth = 0.f;  // hemisphere: angle 90 degrees
+    }
+    return pos || neg;
+}
+
 template <int TYPE>
 __device__ __forceinline__ unsigned walk_region(const Feat &F, const GridP &g, int id, int fid,
                                                 unsigned long long *keys) {
     int i0, i1, j0, j1, k0, k1;
-    if (!feature_box<TYPE>(F, g, id, i0, i1, j0, j1, k0, k1)) return 0;
+    bool vpos = false, vneg = false;
+    float vcth = 0.f;
+    float3 vaxis = make_float3(0.f, 0.f, 0.f), vv = vaxis;
+    if (TYPE == VERT && F.vmode != VM_EXACT) {
+        if (!paper_vertex(F, id, vpos, vneg, vcth, vaxis)) return 0;
+        vv = f3(__ldg(F.vert_rec + 3 * id));
+        const float R = g.W + g.eps + g.eps;
+        if (!to_index_box(vv.x - R, vv.y - R, vv.z - R, vv.x + R, vv.y + R, vv.z + R, g, i0, i1, j0, j1, k0, k1))
+            return 0;
+    } else if (!feature_box<TYPE>(F, g, id, i0, i1, j0, j1, k0, k1)) {
+        return 0;
+    }
     unsigned cand = 0;
     for (int k = k0; k <= k1; k++)
         for (int j = j0; j <= j1; j++)
             for (int i = i0; i <= i1; i++) {
                 const float3 p = make_float3(fmaf((float)i + 0.5f, g.h, g.ox), fmaf((float)j + 0.5f, g.h, g.oy),
                                              fmaf((float)k + 0.5f, g.h, g.oz));
-                if (!region_contains<TYPE>(F, g, id, p)) continue;
+                if (TYPE == VERT && F.vmode != VM_EXACT) {
+                    const float3 u = p - vv;
+                    const float R = g.W + g.eps, lu2 = dot3(u, u);
+                    if (lu2 > R * R) continue;
+                    const float ua = dot3(u, vaxis), lim = sqrtf(lu2) * vcth - g.eps;
+                    if (!((vpos && ua >= lim) || (vneg && -ua >= lim))) continue;
+                } else if (!region_contains<TYPE>(F, g, id, p)) {
+                    continue;
+                }
                 bool neg;
                 const float d = eval_point<TYPE>(F, g, id, i, j, k, neg);
                 if (d < g.W) {
@@ -1048,6 +1096,7 @@ static Feat make_feat(const sdf_features_s *f) {
     F.face_vid = f->face_vid; F.face_edge = f->face_edge; F.vert_start = f->vert_start;
     F.vert_corner = f->vert_corner; F.edge_vf = f->edge_vf; F.vpos = f->vpos;
     F.skip_saddle = (f->flags & SDF_FLAG_DISABLE_SADDLE) ? 1 : 0;
+    F.vmode = VM_EXACT;
     return F;
 }
 
@@ -1101,6 +1150,7 @@ struct Plan {
     long long r_tot = 0, z_tot = 0, y_tot = 0;
     // the paper's schedule (SDF_FLAG_CELL_LOOP): prefix sums of grid points, one key per point
     bool cell_loop = false;
+    int vmode = VM_EXACT;
     std::vector<long long> pbase;
     long long p_tot = 0;
     DevBuf tables, bins, pairs, patch, scan_tmp, lists, rowsign, keys;
@@ -1162,6 +1212,7 @@ static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *gr
         int st = make_grid(grids[p], band_w[p], shape, pr.g);
         if (st) return st;
         pr.F = make_feat(feats[p]);
+        pr.F.vmode = pl.vmode;
         pr.dist = out_dist[p];
         pr.winner = out_winner ? out_winner[p] : nullptr;
         pr.vec = ((pr.g.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(pr.dist) & 15) == 0) &&
@@ -1500,6 +1551,9 @@ int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const floa
         if (!feats[p] || !out_dist[p]) return SDF_ERR_INVALID_ARG;
     const bool sync = !(flags & SDF_FLAG_NO_SYNC), timing = (flags & SDF_FLAG_TIMING) != 0;
     const bool fill = (flags & SDF_FLAG_FILL_SIGN) != 0, cell_loop = (flags & SDF_FLAG_CELL_LOOP) != 0;
+    const int vmode = (flags & SDF_FLAG_VERTEX_CONE) ? VM_CONE : ((flags & SDF_FLAG_VERTEX_HEMISPHERE) ? VM_HEMISPHERE : VM_EXACT);
+    if (vmode != VM_EXACT && (!cell_loop || (flags & SDF_FLAG_VERTEX_CONE && flags & SDF_FLAG_VERTEX_HEMISPHERE)))
+        return SDF_ERR_INVALID_ARG;  // the paper's vertex extrusions exist in the cell-loop schedule only
     if (n == 1) {  // a batch of one, with the plan (and its scratch) cached in the handle
         sdf_features_s *f = feats[0];
         if (!f->plan) {
@@ -1509,6 +1563,7 @@ int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const floa
         }
         Plan &pl = *f->plan;
         pl.cell_loop = cell_loop;
+        pl.vmode = vmode;
         SDF_TRY_ST(plan_describe(pl, feats, grids, band_w, 1, out_dist, out_winner, 0, fill));
         return plan_execute(pl, feats, s, sync, timing);
     }
@@ -1521,6 +1576,7 @@ int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const floa
     Plan pl;
     pl.pageable = true;
     pl.cell_loop = cell_loop;
+    pl.vmode = vmode;
     int st = plan_describe(pl, feats, grids, band_w, n, out_dist, out_winner, shape, fill);
     if (!st) st = plan_execute(pl, feats, s, true, false);
     // the temporary plan's memory returns to the pool in stream order
@@ -1557,6 +1613,11 @@ extern "C" int sdf_batch_create(const sdf_features *feats, const sdf_grid *grids
     const int n_try = (flags & SDF_FLAG_AUTOTUNE) ? N_SHAPES : 1;
     const bool fill = (flags & SDF_FLAG_FILL_SIGN) != 0;
     b->plan.cell_loop = (flags & SDF_FLAG_CELL_LOOP) != 0;
+    b->plan.vmode = (flags & SDF_FLAG_VERTEX_CONE) ? VM_CONE : ((flags & SDF_FLAG_VERTEX_HEMISPHERE) ? VM_HEMISPHERE : VM_EXACT);
+    if (b->plan.vmode != VM_EXACT && (!b->plan.cell_loop || (flags & SDF_FLAG_VERTEX_CONE && flags & SDF_FLAG_VERTEX_HEMISPHERE))) {
+        delete b;
+        return SDF_ERR_INVALID_ARG;
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int st = SDF_OK;
     if (n_try > 1 && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = SDF_ERR_CUDA;
