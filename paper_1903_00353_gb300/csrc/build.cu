@@ -418,6 +418,55 @@ __global__ void k_vertex_records(const int32_t *vert_start, const int32_t *vert_
     cvx = !gor8(!cvx);
     ccv = !gor8(!ccv);
     cmin = gmin8(cmin);
+    // Bound of the vertex region {y : y.e_j <= 0}.  Locally convex (every incident edge below every
+    // incident face plane): the cone spanned by the face normals; locally concave: by their
+    // negatives; otherwise the extreme rays are searched among +-(e_j x e_l): the deg (deg - 1) / 2
+    // plane pairs are spread over the group's 8 lanes, and each candidate ray is tested against
+    // every plane without early exit, so the lanes of a group stay converged.  A cone is kept only
+    // if all its rays lie within 89 degrees of +N_alpha (or of -N_alpha).  The flags and bounds
+    // below are uniform over the 8 lanes of a vertex after the group reductions.
+    const int deg = s1 - s0;
+    const bool conv_cone = cvx && !ccv && cmin > 0.02f, conc_cone = ccv && !cvx && cmin > 0.02f;
+    const bool search = valid && Nlen > 0.f && !conv_cone && !conc_cone && deg <= 24;
+    bool any = false, all_pos = true, all_neg = true;
+    float cpos = 1.f, cng = 1.f;
+    if (search) {
+        const int npairs = deg * (deg - 1) / 2;
+        for (int pidx = sub; pidx < npairs; pidx += VL) {
+            int a = 0, rem = pidx;  // pair pidx = (a, b), a < b, in row-major order
+            while (rem >= deg - 1 - a) {
+                rem -= deg - 1 - a;
+                a++;
+            }
+            const int b = a + 1 + rem;
+            float3 y = cross3(f3(vert_plane[s0 + a]), f3(vert_plane[s0 + b]));  // planes hold -e
+            const float ly = sqrtf(dot3(y, y));
+            const bool ok = ly > 1e-6f;
+            y = (ok ? 1.f / ly : 0.f) * y;
+            bool fp = ok, fn = ok;  // +y and -y feasible
+            for (int m = s0; m < s1; m++) {
+                const float dm = dot3(y, f3(vert_plane[m]));
+                fp = fp && dm >= -1e-4f;
+                fn = fn && -dm >= -1e-4f;
+            }
+            const float cc = dot3(y, Nu);
+            if (fp) {
+                any = true;
+                if (cc > 0.02f) cpos = fminf(cpos, cc); else all_pos = false;
+                if (cc < -0.02f) cng = fminf(cng, -cc); else all_neg = false;
+            }
+            if (fn) {
+                any = true;
+                if (-cc > 0.02f) cpos = fminf(cpos, -cc); else all_pos = false;
+                if (-cc < -0.02f) cng = fminf(cng, cc); else all_neg = false;
+            }
+        }
+    }
+    any = gor8(any);
+    all_pos = !gor8(!all_pos);
+    all_neg = !gor8(!all_neg);
+    cpos = gmin8(cpos);
+    cng = gmin8(cng);
     int8_t my_cls = 99;  // class of the vertex held by lane sub == 0
     if (valid && sub == 0) {
         if (unsure) {  // FP64 filtered predicate (rare): recompute N_alpha and the signs in FP64
@@ -446,43 +495,12 @@ __global__ void k_vertex_records(const int32_t *vert_start, const int32_t *vert_
         }
         const int8_t cls = below && above ? CLS_SADDLE : (below ? CLS_CONVEX : (above ? CLS_CONCAVE : CLS_FLAT));
         vert_class[v] = cls;
-        // Bound of the vertex region {y : y.e_j <= 0}.  Locally convex (every incident edge below
-        // every incident face plane): the cone spanned by the face normals; locally concave: by
-        // their negatives; otherwise the extreme rays are searched among +-(e_j x e_l).  A cone
-        // is kept only if all its rays lie within 89 degrees of +N_alpha (or of -N_alpha).
         float4 cone = make_float4(0.f, 0.f, 0.f, -2.f);
-        const int deg = s1 - s0;
         if (Nlen > 0.f) {
-            if (cvx && !ccv && cmin > 0.02f) {
-                cone = make_float4(Nu.x, Nu.y, Nu.z, cmin - 2e-3f);
-            } else if (ccv && !cvx && cmin > 0.02f) {
-                cone = make_float4(-Nu.x, -Nu.y, -Nu.z, cmin - 2e-3f);
-            } else if (deg <= 24) {
-                bool any = false, all_pos = true, all_neg = true;
-                float cpos = 1.f, cng = 1.f;
-                for (int a = s0; a < s1; a++) {
-                    const float3 ea = f3(vert_plane[a]);  // -e_a
-                    for (int b = a + 1; b < s1; b++) {
-                        const float3 eb = f3(vert_plane[b]);
-                        float3 y = cross3(ea, eb);
-                        const float ly = sqrtf(dot3(y, y));
-                        if (!(ly > 1e-6f)) continue;
-                        y = (1.f / ly) * y;
-                        for (int sg = 0; sg < 2; sg++) {
-                            const float3 ys = sg ? make_float3(-y.x, -y.y, -y.z) : y;
-                            bool feas = true;
-                            for (int m = s0; m < s1 && feas; m++) feas = dot3(ys, f3(vert_plane[m])) >= -1e-4f;
-                            if (!feas) continue;
-                            any = true;
-                            const float cc = dot3(ys, Nu);
-                            if (cc > 0.02f) cpos = fminf(cpos, cc); else all_pos = false;
-                            if (cc < -0.02f) cng = fminf(cng, -cc); else all_neg = false;
-                        }
-                    }
-                }
-                if (any && all_pos) cone = make_float4(Nu.x, Nu.y, Nu.z, cpos - 2e-3f);
-                else if (any && all_neg) cone = make_float4(-Nu.x, -Nu.y, -Nu.z, cng - 2e-3f);
-            }
+            if (conv_cone) cone = make_float4(Nu.x, Nu.y, Nu.z, cmin - 2e-3f);
+            else if (conc_cone) cone = make_float4(-Nu.x, -Nu.y, -Nu.z, cmin - 2e-3f);
+            else if (search && any && all_pos) cone = make_float4(Nu.x, Nu.y, Nu.z, cpos - 2e-3f);
+            else if (search && any && all_neg) cone = make_float4(-Nu.x, -Nu.y, -Nu.z, cng - 2e-3f);
         }
         vert_rec[3 * v + 0] = make_float4(p.x, p.y, p.z, __int_as_float(s0));
         vert_rec[3 * v + 1] = make_float4(Nu.x, Nu.y, Nu.z, __int_as_float(s1 - s0));
