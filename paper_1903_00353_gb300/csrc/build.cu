@@ -5,10 +5,10 @@
 //        --> face / edge / vertex records (normals, side planes, pseudonormals, classes)
 //
 // Welding (Section 7.2).  The paper sorts 30-bit Morton codes and then groups identical
-// vertices serially inside each equal-code run.  Here the sort key is 48 bits: the 30-bit Morton
-// code of the quantised position (over the soup's bounding box, Section 7.1) in the high bits and
-// an 18-bit hash of the exact coordinate bits in the low bits, so equal vertices always share a
-// key and distinct vertices rarely do.  Runs of equal keys holding different coordinates (hash
+// vertices serially inside each equal-code run.  Here the sort key is 40 bits (five 8-bit radix
+// passes): the 30-bit Morton code of the quantised position (over the soup's bounding box,
+// Section 7.1) in the high bits and a 10-bit hash of the exact coordinate bits in the low bits, so
+// equal vertices always share a key and distinct vertices rarely do.  Runs of equal keys holding different coordinates (hash
 // collisions, or distinct vertices in one Morton cell) are re-ordered by exact coordinates by one
 // thread per such run, the only serial step left of the paper's fix-up.
 //
@@ -91,7 +91,7 @@ __global__ void k_weld_keys(const float *soup, int64_t n3, const float *bb, uint
     }
     uint64_t morton = (uint64_t)(expand10(q[0]) | (expand10(q[1]) << 1) | (expand10(q[2]) << 2));
     uint64_t hsh = mix64(((uint64_t)__float_as_uint(x) << 32 | __float_as_uint(y)) ^ mix64(__float_as_uint(z) + 0x9e3779b97f4a7c15ull));
-    keys[s] = (morton << 18) | (hsh & ((1ull << 18) - 1));  // 48-bit key: 6 radix passes
+    keys[s] = (morton << 10) | (hsh & ((1ull << 10) - 1));  // 40-bit key: 5 radix passes
     vals[s] = (uint32_t)s;
 }
 
@@ -608,7 +608,7 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     k_weld_keys<<<nblk(n), BT, 0, s>>>(soup, n, bb, keys, vals);
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
-    B_TRY(radix_sort_u64(keys, vals, kalt, valt, n, 48, rtmp, s));
+    B_TRY(radix_sort_u64(keys, vals, kalt, valt, n, 40, rtmp, s));
     k_weld_fix<<<nblk(n), BT, 0, s>>>(keys, vals, soup, n);
     SDF_LAUNCHED(1);
     k_weld_heads<<<nblk(n), BT, 0, s>>>(keys, vals, soup, n, valt);
