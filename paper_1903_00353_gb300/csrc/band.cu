@@ -342,15 +342,17 @@ __device__ __forceinline__ float eval_any(const Feat &F, const GridP &g, int typ
 // region, and a point outside the exact vertex region has a strictly closer point on an incident
 // edge.  Faces have 5 planes, edges 4.
 constexpr int KMAX = 6, MAXVP = 6;
+constexpr float Q_NONE = 0.f, Q_EDGE = 1.f, Q_VERT = 2.f;  // kinds of quadratic row bound
 
 template <int TY, int TZ>
 struct TileSmem {
     unsigned long long key[TILE_X * TY * TZ];  // packed (|d| bits << 32 | id << 1 | sign) per tile point
     float4 coef[NT][KMAX];             // span coefficients (A, B, C, -): nl lower bounds, then upper bounds
-    float4 ball[NT];                   // vertex ball in index units (j_v, db0, dc0, R^2), R^2 < 0: none
-    uint4 rinfo[NT];                   // row set-up of each region, packed (see process_band_tile)
+    float4 quad[NT][2];                // quadratic bound of a region's rows: vertex ball, edge cylinder
+    uint2 rinfo[NT];                   // row set-up of each region, packed (see process_band_tile)
     int fid[NT];                       // regions of the current pass (global feature ids)
     unsigned char ax[NT];              // scan axis
+    unsigned char qkind[NT];           // kind of quadratic row bound: Q_NONE, Q_EDGE or Q_VERT
     unsigned rowq[NT / 32][64];        // per-warp ring of non-empty rows waiting for point evaluation
     int chunk_next;                    // next 32-region chunk of the tile to hand to a warp
     long long work;
@@ -469,7 +471,10 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int2 *pai
             const int loc = lc - (cx == 1 ? y0 : z0);
             const int nbc = max(nb, 1);
             int nl = 0, nu = 0;
-            float4 ballv = make_float4(0.f, 0.f, 0.f, -1.f);
+            // quadratic row bound in index units: vertex (j_v, db0, dc0, R^2); edge (Qa, Qb, Qc, R^2),
+            // (t_a, t_b, t_c, -) with Q the edge point a seen from the row origin; faces none (their
+            // slab planes bound the distance)
+            float4 q0v = make_float4(0.f, 0.f, 0.f, 0.f), q1v = make_float4(0.f, 0.f, 0.f, Q_NONE);
             if (nrows > 0) {
                 const float pb0 = fmaf((float)lb + 0.5f, g.h, comp3(org, bx));
                 const float pc0 = fmaf((float)lc + 0.5f, g.h, comp3(org, cx));
@@ -490,6 +495,14 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int2 *pai
                     add_coef(E, nl, nu, make_float4(-tt.x, -tt.y, -tt.z, tt.w + a.w), ax, bx, cx, pb0, pc0, K, g);
                     add_coef(E, nl, nu, __ldg(r + 2), ax, bx, cx, pb0, pc0, K, g);
                     add_coef(E, nl, nu, __ldg(r + 3), ax, bx, cx, pb0, pc0, K, g);
+                    // the wedge planes do not bound the distance to the edge line: add the cylinder
+                    // |(p - a) x t| <= W (+ tolerance and a slack of 1/64 cell), which only removes
+                    // points the merge would reject (d >= W)
+                    const float3 av = f3(a), tv = f3(tt);
+                    const float Rs = (g.W + g.eps) * g.inv_h + 1.f / 64.f;
+                    q0v = make_float4((comp3(org, ax) - comp3(av, ax)) * g.inv_h + 0.5f + (float)la,
+                                      (pb0 - comp3(av, bx)) * g.inv_h, (pc0 - comp3(av, cx)) * g.inv_h, Rs * Rs);
+                    q1v = make_float4(comp3(tv, ax), comp3(tv, bx), comp3(tv, cx), Q_EDGE);
                 } else {
                     const float4 v = __ldg(F.vert_rec + 3 * id), nv = __ldg(F.vert_rec + 3 * id + 1);
                     const int s0 = __float_as_int(v.w), cnt = min(__float_as_int(nv.w), MAXVP);
@@ -497,17 +510,20 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int2 *pai
                         add_coef(E, nl, nu, __ldg(F.vert_plane + s0 + k), ax, bx, cx, pb0, pc0, K, g);
                     const float3 vv = f3(v);
                     const float Rh = (g.W + g.eps) * g.inv_h;
-                    ballv = make_float4((comp3(vv, ax) - comp3(org, ax)) * g.inv_h - 0.5f - (float)la,
-                                        (pb0 - comp3(vv, bx)) * g.inv_h, (pc0 - comp3(vv, cx)) * g.inv_h, Rh * Rh);
+                    q0v = make_float4((comp3(vv, ax) - comp3(org, ax)) * g.inv_h - 0.5f - (float)la,
+                                      (pb0 - comp3(vv, bx)) * g.inv_h, (pc0 - comp3(vv, cx)) * g.inv_h, Rh * Rh);
+                    q1v.w = Q_VERT;
                 }
             }
             for (int k = nl; k < KMAX - nu; k++) S.coef[t][k] = make_float4(1e30f, 0.f, 0.f, 0.f);
-            S.ball[t] = ballv;
-            // rinfo: y = nb | nl << 8 | span_hi << 12 | lo_a << 17 | lo_b << 22 | lo_c << 27 (tile-local,
-            // 5 bits each), z = 1 / nb
-            S.rinfo[t] = make_uint4(0u, (unsigned)(nbc | (nl << 8) | (max(ha - la, 0) << 12) | (loa << 17) |
-                                                   (lob << 22) | (loc << 27)),
-                                    __float_as_uint(1.f / (float)nbc), 0u);
+            S.quad[t][0] = q0v;
+            S.quad[t][1] = q1v;
+            S.qkind[t] = (unsigned char)q1v.w;
+            // rinfo: x = nb | nl << 8 | span_hi << 12 | lo_a << 17 | lo_b << 22 | lo_c << 27 (tile-local,
+            // 5 bits each), y = 1 / nb
+            S.rinfo[t] = make_uint2((unsigned)(nbc | (nl << 8) | (max(ha - la, 0) << 12) | (loa << 17) | (lob << 22) |
+                                               (loc << 27)),
+                                    __float_as_uint(1.f / (float)nbc));
         }
         // rows of the warp's regions, numbered by a warp scan
         const int incl = warp_incl_scan(nrows);
@@ -521,10 +537,10 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int2 *pai
             const int reg = warp * 32 + own;
             int len = 0, packed = 0;
             if (r < R) {
-                const uint4 ri = S.rinfo[reg];
-                const int nbv = (int)(ri.y & 255u), nl = (int)((ri.y >> 8) & 15u);
+                const uint2 ri = S.rinfo[reg];
+                const int nbv = (int)(ri.x & 255u), nl = (int)((ri.x >> 8) & 15u);
                 const int local = r - r0;
-                const int ic = (int)(((float)local + 0.5f) * __uint_as_float(ri.z));  // exact for these sizes
+                const int ic = (int)(((float)local + 0.5f) * __uint_as_float(ri.y));  // exact for these sizes
                 const int ib = local - ic * nbv;
                 const float fb = (float)ib, fc = (float)ic;
                 float lo_f = -1e30f, hi_f = 1e30f;
@@ -537,8 +553,9 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int2 *pai
                     if (k < nl) lo_f = fmaxf(lo_f, v);
                     else hi_f = fminf(hi_f, v);
                 }
-                const float4 bl = S.ball[reg];
-                if (bl.w >= 0.f) {
+                const int qk = S.qkind[reg];
+                if (qk == (int)Q_VERT) {  // ball around the vertex
+                    const float4 bl = S.quad[reg][0];
                     const float db = bl.y + fb, dc = bl.z + fc;
                     const float q2 = bl.w - db * db - dc * dc;
                     if (q2 < 0.f) {
@@ -548,16 +565,41 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int2 *pai
                         lo_f = fmaxf(lo_f, bl.x - sq);
                         hi_f = fminf(hi_f, bl.x + sq);
                     }
+                } else if (qk == (int)Q_EDGE && hi_f - lo_f > 2.f) {
+                    // cylinder around the edge line, c2 j^2 + c1 j + c0 <= 0: only for spans of more than
+                    // a few points (long spans come from wide wedges, whose planes leave the radius open)
+                    const float4 cq = S.quad[reg][0], q1 = S.quad[reg][1];
+                    const float ub = cq.y + fb, uc = cq.z + fc;
+                    const float k0 = fmaf(q1.x, cq.x, fmaf(q1.y, ub, q1.z * uc));
+                    const float c2 = fmaf(-q1.x, q1.x, 1.f);
+                    const float c1 = 2.f * fmaf(-q1.x, k0, cq.x);
+                    const float c0 = fmaf(cq.x, cq.x, fmaf(ub, ub, fmaf(uc, uc, fmaf(-k0, k0, -cq.w))));
+                    if (c2 > 1e-6f) {
+                        const float disc = fmaf(c1, c1, -4.f * c2 * c0);
+                        if (disc < 0.f) {
+                            open = false;
+                        } else {  // roots by the cancellation-free form
+                            const float qq = -0.5f * (c1 + copysignf(sqrtf(disc), c1));
+                            const float r1 = qq / c2, r2 = qq != 0.f ? c0 / qq : r1;
+                            lo_f = fmaxf(lo_f, fminf(r1, r2));
+                            hi_f = fminf(hi_f, fmaxf(r1, r2));
+                        }
+                    } else if (c1 == 0.f || fabsf(c1) < 1e-6f) {  // the edge runs along the row
+                        if (c0 > 0.f) open = false;
+                    } else {  // linear: c1 j + c0 <= 0
+                        const float r = -c0 / c1;
+                        if (c1 > 0.f) hi_f = fminf(hi_f, r); else lo_f = fmaxf(lo_f, r);
+                    }
                 }
                 const float sl = 1.f / 4096.f;
-                const float span_hi = (float)((ri.y >> 12) & 31u);
+                const float span_hi = (float)((ri.x >> 12) & 31u);
                 const float fa = fminf(fmaxf(lo_f - sl, 0.f), span_hi + 1.f);
                 const float fz = fmaxf(fminf(hi_f + sl, span_hi), -1.f);
                 const int ja = (int)ceilf(fa), jb = (int)floorf(fz);
                 len = open ? max(jb - ja + 1, 0) : 0;
                 // row record: slot | start along a << 8 | len << 13 | b << 19 | c << 24 (tile-local)
-                packed = reg | ((int)((ri.y >> 17) & 31u) + ja) << 8 | (len << 13) |
-                         (((int)((ri.y >> 22) & 31u) + ib) << 19) | (((int)(ri.y >> 27) + ic) << 24);
+                packed = reg | ((int)((ri.x >> 17) & 31u) + ja) << 8 | (len << 13) |
+                         (((int)((ri.x >> 22) & 31u) + ib) << 19) | (((int)(ri.x >> 27) + ic) << 24);
                 rows++;
                 hits += len > 0;
             }
