@@ -57,7 +57,7 @@ WORKLOADS = {
                   desc="shape fitting: displaced icosphere nu=100 (200,000 triangles), grid 512^3, band 4h; "
                        "one plain gradient-descent step on the welded vertices of "
                        "sum_band (d - d_ellipsoid(0.35, 0.25, 0.2))^2 (position update, forward with winner "
-                       "checkpoint, loss, adjoint)"),
+                       "checkpoint, fused loss and gradient, adjoint)"),
 }
 FIT_LR = 1e-4  # fixed learning rate of the shape-fitting workload
 
@@ -267,24 +267,28 @@ def run_fit(args, wl, sdf, soup_np, soup, grid, w, N, dev, world, rank):
     import torch.distributed as tdist
     target = ellipsoid_target(N, dev)
     feats = sdf.sdf_build_features(soup)
-    X = feats.vertices().clone().requires_grad_(True)
+    X = feats.vertices().clone()
+    dist = torch.empty(grid.shape, dtype=torch.float32, device=dev)
+    win = torch.empty(grid.shape, dtype=torch.int32, device=dev)
+    g = torch.empty_like(dist)
+    gv = torch.zeros_like(X)
 
     def fit_step(ev=None):
+        """Positions in, forward with winners, fused loss and gradient, vertex adjoint, update: all
+        in the library's kernels except the update (a 1 MB axpy)."""
         if ev:
             ev[0].record()
-        dist = sdf.SDFFunction.apply(X, feats, grid, w)
+        feats.update_positions(X)
+        sdf.sdf_narrow_band(feats, grid, w, out=dist, winner=win, flags=sdf.FLAG_NO_SYNC)
         if ev:
             ev[1].record()
-        band = torch.isfinite(dist)
-        d = torch.where(band, dist, target)
-        loss = ((d - target) ** 2).sum()
-        X.grad = None
-        loss.backward()
-        with torch.no_grad():
-            X.sub_(FIT_LR * X.grad)
+        loss, _, band = sdf.band_l2_loss(dist, target, grad=g)
+        gv.zero_()
+        sdf.sdf_narrow_band_backward(feats, grid, w, g, winner=win, grad_vertices=gv)
+        X.sub_(FIT_LR * gv)
         if ev:
             ev[2].record()
-        return loss.detach(), band.sum()
+        return loss, band
 
     losses = []
     for _ in range(args.warmup):
@@ -309,6 +313,7 @@ def run_fit(args, wl, sdf, soup_np, soup, grid, w, N, dev, world, rank):
             per.append(evs)
         torch.cuda.synchronize()
     launches = sdf.kernel_launches() - launches0
+    feats.status()  # raises if a forward without synchronisation outgrew its scratch
     times = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])] for e in per])
     total_ms = float(times.sum())
     if world > 1:
@@ -319,14 +324,13 @@ def run_fit(args, wl, sdf, soup_np, soup, grid, w, N, dev, world, rank):
     value = band_total * world / (total_ms / 1e3)
     loss_curve = [float(x) for x in losses]
     # end to end: vertex positions from pinned host memory each step, loss read back each step
-    Xh = X.detach().cpu().pin_memory()
+    Xh = X.cpu().pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_steps = max(3, min(args.steps, 10))
     e2e_band = 0
     for _ in range(e2e_steps):
-        with torch.no_grad():
-            X.copy_(Xh, non_blocking=True)
+        X.copy_(Xh, non_blocking=True)
         l, b = fit_step()
         e2e_band += int(b)
         float(l)

@@ -309,6 +309,18 @@ int sdf_batch_info(sdf_batch b, int32_t *tile_shape, double *tuned_ms);
 int sdf_batch_timing(sdf_batch b, float *ms);
 void sdf_batch_destroy(sdf_batch b);
 
+/*
+ * sdf_band_l2_loss -- the loss of the shape-fitting workload and its gradient in one pass (a project
+ * addition; the paper has no loss): L = sum over band points (finite d) of (d - target)^2, written
+ * to *loss_out (device double, overwritten), and dL/dd = 2 (d - target) on the band, 0 elsewhere,
+ * written to grad_out (device float[n], nullable), ready for sdf_narrow_band_backward; the number
+ * of band points to *band_out (device uint64, nullable, overwritten).
+ *   dist, target  device float[n]; n >= 0 points.
+ * No synchronisation.  Errors: SDF_ERR_INVALID_ARG, SDF_ERR_CUDA.
+ */
+int sdf_band_l2_loss(const float *dist, const float *target, int64_t n, float *grad_out, double *loss_out,
+                     unsigned long long *band_out, void *stream);
+
 /* Release the handle and its device memory (NULL is a no-op). */
 void sdf_features_destroy(sdf_features f);
 

@@ -19,7 +19,7 @@ import torch
 from . import _buildlib
 
 __all__ = ["Grid", "Features", "sdf_build_features", "sdf_narrow_band", "sdf_narrow_band_backward",
-           "SDFFunction", "Batch", "sdf_batch_create", "load_library", "kernel_launches", "SDFError",
+           "SDFFunction", "Batch", "sdf_batch_create", "band_l2_loss", "load_library", "kernel_launches", "SDFError",
            "FLAG_DISABLE_SADDLE", "FLAG_NO_SYNC", "FLAG_TIMING", "FLAG_AUTOTUNE", "FLAG_FILL_SIGN",
            "FLAG_CELL_LOOP", "FLAG_VERTEX_CONE", "FLAG_VERTEX_HEMISPHERE"]
 
@@ -88,12 +88,13 @@ def load_library(path: str | None = None):
     L.sdf_batch_status.argtypes = [P, ctypes.POINTER(I64), P]
     L.sdf_batch_info.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_double)]
     L.sdf_batch_timing.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+    L.sdf_band_l2_loss.argtypes = [P, P, I64, P, P, P, P]
     L.sdf_batch_destroy.argtypes = [P]
     L.sdf_batch_destroy.restype = None
     for name in ("sdf_build_features", "sdf_features_update_positions", "sdf_narrow_band",
                  "sdf_narrow_band_backward", "sdf_features_info", "sdf_features_vertex_map",
                  "sdf_features_vertices", "sdf_features_status", "sdf_batch_create", "sdf_batch_run",
-                 "sdf_batch_status", "sdf_batch_info", "sdf_batch_timing"):
+                 "sdf_batch_status", "sdf_batch_info", "sdf_batch_timing", "sdf_band_l2_loss"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -363,6 +364,24 @@ def sdf_narrow_band_backward(features: Features, grid: Grid, w: float, grad_dist
                                                    _ptr_array([grad_vertices]), flags, _stream(stream)),
            "sdf_narrow_band_backward")
     return grad_vertices
+
+
+def band_l2_loss(dist: torch.Tensor, target: torch.Tensor, grad: torch.Tensor | None = None, stream=None):
+    """L = sum over the band (finite dist) of (dist - target)^2 and dL/d dist (0 outside the band),
+    in one pass; returns (loss as a 0-d float64 CUDA tensor, grad, band point count as a 0-d int64
+    CUDA tensor)."""
+    d, t = _dev_f32(dist, "dist"), _dev_f32(target, "target")
+    if d.numel() != t.numel():
+        raise ValueError("dist and target differ in size")
+    if grad is None:
+        grad = torch.empty_like(d)
+    else:
+        _dev_f32(grad, "grad")
+    loss = torch.empty((), dtype=torch.float64, device=d.device)
+    band = torch.empty((), dtype=torch.int64, device=d.device)
+    _check(load_library().sdf_band_l2_loss(d.data_ptr(), t.data_ptr(), d.numel(), grad.data_ptr(),
+                                           loss.data_ptr(), band.data_ptr(), _stream(stream)), "sdf_band_l2_loss")
+    return loss, grad, band
 
 
 class SDFFunction(torch.autograd.Function):

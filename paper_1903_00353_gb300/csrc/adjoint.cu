@@ -284,3 +284,86 @@ extern "C" int sdf_narrow_band_backward(const sdf_features *feats, const sdf_gri
     }
     return SDF_OK;
 }
+
+// ----------------------------------------------------------------------------- band L2 loss
+// L = sum over band points of (d - target)^2 and its gradient dL/dd = 2 (d - target) on the band,
+// 0 elsewhere, in one pass over the grid (the loss of the shape-fitting workload; the paper has no
+// loss).  Points outside the band hold +-inf in d and contribute nothing.
+namespace sdf {
+namespace {
+__global__ void __launch_bounds__(256) k_band_l2(const float *dist, const float *target, int64_t n, float *grad,
+                                                 double *loss, unsigned long long *band, int vec) {
+    double acc = 0.0;
+    unsigned cnt = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (vec) {
+        const int64_t n4 = n / 4;
+        for (int64_t q = t0; q < n4; q += stride) {
+            const float4 d = __ldcs(reinterpret_cast<const float4 *>(dist) + q);
+            const float4 t = __ldcs(reinterpret_cast<const float4 *>(target) + q);
+            float4 gq;
+            const float dx = d.x - t.x, dy = d.y - t.y, dz = d.z - t.z, dw = d.w - t.w;
+            gq.x = isfinite(d.x) ? 2.f * dx : 0.f;
+            gq.y = isfinite(d.y) ? 2.f * dy : 0.f;
+            gq.z = isfinite(d.z) ? 2.f * dz : 0.f;
+            gq.w = isfinite(d.w) ? 2.f * dw : 0.f;
+            acc += (isfinite(d.x) ? (double)dx * dx : 0.0) + (isfinite(d.y) ? (double)dy * dy : 0.0) +
+                   (isfinite(d.z) ? (double)dz * dz : 0.0) + (isfinite(d.w) ? (double)dw * dw : 0.0);
+            cnt += isfinite(d.x) + isfinite(d.y) + isfinite(d.z) + isfinite(d.w);
+            if (grad) __stcs(reinterpret_cast<float4 *>(grad) + q, gq);
+        }
+        for (int64_t q = 4 * n4 + t0; q < n; q += stride) {  // tail of a length that is not a multiple of 4
+            const float d = dist[q], t = target[q], df = d - t;
+            if (grad) grad[q] = isfinite(d) ? 2.f * df : 0.f;
+            if (isfinite(d)) { acc += (double)df * df; cnt++; }
+        }
+    } else {
+        for (int64_t q = t0; q < n; q += stride) {
+            const float d = dist[q], t = target[q], df = d - t;
+            if (grad) grad[q] = isfinite(d) ? 2.f * df : 0.f;
+            if (isfinite(d)) { acc += (double)df * df; cnt++; }
+        }
+    }
+    // band points: one atomic per warp
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (band && (threadIdx.x & 31) == 0 && cnt) atomicAdd(band, (unsigned long long)cnt);
+    // block sum in FP64, one atomic per block
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double s_acc[8];
+    if ((threadIdx.x & 31) == 0) s_acc[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) b += s_acc[w];
+        atomicAdd(loss, b);
+    }
+}
+}  // namespace
+}  // namespace sdf
+
+extern "C" int sdf_band_l2_loss(const float *dist, const float *target, int64_t n, float *grad_out, double *loss_out,
+                                unsigned long long *band_out, void *stream) {
+    using namespace sdf;
+    if (!dist || !target || !loss_out || n < 0) return SDF_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    SDF_TRY(cudaMemsetAsync(loss_out, 0, sizeof(double), s));
+    if (band_out) SDF_TRY(cudaMemsetAsync(band_out, 0, sizeof(unsigned long long), s));
+    if (n == 0) return SDF_OK;
+    static int n_sm = 0;
+    if (!n_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 152;
+    }
+    const int vec = ((reinterpret_cast<uintptr_t>(dist) | reinterpret_cast<uintptr_t>(target) |
+                      reinterpret_cast<uintptr_t>(grad_out)) & 15) == 0;
+    int64_t blocks = (n / (vec ? 4 : 1) + 255) / 256;
+    if (blocks > 8 * (int64_t)n_sm) blocks = 8 * (int64_t)n_sm;
+    if (blocks < 1) blocks = 1;
+    k_band_l2<<<(unsigned)blocks, 256, 0, s>>>(dist, target, n, grad_out, loss_out, band_out, vec);
+    SDF_LAUNCHED(1);
+    SDF_TRY(cudaGetLastError());
+    return SDF_OK;
+}

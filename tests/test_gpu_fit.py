@@ -70,3 +70,47 @@ def test_fit_loss_decreases_and_gradient_matches_oracle():
             X -= lr * X.grad
     assert all(b <= a for a, b in zip(losses, losses[1:])), losses
     assert losses[-1] < 0.95 * losses[0], losses
+
+
+def test_band_l2_loss_matches_torch():
+    torch.manual_seed(3)
+    for n in (1, 7, 4096, 1_000_003):
+        d = torch.randn(n, device="cuda") * 0.01
+        d[torch.rand(n, device="cuda") < 0.6] = float("inf")
+        d[torch.rand(n, device="cuda") < 0.1] = float("-inf")
+        t = torch.randn(n, device="cuda") * 0.01
+        loss, g, band = sdf.band_l2_loss(d, t)
+        fin = torch.isfinite(d)
+        # the difference is taken in FP32 (as the gradient is), its square and the sum in FP64
+        ref = ((d[fin] - t[fin]).double() ** 2).sum()
+        assert abs(float(loss) - float(ref)) <= 1e-12 * max(1.0, float(ref))
+        ref64 = ((d[fin].double() - t[fin].double()) ** 2).sum()
+        assert abs(float(loss) - float(ref64)) <= 2e-7 * max(1e-30, float(ref64))
+        assert int(band) == int(fin.sum())
+        gref = torch.where(fin, 2.0 * (d - t), torch.zeros_like(d))
+        assert torch.allclose(g, gref, rtol=0, atol=1e-7)
+
+
+def test_fused_fit_step_matches_autograd_step():
+    """One step of the fused path (loss kernel + backward) gives the autograd step's gradient."""
+    soup = meshgen.icosphere(20, radius=0.3, displacement=0.02, seed=5).soup(seed=6)
+    N = 96
+    grid, w = sdf.Grid.cube(N), 4 / N
+    feats = sdf.sdf_build_features(torch.from_numpy(soup).cuda())
+    X = feats.vertices().clone()
+    c = (torch.arange(N, device="cuda", dtype=torch.float64) + 0.5) / N
+    Z, Y, Xc = torch.meshgrid(c, c, c, indexing="ij")
+    target = meshgen.ellipsoid_sdf_torch(torch.stack([Xc, Y, Z], dim=-1)).float()
+    # autograd
+    Xa = X.clone().requires_grad_(True)
+    dist = sdf.SDFFunction.apply(Xa, feats, grid, w)
+    band = torch.isfinite(dist)
+    ((torch.where(band, dist, target) - target) ** 2).sum().backward()
+    # fused
+    feats.update_positions(X)
+    d2, win = sdf.sdf_narrow_band(feats, grid, w, winner=True)
+    loss, g, nb = sdf.band_l2_loss(d2, target)
+    gv = sdf.sdf_narrow_band_backward(feats, grid, w, g, winner=win)
+    assert int(nb) == int(band.sum())
+    rel = float((gv - Xa.grad).norm() / Xa.grad.norm())
+    assert rel < 1e-5, rel
