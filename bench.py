@@ -437,21 +437,42 @@ def run_batch(args, wl, sdf, local, world, rank):
         plain.append(e0.elapsed_time(e1))
     plain_ms = float(np.mean(plain))
 
-    # end to end: soups from pinned host memory, 64 builds, one batched list call, all fields read back
+    # end to end: soups from pinned host memory, 64 builds, one batched list call, all fields read back;
+    # two output sets and two streams let the copy-out of step i overlap the work of step i + 1
     soups_host = [torch.from_numpy(s).pin_memory() for s, _, _ in problems]
     outs_host = [torch.empty(g.shape, dtype=torch.float32).pin_memory() for g in grids]
+    outs2 = [outs, [torch.empty_like(o) for o in outs]]
+    sc, sx = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    computed = [torch.cuda.Event(), torch.cuda.Event()]
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    handles = []
+
+    def e2e_step(i):
+        b = i & 1
+        with torch.cuda.stream(sc):
+            if i >= 2:
+                sc.wait_event(copied[b])
+            fl = [sdf.sdf_build_features(sh.to(dev, non_blocking=True), stream=sc) for sh in soups_host]
+            sdf.sdf_narrow_band(fl, grids, ws, out=outs2[b], stream=sc)
+            computed[b].record(sc)
+        with torch.cuda.stream(sx):
+            sx.wait_event(computed[b])
+            for oh, o in zip(outs_host, outs2[b]):
+                oh.copy_(o, non_blocking=True)
+            copied[b].record(sx)
+        handles.extend(fl)
+
+    for i in range(2):  # fill the two-stage pipeline
+        e2e_step(i)
     e2e_steps = 3
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        fl = [sdf.sdf_build_features(sh.to(dev, non_blocking=True)) for sh in soups_host]
-        sdf.sdf_narrow_band(fl, grids, ws, out=outs)
-        for oh, o in zip(outs_host, outs):
-            oh.copy_(o, non_blocking=True)
-        torch.cuda.synchronize()
-        for f in fl:
-            f.destroy()
+    for i in range(2, 2 + e2e_steps):
+        e2e_step(i)
+    torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    for f in handles:
+        f.destroy()
     e2e = {"value": band_points * e2e_steps * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(sum(s.nbytes for s, _, _ in problems)),
            "d2h_bytes_per_step": int(4 * grid_points)}
@@ -634,28 +655,58 @@ def main():
     value = band_total * args.steps / (total_ms / 1e3)
     build_ms, fwd_ms, adj_ms = (float(x) for x in per.mean(axis=0))
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: every step copies the soup in from
+    # pinned host memory and the field (and the vertex gradient) out to pinned host memory.  Two
+    # buffer sets and two streams let the copy-out of step i overlap the work of step i + 1.
     soup_host = torch.from_numpy(soup_np).pin_memory()
-    dist_host = torch.empty(grid.shape, dtype=torch.float32).pin_memory()
-    gv_host = torch.empty(max(1, gv.shape[0] if gv is not None else 1), 3, dtype=torch.float32).pin_memory()
+    sc, sx = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    dists = [dist, torch.empty_like(dist)]
+    wins = [win, torch.empty_like(win)] if win is not None else [None, None]
+    gvs = [gv, torch.empty_like(gv)] if gv is not None else [None, None]
+    dist_hosts = [torch.empty(grid.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+    gv_hosts = [torch.empty(gv.shape, dtype=torch.float32).pin_memory() for _ in range(2)] if gv is not None else None
+    computed = [torch.cuda.Event(), torch.cuda.Event()]
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    handles = []
+    if wl["adjoint"]:  # the loss's constant target (d = 0.01) and the gradient buffer
+        target = torch.full(grid.shape, 0.01, dtype=torch.float32, device=dev)
+        ge = torch.empty_like(dist)
+
+    def e2e_step(i):
+        b = i & 1
+        with torch.cuda.stream(sc):
+            if i >= 2:
+                sc.wait_event(copied[b])  # the copy-out of step i - 2 has left these buffers
+            s_dev = soup_host.to(dev, non_blocking=True)
+            f = sdf.sdf_build_features(s_dev, stream=sc)
+            sdf.sdf_narrow_band(f, grid, w, out=dists[b], winner=wins[b] if wins[b] is not None else False,
+                                flags=sched_flag, stream=sc)
+            if wl["adjoint"]:
+                sdf.band_l2_loss(dists[b], target, grad=ge, stream=sc)  # dL/dd of sum_band (d - 0.01)^2
+                gvs[b].zero_()
+                sdf.sdf_narrow_band_backward(f, grid, w, ge, winner=wins[b], grad_vertices=gvs[b], stream=sc)
+                if shard:
+                    slabs.all_reduce_sum(gvs[b])
+            computed[b].record(sc)
+        with torch.cuda.stream(sx):
+            sx.wait_event(computed[b])
+            dist_hosts[b].copy_(dists[b], non_blocking=True)
+            if gv is not None:
+                gv_hosts[b].copy_(gvs[b], non_blocking=True)
+            copied[b].record(sx)
+        handles.append(f)  # released after the timed loop (releasing synchronises the device)
+
+    for i in range(2):  # fill the two-stage pipeline
+        e2e_step(i)
     e2e_steps = max(3, min(args.steps, 10))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        s_dev = soup_host.to(dev, non_blocking=True)
-        f = sdf.sdf_build_features(s_dev)
-        sdf.sdf_narrow_band(f, grid, w, out=dist, winner=win if win is not None else False, flags=sched_flag)
-        if wl["adjoint"]:
-            ge = torch.where(torch.isfinite(dist), 2.0 * (dist - 0.01), torch.zeros_like(dist))
-            gv.zero_()
-            sdf.sdf_narrow_band_backward(f, grid, w, ge, winner=win, grad_vertices=gv)
-            if shard:
-                slabs.all_reduce_sum(gv)
-            gv_host.copy_(gv, non_blocking=True)
-        dist_host.copy_(dist, non_blocking=True)
-        torch.cuda.synchronize()
-        f.destroy()
+    for i in range(2, 2 + e2e_steps):
+        e2e_step(i)
+    torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    for f in handles:
+        f.destroy()
     e2e = {"value": band_total * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(soup_np.nbytes),
            "d2h_bytes_per_step": int(dist.numel() * 4 + (gv.numel() * 4 if gv is not None else 0))}

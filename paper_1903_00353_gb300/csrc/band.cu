@@ -1213,6 +1213,36 @@ struct Plan {
     cudaEvent_t bev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
+// Pinned staging blocks for the problem tables, kept for reuse by later plans (a plan per handle
+// is created on the first call, and pinning host memory is slow).  A block is returned only after
+// its last copy has completed.
+static std::mutex g_pin_mu;
+static std::vector<std::pair<char *, size_t>> g_pin_free;
+
+static cudaError_t pinned_get(size_t bytes, char **p, size_t *got) {
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        for (size_t i = 0; i < g_pin_free.size(); i++)
+            if (g_pin_free[i].second >= bytes) {
+                *p = g_pin_free[i].first;
+                *got = g_pin_free[i].second;
+                g_pin_free.erase(g_pin_free.begin() + (long)i);
+                return cudaSuccess;
+            }
+    }
+    const size_t want = bytes < 4096 ? 4096 : bytes;
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void **>(p), want);
+    *got = e == cudaSuccess ? want : 0;
+    return e;
+}
+
+static void pinned_put(char *p, size_t bytes) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.size() < 64) g_pin_free.emplace_back(p, bytes);
+    else cudaFreeHost(p);
+}
+
 void plan_free(Plan *pl, cudaStream_t s) {
     if (!pl) return;
     pl->tables.release(s);
@@ -1228,7 +1258,7 @@ void plan_free(Plan *pl, cudaStream_t s) {
         cudaEventSynchronize(pl->pinned_ev);
         cudaEventDestroy(pl->pinned_ev);
     }
-    if (pl->pinned) cudaFreeHost(pl->pinned);
+    pinned_put(pl->pinned, pl->pinned_bytes);
     for (cudaEvent_t e : pl->bev)
         if (e) cudaEventDestroy(e);
     delete pl;
@@ -1321,11 +1351,10 @@ static int plan_reserve(Plan &pl, cudaStream_t s) {
     if (!pl.pinned_ev) SDF_TRY(cudaEventCreateWithFlags(&pl.pinned_ev, cudaEventDisableTiming));
     SDF_TRY(cudaEventSynchronize(pl.pinned_ev));  // the previous copy out of the staging buffer
     if (pl.pinned_bytes < tab.size()) {
-        if (pl.pinned) cudaFreeHost(pl.pinned);
+        pinned_put(pl.pinned, pl.pinned_bytes);
         pl.pinned = nullptr;
         pl.pinned_bytes = 0;
-        SDF_TRY(cudaMallocHost(reinterpret_cast<void **>(&pl.pinned), tab.size() + 1024));
-        pl.pinned_bytes = tab.size() + 1024;
+        SDF_TRY(pinned_get(tab.size() + 1024, &pl.pinned, &pl.pinned_bytes));
     }
     memcpy(pl.pinned, tab.data(), tab.size());
     SDF_TRY(cudaMemcpyAsync(pl.tables.p, pl.pinned, tab.size(), cudaMemcpyHostToDevice, s));
@@ -1519,17 +1548,25 @@ static int plan_launch(Plan &pl, cudaStream_t s, bool timing) {
 static int plan_check(Plan &pl, const sdf_features *feats, cudaStream_t s, bool *retry) {
     DevCounters c;
     uint32_t total_pairs = 0;
-    SDF_TRY(cudaMemcpyAsync(&c, pl.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
-    SDF_TRY(cudaMemcpyAsync(&total_pairs, plan_scratch(pl).start + 3 * pl.n_tiles, sizeof(uint32_t),
-                            cudaMemcpyDeviceToHost, s));
-    SDF_TRY(cudaStreamSynchronize(s));
+    {
+        const HostRead rd[2] = {{&c, pl.ctr, sizeof(DevCounters)},
+                                {&total_pairs, plan_scratch(pl).start + 3 * pl.n_tiles, sizeof(uint32_t)}};
+        SDF_TRY(read_small(rd, 2, s));
+    }
     *retry = false;
-    for (int p = 0; p < pl.n; p++) {
-        if (feats[p]->ctr != pl.ctr) {  // degenerate positions flagged in the handle's own word
-            unsigned st = 0;
-            SDF_TRY(cudaMemcpy(&st, &feats[p]->ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
-            if (st & ST_DEGENERATE) return SDF_ERR_DEGENERATE;
-        }
+    // degenerate positions are flagged in each handle's own status word (batches: four per read)
+    for (int p0 = 0; p0 < pl.n; p0 += 4) {
+        unsigned st[4] = {0, 0, 0, 0};
+        HostRead rd[4];
+        int m = 0;
+        for (int p = p0; p < pl.n && p < p0 + 4; p++)
+            if (feats[p]->ctr != pl.ctr) {
+                rd[m] = HostRead{&st[m], &feats[p]->ctr->status, sizeof(unsigned)};
+                m++;
+            }
+        if (m) SDF_TRY(read_small(rd, m, s));
+        for (int i = 0; i < m; i++)
+            if (st[i] & ST_DEGENERATE) return SDF_ERR_DEGENERATE;
     }
     if (c.status & ST_DEGENERATE) return SDF_ERR_DEGENERATE;
     if (c.nb_status & ST_PAIR_OVERFLOW) {
@@ -1559,8 +1596,10 @@ static int plan_execute(Plan &pl, const sdf_features *feats, cudaStream_t s, boo
 // stats of the last call (host), used by sdf_features_status
 int narrow_band_stats(sdf_features_s *f, int64_t *stats, cudaStream_t s) {
     DevCounters c;
-    SDF_TRY(cudaMemcpyAsync(&c, f->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
-    SDF_TRY(cudaStreamSynchronize(s));
+    {
+        const HostRead rd[1] = {{&c, f->ctr, sizeof(DevCounters)}};
+        SDF_TRY(read_small(rd, 1, s));
+    }
     if (stats) {
         stats[0] = (int64_t)c.n_candidates;
         stats[1] = (int64_t)c.n_band;
@@ -1716,8 +1755,10 @@ extern "C" int sdf_batch_status(sdf_batch b, int64_t *stats, void *stream) {
     if (!b) return SDF_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     DevCounters c;
-    SDF_TRY(cudaMemcpyAsync(&c, b->plan.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
-    SDF_TRY(cudaStreamSynchronize(s));
+    {
+        const HostRead rd[1] = {{&c, b->plan.ctr, sizeof(DevCounters)}};
+        SDF_TRY(read_small(rd, 1, s));
+    }
     if (stats) {
         stats[0] = (int64_t)c.n_candidates;
         stats[1] = (int64_t)c.n_band;
@@ -1883,8 +1924,10 @@ extern "C" int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, floa
     DevCounters *ctr = sc.ctr;
     // read the status word: a pair or re-decision list beyond the static limits is an error
     unsigned status = 0;
-    SDF_TRY(cudaMemcpyAsync(&status, &ctr->nb_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    SDF_TRY(cudaStreamSynchronize(s));
+    {
+        const HostRead rd[1] = {{&status, &ctr->nb_status, sizeof(unsigned)}};
+        SDF_TRY(read_small(rd, 1, s));
+    }
     if (status & (ST_PAIR_OVERFLOW | ST_PATCH_OVERFLOW)) return SDF_ERR_TOO_LARGE;
     return SDF_OK;
 }

@@ -618,9 +618,10 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     B_TRY(scan_exclusive_u32(valt, head, n, true, rtmp, s));
     uint32_t Vh = 0;
     unsigned st_h = 0;
-    B_TRY(cudaMemcpyAsync(&Vh, head + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    B_TRY(cudaMemcpyAsync(&st_h, &f->ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    B_TRY(cudaStreamSynchronize(s));
+    {
+        const HostRead rd[2] = {{&Vh, head + n, sizeof(uint32_t)}, {&st_h, &f->ctr->status, sizeof(unsigned)}};
+        B_TRY(read_small(rd, 2, s));
+    }
     if (st_h) {
         tmp.release(s);
         free_handle(f);
@@ -678,8 +679,10 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     B_TRY(dalloc_s(&f->vert_plane, n, s));
     B_TRY(dalloc_s(&f->vert_class, V, s));
     unsigned st = 0;
-    B_TRY(cudaMemcpyAsync(&st, &f->ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    B_TRY(cudaStreamSynchronize(s));
+    {
+        const HostRead rd[1] = {{&st, &f->ctr->status, sizeof(unsigned)}};
+        B_TRY(read_small(rd, 1, s));
+    }
     if (st) {  // do not evaluate geometry on broken connectivity
         tmp.release(s);
         free_handle(f);
@@ -688,9 +691,10 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     if (build_records(f, s) != SDF_OK) B_TRY(cudaErrorUnknown);
     DevCounters c;
     uint32_t n_canon = 0;
-    B_TRY(cudaMemcpyAsync(&c, f->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
-    B_TRY(cudaMemcpyAsync(&n_canon, head + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    B_TRY(cudaStreamSynchronize(s));
+    {
+        const HostRead rd[2] = {{&c, f->ctr, sizeof(DevCounters)}, {&n_canon, head + n, sizeof(uint32_t)}};
+        B_TRY(read_small(rd, 2, s));
+    }
     tmp.release(s);
     if (!c.status && (int64_t)n_canon != E) c.status |= ST_NONMANIFOLD;
     if (c.status) {

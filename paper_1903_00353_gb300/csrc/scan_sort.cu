@@ -6,6 +6,11 @@
 // digits, a per-tile histogram pass, a device-wide scan of the digit offsets and a
 // scatter pass that ranks keys inside each warp with __match_any_sync and stages
 // the tile in shared memory so global writes of one digit run are contiguous.
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
 #include "sdf_internal.cuh"
 
 namespace sdf {
@@ -343,4 +348,58 @@ cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
 }
 
 cudaError_t pool_free(void *p, cudaStream_t s) { return p ? cudaFreeAsync(p, s) : cudaSuccess; }
+}  // namespace sdf
+
+// ----------------------------------------------------------------------------- small reads
+namespace sdf {
+namespace {
+constexpr int MAX_READS = 4;
+constexpr unsigned MAX_READ_BYTES = 1024;
+struct SmallReads {
+    const unsigned char *src[MAX_READS];
+    unsigned bytes[MAX_READS];
+    unsigned off[MAX_READS];
+    int n;
+};
+__global__ void k_read_small(SmallReads r, unsigned char *out) {
+    for (int i = 0; i < r.n; i++)
+        for (unsigned b = threadIdx.x; b < r.bytes[i]; b += blockDim.x) out[r.off[i] + b] = r.src[i][b];
+}
+std::mutex g_small_mu;
+std::vector<unsigned char *> g_small_free;  // pinned blocks of MAX_READ_BYTES
+}  // namespace
+
+cudaError_t read_small(const HostRead *reads, int n, cudaStream_t s) {
+    if (n < 1 || n > MAX_READS) return cudaErrorInvalidValue;
+    SmallReads r;
+    r.n = n;
+    unsigned total = 0;
+    for (int i = 0; i < n; i++) {
+        r.src[i] = static_cast<const unsigned char *>(reads[i].src);
+        r.bytes[i] = reads[i].bytes;
+        r.off[i] = total;
+        total += (reads[i].bytes + 15u) & ~15u;
+    }
+    if (total > MAX_READ_BYTES) return cudaErrorInvalidValue;
+    unsigned char *buf = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_small_mu);
+        if (!g_small_free.empty()) {
+            buf = g_small_free.back();
+            g_small_free.pop_back();
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (!buf) e = cudaMallocHost(reinterpret_cast<void **>(&buf), MAX_READ_BYTES);
+    if (e != cudaSuccess) return e;
+    k_read_small<<<1, 128, 0, s>>>(r, buf);  // pinned host memory is device-addressable (unified addressing)
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess)
+        for (int i = 0; i < n; i++) memcpy(reads[i].dst, buf + r.off[i], reads[i].bytes);
+    std::lock_guard<std::mutex> lk(g_small_mu);
+    g_small_free.push_back(buf);
+    return e;
+}
 }  // namespace sdf

@@ -122,6 +122,17 @@ size_t radix_tmp_bytes(int64_t n);
 cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int64_t n,
                            int bits, void *tmp, cudaStream_t s);
 
+// ----------------------------------------------------------------------------- small reads (scan_sort.cu)
+// Reads up to 4 small device values (counters, sizes, status words) into host variables and
+// synchronises the stream.  A one-block kernel writes them into pinned host memory, so the read
+// does not queue behind large copies that the caller may have in flight on the copy engines.
+struct HostRead {
+    void *dst;
+    const void *src;
+    unsigned bytes;
+};
+cudaError_t read_small(const HostRead *reads, int n, cudaStream_t s);
+
 // ----------------------------------------------------------------------------- sign beyond the band (fill.cu)
 // One problem's dense output, float[nz][ny][nx].
 struct FillProb {
