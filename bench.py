@@ -44,7 +44,7 @@ WORKLOADS = {
                     "forward + vertex adjoint of sum_band (d - 0.01)^2"),
     "c3": dict(index=3, adjoint=False, winner=False, batch=True,
                desc="batch of 64 seeded uneven meshes (log-uniform 1e3..2e5 triangles; displaced icospheres, "
-                    "displaced tori, clusters of 2-4 rotated boxes), per-mesh grids N in {64, 96, ..., 384} "
+                    "displaced tori, unions of 2-4 overlapping rotated boxes), per-mesh grids N in {64, 96, ..., 384} "
                     "on [0,1]^3, band 3h; forward of all 64 problems as one launch sequence replayed from a "
                     "CUDA graph, autotuned tile shape"),
     "c4": dict(index=4, adjoint=False, winner=False,

@@ -419,9 +419,255 @@ def box_cluster(n_boxes: int, target_tris: float, seed: int, half_range=(0.06, 0
     return Mesh(np.concatenate(verts), np.concatenate(tris).astype(np.int32))
 
 
+# ----------------------------------------------------------------------------- union of rotated boxes
+
+def _rotated_box_faces(c: np.ndarray, R: np.ndarray, half: np.ndarray):
+    """The 6 faces of the box c + R diag(half) [-1, 1]^3: (quad [4,3] counter-clockwise seen from
+    outside, outward unit normal n, offset d) with the box on the side n.x <= d."""
+    faces = []
+    for k in range(3):
+        u, v = R[:, (k + 1) % 3], R[:, (k + 2) % 3]
+        hu, hv = half[(k + 1) % 3], half[(k + 2) % 3]
+        for s in (-1.0, 1.0):
+            n = s * R[:, k]
+            fc = c + n * half[k]
+            quad = np.array([fc - hu * u - hv * v, fc + hu * u - hv * v, fc + hu * u + hv * v, fc - hu * u + hv * v])
+            if s < 0:
+                quad = quad[::-1]
+            faces.append((quad, n, float(n @ fc)))
+    return faces
+
+
+def _split_convex(poly: np.ndarray, n: np.ndarray, d: float, tol: float = 1e-12):
+    """Split a planar convex polygon by the plane n.x = d: (part with n.x <= d, part with n.x >= d),
+    each None when empty or degenerate; vertex order (orientation) is kept."""
+    s = poly @ n - d
+    if np.all(s <= tol):
+        return poly, None
+    if np.all(s >= -tol):
+        return None, poly
+    inside, outside = [], []
+    m = poly.shape[0]
+    for i in range(m):
+        p, q = poly[i], poly[(i + 1) % m]
+        sp, sq = s[i], s[(i + 1) % m]
+        if sp <= tol:
+            inside.append(p)
+        if sp >= -tol:
+            outside.append(p)
+        if (sp < -tol and sq > tol) or (sp > tol and sq < -tol):
+            x = p + (sp / (sp - sq)) * (q - p)
+            inside.append(x)
+            outside.append(x)
+
+    def ok(pts):
+        return np.array(pts) if len(pts) >= 3 else None
+    return ok(inside), ok(outside)
+
+
+def _weld(points: np.ndarray, tol: float) -> tuple[np.ndarray, np.ndarray]:
+    """Merge points closer than tol (transitively): (unique points, index of each input point)."""
+    from scipy.spatial import cKDTree
+    parent = np.arange(points.shape[0])
+
+    def find(i):
+        while parent[i] != i:
+            parent[i] = parent[parent[i]]
+            i = parent[i]
+        return i
+    for i, j in cKDTree(points).query_pairs(tol):
+        ri, rj = find(i), find(j)
+        if ri != rj:
+            parent[max(ri, rj)] = min(ri, rj)
+    roots = np.array([find(i) for i in range(points.shape[0])])
+    uniq, idx = np.unique(roots, return_inverse=True)
+    return points[uniq], idx
+
+
+def _midpoint_subdivide(v: np.ndarray, t: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """One level of 1-to-4 midpoint subdivision of an indexed mesh (orientation kept); an edge's
+    midpoint is shared by both triangles on it."""
+    e = np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]])
+    key = np.sort(e, axis=1)
+    uk, inv = np.unique(key, axis=0, return_inverse=True)
+    inv = inv.reshape(-1)
+    mid = 0.5 * (v[uk[:, 0]] + v[uk[:, 1]])
+    nt = t.shape[0]
+    m01, m12, m20 = (v.shape[0] + inv[k * nt:(k + 1) * nt] for k in range(3))
+    a, b, c = t[:, 0], t[:, 1], t[:, 2]
+    out = np.concatenate([np.stack([a, m01, m20], 1), np.stack([m01, b, m12], 1),
+                          np.stack([m20, m12, c], 1), np.stack([m01, m12, m20], 1)])
+    return np.concatenate([v, mid]), out
+
+
+def _closed_manifold(t: np.ndarray) -> bool:
+    """Every directed edge occurs once and its reverse once (closed, consistently oriented, manifold)."""
+    e = np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]])
+    if np.unique(e, axis=0).shape[0] != e.shape[0]:
+        return False
+    fwd = {tuple(x) for x in e.tolist()}
+    return all((b, a) in fwd for a, b in fwd)
+
+
+def _triangulate_convex(v: np.ndarray, ring: list):
+    """Triangulation of a planar convex polygon (whose edges may hold extra collinear points) that
+    maximises the smallest triangle quality, by the interval dynamic programme over diagonals;
+    None if every triangulation has a degenerate triangle."""
+    m = len(ring)
+    P = v[ring]
+    i, j, k = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+    pa, pb, pc = P[i], P[j], P[k]
+    area = 0.5 * np.linalg.norm(np.cross(pb - pa, pc - pa), axis=-1)
+    e2 = ((pb - pa) ** 2).sum(-1) + ((pc - pb) ** 2).sum(-1) + ((pa - pc) ** 2).sum(-1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        Q = np.where(e2 > 0, 4.0 * math.sqrt(3.0) * area / e2, 0.0)
+    best = np.full((m, m), np.inf)
+    arg = np.zeros((m, m), dtype=np.int64)
+    for span in range(2, m):
+        for a in range(0, m - span):
+            c = a + span
+            ks = np.arange(a + 1, c)
+            val = np.minimum(np.minimum(best[a, ks], best[ks, c]), Q[a, ks, c])
+            t = int(np.argmax(val))
+            best[a, c], arg[a, c] = val[t], ks[t]
+    if best[0, m - 1] <= 1e-12:
+        return None
+    out, stack = [], [(0, m - 1)]
+    while stack:
+        a, c = stack.pop()
+        if c - a < 2:
+            continue
+        k = int(arg[a, c])
+        out.append((ring[a], ring[k], ring[c]))
+        stack.extend(((a, k), (k, c)))
+    return out
+
+
+def _union_surface(boxes, weld_tol: float = 1e-9):
+    """Boundary of the union of convex boxes as an indexed triangle mesh.
+
+    Each face of each box is clipped against every other box: the part of a face inside box j
+    is the face cut successively by j's six planes, and what is cut off on the outer side of a
+    plane is kept; a face piece that ends inside j is dropped.  The kept convex pieces are
+    welded; a welded vertex that lies inside an edge of a piece (a T-junction: the neighbouring
+    face was cut at that point and this one was not) is inserted into that edge.  Each piece is
+    then triangulated so that its worst triangle is as well shaped as possible (a fan around its
+    centroid if every triangulation of it has a degenerate triangle)."""
+    planes = [_rotated_box_faces(*b) for b in boxes]
+    pieces = []
+    for i, faces in enumerate(planes):
+        for quad, _n, _d in faces:
+            cells = [quad]
+            for j, other in enumerate(planes):
+                if j == i:
+                    continue
+                kept = []
+                for cell in cells:
+                    rest = cell
+                    for _q, n, d in other:
+                        rest, out = _split_convex(rest, n, d)
+                        if out is not None:
+                            kept.append(out)
+                        if rest is None:
+                            break
+                    # a remaining piece lies inside box j: hidden
+                cells = kept
+            pieces.extend(cells)
+    if not pieces:
+        return None
+    pts = np.concatenate(pieces)
+    uv, idx = _weld(pts, weld_tol)
+    polys, off = [], 0
+    for p in pieces:
+        ids = list(idx[off:off + p.shape[0]])
+        off += p.shape[0]
+        ids = [a for k, a in enumerate(ids) if a != ids[k - 1]]  # welded duplicates
+        polys.append(ids)
+    # T-junctions: welded vertices inside piece edges
+    tris = []
+    for ids in polys:
+        if len(ids) < 3:
+            continue
+        ring = []
+        for k, a in enumerate(ids):
+            b = ids[(k + 1) % len(ids)]
+            ring.append(a)
+            pa, pb = uv[a], uv[b]
+            ab = pb - pa
+            rel = uv - pa
+            tpar = rel @ ab / float(ab @ ab)
+            off_line = np.linalg.norm(rel - tpar[:, None] * ab[None, :], axis=1)
+            on = np.nonzero((off_line < 1e3 * weld_tol) & (tpar > 1e-9) & (tpar < 1 - 1e-9))[0]
+            ring.extend(x for x in on[np.argsort(tpar[on])] if x != a and x != b)
+        tri = _triangulate_convex(uv, ring)
+        if tri is None:  # no ear with positive area left: fan around the centroid
+            cidx = uv.shape[0]
+            uv = np.concatenate([uv, uv[ring].mean(axis=0)[None, :]])
+            tri = [(cidx, ring[k], ring[(k + 1) % len(ring)]) for k in range(len(ring))]
+        tris.extend(tri)
+    return uv, np.array(tris, dtype=np.int64)
+
+
+def _triangle_quality(v: np.ndarray, t: np.ndarray) -> tuple[float, float]:
+    """(min over triangles of 4 sqrt(3) area / sum of squared edges (1 for equilateral), min edge)."""
+    a, b, c = v[t[:, 0]], v[t[:, 1]], v[t[:, 2]]
+    area = 0.5 * np.linalg.norm(np.cross(b - a, c - a), axis=1)
+    e2 = ((b - a) ** 2).sum(1) + ((c - b) ** 2).sum(1) + ((a - c) ** 2).sum(1)
+    edges = np.sqrt(np.minimum(np.minimum(((b - a) ** 2).sum(1), ((c - b) ** 2).sum(1)), ((a - c) ** 2).sum(1)))
+    return float((4.0 * math.sqrt(3.0) * area / e2).min()), float(edges.min())
+
+
+def box_union(n_boxes: int, target_tris: float, seed: int, half_range=(0.08, 0.25),
+              min_quality: float = 0.01, min_edge: float = 1e-4, return_boxes: bool = False):
+    """Union of n_boxes seeded, randomly rotated, overlapping boxes as one closed mesh.
+
+    Box j > 0 is centred at a random point inside an earlier box, so the boxes overlap and their
+    union is connected.  The union's boundary is built exactly in float64 (the faces clipped
+    against the other boxes, T-junctions resolved, see _union_surface) and then midpoint-
+    subdivided toward target_tris triangles.  Along the intersection curves the union has
+    concave edges and, where those curves meet box edges, saddle vertices.  The union is moved
+    so that its bounding box is centred in the unit cube.  Placements whose triangles are too
+    thin (quality below min_quality, an edge shorter than min_edge), that do not fit in
+    [0.05, 0.95]^3, or that do not give a closed manifold are drawn again.  With return_boxes the boxes (centre, rotation, half-extents) come back too."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    for _attempt in range(2000):
+        boxes = []
+        for j in range(n_boxes):
+            half = rng.uniform(*half_range, size=3)
+            R = random_rotation(rng)
+            if j == 0:
+                c = CENTER + rng.uniform(-0.05, 0.05, size=3)
+            else:
+                cp, Rp, hp = boxes[int(rng.integers(0, j))]
+                c = cp + Rp @ (rng.uniform(-0.9, 0.9, size=3) * hp)
+            boxes.append((c, R, half))
+        # centre the union's bounding box in the unit cube; draw again if it does not fit
+        corners = np.concatenate([f[0] for b in boxes for f in _rotated_box_faces(*b)])
+        lo, hi = corners.min(axis=0), corners.max(axis=0)
+        if (hi - lo).max() > 0.9:
+            continue
+        shift = CENTER - 0.5 * (lo + hi)
+        boxes = [(c + shift, R, half) for c, R, half in boxes]
+        surf = _union_surface(boxes)
+        if surf is None:
+            continue
+        v, t = surf
+        if not _closed_manifold(t):
+            continue
+        q, emin = _triangle_quality(v, t)
+        if q < min_quality or emin < min_edge:
+            continue
+        levels = max(0, int(round(math.log(max(target_tris, 1.0) / t.shape[0], 4))))
+        for _ in range(levels):
+            v, t = _midpoint_subdivide(v, t)
+        mesh = Mesh(v, _orient_outward(v, t))
+        return (mesh, boxes) if return_boxes else mesh
+    raise RuntimeError("could not place a well-shaped box union")
+
+
 def batch_meshes(n: int = 64, seed: int = 353_003, t_min: float = 1e3, t_max: float = 2e5):
-    """Batch of uneven meshes: displaced icospheres, displaced tori and clusters of 2-4 rotated
-    boxes (type uniform), sizes log-uniform in triangles, each paired with a grid size N in
+    """Batch of uneven meshes: displaced icospheres, displaced tori and unions of 2-4 overlapping
+    rotated boxes (type uniform), sizes log-uniform in triangles, each paired with a grid size N in
     {64, 96, ..., 384}.  Returns a list of (Mesh, N)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
@@ -430,7 +676,7 @@ def batch_meshes(n: int = 64, seed: int = 353_003, t_min: float = 1e3, t_max: fl
         kind = int(rng.integers(0, 3))
         sub = 353_000 + 100 * 3 + m
         if kind == 2:
-            mesh = box_cluster(int(rng.integers(2, 5)), target, seed=sub)
+            mesh = box_union(int(rng.integers(2, 5)), target, seed=sub)
         elif kind == 0:
             f = max(2, int(round(math.sqrt(target / 20.0))))
             mesh = icosphere(f, radius=float(rng.uniform(0.2, 0.35)),

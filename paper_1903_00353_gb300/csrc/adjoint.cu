@@ -299,19 +299,28 @@ __global__ void __launch_bounds__(256) k_band_l2(const float *dist, const float 
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (vec) {
         const int64_t n4 = n / 4;
-        for (int64_t q = t0; q < n4; q += stride) {
-            const float4 d = __ldcs(reinterpret_cast<const float4 *>(dist) + q);
-            const float4 t = __ldcs(reinterpret_cast<const float4 *>(target) + q);
+        // the trip count is uniform across each warp (the warp vote below needs all 32 lanes)
+        for (int64_t q0 = t0 & ~(int64_t)31; q0 < n4; q0 += stride) {
+            const int64_t q = q0 + (threadIdx.x & 31);
+            const bool in = q < n4;
+            const float4 d = in ? __ldcs(reinterpret_cast<const float4 *>(dist) + q)
+                                : make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+            const float4 t = in ? __ldcs(reinterpret_cast<const float4 *>(target) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
             float4 gq;
             const float dx = d.x - t.x, dy = d.y - t.y, dz = d.z - t.z, dw = d.w - t.w;
             gq.x = isfinite(d.x) ? 2.f * dx : 0.f;
             gq.y = isfinite(d.y) ? 2.f * dy : 0.f;
             gq.z = isfinite(d.z) ? 2.f * dz : 0.f;
             gq.w = isfinite(d.w) ? 2.f * dw : 0.f;
-            acc += (isfinite(d.x) ? (double)dx * dx : 0.0) + (isfinite(d.y) ? (double)dy * dy : 0.0) +
-                   (isfinite(d.z) ? (double)dz * dz : 0.0) + (isfinite(d.w) ? (double)dw * dw : 0.0);
-            cnt += isfinite(d.x) + isfinite(d.y) + isfinite(d.z) + isfinite(d.w);
-            if (grad) __stcs(reinterpret_cast<float4 *>(grad) + q, gq);
+            const unsigned fin = isfinite(d.x) | isfinite(d.y) << 1 | isfinite(d.z) << 2 | isfinite(d.w) << 3;
+            // FP64 runs at a small fraction of the FP32 rate on this part and band points are a few
+            // percent of the grid: the FP64 sum is taken only by warps that hold a band point
+            if (__any_sync(0xffffffffu, fin != 0u)) {
+                acc += ((fin & 1u) ? (double)dx * dx : 0.0) + ((fin & 2u) ? (double)dy * dy : 0.0) +
+                       ((fin & 4u) ? (double)dz * dz : 0.0) + ((fin & 8u) ? (double)dw * dw : 0.0);
+                cnt += __popc(fin);
+            }
+            if (grad && in) __stcs(reinterpret_cast<float4 *>(grad) + q, gq);
         }
         for (int64_t q = 4 * n4 + t0; q < n; q += stride) {  // tail of a length that is not a multiple of 4
             const float d = dist[q], t = target[q], df = d - t;
@@ -319,10 +328,11 @@ __global__ void __launch_bounds__(256) k_band_l2(const float *dist, const float 
             if (isfinite(d)) { acc += (double)df * df; cnt++; }
         }
     } else {
-        for (int64_t q = t0; q < n; q += stride) {
-            const float d = dist[q], t = target[q], df = d - t;
-            if (grad) grad[q] = isfinite(d) ? 2.f * df : 0.f;
-            if (isfinite(d)) { acc += (double)df * df; cnt++; }
+        for (int64_t q0 = t0 & ~(int64_t)31; q0 < n; q0 += stride) {  // warp-uniform trip count
+            const int64_t q = q0 + (threadIdx.x & 31);
+            const float d = q < n ? dist[q] : INFINITY, t = q < n ? target[q] : 0.f, df = d - t;
+            if (grad && q < n) grad[q] = isfinite(d) ? 2.f * df : 0.f;
+            if (__any_sync(0xffffffffu, isfinite(d)) && isfinite(d)) { acc += (double)df * df; cnt++; }
         }
     }
     // band points: one atomic per warp

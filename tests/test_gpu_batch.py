@@ -25,17 +25,19 @@ def f32(x: float) -> float:
 
 def _problems():
     """Uneven meshes on ragged, non-cubic grids: a displaced icosphere, a torus, a box cluster,
-    a saddle solid and a small knot tube."""
+    a saddle solid, a small knot tube and a union of overlapping boxes."""
     meshes = [meshgen.icosphere(8, radius=0.3, displacement=0.02, seed=11),
               meshgen.torus(nu=60, nv=24, seed=12),
               meshgen.box_cluster(3, 3000, seed=13),
               meshgen.star_fan_solid(8, [0.06, -0.06] * 4, apex_h=0.0),
-              meshgen.knot_tube(n_along=600, n_around=12, seed=14)]
+              meshgen.knot_tube(n_along=600, n_around=12, seed=14),
+              meshgen.box_union(3, 2500, seed=15)]
     grids = [sdf.Grid.cube(64),
              sdf.Grid(70, 45, 38, (0.05, 0.12, 0.21), f32(0.0201)),
              sdf.Grid.cube(96),
              sdf.Grid(33, 64, 17, (0.1, 0.0, 0.35), f32(1 / 60)),
-             sdf.Grid(100, 100, 40, (0.0, 0.0, 0.3), f32(0.01))]
+             sdf.Grid(100, 100, 40, (0.0, 0.0, 0.3), f32(0.01)),
+             sdf.Grid(61, 70, 66, (0.02, 0.01, 0.03), f32(0.0141))]
     ws = [3 * g.h for g in grids]
     soups = [m.soup(seed=20 + i) for i, m in enumerate(meshes)]
     feats = [sdf.sdf_build_features(torch.from_numpy(s).cuda()) for s in soups]

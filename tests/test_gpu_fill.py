@@ -39,6 +39,7 @@ CASES = {
                      lambda: sdf.Grid(90, 77, 45, (0.0, 0.0, f32(0.28)), f32(1 / 88)), 3.0),
     # several components
     "box_cluster": (lambda: meshgen.box_cluster(3, 2000, seed=7), lambda: sdf.Grid.cube(80), 2.5),
+    "box_union": (lambda: meshgen.box_union(4, 2000, seed=6), lambda: sdf.Grid.cube(72), 3.0),
     # the grid lies partly deep inside a large sphere: whole rows and slabs without band points
     "inside_window": (lambda: meshgen.icosphere(12, radius=0.45),
                       lambda: sdf.Grid(40, 36, 33, (f32(0.3), f32(0.31), f32(0.05)), f32(1 / 100)), 3.0),

@@ -56,6 +56,9 @@ TINY = {
     "ruff": lambda: meshgen.star_fan_solid(6, [0.25, -0.12] * 3, apex_h=0.05, bottom=-0.25),
     "torus_small": lambda: meshgen.torus(nu=40, nv=16, seed=7),
     "knot_small": lambda: meshgen.knot_tube(n_along=400, n_around=16, seed=8),
+    # overlapping rotated boxes: concave creases, saddle vertices where a crease meets a box edge
+    "box_union3": lambda: meshgen.box_union(3, 1500, seed=2),
+    "box_union4": lambda: meshgen.box_union(4, 3000, seed=3),
 }
 
 
@@ -72,7 +75,7 @@ def test_small_meshes_full_grid_dyadic(name):
     full_grid_case(soup, sdf.Grid.cube(64), 3 / 64)
 
 
-@pytest.mark.parametrize("name", ["torus_small", "saddle", "cube_flat", "knot_small"])
+@pytest.mark.parametrize("name", ["torus_small", "saddle", "cube_flat", "knot_small", "box_union4"])
 def test_ragged_grid_nondyadic_spacing(name):
     soup = TINY[name]().soup(seed=4)
     h = f32(0.0137)
@@ -82,7 +85,7 @@ def test_ragged_grid_nondyadic_spacing(name):
 
 def test_classification_and_weld_match_oracle():
     for mesh in (meshgen.torus(nu=60, nv=24, seed=2), meshgen.knot_tube(n_along=600, n_around=20, seed=5),
-                 meshgen.box(subdiv=2), TINY["ruff"]()):
+                 meshgen.box(subdiv=2), TINY["ruff"](), TINY["box_union4"]()):
         soup = mesh.soup(seed=1)
         feats = sdf.sdf_build_features(torch.from_numpy(soup).cuda())
         om = oracle.OracleMesh.from_soup(soup)

@@ -31,6 +31,7 @@ CASES = {
     "torus_ragged": (lambda: meshgen.torus(nu=60, nv=24, seed=5),
                      lambda: sdf.Grid(90, 77, 45, (0.0, 0.0, f32(0.28)), f32(1 / 88)), 3.0),
     "box_cluster": (lambda: meshgen.box_cluster(3, 2000, seed=7), lambda: sdf.Grid.cube(80), 2.5),
+    "box_union": (lambda: meshgen.box_union(4, 2000, seed=6), lambda: sdf.Grid.cube(72), 3.0),
 }
 
 

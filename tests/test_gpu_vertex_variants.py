@@ -29,6 +29,7 @@ MESHES = {
     "torus": lambda: meshgen.torus(nu=40, nv=16, seed=7),
     "knot": lambda: meshgen.knot_tube(n_along=400, n_around=16, seed=8),
     "box_cluster": lambda: meshgen.box_cluster(2, 1500, seed=9),
+    "box_union": lambda: meshgen.box_union(4, 2000, seed=6),
 }
 VARIANTS = {"cone": sdf.FLAG_VERTEX_CONE, "hemisphere": sdf.FLAG_VERTEX_HEMISPHERE}
 

@@ -105,3 +105,67 @@ def test_random_rotation_is_proper():
         R = meshgen.random_rotation(rng)
         assert np.allclose(R @ R.T, np.eye(3), atol=1e-12)
         assert abs(np.linalg.det(R) - 1.0) < 1e-12
+
+
+def _box_halfspaces(c, R, half):
+    """The box c + R diag(half) [-1, 1]^3 as rows [n, -d] of n.x - d <= 0 (scipy's convention)."""
+    rows = []
+    for k in range(3):
+        for s in (-1.0, 1.0):
+            n = s * R[:, k]
+            rows.append(np.concatenate([n, [-(n @ c + half[k])]]))
+    return np.array(rows)
+
+
+def _convex_volume(H):
+    """Volume of the polytope {x : H[:, :3] x + H[:, 3] <= 0}, 0 if it has no interior: an interior
+    point from the Chebyshev-centre linear programme, the vertices from qhull's halfspace
+    intersection, the volume from their convex hull."""
+    from scipy.optimize import linprog
+    from scipy.spatial import ConvexHull, HalfspaceIntersection
+    A, b = H[:, :3], -H[:, 3]
+    norm = np.linalg.norm(A, axis=1)
+    res = linprog([0, 0, 0, -1], A_ub=np.hstack([A, norm[:, None]]), b_ub=b, bounds=[(None, None)] * 3 + [(0, None)])
+    if res.status != 0 or res.x[3] < 1e-9:
+        return 0.0
+    hs = HalfspaceIntersection(H, res.x[:3])
+    return ConvexHull(hs.intersections).volume
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_box_union_is_the_union_boundary(k):
+    """The union mesh is closed and oriented, every vertex lies on some box's surface and inside
+    none, and its enclosed volume equals the union's volume by inclusion-exclusion over the boxes'
+    intersections (convex polytopes measured with qhull, independent of the face clipping)."""
+    import itertools
+    m, boxes = meshgen.box_union(k, 2000, seed=353_310 + k, return_boxes=True)
+    E = _check_closed_oriented(m)
+    T, V = m.triangles.shape[0], m.vertices.shape[0]
+    assert V - E + T == 2
+    assert 2000 / 2.1 <= T <= 2000 * 2.1
+    assert m.vertices.min() > 0.05 - 1e-12 and m.vertices.max() < 0.95 + 1e-12
+    sd = np.stack([_box_sdf_rotated(m.vertices, *b) for b in boxes])
+    assert np.abs(sd).min(axis=0).max() < 1e-12
+    assert sd.min(axis=0).min() > -1e-12
+    H = [_box_halfspaces(*b) for b in boxes]
+    vol_union = 0.0
+    for r in range(1, k + 1):
+        for sub in itertools.combinations(range(k), r):
+            vol_union += (-1) ** (r + 1) * _convex_volume(np.concatenate([H[i] for i in sub]))
+    X, tri = m.vertices, m.triangles
+    vol_mesh = np.einsum("ij,ij->i", X[tri[:, 0]], np.cross(X[tri[:, 1]], X[tri[:, 2]])).sum() / 6
+    assert abs(vol_mesh - vol_union) < 1e-12 * max(1.0, vol_union) * 100
+    # the boxes overlap: the union is smaller than the sum of the boxes
+    assert vol_union < sum(8 * np.prod(b[2]) for b in boxes) - 1e-6
+
+
+def _box_sdf_rotated(p, c, R, half):
+    """Exact SDF of the box c + R diag(half) [-1, 1]^3 (in the box's frame: |max(q,0)| + min(max q, 0))."""
+    q = np.abs((np.asarray(p) - c) @ R) - half
+    return np.linalg.norm(np.maximum(q, 0.0), axis=-1) + np.minimum(q.max(axis=-1), 0.0)
+
+
+def test_box_union_is_seeded():
+    a = meshgen.box_union(3, 1500, seed=5)
+    b = meshgen.box_union(3, 1500, seed=5)
+    assert np.array_equal(a.vertices, b.vertices) and np.array_equal(a.triangles, b.triangles)

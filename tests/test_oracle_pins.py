@@ -350,3 +350,51 @@ def test_adjoint_exact_identities():
     # homogeneity: sum_i x_i . dL/dx_i + sum_p g_p p . grad_p d = sum_p g_p d_p
     lhs = float(np.sum(X * grad) + np.sum(g * np.einsum("ij,ij->i", pts, gp)))
     assert abs(lhs - float(g @ d)) <= 1e-5 * np.abs(g).sum()
+
+
+def _rotated_box_sdf(p, c, R, half):
+    """Exact SDF of the box c + R diag(half) [-1, 1]^3 and the closest point of its surface."""
+    q = (np.asarray(p) - c) @ R
+    e = np.abs(q) - half
+    d = np.linalg.norm(np.maximum(e, 0.0), axis=-1) + np.minimum(e.max(axis=-1), 0.0)
+    # closest surface point from inside: push the coordinate of the nearest face out to it
+    k = np.argmax(e, axis=-1)
+    qs = q.copy()
+    rows = np.arange(q.shape[0])
+    qs[rows, k] = np.sign(q[rows, k]) * half[k]
+    return d, qs @ R.T + c
+
+
+@pytest.mark.parametrize("k,seed", [(2, 1), (3, 2), (4, 3)])
+def test_box_union_closed_form(k, seed):
+    """Union of overlapping rotated boxes (concave creases, saddle vertices where they meet box
+    edges).  Outside the union, the distance to it is the smallest distance to a box.  Inside,
+    -d is at least the largest depth in a box, max_j(-sdf_j), and equals it where the closest
+    surface point of that box lies outside all other boxes (then it is on the union's surface).
+    The sign is negative exactly inside some box."""
+    mesh, boxes = meshgen.box_union(k, 600, seed=seed, return_boxes=True)
+    om = oracle.OracleMesh.from_indexed(mesh.vertices, mesh.triangles)
+    assert om.n_concave_edges > 0 and om.n_saddle > 0
+    rng = np.random.default_rng(40 + seed)
+    pts = np.concatenate([_points_near(mesh, 3000, rng, spread=0.04), rng.uniform(0.0, 1.0, size=(1000, 3))])
+    d, _, _ = om.sdf_points(pts)
+    sd = np.stack([_rotated_box_sdf(pts, *b)[0] for b in boxes])
+    inside = (sd < -1e-12).any(axis=0)
+    outside = (sd > 1e-12).all(axis=0)
+    assert inside.sum() > 500 and outside.sum() > 500
+    assert np.all(d[inside] < 0) and np.all(d[outside] > 0)
+    assert np.max(np.abs(d[outside] - sd.min(axis=0)[outside])) < 1e-12
+    depth = (-sd).max(axis=0)
+    assert np.all(-d[inside] >= depth[inside] - 1e-12)
+    jstar = np.argmax(-sd, axis=0)
+    exact = np.zeros(pts.shape[0], dtype=bool)
+    for j, b in enumerate(boxes):
+        sel = inside & (jstar == j)
+        _, cp = _rotated_box_sdf(pts[sel], *b)
+        free = np.ones(sel.sum(), dtype=bool)
+        for m2, b2 in enumerate(boxes):
+            if m2 != j:
+                free &= _rotated_box_sdf(cp, *b2)[0] > 1e-9
+        exact[np.nonzero(sel)[0][free]] = True
+    assert exact.sum() > 300
+    assert np.max(np.abs(-d[exact] - depth[exact])) < 1e-12
