@@ -3,10 +3,12 @@
 
 Default workload (--workload c2): a 50,000-triangle displaced, jittered torus soup
 (R=0.3, r=0.1), grid 512^3 on [0,1]^3, band half-width 4h.  One step is the whole
-path: sdf_build_features (weld, pair, records) + sdf_narrow_band (bin, scan
-conversion + merge + dense write, FP64 re-decision) + sdf_narrow_band_backward
-(vertex adjoint of L = sum_band (d - 0.01)^2, its upstream gradient formed once from
-the first forward since the mesh is the same every step).  --workload c4 times the
+path: sdf_build_features (weld, pair, records) + sdf_narrow_band_list (bin, scan
+conversion + merge + dense write of the field and the compact band list, FP64
+re-decision) + sdf_band_list_l2 (L = sum_band (d - 0.01)^2 and its vertex adjoint,
+fused in one pass over the band list).  With --schedule cell or --shard slabs the
+adjoint takes the dense path instead (dense winners, sdf_narrow_band_backward with the
+upstream gradient formed once from the first forward).  --workload c4 times the
 2,097,152-triangle knot tube on 1024^3, band 3h (forward only).
 
 value = band points produced per second (all ranks), device-timed with CUDA events;
@@ -41,7 +43,7 @@ WORKLOADS = {
                desc="icosphere nu=4 r=0.3 (320 triangles), grid 64^3 on [0,1]^3, band 3h, forward"),
     "c2": dict(index=2, adjoint=True, winner=True,
                desc="displaced jittered torus R=0.3 r=0.1 (50,000 triangles), grid 512^3 on [0,1]^3, band 4h, "
-                    "forward + vertex adjoint of sum_band (d - 0.01)^2"),
+                    "forward + loss and vertex adjoint of sum_band (d - 0.01)^2"),
     "c3": dict(index=3, adjoint=False, winner=False, batch=True,
                desc="batch of 64 seeded uneven meshes (log-uniform 1e3..2e5 triangles; displaced icospheres, "
                     "displaced tori, unions of 2-4 overlapping rotated boxes), per-mesh grids N in {64, 96, ..., 384} "
@@ -56,8 +58,8 @@ WORKLOADS = {
     "c5fit": dict(index=5, adjoint=True, winner=True, fit=True,
                   desc="shape fitting: displaced icosphere nu=100 (200,000 triangles), grid 512^3, band 4h; "
                        "one plain gradient-descent step on the welded vertices of "
-                       "sum_band (d - d_ellipsoid(0.35, 0.25, 0.2))^2 (position update, forward with winner "
-                       "checkpoint, fused loss and gradient, adjoint)"),
+                       "sum_band (d - d_ellipsoid(0.35, 0.25, 0.2))^2 (position update, forward with the "
+                       "compact band list, loss and vertex gradient fused in one pass over the list)"),
 }
 FIT_LR = 1e-4  # fixed learning rate of the shape-fitting workload
 
@@ -269,22 +271,23 @@ def run_fit(args, wl, sdf, soup_np, soup, grid, w, N, dev, world, rank):
     feats = sdf.sdf_build_features(soup)
     X = feats.vertices().clone()
     dist = torch.empty(grid.shape, dtype=torch.float32, device=dev)
-    win = torch.empty(grid.shape, dtype=torch.int32, device=dev)
-    g = torch.empty_like(dist)
     gv = torch.zeros_like(X)
+    # one synchronous forward sizes the band list (a quarter of spare room: the band changes little
+    # over the steps, and an overflow would be reported by the status check after the loop)
+    _, bl = sdf.sdf_narrow_band_list(feats, grid, w, out=dist)
+    bl = sdf.BandList(len(bl) + len(bl) // 4 + 4096, device=dev)
 
     def fit_step(ev=None):
-        """Positions in, forward with winners, fused loss and gradient, vertex adjoint, update: all
-        in the library's kernels except the update (a 1 MB axpy)."""
+        """Positions in, forward with the compact band list, loss and vertex gradient fused over
+        the list, update: all in the library's kernels except the update (a 1 MB axpy)."""
         if ev:
             ev[0].record()
         feats.update_positions(X)
-        sdf.sdf_narrow_band(feats, grid, w, out=dist, winner=win, flags=sdf.FLAG_NO_SYNC)
+        sdf.sdf_narrow_band_list(feats, grid, w, out=dist, band_list=bl, flags=sdf.FLAG_NO_SYNC)
         if ev:
             ev[1].record()
-        loss, _, band = sdf.band_l2_loss(dist, target, grad=g)
         gv.zero_()
-        sdf.sdf_narrow_band_backward(feats, grid, w, g, winner=win, grad_vertices=gv)
+        loss, _, band = sdf.band_list_l2(feats, grid, bl, dist, target, grad_vertices=gv)
         X.sub_(FIT_LR * gv)
         if ev:
             ev[2].record()
@@ -591,9 +594,17 @@ def main():
     stats = feats.status()
     rec_bytes = record_bytes(feats)
     g = None
+    # the adjoint runs over the compact band list (loss and gradient fused) on the tile schedule;
+    # the paper's schedule and z-slabs keep the dense winners and the dense upstream gradient
+    use_list = bool(wl["adjoint"]) and args.schedule == "tile" and not shard
+    target = torch.full(grid.shape, 0.01, dtype=torch.float32, device=dev) if wl["adjoint"] else None
+    bls = [None, None]
     if wl["adjoint"]:
         g = torch.where(torch.isfinite(dist), 2.0 * (dist - 0.01), torch.zeros_like(dist))
         gv = torch.zeros(feats.n_vert, 3, dtype=torch.float32, device=dev)
+    if use_list:
+        bls = [sdf.BandList(band_points + band_points // 4 + 4096, device=dev) for _ in range(2)]
+        win = None
     feats.destroy()
 
     def step(timed_events=None):
@@ -603,11 +614,17 @@ def main():
         f = sdf.sdf_build_features(soup)
         if ev:
             ev[1].record()
-        sdf.sdf_narrow_band(f, grid, w, out=dist, winner=win if win is not None else False,
-                            flags=sdf.FLAG_TIMING | sched_flag)
+        if use_list:
+            sdf.sdf_narrow_band_list(f, grid, w, out=dist, band_list=bls[0], flags=sdf.FLAG_TIMING)
+        else:
+            sdf.sdf_narrow_band(f, grid, w, out=dist, winner=win if win is not None else False,
+                                flags=sdf.FLAG_TIMING | sched_flag)
         if ev:
             ev[2].record()
-        if wl["adjoint"]:
+        if use_list:  # L = sum_band (d - 0.01)^2 and dL/dV in one pass over the band list
+            gv.zero_()
+            sdf.band_list_l2(f, grid, bls[0], dist, target, grad_vertices=gv, flags=sdf.FLAG_TIMING)
+        elif wl["adjoint"]:
             gv.zero_()
             sdf.sdf_narrow_band_backward(f, grid, w, g, winner=win, grad_vertices=gv, flags=sdf.FLAG_TIMING)
             if shard:
@@ -668,8 +685,7 @@ def main():
     computed = [torch.cuda.Event(), torch.cuda.Event()]
     copied = [torch.cuda.Event(), torch.cuda.Event()]
     handles = []
-    if wl["adjoint"]:  # the loss's constant target (d = 0.01) and the gradient buffer
-        target = torch.full(grid.shape, 0.01, dtype=torch.float32, device=dev)
+    if wl["adjoint"]:  # the dense path's gradient buffer
         ge = torch.empty_like(dist)
 
     def e2e_step(i):
@@ -679,9 +695,14 @@ def main():
                 sc.wait_event(copied[b])  # the copy-out of step i - 2 has left these buffers
             s_dev = soup_host.to(dev, non_blocking=True)
             f = sdf.sdf_build_features(s_dev, stream=sc)
-            sdf.sdf_narrow_band(f, grid, w, out=dists[b], winner=wins[b] if wins[b] is not None else False,
-                                flags=sched_flag, stream=sc)
-            if wl["adjoint"]:
+            if use_list:
+                sdf.sdf_narrow_band_list(f, grid, w, out=dists[b], band_list=bls[b], stream=sc)
+                gvs[b].zero_()
+                sdf.band_list_l2(f, grid, bls[b], dists[b], target, grad_vertices=gvs[b], stream=sc)
+            else:
+                sdf.sdf_narrow_band(f, grid, w, out=dists[b], winner=wins[b] if wins[b] is not None else False,
+                                    flags=sched_flag, stream=sc)
+            if wl["adjoint"] and not use_list:
                 sdf.band_l2_loss(dists[b], target, grad=ge, stream=sc)  # dL/dd of sum_band (d - 0.01)^2
                 gvs[b].zero_()
                 sdf.sdf_narrow_band_backward(f, grid, w, ge, winner=wins[b], grad_vertices=gvs[b], stream=sc)
@@ -714,14 +735,16 @@ def main():
     hbm, peak_kind = peaks()
     tile_avg_ms = tile_ms / max(1, tile_calls)
     npts = grid.nx * grid.ny * grid.nz
-    alg_bytes = 4 * npts + (4 * npts if wl["winner"] else 0) + rec_bytes
+    # output bytes of the tile kernel: the field, and the band list (8 B per band point) or the
+    # dense winners
+    alg_bytes = 4 * npts + (8 * band_points if use_list else (4 * npts if win is not None else 0)) + rec_bytes
     achieved = alg_bytes / (tile_avg_ms / 1e3) / 1e9
     kname = ("k_cell_loop + k_decode_keys (the paper's schedule: region walk, global atomicMin, decode)"
              if args.schedule == "cell" else "k_tile (scan conversion + merge + dense write)")
     roofline = {"kernel": kname, "bound": "hbm",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "peak_source": peak_kind,
-                "traffic": tile_traffic(args.workload, not args.grid and not shard and args.schedule == "tile"),
+                "traffic": tile_traffic(args.workload, not args.grid and not shard and args.schedule == "tile" and use_list),
                 "algorithmic_bytes": int(alg_bytes),
                 "avg_ms": tile_avg_ms}
 
@@ -739,6 +762,8 @@ def main():
         "config": {"workload": wl["desc"], "triangles": int(soup_np.shape[0]), "grid": [N, N, N], "band_w": w,
                    "band_points": band_points, "l2": "flushed between timed steps (256 MiB write)",
                    "schedule": args.schedule,
+                   "adjoint": ("loss and vertex gradient fused over the compact band list" if use_list else
+                               "dense upstream gradient and winners") if wl["adjoint"] else None,
                    "parallelism": (f"z-slabs x{world}" if shard else "replicas") if world > 1 else "single GPU"},
         "build_ms": build_ms, "fwd_ms": fwd_ms, "adjoint_ms": adj_ms if wl["adjoint"] else None,
         "fwd_adjoint_ms": fwd_ms + adj_ms if wl["adjoint"] else None,

@@ -57,7 +57,9 @@ typedef enum sdf_status {
     SDF_ERR_TOO_LARGE = 5,    /* sizes beyond the index ranges (2^31 features, 2^31 rows)  */
     SDF_ERR_OOM = 6,          /* device allocation failed                                 */
     SDF_ERR_CUDA = 7,         /* a CUDA runtime call failed                               */
-    SDF_ERR_TIMEOUT = 8       /* a bounded device wait gave up (reserved)                 */
+    SDF_ERR_TIMEOUT = 8,      /* a bounded device wait gave up (reserved)                 */
+    SDF_ERR_LIST_OVERFLOW = 9 /* the caller's band list holds fewer entries than the band
+                                 has points; its count holds the length needed             */
 } sdf_status;
 
 /* Grid description (host struct, passed by pointer). */
@@ -320,6 +322,66 @@ void sdf_batch_destroy(sdf_batch b);
  */
 int sdf_band_l2_loss(const float *dist, const float *target, int64_t n, float *grad_out, double *loss_out,
                      unsigned long long *band_out, void *stream);
+
+/*
+ * Compact band list (a project addition).  The dense field keeps one value per grid point, but
+ * the band is a thin shell (a few percent of the points at 512^3); a list of the band points
+ * lets a later pass (loss, adjoint) touch only them instead of streaming the whole grid again.
+ * One entry per band point: its linear index (x fastest, as in the dense outputs) and its winner
+ * feature id (the value the dense winner array holds there).
+ */
+typedef struct sdf_band_entry {
+    uint32_t idx;    /* point index k * ny * nx + j * nx + i */
+    int32_t winner;  /* winning feature: face t, edge T + e, or vertex T + E + v */
+} sdf_band_entry;
+
+/*
+ * sdf_narrow_band_list -- sdf_narrow_band for one problem that also writes the band as a compact
+ * list (the tile kernel appends each tile's band points, the FP64 re-decision appends the points
+ * it decides into the band).
+ *   out_dist     device float[nz][ny][nx] (as sdf_narrow_band).
+ *   out_winner   device int32[nz][ny][nx] or NULL (the list carries the winners).
+ *   list         device sdf_band_entry[list_cap]; entries in no particular order (tiles finish in
+ *                any order), each band point exactly once.
+ *   list_count   device uint64, overwritten with the number of band points (also when that
+ *                exceeds list_cap; entries from list_cap on are then not written).
+ *   flags        as sdf_narrow_band, but not SDF_FLAG_CELL_LOOP.
+ * The grid must have at most 2^32 - 1 points.  With SDF_FLAG_NO_SYNC an overflow of the list is
+ * reported by the next sdf_features_status.
+ * Errors: those of sdf_narrow_band, and SDF_ERR_LIST_OVERFLOW.
+ */
+int sdf_narrow_band_list(sdf_features f, const sdf_grid *grid, float band_w, float *out_dist,
+                         int32_t *out_winner, sdf_band_entry *list, int64_t list_cap,
+                         unsigned long long *list_count, uint32_t flags, void *stream);
+
+/*
+ * sdf_band_list_backward -- the adjoint of sdf_narrow_band_backward over the entries of a band
+ * list: grad_vertices += sum over entries e of g(idx_e) * d d(p) / d X at p = point idx_e with
+ * winner winner_e (the same per-point contribution as sdf_narrow_band_backward).
+ *   list, list_cap, list_count  as written by sdf_narrow_band_list (min(count, cap) entries used;
+ *                                the count is read on the device, so the call never synchronises).
+ *   grad_dist      device float[nz][ny][nx] (dL/dd; read at the listed points only).
+ *   grad_vertices  device float[V][3], ACCUMULATED into.
+ * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_CUDA.
+ */
+int sdf_band_list_backward(sdf_features f, const sdf_grid *grid, const sdf_band_entry *list, int64_t list_cap,
+                           const unsigned long long *list_count, const float *grad_dist, float *grad_vertices,
+                           uint32_t flags, void *stream);
+
+/*
+ * sdf_band_list_l2 -- the loss of the shape-fitting workload and its vertex gradient in one pass
+ * over a band list: L = sum over the listed points of (d - target)^2 with d = dist[idx] (the same
+ * L as sdf_band_l2_loss), dL/dX = sum of 2 (d - target) d d / d X accumulated into grad_vertices,
+ * without a dense gradient field.
+ *   dist, target   device float[nz][ny][nx] (read at the listed points only).
+ *   loss_out       device double, overwritten (FP64 sum of the FP32 squared differences).
+ *   band_out       device uint64 or NULL, overwritten with the number of listed points used.
+ * No synchronisation.  Errors: SDF_ERR_INVALID_ARG, SDF_ERR_CUDA.
+ */
+int sdf_band_list_l2(sdf_features f, const sdf_grid *grid, const sdf_band_entry *list, int64_t list_cap,
+                     const unsigned long long *list_count, const float *dist, const float *target,
+                     float *grad_vertices, double *loss_out, unsigned long long *band_out, uint32_t flags,
+                     void *stream);
 
 /* Release the handle and its device memory (NULL is a no-op). */
 void sdf_features_destroy(sdf_features f);

@@ -20,6 +20,7 @@ from . import _buildlib
 
 __all__ = ["Grid", "Features", "sdf_build_features", "sdf_narrow_band", "sdf_narrow_band_backward",
            "SDFFunction", "Batch", "sdf_batch_create", "band_l2_loss", "load_library", "kernel_launches", "SDFError",
+           "BandList", "sdf_narrow_band_list", "band_list_backward", "band_list_l2",
            "FLAG_DISABLE_SADDLE", "FLAG_NO_SYNC", "FLAG_TIMING", "FLAG_AUTOTUNE", "FLAG_FILL_SIGN",
            "FLAG_CELL_LOOP", "FLAG_VERTEX_CONE", "FLAG_VERTEX_HEMISPHERE"]
 
@@ -34,6 +35,7 @@ FLAG_VERTEX_HEMISPHERE = 0x80
 
 
 _STATUS_KEYS = ("candidates", "band_points", "fp64_points", "pairs", "rows", "rows_hit")
+ERR_LIST_OVERFLOW = 9
 
 
 class SDFError(RuntimeError):
@@ -89,12 +91,16 @@ def load_library(path: str | None = None):
     L.sdf_batch_info.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_double)]
     L.sdf_batch_timing.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
     L.sdf_band_l2_loss.argtypes = [P, P, I64, P, P, P, P]
+    L.sdf_narrow_band_list.argtypes = [P, ctypes.POINTER(_CGrid), ctypes.c_float, P, P, P, I64, P, U32, P]
+    L.sdf_band_list_backward.argtypes = [P, ctypes.POINTER(_CGrid), P, I64, P, P, P, U32, P]
+    L.sdf_band_list_l2.argtypes = [P, ctypes.POINTER(_CGrid), P, I64, P, P, P, P, P, P, U32, P]
     L.sdf_batch_destroy.argtypes = [P]
     L.sdf_batch_destroy.restype = None
     for name in ("sdf_build_features", "sdf_features_update_positions", "sdf_narrow_band",
                  "sdf_narrow_band_backward", "sdf_features_info", "sdf_features_vertex_map",
                  "sdf_features_vertices", "sdf_features_status", "sdf_batch_create", "sdf_batch_run",
-                 "sdf_batch_status", "sdf_batch_info", "sdf_batch_timing", "sdf_band_l2_loss"):
+                 "sdf_batch_status", "sdf_batch_info", "sdf_batch_timing", "sdf_band_l2_loss",
+                 "sdf_narrow_band_list", "sdf_band_list_backward", "sdf_band_list_l2"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -382,6 +388,108 @@ def band_l2_loss(dist: torch.Tensor, target: torch.Tensor, grad: torch.Tensor | 
     _check(load_library().sdf_band_l2_loss(d.data_ptr(), t.data_ptr(), d.numel(), grad.data_ptr(),
                                            loss.data_ptr(), band.data_ptr(), _stream(stream)), "sdf_band_l2_loss")
     return loss, grad, band
+
+
+class BandList:
+    """Compact band list on the device: entries int32 [capacity, 2] = (point index, winner feature),
+    written by sdf_narrow_band_list, and its length as a device int64 [1] (count, which may exceed
+    the capacity after an overflow).  Reading len() synchronises; the list calls do not."""
+
+    def __init__(self, capacity: int, device="cuda"):
+        self.entries = torch.empty((max(int(capacity), 1), 2), dtype=torch.int32, device=device)
+        self.count = torch.zeros(1, dtype=torch.int64, device=device)
+
+    @property
+    def capacity(self) -> int:
+        return self.entries.shape[0]
+
+    def __len__(self) -> int:
+        return min(int(self.count.item()), self.capacity)
+
+    def indices(self) -> torch.Tensor:
+        return self.entries[: len(self), 0]
+
+    def winners(self) -> torch.Tensor:
+        return self.entries[: len(self), 1]
+
+    @staticmethod
+    def default_capacity(grid: "Grid") -> int:
+        """An eighth of the grid points (at least 2^16, at most all): the band is a thin shell."""
+        n = grid.nx * grid.ny * grid.nz
+        return min(n, max(1 << 16, n // 8))
+
+
+def sdf_narrow_band_list(features: Features, grid: Grid, w: float, out: torch.Tensor | None = None,
+                         band_list: BandList | None = None, winner: bool | torch.Tensor = False, flags: int = 0,
+                         stream=None):
+    """The narrow band of one problem and its band as a compact list: returns (dist, band_list) or
+    (dist, band_list, winner).  A list that turns out too short is grown to the band's length and
+    the call repeated (synchronous calls only; with FLAG_NO_SYNC the overflow is reported by
+    features.status())."""
+    if out is None:
+        out = torch.empty(grid.shape, dtype=torch.float32, device="cuda")
+    else:
+        _dev_f32(out, "out")
+        if out.numel() != grid.nx * grid.ny * grid.nz:
+            raise ValueError("out has the wrong size")
+    if isinstance(winner, torch.Tensor):
+        if not winner.is_cuda or winner.dtype != torch.int32 or not winner.is_contiguous():
+            raise ValueError("winner must be a contiguous int32 CUDA tensor")
+        win = winner
+    else:
+        win = torch.empty(grid.shape, dtype=torch.int32, device="cuda") if winner else None
+    if band_list is None:
+        band_list = BandList(BandList.default_capacity(grid))
+    ga = (_CGrid * 1)(grid.c())
+    for attempt in range(2):
+        code = load_library().sdf_narrow_band_list(
+            features.handle, ga, float(w), out.data_ptr(), win.data_ptr() if win is not None else None,
+            band_list.entries.data_ptr(), band_list.capacity, band_list.count.data_ptr(), flags, _stream(stream))
+        if code == ERR_LIST_OVERFLOW and attempt == 0:
+            need = int(band_list.count.item())
+            band_list.entries = torch.empty((need + need // 4 + 1024, 2), dtype=torch.int32, device="cuda")
+            continue
+        _check(code, "sdf_narrow_band_list")
+        break
+    return (out, band_list, win) if win is not None else (out, band_list)
+
+
+def band_list_backward(features: Features, grid: Grid, band_list: BandList, grad_dist: torch.Tensor,
+                       grad_vertices: torch.Tensor | None = None, flags: int = 0, stream=None) -> torch.Tensor:
+    """dL/d(welded vertices) [V, 3] for upstream dL/dd, summed over the listed band points only;
+    accumulates into grad_vertices."""
+    g = _dev_f32(grad_dist, "grad_dist")
+    if g.numel() != grid.nx * grid.ny * grid.nz:
+        raise ValueError("grad_dist has the wrong size")
+    if grad_vertices is None:
+        grad_vertices = torch.zeros(features.n_vert, 3, dtype=torch.float32, device="cuda")
+    ga = (_CGrid * 1)(grid.c())
+    _check(load_library().sdf_band_list_backward(features.handle, ga, band_list.entries.data_ptr(),
+                                                 band_list.capacity, band_list.count.data_ptr(), g.data_ptr(),
+                                                 _dev_f32(grad_vertices, "grad_vertices").data_ptr(), flags,
+                                                 _stream(stream)), "sdf_band_list_backward")
+    return grad_vertices
+
+
+def band_list_l2(features: Features, grid: Grid, band_list: BandList, dist: torch.Tensor, target: torch.Tensor,
+                 grad_vertices: torch.Tensor | None = None, flags: int = 0, stream=None):
+    """L = sum over the listed band points of (dist - target)^2 and dL/d(welded vertices), fused in
+    one pass over the list (no dense gradient); accumulates into grad_vertices.  Returns (loss as a
+    0-d float64 CUDA tensor, grad_vertices, band point count as a 0-d int64 CUDA tensor)."""
+    d, t = _dev_f32(dist, "dist"), _dev_f32(target, "target")
+    n = grid.nx * grid.ny * grid.nz
+    if d.numel() != n or t.numel() != n:
+        raise ValueError("dist and target must have the grid's size")
+    if grad_vertices is None:
+        grad_vertices = torch.zeros(features.n_vert, 3, dtype=torch.float32, device="cuda")
+    loss = torch.empty((), dtype=torch.float64, device=d.device)
+    band = torch.empty((), dtype=torch.int64, device=d.device)
+    ga = (_CGrid * 1)(grid.c())
+    _check(load_library().sdf_band_list_l2(features.handle, ga, band_list.entries.data_ptr(), band_list.capacity,
+                                           band_list.count.data_ptr(), d.data_ptr(), t.data_ptr(),
+                                           _dev_f32(grad_vertices, "grad_vertices").data_ptr(), loss.data_ptr(),
+                                           band.data_ptr(), flags, _stream(stream)), "sdf_band_list_l2")
+    return loss, grad_vertices, band
 
 
 class SDFFunction(torch.autograd.Function):

@@ -174,7 +174,7 @@ __device__ __forceinline__ void adjoint_batch(const AdjArgs &a, const long long 
 __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a, int vec) {
     __shared__ long long s_idx[8][ADJ_RING];
     __shared__ int s_wid[8][ADJ_RING];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5;
     long long *ridx = s_idx[warp];
     int *rwid = s_wid[warp];
     const int64_t n = (int64_t)a.nx * a.ny * a.nz;
@@ -217,15 +217,147 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a, int vec) {
     if (qn > 0) adjoint_batch(a, ridx, rwid, qh, qn);
 }
 
+// The adjoint over a compact band list: a warp takes 32 consecutive entries (one per lane; the
+// list holds a tile's band points in tile order, so neighbours mostly share a winner for
+// warp_add).  The upstream gradient is read at the listed point (a.grad), or, when target is
+// set, formed there as 2 (d - target) with the loss (d - target)^2 summed in FP64 (the
+// shape-fitting loss fused with its adjoint).
+__global__ void __launch_bounds__(256) k_adjoint_list(AdjArgs a, const uint2 *list, const unsigned long long *count,
+                                                      long long cap, const float *dist, const float *target,
+                                                      double *loss, unsigned long long *band_out) {
+    const long long n = min((long long)*count, cap);
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    double acc = 0.0;
+    unsigned cnt = 0;
+    // warp-uniform trip count: warp_add votes over all 32 lanes
+    for (long long e0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) & ~31ll; e0 < n; e0 += stride) {
+        const long long e = e0 + lane;
+        bool act = false;
+        uint2 en = make_uint2(0u, 0u);
+        float g = 0.f;
+        if (e < n) {
+            en = __ldcs(list + e);
+            if (target) {
+                const float df = __ldg(dist + en.x) - __ldg(target + en.x);
+                g = 2.f * df;
+                acc += (double)df * df;
+                cnt++;
+            } else {
+                g = __ldg(a.grad + en.x);
+            }
+            act = g != 0.f;
+        }
+        int vtx[3] = {0, 0, 0};
+        float c[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        const int nv = act ? point_adjoint(a, (int64_t)en.x, (int)en.y, g, vtx, c) : 0;
+        for (int q = 0; q < 3; q++) warp_add(a.gv, vtx[q], c[q][0], c[q][1], c[q][2], q < nv);
+    }
+    if (!target) return;
+    // loss and count: warp sums, then one atomic per block
+    cnt = __reduce_add_sync(FULL, cnt);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    __shared__ double s_acc[8];
+    __shared__ unsigned s_cnt[8];
+    if (lane == 0) {
+        s_acc[threadIdx.x >> 5] = acc;
+        s_cnt[threadIdx.x >> 5] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        unsigned long long c = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            b += s_acc[w];
+            c += s_cnt[w];
+        }
+        if (c) {
+            atomicAdd(loss, b);
+            if (band_out) atomicAdd(band_out, c);
+        }
+    }
+}
+
+AdjArgs make_adj_args(const sdf_features_s *f, const sdf_grid &gr) {
+    AdjArgs a;
+    a.T = (int)f->T; a.E = (int)f->E; a.V = (int)f->V;
+    a.nx = gr.nx; a.ny = gr.ny; a.nz = gr.nz;
+    a.div_nx = FastDiv((uint32_t)gr.nx);
+    a.div_ny = FastDiv((uint32_t)gr.ny);
+    a.ox = gr.origin[0]; a.oy = gr.origin[1]; a.oz = gr.origin[2]; a.h = gr.h;
+    a.grad = nullptr;
+    a.winner = nullptr;
+    a.gv = nullptr;
+    a.face_rec = f->face_rec; a.edge_rec = f->edge_rec; a.vert_rec = f->vert_rec;
+    a.face_vid = f->face_vid; a.edge_vf = f->edge_vf; a.vpos = f->vpos;
+    return a;
+}
+
+int list_adjoint(sdf_features_s *f, const sdf_grid *grid, const sdf_band_entry *list, int64_t list_cap,
+                 const unsigned long long *list_count, const float *grad_dist, const float *dist,
+                 const float *target, float *grad_vertices, double *loss_out, unsigned long long *band_out,
+                 uint32_t flags, cudaStream_t s) {
+    if (!f || !grid || !list || !list_count || list_cap < 0 || !grad_vertices) return SDF_ERR_INVALID_ARG;
+    const sdf_grid &gr = *grid;
+    if (gr.nx < 1 || gr.ny < 1 || gr.nz < 1 || !(gr.h > 0.f)) return SDF_ERR_INVALID_ARG;
+    if ((long long)gr.nx * gr.ny * gr.nz > (long long)UINT32_MAX) return SDF_ERR_TOO_LARGE;
+    AdjArgs a = make_adj_args(f, gr);
+    a.grad = grad_dist;
+    a.gv = grad_vertices;
+    if (target) {
+        SDF_TRY(cudaMemsetAsync(loss_out, 0, sizeof(double), s));
+        if (band_out) SDF_TRY(cudaMemsetAsync(band_out, 0, sizeof(unsigned long long), s));
+    }
+    static int n_sm = 0;
+    if (!n_sm) {
+        int dev = 0;
+        SDF_TRY(cudaGetDevice(&dev));
+        SDF_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const bool timing = (flags & SDF_FLAG_TIMING) != 0;
+    if (timing) {
+        if (ensure_events(f)) return SDF_ERR_CUDA;
+        SDF_TRY(cudaEventRecord(f->ev[4], s));
+    }
+    // the length is known on the device only: a grid of 8 CTAs per SM strides over the list
+    k_adjoint_list<<<8 * n_sm, 256, 0, s>>>(a, reinterpret_cast<const uint2 *>(list), list_count, (long long)list_cap,
+                                             dist, target, loss_out, band_out);
+    SDF_LAUNCHED(1);
+    SDF_TRY(cudaGetLastError());
+    if (timing) {
+        SDF_TRY(cudaEventRecord(f->ev[5], s));
+        SDF_TRY(cudaEventSynchronize(f->ev[5]));
+        float ms = 0.f;
+        SDF_TRY(cudaEventElapsedTime(&ms, f->ev[4], f->ev[5]));
+        f->t_ms[3] += ms;
+        f->t_calls[3]++;
+    }
+    return SDF_OK;
+}
+
 }  // namespace
 
-int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const float *band_w, int32_t n,
-                    float *const *out_dist, int32_t *const *out_winner, uint32_t flags, cudaStream_t s);
-int ensure_events(sdf_features_s *f);
 
 }  // namespace sdf
 
 using namespace sdf;
+
+extern "C" int sdf_band_list_backward(sdf_features f, const sdf_grid *grid, const sdf_band_entry *list,
+                                      int64_t list_cap, const unsigned long long *list_count, const float *grad_dist,
+                                      float *grad_vertices, uint32_t flags, void *stream) {
+    if (!grad_dist) return SDF_ERR_INVALID_ARG;
+    return list_adjoint(f, grid, list, list_cap, list_count, grad_dist, nullptr, nullptr, grad_vertices, nullptr,
+                        nullptr, flags, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int sdf_band_list_l2(sdf_features f, const sdf_grid *grid, const sdf_band_entry *list, int64_t list_cap,
+                                const unsigned long long *list_count, const float *dist, const float *target,
+                                float *grad_vertices, double *loss_out, unsigned long long *band_out, uint32_t flags,
+                                void *stream) {
+    if (!dist || !target || !loss_out) return SDF_ERR_INVALID_ARG;
+    return list_adjoint(f, grid, list, list_cap, list_count, nullptr, dist, target, grad_vertices, loss_out, band_out,
+                        flags, reinterpret_cast<cudaStream_t>(stream));
+}
 
 extern "C" int sdf_narrow_band_backward(const sdf_features *feats, const sdf_grid *grids, const float *band_w,
                                         int32_t n, const float *const *grad_dist, const int32_t *const *winner,
@@ -251,17 +383,10 @@ extern "C" int sdf_narrow_band_backward(const sdf_features *feats, const sdf_gri
             if (st) return st;
             win = w;
         }
-        AdjArgs a;
-        a.T = (int)f->T; a.E = (int)f->E; a.V = (int)f->V;
-        a.nx = gr.nx; a.ny = gr.ny; a.nz = gr.nz;
-        a.div_nx = FastDiv((uint32_t)gr.nx);
-        a.div_ny = FastDiv((uint32_t)gr.ny);
-        a.ox = gr.origin[0]; a.oy = gr.origin[1]; a.oz = gr.origin[2]; a.h = gr.h;
+        AdjArgs a = make_adj_args(f, gr);
         a.grad = grad_dist[p];
         a.winner = win;
         a.gv = grad_vertices[p];
-        a.face_rec = f->face_rec; a.edge_rec = f->edge_rec; a.vert_rec = f->vert_rec;
-        a.face_vid = f->face_vid; a.edge_vf = f->edge_vf; a.vpos = f->vpos;
         int64_t blocks = ((npts + 3) / 4 + 255) / 256;
         if (blocks > 152 * 16) blocks = 152 * 16;
         const int vec = (npts % 4 == 0) && ((reinterpret_cast<uintptr_t>(win) & 15) == 0);

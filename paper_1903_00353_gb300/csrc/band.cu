@@ -95,6 +95,11 @@ struct Prob {
     float *dist;
     int32_t *winner;
     int vec;  // rows 16-byte aligned: x-rows of 4 points are stored with one vector store
+    // compact band list (null: not requested): one (point index, winner) entry per band point;
+    // list_count receives the number of band points, entries at or beyond list_cap are not written
+    uint2 *list = nullptr;
+    unsigned long long *list_count = nullptr;
+    long long list_cap = 0;
 };
 
 // largest p in [0, n) with base[p] <= x (base ascending, base[0] = 0)
@@ -356,6 +361,8 @@ struct TileSmem {
     unsigned rowq[NT / 32][64];        // per-warp ring of non-empty rows waiting for point evaluation
     int chunk_next;                    // next 32-region chunk of the tile to hand to a warp
     long long work;
+    unsigned warp_total[NT / 32];      // band-list entries per warp (block scan)
+    unsigned long long list_base;      // first band-list slot of the current tile
 };
 
 
@@ -652,22 +659,109 @@ __device__ __forceinline__ float decode_key(unsigned long long key, const GridP 
     return val;
 }
 
-__global__ void k_band_flags(const uint32_t *bin_start, int64_t n_tiles, uint32_t *flag) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t < n_tiles) flag[t] = bin_start[3 * t + 3] != bin_start[3 * t] ? 1u : 0u;
+// A decoded key goes to the compact band list here iff it is a band point that the FP64
+// re-decision will not revisit (those are listed by k_patch once decided).
+__device__ __forceinline__ bool list_entry(unsigned long long key, const GridP &g) {
+    if (key == ~0ull) return false;
+    const float d = __uint_as_float((unsigned)(key >> 32));
+    return d < g.w && !(d < g.ds || d >= g.dlo);
 }
 
-// Work list of the tile kernel: first the band tiles (tiles that some region meets), then chunks
-// of FILL_CHUNK empty tiles.  band_list / empty_list come from one scan of the band flags.
+// Append the band-list entries of a band tile (keys still in shared memory; lc = this thread's
+// count from the decode pass) at consecutive slots from one atomicAdd per tile: a block scan of
+// the counts, then a second pass over the same points in the same order.
+template <int TY, int TZ>
+__device__ void list_band_tile(const Prob &pr, TileSmem<TY, TZ> &S, unsigned lc, int x0, int y0, int z0, int cx1,
+                               int cy1, int cz1, bool vec_rows, bool &overflow) {
+    constexpr int TP = TILE_X * TY * TZ;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned incl = lc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) S.warp_total[warp] = incl;
+    __syncthreads();
+    unsigned before = 0, total = 0;
+    for (int w = 0; w < NT / 32; w++) {
+        const unsigned t = S.warp_total[w];
+        if (w < warp) before += t;
+        total += t;
+    }
+    if (threadIdx.x == 0) S.list_base = atomicAdd(pr.list_count, (unsigned long long)total);
+    __syncthreads();
+    unsigned long long pos = S.list_base + before + incl - lc;
+    const GridP &g = pr.g;
+    const int64_t plane = (int64_t)g.nx * g.ny;
+    if (lc == 0) return;
+    if (vec_rows) {
+        for (int r = threadIdx.x >> 3; r < TY * TZ; r += NT / 8) {
+            const int y = r % TY, z = r / TY;
+            const int gj = y0 + y, gk = z0 + z;
+            if (gj > cy1 || gk > cz1) continue;
+            const int x = (threadIdx.x & 7) * 4;
+            const int64_t idx = (int64_t)gk * plane + (int64_t)gj * g.nx + x0 + x;
+            for (int u = 0; u < 4; u++) {
+                const unsigned long long key = S.key[r * TILE_X + x + u];
+                if (!list_entry(key, g)) continue;
+                if ((long long)pos < pr.list_cap)
+                    pr.list[pos] = make_uint2((uint32_t)(idx + u), (uint32_t)((key >> 1) & 0x7fffffffu));
+                else
+                    overflow = true;
+                pos++;
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < TP; e += NT) {
+            const int x = e % TILE_X, y = (e / TILE_X) % TY, z = e / (TILE_X * TY);
+            const int gi = x0 + x, gj = y0 + y, gk = z0 + z;
+            if (gi > cx1 || gj > cy1 || gk > cz1) continue;
+            const unsigned long long key = S.key[e];
+            if (!list_entry(key, g)) continue;
+            const int64_t idx = (int64_t)gk * plane + (int64_t)gj * g.nx + gi;
+            if ((long long)pos < pr.list_cap)
+                pr.list[pos] = make_uint2((uint32_t)idx, (uint32_t)((key >> 1) & 0x7fffffffu));
+            else
+                overflow = true;
+            pos++;
+        }
+    }
+}
+
+// Cost class of a band tile with np >= 1 (tile, region) pairs: 15 - floor(log2 np), clamped to
+// [0, 15], so class 0 holds the tiles with the most pairs.
+constexpr int N_COST_CLASSES = 16;
+__device__ __forceinline__ int tile_cost_class(uint32_t np) { return N_COST_CLASSES - 1 - min(15, 31 - __clz(np)); }
+
+__global__ void k_band_flags(const uint32_t *bin_start, int64_t n_tiles, uint32_t *flag, DevCounters *ctr) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const uint32_t np = bin_start[3 * t + 3] - bin_start[3 * t];
+    flag[t] = np ? 1u : 0u;
+    if (np) atomicAdd(&ctr->tile_hist[tile_cost_class(np)], 1u);
+}
+
+// Work list of the tile kernel: first the band tiles (tiles that some region meets), heaviest
+// cost class first (largest-first order, so that the last work items of the persistent kernel are
+// short and its CTAs finish together), then chunks of FILL_CHUNK empty tiles.  Within a class the
+// order is that of the atomic cursor; a tile's output does not depend on it.  empty_list comes
+// from one scan of the band flags.
 constexpr int FILL_CHUNK = 32;
 
 __global__ void k_tile_lists(const uint32_t *bin_start, int64_t n_tiles, const uint32_t *band_pos,
-                             int32_t *band_list, int32_t *empty_list) {
+                             int32_t *band_list, int32_t *empty_list, DevCounters *ctr) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
-    const bool band = bin_start[3 * t + 3] != bin_start[3 * t];
-    if (band) band_list[band_pos[t]] = (int32_t)t;
-    else empty_list[t - band_pos[t]] = (int32_t)t;
+    const uint32_t np = bin_start[3 * t + 3] - bin_start[3 * t];
+    if (np) {
+        const int c = tile_cost_class(np);
+        uint32_t base = 0;
+        for (int k = 0; k < c; k++) base += ctr->tile_hist[k];
+        band_list[base + atomicAdd(&ctr->tile_cursor[c], 1u)] = (int32_t)t;
+    } else {
+        empty_list[t - band_pos[t]] = (int32_t)t;
+    }
 }
 
 // Persistent tile kernel over all tiles of all problems of a batch: CTAs take work items from one
@@ -686,7 +780,7 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
     __shared__ unsigned s_cand, s_band, s_ovf, s_rows, s_hits, s_pairs;
     if (threadIdx.x == 0) { s_cand = 0; s_band = 0; s_ovf = 0; s_rows = 0; s_hits = 0; s_pairs = 0; }
     unsigned cand = 0, band = 0, rows = 0, hits = 0, pairs = 0;
-    bool overflow = false;
+    bool overflow = false, list_ovf = false;
     const int64_t n_band = *n_band_ptr, n_empty = n_tiles - n_band;
     const int64_t n_work = n_band > 0 ? n_band : (n_empty + FILL_CHUNK - 1) / FILL_CHUNK;
     for (;;) {
@@ -722,7 +816,10 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
                 __syncthreads();  // every merge is in before the decode
                 if (threadIdx.x == 0) pairs += (unsigned)(q3 - q0);
             }
-            if (pr.vec && cx1 == x0 + TILE_X - 1) {
+            const bool list = is_band && pr.list != nullptr;
+            const bool vec_rows = pr.vec && cx1 == x0 + TILE_X - 1;
+            unsigned lc = 0;  // this thread's band-list entries in the tile
+            if (vec_rows) {
                 // 8 threads per 32-point row, 4 points each
                 for (int r = threadIdx.x >> 3; r < TY * TZ; r += NT / 8) {
                     const int y = r % TY, z = r / TY;
@@ -738,6 +835,9 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
                         v.y = decode_key(kp[1], g, o, idx + 1, p, wv.y, band, overflow);
                         v.z = decode_key(kp[2], g, o, idx + 2, p, wv.z, band, overflow);
                         v.w = decode_key(kp[3], g, o, idx + 3, p, wv.w, band, overflow);
+                        if (list)
+                            lc += list_entry(kp[0], g) + list_entry(kp[1], g) + list_entry(kp[2], g) +
+                                  list_entry(kp[3], g);
                     }
                     *reinterpret_cast<float4 *>(dist + idx) = v;
                     if (winner) *reinterpret_cast<int4 *>(winner + idx) = wv;
@@ -750,10 +850,12 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
                     const int64_t idx = (int64_t)gk * plane + (int64_t)gj * g.nx + gi;
                     int wid = -1;
                     const float val = is_band ? decode_key(S.key[e], g, o, idx, p, wid, band, overflow) : INFINITY;
+                    if (list) lc += list_entry(S.key[e], g);
                     dist[idx] = val;
                     if (winner) winner[idx] = wid;
                 }
             }
+            if (list) list_band_tile<TY, TZ>(pr, S, lc, x0, y0, z0, cx1, cy1, cz1, vec_rows, list_ovf);
             if (is_band) __syncthreads();  // keys are reused by the next band tile
         }
     }
@@ -762,7 +864,8 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
     atomicAdd(&s_rows, rows);
     atomicAdd(&s_hits, hits);
     atomicAdd(&s_pairs, pairs);
-    if (overflow) s_ovf = 1;
+    if (overflow) atomicOr(&s_ovf, 1u);
+    if (list_ovf) atomicOr(&s_ovf, 2u);
     __syncthreads();
     if (threadIdx.x == 0) {
         atomicAdd(&o.ctr->n_candidates, (unsigned long long)s_cand);
@@ -770,7 +873,8 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
         atomicAdd(&o.ctr->n_rows, (unsigned long long)s_rows);
         atomicAdd(&o.ctr->n_rows_hit, (unsigned long long)s_hits);
         atomicAdd(&o.ctr->n_pairs, (unsigned long long)s_pairs);
-        if (s_ovf) atomicOr(&o.ctr->nb_status, ST_PATCH_OVERFLOW);
+        if (s_ovf & 1u) atomicOr(&o.ctr->nb_status, ST_PATCH_OVERFLOW);
+        if (s_ovf & 2u) atomicOr(&o.ctr->nb_status, ST_LIST_OVERFLOW);
     }
 }
 
@@ -943,6 +1047,12 @@ __global__ void k_patch(const Prob *P, Outputs o) {
             }
             dist[idx] = val;
             if (winner) winner[idx] = w;
+            const Prob &pr = P[pe.prob];
+            if (pr.list && w >= 0) {
+                const unsigned long long pos = atomicAdd(pr.list_count, 1ull);
+                if ((long long)pos < pr.list_cap) pr.list[pos] = make_uint2((uint32_t)idx, (uint32_t)w);
+                else atomicOr(&o.ctr->nb_status, ST_LIST_OVERFLOW);
+            }
         }
     }
 }
@@ -1265,7 +1375,8 @@ void plan_free(Plan *pl, cudaStream_t s) {
 }
 
 static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *grids, const float *band_w, int n,
-                         float *const *out_dist, int32_t *const *out_winner, int shape, bool fill) {
+                         float *const *out_dist, int32_t *const *out_winner, int shape, bool fill,
+                         const ListOut *lists = nullptr) {
     if (!feats || !grids || !band_w || n < 1 || !out_dist) return SDF_ERR_INVALID_ARG;
     pl.n = n;
     pl.shape = shape;
@@ -1289,6 +1400,17 @@ static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *gr
         pr.winner = out_winner ? out_winner[p] : nullptr;
         pr.vec = ((pr.g.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(pr.dist) & 15) == 0) &&
                  ((reinterpret_cast<uintptr_t>(pr.winner) & 15) == 0);
+        pr.list = nullptr;
+        pr.list_count = nullptr;
+        pr.list_cap = 0;
+        if (lists && lists[p].list) {
+            // entries hold 32-bit point indices; the paper's own schedule writes no list
+            if (!lists[p].count || lists[p].cap < 0 || pl.cell_loop) return SDF_ERR_INVALID_ARG;
+            if ((long long)grids[p].nx * grids[p].ny * grids[p].nz > (long long)UINT32_MAX) return SDF_ERR_TOO_LARGE;
+            pr.list = reinterpret_cast<uint2 *>(lists[p].list);
+            pr.list_count = lists[p].count;
+            pr.list_cap = lists[p].cap;
+        }
         pl.fbase[p + 1] = pl.fbase[p] + feats[p]->T + feats[p]->E + feats[p]->V;
         pl.tbase[p + 1] = pl.tbase[p] + (long long)pr.g.ntx * pr.g.nty * pr.g.ntz;
         // the fill's argument (rows outside the band run uncrossed) needs w > h
@@ -1446,11 +1568,13 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
     SDF_TRY(cudaGetLastError());
     // band / empty tile lists for the persistent tile kernel (one scan of the band flags)
     uint32_t *flags = sc.cnt;  // the fill cursors are no longer needed
-    k_band_flags<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, flags);
+    SDF_TRY(cudaMemsetAsync(sc.ctr->tile_hist, 0, 2 * N_COST_CLASSES * sizeof(unsigned), s));
+    k_band_flags<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, flags, sc.ctr);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
     SDF_TRY(scan_exclusive_u32(flags, sc.band_pos, n_tiles, true, sc.scan_tmp, s));
-    k_tile_lists<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, sc.band_pos, sc.band_list, sc.empty_list);
+    k_tile_lists<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, sc.band_pos, sc.band_list, sc.empty_list,
+                                                    sc.ctr);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaMemsetAsync(sc.ticket, 0, sizeof(unsigned long long), s));
     Outputs o;
@@ -1529,6 +1653,8 @@ static int plan_launch(Plan &pl, cudaStream_t s, bool timing) {
         if (ensure_events(pl.events)) return SDF_ERR_CUDA;
         ev = pl.events->ev;
     }
+    for (const Prob &pr : pl.probs)  // band-list lengths count up from 0 in every launch
+        if (pr.list_count) SDF_TRY(cudaMemsetAsync(pr.list_count, 0, sizeof(unsigned long long), s));
     int st = launch_any(pl.shape, pl.n, pl.f_tot, pl.n_tiles, plan_scratch(pl), s, ev);
     if (st) return st;
     if (ev && !pl.batch_timing) {
@@ -1577,6 +1703,9 @@ static int plan_check(Plan &pl, const sdf_features *feats, cudaStream_t s, bool 
         pl.patch_cap = (int64_t)c.n_patch + c.n_patch / 2 + 4096;
         *retry = true;
     }
+    // the caller's band list is too short: its count holds the length needed (no retry here, the
+    // caller owns the list)
+    if (!*retry && (c.nb_status & ST_LIST_OVERFLOW)) return SDF_ERR_LIST_OVERFLOW;
     return SDF_OK;
 }
 
@@ -1610,6 +1739,7 @@ int narrow_band_stats(sdf_features_s *f, int64_t *stats, cudaStream_t s) {
     }
     if (c.status & ST_DEGENERATE) return SDF_ERR_DEGENERATE;
     if (c.nb_status & (ST_PAIR_OVERFLOW | ST_PATCH_OVERFLOW)) return SDF_ERR_OOM;
+    if (c.nb_status & ST_LIST_OVERFLOW) return SDF_ERR_LIST_OVERFLOW;
     return SDF_OK;
 }
 
@@ -1626,7 +1756,8 @@ static std::tuple<int, long long, long long> tune_key(const sdf_features *feats,
 }
 
 int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const float *band_w, int32_t n,
-                    float *const *out_dist, int32_t *const *out_winner, uint32_t flags, cudaStream_t s) {
+                    float *const *out_dist, int32_t *const *out_winner, uint32_t flags, cudaStream_t s,
+                    const ListOut *lists) {
     if (!feats || !grids || !band_w || n < 1 || !out_dist) return SDF_ERR_INVALID_ARG;
     for (int p = 0; p < n; p++)
         if (!feats[p] || !out_dist[p]) return SDF_ERR_INVALID_ARG;
@@ -1645,7 +1776,7 @@ int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const floa
         Plan &pl = *f->plan;
         pl.cell_loop = cell_loop;
         pl.vmode = vmode;
-        SDF_TRY_ST(plan_describe(pl, feats, grids, band_w, 1, out_dist, out_winner, 0, fill));
+        SDF_TRY_ST(plan_describe(pl, feats, grids, band_w, 1, out_dist, out_winner, 0, fill, lists));
         return plan_execute(pl, feats, s, sync, timing);
     }
     int shape = 0;
@@ -1658,7 +1789,7 @@ int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const floa
     pl.pageable = true;
     pl.cell_loop = cell_loop;
     pl.vmode = vmode;
-    int st = plan_describe(pl, feats, grids, band_w, n, out_dist, out_winner, shape, fill);
+    int st = plan_describe(pl, feats, grids, band_w, n, out_dist, out_winner, shape, fill, lists);
     if (!st) st = plan_execute(pl, feats, s, true, false);
     // the temporary plan's memory returns to the pool in stream order
     plan_free(new Plan(std::move(pl)), s);
@@ -1671,6 +1802,18 @@ extern "C" int sdf_narrow_band(const sdf_features *feats, const sdf_grid *grids,
                                float *const *out_dist, int32_t *const *out_winner, uint32_t flags, void *stream) {
     return sdf::narrow_band_all(feats, grids, band_w, n, out_dist, out_winner, flags,
                                 reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int sdf_narrow_band_list(sdf_features f, const sdf_grid *grid, float band_w, float *out_dist,
+                                    int32_t *out_winner, sdf_band_entry *list, int64_t list_cap,
+                                    unsigned long long *list_count, uint32_t flags, void *stream) {
+    if (!f || !grid || !out_dist || !list || !list_count || list_cap < 0) return SDF_ERR_INVALID_ARG;
+    if (flags & SDF_FLAG_CELL_LOOP) return SDF_ERR_INVALID_ARG;
+    const sdf_features fl[1] = {f};
+    float *const dl[1] = {out_dist};
+    int32_t *const wl[1] = {out_winner};
+    const sdf::ListOut lo[1] = {{list, (long long)list_cap, list_count}};
+    return sdf::narrow_band_all(fl, grid, &band_w, 1, dl, wl, flags, reinterpret_cast<cudaStream_t>(stream), lo);
 }
 
 // ----------------------------------------------------------------------------- batches for CUDA graphs
@@ -1768,6 +1911,7 @@ extern "C" int sdf_batch_status(sdf_batch b, int64_t *stats, void *stream) {
         stats[5] = (int64_t)c.n_rows_hit;
     }
     if (c.nb_status & (ST_PAIR_OVERFLOW | ST_PATCH_OVERFLOW)) return SDF_ERR_OOM;
+    if (c.nb_status & ST_LIST_OVERFLOW) return SDF_ERR_LIST_OVERFLOW;
     return SDF_OK;
 }
 

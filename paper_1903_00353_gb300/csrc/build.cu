@@ -764,6 +764,7 @@ extern "C" const char *sdf_status_string(int status) {
     case SDF_ERR_OOM: return "device out of memory";
     case SDF_ERR_CUDA: return "CUDA runtime error";
     case SDF_ERR_TIMEOUT: return "bounded device wait gave up";
+    case SDF_ERR_LIST_OVERFLOW: return "band list too short for the band";
     default: return "unknown status";
     }
 }

@@ -16,6 +16,7 @@ enum : unsigned {
     ST_NONMANIFOLD = 4u,
     ST_PAIR_OVERFLOW = 8u,   // (tile, region) pair list too small: grow and rerun
     ST_PATCH_OVERFLOW = 16u, // FP64 re-decision list too small: grow and rerun
+    ST_LIST_OVERFLOW = 32u,  // the caller's compact band list is too short (its count holds the length)
 };
 
 // vertex / edge classes (Section 3.1, Section 3.2)
@@ -56,7 +57,7 @@ struct DevBuf {
 // ----------------------------------------------------------------------------- device status / counters
 struct DevCounters {
     unsigned status;     // build / position-update errors (ST_NONFINITE, ST_DEGENERATE, ST_NONMANIFOLD)
-    unsigned nb_status;  // narrow-band scratch overflows (ST_PAIR_OVERFLOW, ST_PATCH_OVERFLOW)
+    unsigned nb_status;  // narrow-band overflows (ST_PAIR_OVERFLOW, ST_PATCH_OVERFLOW, ST_LIST_OVERFLOW)
     unsigned long long n_candidates;   // (point, region) pairs merged
     unsigned long long n_band;         // band points written
     unsigned long long n_patch;        // points re-decided in FP64
@@ -64,10 +65,26 @@ struct DevCounters {
     unsigned long long n_rows;         // grid rows intersected with a region
     unsigned long long n_rows_hit;     // of which non-empty
     unsigned long long cls[8];         // classification counts
+    unsigned tile_hist[16];            // band tiles per cost class (class 0: the most pairs)
+    unsigned tile_cursor[16];          // fill cursors of the classes in the band tile list
 };
 
 struct Plan;
 void plan_free(Plan *pl, cudaStream_t s);
+
+// compact band list of one problem (see sdf_narrow_band_list)
+struct ListOut {
+    sdf_band_entry *list;
+    long long cap;
+    unsigned long long *count;
+};
+
+// the narrow band of n problems (sdf_narrow_band), with optional band lists (host array [n] or
+// null; an entry with a null list asks for none)
+int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const float *band_w, int32_t n,
+                    float *const *out_dist, int32_t *const *out_winner, uint32_t flags, cudaStream_t s,
+                    const ListOut *lists = nullptr);
+int ensure_events(sdf_features_s *f);
 
 }  // namespace sdf
 

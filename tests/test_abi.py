@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "sdf.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sdf_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(sdf_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -32,7 +32,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_status_strings(lib):
-    for code in range(0, 9):
+    for code in range(0, 10):
         s = lib.sdf_status_string(code)
         assert s and s != b"unknown status"
     assert lib.sdf_status_string(99) == b"unknown status"
@@ -55,6 +55,10 @@ def test_argument_validation_without_device(lib):
     assert lib.sdf_batch_info(None, None, None) == 1
     assert lib.sdf_batch_timing(None, None) == 1
     lib.sdf_batch_destroy(None)
+    assert lib.sdf_band_l2_loss(None, None, 0, None, None, None, None) == 1
+    assert lib.sdf_narrow_band_list(None, None, 0.1, None, None, None, 0, None, 0, None) == 1
+    assert lib.sdf_band_list_backward(None, None, None, 0, None, None, None, 0, None) == 1
+    assert lib.sdf_band_list_l2(None, None, None, 0, None, None, None, None, None, None, 0, None) == 1
 
 
 def test_product_package_does_not_import_oracle():
