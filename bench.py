@@ -69,8 +69,11 @@ FIT_LR = 1e-4  # fixed learning rate of the shape-fitting workload
 # of band.cu with // comments and blank lines removed (code_hash below).
 TILE_TRAFFIC = {
     "c2": {"bytes": 18_923_264 + 1_012_706_560, "band_cu_code_hash": "df461e2df890f38c",
-           "profile": "profiles/k_tile_torus_50k_512.md"},
+           "profile": "profiles/k_tile_torus_50k_512.md", "warp_instructions": 202_231_525},
 }
+# Instruction issue is the other roof of the tile kernel (its band work): 152 SMs x 4 schedulers x
+# 1 warp instruction per clock at the 2070 MHz maximum SM clock.
+ISSUE_PEAK = 152 * 4 * 2070e6  # warp instructions per second
 
 
 def code_hash(path: str) -> str:
@@ -85,13 +88,13 @@ def code_hash(path: str) -> str:
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
 
 
-def tile_traffic(name: str, default_grid: bool):
+def tile_traffic(name: str, default_grid: bool, key: str = "bytes"):
     rec = TILE_TRAFFIC.get(name)
     if rec is None or not default_grid:
         return None
     if code_hash(os.path.join(ROOT, "paper_1903_00353_gb300", "csrc", "band.cu")) != rec["band_cu_code_hash"]:
         return None
-    return rec["bytes"]
+    return rec.get(key)
 
 
 def peaks():
@@ -614,11 +617,12 @@ def main():
         f = sdf.sdf_build_features(soup)
         if ev:
             ev[1].record()
+        # no status read inside the step: the caller checks each step's status after its events
         if use_list:
-            sdf.sdf_narrow_band_list(f, grid, w, out=dist, band_list=bls[0], flags=sdf.FLAG_TIMING)
+            sdf.sdf_narrow_band_list(f, grid, w, out=dist, band_list=bls[0], flags=sdf.FLAG_TIMING | sdf.FLAG_NO_SYNC)
         else:
             sdf.sdf_narrow_band(f, grid, w, out=dist, winner=win if win is not None else False,
-                                flags=sdf.FLAG_TIMING | sched_flag)
+                                flags=sdf.FLAG_TIMING | sdf.FLAG_NO_SYNC | sched_flag)
         if ev:
             ev[2].record()
         if use_list:  # L = sum_band (d - 0.01)^2 and dL/dV in one pass over the band list
@@ -634,7 +638,9 @@ def main():
         return f
 
     for _ in range(args.warmup):
-        step().destroy()
+        f = step()
+        f.status()  # raises if the step's forward outgrew its scratch or its band list
+        f.destroy()
     torch.cuda.synchronize()
 
     uuid = None
@@ -654,6 +660,7 @@ def main():
             evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             f = step(evs)
             torch.cuda.synchronize()
+            f.status()
             t = f.timing()
             tile_ms += t["tile"][0]
             tile_calls += t["tile"][1]
@@ -696,12 +703,13 @@ def main():
             s_dev = soup_host.to(dev, non_blocking=True)
             f = sdf.sdf_build_features(s_dev, stream=sc)
             if use_list:
-                sdf.sdf_narrow_band_list(f, grid, w, out=dists[b], band_list=bls[b], stream=sc)
+                sdf.sdf_narrow_band_list(f, grid, w, out=dists[b], band_list=bls[b], flags=sdf.FLAG_NO_SYNC,
+                                         stream=sc)
                 gvs[b].zero_()
                 sdf.band_list_l2(f, grid, bls[b], dists[b], target, grad_vertices=gvs[b], stream=sc)
             else:
                 sdf.sdf_narrow_band(f, grid, w, out=dists[b], winner=wins[b] if wins[b] is not None else False,
-                                    flags=sched_flag, stream=sc)
+                                    flags=sched_flag | sdf.FLAG_NO_SYNC, stream=sc)
             if wl["adjoint"] and not use_list:
                 sdf.band_l2_loss(dists[b], target, grad=ge, stream=sc)  # dL/dd of sum_band (d - 0.01)^2
                 gvs[b].zero_()
@@ -727,6 +735,7 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     for f in handles:
+        f.status()  # every step's forward completed within its scratch and band list
         f.destroy()
     e2e = {"value": band_total * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(soup_np.nbytes),
@@ -747,6 +756,13 @@ def main():
                 "traffic": tile_traffic(args.workload, not args.grid and not shard and args.schedule == "tile" and use_list),
                 "algorithmic_bytes": int(alg_bytes),
                 "avg_ms": tile_avg_ms}
+    # the issue roof: warp instructions of the same ncu capture / the live duration
+    instr = tile_traffic(args.workload, not args.grid and not shard and args.schedule == "tile" and use_list,
+                         "warp_instructions")
+    if instr:
+        roofline["issue"] = {"bound": "alu", "achieved": instr / (tile_avg_ms / 1e3), "peak": ISSUE_PEAK,
+                             "unit": "warp instructions/s", "frac": instr / (tile_avg_ms / 1e3) / ISSUE_PEAK,
+                             "warp_instructions": instr}
 
     if rank != 0:
         if world > 1:

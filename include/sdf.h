@@ -78,9 +78,9 @@ typedef struct sdf_features_s *sdf_features;
 #define SDF_FLAG_NO_SYNC 0x2u        /* sdf_narrow_band: skip the final status read; call
                                         sdf_features_status later (needed inside graphs)     */
 #define SDF_FLAG_TIMING 0x4u         /* record CUDA events on `stream` around the stages of
-                                        sdf_narrow_band / sdf_narrow_band_backward (adds one
-                                        host synchronisation per call); read them with
-                                        sdf_features_timing                                  */
+                                        sdf_narrow_band(_list) and the adjoints; no call waits
+                                        for them: sdf_features_timing (or the next timed call
+                                        on the handle) reads them                            */
 #define SDF_FLAG_AUTOTUNE 0x8u       /* sdf_batch_create: time every tile shape on the batch
                                         and keep the fastest (also remembered for later
                                         sdf_narrow_band calls with n > 1 of the same sizes)  */
@@ -104,6 +104,11 @@ typedef struct sdf_features_s *sdf_features;
                                         open (Section 11.1), so gaps are possible            */
 #define SDF_FLAG_VERTEX_HEMISPHERE 0x80u /* with SDF_FLAG_CELL_LOOP: half-balls on the N_alpha
                                         and -N_alpha sides (Section 4.3), same class rule    */
+#define SDF_FLAG_GRAD_F64 0x100u     /* the adjoints (sdf_narrow_band_backward, sdf_band_list_backward,
+                                        sdf_band_list_l2): grad_vertices points to double[V][3] and
+                                        the per-point contributions (FP32) are summed in FP64, for
+                                        comparisons where the order of FP32 atomics would blur the
+                                        result                                               */
 
 /*
  * sdf_build_features -- mesh-connectivity stage (Section 7, Section 8).
@@ -192,8 +197,8 @@ int sdf_narrow_band(const sdf_features *feats, const sdf_grid *grids, const floa
  *   grad_dist      host array [n] of device float[nz][ny][nx] (dL/dd).
  *   winner         host array [n] of device int32 winners from the forward, or
  *                  NULL (array or entry) to recompute them.
- *   grad_vertices  host array [n] of device float[V][3]; ACCUMULATED into (the
- *                  caller zeroes it first).
+ *   grad_vertices  host array [n] of device float[V][3] (double[V][3] with
+ *                  SDF_FLAG_GRAD_F64); ACCUMULATED into (the caller zeroes it first).
  * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_OOM, SDF_ERR_CUDA.
  */
 int sdf_narrow_band_backward(const sdf_features *feats, const sdf_grid *grids, const float *band_w, int32_t n,
@@ -361,7 +366,7 @@ int sdf_narrow_band_list(sdf_features f, const sdf_grid *grid, float band_w, flo
  *   list, list_cap, list_count  as written by sdf_narrow_band_list (min(count, cap) entries used;
  *                                the count is read on the device, so the call never synchronises).
  *   grad_dist      device float[nz][ny][nx] (dL/dd; read at the listed points only).
- *   grad_vertices  device float[V][3], ACCUMULATED into.
+ *   grad_vertices  device float[V][3] (double[V][3] with SDF_FLAG_GRAD_F64), ACCUMULATED into.
  * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_CUDA.
  */
 int sdf_band_list_backward(sdf_features f, const sdf_grid *grid, const sdf_band_entry *list, int64_t list_cap,
@@ -371,8 +376,8 @@ int sdf_band_list_backward(sdf_features f, const sdf_grid *grid, const sdf_band_
 /*
  * sdf_band_list_l2 -- the loss of the shape-fitting workload and its vertex gradient in one pass
  * over a band list: L = sum over the listed points of (d - target)^2 with d = dist[idx] (the same
- * L as sdf_band_l2_loss), dL/dX = sum of 2 (d - target) d d / d X accumulated into grad_vertices,
- * without a dense gradient field.
+ * L as sdf_band_l2_loss), dL/dX = sum of 2 (d - target) d d / d X accumulated into grad_vertices
+ * (float[V][3], or double[V][3] with SDF_FLAG_GRAD_F64), without a dense gradient field.
  *   dist, target   device float[nz][ny][nx] (read at the listed points only).
  *   loss_out       device double, overwritten (FP64 sum of the FP32 squared differences).
  *   band_out       device uint64 or NULL, overwritten with the number of listed points used.

@@ -22,7 +22,7 @@ __all__ = ["Grid", "Features", "sdf_build_features", "sdf_narrow_band", "sdf_nar
            "SDFFunction", "Batch", "sdf_batch_create", "band_l2_loss", "load_library", "kernel_launches", "SDFError",
            "BandList", "sdf_narrow_band_list", "band_list_backward", "band_list_l2",
            "FLAG_DISABLE_SADDLE", "FLAG_NO_SYNC", "FLAG_TIMING", "FLAG_AUTOTUNE", "FLAG_FILL_SIGN",
-           "FLAG_CELL_LOOP", "FLAG_VERTEX_CONE", "FLAG_VERTEX_HEMISPHERE"]
+           "FLAG_CELL_LOOP", "FLAG_VERTEX_CONE", "FLAG_VERTEX_HEMISPHERE", "FLAG_GRAD_F64"]
 
 FLAG_DISABLE_SADDLE = 0x1
 FLAG_NO_SYNC = 0x2
@@ -32,6 +32,7 @@ FLAG_FILL_SIGN = 0x10
 FLAG_CELL_LOOP = 0x20
 FLAG_VERTEX_CONE = 0x40
 FLAG_VERTEX_HEMISPHERE = 0x80
+FLAG_GRAD_F64 = 0x100
 
 
 _STATUS_KEYS = ("candidates", "band_points", "fp64_points", "pairs", "rows", "rows_hit")
@@ -125,6 +126,17 @@ def _dev_f32(t: torch.Tensor, name: str) -> torch.Tensor:
     if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
         raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
     return t
+
+
+def _grad_vertices(gv: torch.Tensor | None, n_vert: int) -> tuple[torch.Tensor, int]:
+    """The vertex-gradient accumulator: a new float32 [V, 3] zero tensor, or the caller's float32
+    or float64 one (float64 sets FLAG_GRAD_F64: the sums are taken in FP64)."""
+    if gv is None:
+        return torch.zeros(n_vert, 3, dtype=torch.float32, device="cuda"), 0
+    if not gv.is_cuda or gv.dtype not in (torch.float32, torch.float64) or not gv.is_contiguous() \
+            or tuple(gv.shape) != (n_vert, 3):
+        raise ValueError("grad_vertices must be a contiguous float32 or float64 CUDA tensor [V, 3]")
+    return gv, FLAG_GRAD_F64 if gv.dtype == torch.float64 else 0
 
 
 @dataclass(frozen=True)
@@ -360,8 +372,8 @@ def sdf_narrow_band_backward(features: Features, grid: Grid, w: float, grad_dist
                              flags: int = 0, stream=None) -> torch.Tensor:
     """dL/d(welded vertices) [V, 3] for upstream dL/dd on the grid; accumulates into grad_vertices."""
     g = _dev_f32(grad_dist, "grad_dist")
-    if grad_vertices is None:
-        grad_vertices = torch.zeros(features.n_vert, 3, dtype=torch.float32, device="cuda")
+    grad_vertices, f64 = _grad_vertices(grad_vertices, features.n_vert)
+    flags |= f64
     fa = (ctypes.c_void_p * 1)(features.handle.value)
     ga = (_CGrid * 1)(grid.c())
     wa = (ctypes.c_float * 1)(float(w))
@@ -461,13 +473,12 @@ def band_list_backward(features: Features, grid: Grid, band_list: BandList, grad
     g = _dev_f32(grad_dist, "grad_dist")
     if g.numel() != grid.nx * grid.ny * grid.nz:
         raise ValueError("grad_dist has the wrong size")
-    if grad_vertices is None:
-        grad_vertices = torch.zeros(features.n_vert, 3, dtype=torch.float32, device="cuda")
+    grad_vertices, f64 = _grad_vertices(grad_vertices, features.n_vert)
     ga = (_CGrid * 1)(grid.c())
     _check(load_library().sdf_band_list_backward(features.handle, ga, band_list.entries.data_ptr(),
                                                  band_list.capacity, band_list.count.data_ptr(), g.data_ptr(),
-                                                 _dev_f32(grad_vertices, "grad_vertices").data_ptr(), flags,
-                                                 _stream(stream)), "sdf_band_list_backward")
+                                                 grad_vertices.data_ptr(), flags | f64, _stream(stream)),
+           "sdf_band_list_backward")
     return grad_vertices
 
 
@@ -480,15 +491,14 @@ def band_list_l2(features: Features, grid: Grid, band_list: BandList, dist: torc
     n = grid.nx * grid.ny * grid.nz
     if d.numel() != n or t.numel() != n:
         raise ValueError("dist and target must have the grid's size")
-    if grad_vertices is None:
-        grad_vertices = torch.zeros(features.n_vert, 3, dtype=torch.float32, device="cuda")
+    grad_vertices, f64 = _grad_vertices(grad_vertices, features.n_vert)
     loss = torch.empty((), dtype=torch.float64, device=d.device)
     band = torch.empty((), dtype=torch.int64, device=d.device)
     ga = (_CGrid * 1)(grid.c())
     _check(load_library().sdf_band_list_l2(features.handle, ga, band_list.entries.data_ptr(), band_list.capacity,
                                            band_list.count.data_ptr(), d.data_ptr(), t.data_ptr(),
-                                           _dev_f32(grad_vertices, "grad_vertices").data_ptr(), loss.data_ptr(),
-                                           band.data_ptr(), flags, _stream(stream)), "sdf_band_list_l2")
+                                           grad_vertices.data_ptr(), loss.data_ptr(), band.data_ptr(), flags | f64,
+                                           _stream(stream)), "sdf_band_list_l2")
     return loss, grad_vertices, band
 
 

@@ -25,6 +25,7 @@ struct AdjArgs {
     const float *grad;
     const int32_t *winner;
     float *gv;
+    double *gv64;  // SDF_FLAG_GRAD_F64: the vertex gradient accumulated in FP64 instead
     const float4 *face_rec, *edge_rec, *vert_rec;
     const int32_t *face_vid;
     const int4 *edge_vf;
@@ -33,8 +34,10 @@ struct AdjArgs {
 
 // add (gx, gy, gz) to vertex v, merged over runs of consecutive lanes that target the same vertex
 // (band points arrive in grid order, so neighbours with a common winner sit in adjacent lanes): a
-// segmented warp scan sums each run and its last lane issues the atomics
-__device__ __forceinline__ void warp_add(float *gv, int v, float gx, float gy, float gz, bool active) {
+// segmented warp scan sums each run and its last lane issues the atomics.  T is the accumulation
+// type (float, or double for SDF_FLAG_GRAD_F64, where the run sums are taken in FP64 as well).
+template <typename T>
+__device__ __forceinline__ void warp_add(T *gv, int v, T gx, T gy, T gz, bool active) {
     const int lane = threadIdx.x & 31;
     const int key = active ? v : -1;
     const int prev = __shfl_up_sync(FULL, key, 1), next = __shfl_down_sync(FULL, key, 1);
@@ -42,8 +45,8 @@ __device__ __forceinline__ void warp_add(float *gv, int v, float gx, float gy, f
     const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // first lane of this run
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const float tx = __shfl_up_sync(FULL, gx, o), ty = __shfl_up_sync(FULL, gy, o),
-                    tz = __shfl_up_sync(FULL, gz, o);
+        const T tx = __shfl_up_sync(FULL, gx, o), ty = __shfl_up_sync(FULL, gy, o),
+                tz = __shfl_up_sync(FULL, gz, o);
         if (lane - o >= start) {
             gx += tx;
             gy += ty;
@@ -54,6 +57,17 @@ __device__ __forceinline__ void warp_add(float *gv, int v, float gx, float gy, f
         atomicAdd(gv + 3 * v, gx);
         atomicAdd(gv + 3 * v + 1, gy);
         atomicAdd(gv + 3 * v + 2, gz);
+    }
+}
+
+// the contributions of one point (from point_adjoint) into the FP32 or FP64 vertex gradient
+template <bool F64>
+__device__ __forceinline__ void add_point(const AdjArgs &a, const int *vtx, const float (*c)[3], int nv) {
+    for (int q = 0; q < 3; q++) {
+        if (F64)
+            warp_add<double>(a.gv64, vtx[q], (double)c[q][0], (double)c[q][1], (double)c[q][2], q < nv);
+        else
+            warp_add<float>(a.gv, vtx[q], c[q][0], c[q][1], c[q][2], q < nv);
     }
 }
 
@@ -151,6 +165,7 @@ __device__ __forceinline__ int warp_incl_scan_i(int v) {
 // contribution step on full warps.
 constexpr int ADJ_RING = 256;  // > 31 waiting + 128 appended per pass
 
+template <bool F64>
 __device__ __forceinline__ void adjoint_batch(const AdjArgs &a, const long long *ridx, const int *rwid, int q0,
                                               int m) {
     const int lane = threadIdx.x & 31;
@@ -168,9 +183,10 @@ __device__ __forceinline__ void adjoint_batch(const AdjArgs &a, const long long 
     int vtx[3] = {0, 0, 0};
     float c[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     const int nv = act ? point_adjoint(a, idx, wid, g, vtx, c) : 0;
-    for (int q = 0; q < 3; q++) warp_add(a.gv, vtx[q], c[q][0], c[q][1], c[q][2], q < nv);
+    add_point<F64>(a, vtx, c, nv);
 }
 
+template <bool F64>
 __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a, int vec) {
     __shared__ long long s_idx[8][ADJ_RING];
     __shared__ int s_wid[8][ADJ_RING];
@@ -208,13 +224,13 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a, int vec) {
         qn += total;
         __syncwarp();
         while (qn >= 32) {
-            adjoint_batch(a, ridx, rwid, qh, 32);
+            adjoint_batch<F64>(a, ridx, rwid, qh, 32);
             qh = (qh + 32) & (ADJ_RING - 1);
             qn -= 32;
         }
         __syncwarp();  // ring slots are rewritten by the next pass
     }
-    if (qn > 0) adjoint_batch(a, ridx, rwid, qh, qn);
+    if (qn > 0) adjoint_batch<F64>(a, ridx, rwid, qh, qn);
 }
 
 // The adjoint over a compact band list: a warp takes 32 consecutive entries (one per lane; the
@@ -222,6 +238,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a, int vec) {
 // warp_add).  The upstream gradient is read at the listed point (a.grad), or, when target is
 // set, formed there as 2 (d - target) with the loss (d - target)^2 summed in FP64 (the
 // shape-fitting loss fused with its adjoint).
+template <bool F64>
 __global__ void __launch_bounds__(256) k_adjoint_list(AdjArgs a, const uint2 *list, const unsigned long long *count,
                                                       long long cap, const float *dist, const float *target,
                                                       double *loss, unsigned long long *band_out) {
@@ -251,7 +268,7 @@ __global__ void __launch_bounds__(256) k_adjoint_list(AdjArgs a, const uint2 *li
         int vtx[3] = {0, 0, 0};
         float c[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         const int nv = act ? point_adjoint(a, (int64_t)en.x, (int)en.y, g, vtx, c) : 0;
-        for (int q = 0; q < 3; q++) warp_add(a.gv, vtx[q], c[q][0], c[q][1], c[q][2], q < nv);
+        add_point<F64>(a, vtx, c, nv);
     }
     if (!target) return;
     // loss and count: warp sums, then one atomic per block
@@ -288,6 +305,7 @@ AdjArgs make_adj_args(const sdf_features_s *f, const sdf_grid &gr) {
     a.grad = nullptr;
     a.winner = nullptr;
     a.gv = nullptr;
+    a.gv64 = nullptr;
     a.face_rec = f->face_rec; a.edge_rec = f->edge_rec; a.vert_rec = f->vert_rec;
     a.face_vid = f->face_vid; a.edge_vf = f->edge_vf; a.vpos = f->vpos;
     return a;
@@ -303,7 +321,9 @@ int list_adjoint(sdf_features_s *f, const sdf_grid *grid, const sdf_band_entry *
     if ((long long)gr.nx * gr.ny * gr.nz > (long long)UINT32_MAX) return SDF_ERR_TOO_LARGE;
     AdjArgs a = make_adj_args(f, gr);
     a.grad = grad_dist;
-    a.gv = grad_vertices;
+    const bool f64 = (flags & SDF_FLAG_GRAD_F64) != 0;
+    a.gv = f64 ? nullptr : grad_vertices;
+    a.gv64 = f64 ? reinterpret_cast<double *>(grad_vertices) : nullptr;
     if (target) {
         SDF_TRY(cudaMemsetAsync(loss_out, 0, sizeof(double), s));
         if (band_out) SDF_TRY(cudaMemsetAsync(band_out, 0, sizeof(unsigned long long), s));
@@ -317,20 +337,21 @@ int list_adjoint(sdf_features_s *f, const sdf_grid *grid, const sdf_band_entry *
     const bool timing = (flags & SDF_FLAG_TIMING) != 0;
     if (timing) {
         if (ensure_events(f)) return SDF_ERR_CUDA;
+        SDF_TRY_ST(resolve_timing(f));
         SDF_TRY(cudaEventRecord(f->ev[4], s));
     }
     // the length is known on the device only: a grid of 8 CTAs per SM strides over the list
-    k_adjoint_list<<<8 * n_sm, 256, 0, s>>>(a, reinterpret_cast<const uint2 *>(list), list_count, (long long)list_cap,
-                                             dist, target, loss_out, band_out);
+    if (f64)
+        k_adjoint_list<true><<<8 * n_sm, 256, 0, s>>>(a, reinterpret_cast<const uint2 *>(list), list_count,
+                                                       (long long)list_cap, dist, target, loss_out, band_out);
+    else
+        k_adjoint_list<false><<<8 * n_sm, 256, 0, s>>>(a, reinterpret_cast<const uint2 *>(list), list_count,
+                                                        (long long)list_cap, dist, target, loss_out, band_out);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
     if (timing) {
         SDF_TRY(cudaEventRecord(f->ev[5], s));
-        SDF_TRY(cudaEventSynchronize(f->ev[5]));
-        float ms = 0.f;
-        SDF_TRY(cudaEventElapsedTime(&ms, f->ev[4], f->ev[5]));
-        f->t_ms[3] += ms;
-        f->t_calls[3]++;
+        f->adj_pending = true;  // read later (resolve_timing)
     }
     return SDF_OK;
 }
@@ -386,25 +407,27 @@ extern "C" int sdf_narrow_band_backward(const sdf_features *feats, const sdf_gri
         AdjArgs a = make_adj_args(f, gr);
         a.grad = grad_dist[p];
         a.winner = win;
-        a.gv = grad_vertices[p];
+        const bool f64 = (flags & SDF_FLAG_GRAD_F64) != 0;
+        a.gv = f64 ? nullptr : grad_vertices[p];
+        a.gv64 = f64 ? reinterpret_cast<double *>(grad_vertices[p]) : nullptr;
         int64_t blocks = ((npts + 3) / 4 + 255) / 256;
         if (blocks > 152 * 16) blocks = 152 * 16;
         const int vec = (npts % 4 == 0) && ((reinterpret_cast<uintptr_t>(win) & 15) == 0);
         const bool timing = (flags & SDF_FLAG_TIMING) != 0;
         if (timing) {
             if (ensure_events(f)) return SDF_ERR_CUDA;
+            SDF_TRY_ST(resolve_timing(f));
             SDF_TRY(cudaEventRecord(f->ev[4], s));
         }
-        k_adjoint<<<(unsigned)blocks, 256, 0, s>>>(a, vec);
+        if (f64)
+            k_adjoint<true><<<(unsigned)blocks, 256, 0, s>>>(a, vec);
+        else
+            k_adjoint<false><<<(unsigned)blocks, 256, 0, s>>>(a, vec);
         SDF_LAUNCHED(1);
         SDF_TRY(cudaGetLastError());
         if (timing) {
             SDF_TRY(cudaEventRecord(f->ev[5], s));
-            SDF_TRY(cudaEventSynchronize(f->ev[5]));
-            float ms = 0.f;
-            SDF_TRY(cudaEventElapsedTime(&ms, f->ev[4], f->ev[5]));
-            f->t_ms[3] += ms;
-            f->t_calls[3]++;
+            f->adj_pending = true;  // read later (resolve_timing)
         }
     }
     return SDF_OK;

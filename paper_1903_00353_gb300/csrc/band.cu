@@ -361,8 +361,6 @@ struct TileSmem {
     unsigned rowq[NT / 32][64];        // per-warp ring of non-empty rows waiting for point evaluation
     int chunk_next;                    // next 32-region chunk of the tile to hand to a warp
     long long work;
-    unsigned warp_total[NT / 32];      // band-list entries per warp (block scan)
-    unsigned long long list_base;      // first band-list slot of the current tile
 };
 
 
@@ -631,10 +629,12 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int2 *pai
     }
 }
 
-// decode one merged key into the output value / winner, queueing FP64 re-decisions
+// decode one merged key into the output value / winner, queueing FP64 re-decisions; entry tells
+// whether the point goes to the compact band list here (a band point outside the FP32 window)
 __device__ __forceinline__ float decode_key(unsigned long long key, const GridP &g, const Outputs &o, int64_t idx,
-                                            int prob, int &wid, unsigned &band, bool &overflow) {
+                                            int prob, int &wid, unsigned &band, bool &overflow, bool &entry) {
     wid = -1;
+    entry = false;
     if (key == ~0ull) return INFINITY;
     const float d = __uint_as_float((unsigned)(key >> 32));
     const int fid = (int)((key >> 1) & 0x7fffffffu);
@@ -644,7 +644,9 @@ __device__ __forceinline__ float decode_key(unsigned long long key, const GridP 
         wid = fid;
         band++;
     }
-    if (d < g.ds || d >= g.dlo) {  // inside the FP32 error window: re-decide in FP64
+    const bool window = d < g.ds || d >= g.dlo;
+    entry = wid >= 0 && !window;
+    if (window) {  // inside the FP32 error window: re-decide in FP64
         unsigned long long slot = atomicAdd(&o.ctr->n_patch, 1ull);
         if ((int64_t)slot < o.patch_cap) {
             PatchEntry pe;
@@ -659,73 +661,52 @@ __device__ __forceinline__ float decode_key(unsigned long long key, const GridP 
     return val;
 }
 
-// A decoded key goes to the compact band list here iff it is a band point that the FP64
-// re-decision will not revisit (those are listed by k_patch once decided).
-__device__ __forceinline__ bool list_entry(unsigned long long key, const GridP &g) {
-    if (key == ~0ull) return false;
-    const float d = __uint_as_float((unsigned)(key >> 32));
-    return d < g.w && !(d < g.ds || d >= g.dlo);
-}
-
-// Append the band-list entries of a band tile (keys still in shared memory; lc = this thread's
-// count from the decode pass) at consecutive slots from one atomicAdd per tile: a block scan of
-// the counts, then a second pass over the same points in the same order.
+// Append the band-list entries of a band tile.  During the decode each thread marks in emask
+// which of its points (bit k: the k-th point of its decode loop) are entries; here every warp
+// takes consecutive slots for its entries with one atomicAdd (no block barrier, so the atomic's
+// latency overlaps the other warps' work) and its threads write their entries, re-reading the
+// winners from the tile's keys, which stay in shared memory until the tile's end.
 template <int TY, int TZ>
-__device__ void list_band_tile(const Prob &pr, TileSmem<TY, TZ> &S, unsigned lc, int x0, int y0, int z0, int cx1,
-                               int cy1, int cz1, bool vec_rows, bool &overflow) {
-    constexpr int TP = TILE_X * TY * TZ;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned incl = lc;
+__device__ __forceinline__ void list_write(const Prob &pr, const TileSmem<TY, TZ> &S, unsigned emask, int x0, int y0,
+                                           int z0, bool vec_rows, bool &overflow) {
+    const int lane = threadIdx.x & 31;
+    const unsigned c = __popc(emask);
+    unsigned incl = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += t;
     }
-    if (lane == 31) S.warp_total[warp] = incl;
-    __syncthreads();
-    unsigned before = 0, total = 0;
-    for (int w = 0; w < NT / 32; w++) {
-        const unsigned t = S.warp_total[w];
-        if (w < warp) before += t;
-        total += t;
-    }
-    if (threadIdx.x == 0) S.list_base = atomicAdd(pr.list_count, (unsigned long long)total);
-    __syncthreads();
-    unsigned long long pos = S.list_base + before + incl - lc;
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(pr.list_count, (unsigned long long)total);
+    unsigned long long pos = __shfl_sync(0xffffffffu, base, 31) + incl - c;
     const GridP &g = pr.g;
     const int64_t plane = (int64_t)g.nx * g.ny;
-    if (lc == 0) return;
-    if (vec_rows) {
-        for (int r = threadIdx.x >> 3; r < TY * TZ; r += NT / 8) {
-            const int y = r % TY, z = r / TY;
-            const int gj = y0 + y, gk = z0 + z;
-            if (gj > cy1 || gk > cz1) continue;
-            const int x = (threadIdx.x & 7) * 4;
-            const int64_t idx = (int64_t)gk * plane + (int64_t)gj * g.nx + x0 + x;
-            for (int u = 0; u < 4; u++) {
-                const unsigned long long key = S.key[r * TILE_X + x + u];
-                if (!list_entry(key, g)) continue;
-                if ((long long)pos < pr.list_cap)
-                    pr.list[pos] = make_uint2((uint32_t)(idx + u), (uint32_t)((key >> 1) & 0x7fffffffu));
-                else
-                    overflow = true;
-                pos++;
-            }
+    while (emask) {
+        const int k = __ffs(emask) - 1;
+        emask &= emask - 1;
+        int e, gi, gj, gk;
+        if (vec_rows) {  // decode loop: rows r = threadIdx.x / 8 + (k / 4) * (NT / 8), 4 points from x
+            const int r = (threadIdx.x >> 3) + (k >> 2) * (NT / 8);
+            const int x = (threadIdx.x & 7) * 4 + (k & 3);
+            e = r * TILE_X + x;
+            gi = x0 + x;
+            gj = y0 + r % TY;
+            gk = z0 + r / TY;
+        } else {  // decode loop: points e = threadIdx.x + k * NT
+            e = threadIdx.x + k * NT;
+            gi = x0 + e % TILE_X;
+            gj = y0 + (e / TILE_X) % TY;
+            gk = z0 + e / (TILE_X * TY);
         }
-    } else {
-        for (int e = threadIdx.x; e < TP; e += NT) {
-            const int x = e % TILE_X, y = (e / TILE_X) % TY, z = e / (TILE_X * TY);
-            const int gi = x0 + x, gj = y0 + y, gk = z0 + z;
-            if (gi > cx1 || gj > cy1 || gk > cz1) continue;
-            const unsigned long long key = S.key[e];
-            if (!list_entry(key, g)) continue;
-            const int64_t idx = (int64_t)gk * plane + (int64_t)gj * g.nx + gi;
-            if ((long long)pos < pr.list_cap)
-                pr.list[pos] = make_uint2((uint32_t)idx, (uint32_t)((key >> 1) & 0x7fffffffu));
-            else
-                overflow = true;
-            pos++;
-        }
+        const int64_t idx = (int64_t)gk * plane + (int64_t)gj * g.nx + gi;
+        if ((long long)pos < pr.list_cap)
+            pr.list[pos] = make_uint2((uint32_t)idx, (uint32_t)((S.key[e] >> 1) & 0x7fffffffu));
+        else
+            overflow = true;
+        pos++;
     }
 }
 
@@ -734,27 +715,30 @@ __device__ void list_band_tile(const Prob &pr, TileSmem<TY, TZ> &S, unsigned lc,
 constexpr int N_COST_CLASSES = 16;
 __device__ __forceinline__ int tile_cost_class(uint32_t np) { return N_COST_CLASSES - 1 - min(15, 31 - __clz(np)); }
 
-__global__ void k_band_flags(const uint32_t *bin_start, int64_t n_tiles, uint32_t *flag, DevCounters *ctr) {
+__global__ void k_band_flags(const uint32_t *bin_start, int64_t n_tiles, uint32_t *flag, DevCounters *ctr, int lpt) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
     const uint32_t np = bin_start[3 * t + 3] - bin_start[3 * t];
     flag[t] = np ? 1u : 0u;
-    if (np) atomicAdd(&ctr->tile_hist[tile_cost_class(np)], 1u);
+    if (lpt && np) atomicAdd(&ctr->tile_hist[tile_cost_class(np)], 1u);
 }
 
-// Work list of the tile kernel: first the band tiles (tiles that some region meets), heaviest
-// cost class first (largest-first order, so that the last work items of the persistent kernel are
-// short and its CTAs finish together), then chunks of FILL_CHUNK empty tiles.  Within a class the
-// order is that of the atomic cursor; a tile's output does not depend on it.  empty_list comes
-// from one scan of the band flags.
+// Work list of the tile kernel: first the band tiles (tiles that some region meets), then chunks
+// of FILL_CHUNK empty tiles; empty_list comes from one scan of the band flags.  For a batch (lpt)
+// the band tiles are listed heaviest cost class first (largest-first order, so that the last work
+// items of the persistent kernel are short and its CTAs finish together; within a class the order
+// is that of the atomic cursor); for one problem they stay in tile order, where neighbouring
+// tiles, taken at the same time, share feature records in L2.  A tile's output depends on neither.
 constexpr int FILL_CHUNK = 32;
 
 __global__ void k_tile_lists(const uint32_t *bin_start, int64_t n_tiles, const uint32_t *band_pos,
-                             int32_t *band_list, int32_t *empty_list, DevCounters *ctr) {
+                             int32_t *band_list, int32_t *empty_list, DevCounters *ctr, int lpt) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
     const uint32_t np = bin_start[3 * t + 3] - bin_start[3 * t];
-    if (np) {
+    if (np && !lpt) {
+        band_list[band_pos[t]] = (int32_t)t;
+    } else if (np) {
         const int c = tile_cost_class(np);
         uint32_t base = 0;
         for (int k = 0; k < c; k++) base += ctr->tile_hist[k];
@@ -768,8 +752,10 @@ __global__ void k_tile_lists(const uint32_t *bin_start, int64_t n_tiles, const u
 // atomic ticket.  Work item w < n_band is band tile w plus its share of the empty tiles (so the
 // HBM-bound +inf fill is spread over the compute-bound band work); without band tiles, items are
 // chunks of FILL_CHUNK empty tiles.  A band tile merges its regions' candidates in shared memory
-// and writes its points; an empty tile is written +inf (Algorithm 1's initial value).
-template <int TY, int TZ>
+// and writes its points; an empty tile is written +inf (Algorithm 1's initial value).  LIST: some
+// problem of the launch writes a compact band list (compiled apart, so that the plain kernel
+// carries none of its code).
+template <int TY, int TZ, bool LIST>
 __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *tile_base, int n, Outputs o,
                                                 int64_t n_tiles, const int32_t *band_list,
                                                 const int32_t *empty_list, const uint32_t *n_band_ptr,
@@ -816,9 +802,9 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
                 __syncthreads();  // every merge is in before the decode
                 if (threadIdx.x == 0) pairs += (unsigned)(q3 - q0);
             }
-            const bool list = is_band && pr.list != nullptr;
+            const bool list = LIST && is_band && pr.list != nullptr;
             const bool vec_rows = pr.vec && cx1 == x0 + TILE_X - 1;
-            unsigned lc = 0;  // this thread's band-list entries in the tile
+            unsigned emask = 0;  // this thread's points that go to the band list (bit: decode order)
             if (vec_rows) {
                 // 8 threads per 32-point row, 4 points each
                 for (int r = threadIdx.x >> 3; r < TY * TZ; r += NT / 8) {
@@ -831,13 +817,15 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
                     int4 wv = make_int4(-1, -1, -1, -1);
                     if (is_band) {
                         const unsigned long long *kp = S.key + r * TILE_X + x;
-                        v.x = decode_key(kp[0], g, o, idx, p, wv.x, band, overflow);
-                        v.y = decode_key(kp[1], g, o, idx + 1, p, wv.y, band, overflow);
-                        v.z = decode_key(kp[2], g, o, idx + 2, p, wv.z, band, overflow);
-                        v.w = decode_key(kp[3], g, o, idx + 3, p, wv.w, band, overflow);
-                        if (list)
-                            lc += list_entry(kp[0], g) + list_entry(kp[1], g) + list_entry(kp[2], g) +
-                                  list_entry(kp[3], g);
+                        bool e0, e1, e2, e3;
+                        v.x = decode_key(kp[0], g, o, idx, p, wv.x, band, overflow, e0);
+                        v.y = decode_key(kp[1], g, o, idx + 1, p, wv.y, band, overflow, e1);
+                        v.z = decode_key(kp[2], g, o, idx + 2, p, wv.z, band, overflow, e2);
+                        v.w = decode_key(kp[3], g, o, idx + 3, p, wv.w, band, overflow, e3);
+                        if (list) {
+                            const int sh = 4 * ((r - (int)(threadIdx.x >> 3)) / (NT / 8));
+                            emask |= ((unsigned)e0 | (unsigned)e1 << 1 | (unsigned)e2 << 2 | (unsigned)e3 << 3) << sh;
+                        }
                     }
                     *reinterpret_cast<float4 *>(dist + idx) = v;
                     if (winner) *reinterpret_cast<int4 *>(winner + idx) = wv;
@@ -849,13 +837,14 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
                     if (gi > cx1 || gj > cy1 || gk > cz1) continue;
                     const int64_t idx = (int64_t)gk * plane + (int64_t)gj * g.nx + gi;
                     int wid = -1;
-                    const float val = is_band ? decode_key(S.key[e], g, o, idx, p, wid, band, overflow) : INFINITY;
-                    if (list) lc += list_entry(S.key[e], g);
+                    bool en = false;
+                    const float val = is_band ? decode_key(S.key[e], g, o, idx, p, wid, band, overflow, en) : INFINITY;
+                    if (list && en) emask |= 1u << ((e - (int)threadIdx.x) / NT);
                     dist[idx] = val;
                     if (winner) winner[idx] = wid;
                 }
             }
-            if (list) list_band_tile<TY, TZ>(pr, S, lc, x0, y0, z0, cx1, cy1, cz1, vec_rows, list_ovf);
+            if (list) list_write<TY, TZ>(pr, S, emask, x0, y0, z0, vec_rows, list_ovf);
             if (is_band) __syncthreads();  // keys are reused by the next band tile
         }
     }
@@ -1188,7 +1177,8 @@ __global__ void k_decode_keys(const Prob *P, const long long *pbase, int n, long
         const int p = find_prob(pbase, n, q);
         const int64_t idx = q - pbase[p];
         int wid = -1;
-        const float v = decode_key(__ldg(keys + q), P[p].g, o, idx, p, wid, band, overflow);
+        bool en;
+        const float v = decode_key(__ldg(keys + q), P[p].g, o, idx, p, wid, band, overflow, en);
         __stcs(P[p].dist + idx, v);
         if (P[p].winner) __stcs(P[p].winner + idx, wid);
     }
@@ -1263,12 +1253,12 @@ static int num_sms() {
     return n;
 }
 
-template <int TY, int TZ> static int tile_blocks_per_sm() {
+template <int TY, int TZ, bool LIST> static int tile_blocks_per_sm() {
     static int b = 0;
     if (!b) {
-        cudaFuncSetAttribute(k_tile<TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_tile<TY, TZ, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(TileSmem<TY, TZ>));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tile<TY, TZ>, NT, sizeof(TileSmem<TY, TZ>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tile<TY, TZ, LIST>, NT, sizeof(TileSmem<TY, TZ>));
         if (b <= 0) b = 1;
     }
     return b;
@@ -1286,6 +1276,28 @@ static cudaError_t record_event(cudaEvent_t e, cudaStream_t s) {
 int ensure_events(sdf_features_s *f) {
     for (int i = 0; i < 6; i++)
         if (!f->ev[i]) SDF_TRY(cudaEventCreate(&f->ev[i]));
+    return SDF_OK;
+}
+
+int resolve_timing(sdf_features_s *f) {
+    if (f->fwd_pending) {
+        SDF_TRY(cudaEventSynchronize(f->ev[3]));
+        for (int i = 0; i < 3; i++) {
+            float ms = 0.f;
+            SDF_TRY(cudaEventElapsedTime(&ms, f->ev[i], f->ev[i + 1]));
+            f->t_ms[i] += ms;
+            f->t_calls[i]++;
+        }
+        f->fwd_pending = false;
+    }
+    if (f->adj_pending) {
+        SDF_TRY(cudaEventSynchronize(f->ev[5]));
+        float ms = 0.f;
+        SDF_TRY(cudaEventElapsedTime(&ms, f->ev[4], f->ev[5]));
+        f->t_ms[3] += ms;
+        f->t_calls[3]++;
+        f->adj_pending = false;
+    }
     return SDF_OK;
 }
 
@@ -1488,6 +1500,7 @@ static int plan_reserve(Plan &pl, cudaStream_t s) {
 
 struct Scratch {  // device pointers used by one launch of the pipeline
     const Prob *probs;
+    bool any_list = false;  // some problem writes a compact band list
     const long long *fbase, *tbase;
     uint32_t *cnt, *start;
     void *scan_tmp;
@@ -1512,6 +1525,7 @@ struct Scratch {  // device pointers used by one launch of the pipeline
 
 static Scratch plan_scratch(const Plan &pl) {
     Scratch sc;
+    for (const Prob &pr : pl.probs) sc.any_list |= pr.list != nullptr;
     const char *t = pl.tables.as<char>();
     sc.probs = reinterpret_cast<const Prob *>(t);
     sc.fbase = reinterpret_cast<const long long *>(t + sizeof(Prob) * pl.n);
@@ -1569,12 +1583,13 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
     // band / empty tile lists for the persistent tile kernel (one scan of the band flags)
     uint32_t *flags = sc.cnt;  // the fill cursors are no longer needed
     SDF_TRY(cudaMemsetAsync(sc.ctr->tile_hist, 0, 2 * N_COST_CLASSES * sizeof(unsigned), s));
-    k_band_flags<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, flags, sc.ctr);
+    const int lpt = n > 1;  // largest-first order of the band tiles for batches
+    k_band_flags<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, flags, sc.ctr, lpt);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
     SDF_TRY(scan_exclusive_u32(flags, sc.band_pos, n_tiles, true, sc.scan_tmp, s));
     k_tile_lists<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, sc.band_pos, sc.band_list, sc.empty_list,
-                                                    sc.ctr);
+                                                    sc.ctr, lpt);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaMemsetAsync(sc.ticket, 0, sizeof(unsigned long long), s));
     Outputs o;
@@ -1585,9 +1600,15 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
     o.patch_cap = sc.patch_cap;
     o.ctr = sc.ctr;
     if (ev) SDF_TRY(record_event(ev[1], s));
-    const int64_t ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm<TY, TZ>() * num_sms());
-    k_tile<TY, TZ><<<(unsigned)ctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
-        sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket);
+    if (sc.any_list) {
+        const int64_t ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm<TY, TZ, true>() * num_sms());
+        k_tile<TY, TZ, true><<<(unsigned)ctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
+            sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket);
+    } else {
+        const int64_t ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm<TY, TZ, false>() * num_sms());
+        k_tile<TY, TZ, false><<<(unsigned)ctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
+            sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket);
+    }
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
     if (ev) SDF_TRY(record_event(ev[2], s));
@@ -1651,22 +1672,14 @@ static int plan_launch(Plan &pl, cudaStream_t s, bool timing) {
         ev = pl.bev;
     } else if (timing && pl.events) {
         if (ensure_events(pl.events)) return SDF_ERR_CUDA;
+        SDF_TRY_ST(resolve_timing(pl.events));  // the previous timed call's events are reused
         ev = pl.events->ev;
     }
     for (const Prob &pr : pl.probs)  // band-list lengths count up from 0 in every launch
         if (pr.list_count) SDF_TRY(cudaMemsetAsync(pr.list_count, 0, sizeof(unsigned long long), s));
     int st = launch_any(pl.shape, pl.n, pl.f_tot, pl.n_tiles, plan_scratch(pl), s, ev);
     if (st) return st;
-    if (ev && !pl.batch_timing) {
-        sdf_features_s *f = pl.events;
-        SDF_TRY(cudaEventSynchronize(f->ev[3]));
-        for (int i = 0; i < 3; i++) {
-            float ms = 0.f;
-            SDF_TRY(cudaEventElapsedTime(&ms, f->ev[i], f->ev[i + 1]));
-            f->t_ms[i] += ms;
-            f->t_calls[i]++;
-        }
-    }
+    if (ev && !pl.batch_timing) pl.events->fwd_pending = true;  // read later (resolve_timing)
     return SDF_OK;
 }
 
@@ -1950,6 +1963,7 @@ extern "C" int sdf_features_status(sdf_features f, int64_t *stats, void *stream)
 
 extern "C" int sdf_features_timing(sdf_features f, double *ms, int64_t *calls, int reset) {
     if (!f) return SDF_ERR_INVALID_ARG;
+    SDF_TRY_ST(sdf::resolve_timing(f));
     for (int i = 0; i < 4; i++) {
         if (ms) ms[i] = f->t_ms[i];
         if (calls) calls[i] = f->t_calls[i];

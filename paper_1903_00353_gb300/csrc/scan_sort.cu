@@ -94,7 +94,9 @@ size_t scan_tmp_bytes(int64_t n) {
 }
 
 // one block, 1024 threads, walks the whole array in chunks carrying the running prefix: one
-// launch instead of three for the small arrays of the sorts and of the tile lists
+// launch instead of three for the small arrays of the sorts and of the tile lists.  A thread
+// takes 4 consecutive items, so a warp reads 512 contiguous bytes per load (16 items per thread
+// were measured slower: the 64-byte stride between threads breaks the coalescing).
 __global__ void __launch_bounds__(1024) k_scan_single(const uint32_t *in, uint32_t *out, int64_t n,
                                                       uint32_t *total_out) {
     __shared__ uint32_t wt[32];
@@ -164,19 +166,29 @@ cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, boo
 }
 
 // ============================================================================= radix sort
+// LSD radix sort of 64-bit keys with 32-bit values, 8 bits per pass: per pass a digit histogram
+// per tile of keys, one scan of the digit-major histograms, and a stable scatter (ranks within
+// each warp by match_any, then across the warps of the tile, the tile staged in shared memory so
+// that the global writes of each digit run are contiguous).  The tile holds 256 x ITEMS keys;
+// ITEMS is chosen per sort so that small sorts (the weld of a 50 k-triangle mesh sorts 150 k
+// keys) still spread over every SM instead of a few dozen CTAs.
 namespace {
-constexpr int RS_THREADS = 256, RS_WARPS = RS_THREADS / 32, RS_ITEMS = 16;
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS, RADIX = 256;
-constexpr size_t RS_SMEM = (size_t)RS_TILE * (sizeof(uint64_t) + sizeof(uint32_t)) +
-                           (size_t)RS_WARPS * RADIX * sizeof(uint32_t) + 2 * RADIX * sizeof(uint32_t);
+constexpr int RS_THREADS = 256, RS_WARPS = RS_THREADS / 32, RADIX = 256;
+template <int ITEMS>
+constexpr size_t rs_smem() {
+    return (size_t)RS_THREADS * ITEMS * (sizeof(uint64_t) + sizeof(uint32_t)) +
+           (size_t)RS_WARPS * RADIX * sizeof(uint32_t) + 2 * RADIX * sizeof(uint32_t);
+}
 
+template <int ITEMS>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *keys, int64_t n, int shift,
                                                         uint32_t *hist, int64_t nb) {
+    constexpr int TILE = RS_THREADS * ITEMS;
     __shared__ uint32_t h[RADIX];
     h[threadIdx.x] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    for (int i = 0; i < RS_ITEMS; i++) {
+    int64_t base = (int64_t)blockIdx.x * TILE;
+    for (int i = 0; i < ITEMS; i++) {
         int64_t idx = base + (int64_t)i * RS_THREADS + threadIdx.x;
         if (idx < n) atomicAdd(&h[(unsigned)(keys[idx] >> shift) & (RADIX - 1)], 1u);
     }
@@ -184,27 +196,29 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *keys, in
     hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];  // digit-major
 }
 
+template <int ITEMS>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *kin, const uint32_t *vin,
                                                            uint64_t *kout, uint32_t *vout, int64_t n, int shift,
                                                            const uint32_t *offs, int64_t nb) {
+    constexpr int TILE = RS_THREADS * ITEMS;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *skey = reinterpret_cast<uint64_t *>(smem);
-    uint32_t *sval = reinterpret_cast<uint32_t *>(skey + RS_TILE);
-    uint32_t *wcnt = sval + RS_TILE;           // [RS_WARPS][RADIX]
+    uint32_t *sval = reinterpret_cast<uint32_t *>(skey + TILE);
+    uint32_t *wcnt = sval + TILE;               // [RS_WARPS][RADIX]
     uint32_t *bstart = wcnt + RS_WARPS * RADIX; // [RADIX]
     uint32_t *btot = bstart + RADIX;           // [RADIX]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < RS_WARPS * RADIX; i += RS_THREADS) wcnt[i] = 0;
     __syncthreads();
 
-    const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
-    const int64_t wbase = tile0 + (int64_t)warp * (32 * RS_ITEMS);
+    const int64_t tile0 = (int64_t)blockIdx.x * TILE;
+    const int64_t wbase = tile0 + (int64_t)warp * (32 * ITEMS);
     const uint32_t lt_mask = (1u << lane) - 1u;
-    uint64_t k[RS_ITEMS];
-    uint32_t v[RS_ITEMS], rank[RS_ITEMS];
+    uint64_t k[ITEMS];
+    uint32_t v[ITEMS], rank[ITEMS];
     uint32_t *mycnt = wcnt + warp * RADIX;
 #pragma unroll
-    for (int it = 0; it < RS_ITEMS; it++) {
+    for (int it = 0; it < ITEMS; it++) {
         int64_t idx = wbase + it * 32 + lane;
         bool valid = idx < n;
         k[it] = valid ? kin[idx] : 0ull;
@@ -239,7 +253,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *kin, 
     }
     __syncthreads();
 #pragma unroll
-    for (int it = 0; it < RS_ITEMS; it++) {
+    for (int it = 0; it < ITEMS; it++) {
         int64_t idx = wbase + it * 32 + lane;
         if (idx < n) {
             unsigned d = (unsigned)(k[it] >> shift) & (RADIX - 1);
@@ -249,7 +263,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *kin, 
         }
     }
     __syncthreads();
-    int cnt = (n - tile0 < (int64_t)RS_TILE) ? (int)(n - tile0) : RS_TILE;
+    int cnt = (n - tile0 < (int64_t)TILE) ? (int)(n - tile0) : TILE;
     for (int i = threadIdx.x; i < cnt; i += RS_THREADS) {
         uint64_t key = skey[i];
         unsigned d = (unsigned)(key >> shift) & (RADIX - 1);
@@ -258,24 +272,27 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *kin, 
         vout[g] = sval[i];
     }
 }
-}  // namespace
 
-size_t radix_tmp_bytes(int64_t n) {
-    int64_t nb = (n + RS_TILE - 1) / RS_TILE;
-    size_t hist = ((size_t)nb * RADIX + 64) * sizeof(uint32_t);
-    return hist + scan_tmp_bytes(nb * RADIX) + 256;
+// keys per thread: the largest of 16, 8, 4, 2 that still gives at least one tile per SM (the
+// SM count of this part; the count only changes the choice, not the result)
+int rs_items(int64_t n) {
+    for (int items = 16; items > 2; items >>= 1)
+        if ((n + RS_THREADS * items - 1) / (RS_THREADS * items) >= 152) return items;
+    return 2;
 }
 
-cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int64_t n,
-                           int bits, void *tmp, cudaStream_t s) {
-    if (n <= 1 || bits <= 0) return cudaSuccess;
+template <int ITEMS>
+cudaError_t rs_passes(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int64_t n, int bits,
+                      void *tmp, cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SMEM);
+        cudaError_t e = cudaFuncSetAttribute(k_rs_scatter<ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)rs_smem<ITEMS>());
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    int64_t nb = (n + RS_TILE - 1) / RS_TILE;
+    constexpr int TILE = RS_THREADS * ITEMS;
+    int64_t nb = (n + TILE - 1) / TILE;
     uint32_t *hist = reinterpret_cast<uint32_t *>(tmp);
     void *scan_tmp = hist + nb * RADIX + 64;
     int passes = (bits + 7) / 8;
@@ -283,13 +300,13 @@ cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, u
     uint32_t *vi = vals, *vo = vals_alt;
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
-        k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, s>>>(ki, n, shift, hist, nb);
+        k_rs_hist<ITEMS><<<(unsigned)nb, RS_THREADS, 0, s>>>(ki, n, shift, hist, nb);
         SDF_LAUNCHED(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = scan_exclusive_u32(hist, hist, nb * RADIX, false, scan_tmp, s);
         if (e != cudaSuccess) return e;
-        k_rs_scatter<<<(unsigned)nb, RS_THREADS, RS_SMEM, s>>>(ki, vi, ko, vo, n, shift, hist, nb);
+        k_rs_scatter<ITEMS><<<(unsigned)nb, RS_THREADS, rs_smem<ITEMS>(), s>>>(ki, vi, ko, vo, n, shift, hist, nb);
         SDF_LAUNCHED(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -303,6 +320,27 @@ cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, u
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+}  // namespace
+
+// scratch of a sort of at most n keys: sized for the smallest tile (the most tiles), so that it
+// also holds the histograms of any shorter sort, whatever tile size that one picks
+size_t radix_tmp_bytes(int64_t n) {
+    const int64_t tile = (int64_t)RS_THREADS * 2;
+    int64_t nb = (n + tile - 1) / tile;
+    size_t hist = ((size_t)nb * RADIX + 64) * sizeof(uint32_t);
+    return hist + scan_tmp_bytes(nb * RADIX) + 256;
+}
+
+cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int64_t n,
+                           int bits, void *tmp, cudaStream_t s) {
+    if (n <= 1 || bits <= 0) return cudaSuccess;
+    switch (rs_items(n)) {
+    case 16: return rs_passes<16>(keys, vals, keys_alt, vals_alt, n, bits, tmp, s);
+    case 8: return rs_passes<8>(keys, vals, keys_alt, vals_alt, n, bits, tmp, s);
+    case 4: return rs_passes<4>(keys, vals, keys_alt, vals_alt, n, bits, tmp, s);
+    default: return rs_passes<2>(keys, vals, keys_alt, vals_alt, n, bits, tmp, s);
+    }
 }
 
 }  // namespace sdf

@@ -85,6 +85,8 @@ int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const floa
                     float *const *out_dist, int32_t *const *out_winner, uint32_t flags, cudaStream_t s,
                     const ListOut *lists = nullptr);
 int ensure_events(sdf_features_s *f);
+// add the durations of pending timed calls to the handle's totals (waits for their events)
+int resolve_timing(sdf_features_s *f);
 
 }  // namespace sdf
 
@@ -119,6 +121,10 @@ struct sdf_features_s {
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     double t_ms[4] = {0, 0, 0, 0};
     int64_t t_calls[4] = {0, 0, 0, 0};
+    // events recorded by the last timed forward (ev[0..3]) / adjoint (ev[4..5]) and not read yet:
+    // they are read when the next timed call needs the events or when sdf_features_timing asks,
+    // so that timing never makes a call wait for its own work
+    bool fwd_pending = false, adj_pending = false;
 };
 
 namespace sdf {

@@ -175,3 +175,30 @@ def test_fused_list_fit_step_matches_the_dense_fit_step():
     assert torch.equal(d, d2)
     assert abs(float(loss_l) - float(loss_d)) <= 1e-12 * float(loss_d)
     assert float((gv_l - gv_d).norm()) <= 1e-5 * float(gv_d.norm())
+
+
+def test_fp64_gradient_accumulation():
+    """SDF_FLAG_GRAD_F64 (a float64 grad_vertices): the same per-point contributions summed in FP64,
+    so two runs agree to FP64 rounding whatever the order of the atomics, and the result is the
+    FP32 accumulation's up to FP32 rounding; the dense adjoint and both list adjoints agree."""
+    soup, feats, grid, w = _case("torus_ragged")
+    d, bl, wn = sdf.sdf_narrow_band_list(feats, grid, w, winner=True)
+    gen = torch.Generator(device="cuda").manual_seed(9)
+    target = (torch.rand(grid.shape, device="cuda", generator=gen) - 0.5) * 0.02
+    _, g, _ = sdf.band_l2_loss(d, target)
+    gv32 = sdf.band_list_backward(feats, grid, bl, g)
+    runs = []
+    for _ in range(2):
+        gv64 = torch.zeros(feats.n_vert, 3, dtype=torch.float64, device="cuda")
+        runs.append(sdf.band_list_backward(feats, grid, bl, g, grad_vertices=gv64))
+    scale = float(runs[0].norm())
+    assert float((runs[0] - runs[1]).norm()) <= 1e-12 * scale
+    assert float((runs[0] - gv32.double()).norm()) <= 1e-5 * scale
+    dense64 = sdf.sdf_narrow_band_backward(feats, grid, w, g, winner=wn,
+                                           grad_vertices=torch.zeros_like(runs[0]))
+    assert float((dense64 - runs[0]).norm()) <= 1e-12 * scale
+    _, fused64, _ = sdf.band_list_l2(feats, grid, bl, d, target, grad_vertices=torch.zeros_like(runs[0]))
+    assert float((fused64 - runs[0]).norm()) <= 1e-6 * scale  # g formed in the kernel vs read (FP32)
+    with pytest.raises(ValueError):
+        sdf.band_list_backward(feats, grid, bl, g, grad_vertices=torch.zeros(3, 3, dtype=torch.float64,
+                                                                             device="cuda"))
