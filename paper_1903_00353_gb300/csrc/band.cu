@@ -215,39 +215,6 @@ __device__ __forceinline__ int pack_box(int i0, int i1, int j0, int j1, int k0, 
     return a0 | (a1 << 5) | (b0 << 10) | (b1 << 14) | (c0 << 18) | (c1 << 22);
 }
 
-template <bool FILL, int TY, int TZ>
-__global__ void k_bin(const Prob *P, const long long *feat_base, const long long *tile_base, int n, long long f_tot,
-                      uint32_t *cnt, const uint32_t *start, int2 *pairs, int64_t pair_cap, DevCounters *ctr) {
-    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (gid >= f_tot) return;
-    const int p = find_prob(feat_base, n, gid);
-    const Feat &F = P[p].F;
-    const GridP &g = P[p].g;
-    const int64_t lid = gid - feat_base[p];
-    int type, id;
-    bool ok;
-    int i0, i1, j0, j1, k0, k1;
-    if (lid < F.T) { type = FACE; id = (int)lid; ok = feature_box<FACE>(F, g, id, i0, i1, j0, j1, k0, k1); }
-    else if (lid < (int64_t)F.T + F.E) { type = EDGE; id = (int)(lid - F.T); ok = feature_box<EDGE>(F, g, id, i0, i1, j0, j1, k0, k1); }
-    else { type = VERT; id = (int)(lid - F.T - F.E); ok = feature_box<VERT>(F, g, id, i0, i1, j0, j1, k0, k1); }
-    if (!ok) return;
-    const int fid = (int)lid;  // face f -> f, edge e -> T + e, vertex v -> T + E + v (within its problem)
-    const int64_t tb = tile_base[p];
-    for (int tz = k0 / TZ; tz <= k1 / TZ; tz++)
-        for (int ty = j0 / TY; ty <= j1 / TY; ty++)
-            for (int tx = i0 / TILE_X; tx <= i1 / TILE_X; tx++) {
-                const int64_t tile = tb + ((int64_t)tz * g.nty + ty) * g.ntx + tx;
-                const int64_t bin = 3 * tile + type;
-                if (!FILL) {
-                    atomicAdd(cnt + bin, 1u);
-                } else {
-                    const int64_t pos = (int64_t)start[bin] + atomicAdd(cnt + bin, 1u);
-                    if (pos < pair_cap) pairs[pos] = make_int2(fid, pack_box<TY, TZ>(i0, i1, j0, j1, k0, k1, tx, ty, tz));
-                    else atomicOr(&ctr->nb_status, ST_PAIR_OVERFLOW);
-                }
-            }
-}
-
 // ----------------------------------------------------------------------------- warp helpers
 __device__ __forceinline__ int warp_incl_scan(int v) {
     const int lane = threadIdx.x & 31;
@@ -267,6 +234,69 @@ __device__ __forceinline__ int warp_owner(int incl, int r) {
         if (v <= r) lo += s;
     }
     return lo;
+}
+
+// Binning of the regions into tiles, one thread per feature, its (feature, tile) pairs flattened
+// over the warp: in each round every lane takes one pair, lanes whose pairs fall in the same bin
+// (neighbouring features share tiles: faces, edges and vertices are numbered in spatial order)
+// are grouped by __match_any_sync, and one atomicAdd per group takes their slots.  The count pass
+// (FILL false) and the fill pass walk the same pairs in the same order.
+template <bool FILL, int TY, int TZ>
+__global__ void k_bin(const Prob *P, const long long *feat_base, const long long *tile_base, int n, long long f_tot,
+                      uint32_t *cnt, const uint32_t *start, int2 *pairs, int64_t pair_cap, DevCounters *ctr) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int p = 0, type = 0, fid = 0, ntile = 0;
+    int i0 = 0, i1 = -1, j0 = 0, j1 = -1, k0 = 0, k1 = -1;
+    if (gid < f_tot) {
+        p = find_prob(feat_base, n, gid);
+        const Feat &F = P[p].F;
+        const GridP &g = P[p].g;
+        const int64_t lid = gid - feat_base[p];
+        bool ok;
+        int id;
+        if (lid < F.T) { type = FACE; id = (int)lid; ok = feature_box<FACE>(F, g, id, i0, i1, j0, j1, k0, k1); }
+        else if (lid < (int64_t)F.T + F.E) { type = EDGE; id = (int)(lid - F.T); ok = feature_box<EDGE>(F, g, id, i0, i1, j0, j1, k0, k1); }
+        else { type = VERT; id = (int)(lid - F.T - F.E); ok = feature_box<VERT>(F, g, id, i0, i1, j0, j1, k0, k1); }
+        fid = (int)lid;  // face f -> f, edge e -> T + e, vertex v -> T + E + v (within its problem)
+        if (ok)
+            ntile = (i1 / TILE_X - i0 / TILE_X + 1) * (j1 / TY - j0 / TY + 1) * (k1 / TZ - k0 / TZ + 1);
+    }
+    const int incl = warp_incl_scan(ntile);
+    const int total = __shfl_sync(FULL, incl, 31);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int r0 = 0; r0 < total; r0 += 32) {
+        const int r = r0 + lane;
+        const bool has = r < total;
+        const int o = warp_owner(incl, has ? r : total - 1);  // every lane takes part in the search
+        const int o_incl = __shfl_sync(FULL, incl, o), o_n = __shfl_sync(FULL, ntile, o);
+        const int op = __shfl_sync(FULL, p, o), otype = __shfl_sync(FULL, type, o), ofid = __shfl_sync(FULL, fid, o);
+        const int oi0 = __shfl_sync(FULL, i0, o), oi1 = __shfl_sync(FULL, i1, o);
+        const int oj0 = __shfl_sync(FULL, j0, o), oj1 = __shfl_sync(FULL, j1, o);
+        const int ok0 = __shfl_sync(FULL, k0, o), ok1 = __shfl_sync(FULL, k1, o);
+        unsigned long long bin = (1ull << 63) | (unsigned)lane;  // inactive lanes: a group of their own
+        int tx = 0, ty = 0, tz = 0;
+        if (has) {
+            const int k = r - (o_incl - o_n);  // the owner's k-th tile, x fastest
+            const int nx = oi1 / TILE_X - oi0 / TILE_X + 1, ny = oj1 / TY - oj0 / TY + 1;
+            tx = oi0 / TILE_X + k % nx;
+            ty = oj0 / TY + (k / nx) % ny;
+            tz = ok0 / TZ + k / (nx * ny);
+            const GridP &g = P[op].g;
+            const int64_t tile = tile_base[op] + ((int64_t)tz * g.nty + ty) * g.ntx + tx;
+            bin = (unsigned long long)(3 * tile + otype);
+        }
+        const unsigned peers = __match_any_sync(FULL, bin);
+        const int leader = __ffs(peers) - 1;
+        unsigned base = 0;
+        if (has && lane == leader) base = atomicAdd(cnt + bin, (unsigned)__popc(peers));
+        base = __shfl_sync(FULL, base, leader);
+        if (FILL && has) {
+            const int64_t pos = (int64_t)start[bin] + base + __popc(peers & lt_mask);
+            if (pos < pair_cap) pairs[pos] = make_int2(ofid, pack_box<TY, TZ>(oi0, oi1, oj0, oj1, ok0, ok1, tx, ty, tz));
+            else atomicOr(&ctr->nb_status, ST_PAIR_OVERFLOW);
+        }
+    }
 }
 
 __device__ __forceinline__ float comp(float4 P, int ax) { return ax == 0 ? P.x : (ax == 1 ? P.y : P.z); }
