@@ -273,10 +273,12 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *kin, 
     }
 }
 
-// keys per thread: the largest of 16, 8, 4, 2 that still gives at least one tile per SM (the
-// SM count of this part; the count only changes the choice, not the result)
+// keys per thread: the largest of 8, 4, 2 that still gives at least one tile per SM (the SM
+// count of this part; the count only changes the choice, not the result).  16 keys per thread
+// would need 127 registers, two CTAs per SM: the 6.3 M-key sort of the knot tube ran its scatter
+// passes faster with 8.
 int rs_items(int64_t n) {
-    for (int items = 16; items > 2; items >>= 1)
+    for (int items = 8; items > 2; items >>= 1)
         if ((n + RS_THREADS * items - 1) / (RS_THREADS * items) >= 152) return items;
     return 2;
 }
@@ -336,7 +338,6 @@ cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, u
                            int bits, void *tmp, cudaStream_t s) {
     if (n <= 1 || bits <= 0) return cudaSuccess;
     switch (rs_items(n)) {
-    case 16: return rs_passes<16>(keys, vals, keys_alt, vals_alt, n, bits, tmp, s);
     case 8: return rs_passes<8>(keys, vals, keys_alt, vals_alt, n, bits, tmp, s);
     case 4: return rs_passes<4>(keys, vals, keys_alt, vals_alt, n, bits, tmp, s);
     default: return rs_passes<2>(keys, vals, keys_alt, vals_alt, n, bits, tmp, s);
