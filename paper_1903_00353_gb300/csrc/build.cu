@@ -49,15 +49,32 @@ __global__ void k_soup_bounds(const float *soup, int64_t n3, float *bb, DevCount
         }
     }
     if (bad) atomicOr(&ctr->status, ST_NONFINITE);
+    // warp, then block reduction; six atomics per block (same-address atomics serialise in L2)
     for (int j = 0; j < 3; j++) {
         for (int o = 16; o > 0; o >>= 1) {
             lo[j] = fminf(lo[j], __shfl_xor_sync(0xffffffffu, lo[j], o));
             hi[j] = fmaxf(hi[j], __shfl_xor_sync(0xffffffffu, hi[j], o));
         }
     }
-    if ((threadIdx.x & 31) == 0) {
+    __shared__ float s_lo[3][32], s_hi[3][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0)
         for (int j = 0; j < 3; j++) {
-            if (lo[j] <= hi[j]) { atomic_min_f(bb + j, lo[j]); atomic_max_f(bb + 3 + j, hi[j]); }
+            s_lo[j][warp] = lo[j];
+            s_hi[j][warp] = hi[j];
+        }
+    __syncthreads();
+    if (warp == 0) {
+        for (int j = 0; j < 3; j++) {
+            float l = lane < nw ? s_lo[j][lane] : INFINITY, h = lane < nw ? s_hi[j][lane] : -INFINITY;
+            for (int o = 16; o > 0; o >>= 1) {
+                l = fminf(l, __shfl_xor_sync(0xffffffffu, l, o));
+                h = fmaxf(h, __shfl_xor_sync(0xffffffffu, h, o));
+            }
+            if (lane == 0 && l <= h) {
+                atomic_min_f(bb + j, l);
+                atomic_max_f(bb + 3 + j, h);
+            }
         }
     }
 }
@@ -603,7 +620,8 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     B_TRY(cudaMemsetAsync(f->ctr, 0, sizeof(DevCounters), s));
     float bb_init[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
     B_TRY(cudaMemcpyAsync(bb, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
-    k_soup_bounds<<<(unsigned)std::min<int64_t>(nblk(n), 4 * 152), BT, 0, s>>>(soup, n, bb, f->ctr);
+    // about four corners per thread, at most four blocks per SM of this part
+    k_soup_bounds<<<(unsigned)std::min<int64_t>((n + 4 * BT - 1) / (4 * BT), 4 * 152), BT, 0, s>>>(soup, n, bb, f->ctr);
     SDF_LAUNCHED(1);
     k_weld_keys<<<nblk(n), BT, 0, s>>>(soup, n, bb, keys, vals);
     SDF_LAUNCHED(1);
