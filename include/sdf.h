@@ -360,6 +360,20 @@ int sdf_narrow_band_list(sdf_features f, const sdf_grid *grid, float band_w, flo
                          unsigned long long *list_count, uint32_t flags, void *stream);
 
 /*
+ * sdf_narrow_band_lists -- the same for n problems in one batch (as sdf_narrow_band with n > 1:
+ * one persistent tile launch over all problems, synchronous): problem p writes its field to
+ * out_dist[p] and its band list to lists[p] (list_caps[p] entries, length to *list_counts[p],
+ * point indices within its own grid).  out_winner as for sdf_narrow_band (nullable).  A list that
+ * is too short makes the call return SDF_ERR_LIST_OVERFLOW; every count still holds the length
+ * its problem needs.
+ * Errors: those of sdf_narrow_band, and SDF_ERR_LIST_OVERFLOW.
+ */
+int sdf_narrow_band_lists(const sdf_features *feats, const sdf_grid *grids, const float *band_w, int32_t n,
+                          float *const *out_dist, int32_t *const *out_winner, sdf_band_entry *const *lists,
+                          const int64_t *list_caps, unsigned long long *const *list_counts, uint32_t flags,
+                          void *stream);
+
+/*
  * sdf_band_list_backward -- the adjoint of sdf_narrow_band_backward over the entries of a band
  * list: grad_vertices += sum over entries e of g(idx_e) * d d(p) / d X at p = point idx_e with
  * winner winner_e (the same per-point contribution as sdf_narrow_band_backward).

@@ -20,7 +20,7 @@ from . import _buildlib
 
 __all__ = ["Grid", "Features", "sdf_build_features", "sdf_narrow_band", "sdf_narrow_band_backward",
            "SDFFunction", "Batch", "sdf_batch_create", "band_l2_loss", "load_library", "kernel_launches", "SDFError",
-           "BandList", "sdf_narrow_band_list", "band_list_backward", "band_list_l2",
+           "BandList", "sdf_narrow_band_list", "sdf_narrow_band_lists", "band_list_backward", "band_list_l2",
            "FLAG_DISABLE_SADDLE", "FLAG_NO_SYNC", "FLAG_TIMING", "FLAG_AUTOTUNE", "FLAG_FILL_SIGN",
            "FLAG_CELL_LOOP", "FLAG_VERTEX_CONE", "FLAG_VERTEX_HEMISPHERE", "FLAG_GRAD_F64"]
 
@@ -93,6 +93,9 @@ def load_library(path: str | None = None):
     L.sdf_batch_timing.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
     L.sdf_band_l2_loss.argtypes = [P, P, I64, P, P, P, P]
     L.sdf_narrow_band_list.argtypes = [P, ctypes.POINTER(_CGrid), ctypes.c_float, P, P, P, I64, P, U32, P]
+    L.sdf_narrow_band_lists.argtypes = [ctypes.POINTER(P), ctypes.POINTER(_CGrid), ctypes.POINTER(ctypes.c_float), I32,
+                                        ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I64),
+                                        ctypes.POINTER(P), U32, P]
     L.sdf_band_list_backward.argtypes = [P, ctypes.POINTER(_CGrid), P, I64, P, P, P, U32, P]
     L.sdf_band_list_l2.argtypes = [P, ctypes.POINTER(_CGrid), P, I64, P, P, P, P, P, P, U32, P]
     L.sdf_batch_destroy.argtypes = [P]
@@ -101,7 +104,7 @@ def load_library(path: str | None = None):
                  "sdf_narrow_band_backward", "sdf_features_info", "sdf_features_vertex_map",
                  "sdf_features_vertices", "sdf_features_status", "sdf_batch_create", "sdf_batch_run",
                  "sdf_batch_status", "sdf_batch_info", "sdf_batch_timing", "sdf_band_l2_loss",
-                 "sdf_narrow_band_list", "sdf_band_list_backward", "sdf_band_list_l2"):
+                 "sdf_narrow_band_list", "sdf_narrow_band_lists", "sdf_band_list_backward", "sdf_band_list_l2"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -464,6 +467,46 @@ def sdf_narrow_band_list(features: Features, grid: Grid, w: float, out: torch.Te
         _check(code, "sdf_narrow_band_list")
         break
     return (out, band_list, win) if win is not None else (out, band_list)
+
+
+def sdf_narrow_band_lists(features: Sequence[Features], grids: Sequence[Grid], ws: Sequence[float],
+                          outs: Sequence[torch.Tensor] | None = None,
+                          band_lists: Sequence[BandList] | None = None, stream=None):
+    """The narrow bands of a batch of problems in one launch sequence, each with its band list:
+    returns (dists, band_lists).  Lists that turn out too short are grown to their band's length
+    and the call repeated once."""
+    feats, grids, ws = list(features), list(grids), list(ws)
+    n = len(feats)
+    if not (len(grids) == len(ws) == n) or n == 0:
+        raise ValueError("features, grids and ws must have the same, non-zero length")
+    if outs is None:
+        outs = [torch.empty(g.shape, dtype=torch.float32, device="cuda") for g in grids]
+    else:
+        outs = list(outs)
+        for o, g in zip(outs, grids):
+            _dev_f32(o, "out")
+            if o.numel() != g.nx * g.ny * g.nz:
+                raise ValueError("out has the wrong size")
+    lists = list(band_lists) if band_lists is not None else [BandList(BandList.default_capacity(g)) for g in grids]
+    if len(lists) != n:
+        raise ValueError("one band list per problem")
+    fa = (ctypes.c_void_p * n)(*[f.handle.value for f in feats])
+    ga = (_CGrid * n)(*[g.c() for g in grids])
+    wa = (ctypes.c_float * n)(*[float(x) for x in ws])
+    for attempt in range(2):
+        caps = (ctypes.c_int64 * n)(*[bl.capacity for bl in lists])
+        code = load_library().sdf_narrow_band_lists(
+            fa, ga, wa, n, _ptr_array(outs), None, _ptr_array([bl.entries for bl in lists]), caps,
+            _ptr_array([bl.count for bl in lists]), 0, _stream(stream))
+        if code == ERR_LIST_OVERFLOW and attempt == 0:
+            for bl in lists:
+                need = int(bl.count.item())
+                if need > bl.capacity:
+                    bl.entries = torch.empty((need + need // 4 + 1024, 2), dtype=torch.int32, device="cuda")
+            continue
+        _check(code, "sdf_narrow_band_lists")
+        break
+    return outs, lists
 
 
 def band_list_backward(features: Features, grid: Grid, band_list: BandList, grad_dist: torch.Tensor,

@@ -1859,6 +1859,22 @@ extern "C" int sdf_narrow_band_list(sdf_features f, const sdf_grid *grid, float 
     return sdf::narrow_band_all(fl, grid, &band_w, 1, dl, wl, flags, reinterpret_cast<cudaStream_t>(stream), lo);
 }
 
+extern "C" int sdf_narrow_band_lists(const sdf_features *feats, const sdf_grid *grids, const float *band_w, int32_t n,
+                                     float *const *out_dist, int32_t *const *out_winner, sdf_band_entry *const *lists,
+                                     const int64_t *list_caps, unsigned long long *const *list_counts, uint32_t flags,
+                                     void *stream) {
+    if (!feats || !grids || !band_w || n < 1 || !out_dist || !lists || !list_caps || !list_counts)
+        return SDF_ERR_INVALID_ARG;
+    if (flags & SDF_FLAG_CELL_LOOP) return SDF_ERR_INVALID_ARG;
+    std::vector<sdf::ListOut> lo((size_t)n);
+    for (int p = 0; p < n; p++) {
+        if (!lists[p] || !list_counts[p] || list_caps[p] < 0) return SDF_ERR_INVALID_ARG;
+        lo[p] = sdf::ListOut{lists[p], (long long)list_caps[p], list_counts[p]};
+    }
+    return sdf::narrow_band_all(feats, grids, band_w, n, out_dist, out_winner, flags,
+                                reinterpret_cast<cudaStream_t>(stream), lo.data());
+}
+
 // ----------------------------------------------------------------------------- batches for CUDA graphs
 struct sdf_batch_s {
     sdf::Plan plan;

@@ -57,6 +57,7 @@ def test_argument_validation_without_device(lib):
     lib.sdf_batch_destroy(None)
     assert lib.sdf_band_l2_loss(None, None, 0, None, None, None, None) == 1
     assert lib.sdf_narrow_band_list(None, None, 0.1, None, None, None, 0, None, 0, None) == 1
+    assert lib.sdf_narrow_band_lists(None, None, None, 1, None, None, None, None, None, 0, None) == 1
     assert lib.sdf_band_list_backward(None, None, None, 0, None, None, None, 0, None) == 1
     assert lib.sdf_band_list_l2(None, None, None, 0, None, None, None, None, None, None, 0, None) == 1
 

@@ -202,3 +202,20 @@ def test_fp64_gradient_accumulation():
     with pytest.raises(ValueError):
         sdf.band_list_backward(feats, grid, bl, g, grad_vertices=torch.zeros(3, 3, dtype=torch.float64,
                                                                              device="cuda"))
+
+
+def test_batched_lists_equal_the_single_problem_fields_and_bands():
+    """sdf_narrow_band_lists: a batch of three problems in one launch sequence, every list starting
+    too short (grown by the binding after the call reports the overflow)."""
+    names = ["icosphere_c1", "torus_ragged", "box_union"]
+    cases = [_case(nm) for nm in names]
+    feats, grids, ws = [c[1] for c in cases], [c[2] for c in cases], [c[3] for c in cases]
+    dists, lists = sdf.sdf_narrow_band_lists(feats, grids, ws, band_lists=[sdf.BandList(100) for _ in names])
+    for f, g, w, d, bl in zip(feats, grids, ws, dists, lists):
+        d_ref, w_ref = sdf.sdf_narrow_band(f, g, w, winner=True)
+        assert torch.equal(d, d_ref)
+        band = torch.nonzero(torch.isfinite(d_ref.view(-1))).view(-1)
+        idx = bl.indices().long()
+        assert len(bl) == band.numel() > 100
+        assert torch.equal(torch.sort(idx).values, band)
+        assert torch.equal(bl.winners().long(), w_ref.view(-1)[idx].long())
