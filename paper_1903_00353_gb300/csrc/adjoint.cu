@@ -7,9 +7,12 @@
 // vertices x_k: lam are the barycentric weights on a face, (1 - t, t) on an edge, 1 at a vertex.
 // Inside a face region s * (p - q)/|p - q| is the face normal n, so no sign is needed there.
 //
-// Band points are compacted over the lanes of a warp in grid order; lanes that hit the same vertex
-// in a run are merged by a segmented warp scan before the atomicAdd (warp-aggregated atomics),
-// since neighbouring band points usually share their winner.
+// Band points come either from the dense winner array (k_adjoint: compacted over the lanes of a
+// warp in grid order) or from a compact band list (k_adjoint_list, which can also form the
+// fitting loss's upstream gradient itself); lanes that hit the same vertex in a run are merged by
+// a segmented warp scan before the atomicAdd (warp-aggregated atomics), since neighbouring band
+// points usually share their winner.  The sums are FP32, or FP64 with SDF_FLAG_GRAD_F64.  The
+// file ends with the dense fused loss (sdf_band_l2_loss).
 #include "sdf_internal.cuh"
 
 namespace sdf {

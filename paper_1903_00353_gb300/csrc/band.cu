@@ -17,20 +17,23 @@
 // GB300 schedule (replacing the paper's thread-per-extrusion cell loop, Section 9), for a batch of
 // one or more (mesh, grid) problems described by a device table of Prob entries:
 //   1. bin: every region's integer bounding box is split over 32xTYxTZ-point tiles (8x8 by
-//      default; 4x4 and 16x8 for the autotuner) and the (tile, region) pairs are bucketed per
-//      tile and type (count, scan, fill); tiles of all problems share one numbering;
-//   2. tile kernel: a persistent grid (3 CTAs of 256 threads per SM) takes work items from one
-//      atomic ticket: a band tile plus its share of the empty tiles.  A band tile keeps the
-//      packed keys (|d| bits << 32 | id << 1 | sign) of its points in shared memory; for 256
-//      regions at a time, one thread per region computes the region's box in the tile, its scan
-//      axis and per-plane span coefficients (Algorithm 2 restricted to grid lines, with the
-//      inclusion tolerance of Section 10), a block scan numbers their rows, each lane evaluates
-//      one row's span from the coefficients, and the span points are flattened across lanes,
-//      evaluated against the feature and merged with a shared-memory 64-bit atomicMin
-//      (Algorithm 1's min-magnitude rule).  The CTA then writes its tile of the dense output
-//      (coalesced 16-byte rows), +inf outside the band, and queues the few points whose band
-//      membership or sign lies inside the FP32 error window.  Empty tiles are written +inf;
-//   3. patch kernel: re-decides the queued points in FP64 from the winner's neighbourhood.
+//      default; 4x4 and 16x8 for the autotuner) and the (tile, region) pairs, each with the
+//      region's box clipped to the tile, are bucketed per tile and type (count, scan, fill;
+//      a warp's pairs share one atomic per bin); tiles of all problems share one numbering;
+//   2. tile kernel: a persistent grid (4 CTAs of 256 threads per SM) takes work items from one
+//      atomic ticket: a band tile plus its share of the empty tiles (band tiles largest first
+//      for batches).  A band tile keeps the packed keys (|d| bits << 32 | id << 1 | sign) of
+//      its points in shared memory.  Warps take chunks of at most 32 of the tile's regions
+//      without block barriers: one lane per region computes its scan axis and per-plane span
+//      coefficients (Algorithm 2 restricted to grid lines, with the inclusion tolerance of
+//      Section 10), a warp scan numbers the rows, each lane evaluates one row's span, and the
+//      span points are flattened across lanes, evaluated against the feature and merged with a
+//      shared-memory 64-bit atomicMin (Algorithm 1's min-magnitude rule).  The CTA then writes
+//      its tile of the dense output (coalesced 16-byte rows), +inf outside the band, optionally
+//      the winners or the compact band list, and queues the few points whose band membership
+//      or sign lies inside the FP32 error window.  Empty tiles are written +inf;
+//   3. patch kernel: re-decides the queued points in FP64 from the winner's neighbourhood (and
+//      appends those it puts in the band to the band list).
 #include <math.h>
 #include <stddef.h>
 #include <stdint.h>
