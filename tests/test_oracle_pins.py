@@ -398,3 +398,39 @@ def test_box_union_closed_form(k, seed):
         exact[np.nonzero(sel)[0][free]] = True
     assert exact.sum() > 300
     assert np.max(np.abs(-d[exact] - depth[exact])) < 1e-12
+
+
+def test_adjoint_matches_finite_differences_on_a_box_union():
+    """The adjoint where the closest feature is a concave crease or a saddle vertex: a union of
+    three overlapping rotated boxes, with the perturbed vertices drawn from those on the
+    intersection curves (vertices inside no box face's interior grid), against central
+    differences of the oracle's own distances."""
+    mesh, boxes = meshgen.box_union(3, 300, seed=2, return_boxes=True)
+    X, tri = mesh.vertices, mesh.triangles
+    w = 0.05
+    pts, g = _band_loss_points(mesh, w, 4000, 5)
+    om = oracle.OracleMesh.from_indexed(X, tri)
+    d0, _, _ = om.sdf_points(pts)
+    frozen = np.abs(d0) < w
+    pts, g = pts[frozen], g[frozen]
+    grad = om.adjoint_points(pts, g, w=np.inf)
+    # vertices on two box surfaces at once: the creases and their corners
+    sd = np.stack([_rotated_box_sdf(X, *b)[0] for b in boxes])
+    crease = np.nonzero((np.abs(sd) < 1e-9).sum(axis=0) >= 2)[0]
+    assert crease.size >= 12
+    rng = np.random.default_rng(6)
+    verts = rng.choice(crease, size=min(24, crease.size), replace=False)
+    eps = 1e-6
+    fd, an = [], []
+    for v in verts:
+        for c in range(3):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[v, c] += eps
+            Xm[v, c] -= eps
+            dp, _, _ = oracle.OracleMesh.from_indexed(Xp, tri).sdf_points(pts)
+            dm, _, _ = oracle.OracleMesh.from_indexed(Xm, tri).sdf_points(pts)
+            fd.append(float(g @ (dp - dm)) / (2 * eps))
+            an.append(grad[v, c])
+    fd, an = np.array(fd), np.array(an)
+    assert np.linalg.norm(fd) > 0
+    assert np.linalg.norm(fd - an) <= 1e-4 * np.linalg.norm(fd)
