@@ -381,7 +381,8 @@ int sdf_narrow_band_lists(const sdf_features *feats, const sdf_grid *grids, cons
  *                                the count is read on the device, so the call never synchronises).
  *   grad_dist      device float[nz][ny][nx] (dL/dd; read at the listed points only).
  *   grad_vertices  device float[V][3] (double[V][3] with SDF_FLAG_GRAD_F64), ACCUMULATED into.
- * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_CUDA.
+ * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_TOO_LARGE (a grid of more than 2^32 - 1 points),
+ * SDF_ERR_CUDA.
  */
 int sdf_band_list_backward(sdf_features f, const sdf_grid *grid, const sdf_band_entry *list, int64_t list_cap,
                            const unsigned long long *list_count, const float *grad_dist, float *grad_vertices,
@@ -395,7 +396,7 @@ int sdf_band_list_backward(sdf_features f, const sdf_grid *grid, const sdf_band_
  *   dist, target   device float[nz][ny][nx] (read at the listed points only).
  *   loss_out       device double, overwritten (FP64 sum of the FP32 squared differences).
  *   band_out       device uint64 or NULL, overwritten with the number of listed points used.
- * No synchronisation.  Errors: SDF_ERR_INVALID_ARG, SDF_ERR_CUDA.
+ * No synchronisation.  Errors: SDF_ERR_INVALID_ARG, SDF_ERR_TOO_LARGE (as above), SDF_ERR_CUDA.
  */
 int sdf_band_list_l2(sdf_features f, const sdf_grid *grid, const sdf_band_entry *list, int64_t list_cap,
                      const unsigned long long *list_count, const float *dist, const float *target,
