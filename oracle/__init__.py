@@ -50,6 +50,9 @@ def lib():
             L.om_band_points.argtypes = [P, P, P, D, D, P, I64, ctypes.c_int, P, P, P]
             L.om_narrow_band.argtypes = [P, P, P, D, D, ctypes.c_int, P, P]
             L.om_adjoint_points.argtypes = [P, P, P, I64, D, P]
+            L.om_adjoint_features.argtypes = [P, P, P, P, P, I64, P, P]
+            L.om_set_num_threads.argtypes = [ctypes.c_int]
+            L.om_set_num_threads.restype = None
             L.om_num_threads.restype = ctypes.c_int
             _lib = L
         return _lib
@@ -167,9 +170,42 @@ class OracleMesh:
         lib().om_adjoint_points(self._h, _ptr(p), _ptr(g), p.shape[0], float(w), _ptr(out))
         return out
 
+    def adjoint_features(self, pts: np.ndarray, g: np.ndarray, tri: np.ndarray, region: np.ndarray):
+        """The adjoint of sum_p g_p d_F(p) [V,3] with each point's feature F GIVEN as (triangle,
+        region label: 0 face, 1+k edge from corner k to k+1, 4+k corner k), and the signed
+        distances d_F(p) [n]; no band test."""
+        p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        region = np.ascontiguousarray(region, dtype=np.int32)
+        n = p.shape[0]
+        assert g.shape == (n,) and tri.shape == (n,) and region.shape == (n,)
+        if n and (tri.min() < 0 or tri.max() >= self.T or region.min() < 0 or region.max() > 6):
+            raise ValueError("feature out of range")
+        out = np.empty((self.V, 3))
+        d = np.empty(n)
+        lib().om_adjoint_features(self._h, _ptr(p), _ptr(g), _ptr(tri), _ptr(region), n, _ptr(out), _ptr(d))
+        return out, d
+
 
 def num_threads() -> int:
     return int(lib().om_num_threads())
+
+
+_DEFAULT_THREADS = None
+
+
+def num_threads_default() -> int:
+    """The thread count the oracle started with (before any set_num_threads)."""
+    return _DEFAULT_THREADS if _DEFAULT_THREADS else num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """OpenMP threads of the following oracle calls (1: sums in one fixed order)."""
+    global _DEFAULT_THREADS
+    if _DEFAULT_THREADS is None:
+        _DEFAULT_THREADS = num_threads()
+    lib().om_set_num_threads(int(n))
 
 
 def grid_points(dims, origin, h: float, idx: np.ndarray) -> np.ndarray:

@@ -37,6 +37,11 @@
  * welded (qsort on the exact values; -0 == +0), and each directed edge must
  * meet exactly one opposite directed edge (closed 2-manifold), else an error.
  *
+ * The adjoint (a project addition) is the envelope-theorem derivative of d = s |p - q(X)|
+ * with respect to the welded vertices, either at each point's own closest feature
+ * (om_adjoint_points) or at a feature the caller gives per point (om_adjoint_features), so
+ * that another implementation's winners can be evaluated in FP64.
+ *
  * Parity pins: see tests/test_oracle_*.py (exact-rational brute force,
  * closed forms of a box and a regular tetrahedron, Eikonal, translation and
  * rotation covariance, ray-parity inside test, finite differences).
@@ -537,17 +542,53 @@ void om_narrow_band(const om_mesh *m, const int32_t *dims, const double *origin,
     }
 }
 
+/* Contribution of one point to the adjoint of L = sum_p g_p d(p): for d = s |p - q(X)| with
+ * q = sum_k lam_k X_k the closest point of the triangle's feature (lam fixed at the minimiser:
+ * envelope theorem), dd/dX_k = -s lam_k (p - q)/|p - q|.  b is the point's hit (triangle, region
+ * label, weights, squared distance) and d its signed value; mine [V][3] is accumulated into. */
+static void add_point_adjoint(const om_mesh *m, const double *p, double g, const hit *b, double d, double *mine) {
+    const int32_t *tv = m->tri + 3 * b->t;
+    const double *A = m->X + 3 * tv[0];
+    double pq[3];
+    v_sub(p, A, pq);
+    for (int k = 1; k < 3; k++)
+        for (int j = 0; j < 3; j++) pq[j] -= b->lam[k] * (m->X[3 * tv[k] + j] - A[j]);
+    double u[3];
+    if (b->region == 0) {
+        /* (p - q)/|p - q| = s n inside the face region */
+        for (int j = 0; j < 3; j++) u[j] = m->fn[3 * b->t + j] * (d < 0 ? -1.0 : 1.0);
+    } else {
+        double r = sqrt(b->d2);
+        for (int j = 0; j < 3; j++) u[j] = pq[j] / r;
+    }
+    double s = d < 0 ? -1.0 : 1.0;
+    for (int k = 0; k < 3; k++)
+        for (int j = 0; j < 3; j++) mine[3 * tv[k] + j] += -g * s * b->lam[k] * u[j];
+}
+
+/* Per-thread accumulators summed into out_grad [V][3] (overwritten) in thread order. */
+static double *adjoint_acc(const om_mesh *m, int *nth) {
+    *nth = 1;
+#ifdef _OPENMP
+    *nth = omp_get_max_threads();
+#endif
+    return (double *)calloc((size_t)*nth * 3 * (m->V ? m->V : 1), sizeof(double));
+}
+static void adjoint_sum(const om_mesh *m, double *acc, int nth, double *out_grad) {
+    memset(out_grad, 0, sizeof(double) * 3 * m->V);
+    for (int t = 0; t < nth; t++)
+        for (int64_t v = 0; v < 3 * m->V; v++) out_grad[v] += acc[(size_t)t * 3 * m->V + v];
+    free(acc);
+}
+
 /* Adjoint of L = sum_p g_p d(p) with respect to the welded vertex positions, at the given
  * points (their band membership and winners as found here).  For d = s |p - q(X)| with
  * q = sum_k lam_k X_k the closest point (lam fixed at the minimiser: envelope theorem),
  * dd/dX_k = -s lam_k (p - q)/|p - q|.  out_grad [V][3] is overwritten. */
 void om_adjoint_points(const om_mesh *m, const double *pts, const double *g, int64_t n, double w,
                        double *out_grad) {
-    int nth = 1;
-#ifdef _OPENMP
-    nth = omp_get_max_threads();
-#endif
-    double *acc = (double *)calloc((size_t)nth * 3 * (m->V ? m->V : 1), sizeof(double));
+    int nth;
+    double *acc = adjoint_acc(m, &nth);
 #pragma omp parallel
     {
         int tid = 0;
@@ -562,29 +603,100 @@ void om_adjoint_points(const om_mesh *m, const double *pts, const double *g, int
             if (b.t < 0 || g[i] == 0.0 || b.d2 == 0.0) continue;
             double d = signed_from(m, p, b.t, b.region, b.lam, b.d2);
             if (!(fabs(d) < w)) continue;
-            const int32_t *tv = m->tri + 3 * b.t;
-            const double *A = m->X + 3 * tv[0];
-            double pq[3];
-            v_sub(p, A, pq);
-            for (int k = 1; k < 3; k++)
-                for (int j = 0; j < 3; j++) pq[j] -= b.lam[k] * (m->X[3 * tv[k] + j] - A[j]);
-            double u[3];
-            if (b.region == 0) {
-                /* (p - q)/|p - q| = s n inside the face region */
-                for (int j = 0; j < 3; j++) u[j] = m->fn[3 * b.t + j] * (d < 0 ? -1.0 : 1.0);
-            } else {
-                double r = sqrt(b.d2);
-                for (int j = 0; j < 3; j++) u[j] = pq[j] / r;
-            }
-            double s = d < 0 ? -1.0 : 1.0;
-            for (int k = 0; k < 3; k++)
-                for (int j = 0; j < 3; j++) mine[3 * tv[k] + j] += -g[i] * s * b.lam[k] * u[j];
+            add_point_adjoint(m, p, g[i], &b, d, mine);
         }
     }
-    memset(out_grad, 0, sizeof(double) * 3 * m->V);
-    for (int t = 0; t < nth; t++)
-        for (int64_t v = 0; v < 3 * m->V; v++) out_grad[v] += acc[(size_t)t * 3 * m->V + v];
-    free(acc);
+    adjoint_sum(m, acc, nth, out_grad);
+}
+
+/* The closest point of p on one given feature of triangle t: region 0 the closed triangle,
+ * 1 + k its closed edge from corner k to corner k + 1, 4 + k its corner k (the labels of
+ * pt_tri).  Returns the hit (whose region labels where on the feature the closest point lies:
+ * the feature's relative interior or one of its end points) and sets *d to the signed
+ * distance, the sign from the pseudonormal of that feature (Section 4.3, Eq. 8).
+ *
+ * If the closest point of the whole triangle lies on the given feature, it is also the
+ * feature's closest point (the feature is a subset of the triangle), so pt_tri's result is
+ * taken as it is; otherwise the feature's own closest point is computed on the segment (with
+ * the arithmetic of pt_tri's segment loop, relative to corner 0) or is the corner itself. */
+static hit feature_hit(const om_mesh *m, const double *p, int64_t t, int region, double *d) {
+    const int32_t *tv = m->tri + 3 * t;
+    const double *A = m->X + 3 * tv[0];
+    hit b = {INFINITY, t, -1, {0, 0, 0}};
+    b.d2 = pt_tri(p, A, m->X + 3 * tv[1], m->X + 3 * tv[2], m->fn + 3 * t, &b.region, b.lam);
+    int on_feature;
+    if (region == 0) on_feature = 1;
+    else if (region <= 3) on_feature = b.region == region || b.region == 4 + (region - 1) || b.region == 4 + region % 3;
+    else on_feature = b.region == region;
+    if (!on_feature) {
+        double ap[3], P[3][3];
+        v_sub(p, A, ap);
+        P[0][0] = P[0][1] = P[0][2] = 0.0;
+        v_sub(m->X + 3 * tv[1], A, P[1]);
+        v_sub(m->X + 3 * tv[2], A, P[2]);
+        b.lam[0] = b.lam[1] = b.lam[2] = 0.0;
+        if (region <= 3) {
+            int k = region - 1;
+            const double *S = P[k], *E = P[(k + 1) % 3];
+            double se[3], sp[3];
+            v_sub(E, S, se);
+            v_sub(ap, S, sp);
+            double tt = v_dot(sp, se) / v_dot(se, se);
+            tt = tt < 0 ? 0 : (tt > 1 ? 1 : tt);
+            double r[3] = {sp[0] - tt * se[0], sp[1] - tt * se[1], sp[2] - tt * se[2]};
+            b.d2 = v_dot(r, r);
+            b.lam[k] = 1.0 - tt;
+            b.lam[(k + 1) % 3] = tt;
+            b.region = tt == 0.0 ? 4 + k : (tt == 1.0 ? 4 + (k + 1) % 3 : 1 + k);
+        } else {
+            int k = region - 4;
+            double r[3];
+            v_sub(ap, P[k], r);
+            b.d2 = v_dot(r, r);
+            b.lam[k] = 1.0;
+            b.region = region;
+        }
+    }
+    *d = signed_from(m, p, t, b.region, b.lam, b.d2);
+    return b;
+}
+
+/* The adjoint of L = sum_p g_p d_F(p) where d_F(p) is the signed distance of point p to a
+ * GIVEN feature (tri[i], region[i]) (labels as in feature_hit), not to its own closest one:
+ * the same per-point contribution as om_adjoint_points with the winner fixed by the caller, so
+ * that another implementation's choice of winners can be evaluated in FP64.  No band test.
+ * out_grad [V][3] is overwritten; out_d [n] (nullable) receives d_F(p). */
+void om_adjoint_features(const om_mesh *m, const double *pts, const double *g, const int32_t *tri,
+                         const int32_t *region, int64_t n, double *out_grad, double *out_d) {
+    int nth;
+    double *acc = adjoint_acc(m, &nth);
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *mine = acc + (size_t)tid * 3 * m->V;
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < n; i++) {
+            const double *p = pts + 3 * i;
+            double d = INFINITY;
+            hit b = feature_hit(m, p, tri[i], region[i], &d);
+            if (out_d) out_d[i] = d;
+            if (g[i] == 0.0 || b.d2 == 0.0) continue;
+            add_point_adjoint(m, p, g[i], &b, d, mine);
+        }
+    }
+    adjoint_sum(m, acc, nth, out_grad);
+}
+
+/* Number of OpenMP threads of the following calls (tests compare sums in one fixed order). */
+void om_set_num_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
 }
 
 int om_num_threads(void) {

@@ -434,3 +434,112 @@ def test_adjoint_matches_finite_differences_on_a_box_union():
     fd, an = np.array(fd), np.array(an)
     assert np.linalg.norm(fd) > 0
     assert np.linalg.norm(fd - an) <= 1e-4 * np.linalg.norm(fd)
+
+
+# ------------------------------------------------------------------ the adjoint on given features
+def test_adjoint_on_given_features_equals_own_winner_adjoint_bitwise():
+    """Where each point's given feature is the oracle's own winner (triangle and region label from
+    the point query), the given-feature adjoint and distances are bitwise those of the searching
+    adjoint and of the point query (one thread, so both sum in the same order)."""
+    for mesh, w in ((meshgen.torus(nu=40, nv=16, seed=5), 0.04), (meshgen.box_union(3, 300, seed=2), 0.05)):
+        X, tri = mesh.vertices, mesh.triangles
+        om = oracle.OracleMesh.from_indexed(X, tri)
+        pts, g = _band_loss_points(mesh, w, 3000, 21)
+        d, t, r = om.sdf_points(pts)
+        keep = np.abs(d) < w
+        pts, g, d, t, r = pts[keep], g[keep], d[keep], t[keep], r[keep]
+        labels = set(r.tolist())  # face, edge and corner winners all occur
+        assert 0 in labels and labels & {1, 2, 3} and labels & {4, 5, 6}
+        oracle.set_num_threads(1)
+        try:
+            ref = om.adjoint_points(pts, g, w=np.inf)
+            got, dF = om.adjoint_features(pts, g, t, r)
+        finally:
+            oracle.set_num_threads(oracle.num_threads_default())
+        assert np.array_equal(dF, d)
+        assert np.array_equal(got, ref)
+
+
+def _segment_dist_sampled(p, a, b, n=200001):
+    s = np.linspace(0.0, 1.0, n)
+    q = a[None, :] + s[:, None] * (b - a)[None, :]
+    return np.sqrt(((q - p[None, :]) ** 2).sum(axis=1).min())
+
+
+def _triangle_dist_sampled(p, a, b, c, n=400):
+    i, j = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="ij")
+    m = i + j <= n
+    u, v = i[m] / n, j[m] / n
+    q = a[None, :] + u[:, None] * (b - a)[None, :] + v[:, None] * (c - a)[None, :]
+    return np.sqrt(((q - p[None, :]) ** 2).sum(axis=1).min())
+
+
+def test_given_feature_distance_against_dense_sampling():
+    """The distance to a given feature that is mostly NOT the closest one (a random nearby
+    triangle and a random label: the closed triangle, one of its closed edges or a corner)
+    against the minimum over a dense sample of that feature: never below it by more than
+    rounding, never above it by more than the sampling step."""
+    mesh = meshgen.icosphere(2, radius=0.3, displacement=0.02, seed=4)
+    X, tri = mesh.vertices, mesh.triangles
+    om = oracle.OracleMesh.from_indexed(X, tri)
+    rng = np.random.default_rng(31)
+    pts, _ = _band_loss_points(mesh, 0.08, 120, 32)
+    t = rng.integers(0, tri.shape[0], size=pts.shape[0])
+    r = rng.integers(0, 7, size=pts.shape[0])
+    _, dF = om.adjoint_features(pts, np.zeros(pts.shape[0]), t, r)
+    for p, tt, rr, d in zip(pts, t, r, dF):
+        A, B, C = X[tri[tt]]
+        if rr == 0:
+            ref, step = _triangle_dist_sampled(p, A, B, C), 0.75 * max(np.linalg.norm(B - A), np.linalg.norm(C - A),
+                                                                       np.linalg.norm(C - B)) / 400
+        elif rr <= 3:
+            k = rr - 1
+            P0, P1 = X[tri[tt, k]], X[tri[tt, (k + 1) % 3]]
+            ref, step = _segment_dist_sampled(p, P0, P1), np.linalg.norm(P1 - P0) / 200000
+        else:
+            ref, step = np.linalg.norm(p - X[tri[tt, rr - 4]]), 0.0
+        assert abs(d) <= ref + 1e-12 and abs(d) >= ref - step - 1e-12, (rr, abs(d), ref)
+
+
+def test_adjoint_on_given_features_matches_finite_differences():
+    """d(sum_p g_p d_F(p)) / dX for features fixed by the caller (random triangles near the
+    point and random labels, so mostly not the closest feature), against central differences
+    of the same given-feature distances, on a union of rotated boxes (concave creases)."""
+    mesh = meshgen.box_union(3, 300, seed=2)
+    X, tri = mesh.vertices, mesh.triangles
+    om = oracle.OracleMesh.from_indexed(X, tri)
+    rng = np.random.default_rng(41)
+    pts, g = _band_loss_points(mesh, 0.05, 1500, 42)
+    # a feature of a triangle near the point: its own winner's triangle or a neighbour of it
+    _, t0, _ = om.sdf_points(pts)
+    nb = [[] for _ in range(tri.shape[0])]
+    for a in range(tri.shape[0]):
+        for v in tri[a]:
+            nb[a].append(v)
+    vert_tris = [[] for _ in range(X.shape[0])]
+    for a in range(tri.shape[0]):
+        for v in tri[a]:
+            vert_tris[v].append(a)
+    t = np.array([rng.choice(vert_tris[tri[a, rng.integers(0, 3)]]) for a in t0], dtype=np.int32)
+    r = rng.integers(0, 7, size=pts.shape[0]).astype(np.int32)
+    grad, d = om.adjoint_features(pts, g, t, r)
+    keep = np.abs(d) > 1e-3  # the sign (and the derivative) is smooth away from the feature
+    assert keep.mean() > 0.9
+    g = np.where(keep, g, 0.0)
+    grad, _ = om.adjoint_features(pts, g, t, r)
+    used = np.unique(tri[t[keep]].ravel())
+    verts = rng.choice(used, size=min(30, used.size), replace=False)
+    eps = 1e-6
+    fd, an = [], []
+    for v in verts:
+        for c in range(3):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[v, c] += eps
+            Xm[v, c] -= eps
+            _, dp = oracle.OracleMesh.from_indexed(Xp, tri).adjoint_features(pts, g, t, r)
+            _, dm = oracle.OracleMesh.from_indexed(Xm, tri).adjoint_features(pts, g, t, r)
+            fd.append(float(g @ (dp - dm)) / (2 * eps))
+            an.append(grad[v, c])
+    fd, an = np.array(fd), np.array(an)
+    assert np.linalg.norm(fd) > 0
+    assert np.linalg.norm(fd - an) <= 1e-4 * np.linalg.norm(fd)
