@@ -219,6 +219,27 @@ int sdf_features_vertex_map(sdf_features f, int32_t *soup_to_vertex, void *strea
 /* Soup triangle of every library face id: device int32[n_tri]. */
 int sdf_features_face_map(sdf_features f, int32_t *face_to_soup, void *stream);
 
+/* Edge table: device int32[E][4] = (va, vb, f1, f2) per library edge id e: the welded end
+ * points va < vb, the face f1 holding the directed edge va -> vb and the face f2 holding vb -> va
+ * (library face ids).  Relates edge winners (feature id T + e) to the mesh. */
+int sdf_features_edges(sdf_features f, int32_t *edges, void *stream);
+
+/*
+ * sdf_features_error_bound -- the FP32 error windows the narrow band uses for this mesh at its
+ * current positions on the given grid and band (host outputs, synchronises `stream`):
+ *   bounds[0] delta: bound on | |d_fp32| - |d| | for every FP32 distance the tile kernel keeps,
+ *             delta = (2^-20 M + tau_a + tau_b w) / (1 - 2 tau_b), M the largest coordinate
+ *             magnitude of the grid and the mesh, tau_a, tau_b the mesh's normal-error terms;
+ *   bounds[1] the inclusion tolerance of the region tests (world units);
+ *   bounds[2] the sign window: a candidate whose sign predicate is within it of zero is
+ *             re-decided in FP64;
+ *   bounds[3] the largest extra sign-window term of the edge and vertex pseudonormals.
+ * A point whose FP32 distance lies within delta of w, or whose sign is uncertain, is re-decided
+ * in FP64, so the band mask and the sign are exact elsewhere and |d| errs by at most delta.
+ * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_CUDA.
+ */
+int sdf_features_error_bound(sdf_features f, const sdf_grid *grid, float band_w, double *bounds, void *stream);
+
 /* Welded vertex positions: device float[V][3]. */
 int sdf_features_vertices(sdf_features f, float *out, void *stream);
 
@@ -244,6 +265,15 @@ int sdf_features_timing(sdf_features f, double *ms, int64_t *calls, int reset);
 int64_t sdf_kernel_launches(void);
 
 /*
+ * Memory the library has taken (diagnostics; host outputs [4]): out[0] the number of device
+ * allocations it has made from its stream-ordered pool (process-wide), out[1] and out[2] the
+ * bytes in use and reserved in the current device's pool, out[3] the number of pinned host
+ * allocations it has made (staging blocks for small reads and table uploads).
+ * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_CUDA.
+ */
+int sdf_memory_stats(int64_t *out);
+
+/*
  * sdf_narrow_band_static -- the same narrow band as sdf_narrow_band for one (mesh, grid) problem,
  * but the call allocates no device memory.  The paper has no counterpart: this entry point is
  * for callers that cannot allocate during the call, such as a process whose device memory is
@@ -259,14 +289,16 @@ int64_t sdf_kernel_launches(void);
  * whose work overlaps on the GPU (for example on two streams) race on it and must not be made.
  * The first call on a device performs the set-up (it looks up the array's device address with
  * that device current); make that first call before any stream capture.  The call
- * synchronises `stream` once to read its status word.
+ * synchronises `stream` once to read its status words, by a copy into host stack memory: it
+ * allocates neither device memory nor pinned host memory (sdf_memory_stats counts both).
  *
  *   f           handle from sdf_build_features.
  *   grid        host pointer to the grid.
  *   band_w      band half-width w > 0.
  *   out_dist    device float[nz][ny][nx].
  *   out_winner  device int32[nz][ny][nx] or NULL.
- * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_TOO_LARGE, SDF_ERR_CUDA.
+ * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_TOO_LARGE, SDF_ERR_CUDA, SDF_ERR_DEGENERATE (positions set by
+ * sdf_features_update_positions).
  */
 int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, float band_w, float *out_dist,
                            int32_t *out_winner, void *stream);

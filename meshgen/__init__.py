@@ -272,10 +272,13 @@ def knot_min_strand_separation(n: int = 4096, p: int = 3, q: int = 7, R: float =
 
 # ----------------------------------------------------------------------------- small exact shapes
 
-def box(center=(0.5, 0.5, 0.5), half=(0.2, 0.15, 0.1), subdiv: int = 1) -> Mesh:
-    """Axis-aligned box; each face split into subdiv x subdiv quads (two triangles each)."""
+def box(center=(0.5, 0.5, 0.5), half=(0.2, 0.15, 0.1), subdiv=1, axes=None) -> Mesh:
+    """Box center + sum_k s_k half_k axes_k (s_k in [-1, 1]; axes: orthonormal rows, default the
+    coordinate axes); each face split into quads of two triangles, subdiv segments along every
+    local axis (an int, or one count per axis)."""
     c = np.asarray(center, dtype=np.float64)
     hx = np.asarray(half, dtype=np.float64)
+    segs = (subdiv,) * 3 if np.isscalar(subdiv) else tuple(int(x) for x in subdiv)
     verts: dict = {}
     pos: list = []
 
@@ -287,23 +290,24 @@ def box(center=(0.5, 0.5, 0.5), half=(0.2, 0.15, 0.1), subdiv: int = 1) -> Mesh:
         return verts[key]
 
     tris = []
-    s = subdiv
     for axis in range(3):
         for sgn in (-1, 1):
             u_ax, v_ax = [k for k in range(3) if k != axis]
-            for i in range(s):
-                for j in range(s):
+            su, sv = segs[u_ax], segs[v_ax]
+            for i in range(su):
+                for j in range(sv):
                     quad = []
                     for di, dj in ((0, 0), (1, 0), (1, 1), (0, 1)):
                         p = [0.0, 0.0, 0.0]
                         p[axis] = sgn
-                        p[u_ax] = -1 + 2 * (i + di) / s
-                        p[v_ax] = -1 + 2 * (j + dj) / s
+                        p[u_ax] = -1 + 2 * (i + di) / su
+                        p[v_ax] = -1 + 2 * (j + dj) / sv
                         quad.append(vid(tuple(p)))
                     tris.append((quad[0], quad[1], quad[2]))
                     tris.append((quad[0], quad[2], quad[3]))
     unit = np.array(pos)
-    v = c + unit * hx
+    ax = np.eye(3) if axes is None else np.asarray(axes, dtype=np.float64)
+    v = c + (unit * hx) @ ax
     tri = np.array(tris, dtype=np.int64)
     # orient each triangle so its normal points away from the box centre
     a, b, cc = (v[tri[:, k]] for k in range(3))
@@ -311,6 +315,52 @@ def box(center=(0.5, 0.5, 0.5), half=(0.2, 0.15, 0.1), subdiv: int = 1) -> Mesh:
     out = np.einsum("ij,ij->i", nrm, (a + b + cc) / 3 - c)
     tri[out < 0] = tri[out < 0][:, [0, 2, 1]]
     return Mesh(v, tri.astype(np.int32))
+
+
+def lattice_plate(n_grid: int, half_thickness: float, offset: float, half_extent: float = 0.25,
+                  subdiv: int = 24) -> Mesh:
+    """A thin plate (a box) whose mid-plane is a lattice plane of the n_grid^3 cell-centre grid on
+    [0, 1]^3, moved along its normal by `offset`.  The normal is (1, 2, 2)/3, so the grid points
+    (i + 1/2, j + 1/2, k + 1/2)/n with i + 2j + 2k = K all lie at distance -offset from the mid-plane
+    (K is chosen so that the plane passes near the domain centre), and with half_thickness = w they
+    are within |offset| of the band edge, equally close to both sheets up to 2 |offset|: the
+    two-sheet near tie of the FP32 winner.  Returns the mesh; the lattice index K is mesh.K."""
+    nrm = np.array([1.0, 2.0, 2.0]) / 3.0
+    u = np.array([2.0, 1.0, -2.0]) / 3.0
+    v = np.cross(nrm, u)
+    h = 1.0 / n_grid
+    K = int(round((2.5 / h) - 2.5))  # n . p = h (K + 2.5) / 3 near n . (1/2, 1/2, 1/2) = 5/6
+    target = h * (K + 2.5) / 3.0 + offset
+    c0 = CENTER
+    c = c0 + (target - float(nrm @ c0)) * nrm
+    m = box(center=c, half=(half_extent, half_extent, half_thickness), subdiv=(subdiv, subdiv, 1),
+            axes=np.stack([u, v, nrm]))
+    m.K = K
+    return m
+
+
+def knife_prism(apex_deg: float = 10.0, depth: float = 0.3, length: float = 0.4, n_seg: int = 12,
+                center=(0.5, 0.5, 0.5), seed: int = 0) -> Mesh:
+    """A triangular prism whose cross-section has an apex angle of apex_deg (a knife edge: its two
+    faces turn by 180 - apex_deg degrees), extruded over `length` in n_seg segments and rotated by
+    a seeded random rotation."""
+    half = depth * math.tan(math.radians(apex_deg) / 2)
+    sec = np.array([[-depth / 2, 0.0], [depth / 2, half], [depth / 2, -half]])
+    zs = np.linspace(-length / 2, length / 2, n_seg + 1)
+    v = np.array([[x, y, z] for z in zs for x, y in sec])
+    tri = []
+    for s_ in range(n_seg):
+        for a in range(3):
+            b = (a + 1) % 3
+            p0, p1, q0, q1 = 3 * s_ + a, 3 * s_ + b, 3 * (s_ + 1) + a, 3 * (s_ + 1) + b
+            tri.append((p0, p1, q1))
+            tri.append((p0, q1, q0))
+    last = 3 * n_seg
+    tri.append((0, 2, 1))
+    tri.append((last, last + 1, last + 2))
+    R = random_rotation(np.random.Generator(np.random.PCG64(seed)))
+    v = v @ R.T + np.asarray(center)
+    return Mesh(v, _orient_outward(v, np.array(tri, dtype=np.int64)))
 
 
 def regular_tetrahedron(center=(0.5, 0.5, 0.5), size: float = 0.25) -> Mesh:

@@ -20,6 +20,7 @@ from . import _buildlib
 
 __all__ = ["Grid", "Features", "sdf_build_features", "sdf_narrow_band", "sdf_narrow_band_backward",
            "SDFFunction", "Batch", "sdf_batch_create", "band_l2_loss", "load_library", "kernel_launches", "SDFError",
+           "memory_stats",
            "BandList", "sdf_narrow_band_list", "sdf_narrow_band_lists", "band_list_backward", "band_list_l2",
            "FLAG_DISABLE_SADDLE", "FLAG_NO_SYNC", "FLAG_TIMING", "FLAG_AUTOTUNE", "FLAG_FILL_SIGN",
            "FLAG_CELL_LOOP", "FLAG_VERTEX_CONE", "FLAG_VERTEX_HEMISPHERE", "FLAG_GRAD_F64"]
@@ -76,6 +77,10 @@ def load_library(path: str | None = None):
     L.sdf_features_face_map.argtypes = [P, P, P]
     L.sdf_features_face_map.restype = ctypes.c_int
     L.sdf_features_vertices.argtypes = [P, P, P]
+    L.sdf_features_edges.argtypes = [P, P, P]
+    L.sdf_features_edges.restype = ctypes.c_int
+    L.sdf_features_error_bound.argtypes = [P, ctypes.POINTER(_CGrid), ctypes.c_float, ctypes.POINTER(ctypes.c_double), P]
+    L.sdf_features_error_bound.restype = ctypes.c_int
     L.sdf_features_status.argtypes = [P, ctypes.POINTER(I64), P]
     L.sdf_features_destroy.argtypes = [P]
     L.sdf_features_destroy.restype = None
@@ -83,6 +88,8 @@ def load_library(path: str | None = None):
     L.sdf_features_timing.restype = ctypes.c_int
     L.sdf_kernel_launches.argtypes = []
     L.sdf_kernel_launches.restype = I64
+    L.sdf_memory_stats.argtypes = [ctypes.POINTER(I64)]
+    L.sdf_memory_stats.restype = ctypes.c_int
     L.sdf_status_string.argtypes = [ctypes.c_int]
     L.sdf_status_string.restype = ctypes.c_char_p
     L.sdf_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(_CGrid), ctypes.POINTER(ctypes.c_float), I32,
@@ -113,6 +120,15 @@ def load_library(path: str | None = None):
 def kernel_launches() -> int:
     """Process-wide number of kernels the library has launched."""
     return int(load_library().sdf_kernel_launches())
+
+
+def memory_stats() -> dict:
+    """Memory the library has taken: device pool allocations made (process-wide), bytes in use and
+    reserved in the current device's pool, pinned host allocations made."""
+    out = (ctypes.c_int64 * 4)()
+    _check(load_library().sdf_memory_stats(out), "sdf_memory_stats")
+    return {"pool_allocs": int(out[0]), "pool_used": int(out[1]), "pool_reserved": int(out[2]),
+            "host_allocs": int(out[3])}
 
 
 def _stream(stream=None) -> int:
@@ -196,6 +212,23 @@ class Features:
         out = torch.empty(self.n_tri, dtype=torch.int32, device="cuda")
         _check(load_library().sdf_features_face_map(self.handle, out.data_ptr(), _stream()), "face_map")
         return out
+
+    def edges(self) -> torch.Tensor:
+        """Edge table int32 [E, 4]: (va, vb, f1, f2) per library edge id (end points va < vb, f1 the
+        face holding va -> vb, f2 the face holding vb -> va)."""
+        out = torch.empty(self.n_edge, 4, dtype=torch.int32, device="cuda")
+        _check(load_library().sdf_features_edges(self.handle, out.data_ptr(), _stream()), "edges")
+        return out
+
+    def error_bound(self, grid: "Grid", w: float) -> dict:
+        """The FP32 error windows of the narrow band on this grid and band (synchronises):
+        delta (bound on the FP32 distance error), eps (inclusion tolerance), ds (sign window) and
+        the largest pseudonormal term of the sign window."""
+        b = (ctypes.c_double * 4)()
+        cg = grid.c()
+        _check(load_library().sdf_features_error_bound(self.handle, ctypes.byref(cg), float(w), b, _stream()),
+               "sdf_features_error_bound")
+        return {"delta": b[0], "eps": b[1], "ds": b[2], "ds_normal": b[3]}
 
     def vertices(self) -> torch.Tensor:
         out = torch.empty(self.n_vert, 3, dtype=torch.float32, device="cuda")

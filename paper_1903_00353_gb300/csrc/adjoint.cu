@@ -33,7 +33,60 @@ struct AdjArgs {
     const int32_t *face_vid;
     const int4 *edge_vf;
     const float *vpos;
+    const int32_t *vert_start, *vert_corner;
 };
+
+// One coordinate of p - x for the grid point p = o + (i + 1/2) h and a vertex coordinate x, with
+// relative rather than absolute rounding: o - x is split exactly into hi + lo (Knuth's two-sum),
+// hi + (i + 1/2) h is formed by one fused multiply-add, then lo is added.  A plain FP32 p - x
+// errs by about u |p|, which near the surface (|p - x| small) ruins the direction (p - q)/|p - q|.
+__device__ __forceinline__ float rel_coord(float o, float h, int i, float x) {
+    const float a = o, b = -x;
+    const float hi = a + b;
+    const float bv = hi - a;
+    const float lo = (a - (hi - bv)) + (b - bv);
+    return fmaf((float)i + 0.5f, h, hi) + lo;
+}
+__device__ __forceinline__ float3 rel_point(const AdjArgs &a, int i, int j, int k, float3 x) {
+    return make_float3(rel_coord(a.ox, a.h, i, x.x), rel_coord(a.oy, a.h, j, x.y), rel_coord(a.oz, a.h, k, x.z));
+}
+
+__device__ double3 face_normal64(const AdjArgs &a, int f) {
+    const double3 A = d3(load_vpos(a.vpos, a.face_vid[3 * f])), B = d3(load_vpos(a.vpos, a.face_vid[3 * f + 1])),
+                  C = d3(load_vpos(a.vpos, a.face_vid[3 * f + 2]));
+    const double3 cr = dcross3(B - A, C - A);
+    return (1.0 / sqrt(ddot3(cr, cr))) * cr;
+}
+
+// FP64 sign of (p - q).N for an edge (N = n1 + n2) or a vertex (N = N_alpha, Eq. 8), taken when the
+// FP32 predicate is within 1e-3 |N| |p - q| of zero (its FP32 error is far smaller, so elsewhere the
+// FP32 sign is the FP64 one); p is the grid point (i, j, k) in FP64.
+__device__ float sign64_edge(const AdjArgs &a, int e, int i, int j, int k) {
+    const int4 q = a.edge_vf[e];
+    const double3 p = make_double3((double)a.ox + (i + 0.5) * (double)a.h, (double)a.oy + (j + 0.5) * (double)a.h,
+                                   (double)a.oz + (k + 0.5) * (double)a.h);
+    const double3 A = d3(load_vpos(a.vpos, q.x)), B = d3(load_vpos(a.vpos, q.y));
+    const double3 ab = B - A, ap = p - A;
+    double t = ddot3(ap, ab) / ddot3(ab, ab);
+    t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+    const double3 d = ap - t * ab;
+    return ddot3(d, face_normal64(a, q.z) + face_normal64(a, q.w)) < 0.0 ? -1.f : 1.f;
+}
+__device__ float sign64_vertex(const AdjArgs &a, int v, int i, int j, int k) {
+    const double3 p = make_double3((double)a.ox + (i + 0.5) * (double)a.h, (double)a.oy + (j + 0.5) * (double)a.h,
+                                   (double)a.oz + (k + 0.5) * (double)a.h);
+    const double3 P = d3(load_vpos(a.vpos, v));
+    double3 N = make_double3(0, 0, 0);
+    for (int c = a.vert_start[v]; c < a.vert_start[v + 1]; c++) {
+        const int cc = a.vert_corner[c];
+        const int f = cc / 3, kk = cc - 3 * f;
+        const double3 e1 = d3(load_vpos(a.vpos, a.face_vid[3 * f + (kk + 1) % 3])) - P;
+        const double3 e2 = d3(load_vpos(a.vpos, a.face_vid[3 * f + (kk + 2) % 3])) - P;
+        const double3 cr = dcross3(e1, e2);
+        N = N + atan2(sqrt(ddot3(cr, cr)), ddot3(e1, e2)) * face_normal64(a, f);
+    }
+    return ddot3(p - P, N) < 0.0 ? -1.f : 1.f;
+}
 
 // add (gx, gy, gz) to vertex v, merged over runs of consecutive lanes that target the same vertex
 // (band points arrive in grid order, so neighbours with a common winner sit in adjacent lanes): a
@@ -88,15 +141,13 @@ __device__ __forceinline__ int point_adjoint(const AdjArgs &a, int64_t idx, int 
         j = (int)((idx - (int64_t)k * plane) / a.nx);
         i = (int)(idx - (int64_t)k * plane - (int64_t)j * a.nx);
     }
-    const float3 p = make_float3(fmaf((float)i + 0.5f, a.h, a.ox), fmaf((float)j + 0.5f, a.h, a.oy),
-                                 fmaf((float)k + 0.5f, a.h, a.oz));
     if (wid < a.T) {
         // barycentric weights of the projection of p onto the face plane; s (p - q)/|p - q| = n
         const int f = wid;
         const float3 A = load_vpos(a.vpos, a.face_vid[3 * f]), B = load_vpos(a.vpos, a.face_vid[3 * f + 1]),
                      C = load_vpos(a.vpos, a.face_vid[3 * f + 2]);
         const float3 n = f3(a.face_rec[4 * f]);
-        const float3 ab = B - A, ac = C - A, ap = p - A;
+        const float3 ab = B - A, ac = C - A, ap = rel_point(a, i, j, k, A);
         const float d00 = dot3(ab, ab), d01 = dot3(ab, ac), d11 = dot3(ac, ac);
         const float d20 = dot3(ap, ab), d21 = dot3(ap, ac);
         const float den = d00 * d11 - d01 * d01;
@@ -118,12 +169,13 @@ __device__ __forceinline__ int point_adjoint(const AdjArgs &a, int64_t idx, int 
         const int e = wid - a.T;
         const int4 q = a.edge_vf[e];
         const float4 r0 = a.edge_rec[5 * e], r1 = a.edge_rec[5 * e + 1], np = a.edge_rec[5 * e + 4];
-        const float3 u = p - f3(r0);
+        const float3 u = rel_point(a, i, j, k, f3(r0));
         const float t = fminf(fmaxf(dot3(u, f3(r1)), 0.f), r0.w);
         const float3 d = u - t * f3(r1);
         const float len = sqrtf(dot3(d, d));
         if (!(len > 0.f)) return 0;
-        const float s = dot3(d, f3(np)) < 0.f ? -1.f : 1.f;
+        const float P = dot3(d, f3(np));
+        const float s = fabsf(P) < 1e-3f * np.w * len ? sign64_edge(a, e, i, j, k) : (P < 0.f ? -1.f : 1.f);
         const float tt = t / r0.w;
         const float lam[2] = {1.f - tt, tt};
         const float k0 = -g * s / len;
@@ -137,10 +189,11 @@ __device__ __forceinline__ int point_adjoint(const AdjArgs &a, int64_t idx, int 
     } else {
         const int v = wid - a.T - a.E;
         const float4 r0 = a.vert_rec[3 * v], r1 = a.vert_rec[3 * v + 1];
-        const float3 d = p - f3(r0);
+        const float3 d = rel_point(a, i, j, k, f3(r0));
         const float len = sqrtf(dot3(d, d));
         if (!(len > 0.f)) return 0;
-        const float s = dot3(d, f3(r1)) < 0.f ? -1.f : 1.f;
+        const float P = dot3(d, f3(r1));
+        const float s = fabsf(P) < 1e-3f * len ? sign64_vertex(a, v, i, j, k) : (P < 0.f ? -1.f : 1.f);
         const float k0 = -g * s / len;
         vtx[0] = v;
         c[0][0] = k0 * d.x;
@@ -311,6 +364,7 @@ AdjArgs make_adj_args(const sdf_features_s *f, const sdf_grid &gr) {
     a.gv64 = nullptr;
     a.face_rec = f->face_rec; a.edge_rec = f->edge_rec; a.vert_rec = f->vert_rec;
     a.face_vid = f->face_vid; a.edge_vf = f->edge_vf; a.vpos = f->vpos;
+    a.vert_start = f->vert_start; a.vert_corner = f->vert_corner;
     return a;
 }
 

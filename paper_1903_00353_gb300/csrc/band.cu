@@ -60,11 +60,45 @@ struct GridP {
     FastDiv div_ntx, div_nty, div_nx, div_ny;  // tile and grid index decomposition
     float ox, oy, oz, h, inv_h;
     float w;     // band half-width: in band iff |d| < w
-    float W;     // candidate cutoff w + dw
-    float dlo;   // w - dw: points with |d| in [dlo, W) are re-decided in FP64
-    float ds;    // points with |d| < ds are re-decided in FP64 (sign)
+    float Mg;    // coordinate magnitude of the grid (and w)
+    // FP32 error windows (set_windows: from the coordinate magnitude and the mesh's shape terms)
+    float derr;  // bound on the FP32 distance error (delta)
+    float W;     // candidate cutoff w + delta
+    float dlo;   // w - delta: points with |d| in [dlo, W) are re-decided in FP64
+    float ds;    // sign window: a candidate whose sign predicate lies within ds (per unit normal) of 0
+    float ds2;   //   is marked uncertain; ds2 (edges) and dsv (vertices) add the pseudonormal's
+    float dsv;   //   own direction error
     float eps;   // inclusion tolerance of the half-space tests (world units)
 };
+
+// The FP32 error windows of a problem (see the derivation in the design notes of this library):
+//   delta = (2^-20 M + tau_a + tau_b w) / (1 - 2 tau_b),  i.e.  delta = 2^-20 M + tau_a + tau_b (w + 2 delta),
+// with M the largest coordinate magnitude of the grid and the mesh.  2^-20 M = 16 u M bounds the
+// rounding of every FP32 plane test, span bound and distance (at most 12.2 u M: the grid point
+// carries u M per coordinate, a three-term dot product with p and the plane offset -n.a each
+// 3 sqrt(3) u M, and the subtraction u W); tau_a + tau_b W bounds the error of the FP32 normals
+// and planes themselves at points within W + eps of the feature (k_face_records).  The inclusion
+// tolerance is eps = delta; candidates with FP32 |d| >= W = w + delta are dropped (their true
+// distance is >= w), and points whose FP32 winner lies in [w - delta, W) are re-decided in FP64.
+// A candidate's sign is certain when its sign predicate (p - q).N exceeds ds |N| (+ ds2 for
+// edges, + dsv for vertices), ds = 2 delta: moving p by at most eps into the feature's exact
+// region changes (p - q).N^ by at most eps, the FP32 evaluation errs by at most delta (plus the
+// pseudonormal's own direction error), and there the sign of the closest feature's predicate
+// is the sign of the distance (Baerentzen-Aanaes, Section 4.3); otherwise the candidate is
+// marked uncertain and, if it wins, re-decided in FP64.
+__host__ __device__ inline void set_windows(GridP &g, float m_mesh, float tau_a, float tau_b, float tau_v) {
+    const float M = fmaxf(g.Mg, m_mesh);
+    const float tb = fminf(tau_b, 0.25f);
+    const float delta = (M * 0x1p-20f + tau_a + tau_b * g.w) / (1.f - 2.f * tb) * 1.0001f;
+    const float reach = g.w + 2.f * delta;  // largest distance of an evaluated point from its feature
+    g.derr = delta;
+    g.eps = delta;
+    g.W = g.w + delta;
+    g.dlo = g.w - delta;
+    g.ds = 2.f * delta;
+    g.ds2 = 1.1f * tau_b * reach;
+    g.dsv = fminf(tau_v, 1.f) * reach;
+}
 
 struct Feat {
     int T, E, V;
@@ -73,9 +107,18 @@ struct Feat {
     const int32_t *face_vid, *face_edge, *vert_start, *vert_corner;
     const int4 *edge_vf;
     const float *vpos;
+    const unsigned *prec;  // the handle's precision terms (DevCounters::prec)
     int skip_saddle;
     int vmode;  // vertex regions of the cell-loop schedule: VM_EXACT, VM_CONE or VM_HEMISPHERE
 };
+
+// Packed merge key of a candidate (Algorithm 1's minimum-magnitude rule as one 64-bit minimum):
+// |d| bits << 32 | feature id << 2 | sign uncertain << 1 | negative.  Feature ids are < 2^30.
+__device__ __forceinline__ unsigned long long make_key(float d, int fid, bool unc, bool neg) {
+    return ((unsigned long long)__float_as_uint(d) << 32) | ((unsigned long long)(unsigned)fid << 2) |
+           ((unsigned long long)unc << 1) | (unsigned long long)neg;
+}
+__device__ __forceinline__ int key_fid(unsigned long long key) { return (int)((key >> 2) & 0x3fffffffu); }
 
 // Vertex extrusions (cell-loop schedule only).  VM_EXACT: the exact vertex region of the tile path.
 // VM_CONE: the paper's cone (Sections 3.3, 8.3): axis N_alpha, half-angle to the most diverging
@@ -320,10 +363,12 @@ __device__ float tri_boundary_dist(float3 p, float3 a, float3 b, float3 c) {
     return sqrtf(best);
 }
 
-// distance from grid point (i, j, k) to feature `id` and the sign from the feature's
-// pseudonormal (face normal / n1 + n2 / N_alpha, Section 4.3)
+// distance from grid point (i, j, k) to feature `id`, the sign from the feature's pseudonormal
+// (face normal / n1 + n2 / N_alpha, Section 4.3), and whether that sign is within the FP32 sign
+// window (unc: the predicate (p - q).N is smaller than the window allows, see set_windows)
 template <int TYPE>
-__device__ __forceinline__ float eval_point(const Feat &F, const GridP &g, int id, int i, int j, int k, bool &neg) {
+__device__ __forceinline__ float eval_point(const Feat &F, const GridP &g, int id, int i, int j, int k, bool &neg,
+                                            bool &unc) {
     const float3 p = make_float3(fmaf((float)i + 0.5f, g.h, g.ox), fmaf((float)j + 0.5f, g.h, g.oy),
                                  fmaf((float)k + 0.5f, g.h, g.oz));
     if (TYPE == FACE) {
@@ -331,6 +376,7 @@ __device__ __forceinline__ float eval_point(const Feat &F, const GridP &g, int i
         float4 n = __ldg(r), s1 = __ldg(r + 1), s2 = __ldg(r + 2), s3 = __ldg(r + 3);
         float sd = dot3(f3(n), p) + n.w;
         neg = sd < 0.f;
+        unc = fabsf(sd) < g.ds;
         float v1 = dot3(f3(s1), p) + s1.w, v2 = dot3(f3(s2), p) + s2.w, v3 = dot3(f3(s3), p) + s3.w;
         if (v1 >= 0.f && v2 >= 0.f && v3 >= 0.f) return fabsf(sd);
         return tri_boundary_dist(p, load_vpos(F.vpos, F.face_vid[3 * id]), load_vpos(F.vpos, F.face_vid[3 * id + 1]),
@@ -341,12 +387,16 @@ __device__ __forceinline__ float eval_point(const Feat &F, const GridP &g, int i
         float3 u = p - f3(a);
         float s = fminf(fmaxf(dot3(u, f3(t)), 0.f), a.w);
         float3 d = u - s * f3(t);
-        neg = dot3(d, f3(np)) < 0.f;
+        const float P = dot3(d, f3(np));
+        neg = P < 0.f;
+        unc = fabsf(P) < fmaf(g.ds, np.w, g.ds2);
         return sqrtf(dot3(d, d));
     } else {
         float4 v = __ldg(F.vert_rec + 3 * id), nv = __ldg(F.vert_rec + 3 * id + 1);
         float3 u = p - f3(v);
-        neg = dot3(u, f3(nv)) < 0.f;
+        const float P = dot3(u, f3(nv));
+        neg = P < 0.f;
+        unc = fabsf(P) < g.ds + g.dsv;
         return sqrtf(dot3(u, u));
     }
 }
@@ -357,10 +407,10 @@ __device__ __forceinline__ int feat_local(const Feat &F, int fid, int type) {
     return type == FACE ? fid : (type == EDGE ? fid - F.T : fid - F.T - F.E);
 }
 __device__ __forceinline__ float eval_any(const Feat &F, const GridP &g, int type, int id, int i, int j, int k,
-                                          bool &neg) {
-    if (type == FACE) return eval_point<FACE>(F, g, id, i, j, k, neg);
-    if (type == EDGE) return eval_point<EDGE>(F, g, id, i, j, k, neg);
-    return eval_point<VERT>(F, g, id, i, j, k, neg);
+                                          bool &neg, bool &unc) {
+    if (type == FACE) return eval_point<FACE>(F, g, id, i, j, k, neg, unc);
+    if (type == EDGE) return eval_point<EDGE>(F, g, id, i, j, k, neg, unc);
+    return eval_point<VERT>(F, g, id, i, j, k, neg, unc);
 }
 
 // ----------------------------------------------------------------------------- per-tile row coefficients
@@ -438,12 +488,10 @@ __device__ __forceinline__ void eval_rows(const Feat &F, const GridP &g, TileSme
             const int lz = ax == 2 ? la : lc;
             const int fid = S.fid[slot];
             const int type = feat_type(F, fid), id = feat_local(F, fid, type);
-            bool neg;
-            const float d = eval_any(F, g, type, id, x0 + lx, y0 + ly, z0 + lz, neg);
+            bool neg, unc;
+            const float d = eval_any(F, g, type, id, x0 + lx, y0 + ly, z0 + lz, neg, unc);
             if (d < g.W) {
-                const unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) |
-                                               ((unsigned long long)(unsigned)fid << 1) | (unsigned long long)neg;
-                atomicMin(S.key + (lz * TY + ly) * TILE_X + lx, key);
+                atomicMin(S.key + (lz * TY + ly) * TILE_X + lx, make_key(d, fid, unc, neg));
                 cand++;
             }
         }
@@ -670,14 +718,14 @@ __device__ __forceinline__ float decode_key(unsigned long long key, const GridP 
     entry = false;
     if (key == ~0ull) return INFINITY;
     const float d = __uint_as_float((unsigned)(key >> 32));
-    const int fid = (int)((key >> 1) & 0x7fffffffu);
+    const int fid = key_fid(key);
     float val = INFINITY;
     if (d < g.w) {
         val = (key & 1ull) ? -d : d;
         wid = fid;
         band++;
     }
-    const bool window = d < g.ds || d >= g.dlo;
+    const bool window = (key & 2ull) || d >= g.dlo;  // sign uncertain, or near the band edge
     entry = wid >= 0 && !window;
     if (window) {  // inside the FP32 error window: re-decide in FP64
         unsigned long long slot = atomicAdd(&o.ctr->n_patch, 1ull);
@@ -736,7 +784,7 @@ __device__ __forceinline__ void list_write(const Prob &pr, const TileSmem<TY, TZ
         }
         const int64_t idx = (int64_t)gk * plane + (int64_t)gj * g.nx + gi;
         if ((long long)pos < pr.list_cap)
-            pr.list[pos] = make_uint2((uint32_t)idx, (uint32_t)((S.key[e] >> 1) & 0x7fffffffu));
+            pr.list[pos] = make_uint2((uint32_t)idx, (uint32_t)key_fid(S.key[e]));
         else
             overflow = true;
         pos++;
@@ -956,9 +1004,81 @@ __device__ __forceinline__ double wsum(double v) {
     return v;
 }
 
-// one warp per queued point: FP64 minimum over the triangles around the winner's vertices, sign
-// from the pseudonormal of the closest feature (face normal, n1 + n2, or N_alpha, Eq. 8)
-__global__ void k_patch(const Prob *P, Outputs o) {
+// An FP64 candidate of the re-decision: squared distance, the feature holding the closest point q
+// in its relative interior (global feature id: face, edge or vertex), and p - q.
+struct Cand64 {
+    double d2;
+    int id;
+    double3 pq;
+};
+
+__device__ __forceinline__ bool cand_less(double d2, int id, double bd2, int bid) {
+    return d2 < bd2 || (d2 == bd2 && id < bid);
+}
+
+// closest point of the closed triangle t (Voronoi regions of closest_on_tri), as a candidate
+__device__ __forceinline__ Cand64 face_cand64(const Feat &F, double3 p, int t) {
+    const double3 A = d3(load_vpos(F.vpos, F.face_vid[3 * t])), B = d3(load_vpos(F.vpos, F.face_vid[3 * t + 1])),
+                  C = d3(load_vpos(F.vpos, F.face_vid[3 * t + 2]));
+    int reg;
+    double3 lam;
+    Cand64 c;
+    c.d2 = closest_on_tri(p, A, B, C, reg, lam);
+    if (reg == 0) {  // (p - A).n equals (p - q).n for q in the face
+        c.id = t;
+        c.pq = p - A;
+    } else if (reg <= 3) {
+        c.id = F.T + F.face_edge[3 * t + reg - 1];
+        c.pq = (p - A) - lam.y * (B - A) - lam.z * (C - A);
+    } else {
+        c.id = F.T + F.E + F.face_vid[3 * t + reg - 4];
+        c.pq = p - (reg == 4 ? A : (reg == 5 ? B : C));
+    }
+    return c;
+}
+
+// closest point of the closed edge e (segment va - vb), as a candidate
+__device__ __forceinline__ Cand64 edge_cand64(const Feat &F, double3 p, int e) {
+    const int4 q = F.edge_vf[e];
+    const double3 a = d3(load_vpos(F.vpos, q.x)), b = d3(load_vpos(F.vpos, q.y));
+    const double3 ab = b - a, ap = p - a;
+    const double t = ddot3(ap, ab) / ddot3(ab, ab);
+    Cand64 c;
+    if (t <= 0.0) {
+        c.id = F.T + F.E + q.x;
+        c.pq = ap;
+    } else if (t >= 1.0) {
+        c.id = F.T + F.E + q.y;
+        c.pq = p - b;
+    } else {
+        c.id = F.T + e;
+        c.pq = ap - t * ab;
+    }
+    c.d2 = ddot3(c.pq, c.pq);
+    return c;
+}
+
+__device__ __forceinline__ Cand64 vert_cand64(const Feat &F, double3 p, int v) {
+    Cand64 c;
+    c.id = F.T + F.E + v;
+    c.pq = p - d3(load_vpos(F.vpos, v));
+    c.d2 = ddot3(c.pq, c.pq);
+    return c;
+}
+
+// One warp per queued point.  The point's FP32 winner may be wrong by the FP32 error (band edge)
+// or carry an uncertain sign; here the exact FP64 minimum is taken over every feature whose
+// characteristic region can contain the point: those of the (tile, region) pairs of the point's
+// tile whose tile-local box contains it (every region containing the point is listed there, so
+// the true closest feature is among them, Section 4).  A first FP32 pass over these candidates
+// finds the smallest FP32 distance d0; only candidates within d0 + 3 delta are evaluated in FP64
+// (the true closest one's FP32 distance is within delta of the minimum, and d0 is at most delta
+// below it, plus the plane distance's under-estimate in the inclusion margin, at most delta).
+// Without a pair list (the paper's cell-loop schedule) the candidates are the triangles of the
+// fans of the FP32 winner's vertices.  The sign is that of (p - q).N with N the FP64 pseudonormal
+// of the feature holding the closest point q (face normal, n1 + n2, or N_alpha, Eq. 8).
+template <int TY, int TZ>
+__global__ void k_patch(const Prob *P, const long long *tile_base, Outputs o) {
     const int lane = threadIdx.x & 31;
     const int64_t wid0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -986,80 +1106,101 @@ __global__ void k_patch(const Prob *P, Outputs o) {
         const double h = g.h;
         const double3 p = make_double3((double)g.ox + (gi + 0.5) * h, (double)g.oy + (gj + 0.5) * h,
                                        (double)g.oz + (gk + 0.5) * h);
-        int vs[3], nv;
-        if (fid < F.T) { vs[0] = F.face_vid[3 * fid]; vs[1] = F.face_vid[3 * fid + 1]; vs[2] = F.face_vid[3 * fid + 2]; nv = 3; }
-        else if (fid < F.T + F.E) { int4 q = F.edge_vf[fid - F.T]; vs[0] = q.x; vs[1] = q.y; vs[2] = 0; nv = 2; }
-        else { vs[0] = fid - F.T - F.E; vs[1] = vs[2] = 0; nv = 1; }
-        // the fans of the winner's vertices, concatenated; lanes take one corner (triangle) each
-        int c0[3], cn[3];
-        for (int a = 0; a < 3; a++) {
-            c0[a] = a < nv ? F.vert_start[vs[a]] : 0;
-            cn[a] = a < nv ? F.vert_start[vs[a] + 1] - c0[a] : 0;
+        Cand64 best;
+        best.d2 = INFINITY;
+        best.id = 0x7fffffff;
+        best.pq = make_double3(0, 0, 0);
+        if (o.pairs) {
+            const int tx = gi / TILE_X, ty = gj / TY, tz = gk / TZ;
+            const int64_t tile = tile_base[pe.prob] + ((int64_t)tz * g.nty + ty) * g.ntx + tx;
+            const uint32_t *st = o.bin_start + 3 * tile;
+            const int64_t q0 = min((int64_t)st[0], o.pair_cap), q3 = min((int64_t)st[3], o.pair_cap);
+            const unsigned lx = (unsigned)(gi - tx * TILE_X), ly = (unsigned)(gj - ty * TY), lz = (unsigned)(gk - tz * TZ);
+            // pass 1: the smallest FP32 distance over the regions whose box holds the point
+            float d0 = INFINITY;
+            for (int64_t q = q0 + lane; q < q3; q += 32) {
+                const int2 pr = __ldg(o.pairs + q);
+                const unsigned bx = (unsigned)pr.y;
+                if (lx < (bx & 31u) || lx > ((bx >> 5) & 31u) || ly < ((bx >> 10) & 15u) || ly > ((bx >> 14) & 15u) ||
+                    lz < ((bx >> 18) & 15u) || lz > ((bx >> 22) & 15u))
+                    continue;
+                const int type = feat_type(F, pr.x);
+                bool neg, unc;
+                d0 = fminf(d0, eval_any(F, g, type, feat_local(F, pr.x, type), gi, gj, gk, neg, unc));
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) d0 = fminf(d0, __shfl_xor_sync(FULL, d0, off));
+            const float thr = d0 + 3.f * g.derr;
+            // pass 2: FP64 closest points of the candidates within the threshold
+            for (int64_t q = q0 + lane; q < q3; q += 32) {
+                const int2 pr = __ldg(o.pairs + q);
+                const unsigned bx = (unsigned)pr.y;
+                if (lx < (bx & 31u) || lx > ((bx >> 5) & 31u) || ly < ((bx >> 10) & 15u) || ly > ((bx >> 14) & 15u) ||
+                    lz < ((bx >> 18) & 15u) || lz > ((bx >> 22) & 15u))
+                    continue;
+                const int type = feat_type(F, pr.x), id = feat_local(F, pr.x, type);
+                bool neg, unc;
+                if (!(eval_any(F, g, type, id, gi, gj, gk, neg, unc) <= thr)) continue;
+                const Cand64 c = type == FACE ? face_cand64(F, p, id) : (type == EDGE ? edge_cand64(F, p, id)
+                                                                                       : vert_cand64(F, p, id));
+                if (cand_less(c.d2, c.id, best.d2, best.id)) best = c;
+            }
+        } else {
+            // the fans of the winner's vertices, concatenated; lanes take one corner (triangle) each
+            int vs[3], nv;
+            if (fid < F.T) { vs[0] = F.face_vid[3 * fid]; vs[1] = F.face_vid[3 * fid + 1]; vs[2] = F.face_vid[3 * fid + 2]; nv = 3; }
+            else if (fid < F.T + F.E) { int4 q = F.edge_vf[fid - F.T]; vs[0] = q.x; vs[1] = q.y; vs[2] = 0; nv = 2; }
+            else { vs[0] = fid - F.T - F.E; vs[1] = vs[2] = 0; nv = 1; }
+            int c0[3], cn[3];
+            for (int a = 0; a < 3; a++) {
+                c0[a] = a < nv ? F.vert_start[vs[a]] : 0;
+                cn[a] = a < nv ? F.vert_start[vs[a] + 1] - c0[a] : 0;
+            }
+            const int total = cn[0] + cn[1] + cn[2];
+            for (int slot = lane; slot < total; slot += 32) {
+                const int a = slot < cn[0] ? 0 : (slot < cn[0] + cn[1] ? 1 : 2);
+                const int c = c0[a] + slot - (a == 0 ? 0 : (a == 1 ? cn[0] : cn[0] + cn[1]));
+                const Cand64 cd = face_cand64(F, p, F.vert_corner[c] / 3);
+                if (cand_less(cd.d2, cd.id, best.d2, best.id)) best = cd;
+            }
         }
-        const int total = cn[0] + cn[1] + cn[2];
-        double bd = INFINITY;
-        int bt = 0x7fffffff, breg = 0;
-        double3 blam = make_double3(0, 0, 0);
-        for (int slot = lane; slot < total; slot += 32) {
-            const int a = slot < cn[0] ? 0 : (slot < cn[0] + cn[1] ? 1 : 2);
-            const int c = c0[a] + slot - (a == 0 ? 0 : (a == 1 ? cn[0] : cn[0] + cn[1]));
-            const int t = F.vert_corner[c] / 3;
-            int reg;
-            double3 lam;
-            double d2 = closest_on_tri(p, d3(load_vpos(F.vpos, F.face_vid[3 * t])),
-                                       d3(load_vpos(F.vpos, F.face_vid[3 * t + 1])),
-                                       d3(load_vpos(F.vpos, F.face_vid[3 * t + 2])), reg, lam);
-            if (d2 < bd || (d2 == bd && t < bt)) { bd = d2; bt = t; breg = reg; blam = lam; }
-        }
-        // warp argmin over (d2, triangle)
+        // warp argmin over (d2, feature id)
         int src = lane;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            double od = __shfl_xor_sync(FULL, bd, off);
-            int ot = __shfl_xor_sync(FULL, bt, off);
-            int os = __shfl_xor_sync(FULL, src, off);
-            if (od < bd || (od == bd && ot < bt)) { bd = od; bt = ot; src = os; }
+            const double od = __shfl_xor_sync(FULL, best.d2, off);
+            const int oid = __shfl_xor_sync(FULL, best.id, off);
+            const int os = __shfl_xor_sync(FULL, src, off);
+            if (cand_less(od, oid, best.d2, best.id)) { best.d2 = od; best.id = oid; src = os; }
         }
-        breg = __shfl_sync(FULL, breg, src);
-        blam.x = __shfl_sync(FULL, blam.x, src);
-        blam.y = __shfl_sync(FULL, blam.y, src);
-        blam.z = __shfl_sync(FULL, blam.z, src);
-        const int t = bt;
-        const double3 A = d3(load_vpos(F.vpos, F.face_vid[3 * t])), B = d3(load_vpos(F.vpos, F.face_vid[3 * t + 1])),
-                      C = d3(load_vpos(F.vpos, F.face_vid[3 * t + 2]));
-        double3 N;
-        int out_id;
-        if (breg == 0) {
-            N = tri_normal64(F, t);
-            out_id = t;
-        } else if (breg <= 3) {
-            const int k = breg - 1;
-            const int ee = F.face_edge[3 * t + k];
-            const int4 q = F.edge_vf[ee];
+        const double3 pq = make_double3(__shfl_sync(FULL, best.pq.x, src), __shfl_sync(FULL, best.pq.y, src),
+                                        __shfl_sync(FULL, best.pq.z, src));
+        const int out_id = best.id;
+        // FP64 pseudonormal of the feature holding the closest point
+        double3 N = make_double3(0, 0, 0);
+        if (out_id < F.T) {
+            N = tri_normal64(F, out_id);
+        } else if (out_id < F.T + F.E) {
+            const int4 q = F.edge_vf[out_id - F.T];
             N = tri_normal64(F, q.z) + tri_normal64(F, q.w);
-            out_id = F.T + ee;
-        } else {
-            const int u = F.face_vid[3 * t + (breg - 4)];
+        } else if (out_id != 0x7fffffff) {
+            const int u = out_id - F.T - F.E;
             const int c0 = F.vert_start[u], c1 = F.vert_start[u + 1];
-            const double3 P = d3(load_vpos(F.vpos, u));
+            const double3 Pv = d3(load_vpos(F.vpos, u));
             double3 acc = make_double3(0, 0, 0);
             for (int c = c0 + lane; c < c1; c += 32) {  // N_alpha = sum alpha_i n_i, lanes over the fan
                 const int cc = F.vert_corner[c];
                 const int ft = cc / 3, kk = cc - 3 * ft;
-                double3 e1 = d3(load_vpos(F.vpos, F.face_vid[3 * ft + (kk + 1) % 3])) - P;
-                double3 e2 = d3(load_vpos(F.vpos, F.face_vid[3 * ft + (kk + 2) % 3])) - P;
+                double3 e1 = d3(load_vpos(F.vpos, F.face_vid[3 * ft + (kk + 1) % 3])) - Pv;
+                double3 e2 = d3(load_vpos(F.vpos, F.face_vid[3 * ft + (kk + 2) % 3])) - Pv;
                 double3 cr = dcross3(e1, e2);
                 double alpha = atan2(sqrt(ddot3(cr, cr)), ddot3(e1, e2));
                 acc = acc + alpha * tri_normal64(F, ft);
             }
             N = make_double3(wsum(acc.x), wsum(acc.y), wsum(acc.z));
-            out_id = F.T + F.E + u;
         }
-        // p - q relative to corner A: (p - A) - lam_b (B - A) - lam_c (C - A)
-        double3 pq = (p - A) - blam.y * (B - A) - blam.z * (C - A);
-        if (breg == 0) pq = p - A;
         const double s = ddot3(pq, N);
-        const double d = sqrt(bd);
+        const double d = sqrt(best.d2);
         if (lane == 0) {
             float val = INFINITY;
             int w = -1;
@@ -1077,6 +1218,16 @@ __global__ void k_patch(const Prob *P, Outputs o) {
             }
         }
     }
+}
+
+// The FP32 error windows of every problem of a launch, from its grid and the current precision
+// terms of its mesh (set_windows); the first kernel of every narrow-band launch.
+__global__ void k_windows(Prob *P, int n) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const unsigned *pr = P[p].F.prec;
+    set_windows(P[p].g, __uint_as_float(pr[PREC_MESH_M]), __uint_as_float(pr[PREC_TAU_A]),
+                __uint_as_float(pr[PREC_TAU_B]), __uint_as_float(pr[PREC_TAU_V]));
 }
 
 inline unsigned nblk(int64_t n, int bt) { return (unsigned)((n + bt - 1) / bt); }
@@ -1170,12 +1321,10 @@ __device__ __forceinline__ unsigned walk_region(const Feat &F, const GridP &g, i
                 } else if (!region_contains<TYPE>(F, g, id, p)) {
                     continue;
                 }
-                bool neg;
-                const float d = eval_point<TYPE>(F, g, id, i, j, k, neg);
+                bool neg, unc;
+                const float d = eval_point<TYPE>(F, g, id, i, j, k, neg, unc);
                 if (d < g.W) {
-                    const unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) |
-                                                   ((unsigned long long)(unsigned)fid << 1) | (unsigned long long)neg;
-                    atomicMin(keys + ((int64_t)k * g.ny + j) * g.nx + i, key);
+                    atomicMin(keys + ((int64_t)k * g.ny + j) * g.nx + i, make_key(d, fid, unc, neg));
                     cand++;
                 }
             }
@@ -1254,11 +1403,10 @@ static int make_grid(const sdf_grid &gr, float w, int shape, GridP &g) {
     }
     M = fmax(M, (double)w);
     g.w = w;
-    g.eps = (float)(M * 0x1p-21);          // inclusion tolerance, about 8 ulp(M)
-    const float dw = (float)(M * 0x1p-21);  // bound on the FP32 distance error
-    g.W = w + dw;
-    g.dlo = w - dw;
-    g.ds = (float)(M * 0x1p-19);           // sign window, 4x the inclusion tolerance
+    g.Mg = (float)M;
+    // provisional windows of the grid alone; every launch finalises them on the device with the
+    // mesh's current precision terms (k_windows)
+    set_windows(g, 0.f, 0.f, 0.f, 0.f);
     return SDF_OK;
 }
 
@@ -1270,6 +1418,7 @@ static Feat make_feat(const sdf_features_s *f) {
     F.edge_class = f->edge_class; F.vert_class = f->vert_class;
     F.face_vid = f->face_vid; F.face_edge = f->face_edge; F.vert_start = f->vert_start;
     F.vert_corner = f->vert_corner; F.edge_vf = f->edge_vf; F.vpos = f->vpos;
+    F.prec = f->ctr->prec;
     F.skip_saddle = (f->flags & SDF_FLAG_DISABLE_SADDLE) ? 1 : 0;
     F.vmode = VM_EXACT;
     return F;
@@ -1386,6 +1535,7 @@ static cudaError_t pinned_get(size_t bytes, char **p, size_t *got) {
             }
     }
     const size_t want = bytes < 4096 ? 4096 : bytes;
+    count_host_alloc();
     cudaError_t e = cudaMallocHost(reinterpret_cast<void **>(p), want);
     *got = e == cudaSuccess ? want : 0;
     return e;
@@ -1456,6 +1606,7 @@ static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *gr
             pr.list_count = lists[p].count;
             pr.list_cap = lists[p].cap;
         }
+        if (feats[p]->T + feats[p]->E + feats[p]->V >= (int64_t(1) << 30)) return SDF_ERR_TOO_LARGE;  // key ids
         pl.fbase[p + 1] = pl.fbase[p] + feats[p]->T + feats[p]->E + feats[p]->V;
         pl.tbase[p + 1] = pl.tbase[p] + (long long)pr.g.ntx * pr.g.nty * pr.g.ntz;
         // the fill's argument (rows outside the band run uncrossed) needs w > h
@@ -1600,6 +1751,8 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
                         cudaEvent_t *ev) {
     const int64_t n_bins = 3 * n_tiles;
     if (ev) SDF_TRY(record_event(ev[0], s));
+    k_windows<<<nblk(n, 64), 64, 0, s>>>(const_cast<Prob *>(sc.probs), n);
+    SDF_LAUNCHED(1);
     SDF_TRY(cudaMemsetAsync(sc.cnt, 0, sizeof(uint32_t) * n_bins, s));
     SDF_TRY(cudaMemsetAsync(&sc.ctr->nb_status, 0, sizeof(unsigned), s));
     SDF_TRY(cudaMemsetAsync(&sc.ctr->n_candidates, 0, 6 * sizeof(unsigned long long), s));
@@ -1645,7 +1798,7 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
     if (ev) SDF_TRY(record_event(ev[2], s));
-    k_patch<<<4 * num_sms(), 256, 0, s>>>(sc.probs, o);
+    k_patch<TY, TZ><<<4 * num_sms(), 256, 0, s>>>(sc.probs, sc.tbase, o);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
     if (sc.fprobs)
@@ -1658,6 +1811,8 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
 // the paper's schedule: clear the keys, one thread per region, decode, FP64 re-decision (and the fill)
 static int launch_cell_loop(int n, long long f_tot, const Scratch &sc, cudaStream_t s, cudaEvent_t *ev) {
     if (ev) SDF_TRY(record_event(ev[0], s));
+    k_windows<<<nblk(n, 64), 64, 0, s>>>(const_cast<Prob *>(sc.probs), n);
+    SDF_LAUNCHED(1);
     SDF_TRY(cudaMemsetAsync(sc.keys, 0xff, sizeof(unsigned long long) * (size_t)sc.p_tot, s));
     SDF_TRY(cudaMemsetAsync(&sc.ctr->nb_status, 0, sizeof(unsigned), s));
     SDF_TRY(cudaMemsetAsync(&sc.ctr->n_candidates, 0, 6 * sizeof(unsigned long long), s));
@@ -1676,7 +1831,7 @@ static int launch_cell_loop(int n, long long f_tot, const Scratch &sc, cudaStrea
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
     if (ev) SDF_TRY(record_event(ev[2], s));
-    k_patch<<<4 * num_sms(), 256, 0, s>>>(sc.probs, o);
+    k_patch<8, 8><<<4 * num_sms(), 256, 0, s>>>(sc.probs, sc.tbase, o);  // no pairs: fan search
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
     if (sc.fprobs)
@@ -2005,6 +2160,27 @@ extern "C" void sdf_batch_destroy(sdf_batch b) {
     delete b;
 }
 
+extern "C" int sdf_features_error_bound(sdf_features f, const sdf_grid *grid, float band_w, double *bounds,
+                                        void *stream) {
+    using namespace sdf;
+    if (!f || !grid || !bounds) return SDF_ERR_INVALID_ARG;
+    GridP g;
+    SDF_TRY_ST(make_grid(*grid, band_w, 0, g));
+    unsigned prec[4] = {0, 0, 0, 0};
+    {
+        const HostRead rd[1] = {{prec, f->ctr->prec, sizeof(prec)}};
+        SDF_TRY(read_small(rd, 1, reinterpret_cast<cudaStream_t>(stream)));
+    }
+    float v[4];
+    memcpy(v, prec, sizeof(v));
+    set_windows(g, v[PREC_MESH_M], v[PREC_TAU_A], v[PREC_TAU_B], v[PREC_TAU_V]);
+    bounds[0] = g.derr;
+    bounds[1] = g.eps;
+    bounds[2] = g.ds;
+    bounds[3] = fmax(g.ds2, g.dsv);
+    return SDF_OK;
+}
+
 extern "C" int sdf_features_status(sdf_features f, int64_t *stats, void *stream) {
     if (!f) return SDF_ERR_INVALID_ARG;
     return sdf::narrow_band_stats(f, stats, reinterpret_cast<cudaStream_t>(stream));
@@ -2062,6 +2238,8 @@ constexpr size_t ST_BYTES = ST_OFF_PATCH + sizeof(PatchEntry) * ST_MAX_PATCH;   
 static __device__ __align__(256) unsigned char g_static_scratch[ST_BYTES];
 
 // device address of g_static_scratch for each device, looked up once with that device current
+// (under a lock: two host threads may make their first calls at the same time)
+static std::mutex g_static_mu;
 static unsigned char *static_scratch_ptr(int *err) {
     static unsigned char *ptrs[64] = {nullptr};
     int dev = 0;
@@ -2069,6 +2247,7 @@ static unsigned char *static_scratch_ptr(int *err) {
         *err = SDF_ERR_CUDA;
         return nullptr;
     }
+    std::lock_guard<std::mutex> lk(g_static_mu);
     if (!ptrs[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
@@ -2095,7 +2274,6 @@ extern "C" int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, floa
     unsigned char *base = static_scratch_ptr(&st);
     if (st) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    Feat F = make_feat(f);
     const int64_t n_feat = f->T + f->E + f->V;
     // the one-problem table: Prob, feature prefix sums {0, n_feat}, tile prefix sums {0, n_tiles}
     Prob pr;
@@ -2128,13 +2306,14 @@ extern "C" int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, floa
     // the array keeps the previous call's contents: clear the counters (the pipeline clears the rest)
     SDF_TRY(cudaMemsetAsync(sc.ctr, 0, sizeof(DevCounters), s));
     SDF_TRY_ST((launch_shape<8, 8>(1, n_feat, n_tiles, sc, s, nullptr)));
-    DevCounters *ctr = sc.ctr;
-    // read the status word: a pair or re-decision list beyond the static limits is an error
-    unsigned status = 0;
-    {
-        const HostRead rd[1] = {{&status, &ctr->nb_status, sizeof(unsigned)}};
-        SDF_TRY(read_small(rd, 1, s));
-    }
-    if (status & (ST_PAIR_OVERFLOW | ST_PATCH_OVERFLOW)) return SDF_ERR_TOO_LARGE;
+    // The status words, read into host stack memory: this call's list overflows and the handle's
+    // own status (a face that sdf_features_update_positions made degenerate).  A device-to-host
+    // copy into pageable memory returns once the data has arrived and allocates nothing.
+    unsigned status[2] = {0, 0};
+    SDF_TRY(cudaMemcpyAsync(&status[0], &sc.ctr->nb_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    SDF_TRY(cudaMemcpyAsync(&status[1], &f->ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    SDF_TRY(cudaStreamSynchronize(s));
+    if (status[1] & ST_DEGENERATE) return SDF_ERR_DEGENERATE;
+    if (status[0] & (ST_PAIR_OVERFLOW | ST_PATCH_OVERFLOW)) return SDF_ERR_TOO_LARGE;
     return SDF_OK;
 }

@@ -274,30 +274,60 @@ __device__ __forceinline__ float3 normalized(float3 v) {
     return r * v;
 }
 
+// Largest value over the warp, taken into the counter word with one atomic (v >= 0).
+__device__ __forceinline__ void warp_max_into(unsigned *word, float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(word, __float_as_uint(v));
+}
+
+// Face records, and the precision terms of the faces (every thread of the grid takes part in the
+// warp reductions, so the early-exit threads contribute zeros).  The FP32 unit normal n of a
+// face, from e1 = b - a and e2 = c - a, differs in direction from the exact normal of the FP32
+// corners by at most 17 u kappa (u = 2^-24, kappa = |e1| |e2| / |e1 x e2|: the rounding of the
+// two differences and of the cross product give |d(e1 x e2)| <= (2 sqrt 2 + 2) u |e1| |e2|, the
+// direction error of the normalisation at most twice the relative error, plus 7 u for rsqrt and
+// the products).  The side planes n x (edge) then err by at most (17 kappa + 10) u, and a plane
+// test at a point p within the prism, |p - a| <= D + W (D the face's longest edge, W the band
+// cutoff), by at most 27 u kappa (D + W).  The records kernels keep the maxima of
+// tau_a = 32 u kappa D and tau_b = 32 u kappa (rounded up) and of the coordinate magnitude;
+// the narrow band adds tau_a + tau_b W to its FP32 error bound (see the windows in band.cu).
 __global__ void k_face_records(const int32_t *face_vid, const float *vpos, int64_t T, float4 *face_rec,
                                float4 *face_box, DevCounters *ctr) {
     int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (f >= T) return;
-    float3 a = load_vpos(vpos, face_vid[3 * f]), b = load_vpos(vpos, face_vid[3 * f + 1]),
-           c = load_vpos(vpos, face_vid[3 * f + 2]);
-    float3 e1 = b - a, e2 = c - a;
-    float3 cr = cross3(e1, e2);
-    float len2 = dot3(cr, cr);
-    float scale = dot3(e1, e1) + dot3(e2, e2);
-    if (!(len2 > 1e-10f * scale * scale) && degenerate_fp64(a, b, c)) {
-        atomicOr(&ctr->status, ST_DEGENERATE);
-        len2 = fmaxf(len2, 1e-30f);
+    float m_abs = 0.f, tau_a = 0.f, tau_b = 0.f;
+    if (f < T) {
+        float3 a = load_vpos(vpos, face_vid[3 * f]), b = load_vpos(vpos, face_vid[3 * f + 1]),
+               c = load_vpos(vpos, face_vid[3 * f + 2]);
+        float3 e1 = b - a, e2 = c - a, e3 = c - b;
+        float3 cr = cross3(e1, e2);
+        float len2 = dot3(cr, cr);
+        const float l1 = dot3(e1, e1), l2 = dot3(e2, e2), l3 = dot3(e3, e3);
+        float scale = l1 + l2;
+        if (!(len2 > 1e-10f * scale * scale) && degenerate_fp64(a, b, c)) {
+            atomicOr(&ctr->status, ST_DEGENERATE);
+            len2 = fmaxf(len2, 1e-30f);
+        }
+        float3 n = rsqrtf(len2) * cr;
+        // plane of the face, and the three side planes with inward normals n x (edge) (Section 8.1)
+        face_rec[4 * f + 0] = make_float4(n.x, n.y, n.z, -dot3(n, a));
+        face_rec[4 * f + 1] = plane_through(normalized(cross3(n, b - a)), a);
+        face_rec[4 * f + 2] = plane_through(normalized(cross3(n, c - b)), b);
+        face_rec[4 * f + 3] = plane_through(normalized(cross3(n, a - c)), c);
+        face_box[2 * f + 0] = make_float4(fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)),
+                                          fminf(a.z, fminf(b.z, c.z)), 0.f);
+        face_box[2 * f + 1] = make_float4(fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)),
+                                          fmaxf(a.z, fmaxf(b.z, c.z)), 0.f);
+        const float3 lo = f3(face_box[2 * f]), hi = f3(face_box[2 * f + 1]);
+        m_abs = fmaxf(fmaxf(fmaxf(fabsf(lo.x), fabsf(hi.x)), fmaxf(fabsf(lo.y), fabsf(hi.y))),
+                      fmaxf(fabsf(lo.z), fabsf(hi.z)));
+        const float kappa = fminf(sqrtf(l1 * l2 / len2), 1e12f);
+        tau_b = 32.f * U32 * kappa * 1.001f;
+        tau_a = tau_b * sqrtf(fmaxf(l1, fmaxf(l2, l3))) * 1.001f;
     }
-    float3 n = rsqrtf(len2) * cr;
-    // plane of the face, and the three side planes with inward normals n x (edge) (Section 8.1)
-    face_rec[4 * f + 0] = make_float4(n.x, n.y, n.z, -dot3(n, a));
-    face_rec[4 * f + 1] = plane_through(normalized(cross3(n, b - a)), a);
-    face_rec[4 * f + 2] = plane_through(normalized(cross3(n, c - b)), b);
-    face_rec[4 * f + 3] = plane_through(normalized(cross3(n, a - c)), c);
-    face_box[2 * f + 0] = make_float4(fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)),
-                                      fminf(a.z, fminf(b.z, c.z)), 0.f);
-    face_box[2 * f + 1] = make_float4(fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)),
-                                      fmaxf(a.z, fmaxf(b.z, c.z)), 0.f);
+    warp_max_into(&ctr->prec[PREC_MESH_M], m_abs);
+    warp_max_into(&ctr->prec[PREC_TAU_A], tau_a);
+    warp_max_into(&ctr->prec[PREC_TAU_B], tau_b);
 }
 
 __device__ double3 face_normal_fp64(const int32_t *face_vid, const float *vpos, int f) {
@@ -328,7 +358,7 @@ __global__ void k_edge_records(const int4 *edge_vf, const int32_t *face_vid, con
     edge_rec[5 * e + 1] = make_float4(t.x, t.y, t.z, dot3(t, a));
     edge_rec[5 * e + 2] = make_float4(-m1.x, -m1.y, -m1.z, dot3(m1, a));
     edge_rec[5 * e + 3] = make_float4(-m2.x, -m2.y, -m2.z, dot3(m2, a));
-    edge_rec[5 * e + 4] = make_float4(np.x, np.y, np.z, 0.f);
+    edge_rec[5 * e + 4] = make_float4(np.x, np.y, np.z, sqrtf(dot3(np, np)));  // (n1 + n2, |n1 + n2|)
     float d = dot3(cross3(t, n1), n2);
     int8_t cls;
     if (fabsf(d) > 2e-6f) {
@@ -394,19 +424,35 @@ __global__ void k_vertex_records(const int32_t *vert_start, const int32_t *vert_
     const float3 p = valid ? load_vpos(vpos, (int)v) : make_float3(0.f, 0.f, 0.f);
     // pass 1: pseudonormal and region planes
     float3 N = make_float3(0.f, 0.f, 0.f);
+    float asum = 0.f;
     for (int i = s0 + sub; i < s1; i += VL) {
         const int c = vert_corner[i];
         const int f = c / 3, k = c - 3 * f;
         const float3 xn = load_vpos(vpos, face_vid[3 * f + (k + 1) % 3]);
         const float3 xp = load_vpos(vpos, face_vid[3 * f + (k + 2) % 3]);
         const float3 e1 = xn - p, e2 = xp - p;
-        N = N + corner_angle(e1, e2) * f3(face_rec[4 * f]);
+        const float alpha = corner_angle(e1, e2);
+        asum += alpha;
+        N = N + alpha * f3(face_rec[4 * f]);
         const float3 ej = normalized(e1);
         vert_plane[i] = make_float4(-ej.x, -ej.y, -ej.z, dot3(ej, p));
     }
     N = make_float3(gsum8(N.x), gsum8(N.y), gsum8(N.z));
+    asum = gsum8(asum);
     const float Nlen = sqrtf(dot3(N, N));
     const float3 Nu = (Nlen > 0.f ? 1.f / Nlen : 0.f) * N;
+    // Direction error of the unit pseudonormal: each term alpha_i n_i errs by at most
+    // alpha_i (17 kappa + 8) u (the face normal's direction error and the angle's rounding) and the
+    // sum of deg terms adds deg u sum(alpha); the normalisation at most doubles the relative error.
+    // tau_v = 2 sum(alpha) (17 kappa_max + deg + 8) u / |N_alpha|, kept as a maximum (per unit
+    // distance: the sign predicate N^.(p - v) errs by tau_v |p - v| from it).
+    {
+        const float kap17 = 17.f / 32.f * __uint_as_float(ctr->prec[PREC_TAU_B]);  // 17 u kappa_max
+        float tv = 0.f;
+        if (valid && sub == 0 && s1 > s0)
+            tv = Nlen > 0.f ? fminf(2.f * asum * (kap17 + (float)(s1 - s0 + 8) * U32) / Nlen * 1.001f, 1.f) : 1.f;
+        warp_max_into(&ctr->prec[PREC_TAU_V], tv);
+    }
     __syncwarp();  // the group's planes are written before they are read back
     // pass 2: classification (FP32 with an error margin), convexity and the normal spread
     bool below = false, above = false, unsure = false, cvx = true, ccv = true;
@@ -733,6 +779,7 @@ extern "C" int sdf_features_update_positions(sdf_features f, const float *vertic
     SDF_TRY(cudaMemcpyAsync(f->vpos, vertices, sizeof(float) * 3 * f->V, cudaMemcpyDeviceToDevice, s));
     SDF_TRY(cudaMemsetAsync(f->ctr->cls, 0, sizeof(f->ctr->cls), s));
     SDF_TRY(cudaMemsetAsync(&f->ctr->status, 0, sizeof(unsigned), s));  // re-evaluated below
+    SDF_TRY(cudaMemsetAsync(f->ctr->prec, 0, sizeof(f->ctr->prec), s));  // precision terms, likewise
     return build_records(f, s);
 }
 
@@ -760,6 +807,13 @@ extern "C" int sdf_features_vertex_map(sdf_features f, int32_t *soup_to_vertex, 
 extern "C" int sdf_features_face_map(sdf_features f, int32_t *face_to_soup, void *stream) {
     if (!f || !face_to_soup) return SDF_ERR_INVALID_ARG;
     SDF_TRY(cudaMemcpyAsync(face_to_soup, f->face_soup, sizeof(int32_t) * f->T, cudaMemcpyDeviceToDevice,
+                            reinterpret_cast<cudaStream_t>(stream)));
+    return SDF_OK;
+}
+
+extern "C" int sdf_features_edges(sdf_features f, int32_t *out, void *stream) {
+    if (!f || !out) return SDF_ERR_INVALID_ARG;
+    SDF_TRY(cudaMemcpyAsync(out, f->edge_vf, sizeof(int4) * f->E, cudaMemcpyDeviceToDevice,
                             reinterpret_cast<cudaStream_t>(stream)));
     return SDF_OK;
 }

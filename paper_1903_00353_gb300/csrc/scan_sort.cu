@@ -357,11 +357,15 @@ extern "C" int64_t sdf_kernel_launches(void) { return sdf::g_launches.load(); }
 // ============================================================================= memory pool
 namespace sdf {
 static cudaMemPool_t g_pools[64] = {nullptr};
+static std::mutex g_pool_mu;  // guards the creation of the per-device pools
+static std::atomic<int64_t> g_pool_allocs{0}, g_host_allocs{0};
+void count_host_alloc() { g_host_allocs.fetch_add(1, std::memory_order_relaxed); }
 
 static cudaMemPool_t pool_for_current_device(cudaError_t *err) {
     int dev = 0;
     *err = cudaGetDevice(&dev);
     if (*err != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
     if (!g_pools[dev]) {
         cudaMemPoolProps props = {};
         props.allocType = cudaMemAllocationTypePinned;
@@ -383,11 +387,37 @@ cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
     cudaError_t e;
     cudaMemPool_t pool = pool_for_current_device(&e);
     if (!pool) return e;
+    g_pool_allocs.fetch_add(1, std::memory_order_relaxed);
     return cudaMallocFromPoolAsync(p, bytes > 0 ? bytes : 1, pool, s);
 }
 
 cudaError_t pool_free(void *p, cudaStream_t s) { return p ? cudaFreeAsync(p, s) : cudaSuccess; }
 }  // namespace sdf
+
+extern "C" int sdf_memory_stats(int64_t *out) {
+    using namespace sdf;
+    if (!out) return SDF_ERR_INVALID_ARG;
+    out[0] = g_pool_allocs.load();
+    out[1] = out[2] = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+        cudaMemPool_t pool = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(g_pool_mu);
+            pool = g_pools[dev];
+        }
+        if (pool) {
+            uint64_t used = 0, reserved = 0;
+            if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess ||
+                cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess)
+                return SDF_ERR_CUDA;
+            out[1] = (int64_t)used;
+            out[2] = (int64_t)reserved;
+        }
+    }
+    out[3] = g_host_allocs.load();
+    return SDF_OK;
+}
 
 // ----------------------------------------------------------------------------- small reads
 namespace sdf {
@@ -429,7 +459,10 @@ cudaError_t read_small(const HostRead *reads, int n, cudaStream_t s) {
         }
     }
     cudaError_t e = cudaSuccess;
-    if (!buf) e = cudaMallocHost(reinterpret_cast<void **>(&buf), MAX_READ_BYTES);
+    if (!buf) {
+        e = cudaMallocHost(reinterpret_cast<void **>(&buf), MAX_READ_BYTES);
+        count_host_alloc();
+    }
     if (e != cudaSuccess) return e;
     k_read_small<<<1, 128, 0, s>>>(r, buf);  // pinned host memory is device-addressable (unified addressing)
     count_launches(1);

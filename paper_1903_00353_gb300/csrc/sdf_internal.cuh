@@ -32,6 +32,8 @@ constexpr int TILE_PTS = TILE_X * TILE_Y * TILE_Z;
 // size seen before does not reach the driver's allocator.
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);
 cudaError_t pool_free(void *p, cudaStream_t s);
+// counts a pinned host allocation (reported by sdf_memory_stats)
+void count_host_alloc();
 
 struct DevBuf {
     void *p = nullptr;
@@ -67,7 +69,16 @@ struct DevCounters {
     unsigned long long cls[8];         // classification counts
     unsigned tile_hist[16];            // band tiles per cost class (class 0: the most pairs)
     unsigned tile_cursor[16];          // fill cursors of the classes in the band tile list
+    // Precision terms of the current positions (FP32 bits of non-negative floats, so an unsigned
+    // atomicMax takes their maximum), written by the records kernels: PREC_MESH_M the largest
+    // vertex coordinate magnitude, PREC_TAU_A / PREC_TAU_B the shape term of the FP32 plane
+    // and normal errors, tau_a + tau_b * W (see k_face_records), PREC_TAU_V the direction error
+    // of the unit pseudonormals per unit distance (see k_vertex_records).
+    unsigned prec[4];
 };
+enum { PREC_MESH_M = 0, PREC_TAU_A = 1, PREC_TAU_B = 2, PREC_TAU_V = 3 };
+// unit roundoff of FP32 (2^-24)
+constexpr float U32 = 5.9604644775390625e-8f;
 
 struct Plan;
 void plan_free(Plan *pl, cudaStream_t s);
@@ -107,7 +118,7 @@ struct sdf_features_s {
     float *vpos = nullptr;          // [V][3]
     float4 *face_rec = nullptr;     // [T][4] (n, c0) and three inward side planes (m, c)
     float4 *face_box = nullptr;     // [T][2] vertex bounding box lo, hi
-    float4 *edge_rec = nullptr;     // [E][5] (a, L) (t, t.a) (-m1, m1.a) (-m2, m2.a) (n1+n2, 0)
+    float4 *edge_rec = nullptr;     // [E][5] (a, L) (t, t.a) (-m1, m1.a) (-m2, m2.a) (n1+n2, |n1+n2|)
     float4 *vert_rec = nullptr;     // [V][3] (v, start) (unit N_alpha, count) (cone axis, cos theta)
     float4 *vert_plane = nullptr;   // [3T] (-e_j, e_j.v) per incident edge, CSR by vert_start
     int8_t *edge_class = nullptr;   // [E]

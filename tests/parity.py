@@ -69,3 +69,60 @@ def near_surface_indices(soup: np.ndarray, dims, origin, h: float, w: float, n: 
     ijk = np.clip(ijk, 0, dims - 1)
     idx = ijk[:, 0] + dims[0] * (ijk[:, 1] + dims[1] * ijk[:, 2])
     return np.unique(idx)
+
+
+def oracle_of_features(feats):
+    """An oracle mesh with the library's own welded vertex numbering (vertices from the features
+    at their current positions, triangles in soup order), so that vertex gradients compare index
+    by index, and the mapping from library winner ids to oracle features."""
+    import oracle
+    X = feats.vertices().cpu().numpy().astype(np.float64)
+    tri = feats.vertex_map().cpu().numpy().reshape(-1, 3)
+    om = oracle.OracleMesh.from_indexed(X, tri)
+    return om, WinnerMap(feats, tri)
+
+
+class WinnerMap:
+    """Library feature ids (face f, edge T + e, vertex T + E + v) -> oracle features (soup triangle,
+    region label: 0 face, 1 + k edge from corner k to k + 1, 4 + k corner k)."""
+
+    def __init__(self, feats, tri):
+        self.T, self.E = feats.n_tri, feats.n_edge
+        self.face_map = feats.face_map().cpu().numpy().astype(np.int64)
+        self.edges = feats.edges().cpu().numpy().astype(np.int64)
+        self.tri = tri.astype(np.int64)
+        corners = tri.ravel()
+        order = np.argsort(corners, kind="stable")
+        first = np.full(feats.n_vert, -1, dtype=np.int64)
+        first[corners[order[::-1]]] = order[::-1]  # smallest soup corner of every vertex
+        self.first_corner = first
+
+    def __call__(self, wid: np.ndarray):
+        wid = np.asarray(wid, dtype=np.int64)
+        t = np.empty(wid.shape, dtype=np.int32)
+        r = np.empty(wid.shape, dtype=np.int32)
+        face = wid < self.T
+        t[face] = self.face_map[wid[face]]
+        r[face] = 0
+        edge = (wid >= self.T) & (wid < self.T + self.E)
+        e = wid[edge] - self.T
+        va, vb, f1 = self.edges[e, 0], self.edges[e, 1], self.edges[e, 2]
+        ts = self.face_map[f1]
+        k = np.full(e.shape, -1, dtype=np.int64)
+        for c in range(3):  # f1 holds the directed edge va -> vb
+            hit = (self.tri[ts, c] == va) & (self.tri[ts, (c + 1) % 3] == vb)
+            k[hit] = c
+        assert np.all(k >= 0), "edge not found in its face"
+        t[edge] = ts
+        r[edge] = 1 + k
+        vert = wid >= self.T + self.E
+        c = self.first_corner[wid[vert] - self.T - self.E]
+        assert np.all(c >= 0)
+        t[vert] = c // 3
+        r[vert] = 4 + c % 3
+        return t, r
+
+
+def rel_l2(a, b) -> float:
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))

@@ -5,8 +5,10 @@ runtime or a fixed budget, or they cannot afford an allocation's latency).  For 
 library offers one entry point whose scratch is a fixed device array inside the library.  This
 test checks, on two calls in a row (the second one finds the first one's leftovers in the
 shared array), that it returns the same field and winners as the regular sdf_narrow_band,
-within the tolerance of the parity tests, and that a grid beyond the array's limit is
-rejected.  It lives in its own file, collected last, and passes alone or after the other tests.
+within the tolerance of the parity tests, that those calls take no device memory from the
+library's pool and no pinned host memory, that a grid beyond the array's limit is rejected, and
+that positions which collapse a face are reported as the regular call reports them.  It lives in
+its own file, collected last, and passes alone or after the other tests.
 """
 import ctypes
 
@@ -47,12 +49,21 @@ def test_static_matches_regular_two_calls(lib, case):
         grid, w = sdf.Grid(90, 77, 45, (0.0, 0.0, float(np.float32(0.23))), h), float(np.float32(3 * h))
     feats = sdf.sdf_build_features(torch.from_numpy(soup).cuda())
     ref_d, ref_w = sdf.sdf_narrow_band(feats, grid, w, winner=True)
-    for _ in range(2):
-        d = torch.full(grid.shape, 7.0, dtype=torch.float32, device="cuda")
-        wn = torch.full(grid.shape, -7, dtype=torch.int32, device="cuda")
+    outs = [(torch.full(grid.shape, 7.0, dtype=torch.float32, device="cuda"),
+             torch.full(grid.shape, -7, dtype=torch.int32, device="cuda")) for _ in range(2)]
+    torch.cuda.synchronize()
+    before = sdf.memory_stats()
+    torch_before = torch.cuda.memory_allocated()
+    for d, wn in outs:
         assert _static_call(sdf, feats, grid, w, d, wn) == 0
-        torch.cuda.synchronize()
-        fin = torch.isfinite(ref_d)
+    torch.cuda.synchronize()
+    after = sdf.memory_stats()
+    # no allocation of any kind during the two calls: none from the library's device pool (count,
+    # bytes in use and reserved unchanged), no pinned host block, nothing through torch
+    assert after == before, (before, after)
+    assert torch.cuda.memory_allocated() == torch_before
+    fin = torch.isfinite(ref_d)
+    for d, wn in outs:
         assert torch.equal(fin, torch.isfinite(d))
         assert float((d[fin] - ref_d[fin]).abs().max()) <= 2e-6
         assert torch.equal(wn, ref_w)
@@ -66,3 +77,20 @@ def test_static_rejects_grid_beyond_limit(lib):
     assert _static_call(sdf, feats, grid, 3 / 1024, d, None) == 0
     big = sdf.Grid(1024, 1024, 600, (0.0, 0.0, 0.0), 1 / 1024)  # 32 * 128 * 75 tiles > 65536
     assert _static_call(sdf, feats, big, 3 / 1024, d, None) == 5  # SDF_ERR_TOO_LARGE, before any work
+
+
+def test_static_reports_a_collapsed_face(lib):
+    """Positions that collapse a face (one corner moved onto another): both the regular and the
+    allocation-free call return SDF_ERR_DEGENERATE (3)."""
+    sdf = lib
+    feats = sdf.sdf_build_features(torch.from_numpy(meshgen.icosphere(3, radius=0.3).soup(seed=4)).cuda())
+    grid, w = sdf.Grid.cube(48), 3 / 48
+    X = feats.vertices().clone()
+    tri = feats.vertex_map().view(-1, 3)[0].tolist()
+    X[tri[1]] = X[tri[0]]
+    feats.update_positions(X)
+    d = torch.empty(grid.shape, dtype=torch.float32, device="cuda")
+    assert _static_call(sdf, feats, grid, w, d, None) == 3
+    with pytest.raises(sdf.SDFError) as e:
+        sdf.sdf_narrow_band(feats, grid, w, out=d)
+    assert e.value.code == 3
