@@ -195,33 +195,32 @@ def knot_curve(t: np.ndarray, p: int = 3, q: int = 7, R: float = 0.3, a: float =
     return c, dc
 
 
-def _parallel_transport_frame(T: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
-    """Closed parallel-transport frame along unit tangents T[n,3]; closure twist spread uniformly."""
+def _parallel_transport_frame(T: np.ndarray, P: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Closed rotation-minimising frame along a closed polyline P[n,3] with unit tangents T[n,3],
+    by the double-reflection method (Wang, Juettler, Zheng and Liu, 2008): N is reflected across
+    the plane normal to the chord P[i+1] - P[i], then across the plane normal to the difference
+    between T[i+1] and the reflected T[i]; the closure twist is spread uniformly."""
     n = T.shape[0]
     N = np.zeros_like(T)
     a = np.cross(T[0], [0.0, 0.0, 1.0])
     if np.linalg.norm(a) < 1e-6:
         a = np.cross(T[0], [1.0, 0.0, 0.0])
     N[0] = a / np.linalg.norm(a)
-    for i in range(n - 1):
-        # rotate N[i] by the minimal rotation taking T[i] to T[i+1] (double reflection)
-        v1 = T[i + 1] - T[i]
-        c1 = v1 @ v1
-        r = N[i] - (2.0 / c1) * (v1 @ N[i]) * v1 if c1 > 0 else N[i]
-        t = T[i] - (2.0 / c1) * (v1 @ T[i]) * v1 if c1 > 0 else T[i]
-        v2 = T[i + 1] - t
+
+    def step(Ni, Ti, Tj, chord):
+        c1 = chord @ chord
+        r = Ni - (2.0 / c1) * (chord @ Ni) * chord
+        t = Ti - (2.0 / c1) * (chord @ Ti) * chord
+        v2 = Tj - t
         c2 = v2 @ v2
-        N[i + 1] = r - (2.0 / c2) * (v2 @ r) * v2 if c2 > 0 else r
-        N[i + 1] -= (N[i + 1] @ T[i + 1]) * T[i + 1]
-        N[i + 1] /= np.linalg.norm(N[i + 1])
+        Nj = r - (2.0 / c2) * (v2 @ r) * v2 if c2 > 1e-30 else r
+        Nj = Nj - (Nj @ Tj) * Tj
+        return Nj / np.linalg.norm(Nj)
+
+    for i in range(n - 1):
+        N[i + 1] = step(N[i], T[i], T[i + 1], P[i + 1] - P[i])
     # transport once more from the last sample back to the first to measure the twist
-    v1 = T[0] - T[-1]
-    c1 = v1 @ v1
-    r = N[-1] - (2.0 / c1) * (v1 @ N[-1]) * v1 if c1 > 0 else N[-1]
-    t = T[-1] - (2.0 / c1) * (v1 @ T[-1]) * v1 if c1 > 0 else T[-1]
-    v2 = T[0] - t
-    c2 = v2 @ v2
-    Nend = r - (2.0 / c2) * (v2 @ r) * v2 if c2 > 0 else r
+    Nend = step(N[-1], T[-1], T[0], P[0] - P[-1])
     B0 = np.cross(T[0], N[0])
     phi = math.atan2(Nend @ B0, Nend @ N[0])
     ang = -phi * np.arange(n) / n
@@ -238,7 +237,7 @@ def knot_tube(n_along: int = 8192, n_around: int = 128, radius: float = 0.04, no
     t = 2 * math.pi * np.arange(n_along) / n_along
     c, dc = knot_curve(t, p, q, R, a)
     T = dc / np.linalg.norm(dc, axis=1, keepdims=True)
-    N, B = _parallel_transport_frame(T)
+    N, B = _parallel_transport_frame(T, c)
     th = 2 * math.pi * np.arange(n_around) / n_around
     rng = np.random.Generator(np.random.PCG64(seed))
     S, TH = np.meshgrid(t, th, indexing="ij")

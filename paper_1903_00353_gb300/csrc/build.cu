@@ -259,13 +259,6 @@ __global__ void k_edge_emit(const int32_t *vert_corner, const int32_t *face_vid,
 
 // ----------------------------------------------------------------------------- records (geometry)
 // FP64 check of a (filtered) zero-area predicate
-__device__ bool degenerate_fp64(float3 a, float3 b, float3 c) {
-    double3 e1 = d3(b) - d3(a), e2 = d3(c) - d3(a);
-    double3 cr = dcross3(e1, e2);
-    double len = sqrt(ddot3(cr, cr));
-    return !(len > 1e-14 * (ddot3(e1, e1) + ddot3(e2, e2)));
-}
-
 __device__ __forceinline__ float4 plane_through(float3 m, float3 p) {  // (m, -m.p): value m.x + w
     return make_float4(m.x, m.y, m.z, -dot3(m, p));
 }
@@ -282,16 +275,16 @@ __device__ __forceinline__ void warp_max_into(unsigned *word, float v) {
 }
 
 // Face records, and the precision terms of the faces (every thread of the grid takes part in the
-// warp reductions, so the early-exit threads contribute zeros).  The FP32 unit normal n of a
-// face, from e1 = b - a and e2 = c - a, differs in direction from the exact normal of the FP32
-// corners by at most 17 u kappa (u = 2^-24, kappa = |e1| |e2| / |e1 x e2|: the rounding of the
-// two differences and of the cross product give |d(e1 x e2)| <= (2 sqrt 2 + 2) u |e1| |e2|, the
-// direction error of the normalisation at most twice the relative error, plus 7 u for rsqrt and
-// the products).  The side planes n x (edge) then err by at most (17 kappa + 10) u, and a plane
-// test at a point p within the prism, |p - a| <= D + W (D the face's longest edge, W the band
-// cutoff), by at most 27 u kappa (D + W).  The records kernels keep the maxima of
-// tau_a = 32 u kappa D and tau_b = 32 u kappa (rounded up) and of the coordinate magnitude;
-// the narrow band adds tau_a + tau_b W to its FP32 error bound (see the windows in band.cu).
+// warp reductions, so the early-exit threads contribute zeros).  The unit normal and the plane
+// offset -n.a are computed in FP64 from the FP32 corners (their differences are exact in FP64)
+// and rounded once, so the stored normal is within about u = 2^-24 of the exact normal of the
+// corners however thin the triangle.  The side planes n x (edge) are formed in FP32 from it: the
+// edge difference, the cross product and the normalisation add at most 8 u to the direction, so
+// a side-plane test at a point p of the prism errs by at most 8 u |p - a| <= 8 u (D + W) beyond
+// the rounding of its evaluation (D the face's longest edge, W the band cutoff).  The edge wedge
+// planes (k_edge_records) have the same bound with the edge length.  The records kernels keep the
+// maxima of tau_a = 10 u D and tau_b = 10 u (with margin) and of the coordinate magnitude; the
+// narrow band adds tau_a + tau_b W to its FP32 error bound (the windows in band.cu).
 __global__ void k_face_records(const int32_t *face_vid, const float *vpos, int64_t T, float4 *face_rec,
                                float4 *face_box, DevCounters *ctr) {
     int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -299,18 +292,17 @@ __global__ void k_face_records(const int32_t *face_vid, const float *vpos, int64
     if (f < T) {
         float3 a = load_vpos(vpos, face_vid[3 * f]), b = load_vpos(vpos, face_vid[3 * f + 1]),
                c = load_vpos(vpos, face_vid[3 * f + 2]);
-        float3 e1 = b - a, e2 = c - a, e3 = c - b;
-        float3 cr = cross3(e1, e2);
-        float len2 = dot3(cr, cr);
-        const float l1 = dot3(e1, e1), l2 = dot3(e2, e2), l3 = dot3(e3, e3);
-        float scale = l1 + l2;
-        if (!(len2 > 1e-10f * scale * scale) && degenerate_fp64(a, b, c)) {
+        const double3 A = d3(a), E1 = d3(b) - A, E2 = d3(c) - A;
+        const double3 CR = dcross3(E1, E2);
+        double len = sqrt(ddot3(CR, CR));
+        if (!(len > 1e-14 * (ddot3(E1, E1) + ddot3(E2, E2)))) {  // zero area (Section 4)
             atomicOr(&ctr->status, ST_DEGENERATE);
-            len2 = fmaxf(len2, 1e-30f);
+            len = fmax(len, 1e-300);
         }
-        float3 n = rsqrtf(len2) * cr;
+        const double3 N = (1.0 / len) * CR;
+        const float3 n = make_float3((float)N.x, (float)N.y, (float)N.z);
         // plane of the face, and the three side planes with inward normals n x (edge) (Section 8.1)
-        face_rec[4 * f + 0] = make_float4(n.x, n.y, n.z, -dot3(n, a));
+        face_rec[4 * f + 0] = make_float4(n.x, n.y, n.z, (float)-ddot3(N, A));
         face_rec[4 * f + 1] = plane_through(normalized(cross3(n, b - a)), a);
         face_rec[4 * f + 2] = plane_through(normalized(cross3(n, c - b)), b);
         face_rec[4 * f + 3] = plane_through(normalized(cross3(n, a - c)), c);
@@ -321,9 +313,10 @@ __global__ void k_face_records(const int32_t *face_vid, const float *vpos, int64
         const float3 lo = f3(face_box[2 * f]), hi = f3(face_box[2 * f + 1]);
         m_abs = fmaxf(fmaxf(fmaxf(fabsf(lo.x), fabsf(hi.x)), fmaxf(fabsf(lo.y), fabsf(hi.y))),
                       fmaxf(fabsf(lo.z), fabsf(hi.z)));
-        const float kappa = fminf(sqrtf(l1 * l2 / len2), 1e12f);
-        tau_b = 32.f * U32 * kappa * 1.001f;
-        tau_a = tau_b * sqrtf(fmaxf(l1, fmaxf(l2, l3))) * 1.001f;
+        const float3 e3 = c - b;
+        const float diam = sqrtf(fmaxf(fmaxf(dot3(b - a, b - a), dot3(c - a, c - a)), dot3(e3, e3)));
+        tau_b = 10.f * U32;
+        tau_a = tau_b * diam * 1.001f;
     }
     warp_max_into(&ctr->prec[PREC_MESH_M], m_abs);
     warp_max_into(&ctr->prec[PREC_TAU_A], tau_a);
@@ -442,15 +435,14 @@ __global__ void k_vertex_records(const int32_t *vert_start, const int32_t *vert_
     const float Nlen = sqrtf(dot3(N, N));
     const float3 Nu = (Nlen > 0.f ? 1.f / Nlen : 0.f) * N;
     // Direction error of the unit pseudonormal: each term alpha_i n_i errs by at most
-    // alpha_i (17 kappa + 8) u (the face normal's direction error and the angle's rounding) and the
-    // sum of deg terms adds deg u sum(alpha); the normalisation at most doubles the relative error.
-    // tau_v = 2 sum(alpha) (17 kappa_max + deg + 8) u / |N_alpha|, kept as a maximum (per unit
-    // distance: the sign predicate N^.(p - v) errs by tau_v |p - v| from it).
+    // alpha_i 10 u (the stored face normal within u, the angle's rounding) and the sum of deg terms
+    // adds deg u sum(alpha); the normalisation at most doubles the relative error.
+    // tau_v = 2 sum(alpha) (deg + 10) u / |N_alpha|, kept as a maximum (per unit distance: the sign
+    // predicate N^.(p - v) errs by tau_v |p - v| from it).
     {
-        const float kap17 = 17.f / 32.f * __uint_as_float(ctr->prec[PREC_TAU_B]);  // 17 u kappa_max
         float tv = 0.f;
         if (valid && sub == 0 && s1 > s0)
-            tv = Nlen > 0.f ? fminf(2.f * asum * (kap17 + (float)(s1 - s0 + 8) * U32) / Nlen * 1.001f, 1.f) : 1.f;
+            tv = Nlen > 0.f ? fminf(2.f * asum * (float)(s1 - s0 + 10) * U32 / Nlen * 1.001f, 1.f) : 1.f;
         warp_max_into(&ctr->prec[PREC_TAU_V], tv);
     }
     __syncwarp();  // the group's planes are written before they are read back

@@ -154,6 +154,13 @@ def test_c4_knot_tube_stratified_million():
     print(f"C4: {idx.size} points, {within2.size} within 2 delta by FP32 (all of the grid's), stratum {stratum.size}, "
           f"oracle-confirmed within 2 delta {int(true2.sum())}, delta {delta:.2e}", st)
     assert idx.size >= 900_000 and stratum.size >= 100_000 and within2.size > 5_000
+    if st["sign_mismatch"] or st["mask_mismatch"]:  # diagnostics of the failing points
+        g_band, o_band = np.isfinite(d_gpu), np.abs(d_or) < w
+        bad = (g_band & o_band & (np.abs(d_or) > 1e-5 * h) & (np.sign(d_gpu) != np.sign(d_or))) | \
+              ((g_band != o_band) & (np.abs(a_or - w) > 1e-5 * h))
+        win = sdf.sdf_narrow_band(feats, grid, w, winner=True)[1].view(-1)[torch.from_numpy(idx[bad]).cuda()]
+        for i, d1, d2, wi in zip(idx[bad][:20], d_gpu[bad][:20], d_or[bad][:20], win.cpu().numpy()[:20]):
+            print("mismatch", int(i), float(d1), float(d2), int(wi))
     parity.assert_parity(st)
     assert near.sum() == stratum.size
 
