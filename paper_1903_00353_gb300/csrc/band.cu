@@ -829,13 +829,15 @@ __global__ void k_tile_lists(const uint32_t *bin_start, int64_t n_tiles, const u
     }
 }
 
-// Persistent tile kernel over all tiles of all problems of a batch: CTAs take work items from one
-// atomic ticket.  Work item w < n_band is band tile w plus its share of the empty tiles (so the
-// HBM-bound +inf fill is spread over the compute-bound band work); without band tiles, items are
-// chunks of FILL_CHUNK empty tiles.  A band tile merges its regions' candidates in shared memory
-// and writes its points; an empty tile is written +inf (Algorithm 1's initial value).  LIST: some
-// problem of the launch writes a compact band list (compiled apart, so that the plain kernel
-// carries none of its code).
+// Persistent tile kernel over all tiles of all problems of a batch.  Two work queues, each with
+// its own atomic ticket: the band tiles (one per item, largest first for batches) and chunks of
+// FILL_CHUNK empty tiles.  Half of the CTAs start on the empty chunks, the others on the band
+// tiles, and a CTA whose queue runs dry takes work from the other one.  A band tile merges its
+// regions' candidates in shared memory and writes its points; an empty tile is written +inf
+// (Algorithm 1's initial value).  The dense output goes out with streaming (evict-first) stores,
+// so that the write stream does not push the feature records that the band work reads out of
+// L2.  LIST: some problem of the launch writes a compact band list (compiled apart, so that the
+// plain kernel carries none of its code).
 template <int TY, int TZ, bool LIST>
 __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *tile_base, int n, Outputs o,
                                                 int64_t n_tiles, const int32_t *band_list,
@@ -845,21 +847,38 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
     extern __shared__ __align__(16) unsigned char tile_smem[];
     TileSmem<TY, TZ> &S = *reinterpret_cast<TileSmem<TY, TZ> *>(tile_smem);
     __shared__ unsigned s_cand, s_band, s_ovf, s_rows, s_hits, s_pairs;
+    __shared__ int s_kind;
     if (threadIdx.x == 0) { s_cand = 0; s_band = 0; s_ovf = 0; s_rows = 0; s_hits = 0; s_pairs = 0; }
     unsigned cand = 0, band = 0, rows = 0, hits = 0, pairs = 0;
     bool overflow = false, list_ovf = false;
     const int64_t n_band = *n_band_ptr, n_empty = n_tiles - n_band;
-    const int64_t n_work = n_band > 0 ? n_band : (n_empty + FILL_CHUNK - 1) / FILL_CHUNK;
+    const int64_t n_chunks = (n_empty + FILL_CHUNK - 1) / FILL_CHUNK;
     for (;;) {
-        if (threadIdx.x == 0) S.work = (long long)atomicAdd(ticket, 1ull);
+        if (threadIdx.x == 0) {
+            const bool filler = blockIdx.x >= gridDim.x / 2;
+            long long w = -1;
+            int kind = 0;
+            for (int q = 0; q < 2 && w < 0; q++) {
+                const int k = (q == 0) == filler ? 1 : 0;  // 1: empty chunks, 0: band tiles
+                const long long lim = k ? n_chunks : n_band;
+                if ((long long)*(volatile unsigned long long *)(ticket + k) >= lim) continue;
+                const long long t = (long long)atomicAdd(ticket + k, 1ull);
+                if (t < lim) {
+                    w = t;
+                    kind = k;
+                }
+            }
+            S.work = w;
+            s_kind = kind;
+        }
         __syncthreads();
         const int64_t w = S.work;
+        const int kind = s_kind;
         __syncthreads();
-        if (w >= n_work) break;
-        const int64_t e_begin = n_band > 0 ? (w * n_empty) / n_band : w * FILL_CHUNK;
-        const int64_t e_end = n_band > 0 ? ((w + 1) * n_empty) / n_band : min(e_begin + FILL_CHUNK, n_empty);
-        const int64_t t_begin = n_band > 0 ? -1 : 0;  // -1 = the band tile of the item
-        const int64_t t_end = e_end - e_begin;
+        if (w < 0) break;
+        const int64_t e_begin = kind ? w * FILL_CHUNK : 0;
+        const int64_t t_begin = kind ? 0 : -1;  // -1 = the band tile of the item
+        const int64_t t_end = kind ? min(e_begin + FILL_CHUNK, n_empty) - e_begin : 0;
         for (int64_t ti = t_begin; ti < t_end; ti++) {
             const bool is_band = ti < 0;
             const int64_t tile = is_band ? band_list[w] : empty_list[e_begin + ti];
@@ -908,8 +927,8 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
                             emask |= ((unsigned)e0 | (unsigned)e1 << 1 | (unsigned)e2 << 2 | (unsigned)e3 << 3) << sh;
                         }
                     }
-                    *reinterpret_cast<float4 *>(dist + idx) = v;
-                    if (winner) *reinterpret_cast<int4 *>(winner + idx) = wv;
+                    __stcs(reinterpret_cast<float4 *>(dist + idx), v);
+                    if (winner) __stcs(reinterpret_cast<int4 *>(winner + idx), wv);
                 }
             } else {
                 for (int e = threadIdx.x; e < TP; e += NT) {
@@ -921,8 +940,8 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
                     bool en = false;
                     const float val = is_band ? decode_key(S.key[e], g, o, idx, p, wid, band, overflow, en) : INFINITY;
                     if (list && en) emask |= 1u << ((e - (int)threadIdx.x) / NT);
-                    dist[idx] = val;
-                    if (winner) winner[idx] = wid;
+                    __stcs(dist + idx, val);
+                    if (winner) __stcs(winner + idx, wid);
                 }
             }
             if (list) list_write<TY, TZ>(pr, S, emask, x0, y0, z0, vec_rows, list_ovf);
@@ -1777,7 +1796,7 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
     k_tile_lists<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, sc.band_pos, sc.band_list, sc.empty_list,
                                                     sc.ctr, lpt);
     SDF_LAUNCHED(1);
-    SDF_TRY(cudaMemsetAsync(sc.ticket, 0, sizeof(unsigned long long), s));
+    SDF_TRY(cudaMemsetAsync(sc.ticket, 0, 2 * sizeof(unsigned long long), s));  // band and fill tickets
     Outputs o;
     o.pairs = sc.pairs;
     o.bin_start = sc.start;
@@ -2220,7 +2239,7 @@ constexpr int64_t ST_MAX_TILES = 65536;                 // 32x8x8-point tiles (5
 constexpr int64_t ST_MAX_PAIRS = int64_t(2) << 20;      // (tile, region) pairs
 constexpr int64_t ST_MAX_PATCH = 131072;                // points re-decided in FP64
 constexpr size_t ST_OFF_CTR = 0;                        // DevCounters
-constexpr size_t ST_OFF_TICKET = 1024;                  // work ticket (8 bytes)
+constexpr size_t ST_OFF_TICKET = 1024;                  // work tickets (two, 16 bytes)
 constexpr size_t ST_OFF_TABLE = 2048;                   // one Prob, then long long [4] prefix sums
 constexpr size_t ST_PROB_BYTES = (sizeof(Prob) + 15) / 16 * 16;
 constexpr size_t ST_OFF_CNT = ST_OFF_TABLE + 2048;      // uint32 [3 * max tiles]
