@@ -151,18 +151,51 @@ __device__ __forceinline__ int point_adjoint(const AdjArgs &a, int64_t idx, int 
         const float d00 = dot3(ab, ab), d01 = dot3(ab, ac), d11 = dot3(ac, ac);
         const float d20 = dot3(ap, ab), d21 = dot3(ap, ac);
         const float den = d00 * d11 - d01 * d01;
-        float lb = (d11 * d20 - d01 * d21) / den, lc = (d00 * d21 - d01 * d20) / den;
-        // points of the inclusion margin project just outside: clamp onto the triangle
-        lb = fmaxf(lb, 0.f);
-        lc = fmaxf(lc, 0.f);
-        const float sum = lb + lc;
-        if (sum > 1.f) { lb /= sum; lc /= sum; }
-        const float lam[3] = {1.f - lb - lc, lb, lc};
+        const float lb = (d11 * d20 - d01 * d21) / den, lc = (d00 * d21 - d01 * d20) / den;
+        if (lb >= 0.f && lc >= 0.f && lb + lc <= 1.f) {
+            const float lam[3] = {1.f - lb - lc, lb, lc};
+            for (int q = 0; q < 3; q++) {
+                vtx[q] = a.face_vid[3 * f + q];
+                c[q][0] = -g * lam[q] * n.x;
+                c[q][1] = -g * lam[q] * n.y;
+                c[q][2] = -g * lam[q] * n.z;
+            }
+            return 3;
+        }
+        // a point of the inclusion margin: its closest point of the closed triangle lies on the
+        // boundary, q = A + lb ab + lc ac on the nearest of the three edges, and the contribution
+        // takes the direction (p - q)/|p - q| with the face's sign, as at an edge
+        float best = INFINITY, bb = 0.f, bc = 0.f;
+        {
+            const float t = fminf(fmaxf(d20 / d00, 0.f), 1.f);  // edge AB
+            const float3 r = ap - t * ab;
+            const float e = dot3(r, r);
+            if (e < best) { best = e; bb = t; bc = 0.f; }
+        }
+        {
+            const float t = fminf(fmaxf(d21 / d11, 0.f), 1.f);  // edge AC
+            const float3 r = ap - t * ac;
+            const float e = dot3(r, r);
+            if (e < best) { best = e; bb = 0.f; bc = t; }
+        }
+        {
+            const float3 bcv = ac - ab, bp = ap - ab;  // edge BC
+            const float t = fminf(fmaxf(dot3(bp, bcv) / dot3(bcv, bcv), 0.f), 1.f);
+            const float3 r = bp - t * bcv;
+            const float e = dot3(r, r);
+            if (e < best) { best = e; bb = 1.f - t; bc = t; }
+        }
+        const float3 d = ap - bb * ab - bc * ac;
+        const float len = sqrtf(dot3(d, d));
+        if (!(len > 0.f)) return 0;
+        const float s = dot3(d, n) < 0.f ? -1.f : 1.f;
+        const float lam[3] = {1.f - bb - bc, bb, bc};
+        const float k0 = -g * s / len;
         for (int q = 0; q < 3; q++) {
             vtx[q] = a.face_vid[3 * f + q];
-            c[q][0] = -g * lam[q] * n.x;
-            c[q][1] = -g * lam[q] * n.y;
-            c[q][2] = -g * lam[q] * n.z;
+            c[q][0] = k0 * lam[q] * d.x;
+            c[q][1] = k0 * lam[q] * d.y;
+            c[q][2] = k0 * lam[q] * d.z;
         }
         return 3;
     } else if (wid < a.T + a.E) {

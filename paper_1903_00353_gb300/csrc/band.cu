@@ -829,6 +829,60 @@ __global__ void k_tile_lists(const uint32_t *bin_start, int64_t n_tiles, const u
     }
 }
 
+// One chunk of empty tiles (tile ids empty_list[e0 .. e1)): +inf, and winner -1 when winners are
+// kept.  The problem's sizes and pointers are loaded once per problem met (every tile of a
+// single-problem call, and most chunks of a batch, belong to one), so a whole tile costs its index
+// arithmetic and, per thread, TY * TZ / 32 coalesced 16-byte stores; tiles cut by the grid's edge
+// or rows not 16-byte aligned take the per-point path.
+template <int TY, int TZ>
+__device__ __forceinline__ void fill_chunk(const Prob *P, const long long *tile_base, int n, const int32_t *empty_list,
+                                           int64_t e0, int64_t e1) {
+    long long tb_lo = 1, tb_hi = 0;  // tile range of the loaded problem (empty: load on first use)
+    int nx = 0, ny = 0, nz = 0, ntx = 0, nty = 0, vec = 0;
+    FastDiv dtx, dty;
+    float *dist = nullptr;
+    int32_t *winner = nullptr;
+    const float4 inf4 = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+    for (int64_t e = e0; e < e1; e++) {
+        const long long tile = empty_list[e];
+        if (tile < tb_lo || tile >= tb_hi) {
+            const int p = find_prob(tile_base, n, tile);
+            const GridP &g = P[p].g;
+            tb_lo = tile_base[p];
+            tb_hi = tile_base[p + 1];
+            nx = g.nx; ny = g.ny; nz = g.nz; ntx = g.ntx; nty = g.nty;
+            dtx = g.div_ntx; dty = g.div_nty;
+            dist = P[p].dist;
+            winner = P[p].winner;
+            vec = P[p].vec;
+        }
+        const uint32_t tu = (uint32_t)(tile - tb_lo), r1 = dtx.div(tu), tz = dty.div(r1);
+        const int x0 = (int)(tu - r1 * (uint32_t)ntx) * TILE_X, y0 = (int)(r1 - tz * (uint32_t)nty) * TY,
+                  z0 = (int)tz * TZ;
+        const int64_t plane = (int64_t)nx * ny;
+        if (vec && x0 + TILE_X <= nx && y0 + TY <= ny && z0 + TZ <= nz) {
+            const int64_t org = (int64_t)z0 * plane + (int64_t)y0 * nx + x0 + (threadIdx.x & 7) * 4;
+#pragma unroll
+            for (int pass = 0; pass < (TY * TZ + NT / 8 - 1) / (NT / 8); pass++) {
+                const int r = (int)(threadIdx.x >> 3) + pass * (NT / 8);
+                if ((TY * TZ) % (NT / 8) == 0 || r < TY * TZ) {
+                    const int64_t idx = org + (int64_t)(r / TY) * plane + (int64_t)(r % TY) * nx;
+                    __stcs(reinterpret_cast<float4 *>(dist + idx), inf4);
+                    if (winner) __stcs(reinterpret_cast<int4 *>(winner + idx), make_int4(-1, -1, -1, -1));
+                }
+            }
+        } else {
+            for (int q = threadIdx.x; q < TILE_X * TY * TZ; q += NT) {
+                const int gi = x0 + q % TILE_X, gj = y0 + (q / TILE_X) % TY, gk = z0 + q / (TILE_X * TY);
+                if (gi >= nx || gj >= ny || gk >= nz) continue;
+                const int64_t idx = (int64_t)gk * plane + (int64_t)gj * nx + gi;
+                __stcs(dist + idx, INFINITY);
+                if (winner) __stcs(winner + idx, -1);
+            }
+        }
+    }
+}
+
 // Persistent tile kernel over all tiles of all problems of a batch.  Two work queues, each with
 // its own atomic ticket: the band tiles (one per item, largest first for batches) and chunks of
 // FILL_CHUNK empty tiles.  Half of the CTAs start on the empty chunks, the others on the band
@@ -876,12 +930,13 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
         const int kind = s_kind;
         __syncthreads();
         if (w < 0) break;
-        const int64_t e_begin = kind ? w * FILL_CHUNK : 0;
-        const int64_t t_begin = kind ? 0 : -1;  // -1 = the band tile of the item
-        const int64_t t_end = kind ? min(e_begin + FILL_CHUNK, n_empty) - e_begin : 0;
-        for (int64_t ti = t_begin; ti < t_end; ti++) {
-            const bool is_band = ti < 0;
-            const int64_t tile = is_band ? band_list[w] : empty_list[e_begin + ti];
+        if (kind) {  // a chunk of empty tiles
+            fill_chunk<TY, TZ>(P, tile_base, n, empty_list, w * FILL_CHUNK, min((w + 1) * FILL_CHUNK, n_empty));
+            continue;
+        }
+        {  // a band tile
+            const bool is_band = true;
+            const int64_t tile = band_list[w];
             const int p = find_prob(tile_base, n, tile);
             const Prob &pr = P[p];
             const GridP &g = pr.g;
