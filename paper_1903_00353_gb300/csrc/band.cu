@@ -1250,9 +1250,28 @@ __global__ void k_patch(const Prob *P, const long long *tile_base, Outputs o) {
         const double3 pq = make_double3(__shfl_sync(FULL, best.pq.x, src), __shfl_sync(FULL, best.pq.y, src),
                                         __shfl_sync(FULL, best.pq.z, src));
         const int out_id = best.id;
-        // FP64 pseudonormal of the feature holding the closest point
+        // The sign: (p - q).N with the feature's stored FP32 pseudonormal (face normal, n1 + n2, unit
+        // N_alpha) when that cannot flip it, i.e. when |(p - q).N| exceeds |p - q| times the stored
+        // normal's direction error (u for faces and edges, rounded from FP64 normals; tau_v for
+        // N_alpha); otherwise the FP64 pseudonormal (Eq. 8 for a vertex).  The fallback is rare: it
+        // needs p within about 1e-6 |p - q| of the pseudonormal's plane.
+        const double pql = sqrt(ddot3(pq, pq));
         double3 N = make_double3(0, 0, 0);
+        double nerr = 0.0;
         if (out_id < F.T) {
+            N = d3(f3(__ldg(F.face_rec + 4 * out_id)));
+            nerr = 4e-7;
+        } else if (out_id < F.T + F.E) {
+            N = d3(f3(__ldg(F.edge_rec + 5 * (out_id - F.T) + 4)));
+            nerr = 8e-7;
+        } else if (out_id != 0x7fffffff) {
+            N = d3(f3(__ldg(F.vert_rec + 3 * (out_id - F.T - F.E) + 1)));
+            nerr = (double)__uint_as_float(F.prec[PREC_TAU_V]) + 4e-7;
+        }
+        const bool sure = fabs(ddot3(pq, N)) > 2.0 * nerr * pql * sqrt(ddot3(N, N)) + 1e-300;
+        if (sure) {
+            // the stored normal decides
+        } else if (out_id < F.T) {
             N = tri_normal64(F, out_id);
         } else if (out_id < F.T + F.E) {
             const int4 q = F.edge_vf[out_id - F.T];
