@@ -170,6 +170,49 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class StepClocks:
+    """Per-step SM clock and clock-event reasons, read through NVML (read-only queries) right after
+    each timed step; empty when NVML is not available."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, uuid: str | None):
+        import ctypes
+        self.mhz, self.reasons, self.h = [], set(), None
+        try:
+            self.L = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.L.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            u = uuid if uuid is None or uuid.startswith("GPU-") else "GPU-" + uuid
+            if u is None or self.L.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(h)) != 0:
+                return
+            self.h = h
+        except Exception:
+            self.h = None
+
+    def read(self):
+        if self.h is None:
+            return
+        import ctypes
+        mhz, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        if self.L.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(mhz)) == 0:  # NVML_CLOCK_SM
+            self.mhz.append(int(mhz.value))
+        fn = getattr(self.L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(self.L, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        if fn(self.h, ctypes.byref(rs)) == 0:
+            for bit, name in self.REASONS.items():
+                if rs.value & bit:
+                    self.reasons.add(name)
+
+    def summary(self):
+        if not self.mhz:
+            return None
+        a = np.asarray(self.mhz, dtype=np.float64)
+        return {"per_step_sm_mhz_median": float(np.median(a)), "per_step_sm_mhz_min": float(a.min()),
+                "steps_read": int(a.size), "reasons": sorted(self.reasons)}
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -204,9 +247,69 @@ def cpu_baseline(soup, N, w, target_s: float = 12.0):
         layers *= 2
     frac = layers / N
     rate = band / (spent + t_build * frac)
+    one, brute = _oracle_extras(om, near_surface_points(soup, 20_000, 353_402, w))
     return {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{layers} of {N} z-layers through the mesh middle ({band} band points, {spent:.1f} s) "
-                      f"plus the oracle's mesh build ({t_build:.2f} s) prorated by {frac:.4f}"}
+                      f"plus the oracle's mesh build ({t_build:.2f} s) prorated by {frac:.4f}",
+            "one_core": one, "brute_force": brute}
+
+
+def _oracle_extras(om, pts, n_one: int = 20_000, n_brute: int = 4):
+    """The oracle on one core (the first n_one points) and the literal brute-force loop (every
+    point against every triangle, the plain definition of Eq. 1) on n_brute points."""
+    import oracle
+    cores = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        om.sdf_points(pts[:n_one], pruned=True)
+        t1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
+    t0 = time.perf_counter()
+    om.sdf_points(pts[:n_brute], pruned=False)
+    tb = time.perf_counter() - t0
+    return ({"points_per_s": n_one / t1, "cores": 1, "sample": f"{n_one} points near the surface, pruned search"},
+            {"pairs_per_s": n_brute * om.T / tb, "sample": f"{n_brute} points x {om.T} triangles, literal loop"})
+
+
+def near_surface_points(soup, n, seed, spread):
+    """Seeded points near the surface: random points of random triangles moved along the normal."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    s = soup.astype(np.float64)
+    t = rng.integers(0, s.shape[0], size=n)
+    bc = rng.dirichlet([1, 1, 1], size=n)
+    base = np.einsum("ij,ijk->ik", bc, s[t])
+    nrm = np.cross(s[t, 1] - s[t, 0], s[t, 2] - s[t, 0])
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    return base + nrm * rng.uniform(-spread, spread, size=(n, 1))
+
+
+def cpu_baseline_sampled(soup, N, w, band_total, n_points: int = 1_000_000):
+    """The oracle as it stands on 10^6 grid points sampled near the surface of a large workload:
+    band points produced per second on all cores, the time per point, the full band's time
+    extrapolated from it (labelled), a one-core figure and the literal brute-force rate."""
+    import oracle
+    t0 = time.perf_counter()
+    om = oracle.OracleMesh.from_soup(soup)
+    t_build = time.perf_counter() - t0
+    pts = near_surface_points(soup, n_points, 353_404, w)
+    ijk = np.clip(np.rint(pts * N - 0.5).astype(np.int64), 0, N - 1)
+    idx = np.unique(ijk[:, 0] + N * (ijk[:, 1] + N * ijk[:, 2]))
+    t0 = time.perf_counter()
+    d, _, _ = om.band_points((N, N, N), (0.0, 0.0, 0.0), 1.0 / N, w, idx)
+    dt = time.perf_counter() - t0
+    band = int(np.isfinite(d).sum())
+    per_point = dt / idx.size
+    one, brute = _oracle_extras(om, oracle.grid_points((N, N, N), (0, 0, 0), 1.0 / N, idx[:20_000]))
+    return {"value": band / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{idx.size} grid points near the surface ({band} in the band), {dt:.1f} s; mesh build "
+                      f"{t_build:.1f} s not included",
+            "seconds_per_point": per_point,
+            "full_band_seconds_extrapolated": per_point * band_total,
+            "extrapolation": "time per sampled point x the band points of the full grid (a labelled estimate, "
+                             "not a measurement)",
+            "one_core": one, "brute_force": brute}
 
 
 def batch_problems():
@@ -534,6 +637,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-c4", action="store_true", help="leave the knot-tube record out of the default line")
     ap.add_argument("--grid", type=int, default=None, help="override the grid size N (same mesh, same band in cells)")
     ap.add_argument("--schedule", default="tile", choices=["tile", "cell"],
                     help="forward schedule: the binned tile kernel, or the paper's thread-per-region cell loop "
@@ -570,7 +674,29 @@ def main():
         if world > 1:
             tdist.destroy_process_group()
         return
+    line = run_single(args, args.workload, wl, sdf, world, rank, local)
+    # the default workload's line also carries the 2.1M-triangle knot tube at 1024^3 (forward only),
+    # the workload the roofline target is stated for
+    if line is not None and args.workload == "c2" and not args.grid and args.schedule == "tile" and world == 1 \
+            and not args.no_c4:
+        sub = run_single(args, "c4", WORKLOADS["c4"], sdf, world, rank, local)
+        keep = ("value", "unit", "ms_per_step", "ms_per_step_median", "ms_per_step_min", "config", "build_ms",
+                "fwd_ms", "candidates_per_band_point", "fp64_points", "tile_region_pairs", "rows", "rows_hit",
+                "roofline", "sparse", "cpu_baseline", "clocks", "e2e", "gpu_launches")
+        line["c4"] = {k: sub[k] for k in keep if k in sub}
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
 
+
+def run_single(args, name, wl, sdf, world, rank, local):
+    """One single-mesh workload: the timed steps, the end-to-end loop, the roofline records and
+    (rank 0) the CPU baseline.  Returns the JSON line's dict on rank 0, else None."""
+    import torch
+    import torch.distributed as tdist
+
+    import meshgen
     soup_np = meshgen.config_soup(wl["index"])
     N, cells = meshgen.CONFIG_GRID[wl["index"]]
     if args.grid:
@@ -589,7 +715,7 @@ def main():
 
     if wl.get("fit"):
         run_fit(args, wl, sdf, soup_np, soup, grid, w, N, dev, world, rank)
-        return
+        return None
 
     # upstream gradient of L = sum_band (d - 0.01)^2 from one forward (same mesh every step)
     sched_flag = sdf.FLAG_CELL_LOOP if args.schedule == "cell" else 0
@@ -658,6 +784,7 @@ def main():
     per = []
     tile_ms, tile_calls = 0.0, 0
     launches0 = sdf.kernel_launches()
+    step_clk = StepClocks(uuid)
     with ClockSampler(uuid) as clk:
         if world > 1:
             tdist.barrier()
@@ -667,6 +794,7 @@ def main():
             evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             f = step(evs)
             torch.cuda.synchronize()
+            step_clk.read()  # the SM clock right after the step, while it is still at its loaded value
             f.status()
             t = f.timing()
             tile_ms += t["tile"][0]
@@ -760,24 +888,51 @@ def main():
     roofline = {"kernel": kname, "bound": "hbm",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "peak_source": peak_kind,
-                "traffic": tile_traffic(args.workload, not args.grid and not shard and args.schedule == "tile" and use_list),
+                "traffic": tile_traffic(name, not args.grid and not shard and args.schedule == "tile" and use_list),
                 "algorithmic_bytes": int(alg_bytes),
                 "avg_ms": tile_avg_ms}
     # the issue roof: warp instructions of the same ncu capture / the live duration
-    instr = tile_traffic(args.workload, not args.grid and not shard and args.schedule == "tile" and use_list,
+    instr = tile_traffic(name, not args.grid and not shard and args.schedule == "tile" and use_list,
                          "warp_instructions")
     if instr:
         roofline["issue"] = {"bound": "alu", "achieved": instr / (tile_avg_ms / 1e3), "peak": ISSUE_PEAK,
                              "unit": "warp instructions/s", "frac": instr / (tile_avg_ms / 1e3) / ISSUE_PEAK,
                              "warp_instructions": instr}
 
+    # The sparse forward (a project addition, labelled as such): the same tile kernel writing only the
+    # band list with distances (12 B per band point) and no dense field, so no +inf fill.  Its tile
+    # kernel time and the roofline of its own bytes (list + feature records), and the issue roof.
+    sparse = None
+    if args.schedule == "tile" and not shard:
+        sbl = sdf.BandList(band_points + band_points // 4 + 4096, device=dev)
+        fs = sdf.sdf_build_features(soup)
+        for _ in range(3):
+            sdf.sdf_narrow_band_sparse(fs, grid, w, band_list=sbl)
+        fs.timing(reset=True)
+        s_steps = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        for _ in range(s_steps):
+            flush.fill_(1.0)
+            sdf.sdf_narrow_band_sparse(fs, grid, w, band_list=sbl, flags=sdf.FLAG_TIMING | sdf.FLAG_NO_SYNC)
+        torch.cuda.synchronize()
+        fs.status()
+        ts = fs.timing()
+        s_tile = ts["tile"][0] / max(1, ts["tile"][1])
+        s_fwd = (ts["bin"][0] + ts["tile"][0] + ts["fp64"][0]) / max(1, ts["tile"][1])
+        s_bytes = 12 * band_points + rec_bytes
+        sparse = {"what": "sdf_narrow_band_sparse: band list (index, winner) + distances, no dense field "
+                          "(a project addition; the paper writes the dense array)",
+                  "band_points_per_s": band_total / (s_fwd / 1e3), "fwd_device_ms": s_fwd, "tile_ms": s_tile,
+                  "roofline": {"kernel": "k_tile (sparse)", "bound": "hbm", "algorithmic_bytes": int(s_bytes),
+                               "achieved": s_bytes / (s_tile / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                               "frac": s_bytes / (s_tile / 1e3) / 1e9 / hbm, "peak_source": peak_kind}}
+        fs.destroy()
+        del sbl
     if rank != 0:
-        if world > 1:
-            tdist.destroy_process_group()
-        return
+        return None
     cpu = None
     if not args.no_cpu_baseline:
-        cpu = cpu_baseline(soup_np, N, w)
+        cpu = cpu_baseline(soup_np, N, w) if name != "c4" else cpu_baseline_sampled(soup_np, N, w, band_total)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, **step_stats(per.sum(axis=1)), "higher_is_better": True,
@@ -795,12 +950,11 @@ def main():
         "candidates_per_band_point": stats["candidates"] / max(1, stats["band_points"]),
         "fp64_points": stats["fp64_points"], "tile_region_pairs": stats["pairs"], "rows": stats["rows"],
         "rows_hit": stats["rows_hit"],
-        "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(), "e2e": e2e,
+        "roofline": roofline, "sparse": sparse, "cpu_baseline": cpu,
+        "clocks": dict(clk.summary(), per_step=step_clk.summary()), "e2e": e2e,
         "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
     }
-    print(json.dumps(line), flush=True)
-    if world > 1:
-        tdist.destroy_process_group()
+    return line
 
 
 if __name__ == "__main__":

@@ -392,6 +392,24 @@ int sdf_narrow_band_list(sdf_features f, const sdf_grid *grid, float band_w, flo
                          unsigned long long *list_count, uint32_t flags, void *stream);
 
 /*
+ * sdf_narrow_band_sparse -- the narrow band of one problem as the compact band list alone, with no
+ * dense field (a project addition: the paper writes the dense row-major array, Section 10).  Each
+ * band point is listed once, with its signed distance in list_dist at the same position; nothing
+ * is written for the points outside the band, so the output costs 12 bytes per band point
+ * instead of 4 bytes per grid point.  The same tile kernel, merge and FP64 re-decision as
+ * sdf_narrow_band_list.
+ *   list        device sdf_band_entry[list_cap] (as sdf_narrow_band_list).
+ *   list_dist   device float[list_cap]: the signed distance of entry i.
+ *   list_count  device uint64, overwritten with the number of band points.
+ *   flags       0, SDF_FLAG_NO_SYNC, SDF_FLAG_TIMING (not SDF_FLAG_CELL_LOOP or SDF_FLAG_FILL_SIGN).
+ * The grid must have at most 2^32 - 1 points.
+ * Errors: those of sdf_narrow_band_list.
+ */
+int sdf_narrow_band_sparse(sdf_features f, const sdf_grid *grid, float band_w, sdf_band_entry *list,
+                           float *list_dist, int64_t list_cap, unsigned long long *list_count, uint32_t flags,
+                           void *stream);
+
+/*
  * sdf_narrow_band_lists -- the same for n problems in one batch (as sdf_narrow_band with n > 1:
  * one persistent tile launch over all problems, synchronous): problem p writes its field to
  * out_dist[p] and its band list to lists[p] (list_caps[p] entries, length to *list_counts[p],

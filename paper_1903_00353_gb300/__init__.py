@@ -21,7 +21,7 @@ from . import _buildlib
 __all__ = ["Grid", "Features", "sdf_build_features", "sdf_narrow_band", "sdf_narrow_band_backward",
            "SDFFunction", "Batch", "sdf_batch_create", "band_l2_loss", "load_library", "kernel_launches", "SDFError",
            "memory_stats",
-           "BandList", "sdf_narrow_band_list", "sdf_narrow_band_lists", "band_list_backward", "band_list_l2",
+           "BandList", "sdf_narrow_band_list", "sdf_narrow_band_lists", "sdf_narrow_band_sparse", "band_list_backward", "band_list_l2",
            "FLAG_DISABLE_SADDLE", "FLAG_NO_SYNC", "FLAG_TIMING", "FLAG_AUTOTUNE", "FLAG_FILL_SIGN",
            "FLAG_CELL_LOOP", "FLAG_VERTEX_CONE", "FLAG_VERTEX_HEMISPHERE", "FLAG_GRAD_F64"]
 
@@ -100,6 +100,8 @@ def load_library(path: str | None = None):
     L.sdf_batch_timing.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
     L.sdf_band_l2_loss.argtypes = [P, P, I64, P, P, P, P]
     L.sdf_narrow_band_list.argtypes = [P, ctypes.POINTER(_CGrid), ctypes.c_float, P, P, P, I64, P, U32, P]
+    L.sdf_narrow_band_sparse.argtypes = [P, ctypes.POINTER(_CGrid), ctypes.c_float, P, P, I64, P, U32, P]
+    L.sdf_narrow_band_sparse.restype = ctypes.c_int
     L.sdf_narrow_band_lists.argtypes = [ctypes.POINTER(P), ctypes.POINTER(_CGrid), ctypes.POINTER(ctypes.c_float), I32,
                                         ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I64),
                                         ctypes.POINTER(P), U32, P]
@@ -446,6 +448,7 @@ class BandList:
     def __init__(self, capacity: int, device="cuda"):
         self.entries = torch.empty((max(int(capacity), 1), 2), dtype=torch.int32, device=device)
         self.count = torch.zeros(1, dtype=torch.int64, device=device)
+        self.dist = None  # float32 [capacity] signed distances, written by the sparse forward
 
     @property
     def capacity(self) -> int:
@@ -500,6 +503,30 @@ def sdf_narrow_band_list(features: Features, grid: Grid, w: float, out: torch.Te
         _check(code, "sdf_narrow_band_list")
         break
     return (out, band_list, win) if win is not None else (out, band_list)
+
+
+def sdf_narrow_band_sparse(features: Features, grid: Grid, w: float, band_list: BandList | None = None,
+                           flags: int = 0, stream=None) -> BandList:
+    """The narrow band of one problem as a band list with distances and no dense field: returns the
+    BandList, whose `dist` tensor (float32 [capacity]) holds the signed distance of each entry.  A
+    list that turns out too short is grown to the band's length and the call repeated (synchronous
+    calls only)."""
+    if band_list is None:
+        band_list = BandList(BandList.default_capacity(grid))
+    ga = (_CGrid * 1)(grid.c())
+    for attempt in range(2):
+        if band_list.dist is None or band_list.dist.numel() < band_list.capacity:
+            band_list.dist = torch.empty(band_list.capacity, dtype=torch.float32, device=band_list.entries.device)
+        code = load_library().sdf_narrow_band_sparse(
+            features.handle, ga, float(w), band_list.entries.data_ptr(), band_list.dist.data_ptr(),
+            band_list.capacity, band_list.count.data_ptr(), flags, _stream(stream))
+        if code == ERR_LIST_OVERFLOW and attempt == 0:
+            need = int(band_list.count.item())
+            band_list.entries = torch.empty((need + need // 4 + 1024, 2), dtype=torch.int32, device="cuda")
+            continue
+        _check(code, "sdf_narrow_band_sparse")
+        break
+    return band_list
 
 
 def sdf_narrow_band_lists(features: Sequence[Features], grids: Sequence[Grid], ws: Sequence[float],

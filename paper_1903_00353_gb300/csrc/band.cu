@@ -146,6 +146,7 @@ struct Prob {
     uint2 *list = nullptr;
     unsigned long long *list_count = nullptr;
     long long list_cap = 0;
+    float *list_dist = nullptr;  // nullable: the signed distance of every list entry
 };
 
 // largest p in [0, n) with base[p] <= x (base ascending, base[0] = 0)
@@ -783,10 +784,16 @@ __device__ __forceinline__ void list_write(const Prob &pr, const TileSmem<TY, TZ
             gk = z0 + e / (TILE_X * TY);
         }
         const int64_t idx = (int64_t)gk * plane + (int64_t)gj * g.nx + gi;
-        if ((long long)pos < pr.list_cap)
-            pr.list[pos] = make_uint2((uint32_t)idx, (uint32_t)key_fid(S.key[e]));
-        else
+        if ((long long)pos < pr.list_cap) {
+            const unsigned long long key = S.key[e];
+            pr.list[pos] = make_uint2((uint32_t)idx, (uint32_t)key_fid(key));
+            if (pr.list_dist) {
+                const float d = __uint_as_float((unsigned)(key >> 32));
+                pr.list_dist[pos] = (key & 1ull) ? -d : d;
+            }
+        } else {
             overflow = true;
+        }
         pos++;
     }
 }
@@ -856,6 +863,7 @@ __device__ __forceinline__ void fill_chunk(const Prob *P, const long long *tile_
             winner = P[p].winner;
             vec = P[p].vec;
         }
+        if (!dist) continue;  // a sparse problem: no dense field
         const uint32_t tu = (uint32_t)(tile - tb_lo), r1 = dtx.div(tu), tz = dty.div(r1);
         const int x0 = (int)(tu - r1 * (uint32_t)ntx) * TILE_X, y0 = (int)(r1 - tz * (uint32_t)nty) * TY,
                   z0 = (int)tz * TZ;
@@ -896,7 +904,7 @@ template <int TY, int TZ, bool LIST>
 __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *tile_base, int n, Outputs o,
                                                 int64_t n_tiles, const int32_t *band_list,
                                                 const int32_t *empty_list, const uint32_t *n_band_ptr,
-                                                unsigned long long *ticket) {
+                                                unsigned long long *ticket, int dense) {
     constexpr int TP = TILE_X * TY * TZ;
     extern __shared__ __align__(16) unsigned char tile_smem[];
     TileSmem<TY, TZ> &S = *reinterpret_cast<TileSmem<TY, TZ> *>(tile_smem);
@@ -906,7 +914,7 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
     unsigned cand = 0, band = 0, rows = 0, hits = 0, pairs = 0;
     bool overflow = false, list_ovf = false;
     const int64_t n_band = *n_band_ptr, n_empty = n_tiles - n_band;
-    const int64_t n_chunks = (n_empty + FILL_CHUNK - 1) / FILL_CHUNK;
+    const int64_t n_chunks = dense ? (n_empty + FILL_CHUNK - 1) / FILL_CHUNK : 0;  // no field: no +inf fill
     for (;;) {
         if (threadIdx.x == 0) {
             const bool filler = blockIdx.x >= gridDim.x / 2;
@@ -982,7 +990,7 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
                             emask |= ((unsigned)e0 | (unsigned)e1 << 1 | (unsigned)e2 << 2 | (unsigned)e3 << 3) << sh;
                         }
                     }
-                    __stcs(reinterpret_cast<float4 *>(dist + idx), v);
+                    if (dist) __stcs(reinterpret_cast<float4 *>(dist + idx), v);
                     if (winner) __stcs(reinterpret_cast<int4 *>(winner + idx), wv);
                 }
             } else {
@@ -995,7 +1003,7 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
                     bool en = false;
                     const float val = is_band ? decode_key(S.key[e], g, o, idx, p, wid, band, overflow, en) : INFINITY;
                     if (list && en) emask |= 1u << ((e - (int)threadIdx.x) / NT);
-                    __stcs(dist + idx, val);
+                    if (dist) __stcs(dist + idx, val);
                     if (winner) __stcs(winner + idx, wid);
                 }
             }
@@ -1301,13 +1309,17 @@ __global__ void k_patch(const Prob *P, const long long *tile_base, Outputs o) {
                 val = (float)(s < 0.0 ? -d : d);
                 w = out_id;
             }
-            dist[idx] = val;
+            if (dist) dist[idx] = val;
             if (winner) winner[idx] = w;
             const Prob &pr = P[pe.prob];
             if (pr.list && w >= 0) {
                 const unsigned long long pos = atomicAdd(pr.list_count, 1ull);
-                if ((long long)pos < pr.list_cap) pr.list[pos] = make_uint2((uint32_t)idx, (uint32_t)w);
-                else atomicOr(&o.ctr->nb_status, ST_LIST_OVERFLOW);
+                if ((long long)pos < pr.list_cap) {
+                    pr.list[pos] = make_uint2((uint32_t)idx, (uint32_t)w);
+                    if (pr.list_dist) pr.list_dist[pos] = val;
+                } else {
+                    atomicOr(&o.ctr->nb_status, ST_LIST_OVERFLOW);
+                }
             }
         }
     }
@@ -1678,7 +1690,9 @@ static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *gr
     pl.ybase.assign(n + 1, 0);
     pl.pbase.assign(n + 1, 0);
     for (int p = 0; p < n; p++) {
-        if (!feats[p] || !out_dist[p]) return SDF_ERR_INVALID_ARG;
+        // the dense field may be left out only by a sparse forward (a list with its distances)
+        const bool sparse = lists && lists[p].list && lists[p].dist;
+        if (!feats[p] || (!out_dist[p] && !sparse) || (!out_dist[p] && fill)) return SDF_ERR_INVALID_ARG;
         Prob &pr = pl.probs[p];
         int st = make_grid(grids[p], band_w[p], shape, pr.g);
         if (st) return st;
@@ -1691,6 +1705,7 @@ static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *gr
         pr.list = nullptr;
         pr.list_count = nullptr;
         pr.list_cap = 0;
+        pr.list_dist = nullptr;
         if (lists && lists[p].list) {
             // entries hold 32-bit point indices; the paper's own schedule writes no list
             if (!lists[p].count || lists[p].cap < 0 || pl.cell_loop) return SDF_ERR_INVALID_ARG;
@@ -1698,6 +1713,7 @@ static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *gr
             pr.list = reinterpret_cast<uint2 *>(lists[p].list);
             pr.list_count = lists[p].count;
             pr.list_cap = lists[p].cap;
+            pr.list_dist = lists[p].dist;
         }
         if (feats[p]->T + feats[p]->E + feats[p]->V >= (int64_t(1) << 30)) return SDF_ERR_TOO_LARGE;  // key ids
         pl.fbase[p + 1] = pl.fbase[p] + feats[p]->T + feats[p]->E + feats[p]->V;
@@ -1778,6 +1794,7 @@ static int plan_reserve(Plan &pl, cudaStream_t s) {
 struct Scratch {  // device pointers used by one launch of the pipeline
     const Prob *probs;
     bool any_list = false;  // some problem writes a compact band list
+    bool any_dense = true;  // some problem writes a dense field (else the +inf fill is skipped)
     const long long *fbase, *tbase;
     uint32_t *cnt, *start;
     void *scan_tmp;
@@ -1802,7 +1819,11 @@ struct Scratch {  // device pointers used by one launch of the pipeline
 
 static Scratch plan_scratch(const Plan &pl) {
     Scratch sc;
-    for (const Prob &pr : pl.probs) sc.any_list |= pr.list != nullptr;
+    sc.any_dense = false;
+    for (const Prob &pr : pl.probs) {
+        sc.any_list |= pr.list != nullptr;
+        sc.any_dense |= pr.dist != nullptr || pr.winner != nullptr;
+    }
     const char *t = pl.tables.as<char>();
     sc.probs = reinterpret_cast<const Prob *>(t);
     sc.fbase = reinterpret_cast<const long long *>(t + sizeof(Prob) * pl.n);
@@ -1882,11 +1903,13 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
     if (sc.any_list) {
         const int64_t ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm<TY, TZ, true>() * num_sms());
         k_tile<TY, TZ, true><<<(unsigned)ctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
-            sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket);
+            sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket,
+            sc.any_dense ? 1 : 0);
     } else {
         const int64_t ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm<TY, TZ, false>() * num_sms());
         k_tile<TY, TZ, false><<<(unsigned)ctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
-            sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket);
+            sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket,
+            sc.any_dense ? 1 : 0);
     }
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
@@ -2054,7 +2077,7 @@ int narrow_band_all(const sdf_features *feats, const sdf_grid *grids, const floa
                     const ListOut *lists) {
     if (!feats || !grids || !band_w || n < 1 || !out_dist) return SDF_ERR_INVALID_ARG;
     for (int p = 0; p < n; p++)
-        if (!feats[p] || !out_dist[p]) return SDF_ERR_INVALID_ARG;
+        if (!feats[p] || (!out_dist[p] && !(lists && lists[p].list && lists[p].dist))) return SDF_ERR_INVALID_ARG;
     const bool sync = !(flags & SDF_FLAG_NO_SYNC), timing = (flags & SDF_FLAG_TIMING) != 0;
     const bool fill = (flags & SDF_FLAG_FILL_SIGN) != 0, cell_loop = (flags & SDF_FLAG_CELL_LOOP) != 0;
     const int vmode = (flags & SDF_FLAG_VERTEX_CONE) ? VM_CONE : ((flags & SDF_FLAG_VERTEX_HEMISPHERE) ? VM_HEMISPHERE : VM_EXACT);
@@ -2107,6 +2130,19 @@ extern "C" int sdf_narrow_band_list(sdf_features f, const sdf_grid *grid, float 
     float *const dl[1] = {out_dist};
     int32_t *const wl[1] = {out_winner};
     const sdf::ListOut lo[1] = {{list, (long long)list_cap, list_count}};
+    return sdf::narrow_band_all(fl, grid, &band_w, 1, dl, wl, flags, reinterpret_cast<cudaStream_t>(stream), lo);
+}
+
+extern "C" int sdf_narrow_band_sparse(sdf_features f, const sdf_grid *grid, float band_w, sdf_band_entry *list,
+                                      float *list_dist, int64_t list_cap, unsigned long long *list_count,
+                                      uint32_t flags, void *stream) {
+    if (!f || !grid || !list || !list_dist || !list_count || list_cap < 0) return SDF_ERR_INVALID_ARG;
+    if (flags & (SDF_FLAG_CELL_LOOP | SDF_FLAG_FILL_SIGN)) return SDF_ERR_INVALID_ARG;
+    const sdf_features fl[1] = {f};
+    float *const dl[1] = {nullptr};
+    int32_t *const wl[1] = {nullptr};
+    sdf::ListOut lo[1] = {{list, (long long)list_cap, list_count}};
+    lo[0].dist = list_dist;
     return sdf::narrow_band_all(fl, grid, &band_w, 1, dl, wl, flags, reinterpret_cast<cudaStream_t>(stream), lo);
 }
 

@@ -88,6 +88,7 @@ struct ListOut {
     sdf_band_entry *list;
     long long cap;
     unsigned long long *count;
+    float *dist = nullptr;  // nullable: the signed distance of every entry (the sparse forward)
 };
 
 // the narrow band of n problems (sdf_narrow_band), with optional band lists (host array [n] or

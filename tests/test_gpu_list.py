@@ -11,6 +11,7 @@ import torch
 import meshgen
 import oracle
 import paper_1903_00353_gb300 as sdf
+from tests import parity
 
 pytestmark = pytest.mark.gpu
 
@@ -219,3 +220,40 @@ def test_batched_lists_equal_the_single_problem_fields_and_bands():
         assert len(bl) == band.numel() > 100
         assert torch.equal(torch.sort(idx).values, band)
         assert torch.equal(bl.winners().long(), w_ref.view(-1)[idx].long())
+
+
+@pytest.mark.parametrize("case", ["c1_64", "torus_ragged", "c2_512", "c4_1024"])
+def test_sparse_forward_matches_dense_and_oracle(case):
+    """The sparse forward (band list with distances, no dense field): the same band points, winners
+    and values as the dense forward, and the oracle's values at sampled list points."""
+    if case == "c1_64":
+        soup, grid, w = meshgen.config_soup(1), sdf.Grid.cube(64), 3 / 64
+    elif case == "torus_ragged":
+        soup = meshgen.torus(nu=60, nv=24, seed=3).soup(seed=2)
+        h = float(np.float32(0.0123))
+        grid, w = sdf.Grid(90, 77, 45, (0.0, 0.0, float(np.float32(0.23))), h), float(np.float32(3 * h))
+    else:
+        idx = 2 if case == "c2_512" else 4
+        N, cells = meshgen.CONFIG_GRID[idx]
+        soup, grid, w = meshgen.config_soup(idx), sdf.Grid.cube(N), cells / N
+    feats = sdf.sdf_build_features(torch.from_numpy(soup).cuda())
+    bl = sdf.sdf_narrow_band_sparse(feats, grid, w)
+    n = len(bl)
+    idx_s = bl.indices().long()
+    order = torch.argsort(idx_s)
+    idx_s, win_s, d_s = idx_s[order], bl.winners()[order], bl.dist[:n][order]
+    dense, win = sdf.sdf_narrow_band(feats, grid, w, winner=True)
+    band = torch.nonzero(torch.isfinite(dense.view(-1))).view(-1)
+    assert n == band.numel()
+    assert torch.equal(idx_s, band)
+    assert torch.equal(d_s, dense.view(-1)[band])
+    assert torch.equal(win_s, win.view(-1)[band])
+    del dense, win
+    torch.cuda.empty_cache()
+    # oracle at up to 20000 listed points
+    rng = np.random.default_rng(5)
+    pick = rng.choice(n, size=min(n, 20000), replace=False)
+    ii = idx_s.cpu().numpy()[pick]
+    om = oracle.OracleMesh.from_soup(soup)
+    d_or, _, _ = om.band_points((grid.nx, grid.ny, grid.nz), grid.origin, grid.h, w + 2 * grid.h, ii)
+    parity.assert_parity(parity.compare(d_s.cpu().numpy()[pick], d_or, w, grid.h))
