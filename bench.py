@@ -15,9 +15,10 @@ value = band points produced per second (all ranks), device-timed with CUDA even
 e2e = the same metric through the public API with host buffers (pinned H2D of the
 soup, D2H of the SDF and the vertex gradient inside the timed region).
 --impl reference times the FP64 CPU oracle on a bounded slab of the same workload.
-Multi-GPU (torchrun): by default every rank runs its own replica of the workload (independent
-problems, no data-path collective, weak scaling); --shard slabs gives each rank one z-slab of the
-grid instead, with the vertex gradient summed over the ranks by one all-reduce (strong scaling).
+Multi-GPU (torchrun): by default each rank evaluates one z-slab of the grid (the whole mesh's
+features, the slab's layers) with the vertex gradient summed over the ranks by one all-reduce
+(strong scaling); --shard replicas runs an independent copy of the workload per rank instead (weak
+scaling, no data-path collective).
 Timing is the max over ranks.
 """
 from __future__ import annotations
@@ -61,6 +62,11 @@ WORKLOADS = {
                        "sum_band (d - d_ellipsoid(0.35, 0.25, 0.2))^2 (position update, forward with the "
                        "compact band list, loss and vertex gradient fused in one pass over the list)"),
 }
+WORKLOADS["cluster"] = dict(
+    index=None, adjoint=False, winner=False, cluster=True,
+    desc="very uneven triangle sizes: a coarse icosphere (320 triangles, r=0.3) and a separate dense "
+         "cluster (icosphere nu=60, 72,000 triangles of radius 2e-4); build time against a uniform "
+         "icosphere of 72,000 triangles, and the forward on 256^3, band 3h")
 FIT_LR = 1e-4  # fixed learning rate of the shape-fitting workload
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_tile launch on a workload at
@@ -470,6 +476,58 @@ def run_fit(args, wl, sdf, soup_np, soup, grid, w, N, dev, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_cluster(args, wl, sdf, local, world, rank):
+    """Build time of a mesh with a dense cluster of tiny triangles (many distinct vertices under one
+    spatial weld key) against a uniform mesh of about the same size, and its forward."""
+    import torch
+    import meshgen
+    dev = torch.device("cuda", local)
+    soups = {"cluster": meshgen.dense_cluster().soup(seed=353_901),
+             "uniform": meshgen.icosphere(60, radius=0.3).soup(seed=353_902)}
+    res = {}
+    for name, s_np in soups.items():
+        soup = torch.from_numpy(s_np).to(dev)
+        for _ in range(args.warmup):
+            sdf.sdf_build_features(soup).destroy()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f = sdf.sdf_build_features(soup)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            f.destroy()
+        res[name] = {"triangles": int(s_np.shape[0]), "build_ms_median": float(np.median(ms)),
+                     "build_ms_min": float(min(ms))}
+    # the cluster mesh's forward on 256^3, band 3h
+    N = 256
+    grid, w = sdf.Grid.cube(N), 3.0 / N
+    f = sdf.sdf_build_features(torch.from_numpy(soups["cluster"]).to(dev))
+    out = torch.empty(grid.shape, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        sdf.sdf_narrow_band(f, grid, w, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sdf.sdf_narrow_band(f, grid, w, out=out)
+    e1.record()
+    e1.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / args.steps
+    band = int(torch.isfinite(out).sum())
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": band / (fwd_ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": fwd_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "grid": [N, N, N], "band_w": w, "band_points": band},
+            "build": res, "build_cluster_over_uniform": res["cluster"]["build_ms_median"] / res["uniform"]["build_ms_median"],
+            "gpu_launches": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args, wl, sdf, local, world, rank):
     """Batch workload: all 64 problems in one launch sequence (one persistent tile kernel) captured
     in a CUDA graph; one step = one replay.  Also times the plain path (64 single-problem calls)."""
@@ -642,9 +700,10 @@ def main():
     ap.add_argument("--schedule", default="tile", choices=["tile", "cell"],
                     help="forward schedule: the binned tile kernel, or the paper's thread-per-region cell loop "
                          "(schedule comparison)")
-    ap.add_argument("--shard", default="replicas", choices=["replicas", "slabs"],
-                    help="N > 1: every rank runs the whole workload (replicas, weak scaling) or one z-slab of "
-                         "its grid with the vertex gradient summed over the ranks (slabs, strong scaling)")
+    ap.add_argument("--shard", default="slabs", choices=["replicas", "slabs"],
+                    help="N > 1: one z-slab of the grid per rank with the vertex gradient summed over the ranks "
+                         "(slabs, strong scaling: the partitioning of the method, the default) or every rank "
+                         "running the whole workload (replicas, weak scaling)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.warmup < 3:
@@ -671,6 +730,11 @@ def main():
     sdf.load_library()
     if wl.get("batch"):
         run_batch(args, wl, sdf, local, world, rank)
+        if world > 1:
+            tdist.destroy_process_group()
+        return
+    if wl.get("cluster"):
+        run_cluster(args, wl, sdf, local, world, rank)
         if world > 1:
             tdist.destroy_process_group()
         return

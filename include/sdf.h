@@ -26,8 +26,8 @@
  *   - Calls on one handle must not overlap in time (they share its scratch).
  *
  * Grid layout (Section 10, a row-major 1D float array): point (i,j,k) sits at
- * origin + ((i+1/2) h, (j+1/2) h, (k+1/2) h) and is stored at
- * i + nx*(j + ny*k) (x fastest).
+ * origin + ((i+1/2) h, (j+1/2) h, (k0+k+1/2) h) and is stored at
+ * i + nx*(j + ny*k) (x fastest); k0 = 0 except for a z-slab of a larger grid.
  *
  * Feature ids (Section 2: faces, edges and vertices are the features):
  *   face f in [0, T); edge e -> T + e; vertex v -> T + E + v,
@@ -62,11 +62,15 @@ typedef enum sdf_status {
                                  has points; its count holds the length needed             */
 } sdf_status;
 
-/* Grid description (host struct, passed by pointer). */
+/* Grid description (host struct, passed by pointer).  k0 places the grid inside a larger one
+ * along z (a z-slab of it): point (i,j,k) sits at origin + ((i+1/2) h, (j+1/2) h, (k0+k+1/2) h) and
+ * is stored at i + nx*(j + ny*k).  A slab with the same origin, h and a first layer k0 that is a
+ * multiple of 8 gives bitwise the values of those layers of the whole grid, whatever h is. */
 typedef struct sdf_grid {
     int32_t nx, ny, nz;  /* points per axis, each >= 1                        */
-    float origin[3];     /* lower corner of the grid box                      */
+    float origin[3];     /* lower corner of the (whole) grid box              */
     float h;             /* cell size > 0                                     */
+    int32_t k0;          /* index of the first z layer, >= 0 (0: the whole grid) */
 } sdf_grid;
 
 /* Opaque, library-owned feature set of one mesh. */
@@ -87,7 +91,7 @@ typedef struct sdf_features_s *sdf_features;
 #define SDF_FLAG_FILL_SIGN 0x10u     /* sdf_narrow_band / sdf_batch_create: points outside the
                                         band get -inf inside the surface and +inf outside
                                         (the sign fill beyond the band, Section 11.3);
-                                        requires w > h on every grid                         */
+                                        requires w > h and k0 = 0 on every grid              */
 #define SDF_FLAG_CELL_LOOP 0x20u     /* sdf_narrow_band / sdf_batch_create: run the paper's own
                                         schedule (Section 9: one thread per characteristic
                                         region walking its box, a global 64-bit atomicMin per

@@ -316,6 +316,19 @@ def box(center=(0.5, 0.5, 0.5), half=(0.2, 0.15, 0.1), subdiv=1, axes=None) -> M
     return Mesh(v, tri.astype(np.int32))
 
 
+def dense_cluster(freq_big: int = 4, freq_small: int = 60, radius_small: float = 2e-4,
+                  center_small=(0.85, 0.85, 0.85)) -> Mesh:
+    """Very uneven triangle sizes in one closed mesh of two components: a coarse icosphere of large
+    triangles (radius 0.3 at the domain centre) and a separate tiny, finely subdivided icosphere (a
+    dense cluster: 20 freq_small^2 triangles within a few micro-units, so that tens of thousands of
+    distinct vertices share a few cells of any coarse spatial hash)."""
+    a = icosphere(freq_big, radius=0.3)
+    b = icosphere(freq_small, radius=radius_small, center=center_small)
+    v = np.concatenate([a.vertices, b.vertices])
+    t = np.concatenate([a.triangles, b.triangles + a.vertices.shape[0]])
+    return Mesh(v, t.astype(np.int32))
+
+
 def lattice_plate(n_grid: int, half_thickness: float, offset: float, half_extent: float = 0.25,
                   subdiv: int = 24) -> Mesh:
     """A thin plate (a box) whose mid-plane is a lattice plane of the n_grid^3 cell-centre grid on

@@ -48,7 +48,7 @@ class SDFError(RuntimeError):
 
 class _CGrid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
-                ("origin", ctypes.c_float * 3), ("h", ctypes.c_float)]
+                ("origin", ctypes.c_float * 3), ("h", ctypes.c_float), ("k0", ctypes.c_int32)]
 
 
 _lib = None
@@ -162,12 +162,14 @@ def _grad_vertices(gv: torch.Tensor | None, n_vert: int) -> tuple[torch.Tensor, 
 
 @dataclass(frozen=True)
 class Grid:
-    """Cell-centred grid: point (i,j,k) at origin + (i+1/2, j+1/2, k+1/2) h, stored x fastest."""
+    """Cell-centred grid: point (i,j,k) at origin + (i+1/2, j+1/2, k0+k+1/2) h, stored x fastest
+    (k0 > 0: the z-slab of layers k0 .. k0+nz-1 of a larger grid with the same origin and h)."""
     nx: int
     ny: int
     nz: int
     origin: tuple = (0.0, 0.0, 0.0)
     h: float = 1.0
+    k0: int = 0
 
     @staticmethod
     def cube(n: int, lo: float = 0.0, hi: float = 1.0) -> "Grid":
@@ -179,6 +181,7 @@ class Grid:
         for k in range(3):
             g.origin[k] = float(self.origin[k])
         g.h = float(self.h)
+        g.k0 = int(self.k0)
         return g
 
     @property

@@ -23,6 +23,7 @@ constexpr unsigned FULL = 0xffffffffu;
 struct AdjArgs {
     int T, E, V;
     int nx, ny, nz;
+    int kofs;  // index of the first z layer within the whole grid
     FastDiv div_nx, div_ny;
     float ox, oy, oz, h;
     const float *grad;
@@ -48,7 +49,7 @@ __device__ __forceinline__ float rel_coord(float o, float h, int i, float x) {
     return fmaf((float)i + 0.5f, h, hi) + lo;
 }
 __device__ __forceinline__ float3 rel_point(const AdjArgs &a, int i, int j, int k, float3 x) {
-    return make_float3(rel_coord(a.ox, a.h, i, x.x), rel_coord(a.oy, a.h, j, x.y), rel_coord(a.oz, a.h, k, x.z));
+    return make_float3(rel_coord(a.ox, a.h, i, x.x), rel_coord(a.oy, a.h, j, x.y), rel_coord(a.oz, a.h, k + a.kofs, x.z));
 }
 
 __device__ double3 face_normal64(const AdjArgs &a, int f) {
@@ -64,7 +65,7 @@ __device__ double3 face_normal64(const AdjArgs &a, int f) {
 __device__ float sign64_edge(const AdjArgs &a, int e, int i, int j, int k) {
     const int4 q = a.edge_vf[e];
     const double3 p = make_double3((double)a.ox + (i + 0.5) * (double)a.h, (double)a.oy + (j + 0.5) * (double)a.h,
-                                   (double)a.oz + (k + 0.5) * (double)a.h);
+                                   (double)a.oz + (k + a.kofs + 0.5) * (double)a.h);
     const double3 A = d3(load_vpos(a.vpos, q.x)), B = d3(load_vpos(a.vpos, q.y));
     const double3 ab = B - A, ap = p - A;
     double t = ddot3(ap, ab) / ddot3(ab, ab);
@@ -74,7 +75,7 @@ __device__ float sign64_edge(const AdjArgs &a, int e, int i, int j, int k) {
 }
 __device__ float sign64_vertex(const AdjArgs &a, int v, int i, int j, int k) {
     const double3 p = make_double3((double)a.ox + (i + 0.5) * (double)a.h, (double)a.oy + (j + 0.5) * (double)a.h,
-                                   (double)a.oz + (k + 0.5) * (double)a.h);
+                                   (double)a.oz + (k + a.kofs + 0.5) * (double)a.h);
     const double3 P = d3(load_vpos(a.vpos, v));
     double3 N = make_double3(0, 0, 0);
     for (int c = a.vert_start[v]; c < a.vert_start[v + 1]; c++) {
@@ -388,6 +389,7 @@ AdjArgs make_adj_args(const sdf_features_s *f, const sdf_grid &gr) {
     AdjArgs a;
     a.T = (int)f->T; a.E = (int)f->E; a.V = (int)f->V;
     a.nx = gr.nx; a.ny = gr.ny; a.nz = gr.nz;
+    a.kofs = gr.k0;
     a.div_nx = FastDiv((uint32_t)gr.nx);
     a.div_ny = FastDiv((uint32_t)gr.ny);
     a.ox = gr.origin[0]; a.oy = gr.origin[1]; a.oz = gr.origin[2]; a.h = gr.h;
@@ -407,7 +409,7 @@ int list_adjoint(sdf_features_s *f, const sdf_grid *grid, const sdf_band_entry *
                  uint32_t flags, cudaStream_t s) {
     if (!f || !grid || !list || !list_count || list_cap < 0 || !grad_vertices) return SDF_ERR_INVALID_ARG;
     const sdf_grid &gr = *grid;
-    if (gr.nx < 1 || gr.ny < 1 || gr.nz < 1 || !(gr.h > 0.f)) return SDF_ERR_INVALID_ARG;
+    if (gr.nx < 1 || gr.ny < 1 || gr.nz < 1 || !(gr.h > 0.f) || gr.k0 < 0) return SDF_ERR_INVALID_ARG;
     if ((long long)gr.nx * gr.ny * gr.nz > (long long)UINT32_MAX) return SDF_ERR_TOO_LARGE;
     AdjArgs a = make_adj_args(f, gr);
     a.grad = grad_dist;
@@ -479,7 +481,7 @@ extern "C" int sdf_narrow_band_backward(const sdf_features *feats, const sdf_gri
         sdf_features_s *f = feats[p];
         const sdf_grid &gr = grids[p];
         if (!f || !grad_dist[p] || !grad_vertices[p]) return SDF_ERR_INVALID_ARG;
-        if (gr.nx < 1 || gr.ny < 1 || gr.nz < 1 || !(gr.h > 0.f)) return SDF_ERR_INVALID_ARG;
+        if (gr.nx < 1 || gr.ny < 1 || gr.nz < 1 || !(gr.h > 0.f) || gr.k0 < 0) return SDF_ERR_INVALID_ARG;
         const int64_t npts = (int64_t)gr.nx * gr.ny * gr.nz;
         const int32_t *win = winner ? winner[p] : nullptr;
         if (!win) {  // recompute the winners with a forward pass into library scratch

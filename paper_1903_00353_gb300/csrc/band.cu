@@ -56,6 +56,7 @@ enum { FACE = 0, EDGE = 1, VERT = 2 };
 
 struct GridP {
     int nx, ny, nz;
+    int kofs;    // index of the first z layer within the whole grid (sdf_grid::k0)
     int ntx, nty, ntz;
     FastDiv div_ntx, div_nty, div_nx, div_ny;  // tile and grid index decomposition
     float ox, oy, oz, h, inv_h;
@@ -174,7 +175,8 @@ __device__ __forceinline__ bool to_index_box(float lx, float ly, float lz, float
     const float sl = 1.f / 4096.f;  // index slack against rounding of the conversion
     float a0 = fmaxf((lx - g.ox) * g.inv_h - 0.5f - sl, -1.f), a1 = fminf((hx - g.ox) * g.inv_h - 0.5f + sl, (float)g.nx);
     float b0 = fmaxf((ly - g.oy) * g.inv_h - 0.5f - sl, -1.f), b1 = fminf((hy - g.oy) * g.inv_h - 0.5f + sl, (float)g.ny);
-    float c0 = fmaxf((lz - g.oz) * g.inv_h - 0.5f - sl, -1.f), c1 = fminf((hz - g.oz) * g.inv_h - 0.5f + sl, (float)g.nz);
+    const float kz = (float)g.kofs;
+    float c0 = fmaxf((lz - g.oz) * g.inv_h - 0.5f - kz - sl, -1.f), c1 = fminf((hz - g.oz) * g.inv_h - 0.5f - kz + sl, (float)g.nz);
     i0 = max((int)ceilf(a0), 0); i1 = min((int)floorf(a1), g.nx - 1);
     j0 = max((int)ceilf(b0), 0); j1 = min((int)floorf(b1), g.ny - 1);
     k0 = max((int)ceilf(c0), 0); k1 = min((int)floorf(c1), g.nz - 1);
@@ -371,7 +373,7 @@ template <int TYPE>
 __device__ __forceinline__ float eval_point(const Feat &F, const GridP &g, int id, int i, int j, int k, bool &neg,
                                             bool &unc) {
     const float3 p = make_float3(fmaf((float)i + 0.5f, g.h, g.ox), fmaf((float)j + 0.5f, g.h, g.oy),
-                                 fmaf((float)k + 0.5f, g.h, g.oz));
+                                 fmaf((float)(k + g.kofs) + 0.5f, g.h, g.oz));
     if (TYPE == FACE) {
         const float4 *r = F.face_rec + 4 * id;
         float4 n = __ldg(r), s1 = __ldg(r + 1), s2 = __ldg(r + 2), s3 = __ldg(r + 3);
@@ -563,9 +565,11 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int2 *pai
             // slab planes bound the distance)
             float4 q0v = make_float4(0.f, 0.f, 0.f, 0.f), q1v = make_float4(0.f, 0.f, 0.f, Q_NONE);
             if (nrows > 0) {
+                // whole-grid indices of the box's first row (z indices carry the slab's first layer)
+                const int la_g = la + (ax == 2 ? g.kofs : 0), lc_g = lc + (cx == 2 ? g.kofs : 0);
                 const float pb0 = fmaf((float)lb + 0.5f, g.h, comp3(org, bx));
-                const float pc0 = fmaf((float)lc + 0.5f, g.h, comp3(org, cx));
-                const float K = comp3(org, ax) * g.inv_h + 0.5f + (float)la;  // j = (p_a - o_a)/h - 1/2 - lo_a
+                const float pc0 = fmaf((float)lc_g + 0.5f, g.h, comp3(org, cx));
+                const float K = comp3(org, ax) * g.inv_h + 0.5f + (float)la_g;  // j = (p_a - o_a)/h - 1/2 - lo_a
                 float4 *E = S.coef[t];  // written directly to shared memory
                 if (type == FACE) {
                     const float4 *r = F.face_rec + 4 * id;
@@ -587,7 +591,7 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int2 *pai
                     // points the merge would reject (d >= W)
                     const float3 av = f3(a), tv = f3(tt);
                     const float Rs = (g.W + g.eps) * g.inv_h + 1.f / 64.f;
-                    q0v = make_float4((comp3(org, ax) - comp3(av, ax)) * g.inv_h + 0.5f + (float)la,
+                    q0v = make_float4((comp3(org, ax) - comp3(av, ax)) * g.inv_h + 0.5f + (float)la_g,
                                       (pb0 - comp3(av, bx)) * g.inv_h, (pc0 - comp3(av, cx)) * g.inv_h, Rs * Rs);
                     q1v = make_float4(comp3(tv, ax), comp3(tv, bx), comp3(tv, cx), Q_EDGE);
                 } else {
@@ -597,7 +601,7 @@ __device__ void process_band_tile(const Feat &F, const GridP &g, const int2 *pai
                         add_coef(E, nl, nu, __ldg(F.vert_plane + s0 + k), ax, bx, cx, pb0, pc0, K, g);
                     const float3 vv = f3(v);
                     const float Rh = (g.W + g.eps) * g.inv_h;
-                    q0v = make_float4((comp3(vv, ax) - comp3(org, ax)) * g.inv_h - 0.5f - (float)la,
+                    q0v = make_float4((comp3(vv, ax) - comp3(org, ax)) * g.inv_h - 0.5f - (float)la_g,
                                       (pb0 - comp3(vv, bx)) * g.inv_h, (pc0 - comp3(vv, cx)) * g.inv_h, Rh * Rh);
                     q1v.w = Q_VERT;
                 }
@@ -1187,7 +1191,7 @@ __global__ void k_patch(const Prob *P, const long long *tile_base, Outputs o) {
         }
         const double h = g.h;
         const double3 p = make_double3((double)g.ox + (gi + 0.5) * h, (double)g.oy + (gj + 0.5) * h,
-                                       (double)g.oz + (gk + 0.5) * h);
+                                       (double)g.oz + (gk + g.kofs + 0.5) * h);
         Cand64 best;
         best.d2 = INFINITY;
         best.id = 0x7fffffff;
@@ -1416,7 +1420,7 @@ __device__ __forceinline__ unsigned walk_region(const Feat &F, const GridP &g, i
         for (int j = j0; j <= j1; j++)
             for (int i = i0; i <= i1; i++) {
                 const float3 p = make_float3(fmaf((float)i + 0.5f, g.h, g.ox), fmaf((float)j + 0.5f, g.h, g.oy),
-                                             fmaf((float)k + 0.5f, g.h, g.oz));
+                                             fmaf((float)(k + g.kofs) + 0.5f, g.h, g.oz));
                 if (TYPE == VERT && F.vmode != VM_EXACT) {
                     const float3 u = p - vv;
                     const float R = g.W + g.eps, lu2 = dot3(u, u);
@@ -1482,12 +1486,14 @@ static const int SHAPE_TY[N_SHAPES] = {8, 4, 16};
 static const int SHAPE_TZ[N_SHAPES] = {8, 4, 8};
 
 static int make_grid(const sdf_grid &gr, float w, int shape, GridP &g) {
-    if (gr.nx < 1 || gr.ny < 1 || gr.nz < 1 || !(gr.h > 0.f) || !isfinite(gr.h) || !(w > 0.f) || !isfinite(w))
+    if (gr.nx < 1 || gr.ny < 1 || gr.nz < 1 || !(gr.h > 0.f) || !isfinite(gr.h) || !(w > 0.f) || !isfinite(w) ||
+        gr.k0 < 0 || (int64_t)gr.k0 + gr.nz >= (int64_t(1) << 24))
         return SDF_ERR_INVALID_ARG;
     for (int j = 0; j < 3; j++)
         if (!isfinite(gr.origin[j])) return SDF_ERR_INVALID_ARG;
     if ((int64_t)gr.nx * gr.ny >= (int64_t(1) << 40)) return SDF_ERR_TOO_LARGE;
     g.nx = gr.nx; g.ny = gr.ny; g.nz = gr.nz;
+    g.kofs = gr.k0;
     g.ntx = (gr.nx + TILE_X - 1) / TILE_X;
     g.nty = (gr.ny + SHAPE_TY[shape] - 1) / SHAPE_TY[shape];
     g.ntz = (gr.nz + SHAPE_TZ[shape] - 1) / SHAPE_TZ[shape];
@@ -1502,9 +1508,9 @@ static int make_grid(const sdf_grid &gr, float w, int shape, GridP &g) {
     // coordinate magnitude M of the problem: FP32 errors of dot products scale with it
     double M = 0.0;
     for (int j = 0; j < 3; j++) {
-        int n = j == 0 ? gr.nx : (j == 1 ? gr.ny : gr.nz);
-        M = fmax(M, fabs((double)gr.origin[j]));
-        M = fmax(M, fabs((double)gr.origin[j] + (double)n * gr.h));
+        const int lo = j == 2 ? gr.k0 : 0, n = j == 0 ? gr.nx : (j == 1 ? gr.ny : gr.nz);
+        M = fmax(M, fabs((double)gr.origin[j] + (double)lo * gr.h));
+        M = fmax(M, fabs((double)gr.origin[j] + (double)(lo + n) * gr.h));
     }
     M = fmax(M, (double)w);
     g.w = w;
@@ -1718,8 +1724,8 @@ static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *gr
         if (feats[p]->T + feats[p]->E + feats[p]->V >= (int64_t(1) << 30)) return SDF_ERR_TOO_LARGE;  // key ids
         pl.fbase[p + 1] = pl.fbase[p] + feats[p]->T + feats[p]->E + feats[p]->V;
         pl.tbase[p + 1] = pl.tbase[p] + (long long)pr.g.ntx * pr.g.nty * pr.g.ntz;
-        // the fill's argument (rows outside the band run uncrossed) needs w > h
-        if (fill && !(band_w[p] > grids[p].h)) return SDF_ERR_INVALID_ARG;
+        // the fill's argument (rows outside the band run uncrossed) needs w > h, and the whole grid
+        if (fill && (!(band_w[p] > grids[p].h) || grids[p].k0 != 0)) return SDF_ERR_INVALID_ARG;
         pl.fprobs[p] = FillProb{out_dist[p], grids[p].nx, grids[p].ny, grids[p].nz};
         pl.rbase[p + 1] = pl.rbase[p] + (long long)grids[p].ny * grids[p].nz;
         pl.zbase[p + 1] = pl.zbase[p] + grids[p].nz;

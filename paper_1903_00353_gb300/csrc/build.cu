@@ -126,9 +126,14 @@ __device__ __forceinline__ bool less_xyz(const float *soup, uint32_t a, uint32_t
     return a < b;
 }
 
-// one thread per run of equal keys: if the run mixes distinct coordinates (hash collision),
-// insertion-sort it by (coordinate bits, soup index) so equal vertices become contiguous
-__global__ void k_weld_fix(const uint64_t *keys, uint32_t *vals, const float *soup, int64_t n) {
+// One thread per run of equal keys.  A run that mixes distinct coordinates (a hash collision, or
+// distinct vertices in one Morton cell, as in a dense cluster of small triangles) is re-ordered by
+// (coordinate bits, soup index) so that equal vertices become contiguous: runs of up to
+// WELD_SHORT entries by the thread itself (insertion sort), longer ones are listed for
+// k_weld_sort_runs, one block per run.
+constexpr int WELD_SHORT = 32, WELD_BLOCK_MAX = 2048;
+__global__ void k_weld_fix(const uint64_t *keys, uint32_t *vals, const float *soup, int64_t n, int2 *long_runs,
+                           int64_t long_cap, unsigned *n_long) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n || (i > 0 && keys[i] == keys[i - 1])) return;
     int64_t e = i + 1;
@@ -138,11 +143,62 @@ __global__ void k_weld_fix(const uint64_t *keys, uint32_t *vals, const float *so
         e++;
     }
     if (!mixed) return;
-    for (int64_t a = i + 1; a < e; a++) {
+    if (e - i > WELD_SHORT && e - i <= WELD_BLOCK_MAX) {
+        const unsigned slot = atomicAdd(n_long, 1u);
+        if ((int64_t)slot < long_cap) {
+            long_runs[slot] = make_int2((int)i, (int)(e - i));
+            return;
+        }
+    }
+    for (int64_t a = i + 1; a < e; a++) {  // short runs (and runs beyond the block sort's size)
         uint32_t v = vals[a];
         int64_t b = a - 1;
         while (b >= i && less_xyz(soup, v, vals[b])) { vals[b + 1] = vals[b]; b--; }
         vals[b + 1] = v;
+    }
+}
+
+// The listed long mixed runs, one block per run (grid-stride over the device-side count): the
+// run's (x, y, z bits, soup index) records are sorted in shared memory by a bitonic network over
+// the next power of two (padding sorts last), then written back.  Any total order of the
+// coordinate bits makes equal vertices contiguous; -0 is read as +0.
+__global__ void __launch_bounds__(256) k_weld_sort_runs(const int2 *long_runs, const unsigned *n_long, int64_t long_cap,
+                                                        uint32_t *vals, const float *soup) {
+    __shared__ uint4 rec[WELD_BLOCK_MAX];
+    const int64_t nl = min((int64_t)*n_long, long_cap);
+    for (int64_t r = blockIdx.x; r < nl; r += gridDim.x) {
+        const int2 run = long_runs[r];
+        int m = 1;
+        while (m < run.y) m <<= 1;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            if (t < run.y) {
+                const uint32_t v = vals[run.x + t];
+                rec[t] = make_uint4(__float_as_uint(canon_zero(soup[3 * (int64_t)v])),
+                                    __float_as_uint(canon_zero(soup[3 * (int64_t)v + 1])),
+                                    __float_as_uint(canon_zero(soup[3 * (int64_t)v + 2])), v);
+            } else {
+                rec[t] = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+            }
+        }
+        __syncthreads();
+        for (int k = 2; k <= m; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                    const int u = t ^ j;
+                    if (u > t) {
+                        const uint4 a = rec[t], b = rec[u];
+                        const bool gt = a.x != b.x ? a.x > b.x : (a.y != b.y ? a.y > b.y : (a.z != b.z ? a.z > b.z : a.w > b.w));
+                        if (gt == ((t & k) == 0)) {  // ascending where t & k == 0
+                            rec[t] = b;
+                            rec[u] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int t = threadIdx.x; t < run.y; t += blockDim.x) vals[run.x + t] = rec[t].w;
+        __syncthreads();
     }
 }
 
@@ -643,8 +699,11 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     f->flags = flags;
     DevBuf tmp;
     // scratch: keys, vals (+ alternates), heads/scan, sort and scan temporaries, bounds
+    const int64_t long_cap = n / (WELD_SHORT + 1) + 1;  // long mixed runs (each > WELD_SHORT entries)
     size_t off_keys = 0, off_kalt = off_keys + 8 * n, off_vals = off_kalt + 8 * n, off_valt = off_vals + 4 * n,
-           off_head = off_valt + 4 * n, off_bb = off_head + 4 * (n + 1) + 64, off_rtmp = off_bb + 64;
+           off_head = off_valt + 4 * n, off_bb = off_head + 4 * (n + 1) + 64,
+           off_long = (off_bb + 64 + 15) & ~(size_t)15,               // int2: 8-byte aligned (16 here)
+           off_rtmp = (off_long + 8 * long_cap + 64 + 15) & ~(size_t)15;
     size_t need = off_rtmp + radix_tmp_bytes(n) + scan_tmp_bytes(n + 1) + 1024;
     B_TRY(tmp.reserve(need, s));
     char *base = tmp.as<char>();
@@ -652,12 +711,15 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     uint32_t *vals = reinterpret_cast<uint32_t *>(base + off_vals), *valt = reinterpret_cast<uint32_t *>(base + off_valt);
     uint32_t *head = reinterpret_cast<uint32_t *>(base + off_head);
     float *bb = reinterpret_cast<float *>(base + off_bb);
+    unsigned *n_long = reinterpret_cast<unsigned *>(base + off_bb + 32);
+    int2 *long_runs = reinterpret_cast<int2 *>(base + off_long);
     void *rtmp = base + off_rtmp;
 
     B_TRY(dalloc_s(&f->ctr, 1, s));
     B_TRY(cudaMemsetAsync(f->ctr, 0, sizeof(DevCounters), s));
     float bb_init[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
     B_TRY(cudaMemcpyAsync(bb, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
+    B_TRY(cudaMemsetAsync(n_long, 0, sizeof(unsigned), s));
     // about four corners per thread, at most four blocks per SM of this part
     k_soup_bounds<<<(unsigned)std::min<int64_t>((n + 4 * BT - 1) / (4 * BT), 4 * 152), BT, 0, s>>>(soup, n, bb, f->ctr);
     SDF_LAUNCHED(1);
@@ -665,7 +727,9 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
     B_TRY(radix_sort_u64(keys, vals, kalt, valt, n, 40, rtmp, s));
-    k_weld_fix<<<nblk(n), BT, 0, s>>>(keys, vals, soup, n);
+    k_weld_fix<<<nblk(n), BT, 0, s>>>(keys, vals, soup, n, long_runs, long_cap, n_long);
+    SDF_LAUNCHED(1);
+    k_weld_sort_runs<<<2 * 152, 256, 0, s>>>(long_runs, n_long, long_cap, vals, soup);
     SDF_LAUNCHED(1);
     k_weld_heads<<<nblk(n), BT, 0, s>>>(keys, vals, soup, n, valt);
     SDF_LAUNCHED(1);

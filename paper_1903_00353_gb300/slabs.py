@@ -9,28 +9,34 @@ reduction, and the per-rank forward and backward through the library's C ABI.
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from . import Grid, sdf_narrow_band, sdf_narrow_band_backward
 
 
-def slab_bounds(nz: int, world: int, rank: int) -> tuple[int, int]:
-    """Balanced split of the nz grid layers: rank r gets [k0, k1), the first nz % world ranks one
-    layer more; the slabs of all ranks tile [0, nz) without overlap."""
-    if world < 1 or not 0 <= rank < world or nz < 0:
+# Slab boundaries fall on multiples of the tile kernel's tile depth along z, so that the slabs' tiles
+# are the whole grid's tiles and the slabs reproduce it bit for bit.
+SLAB_ALIGN = 8
+
+
+def slab_bounds(nz: int, world: int, rank: int, align: int = SLAB_ALIGN) -> tuple[int, int]:
+    """Balanced split of the nz grid layers in blocks of `align` layers: rank r gets [k0, k1), the
+    first ranks one block more; the slabs of all ranks tile [0, nz) without overlap (a rank may get
+    an empty slab when there are fewer blocks than ranks)."""
+    if world < 1 or not 0 <= rank < world or nz < 0 or align < 1:
         raise ValueError("bad slab request")
-    base, rem = divmod(nz, world)
-    k0 = rank * base + min(rank, rem)
-    return k0, k0 + base + (1 if rank < rem else 0)
+    blocks = (nz + align - 1) // align
+    base, rem = divmod(blocks, world)
+    b0 = rank * base + min(rank, rem)
+    b1 = b0 + base + (1 if rank < rem else 0)
+    return min(nz, b0 * align), min(nz, b1 * align)
 
 
 def slab_grid(grid: Grid, world: int, rank: int) -> Grid:
-    """The grid of rank r's slab: the same x-y layout and spacing, layers k0..k1-1, its origin moved
-    up by k0 cells (float32, as the library stores it)."""
+    """The grid of rank r's slab: the same origin, spacing and x-y layout, layers k0..k1-1 of the
+    whole grid (sdf_grid's k0), so its points are exactly the whole grid's."""
     k0, k1 = slab_bounds(grid.nz, world, rank)
-    oz = float(np.float32(np.float32(grid.origin[2]) + np.float32(k0) * np.float32(grid.h)))
-    return Grid(grid.nx, grid.ny, k1 - k0, (grid.origin[0], grid.origin[1], oz), grid.h)
+    return Grid(grid.nx, grid.ny, k1 - k0, grid.origin, grid.h, grid.k0 + k0)
 
 
 def all_reduce_sum(t: torch.Tensor, group=None) -> torch.Tensor:
@@ -42,8 +48,12 @@ def all_reduce_sum(t: torch.Tensor, group=None) -> torch.Tensor:
 
 
 def forward(features, grid: Grid, w: float, world: int, rank: int, winner: bool = False, flags: int = 0):
-    """This rank's slab of the narrow band: (slab grid, dist [, winner])."""
+    """This rank's slab of the narrow band: (slab grid, dist [, winner]); a rank whose slab is empty
+    (fewer blocks of layers than ranks) gets empty tensors."""
     g = slab_grid(grid, world, rank)
+    if g.nz == 0:
+        empty = torch.empty((0, grid.ny, grid.nx), dtype=torch.float32, device="cuda")
+        return g, ((empty, torch.empty(empty.shape, dtype=torch.int32, device="cuda")) if winner else empty)
     return g, sdf_narrow_band(features, g, w, winner=winner, flags=flags)
 
 
@@ -51,5 +61,8 @@ def backward(features, grid: Grid, w: float, world: int, rank: int, grad_slab: t
              winner_slab: torch.Tensor | None = None, group=None) -> torch.Tensor:
     """dL/d(welded vertices) of the whole grid: this rank's slab adjoint, summed over the ranks."""
     g = slab_grid(grid, world, rank)
-    gv = sdf_narrow_band_backward(features, g, w, grad_slab, winner=winner_slab)
+    if g.nz == 0:
+        gv = torch.zeros(features.n_vert, 3, dtype=torch.float32, device="cuda")
+    else:
+        gv = sdf_narrow_band_backward(features, g, w, grad_slab, winner=winner_slab)
     return all_reduce_sum(gv, group)

@@ -59,6 +59,9 @@ TINY = {
     # overlapping rotated boxes: concave creases, saddle vertices where a crease meets a box edge
     "box_union3": lambda: meshgen.box_union(3, 1500, seed=2),
     "box_union4": lambda: meshgen.box_union(4, 3000, seed=3),
+    # a dense cluster (36k vertices within a few micro-units) next to large triangles: long runs of
+    # distinct vertices under one weld key, sorted by the block-wide fix-up
+    "dense_cluster": lambda: meshgen.dense_cluster(),
 }
 
 
@@ -85,7 +88,7 @@ def test_ragged_grid_nondyadic_spacing(name):
 
 def test_classification_and_weld_match_oracle():
     for mesh in (meshgen.torus(nu=60, nv=24, seed=2), meshgen.knot_tube(n_along=600, n_around=20, seed=5),
-                 meshgen.box(subdiv=2), TINY["ruff"](), TINY["box_union4"]()):
+                 meshgen.box(subdiv=2), TINY["ruff"](), TINY["box_union4"](), TINY["dense_cluster"]()):
         soup = mesh.soup(seed=1)
         feats = sdf.sdf_build_features(torch.from_numpy(soup).cuda())
         om = oracle.OracleMesh.from_soup(soup)

@@ -21,21 +21,22 @@ def test_slab_bounds_tile_the_grid(nz, world):
     for r in range(world):
         k0, k1 = slabs.slab_bounds(nz, world, r)
         assert 0 <= k0 <= k1 <= nz
+        assert k0 % slabs.SLAB_ALIGN == 0 or k0 == nz  # slab starts on a tile layer
         covered.extend(range(k0, k1))
         sizes.append(k1 - k0)
     assert covered == list(range(nz))
-    assert max(sizes) - min(sizes) <= 1
+    assert max(sizes) - min(sizes) < 2 * slabs.SLAB_ALIGN  # balanced to a block of layers (plus a partial last one)
 
 
 def test_slab_grid_origin_and_shape():
-    g = Grid(40, 30, 33, (0.25, 0.5, 0.125), 1 / 64)
+    g = Grid(40, 30, 33, (0.25, 0.5, 0.125), 0.0137)
     total = 0
     for r in range(4):
         s = slabs.slab_grid(g, 4, r)
         k0, k1 = slabs.slab_bounds(33, 4, r)
-        assert (s.nx, s.ny, s.nz, s.h) == (40, 30, k1 - k0, g.h)
-        assert s.origin[:2] == g.origin[:2]
-        assert s.origin[2] == 0.125 + k0 / 64  # dyadic: exact
+        # the slab keeps the whole grid's origin and spacing and names its first layer
+        assert (s.nx, s.ny, s.nz, s.h, s.k0) == (40, 30, k1 - k0, g.h, k0)
+        assert s.origin == g.origin
         total += s.nz
     assert total == 33
     with pytest.raises(ValueError):
@@ -62,8 +63,10 @@ def _rank_main(rank: int, world: int, port: int, out_dir: str):
         om = oracle.OracleMesh.from_soup(soup)
         sg = slabs.slab_grid(grid, world, rank)
         dims = (sg.nx, sg.ny, sg.nz)
-        d = om.narrow_band(dims, sg.origin, sg.h, w).ravel()
-        pts = oracle.grid_points(dims, sg.origin, sg.h, np.arange(d.size))
+        # the oracle's grid of the slab: the slab's points at the whole grid's positions
+        org = (sg.origin[0], sg.origin[1], sg.origin[2] + sg.k0 * sg.h)
+        d = om.narrow_band(dims, org, sg.h, w).ravel()
+        pts = oracle.grid_points(dims, org, sg.h, np.arange(d.size))
         g = np.where(np.isfinite(d), 2.0 * (d - 0.01), 0.0)
         gv = torch.from_numpy(om.adjoint_points(pts, g, w))
         slabs.all_reduce_sum(gv)
