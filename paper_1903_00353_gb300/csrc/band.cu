@@ -1036,7 +1036,8 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
 
 // ----------------------------------------------------------------------------- FP64 re-decision
 // closest point of triangle (a, b, c) to p by Voronoi-region classification of the corner,
-// edge and face regions; region 0 face, 1 + k edge (corner k -> k+1), 4 + k corner k
+// edge and face regions; region 0 face, 1 + k edge (corner k -> k+1), 4 + k corner k.  The
+// published method of C. Ericson, Real-Time Collision Detection (2005), Section 5.1.5, in FP64.
 __device__ double closest_on_tri(double3 p, double3 a, double3 b, double3 c, int &region, double3 &lam) {
     double3 ab = b - a, ac = c - a, ap = p - a;
     double d1 = ddot3(ab, ap), d2 = ddot3(ac, ap);

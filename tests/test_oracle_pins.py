@@ -151,7 +151,7 @@ def test_eikonal_in_face_regions():
     assert same.sum() > 500
     g = np.stack([(d[:, 1] - d[:, 2]), (d[:, 3] - d[:, 4]), (d[:, 5] - d[:, 6])], axis=1) / (2 * e)
     err = np.abs(np.linalg.norm(g[same], axis=1) - 1.0)
-    assert err.max() < 1e-8
+    assert err.max() < 1e-9  # d is affine in a face region: only rounding (about 3e-11 at this step) remains
 
 
 def test_translation_by_grid_steps_is_an_exact_index_shift():
