@@ -119,6 +119,60 @@ def peaks():
         return 6800.0, "fallback"
 
 
+_RATES = None
+
+
+def measured_rates(sdf, dev) -> dict:
+    """Rates of the merge's 64-bit atomicMin (shared memory: the tile kernel; global memory within L2
+    and beyond it: the paper's schedule) and of FP64 FMAs, measured once per process with the
+    library's rate probes (each launch sized to about 2 ms, CUDA events on the launching stream,
+    best of 3 after a warm-up)."""
+    global _RATES
+    if _RATES is not None:
+        return _RATES
+    import torch
+    buf = torch.full((1 << 28,), -1, dtype=torch.int64, device=dev)  # 2 GiB: beyond L2
+    cases = {"smem_atomic_min_per_s": (sdf.PROBE_SMEM_ATOMIC_MIN, buf[: 1 << 12], 4096),
+             "l2_atomic_min_per_s": (sdf.PROBE_GLOBAL_ATOMIC_MIN, buf[: 1 << 21], 256),  # 16 MiB footprint
+             "hbm_atomic_min_per_s": (sdf.PROBE_GLOBAL_ATOMIC_MIN, buf, 256),  # 2 GiB footprint
+             "fp64_flops_per_s": (sdf.PROBE_FP64_FMA, buf[:1], 256)}
+    out = {}
+    for key, (kind, b, iters) in cases.items():
+        def timed(it):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ops = sdf.probe_rate(kind, b, it)
+            e1.record()
+            e1.synchronize()
+            return ops, e0.elapsed_time(e1)
+        _, ms = timed(iters)
+        iters = int(min(1 << 22, max(1, iters * 2.0 / max(ms, 1e-3))))
+        best = 0.0
+        for _ in range(3):
+            ops, ms = timed(iters)
+            best = max(best, ops / (ms / 1e3))
+        out[key] = best
+    del buf
+    torch.cuda.empty_cache()
+    out["how"] = ("sdf_probe_rate: atomicMin(u64) on 32 KB of shared memory per CTA (lane l on word l + 32m); "
+                  "on pseudo-random words of a 16 MiB (L2) and a 2 GiB (HBM) footprint; FP64 FMA chains")
+    _RATES = out
+    return out
+
+
+def atomic_roof(ops: int, rates: dict, space: str, hbm_bytes: int, hbm_gbs: float, measured_ms: float) -> dict:
+    """The atomic side of the roofline max(bytes / HBM bandwidth, atomics / atomic rate): the merge's
+    (point, region) atomicMin count over the measured rate of the space it runs in."""
+    key = {"shared": "smem_atomic_min_per_s", "global": "hbm_atomic_min_per_s"}[space]
+    t_atomic = ops / rates[key] * 1e3
+    t_hbm = hbm_bytes / (hbm_gbs * 1e9) * 1e3
+    t_roof = max(t_atomic, t_hbm)
+    return {"ops": int(ops), "space": space, "rate": rates[key], "rate_unit": "atomicMin(u64)/s",
+            "rate_source": "measured in this run (sdf_probe_rate)", "atomic_ms": t_atomic, "hbm_ms": t_hbm,
+            "roof_ms": t_roof, "bound": "atomic" if t_atomic > t_hbm else "hbm",
+            "frac_of_max_roof": t_roof / measured_ms}
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling in the background (200 ms period)."""
     Q = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -658,6 +712,8 @@ def run_batch(args, wl, sdf, local, world, rank):
     roofline = {"kernel": "k_tile (all 64 problems in one persistent launch)", "bound": "hbm",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind,
                 "traffic": None, "algorithmic_bytes": int(alg_bytes), "avg_ms": tile_avg_ms}
+    roofline["atomic"] = atomic_roof(stats["candidates"], measured_rates(sdf, dev), "shared", alg_bytes, hbm,
+                                     tile_avg_ms)
     del graph
     batch.destroy()
     if rank != 0:
@@ -681,7 +737,8 @@ def run_batch(args, wl, sdf, local, world, rank):
         "autotune_ms_per_run": info["tuned_ms"], "build_all_s": build_s, "batch_create_s": create_s,
         "candidates_per_band_point": stats["candidates"] / max(1, stats["band_points"]),
         "fp64_points": stats["fp64_points"], "tile_region_pairs": stats["pairs"],
-        "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(), "e2e": e2e,
+        "roofline": roofline, "rates": measured_rates(sdf, dev), "cpu_baseline": cpu, "clocks": clk.summary(),
+        "e2e": e2e,
         "gpu_launches": int(launches), "gpu_launches_per_step": per_replay,
     }
     print(json.dumps(line), flush=True)
@@ -955,6 +1012,11 @@ def run_single(args, name, wl, sdf, world, rank, local):
                 "traffic": tile_traffic(name, not args.grid and not shard and args.schedule == "tile" and use_list),
                 "algorithmic_bytes": int(alg_bytes),
                 "avg_ms": tile_avg_ms}
+    rates = measured_rates(sdf, dev)
+    # every (point, region) candidate is one 64-bit atomicMin: in shared memory in the tile kernel, in
+    # global memory (8 B keys per grid point) in the paper's schedule
+    roofline["atomic"] = atomic_roof(stats["candidates"], rates, "global" if args.schedule == "cell" else "shared",
+                                     alg_bytes, hbm, tile_avg_ms)
     # the issue roof: warp instructions of the same ncu capture / the live duration
     instr = tile_traffic(name, not args.grid and not shard and args.schedule == "tile" and use_list,
                          "warp_instructions")
@@ -1014,7 +1076,7 @@ def run_single(args, name, wl, sdf, world, rank, local):
         "candidates_per_band_point": stats["candidates"] / max(1, stats["band_points"]),
         "fp64_points": stats["fp64_points"], "tile_region_pairs": stats["pairs"], "rows": stats["rows"],
         "rows_hit": stats["rows_hit"],
-        "roofline": roofline, "sparse": sparse, "cpu_baseline": cpu,
+        "roofline": roofline, "rates": measured_rates(sdf, dev), "sparse": sparse, "cpu_baseline": cpu,
         "clocks": dict(clk.summary(), per_step=step_clk.summary()), "e2e": e2e,
         "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
     }

@@ -253,6 +253,13 @@ int sdf_features_vertices(sdf_features f, float *out, void *stream);
  * region) pairs merged by atomicMin, band points decided in FP32, points
  * re-decided in FP64, (tile, region) pairs scheduled, grid rows intersected
  * with a region, of which non-empty.
+ * Errors: those of the call, among them SDF_ERR_OOM when a call made with SDF_FLAG_NO_SYNC
+ * outgrew its scratch.  A synchronising call grows the scratch (the (tile, region) pair list and
+ * the FP64 re-decision list) and repeats its launch when it overflows; a call with
+ * SDF_FLAG_NO_SYNC cannot, so its first capacities are sized from the mesh: the expected pairs
+ * of the grid, from the build's sums of the faces' bounding-box extents, with a quarter to spare
+ * and at least 8 per feature.  The environment variable SDF_PAIR_CAPACITY, when set to a
+ * positive count, replaces the first capacity of the pair list (for testing the growth path).
  */
 int sdf_features_status(sdf_features f, int64_t *stats, void *stream);
 
@@ -462,6 +469,30 @@ void sdf_features_destroy(sdf_features f);
 
 /* Static description of a status code. */
 const char *sdf_status_string(int status);
+
+/*
+ * sdf_probe_rate -- one launch of a rate probe for the roofline of the narrow band (a measurement
+ * helper with no counterpart in the paper).  The merge of Algorithm 1 is a 64-bit atomicMin of
+ * the packed key (|d|, feature id): in shared memory in the tile kernel, in global memory in the
+ * paper's own schedule (Section 9, one thread per region walking its cells); the filtered
+ * re-decision runs in FP64.  The launch runs 4 CTAs of 256 threads per SM, each thread `iters`
+ * steps, on `stream`, with no synchronisation; the caller times it (CUDA events on the same
+ * stream) and divides *ops by the time.
+ *
+ *   kind     SDF_PROBE_SMEM_ATOMIC_MIN: atomicMin(u64) on a 32 KB shared-memory array per CTA,
+ *            lane l of a warp on word l + 32 m; buf: device uint64[n_words], n_words >= the
+ *            number of CTAs (one result word per CTA is written).
+ *            SDF_PROBE_GLOBAL_ATOMIC_MIN: atomicMin(u64) on pseudo-random words of buf, device
+ *            uint64[n_words] with n_words a power of two (within L2 or larger than L2); its
+ *            contents are overwritten with smaller values.
+ *            SDF_PROBE_FP64_FMA: FP64 fused multiply-adds, 8 independent chains per thread;
+ *            buf: device double[n_words], n_words >= 1 (not written in practice).
+ *   iters    steps per thread, >= 1.
+ *   ops      host int64, set to the launch's operation count (atomics, or FP64 flops).
+ * Errors: SDF_ERR_INVALID_ARG, SDF_ERR_CUDA.
+ */
+enum { SDF_PROBE_SMEM_ATOMIC_MIN = 0, SDF_PROBE_GLOBAL_ATOMIC_MIN = 1, SDF_PROBE_FP64_FMA = 2 };
+int sdf_probe_rate(int32_t kind, void *buf, int64_t n_words, int64_t iters, int64_t *ops, void *stream);
 
 #ifdef __cplusplus
 }

@@ -90,6 +90,8 @@ def load_library(path: str | None = None):
     L.sdf_kernel_launches.restype = I64
     L.sdf_memory_stats.argtypes = [ctypes.POINTER(I64)]
     L.sdf_memory_stats.restype = ctypes.c_int
+    L.sdf_probe_rate.argtypes = [I32, P, I64, I64, ctypes.POINTER(I64), P]
+    L.sdf_probe_rate.restype = ctypes.c_int
     L.sdf_status_string.argtypes = [ctypes.c_int]
     L.sdf_status_string.restype = ctypes.c_char_p
     L.sdf_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(_CGrid), ctypes.POINTER(ctypes.c_float), I32,
@@ -131,6 +133,20 @@ def memory_stats() -> dict:
     _check(load_library().sdf_memory_stats(out), "sdf_memory_stats")
     return {"pool_allocs": int(out[0]), "pool_used": int(out[1]), "pool_reserved": int(out[2]),
             "host_allocs": int(out[3])}
+
+
+PROBE_SMEM_ATOMIC_MIN, PROBE_GLOBAL_ATOMIC_MIN, PROBE_FP64_FMA = 0, 1, 2
+
+
+def probe_rate(kind: int, buf: torch.Tensor, iters: int, stream=None) -> int:
+    """One launch of a rate probe (sdf_probe_rate) on `buf` (a CUDA tensor of 8-byte words); returns
+    the launch's operation count, which the caller divides by the launch's event-timed duration."""
+    if not buf.is_cuda or buf.element_size() != 8 or not buf.is_contiguous():
+        raise ValueError("buf must be a contiguous CUDA tensor of 8-byte elements")
+    ops = ctypes.c_int64(0)
+    _check(load_library().sdf_probe_rate(int(kind), ctypes.c_void_p(buf.data_ptr()), buf.numel(), int(iters),
+                                         ctypes.byref(ops), _stream(stream)), "sdf_probe_rate")
+    return int(ops.value)
 
 
 def _stream(stream=None) -> int:

@@ -37,6 +37,7 @@
 #include <math.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -1522,6 +1523,29 @@ static int make_grid(const sdf_grid &gr, float w, int shape, GridP &g) {
     return SDF_OK;
 }
 
+// Expected number of (tile, region) pairs of one problem, from the build's face-box moments, so
+// that a call that does not synchronise (and so cannot grow its scratch and repeat) starts with
+// enough room on meshes of large triangles.  A box of extent e cells meets about e / t + 1 tiles of
+// t cells along an axis; a face's region box lies within its bounding box widened by the band
+// (plus one cell of rounding), so a face meets about prod_a (b_a / (h t_a) + c_a) tiles with
+// c_a = (2 w / h + 1) / t_a + 1, which the moments sum over the faces.  Every edge's box lies in the
+// box of either of its faces (1.5 edges per face), and a vertex's box is a cube of side 2 w.
+static int64_t pair_estimate(const sdf_features_s *f, const GridP &g, int shape) {
+    const double h = g.h, w = 1.001 * g.w;
+    const double t[3] = {(double)TILE_X, (double)SHAPE_TY[shape], (double)SHAPE_TZ[shape]};
+    double c[3], sc[3];
+    for (int a = 0; a < 3; a++) {
+        c[a] = (2.0 * w / h + 1.0) / t[a] + 1.0;
+        sc[a] = 1.0 / (h * t[a]);
+    }
+    const double *M = f->box_mom;  // bx, by, bz, bx by, bx bz, by bz, bx by bz
+    const double faces = sc[0] * sc[1] * sc[2] * M[6] + sc[0] * sc[1] * c[2] * M[3] + sc[0] * c[1] * sc[2] * M[4] +
+                         c[0] * sc[1] * sc[2] * M[5] + sc[0] * c[1] * c[2] * M[0] + c[0] * sc[1] * c[2] * M[1] +
+                         c[0] * c[1] * sc[2] * M[2] + c[0] * c[1] * c[2] * (double)f->T;
+    const double est = 2.5 * faces + c[0] * c[1] * c[2] * (double)f->V;
+    return est < 2147483648.0 ? (int64_t)est : (int64_t(1) << 31);  // pair positions are 32-bit
+}
+
 static Feat make_feat(const sdf_features_s *f) {
     Feat F;
     F.T = (int)f->T; F.E = (int)f->E; F.V = (int)f->V;
@@ -1615,6 +1639,7 @@ struct Plan {
     DevCounters *ctr = nullptr;
     bool own_ctr = false;
     int64_t pair_cap = 0, patch_cap = 0;
+    int64_t pair_est = 0;  // expected (tile, region) pairs of the described problems (pair_estimate)
     double tuned_ms = 0.0;
     sdf_features_s *events = nullptr;  // handle whose events time the stages (SDF_FLAG_TIMING)
     // the last uploaded table (host copy), the device address it went to, and a pinned staging
@@ -1696,6 +1721,7 @@ static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *gr
     pl.zbase.assign(n + 1, 0);
     pl.ybase.assign(n + 1, 0);
     pl.pbase.assign(n + 1, 0);
+    pl.pair_est = 0;
     for (int p = 0; p < n; p++) {
         // the dense field may be left out only by a sparse forward (a list with its distances)
         const bool sparse = lists && lists[p].list && lists[p].dist;
@@ -1705,6 +1731,7 @@ static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *gr
         if (st) return st;
         pr.F = make_feat(feats[p]);
         pr.F.vmode = pl.vmode;
+        pl.pair_est += pair_estimate(feats[p], pr.g, shape);
         pr.dist = out_dist[p];
         pr.winner = out_winner ? out_winner[p] : nullptr;
         pr.vec = ((pr.g.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(pr.dist) & 15) == 0) &&
@@ -1754,7 +1781,16 @@ static int plan_reserve(Plan &pl, cudaStream_t s) {
     SDF_TRY(pl.bins.reserve(sizeof(uint32_t) * (size_t)(2 * n_bins + 64), s));
     SDF_TRY(pl.scan_tmp.reserve(scan_tmp_bytes(n_bins), s));
     SDF_TRY(pl.lists.reserve(16 + sizeof(uint32_t) * (size_t)(3 * pl.n_tiles + 256), s));
-    if (pl.pair_cap == 0) pl.pair_cap = 8 * pl.f_tot + 4096;
+    // room for the expected pairs (with a quarter to spare), and never less than 8 per feature;
+    // a synchronising call grows it further when the binning finds more.  SDF_PAIR_CAPACITY, when
+    // set, replaces the first capacity (to exercise that growth in tests).
+    const char *env = getenv("SDF_PAIR_CAPACITY");
+    const int64_t forced = env ? (int64_t)atoll(env) : 0;
+    if (forced > 0) {
+        if (pl.pair_cap == 0) pl.pair_cap = forced;
+    } else {
+        pl.pair_cap = std::max<int64_t>(pl.pair_cap, std::max<int64_t>(8 * pl.f_tot, pl.pair_est + pl.pair_est / 4) + 4096);
+    }
     if (pl.patch_cap == 0) pl.patch_cap = pl.f_tot / 8 + 65536;
     SDF_TRY(pl.pairs.reserve(sizeof(int2) * (size_t)pl.pair_cap, s));
     SDF_TRY(pl.patch.reserve(sizeof(PatchEntry) * (size_t)pl.patch_cap, s));

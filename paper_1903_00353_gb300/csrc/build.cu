@@ -330,8 +330,28 @@ __device__ __forceinline__ void warp_max_into(unsigned *word, float v) {
     if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(word, __float_as_uint(v));
 }
 
-// Face records, and the precision terms of the faces (every thread of the grid takes part in the
-// warp reductions, so the early-exit threads contribute zeros).  The unit normal and the plane
+// Sums of K values over a block of BT threads, added to K counters with one atomic each (FP32
+// within the block, FP64 across blocks).  Every thread of the block must call it.
+template <int K>
+__device__ __forceinline__ void block_sums_into(double *words, float (&v)[K]) {
+    __shared__ float part[BT / 32][K];
+#pragma unroll
+    for (int k = 0; k < K; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) part[threadIdx.x >> 5][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double t = 0.0;
+        for (int w = 0; w < BT / 32; w++) t += part[w][threadIdx.x];
+        if (t != 0.0) atomicAdd(&words[threadIdx.x], t);
+    }
+}
+
+// Face records, and the precision terms and box moments of the faces (every thread of the grid
+// takes part in the warp reductions, so the early-exit threads contribute zeros).  The unit normal and the plane
 // offset -n.a are computed in FP64 from the FP32 corners (their differences are exact in FP64)
 // and rounded once, so the stored normal is within about u = 2^-24 of the exact normal of the
 // corners however thin the triangle.  The side planes n x (edge) are formed in FP32 from it: the
@@ -377,6 +397,15 @@ __global__ void k_face_records(const int32_t *face_vid, const float *vpos, int64
     warp_max_into(&ctr->prec[PREC_MESH_M], m_abs);
     warp_max_into(&ctr->prec[PREC_TAU_A], tau_a);
     warp_max_into(&ctr->prec[PREC_TAU_B], tau_b);
+    float bx = 0.f, by = 0.f, bz = 0.f;
+    if (f < T) {
+        const float4 lo = face_box[2 * f], hi = face_box[2 * f + 1];
+        bx = hi.x - lo.x;
+        by = hi.y - lo.y;
+        bz = hi.z - lo.z;
+    }
+    float mom[7] = {bx, by, bz, bx * by, bx * bz, by * bz, bx * by * bz};
+    block_sums_into<7>(ctr->box_mom, mom);
 }
 
 __device__ double3 face_normal_fp64(const int32_t *face_vid, const float *vpos, int f) {
@@ -825,6 +854,7 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     f->counts[0] = V;
     f->counts[1] = E;
     for (int i = 2; i < 8; i++) f->counts[i] = (int64_t)c.cls[i];
+    for (int i = 0; i < 7; i++) f->box_mom[i] = c.box_mom[i];
     *out = f;
     return SDF_OK;
 }
@@ -836,6 +866,7 @@ extern "C" int sdf_features_update_positions(sdf_features f, const float *vertic
     SDF_TRY(cudaMemsetAsync(f->ctr->cls, 0, sizeof(f->ctr->cls), s));
     SDF_TRY(cudaMemsetAsync(&f->ctr->status, 0, sizeof(unsigned), s));  // re-evaluated below
     SDF_TRY(cudaMemsetAsync(f->ctr->prec, 0, sizeof(f->ctr->prec), s));  // precision terms, likewise
+    SDF_TRY(cudaMemsetAsync(f->ctr->box_mom, 0, sizeof(f->ctr->box_mom), s));
     return build_records(f, s);
 }
 

@@ -75,6 +75,10 @@ struct DevCounters {
     // and normal errors, tau_a + tau_b * W (see k_face_records), PREC_TAU_V the direction error
     // of the unit pseudonormals per unit distance (see k_vertex_records).
     unsigned prec[4];
+    // Sums over the faces of the extents (bx, by, bz) of their bounding boxes, written by the build:
+    // bx, by, bz, bx by, bx bz, by bz, bx by bz.  They give the expected number of (tile, region)
+    // pairs of a grid before any kernel runs (pair_estimate in band.cu).
+    double box_mom[7];
 };
 enum { PREC_MESH_M = 0, PREC_TAU_A = 1, PREC_TAU_B = 2, PREC_TAU_V = 3 };
 // unit roundoff of FP32 (2^-24)
@@ -125,6 +129,7 @@ struct sdf_features_s {
     int8_t *edge_class = nullptr;   // [E]
     int8_t *vert_class = nullptr;   // [V]
     int64_t counts[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double box_mom[7] = {0, 0, 0, 0, 0, 0, 0};  // the build's face-box moments (DevCounters::box_mom)
     sdf::DevCounters *ctr = nullptr; // device counters
     // narrow-band scratch of single-problem calls (problem table, bins, pairs), grown on demand
     sdf::Plan *plan = nullptr;

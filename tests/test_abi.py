@@ -60,6 +60,9 @@ def test_argument_validation_without_device(lib):
     assert lib.sdf_narrow_band_lists(None, None, None, 1, None, None, None, None, None, 0, None) == 1
     assert lib.sdf_band_list_backward(None, None, None, 0, None, None, None, 0, None) == 1
     assert lib.sdf_band_list_l2(None, None, None, 0, None, None, None, None, None, None, 0, None) == 1
+    ops = ctypes.c_int64(0)
+    assert lib.sdf_probe_rate(0, None, 1 << 20, 1, ctypes.byref(ops), None) == 1
+    assert lib.sdf_probe_rate(1, ctypes.c_void_p(256), 1 << 20, 0, ctypes.byref(ops), None) == 1
 
 
 def test_product_package_does_not_import_oracle():

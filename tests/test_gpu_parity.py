@@ -240,18 +240,40 @@ def test_adjoint_matches_oracle_adjoint():
         assert rel < 1e-3, rel
 
 
-def test_pair_list_overflow_is_retried():
-    """Few large triangles on a fine grid: the first launch overflows the initial (tile, region)
-    pair list (sized from the feature count), and the call grows it and runs again."""
+def test_pair_list_overflow_is_retried(monkeypatch):
+    """Few large triangles on a fine grid, with the first (tile, region) pair capacity forced below
+    what the binning needs (SDF_PAIR_CAPACITY): the first launch overflows, and the call grows the
+    list and runs again."""
     soup = meshgen.config_soup(1)  # 320 triangles, each about 50 cells wide at 512^3
     N = 384
     grid, w = sdf.Grid.cube(N), 3 / N
+    monkeypatch.setenv("SDF_PAIR_CAPACITY", "1000")
     feats = sdf.sdf_build_features(torch.from_numpy(soup).cuda())
     dist = sdf.sdf_narrow_band(feats, grid, w)
     st = feats.status()
-    assert st["pairs"] > 8 * (feats.n_tri + feats.n_edge + feats.n_vert) + 4096  # beyond the first capacity
+    assert st["pairs"] > 1000  # beyond the first capacity
+    monkeypatch.delenv("SDF_PAIR_CAPACITY")
+    feats2 = sdf.sdf_build_features(torch.from_numpy(soup).cuda())
+    assert torch.equal(sdf.sdf_narrow_band(feats2, grid, w), dist)
     idx = parity.near_surface_indices(soup, (N, N, N), (0, 0, 0), grid.h, w, 20_000, 353_384, n_uniform=2000)
     d_gpu = dist.view(-1)[torch.from_numpy(idx).cuda()].cpu().numpy()
     om = oracle.OracleMesh.from_soup(soup)
     d_or, _, _ = om.band_points((N, N, N), (0, 0, 0), grid.h, w + 2 * grid.h, idx)
     parity.assert_parity(parity.compare(d_gpu, d_or, w, grid.h))
+
+
+@pytest.mark.parametrize("N", [256, 512])
+def test_unsynchronised_call_on_a_fresh_handle_has_room(N):
+    """A call that does not synchronise cannot grow its scratch and repeat, so a fresh handle's
+    first capacity must hold the (tile, region) pairs of large triangles on a fine grid: it comes
+    from the build's face-box moments, and it needs to exceed the old 8-per-feature floor here."""
+    soup = meshgen.config_soup(1)
+    grid, w = sdf.Grid.cube(N), 3 / N
+    feats = sdf.sdf_build_features(torch.from_numpy(soup).cuda())
+    dist = torch.empty(grid.shape, dtype=torch.float32, device="cuda")
+    sdf.sdf_narrow_band(feats, grid, w, out=dist, flags=sdf.FLAG_NO_SYNC)
+    st = feats.status()  # raises on an overflow
+    if N == 512:
+        assert st["pairs"] > 8 * (feats.n_tri + feats.n_edge + feats.n_vert) + 4096
+    ref = sdf.sdf_narrow_band(sdf.sdf_build_features(torch.from_numpy(soup).cuda()), grid, w)
+    assert torch.equal(dist, ref)
