@@ -57,7 +57,7 @@ typedef enum sdf_status {
     SDF_ERR_TOO_LARGE = 5,    /* sizes beyond the index ranges (2^31 features, 2^31 rows)  */
     SDF_ERR_OOM = 6,          /* device allocation failed                                 */
     SDF_ERR_CUDA = 7,         /* a CUDA runtime call failed                               */
-    SDF_ERR_TIMEOUT = 8,      /* a bounded device wait gave up (reserved)                 */
+    SDF_ERR_TIMEOUT = 8,      /* a bounded device wait gave up (a scan's look-back)       */
     SDF_ERR_LIST_OVERFLOW = 9 /* the caller's band list holds fewer entries than the band
                                  has points; its count holds the length needed             */
 } sdf_status;

@@ -1779,7 +1779,11 @@ static int plan_reserve(Plan &pl, cudaStream_t s) {
     if (pl.fill) SDF_TRY(pl.rowsign.reserve((size_t)pl.r_tot + 64, s));
     if (pl.cell_loop) SDF_TRY(pl.keys.reserve(sizeof(unsigned long long) * (size_t)pl.p_tot, s));
     SDF_TRY(pl.bins.reserve(sizeof(uint32_t) * (size_t)(2 * n_bins + 64), s));
-    SDF_TRY(pl.scan_tmp.reserve(scan_tmp_bytes(n_bins), s));
+    {  // the scan state starts cleared whenever its memory is new (see scan_exclusive_u32)
+        void *const before = pl.scan_tmp.p;
+        SDF_TRY(pl.scan_tmp.reserve(scan_state_bytes(n_bins), s));
+        if (pl.scan_tmp.p != before) SDF_TRY(cudaMemsetAsync(pl.scan_tmp.p, 0, pl.scan_tmp.bytes, s));
+    }
     SDF_TRY(pl.lists.reserve(16 + sizeof(uint32_t) * (size_t)(3 * pl.n_tiles + 256), s));
     // room for the expected pairs (with a quarter to spare), and never less than 8 per feature;
     // a synchronising call grows it further when the binning finds more.  SDF_PAIR_CAPACITY, when
@@ -1917,7 +1921,7 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
                                                           nullptr, 0, sc.ctr);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
-    SDF_TRY(scan_exclusive_u32(sc.cnt, sc.start, n_bins, true, sc.scan_tmp, s));
+    SDF_TRY(scan_exclusive_u32(sc.cnt, sc.start, n_bins, true, sc.scan_tmp, s, &sc.ctr->nb_status));
     SDF_TRY(cudaMemsetAsync(sc.cnt, 0, sizeof(uint32_t) * n_bins, s));
     k_bin<true, TY, TZ><<<nblk(f_tot, 256), 256, 0, s>>>(sc.probs, sc.fbase, sc.tbase, n, f_tot, sc.cnt, sc.start,
                                                          sc.pairs, sc.pair_cap, sc.ctr);
@@ -1930,7 +1934,7 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
     k_band_flags<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, flags, sc.ctr, lpt);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
-    SDF_TRY(scan_exclusive_u32(flags, sc.band_pos, n_tiles, true, sc.scan_tmp, s));
+    SDF_TRY(scan_exclusive_u32(flags, sc.band_pos, n_tiles, true, sc.scan_tmp, s, &sc.ctr->nb_status));
     k_tile_lists<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, sc.band_pos, sc.band_list, sc.empty_list,
                                                     sc.ctr, lpt);
     SDF_LAUNCHED(1);
@@ -2055,6 +2059,7 @@ static int plan_check(Plan &pl, const sdf_features *feats, cudaStream_t s, bool 
             if (st[i] & ST_DEGENERATE) return SDF_ERR_DEGENERATE;
     }
     if (c.status & ST_DEGENERATE) return SDF_ERR_DEGENERATE;
+    if (c.nb_status & ST_TIMEOUT) return SDF_ERR_TIMEOUT;
     if (c.nb_status & ST_PAIR_OVERFLOW) {
         pl.pair_cap = (int64_t)total_pairs + total_pairs / 4 + 4096;
         *retry = true;
@@ -2098,6 +2103,7 @@ int narrow_band_stats(sdf_features_s *f, int64_t *stats, cudaStream_t s) {
         stats[5] = (int64_t)c.n_rows_hit;
     }
     if (c.status & ST_DEGENERATE) return SDF_ERR_DEGENERATE;
+    if (c.nb_status & ST_TIMEOUT) return SDF_ERR_TIMEOUT;
     if (c.nb_status & (ST_PAIR_OVERFLOW | ST_PATCH_OVERFLOW)) return SDF_ERR_OOM;
     if (c.nb_status & ST_LIST_OVERFLOW) return SDF_ERR_LIST_OVERFLOW;
     return SDF_OK;
@@ -2299,6 +2305,7 @@ extern "C" int sdf_batch_status(sdf_batch b, int64_t *stats, void *stream) {
         stats[4] = (int64_t)c.n_rows;
         stats[5] = (int64_t)c.n_rows_hit;
     }
+    if (c.nb_status & ST_TIMEOUT) return SDF_ERR_TIMEOUT;
     if (c.nb_status & (ST_PAIR_OVERFLOW | ST_PATCH_OVERFLOW)) return SDF_ERR_OOM;
     if (c.nb_status & ST_LIST_OVERFLOW) return SDF_ERR_LIST_OVERFLOW;
     return SDF_OK;
@@ -2442,7 +2449,7 @@ extern "C" int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, floa
     if (st) return st;
     const int64_t n_tiles = (int64_t)g.ntx * g.nty * g.ntz, n_bins = 3 * n_tiles;
     if (n_tiles > ST_MAX_TILES) return SDF_ERR_TOO_LARGE;  // grid beyond the static scratch
-    if (scan_tmp_bytes(n_bins) > ST_SCAN_BYTES) return SDF_ERR_TOO_LARGE;
+    if (scan_state_bytes(n_bins) > ST_SCAN_BYTES) return SDF_ERR_TOO_LARGE;
     unsigned char *base = static_scratch_ptr(&st);
     if (st) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -2477,6 +2484,7 @@ extern "C" int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, floa
     SDF_TRY(cudaMemcpyAsync(base + ST_OFF_TABLE + ST_PROB_BYTES, bases, sizeof(bases), cudaMemcpyHostToDevice, s));
     // the array keeps the previous call's contents: clear the counters (the pipeline clears the rest)
     SDF_TRY(cudaMemsetAsync(sc.ctr, 0, sizeof(DevCounters), s));
+    SDF_TRY(cudaMemsetAsync(sc.scan_tmp, 0, scan_state_bytes(n_bins), s));  // the scans' state starts cleared
     SDF_TRY_ST((launch_shape<8, 8>(1, n_feat, n_tiles, sc, s, nullptr)));
     // The status words, read into host stack memory: this call's list overflows and the handle's
     // own status (a face that sdf_features_update_positions made degenerate).  A device-to-host
@@ -2486,6 +2494,7 @@ extern "C" int sdf_narrow_band_static(sdf_features f, const sdf_grid *grid, floa
     SDF_TRY(cudaMemcpyAsync(&status[1], &f->ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     SDF_TRY(cudaStreamSynchronize(s));
     if (status[1] & ST_DEGENERATE) return SDF_ERR_DEGENERATE;
+    if (status[0] & ST_TIMEOUT) return SDF_ERR_TIMEOUT;
     if (status[0] & (ST_PAIR_OVERFLOW | ST_PATCH_OVERFLOW)) return SDF_ERR_TOO_LARGE;
     return SDF_OK;
 }

@@ -679,6 +679,7 @@ int build_records(sdf_features_s *f, cudaStream_t s) {
 using namespace sdf;
 
 static int status_to_code(unsigned st) {
+    if (st & ST_TIMEOUT) return SDF_ERR_TIMEOUT;
     if (st & ST_NONFINITE) return SDF_ERR_NONFINITE;
     if (st & ST_DEGENERATE) return SDF_ERR_DEGENERATE;
     if (st & ST_NONMANIFOLD) return SDF_ERR_NONMANIFOLD;
@@ -733,7 +734,10 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
            off_head = off_valt + 4 * n, off_bb = off_head + 4 * (n + 1) + 64,
            off_long = (off_bb + 64 + 15) & ~(size_t)15,               // int2: 8-byte aligned (16 here)
            off_rtmp = (off_long + 8 * long_cap + 64 + 15) & ~(size_t)15;
-    size_t need = off_rtmp + radix_tmp_bytes(n) + scan_tmp_bytes(n + 1) + 1024;
+    // one scan state for the build's scans and sorts, cleared once here (see scan_exclusive_u32)
+    const size_t scan_bytes = std::max(scan_state_bytes(n + 1), radix_scan_state_bytes(n));
+    const size_t off_scan = (off_rtmp + radix_tmp_bytes(n) + 255) & ~(size_t)255;
+    size_t need = off_scan + scan_bytes + 1024;
     B_TRY(tmp.reserve(need, s));
     char *base = tmp.as<char>();
     uint64_t *keys = reinterpret_cast<uint64_t *>(base + off_keys), *kalt = reinterpret_cast<uint64_t *>(base + off_kalt);
@@ -743,19 +747,22 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     unsigned *n_long = reinterpret_cast<unsigned *>(base + off_bb + 32);
     int2 *long_runs = reinterpret_cast<int2 *>(base + off_long);
     void *rtmp = base + off_rtmp;
+    void *scan_state = base + off_scan;
 
     B_TRY(dalloc_s(&f->ctr, 1, s));
     B_TRY(cudaMemsetAsync(f->ctr, 0, sizeof(DevCounters), s));
+    unsigned *const err = &f->ctr->status;  // a scan whose look-back ran out marks ST_TIMEOUT here
     float bb_init[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
     B_TRY(cudaMemcpyAsync(bb, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
     B_TRY(cudaMemsetAsync(n_long, 0, sizeof(unsigned), s));
+    B_TRY(cudaMemsetAsync(scan_state, 0, scan_bytes, s));
     // about four corners per thread, at most four blocks per SM of this part
     k_soup_bounds<<<(unsigned)std::min<int64_t>((n + 4 * BT - 1) / (4 * BT), 4 * 152), BT, 0, s>>>(soup, n, bb, f->ctr);
     SDF_LAUNCHED(1);
     k_weld_keys<<<nblk(n), BT, 0, s>>>(soup, n, bb, keys, vals);
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
-    B_TRY(radix_sort_u64(keys, vals, kalt, valt, n, 40, rtmp, s));
+    B_TRY(radix_sort_u64(keys, vals, kalt, valt, n, 40, rtmp, scan_state, s, err));
     k_weld_fix<<<nblk(n), BT, 0, s>>>(keys, vals, soup, n, long_runs, long_cap, n_long);
     SDF_LAUNCHED(1);
     k_weld_sort_runs<<<2 * 152, 256, 0, s>>>(long_runs, n_long, long_cap, vals, soup);
@@ -764,7 +771,7 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
     // head[i] = number of run heads before i, head[n] = V (so head[i+1] is the inclusive count at i)
-    B_TRY(scan_exclusive_u32(valt, head, n, true, rtmp, s));
+    B_TRY(scan_exclusive_u32(valt, head, n, true, scan_state, s, err));
     uint32_t Vh = 0;
     unsigned st_h = 0;
     {
@@ -795,7 +802,7 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     k_face_keys<<<nblk(T), BT, 0, s>>>(f->soup_vid, T, keys, vals);
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
-    B_TRY(radix_sort_u64(keys, vals, kalt, valt, T, nb, rtmp, s));
+    B_TRY(radix_sort_u64(keys, vals, kalt, valt, T, nb, rtmp, scan_state, s, err));
     k_face_perm<<<nblk(T), BT, 0, s>>>(vals, f->soup_vid, T, f->face_soup, f->face_vid, valt);
     SDF_LAUNCHED(1);
     k_corner_remap<<<nblk(n), BT, 0, s>>>(f->vert_corner, valt, n);
@@ -814,7 +821,7 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     k_pair_fans<<<nblk(n), BT, 0, s>>>(f->vert_start, f->vert_corner, f->face_vid, n, twin, canon, f->ctr);
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
-    B_TRY(scan_exclusive_u32(canon, head, n, true, rtmp, s));
+    B_TRY(scan_exclusive_u32(canon, head, n, true, scan_state, s, err));
     B_TRY(dalloc_s(&f->edge_vf, E, s));
     k_edge_emit<<<nblk(n), BT, 0, s>>>(f->vert_corner, f->face_vid, twin, canon, head, n, f->edge_vf, f->face_edge);
     SDF_LAUNCHED(1);

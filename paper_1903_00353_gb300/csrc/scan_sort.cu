@@ -48,18 +48,6 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *to
     return r;
 }
 
-__global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *in, int64_t n, uint32_t *sums) {
-    int64_t base = (int64_t)blockIdx.x * SC_TILE;
-    uint32_t s = 0;
-    for (int i = 0; i < SC_ITEMS; i++) {
-        int64_t idx = base + (int64_t)i * SC_THREADS + threadIdx.x;
-        if (idx < n) s += in[idx];
-    }
-    __shared__ uint32_t tot;
-    block_excl_scan_u32(s, &tot);
-    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
-}
-
 // exclusive scan of each tile (blocked arrangement: thread t owns SC_ITEMS consecutive items),
 // offset by offs[blockIdx.x] (nullable)
 __global__ void __launch_bounds__(SC_THREADS) k_scan_apply(const uint32_t *in, uint32_t *out, int64_t n,
@@ -81,86 +69,118 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_apply(const uint32_t *in, u
     }
     if (total_out && blockIdx.x == gridDim.x - 1 && threadIdx.x == SC_THREADS - 1) *total_out = run;
 }
+
+// Single-pass scan with decoupled look-back (D. Merrill and M. Garland, "Single-pass Parallel
+// Prefix Scan with Decoupled Look-back", NVIDIA technical report NVR-2016-002).  Each CTA draws
+// its tile from a ticket, so it only ever waits for tiles whose CTAs have already started; it
+// publishes its tile's total (AGGREGATE), then sums its predecessors' words walking back 32 at a
+// time until one carries an inclusive prefix (PREFIX), and publishes its own inclusive prefix.
+// The state region: [0] ticket, [1] epoch, then one 64-bit word per tile, epoch << 34 | flag << 32 |
+// value.  Words of earlier scans carry an older epoch and count as not yet published.  The CTA
+// that draws the last ticket puts the ticket back to 0, and the one holding the last tile
+// advances the epoch when it is done (by then every CTA has read it), so the region is ready for
+// the next scan issued after this one on the stream.  A wait that runs out of polls marks
+// ST_TIMEOUT in *err (nullable) and leaves the scan unfinished instead of hanging.
+constexpr unsigned long long SCAN_AGG = 1ull << 32, SCAN_PFX = 2ull << 32;
+constexpr unsigned SCAN_POLL_LIMIT = 1u << 20;
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_chained(const uint32_t *in, uint32_t *out, int64_t n,
+                                                             unsigned *hdr, unsigned long long *status,
+                                                             uint32_t *total_out, unsigned *err) {
+    __shared__ unsigned s_tile, s_epoch;
+    __shared__ uint32_t s_prefix, s_tot;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        s_epoch = *(volatile unsigned *)(hdr + 1) & 0x3fffffffu;
+        const unsigned t = atomicAdd(hdr, 1u);
+        if (t == gridDim.x - 1) atomicExch(hdr, 0u);  // every ticket is drawn: ready for the next scan
+        s_tile = t;
+    }
+    __syncthreads();
+    const unsigned tile = s_tile;
+    const unsigned long long tag = (unsigned long long)s_epoch << 34;
+    const int64_t base = (int64_t)tile * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+    uint32_t v[SC_ITEMS];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < SC_ITEMS; i++) {
+        v[i] = (base + i < n) ? in[base + i] : 0u;
+        sum += v[i];
+    }
+    uint32_t run = block_excl_scan_u32(sum, &s_tot);  // ends with a barrier: s_tot is set
+    const uint32_t tot = s_tot;
+    if (threadIdx.x == 0) {
+        atomicExch(status + tile, tag | (tile == 0 ? SCAN_PFX : SCAN_AGG) | tot);
+        if (tile == 0) s_prefix = 0;
+    }
+    if (warp == 0 && tile > 0) {
+        uint32_t acc = 0;
+        int64_t j = (int64_t)tile - 1;  // the nearest predecessor not yet added
+        unsigned polls = 0;
+        bool ok = true;
+        for (;;) {
+            const int64_t idx = j - lane;
+            // before the first tile: an inclusive prefix of 0
+            const unsigned long long w = idx >= 0 ? __ldcv(status + idx) : (tag | SCAN_PFX);
+            const bool valid = (w >> 34) == (tag >> 34) && (w & (3ull << 32)) != 0;
+            const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+            const unsigned pmask = __ballot_sync(0xffffffffu, valid && (w & SCAN_PFX) != 0);
+            const int p = pmask ? __ffs(pmask) - 1 : 31;  // the nearest prefix ends the walk
+            const unsigned need = p == 31 ? 0xffffffffu : (2u << p) - 1u;
+            if ((vmask & need) == need) {
+                uint32_t x = lane <= p ? (uint32_t)w : 0u;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                acc += x;
+                if (pmask) break;
+                j -= 32;
+                continue;
+            }
+            if (++polls > SCAN_POLL_LIMIT) {
+                ok = false;
+                break;
+            }
+        }
+        if (lane == 0) {
+            atomicExch(status + tile, tag | SCAN_PFX | (acc + tot));
+            s_prefix = acc;
+            if (!ok && err) atomicOr(err, ST_TIMEOUT);
+        }
+    }
+    __syncthreads();
+    run += s_prefix;
+#pragma unroll
+    for (int i = 0; i < SC_ITEMS; i++) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+    if (tile == gridDim.x - 1 && threadIdx.x == 0) {
+        if (total_out) *total_out = s_prefix + tot;
+        atomicAdd(hdr + 1, 1u);  // every CTA has read the epoch: the next scan takes the next one
+    }
+}
 }  // namespace
 
-size_t scan_tmp_bytes(int64_t n) {
-    size_t bytes = 0;
-    int64_t m = n;
-    while (m > SC_TILE) {
-        m = (m + SC_TILE - 1) / SC_TILE;
-        bytes += ((size_t)m + 64) * sizeof(uint32_t);
-    }
-    return bytes + 256;
+size_t scan_state_bytes(int64_t n) {
+    const int64_t tiles = (n + SC_TILE - 1) / SC_TILE;
+    return 16 + sizeof(unsigned long long) * (size_t)(tiles + 2);
 }
 
-// one block, 1024 threads, walks the whole array in chunks carrying the running prefix: one
-// launch instead of three for the small arrays of the sorts and of the tile lists.  A thread
-// takes 4 consecutive items, so a warp reads 512 contiguous bytes per load (16 items per thread
-// were measured slower: the 64-byte stride between threads breaks the coalescing).
-__global__ void __launch_bounds__(1024) k_scan_single(const uint32_t *in, uint32_t *out, int64_t n,
-                                                      uint32_t *total_out) {
-    __shared__ uint32_t wt[32];
-    __shared__ uint32_t carry;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    constexpr int IT = 4;
-    for (int64_t base = 0; base < n; base += 1024 * IT) {
-        const int64_t i0 = base + (int64_t)threadIdx.x * IT;
-        uint32_t v[IT], sum = 0;
-#pragma unroll
-        for (int k = 0; k < IT; k++) {
-            v[k] = (i0 + k < n) ? in[i0 + k] : 0u;
-            sum += v[k];
-        }
-        const uint32_t inc = warp_incl_scan_u32(sum);
-        if (lane == 31) wt[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-            const uint32_t t = wt[lane];
-            const uint32_t ti = warp_incl_scan_u32(t);
-            wt[lane] = ti - t;
-        }
-        __syncthreads();
-        uint32_t run = carry + wt[warp] + inc - sum;
-#pragma unroll
-        for (int k = 0; k < IT; k++) {
-            if (i0 + k < n) out[i0 + k] = run;
-            run += v[k];
-        }
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = run;
-        __syncthreads();
-    }
-    if (total_out && threadIdx.x == 0) *total_out = carry;
-}
-
-cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, bool write_total, void *tmp,
-                               cudaStream_t s) {
+cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, bool write_total, void *state,
+                               cudaStream_t s, unsigned *err) {
     if (n <= 0) {
         if (write_total) return cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
         return cudaSuccess;
     }
-    if (n <= 65536) {
-        k_scan_single<<<1, 1024, 0, s>>>(in, out, n, write_total ? out + n : nullptr);
-        SDF_LAUNCHED(1);
-        return cudaGetLastError();
-    }
-    int64_t nb = (n + SC_TILE - 1) / SC_TILE;
+    const int64_t nb = (n + SC_TILE - 1) / SC_TILE;
     if (nb == 1) {
         k_scan_apply<<<1, SC_THREADS, 0, s>>>(in, out, n, nullptr, write_total ? out + n : nullptr);
-        SDF_LAUNCHED(1);
-        return cudaGetLastError();
+    } else {
+        unsigned *hdr = reinterpret_cast<unsigned *>(state);
+        k_scan_chained<<<(unsigned)nb, SC_THREADS, 0, s>>>(in, out, n, hdr,
+                                                          reinterpret_cast<unsigned long long *>(hdr + 4),
+                                                          write_total ? out + n : nullptr, err);
     }
-    uint32_t *sums = reinterpret_cast<uint32_t *>(tmp);
-    void *rest = sums + nb + 64;
-    k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, sums);
-    SDF_LAUNCHED(1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = scan_exclusive_u32(sums, sums, nb, false, rest, s);
-    if (e != cudaSuccess) return e;
-    k_scan_apply<<<(unsigned)nb, SC_THREADS, 0, s>>>(in, out, n, sums, write_total ? out + n : nullptr);
     SDF_LAUNCHED(1);
     return cudaGetLastError();
 }
@@ -285,7 +305,7 @@ int rs_items(int64_t n) {
 
 template <int ITEMS>
 cudaError_t rs_passes(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int64_t n, int bits,
-                      void *tmp, cudaStream_t s) {
+                      void *tmp, void *scan_state, cudaStream_t s, unsigned *err) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_rs_scatter<ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -296,7 +316,6 @@ cudaError_t rs_passes(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     constexpr int TILE = RS_THREADS * ITEMS;
     int64_t nb = (n + TILE - 1) / TILE;
     uint32_t *hist = reinterpret_cast<uint32_t *>(tmp);
-    void *scan_tmp = hist + nb * RADIX + 64;
     int passes = (bits + 7) / 8;
     uint64_t *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
@@ -306,7 +325,7 @@ cudaError_t rs_passes(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
         SDF_LAUNCHED(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        e = scan_exclusive_u32(hist, hist, nb * RADIX, false, scan_tmp, s);
+        e = scan_exclusive_u32(hist, hist, nb * RADIX, false, scan_state, s, err);
         if (e != cudaSuccess) return e;
         k_rs_scatter<ITEMS><<<(unsigned)nb, RS_THREADS, rs_smem<ITEMS>(), s>>>(ki, vi, ko, vo, n, shift, hist, nb);
         SDF_LAUNCHED(1);
@@ -325,22 +344,27 @@ cudaError_t rs_passes(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
 }
 }  // namespace
 
-// scratch of a sort of at most n keys: sized for the smallest tile (the most tiles), so that it
-// also holds the histograms of any shorter sort, whatever tile size that one picks
+// histograms of a sort of at most n keys: sized for the smallest tile (the most tiles), so that
+// they also hold those of any shorter sort, whatever tile size that one picks
 size_t radix_tmp_bytes(int64_t n) {
     const int64_t tile = (int64_t)RS_THREADS * 2;
     int64_t nb = (n + tile - 1) / tile;
-    size_t hist = ((size_t)nb * RADIX + 64) * sizeof(uint32_t);
-    return hist + scan_tmp_bytes(nb * RADIX) + 256;
+    return ((size_t)nb * RADIX + 64) * sizeof(uint32_t);
+}
+
+// the scan state a sort of at most n keys needs (its digit histograms are scanned)
+size_t radix_scan_state_bytes(int64_t n) {
+    const int64_t tile = (int64_t)RS_THREADS * 2;
+    return scan_state_bytes(((n + tile - 1) / tile) * RADIX);
 }
 
 cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int64_t n,
-                           int bits, void *tmp, cudaStream_t s) {
+                           int bits, void *tmp, void *scan_state, cudaStream_t s, unsigned *err) {
     if (n <= 1 || bits <= 0) return cudaSuccess;
     switch (rs_items(n)) {
-    case 8: return rs_passes<8>(keys, vals, keys_alt, vals_alt, n, bits, tmp, s);
-    case 4: return rs_passes<4>(keys, vals, keys_alt, vals_alt, n, bits, tmp, s);
-    default: return rs_passes<2>(keys, vals, keys_alt, vals_alt, n, bits, tmp, s);
+    case 8: return rs_passes<8>(keys, vals, keys_alt, vals_alt, n, bits, tmp, scan_state, s, err);
+    case 4: return rs_passes<4>(keys, vals, keys_alt, vals_alt, n, bits, tmp, scan_state, s, err);
+    default: return rs_passes<2>(keys, vals, keys_alt, vals_alt, n, bits, tmp, scan_state, s, err);
     }
 }
 

@@ -17,6 +17,7 @@ enum : unsigned {
     ST_PAIR_OVERFLOW = 8u,   // (tile, region) pair list too small: grow and rerun
     ST_PATCH_OVERFLOW = 16u, // FP64 re-decision list too small: grow and rerun
     ST_LIST_OVERFLOW = 32u,  // the caller's compact band list is too short (its count holds the length)
+    ST_TIMEOUT = 64u,        // a bounded device wait (the scan's look-back) ran out
 };
 
 // vertex / edge classes (Section 3.1, Section 3.2)
@@ -152,15 +153,20 @@ void count_launches(int64_t n);
 
 // ----------------------------------------------------------------------------- scans and sorts (scan_sort.cu)
 // Exclusive scan of n uint32 values (in may equal out); out[n] receives the total when
-// write_total is set.  tmp must hold scan_tmp_bytes(n) bytes.
-size_t scan_tmp_bytes(int64_t n);
-cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, bool write_total, void *tmp,
-                               cudaStream_t s);
+// write_total is set.  One launch (decoupled look-back).  state holds scan_state_bytes(n) bytes,
+// zeroed before its first scan; every scan leaves it ready for the next one issued after it on
+// the same stream (any n up to the size it was made for).  A look-back wait that runs out sets
+// ST_TIMEOUT in *err (nullable).
+size_t scan_state_bytes(int64_t n);
+cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, bool write_total, void *state,
+                               cudaStream_t s, unsigned *err);
 // Stable LSD radix sort of (keys, vals) on bits [0, bits).  Buffers *_alt are ping-pong
-// scratch of the same size; the result ends in keys/vals.
+// scratch of the same size; the result ends in keys/vals.  tmp holds radix_tmp_bytes(n) bytes of
+// histograms; scan_state is a scan state (as above) of radix_scan_state_bytes(n) bytes.
 size_t radix_tmp_bytes(int64_t n);
+size_t radix_scan_state_bytes(int64_t n);
 cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int64_t n,
-                           int bits, void *tmp, cudaStream_t s);
+                           int bits, void *tmp, void *scan_state, cudaStream_t s, unsigned *err);
 
 // ----------------------------------------------------------------------------- small reads (scan_sort.cu)
 // Reads up to 4 small device values (counters, sizes, status words) into host variables and
