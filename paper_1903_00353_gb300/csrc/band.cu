@@ -898,8 +898,8 @@ __device__ __forceinline__ void fill_chunk(const Prob *P, const long long *tile_
 
 // Persistent tile kernel over all tiles of all problems of a batch.  Two work queues, each with
 // its own atomic ticket: the band tiles (one per item, largest first for batches) and chunks of
-// FILL_CHUNK empty tiles.  Half of the CTAs start on the empty chunks, the others on the band
-// tiles, and a CTA whose queue runs dry takes work from the other one.  A band tile merges its
+// FILL_CHUNK empty tiles.  The CTAs of a fifth of the SMs start on the empty chunks, the others on
+// the band tiles, and a CTA whose queue runs dry takes work from the other one.  A band tile merges its
 // regions' candidates in shared memory and writes its points; an empty tile is written +inf
 // (Algorithm 1's initial value).  The dense output goes out with streaming (evict-first) stores,
 // so that the write stream does not push the feature records that the band work reads out of
@@ -922,7 +922,14 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
     const int64_t n_chunks = dense ? (n_empty + FILL_CHUNK - 1) / FILL_CHUNK : 0;  // no field: no +inf fill
     for (;;) {
         if (threadIdx.x == 0) {
-            const bool filler = blockIdx.x >= gridDim.x / 2;
+            // The CTAs of every fifth SM start on the fill queue, the others on the band tiles.  An
+            // SM that writes +inf at full rate slows the band work of its other CTAs nearly as much
+            // as the fill is worth, so the fill goes to a few SMs, which take band tiles once it
+            // is done (measured on the 2.1 M-triangle knot at 1024^3: 1.91 ms against 2.01 ms with
+            // half of the CTAs of every SM filling, and 1.37 ms for the band work alone).
+            unsigned smid;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            const bool filler = smid % 5 == 0;
             long long w = -1;
             int kind = 0;
             for (int q = 0; q < 2 && w < 0; q++) {
@@ -1166,7 +1173,7 @@ __device__ __forceinline__ Cand64 vert_cand64(const Feat &F, double3 p, int v) {
 // fans of the FP32 winner's vertices.  The sign is that of (p - q).N with N the FP64 pseudonormal
 // of the feature holding the closest point q (face normal, n1 + n2, or N_alpha, Eq. 8).
 template <int TY, int TZ>
-__global__ void k_patch(const Prob *P, const long long *tile_base, Outputs o) {
+__global__ void __launch_bounds__(256) k_patch(const Prob *P, const long long *tile_base, Outputs o) {
     const int lane = threadIdx.x & 31;
     const int64_t wid0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1269,7 +1276,7 @@ __global__ void k_patch(const Prob *P, const long long *tile_base, Outputs o) {
         // normal's direction error (u for faces and edges, rounded from FP64 normals; tau_v for
         // N_alpha); otherwise the FP64 pseudonormal (Eq. 8 for a vertex).  The fallback is rare: it
         // needs p within about 1e-6 |p - q| of the pseudonormal's plane.
-        const double pql = sqrt(ddot3(pq, pq));
+        const double pq2 = ddot3(pq, pq);
         double3 N = make_double3(0, 0, 0);
         double nerr = 0.0;
         if (out_id < F.T) {
@@ -1282,7 +1289,10 @@ __global__ void k_patch(const Prob *P, const long long *tile_base, Outputs o) {
             N = d3(f3(__ldg(F.vert_rec + 3 * (out_id - F.T - F.E) + 1)));
             nerr = (double)__uint_as_float(F.prec[PREC_TAU_V]) + 4e-7;
         }
-        const bool sure = fabs(ddot3(pq, N)) > 2.0 * nerr * pql * sqrt(ddot3(N, N)) + 1e-300;
+        // |(p - q).N| > 2 nerr |p - q| |N|, squared (no FP64 square roots: they are long sequences
+        // on this part's FP64 pipe, which bounds this kernel)
+        const double sN = ddot3(pq, N);
+        const bool sure = sN * sN > 4.0 * nerr * nerr * pq2 * ddot3(N, N) + 1e-300;
         if (sure) {
             // the stored normal decides
         } else if (out_id < F.T) {
@@ -1307,12 +1317,14 @@ __global__ void k_patch(const Prob *P, const long long *tile_base, Outputs o) {
             N = make_double3(wsum(acc.x), wsum(acc.y), wsum(acc.z));
         }
         const double s = ddot3(pq, N);
-        const double d = sqrt(best.d2);
         if (lane == 0) {
             float val = INFINITY;
             int w = -1;
-            if (d < (double)g.w) {
-                val = (float)(s < 0.0 ? -d : d);
+            // |d| < w decided on the squares (w^2 is exact in FP64); the value is the FP32 square root
+            // of the FP64 square distance (within an FP32 ulp of the rounded FP64 distance)
+            if (best.d2 < (double)g.w * (double)g.w) {
+                const float d = sqrtf((float)best.d2);
+                val = s < 0.0 ? -d : d;
                 w = out_id;
             }
             if (dist) dist[idx] = val;
@@ -1578,6 +1590,18 @@ template <int TY, int TZ, bool LIST> static int tile_blocks_per_sm() {
                              (int)sizeof(TileSmem<TY, TZ>));
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tile<TY, TZ, LIST>, NT, sizeof(TileSmem<TY, TZ>));
         if (b <= 0) b = 1;
+    }
+    return b;
+}
+
+// CTAs of k_patch resident at once on the device: its grid, so that its grid-stride loop over the
+// queued points runs in a single wave
+template <int TY, int TZ> static int patch_blocks() {
+    static int b = 0;
+    if (!b) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_patch<TY, TZ>, 256, 0);
+        if (b <= 0) b = 1;
+        b *= num_sms();
     }
     return b;
 }
@@ -1961,7 +1985,7 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
     if (ev) SDF_TRY(record_event(ev[2], s));
-    k_patch<TY, TZ><<<4 * num_sms(), 256, 0, s>>>(sc.probs, sc.tbase, o);
+    k_patch<TY, TZ><<<patch_blocks<TY, TZ>(), 256, 0, s>>>(sc.probs, sc.tbase, o);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
     if (sc.fprobs)
@@ -1994,7 +2018,7 @@ static int launch_cell_loop(int n, long long f_tot, const Scratch &sc, cudaStrea
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
     if (ev) SDF_TRY(record_event(ev[2], s));
-    k_patch<8, 8><<<4 * num_sms(), 256, 0, s>>>(sc.probs, sc.tbase, o);  // no pairs: fan search
+    k_patch<8, 8><<<patch_blocks<8, 8>(), 256, 0, s>>>(sc.probs, sc.tbase, o);  // no pairs: fan search
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
     if (sc.fprobs)

@@ -323,15 +323,42 @@ __device__ __forceinline__ float3 normalized(float3 v) {
     return r * v;
 }
 
-// Largest value over the warp, taken into the counter word with one atomic (v >= 0).
-__device__ __forceinline__ void warp_max_into(unsigned *word, float v) {
+// Block-wide reductions of one value per thread into a device counter, one atomic per block (the
+// records kernels loop over their items with a fixed grid, so a build makes a few thousand
+// atomics on these few words instead of one per warp: same-address atomics serialise in L2).
+// Every thread of the block must call them.
+__device__ __forceinline__ float block_reduce_max(float v) {  // v >= 0; the result is in thread 0
+    __shared__ float part[BT / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(word, __float_as_uint(v));
+    __syncthreads();  // the array may still be read by a previous reduction
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < BT / 32; w++) v = fmaxf(v, part[w]);
+    return v;
+}
+// the largest value (v >= 0) into a word holding FP32 bits, skipping the atomic when it is no larger
+__device__ __forceinline__ void block_max_into(unsigned *word, float v) {
+    v = block_reduce_max(v);
+    if (threadIdx.x == 0 && v > 0.f && __float_as_uint(v) > *(volatile unsigned *)word)
+        atomicMax(word, __float_as_uint(v));
+}
+__device__ __forceinline__ void block_count_into(unsigned long long *word, unsigned c) {
+    __shared__ unsigned part[BT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < BT / 32; w++) c += part[w];
+        if (c) atomicAdd(word, (unsigned long long)c);
+    }
 }
 
 // Sums of K values over a block of BT threads, added to K counters with one atomic each (FP32
-// within the block, FP64 across blocks).  Every thread of the block must call it.
+// within the block, FP64 across blocks).
 template <int K>
 __device__ __forceinline__ void block_sums_into(double *words, float (&v)[K]) {
     __shared__ float part[BT / 32][K];
@@ -339,6 +366,7 @@ __device__ __forceinline__ void block_sums_into(double *words, float (&v)[K]) {
     for (int k = 0; k < K; k++)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    __syncthreads();
     if ((threadIdx.x & 31) == 0)
 #pragma unroll
         for (int k = 0; k < K; k++) part[threadIdx.x >> 5][k] = v[k];
@@ -350,8 +378,11 @@ __device__ __forceinline__ void block_sums_into(double *words, float (&v)[K]) {
     }
 }
 
-// Face records, and the precision terms and box moments of the faces (every thread of the grid
-// takes part in the warp reductions, so the early-exit threads contribute zeros).  The unit normal and the plane
+// fixed grid of the records kernels: a few blocks per SM of this part, each looping over its items
+constexpr int REC_BLOCKS = 8 * 152;
+
+// Face records, and the precision terms and box moments of the faces (a fixed grid looping over
+// the faces; the block reductions at the end take every thread).  The unit normal and the plane
 // offset -n.a are computed in FP64 from the FP32 corners (their differences are exact in FP64)
 // and rounded once, so the stored normal is within about u = 2^-24 of the exact normal of the
 // corners however thin the triangle.  The side planes n x (edge) are formed in FP32 from it: the
@@ -361,18 +392,19 @@ __device__ __forceinline__ void block_sums_into(double *words, float (&v)[K]) {
 // planes (k_edge_records) have the same bound with the edge length.  The records kernels keep the
 // maxima of tau_a = 10 u D and tau_b = 10 u (with margin) and of the coordinate magnitude; the
 // narrow band adds tau_a + tau_b W to its FP32 error bound (the windows in band.cu).
-__global__ void k_face_records(const int32_t *face_vid, const float *vpos, int64_t T, float4 *face_rec,
-                               float4 *face_box, DevCounters *ctr) {
-    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    float m_abs = 0.f, tau_a = 0.f, tau_b = 0.f;
-    if (f < T) {
+__global__ void __launch_bounds__(BT) k_face_records(const int32_t *face_vid, const float *vpos, int64_t T,
+                                                     float4 *face_rec, float4 *face_box, DevCounters *ctr) {
+    float m_abs = 0.f, tau_a = 0.f;
+    float mom[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bool degenerate = false;
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < T; f += (int64_t)gridDim.x * blockDim.x) {
         float3 a = load_vpos(vpos, face_vid[3 * f]), b = load_vpos(vpos, face_vid[3 * f + 1]),
                c = load_vpos(vpos, face_vid[3 * f + 2]);
         const double3 A = d3(a), E1 = d3(b) - A, E2 = d3(c) - A;
         const double3 CR = dcross3(E1, E2);
         double len = sqrt(ddot3(CR, CR));
         if (!(len > 1e-14 * (ddot3(E1, E1) + ddot3(E2, E2)))) {  // zero area (Section 4)
-            atomicOr(&ctr->status, ST_DEGENERATE);
+            degenerate = true;
             len = fmax(len, 1e-300);
         }
         const double3 N = (1.0 / len) * CR;
@@ -382,29 +414,23 @@ __global__ void k_face_records(const int32_t *face_vid, const float *vpos, int64
         face_rec[4 * f + 1] = plane_through(normalized(cross3(n, b - a)), a);
         face_rec[4 * f + 2] = plane_through(normalized(cross3(n, c - b)), b);
         face_rec[4 * f + 3] = plane_through(normalized(cross3(n, a - c)), c);
-        face_box[2 * f + 0] = make_float4(fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)),
-                                          fminf(a.z, fminf(b.z, c.z)), 0.f);
-        face_box[2 * f + 1] = make_float4(fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)),
-                                          fmaxf(a.z, fmaxf(b.z, c.z)), 0.f);
-        const float3 lo = f3(face_box[2 * f]), hi = f3(face_box[2 * f + 1]);
-        m_abs = fmaxf(fmaxf(fmaxf(fabsf(lo.x), fabsf(hi.x)), fmaxf(fabsf(lo.y), fabsf(hi.y))),
-                      fmaxf(fabsf(lo.z), fabsf(hi.z)));
+        const float3 lo = make_float3(fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)), fminf(a.z, fminf(b.z, c.z)));
+        const float3 hi = make_float3(fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)), fmaxf(a.z, fmaxf(b.z, c.z)));
+        face_box[2 * f + 0] = make_float4(lo.x, lo.y, lo.z, 0.f);
+        face_box[2 * f + 1] = make_float4(hi.x, hi.y, hi.z, 0.f);
+        m_abs = fmaxf(m_abs, fmaxf(fmaxf(fmaxf(fabsf(lo.x), fabsf(hi.x)), fmaxf(fabsf(lo.y), fabsf(hi.y))),
+                                   fmaxf(fabsf(lo.z), fabsf(hi.z))));
         const float3 e3 = c - b;
         const float diam = sqrtf(fmaxf(fmaxf(dot3(b - a, b - a), dot3(c - a, c - a)), dot3(e3, e3)));
-        tau_b = 10.f * U32;
-        tau_a = tau_b * diam * 1.001f;
+        tau_a = fmaxf(tau_a, 10.f * U32 * diam * 1.001f);
+        const float bx = hi.x - lo.x, by = hi.y - lo.y, bz = hi.z - lo.z;
+        mom[0] += bx; mom[1] += by; mom[2] += bz;
+        mom[3] += bx * by; mom[4] += bx * bz; mom[5] += by * bz; mom[6] += bx * by * bz;
     }
-    warp_max_into(&ctr->prec[PREC_MESH_M], m_abs);
-    warp_max_into(&ctr->prec[PREC_TAU_A], tau_a);
-    warp_max_into(&ctr->prec[PREC_TAU_B], tau_b);
-    float bx = 0.f, by = 0.f, bz = 0.f;
-    if (f < T) {
-        const float4 lo = face_box[2 * f], hi = face_box[2 * f + 1];
-        bx = hi.x - lo.x;
-        by = hi.y - lo.y;
-        bz = hi.z - lo.z;
-    }
-    float mom[7] = {bx, by, bz, bx * by, bx * bz, by * bz, bx * by * bz};
+    if (degenerate) atomicOr(&ctr->status, ST_DEGENERATE);
+    block_max_into(&ctr->prec[PREC_MESH_M], m_abs);
+    block_max_into(&ctr->prec[PREC_TAU_A], tau_a);
+    block_max_into(&ctr->prec[PREC_TAU_B], T > 0 ? 10.f * U32 : 0.f);
     block_sums_into<7>(ctr->box_mom, mom);
 }
 
@@ -418,46 +444,43 @@ __device__ double3 face_normal_fp64(const int32_t *face_vid, const float *vpos, 
 // edge wedge (Section 8.2): unit direction t (va -> vb, the direction in face f1), the planes
 // (p - a).m1 <= 0 and (p - a).m2 <= 0 with m1 = n1 x t into face 1 and m2 = n2 x (-t) into face 2,
 // and the edge pseudonormal n1 + n2.  Class from d = (ab x n1) . n2 (FP32, FP64 when near zero).
-__global__ void k_edge_records(const int4 *edge_vf, const int32_t *face_vid, const float *vpos,
-                               const float4 *face_rec, int64_t E, float4 *edge_rec, int8_t *edge_class,
-                               DevCounters *ctr) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= E) return;
-    int4 q = edge_vf[e];
-    float3 a = load_vpos(vpos, q.x), b = load_vpos(vpos, q.y);
-    float3 n1 = f3(face_rec[4 * q.z]), n2 = f3(face_rec[4 * q.w]);
-    float3 ab = b - a;
-    float L = sqrtf(dot3(ab, ab));
-    float3 t = (1.f / L) * ab;
-    float3 m1 = normalized(cross3(n1, t));
-    float3 m2 = normalized(cross3(n2, make_float3(-t.x, -t.y, -t.z)));
-    float3 np = n1 + n2;
-    edge_rec[5 * e + 0] = make_float4(a.x, a.y, a.z, L);
-    edge_rec[5 * e + 1] = make_float4(t.x, t.y, t.z, dot3(t, a));
-    edge_rec[5 * e + 2] = make_float4(-m1.x, -m1.y, -m1.z, dot3(m1, a));
-    edge_rec[5 * e + 3] = make_float4(-m2.x, -m2.y, -m2.z, dot3(m2, a));
-    edge_rec[5 * e + 4] = make_float4(np.x, np.y, np.z, sqrtf(dot3(np, np)));  // (n1 + n2, |n1 + n2|)
-    float d = dot3(cross3(t, n1), n2);
-    int8_t cls;
-    if (fabsf(d) > 2e-6f) {
-        cls = d > 0.f ? CLS_CONVEX : CLS_CONCAVE;
-    } else {  // filtered predicate: decide near-flat edges in FP64
-        double3 A = d3(a), B = d3(b);
-        double3 N1 = face_normal_fp64(face_vid, vpos, q.z), N2 = face_normal_fp64(face_vid, vpos, q.w);
-        double3 AB = B - A;
-        double dd = ddot3(dcross3(AB, N1), N2);
-        double tol = 1e-12 * sqrt(ddot3(AB, AB));
-        cls = dd > tol ? CLS_CONVEX : (dd < -tol ? CLS_CONCAVE : CLS_FLAT);
+__global__ void __launch_bounds__(BT) k_edge_records(const int4 *edge_vf, const int32_t *face_vid, const float *vpos,
+                                                     const float4 *face_rec, int64_t E, float4 *edge_rec,
+                                                     int8_t *edge_class, DevCounters *ctr) {
+    unsigned ncv = 0, ncc = 0;  // class counts of this thread's edges
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        const int4 q = edge_vf[e];
+        const float3 a = load_vpos(vpos, q.x), b = load_vpos(vpos, q.y);
+        const float3 n1 = f3(face_rec[4 * q.z]), n2 = f3(face_rec[4 * q.w]);
+        const float3 ab = b - a;
+        const float L = sqrtf(dot3(ab, ab));
+        const float3 t = (1.f / L) * ab;
+        const float3 m1 = normalized(cross3(n1, t));
+        const float3 m2 = normalized(cross3(n2, make_float3(-t.x, -t.y, -t.z)));
+        const float3 np = n1 + n2;
+        edge_rec[5 * e + 0] = make_float4(a.x, a.y, a.z, L);
+        edge_rec[5 * e + 1] = make_float4(t.x, t.y, t.z, dot3(t, a));
+        edge_rec[5 * e + 2] = make_float4(-m1.x, -m1.y, -m1.z, dot3(m1, a));
+        edge_rec[5 * e + 3] = make_float4(-m2.x, -m2.y, -m2.z, dot3(m2, a));
+        edge_rec[5 * e + 4] = make_float4(np.x, np.y, np.z, sqrtf(dot3(np, np)));  // (n1 + n2, |n1 + n2|)
+        const float d = dot3(cross3(t, n1), n2);
+        int8_t cls;
+        if (fabsf(d) > 2e-6f) {
+            cls = d > 0.f ? CLS_CONVEX : CLS_CONCAVE;
+        } else {  // filtered predicate: decide near-flat edges in FP64
+            const double3 A = d3(a), B = d3(b);
+            const double3 N1 = face_normal_fp64(face_vid, vpos, q.z), N2 = face_normal_fp64(face_vid, vpos, q.w);
+            const double3 AB = B - A;
+            const double dd = ddot3(dcross3(AB, N1), N2);
+            const double tol = 1e-12 * sqrt(ddot3(AB, AB));
+            cls = dd > tol ? CLS_CONVEX : (dd < -tol ? CLS_CONCAVE : CLS_FLAT);
+        }
+        edge_class[e] = cls;
+        ncv += cls == CLS_CONVEX;
+        ncc += cls == CLS_CONCAVE;
     }
-    edge_class[e] = cls;
-    // class counts: one atomic per warp and class (same-address atomics serialise in L2)
-    const unsigned act = __activemask();
-    const unsigned ncv = __popc(__ballot_sync(act, cls == CLS_CONVEX));
-    const unsigned ncc = __popc(__ballot_sync(act, cls == CLS_CONCAVE));
-    if ((threadIdx.x & 31) == __ffs(act) - 1) {
-        if (ncv) atomicAdd(&ctr->cls[6], (unsigned long long)ncv);
-        if (ncc) atomicAdd(&ctr->cls[7], (unsigned long long)ncc);
-    }
+    block_count_into(&ctr->cls[6], ncv);
+    block_count_into(&ctr->cls[7], ncc);
 }
 
 __device__ __forceinline__ float corner_angle(float3 e1, float3 e2) {
@@ -491,168 +514,176 @@ __device__ __forceinline__ bool gor8(bool b) {
 // N_alpha = sum alpha_i n_i (Eq. 8); one plane (p - v).e_j <= 0 per incident edge (the region where
 // no incident edge leads closer than v); the class from the signs of (v_n - v).N_alpha over the
 // neighbours (FP32 when clear, FP64 otherwise); and a cone bounding the vertex region.
-__global__ void k_vertex_records(const int32_t *vert_start, const int32_t *vert_corner, const int32_t *face_vid,
-                                 const float *vpos, const float4 *face_rec, int64_t V, float4 *vert_rec,
-                                 float4 *vert_plane, int8_t *vert_class, DevCounters *ctr) {
-    const int64_t gl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t v = gl / VL;
-    const int sub = (int)(gl % VL);
-    const bool valid = v < V;
-    const int s0 = valid ? vert_start[v] : 0, s1 = valid ? vert_start[v + 1] : 0;
-    const float3 p = valid ? load_vpos(vpos, (int)v) : make_float3(0.f, 0.f, 0.f);
-    // pass 1: pseudonormal and region planes
-    float3 N = make_float3(0.f, 0.f, 0.f);
-    float asum = 0.f;
-    for (int i = s0 + sub; i < s1; i += VL) {
-        const int c = vert_corner[i];
-        const int f = c / 3, k = c - 3 * f;
-        const float3 xn = load_vpos(vpos, face_vid[3 * f + (k + 1) % 3]);
-        const float3 xp = load_vpos(vpos, face_vid[3 * f + (k + 2) % 3]);
-        const float3 e1 = xn - p, e2 = xp - p;
-        const float alpha = corner_angle(e1, e2);
-        asum += alpha;
-        N = N + alpha * f3(face_rec[4 * f]);
-        const float3 ej = normalized(e1);
-        vert_plane[i] = make_float4(-ej.x, -ej.y, -ej.z, dot3(ej, p));
-    }
-    N = make_float3(gsum8(N.x), gsum8(N.y), gsum8(N.z));
-    asum = gsum8(asum);
-    const float Nlen = sqrtf(dot3(N, N));
-    const float3 Nu = (Nlen > 0.f ? 1.f / Nlen : 0.f) * N;
-    // Direction error of the unit pseudonormal: each term alpha_i n_i errs by at most
-    // alpha_i 10 u (the stored face normal within u, the angle's rounding) and the sum of deg terms
-    // adds deg u sum(alpha); the normalisation at most doubles the relative error.
-    // tau_v = 2 sum(alpha) (deg + 10) u / |N_alpha|, kept as a maximum (per unit distance: the sign
-    // predicate N^.(p - v) errs by tau_v |p - v| from it).
-    {
-        float tv = 0.f;
-        if (valid && sub == 0 && s1 > s0)
-            tv = Nlen > 0.f ? fminf(2.f * asum * (float)(s1 - s0 + 10) * U32 / Nlen * 1.001f, 1.f) : 1.f;
-        warp_max_into(&ctr->prec[PREC_TAU_V], tv);
-    }
-    __syncwarp();  // the group's planes are written before they are read back
-    // pass 2: classification (FP32 with an error margin), convexity and the normal spread
-    bool below = false, above = false, unsure = false, cvx = true, ccv = true;
-    float cmin = 1.f;
-    for (int i = s0 + sub; i < s1; i += VL) {
-        const int c = vert_corner[i];
-        const float3 ej = -1.f * f3(vert_plane[i]);  // unit direction to the next neighbour
-        const float3 dv = load_vpos(vpos, face_vid[3 * (c / 3) + ((c % 3) + 1) % 3]) - p;
-        const float d = dot3(dv, N);
-        const float bound = 2e-6f * sqrtf(dot3(dv, dv)) * Nlen;
-        if (d < -bound) below = true;
-        else if (d > bound) above = true;
-        else unsure = true;
-        const float3 nf = f3(face_rec[4 * (c / 3)]);
-        cmin = fminf(cmin, dot3(nf, Nu));
-        for (int b = s0; b < s1; b++) {  // every incident edge against this face's plane
-            const float dd = -dot3(nf, f3(vert_plane[b]));
-            cvx = cvx && dd <= 1e-4f;
-            ccv = ccv && dd >= -1e-4f;
+__global__ void __launch_bounds__(BT) k_vertex_records(const int32_t *vert_start, const int32_t *vert_corner,
+                                                       const int32_t *face_vid, const float *vpos,
+                                                       const float4 *face_rec, int64_t V, float4 *vert_rec,
+                                                       float4 *vert_plane, int8_t *vert_class, DevCounters *ctr) {
+    float tv_max = 0.f;
+    unsigned ncls[4] = {0, 0, 0, 0};  // convex, concave, flat and saddle vertices of this thread
+    // a warp-uniform loop (the groups' shuffles take the whole warp): item gl is lane gl % VL of
+    // vertex gl / VL
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); g0 < V * VL; g0 += stride) {
+        const int64_t gl = g0 + (threadIdx.x & 31);
+        const int64_t v = gl / VL;
+        const int sub = (int)(gl % VL);
+        const bool valid = v < V;
+        const int s0 = valid ? vert_start[v] : 0, s1 = valid ? vert_start[v + 1] : 0;
+        const float3 p = valid ? load_vpos(vpos, (int)v) : make_float3(0.f, 0.f, 0.f);
+        // pass 1: pseudonormal and region planes
+        float3 N = make_float3(0.f, 0.f, 0.f);
+        float asum = 0.f;
+        for (int i = s0 + sub; i < s1; i += VL) {
+            const int c = vert_corner[i];
+            const int f = c / 3, k = c - 3 * f;
+            const float3 xn = load_vpos(vpos, face_vid[3 * f + (k + 1) % 3]);
+            const float3 xp = load_vpos(vpos, face_vid[3 * f + (k + 2) % 3]);
+            const float3 e1 = xn - p, e2 = xp - p;
+            const float alpha = corner_angle(e1, e2);
+            asum += alpha;
+            N = N + alpha * f3(face_rec[4 * f]);
+            const float3 ej = normalized(e1);
+            vert_plane[i] = make_float4(-ej.x, -ej.y, -ej.z, dot3(ej, p));
         }
-        (void)ej;
-    }
-    below = gor8(below);
-    above = gor8(above);
-    unsure = gor8(unsure);
-    cvx = !gor8(!cvx);
-    ccv = !gor8(!ccv);
-    cmin = gmin8(cmin);
-    // Bound of the vertex region {y : y.e_j <= 0}.  Locally convex (every incident edge below every
-    // incident face plane): the cone spanned by the face normals; locally concave: by their
-    // negatives; otherwise the extreme rays are searched among +-(e_j x e_l): the deg (deg - 1) / 2
-    // plane pairs are spread over the group's 8 lanes, and each candidate ray is tested against
-    // every plane without early exit, so the lanes of a group stay converged.  A cone is kept only
-    // if all its rays lie within 89 degrees of +N_alpha (or of -N_alpha).  The flags and bounds
-    // below are uniform over the 8 lanes of a vertex after the group reductions.
-    const int deg = s1 - s0;
-    const bool conv_cone = cvx && !ccv && cmin > 0.02f, conc_cone = ccv && !cvx && cmin > 0.02f;
-    const bool search = valid && Nlen > 0.f && !conv_cone && !conc_cone && deg <= 24;
-    bool any = false, all_pos = true, all_neg = true;
-    float cpos = 1.f, cng = 1.f;
-    if (search) {
-        const int npairs = deg * (deg - 1) / 2;
-        for (int pidx = sub; pidx < npairs; pidx += VL) {
-            int a = 0, rem = pidx;  // pair pidx = (a, b), a < b, in row-major order
-            while (rem >= deg - 1 - a) {
-                rem -= deg - 1 - a;
-                a++;
-            }
-            const int b = a + 1 + rem;
-            float3 y = cross3(f3(vert_plane[s0 + a]), f3(vert_plane[s0 + b]));  // planes hold -e
-            const float ly = sqrtf(dot3(y, y));
-            const bool ok = ly > 1e-6f;
-            y = (ok ? 1.f / ly : 0.f) * y;
-            bool fp = ok, fn = ok;  // +y and -y feasible
-            for (int m = s0; m < s1; m++) {
-                const float dm = dot3(y, f3(vert_plane[m]));
-                fp = fp && dm >= -1e-4f;
-                fn = fn && -dm >= -1e-4f;
-            }
-            const float cc = dot3(y, Nu);
-            if (fp) {
-                any = true;
-                if (cc > 0.02f) cpos = fminf(cpos, cc); else all_pos = false;
-                if (cc < -0.02f) cng = fminf(cng, -cc); else all_neg = false;
-            }
-            if (fn) {
-                any = true;
-                if (-cc > 0.02f) cpos = fminf(cpos, -cc); else all_pos = false;
-                if (-cc < -0.02f) cng = fminf(cng, cc); else all_neg = false;
-            }
+        N = make_float3(gsum8(N.x), gsum8(N.y), gsum8(N.z));
+        asum = gsum8(asum);
+        const float Nlen = sqrtf(dot3(N, N));
+        const float3 Nu = (Nlen > 0.f ? 1.f / Nlen : 0.f) * N;
+        // Direction error of the unit pseudonormal: each term alpha_i n_i errs by at most
+        // alpha_i 10 u (the stored face normal within u, the angle's rounding) and the sum of deg terms
+        // adds deg u sum(alpha); the normalisation at most doubles the relative error.
+        // tau_v = 2 sum(alpha) (deg + 10) u / |N_alpha|, kept as a maximum (per unit distance: the sign
+        // predicate N^.(p - v) errs by tau_v |p - v| from it).
+        {
+            float tv = 0.f;
+            if (valid && sub == 0 && s1 > s0)
+                tv = Nlen > 0.f ? fminf(2.f * asum * (float)(s1 - s0 + 10) * U32 / Nlen * 1.001f, 1.f) : 1.f;
+            tv_max = fmaxf(tv_max, tv);
         }
-    }
-    any = gor8(any);
-    all_pos = !gor8(!all_pos);
-    all_neg = !gor8(!all_neg);
-    cpos = gmin8(cpos);
-    cng = gmin8(cng);
-    int8_t my_cls = 99;  // class of the vertex held by lane sub == 0
-    if (valid && sub == 0) {
-        if (unsure) {  // FP64 filtered predicate (rare): recompute N_alpha and the signs in FP64
-            below = above = false;
-            const double3 P = d3(p);
-            double3 ND = make_double3(0, 0, 0);
-            for (int i = s0; i < s1; i++) {
-                const int c = vert_corner[i];
-                const int f = c / 3, k = c - 3 * f;
-                const double3 e1 = d3(load_vpos(vpos, face_vid[3 * f + (k + 1) % 3])) - P;
-                const double3 e2 = d3(load_vpos(vpos, face_vid[3 * f + (k + 2) % 3])) - P;
-                const double3 cr = dcross3(e1, e2);
-                const double alpha = atan2(sqrt(ddot3(cr, cr)), ddot3(e1, e2));
-                ND = ND + alpha * face_normal_fp64(face_vid, vpos, f);
+        __syncwarp();  // the group's planes are written before they are read back
+        // pass 2: classification (FP32 with an error margin), convexity and the normal spread
+        bool below = false, above = false, unsure = false, cvx = true, ccv = true;
+        float cmin = 1.f;
+        for (int i = s0 + sub; i < s1; i += VL) {
+            const int c = vert_corner[i];
+            const float3 ej = -1.f * f3(vert_plane[i]);  // unit direction to the next neighbour
+            const float3 dv = load_vpos(vpos, face_vid[3 * (c / 3) + ((c % 3) + 1) % 3]) - p;
+            const float d = dot3(dv, N);
+            const float bound = 2e-6f * sqrtf(dot3(dv, dv)) * Nlen;
+            if (d < -bound) below = true;
+            else if (d > bound) above = true;
+            else unsure = true;
+            const float3 nf = f3(face_rec[4 * (c / 3)]);
+            cmin = fminf(cmin, dot3(nf, Nu));
+            for (int b = s0; b < s1; b++) {  // every incident edge against this face's plane
+                const float dd = -dot3(nf, f3(vert_plane[b]));
+                cvx = cvx && dd <= 1e-4f;
+                ccv = ccv && dd >= -1e-4f;
             }
-            const double NL = sqrt(ddot3(ND, ND));
-            for (int i = s0; i < s1; i++) {
-                const int c = vert_corner[i];
-                const int f = c / 3, k = c - 3 * f;
-                const double3 dv = d3(load_vpos(vpos, face_vid[3 * f + (k + 1) % 3])) - P;
-                const double d = ddot3(dv, ND);
-                const double tol = 1e-12 * sqrt(ddot3(dv, dv)) * NL;
-                if (d < -tol) below = true;
-                else if (d > tol) above = true;
+            (void)ej;
+        }
+        below = gor8(below);
+        above = gor8(above);
+        unsure = gor8(unsure);
+        cvx = !gor8(!cvx);
+        ccv = !gor8(!ccv);
+        cmin = gmin8(cmin);
+        // Bound of the vertex region {y : y.e_j <= 0}.  Locally convex (every incident edge below every
+        // incident face plane): the cone spanned by the face normals; locally concave: by their
+        // negatives; otherwise the extreme rays are searched among +-(e_j x e_l): the deg (deg - 1) / 2
+        // plane pairs are spread over the group's 8 lanes, and each candidate ray is tested against
+        // every plane without early exit, so the lanes of a group stay converged.  A cone is kept only
+        // if all its rays lie within 89 degrees of +N_alpha (or of -N_alpha).  The flags and bounds
+        // below are uniform over the 8 lanes of a vertex after the group reductions.
+        const int deg = s1 - s0;
+        const bool conv_cone = cvx && !ccv && cmin > 0.02f, conc_cone = ccv && !cvx && cmin > 0.02f;
+        const bool search = valid && Nlen > 0.f && !conv_cone && !conc_cone && deg <= 24;
+        bool any = false, all_pos = true, all_neg = true;
+        float cpos = 1.f, cng = 1.f;
+        if (search) {
+            const int npairs = deg * (deg - 1) / 2;
+            for (int pidx = sub; pidx < npairs; pidx += VL) {
+                int a = 0, rem = pidx;  // pair pidx = (a, b), a < b, in row-major order
+                while (rem >= deg - 1 - a) {
+                    rem -= deg - 1 - a;
+                    a++;
+                }
+                const int b = a + 1 + rem;
+                float3 y = cross3(f3(vert_plane[s0 + a]), f3(vert_plane[s0 + b]));  // planes hold -e
+                const float ly = sqrtf(dot3(y, y));
+                const bool ok = ly > 1e-6f;
+                y = (ok ? 1.f / ly : 0.f) * y;
+                bool fp = ok, fn = ok;  // +y and -y feasible
+                for (int m = s0; m < s1; m++) {
+                    const float dm = dot3(y, f3(vert_plane[m]));
+                    fp = fp && dm >= -1e-4f;
+                    fn = fn && -dm >= -1e-4f;
+                }
+                const float cc = dot3(y, Nu);
+                if (fp) {
+                    any = true;
+                    if (cc > 0.02f) cpos = fminf(cpos, cc); else all_pos = false;
+                    if (cc < -0.02f) cng = fminf(cng, -cc); else all_neg = false;
+                }
+                if (fn) {
+                    any = true;
+                    if (-cc > 0.02f) cpos = fminf(cpos, -cc); else all_pos = false;
+                    if (-cc < -0.02f) cng = fminf(cng, cc); else all_neg = false;
+                }
             }
         }
-        const int8_t cls = below && above ? CLS_SADDLE : (below ? CLS_CONVEX : (above ? CLS_CONCAVE : CLS_FLAT));
-        vert_class[v] = cls;
-        float4 cone = make_float4(0.f, 0.f, 0.f, -2.f);
-        if (Nlen > 0.f) {
-            if (conv_cone) cone = make_float4(Nu.x, Nu.y, Nu.z, cmin - 2e-3f);
-            else if (conc_cone) cone = make_float4(-Nu.x, -Nu.y, -Nu.z, cmin - 2e-3f);
-            else if (search && any && all_pos) cone = make_float4(Nu.x, Nu.y, Nu.z, cpos - 2e-3f);
-            else if (search && any && all_neg) cone = make_float4(-Nu.x, -Nu.y, -Nu.z, cng - 2e-3f);
+        any = gor8(any);
+        all_pos = !gor8(!all_pos);
+        all_neg = !gor8(!all_neg);
+        cpos = gmin8(cpos);
+        cng = gmin8(cng);
+        int8_t my_cls = 99;  // class of the vertex held by lane sub == 0
+        if (valid && sub == 0) {
+            if (unsure) {  // FP64 filtered predicate (rare): recompute N_alpha and the signs in FP64
+                below = above = false;
+                const double3 P = d3(p);
+                double3 ND = make_double3(0, 0, 0);
+                for (int i = s0; i < s1; i++) {
+                    const int c = vert_corner[i];
+                    const int f = c / 3, k = c - 3 * f;
+                    const double3 e1 = d3(load_vpos(vpos, face_vid[3 * f + (k + 1) % 3])) - P;
+                    const double3 e2 = d3(load_vpos(vpos, face_vid[3 * f + (k + 2) % 3])) - P;
+                    const double3 cr = dcross3(e1, e2);
+                    const double alpha = atan2(sqrt(ddot3(cr, cr)), ddot3(e1, e2));
+                    ND = ND + alpha * face_normal_fp64(face_vid, vpos, f);
+                }
+                const double NL = sqrt(ddot3(ND, ND));
+                for (int i = s0; i < s1; i++) {
+                    const int c = vert_corner[i];
+                    const int f = c / 3, k = c - 3 * f;
+                    const double3 dv = d3(load_vpos(vpos, face_vid[3 * f + (k + 1) % 3])) - P;
+                    const double d = ddot3(dv, ND);
+                    const double tol = 1e-12 * sqrt(ddot3(dv, dv)) * NL;
+                    if (d < -tol) below = true;
+                    else if (d > tol) above = true;
+                }
+            }
+            const int8_t cls = below && above ? CLS_SADDLE : (below ? CLS_CONVEX : (above ? CLS_CONCAVE : CLS_FLAT));
+            vert_class[v] = cls;
+            float4 cone = make_float4(0.f, 0.f, 0.f, -2.f);
+            if (Nlen > 0.f) {
+                if (conv_cone) cone = make_float4(Nu.x, Nu.y, Nu.z, cmin - 2e-3f);
+                else if (conc_cone) cone = make_float4(-Nu.x, -Nu.y, -Nu.z, cmin - 2e-3f);
+                else if (search && any && all_pos) cone = make_float4(Nu.x, Nu.y, Nu.z, cpos - 2e-3f);
+                else if (search && any && all_neg) cone = make_float4(-Nu.x, -Nu.y, -Nu.z, cng - 2e-3f);
+            }
+            vert_rec[3 * v + 0] = make_float4(p.x, p.y, p.z, __int_as_float(s0));
+            vert_rec[3 * v + 1] = make_float4(Nu.x, Nu.y, Nu.z, __int_as_float(s1 - s0));
+            vert_rec[3 * v + 2] = cone;
+            my_cls = cls;
         }
-        vert_rec[3 * v + 0] = make_float4(p.x, p.y, p.z, __int_as_float(s0));
-        vert_rec[3 * v + 1] = make_float4(Nu.x, Nu.y, Nu.z, __int_as_float(s1 - s0));
-        vert_rec[3 * v + 2] = cone;
-        my_cls = cls;
+        ncls[0] += my_cls == CLS_CONVEX;
+        ncls[1] += my_cls == CLS_CONCAVE;
+        ncls[2] += my_cls == CLS_FLAT;
+        ncls[3] += my_cls == CLS_SADDLE;
     }
-    // class counts: one atomic per warp and class (same-address atomics serialise in L2)
-    for (int c = 0; c < 4; c++) {
-        const int8_t want = c == 0 ? CLS_CONVEX : (c == 1 ? CLS_CONCAVE : (c == 2 ? CLS_FLAT : CLS_SADDLE));
-        const unsigned n = __popc(__ballot_sync(0xffffffffu, my_cls == want));
-        if ((threadIdx.x & 31) == 0 && n) atomicAdd(&ctr->cls[2 + c], (unsigned long long)n);
-    }
+    block_max_into(&ctr->prec[PREC_TAU_V], tv_max);
+    for (int c = 0; c < 4; c++) block_count_into(&ctr->cls[2 + c], ncls[c]);
 }
 
 inline unsigned nblk(int64_t n) { return (unsigned)((n + BT - 1) / BT); }
@@ -661,12 +692,12 @@ inline unsigned nblk(int64_t n) { return (unsigned)((n + BT - 1) / BT); }
 
 int build_records(sdf_features_s *f, cudaStream_t s) {
     if (f->T > 0) {
-        k_face_records<<<nblk(f->T), BT, 0, s>>>(f->face_vid, f->vpos, f->T, f->face_rec, f->face_box, f->ctr);
+        k_face_records<<<std::min<int64_t>(nblk(f->T), REC_BLOCKS), BT, 0, s>>>(f->face_vid, f->vpos, f->T, f->face_rec, f->face_box, f->ctr);
         SDF_LAUNCHED(1);
-        k_edge_records<<<nblk(f->E), BT, 0, s>>>(f->edge_vf, f->face_vid, f->vpos, f->face_rec, f->E, f->edge_rec,
+        k_edge_records<<<std::min<int64_t>(nblk(f->E), REC_BLOCKS), BT, 0, s>>>(f->edge_vf, f->face_vid, f->vpos, f->face_rec, f->E, f->edge_rec,
                                                 f->edge_class, f->ctr);
         SDF_LAUNCHED(1);
-        k_vertex_records<<<nblk(f->V * VL), BT, 0, s>>>(f->vert_start, f->vert_corner, f->face_vid, f->vpos, f->face_rec,
+        k_vertex_records<<<std::min<int64_t>(nblk(f->V * VL), REC_BLOCKS), BT, 0, s>>>(f->vert_start, f->vert_corner, f->face_vid, f->vpos, f->face_rec,
                                                   f->V, f->vert_rec, f->vert_plane, f->vert_class, f->ctr);
         SDF_LAUNCHED(1);
     }
