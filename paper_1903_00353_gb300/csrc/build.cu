@@ -378,9 +378,6 @@ __device__ __forceinline__ void block_sums_into(double *words, float (&v)[K]) {
     }
 }
 
-// fixed grid of the records kernels: a few blocks per SM of this part, each looping over its items
-constexpr int REC_BLOCKS = 8 * 152;
-
 // Face records, and the precision terms and box moments of the faces (a fixed grid looping over
 // the faces; the block reductions at the end take every thread).  The unit normal and the plane
 // offset -n.a are computed in FP64 from the FP32 corners (their differences are exact in FP64)
@@ -488,7 +485,8 @@ __device__ __forceinline__ float corner_angle(float3 e1, float3 e2) {
     return atan2f(sqrtf(dot3(cr, cr)), dot3(e1, e2));
 }
 
-constexpr int VL = 8;  // lanes per vertex in k_vertex_records
+constexpr int VL = 8;      // lanes per vertex in k_vertex_records
+constexpr int VMAXS = 24;  // corners of a fan staged in shared memory (and cone-searched)
 
 __device__ __forceinline__ float gsum8(float v) {
     v += __shfl_xor_sync(0xffffffffu, v, 4, VL);
@@ -518,6 +516,11 @@ __global__ void __launch_bounds__(BT) k_vertex_records(const int32_t *vert_start
                                                        const int32_t *face_vid, const float *vpos,
                                                        const float4 *face_rec, int64_t V, float4 *vert_rec,
                                                        float4 *vert_plane, int8_t *vert_class, DevCounters *ctr) {
+    // the planes and face normals of each group's fan, staged for the classification and the cone
+    // search (fans of more than VMAXS corners read them from global memory and skip the search)
+    __shared__ float4 s_plane[BT / VL][VMAXS];
+    __shared__ float3 s_nf[BT / VL][VMAXS];
+    const int grp = (int)(threadIdx.x / VL);
     float tv_max = 0.f;
     unsigned ncls[4] = {0, 0, 0, 0};  // convex, concave, flat and saddle vertices of this thread
     // a warp-uniform loop (the groups' shuffles take the whole warp): item gl is lane gl % VL of
@@ -533,6 +536,7 @@ __global__ void __launch_bounds__(BT) k_vertex_records(const int32_t *vert_start
         // pass 1: pseudonormal and region planes
         float3 N = make_float3(0.f, 0.f, 0.f);
         float asum = 0.f;
+        const bool staged = s1 - s0 <= VMAXS;  // the fan's planes and normals fit the group's slots
         for (int i = s0 + sub; i < s1; i += VL) {
             const int c = vert_corner[i];
             const int f = c / 3, k = c - 3 * f;
@@ -541,9 +545,15 @@ __global__ void __launch_bounds__(BT) k_vertex_records(const int32_t *vert_start
             const float3 e1 = xn - p, e2 = xp - p;
             const float alpha = corner_angle(e1, e2);
             asum += alpha;
-            N = N + alpha * f3(face_rec[4 * f]);
+            const float3 nf = f3(face_rec[4 * f]);
+            N = N + alpha * nf;
             const float3 ej = normalized(e1);
-            vert_plane[i] = make_float4(-ej.x, -ej.y, -ej.z, dot3(ej, p));
+            const float4 pl = make_float4(-ej.x, -ej.y, -ej.z, dot3(ej, p));
+            vert_plane[i] = pl;
+            if (staged) {
+                s_plane[grp][i - s0] = pl;
+                s_nf[grp][i - s0] = nf;
+            }
         }
         N = make_float3(gsum8(N.x), gsum8(N.y), gsum8(N.z));
         asum = gsum8(asum);
@@ -565,22 +575,21 @@ __global__ void __launch_bounds__(BT) k_vertex_records(const int32_t *vert_start
         bool below = false, above = false, unsure = false, cvx = true, ccv = true;
         float cmin = 1.f;
         for (int i = s0 + sub; i < s1; i += VL) {
-            const int c = vert_corner[i];
-            const float3 ej = -1.f * f3(vert_plane[i]);  // unit direction to the next neighbour
-            const float3 dv = load_vpos(vpos, face_vid[3 * (c / 3) + ((c % 3) + 1) % 3]) - p;
-            const float d = dot3(dv, N);
-            const float bound = 2e-6f * sqrtf(dot3(dv, dv)) * Nlen;
+            // unit direction e_j to the next neighbour (the plane holds -e_j): the sign of
+            // (v_n - v).N_alpha is that of e_j.N_alpha, tested against 2e-6 |N_alpha|
+            const float3 ej = -1.f * (staged ? f3(s_plane[grp][i - s0]) : f3(vert_plane[i]));
+            const float d = dot3(ej, N);
+            const float bound = 2e-6f * Nlen;
             if (d < -bound) below = true;
             else if (d > bound) above = true;
             else unsure = true;
-            const float3 nf = f3(face_rec[4 * (c / 3)]);
+            const float3 nf = staged ? s_nf[grp][i - s0] : f3(face_rec[4 * (vert_corner[i] / 3)]);
             cmin = fminf(cmin, dot3(nf, Nu));
-            for (int b = s0; b < s1; b++) {  // every incident edge against this face's plane
-                const float dd = -dot3(nf, f3(vert_plane[b]));
+            for (int b = 0; b < s1 - s0; b++) {  // every incident edge against this face's plane
+                const float dd = -dot3(nf, staged ? f3(s_plane[grp][b]) : f3(vert_plane[s0 + b]));
                 cvx = cvx && dd <= 1e-4f;
                 ccv = ccv && dd >= -1e-4f;
             }
-            (void)ej;
         }
         below = gor8(below);
         above = gor8(above);
@@ -597,7 +606,7 @@ __global__ void __launch_bounds__(BT) k_vertex_records(const int32_t *vert_start
         // below are uniform over the 8 lanes of a vertex after the group reductions.
         const int deg = s1 - s0;
         const bool conv_cone = cvx && !ccv && cmin > 0.02f, conc_cone = ccv && !cvx && cmin > 0.02f;
-        const bool search = valid && Nlen > 0.f && !conv_cone && !conc_cone && deg <= 24;
+        const bool search = valid && Nlen > 0.f && !conv_cone && !conc_cone && staged;
         bool any = false, all_pos = true, all_neg = true;
         float cpos = 1.f, cng = 1.f;
         if (search) {
@@ -609,13 +618,13 @@ __global__ void __launch_bounds__(BT) k_vertex_records(const int32_t *vert_start
                     a++;
                 }
                 const int b = a + 1 + rem;
-                float3 y = cross3(f3(vert_plane[s0 + a]), f3(vert_plane[s0 + b]));  // planes hold -e
+                float3 y = cross3(f3(s_plane[grp][a]), f3(s_plane[grp][b]));  // planes hold -e
                 const float ly = sqrtf(dot3(y, y));
                 const bool ok = ly > 1e-6f;
                 y = (ok ? 1.f / ly : 0.f) * y;
                 bool fp = ok, fn = ok;  // +y and -y feasible
-                for (int m = s0; m < s1; m++) {
-                    const float dm = dot3(y, f3(vert_plane[m]));
+                for (int m = 0; m < deg; m++) {
+                    const float dm = dot3(y, f3(s_plane[grp][m]));
                     fp = fp && dm >= -1e-4f;
                     fn = fn && -dm >= -1e-4f;
                 }
@@ -681,6 +690,7 @@ __global__ void __launch_bounds__(BT) k_vertex_records(const int32_t *vert_start
         ncls[1] += my_cls == CLS_CONCAVE;
         ncls[2] += my_cls == CLS_FLAT;
         ncls[3] += my_cls == CLS_SADDLE;
+        __syncwarp();  // the group's staged fan is read to the end before the next one is written
     }
     block_max_into(&ctr->prec[PREC_TAU_V], tv_max);
     for (int c = 0; c < 4; c++) block_count_into(&ctr->cls[2 + c], ncls[c]);
@@ -688,16 +698,30 @@ __global__ void __launch_bounds__(BT) k_vertex_records(const int32_t *vert_start
 
 inline unsigned nblk(int64_t n) { return (unsigned)((n + BT - 1) / BT); }
 
+// grid of a records kernel over n threads' worth of items: the blocks resident on the device at
+// once (a single wave of the grid-stride loop), fewer when the items need fewer
+template <class K> unsigned rec_grid(K kernel, int64_t n) {
+    static int resident = 0;  // per kernel (one instance of this function per kernel type)
+    if (!resident) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, BT, 0);
+        resident = std::max(1, per_sm) * std::max(1, sms);
+    }
+    return (unsigned)std::min<int64_t>(nblk(n), resident);
+}
+
 }  // namespace
 
 int build_records(sdf_features_s *f, cudaStream_t s) {
     if (f->T > 0) {
-        k_face_records<<<std::min<int64_t>(nblk(f->T), REC_BLOCKS), BT, 0, s>>>(f->face_vid, f->vpos, f->T, f->face_rec, f->face_box, f->ctr);
+        k_face_records<<<rec_grid(k_face_records, f->T), BT, 0, s>>>(f->face_vid, f->vpos, f->T, f->face_rec, f->face_box, f->ctr);
         SDF_LAUNCHED(1);
-        k_edge_records<<<std::min<int64_t>(nblk(f->E), REC_BLOCKS), BT, 0, s>>>(f->edge_vf, f->face_vid, f->vpos, f->face_rec, f->E, f->edge_rec,
+        k_edge_records<<<rec_grid(k_edge_records, f->E), BT, 0, s>>>(f->edge_vf, f->face_vid, f->vpos, f->face_rec, f->E, f->edge_rec,
                                                 f->edge_class, f->ctr);
         SDF_LAUNCHED(1);
-        k_vertex_records<<<std::min<int64_t>(nblk(f->V * VL), REC_BLOCKS), BT, 0, s>>>(f->vert_start, f->vert_corner, f->face_vid, f->vpos, f->face_rec,
+        k_vertex_records<<<rec_grid(k_vertex_records, f->V * VL), BT, 0, s>>>(f->vert_start, f->vert_corner, f->face_vid, f->vpos, f->face_rec,
                                                   f->V, f->vert_rec, f->vert_plane, f->vert_class, f->ctr);
         SDF_LAUNCHED(1);
     }
