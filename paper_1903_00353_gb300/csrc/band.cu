@@ -446,7 +446,7 @@ struct TileSmem {
     unsigned char ax[NT];              // scan axis
     unsigned char qkind[NT];           // kind of quadratic row bound: Q_NONE, Q_EDGE or Q_VERT
     unsigned rowq[NT / 32][64];        // per-warp ring of non-empty rows waiting for point evaluation
-    int chunk_next;                    // next 32-region chunk of the tile to hand to a warp
+    int next;                          // next chunk of the tile's regions to hand to a warp
     long long work;
 };
 
@@ -502,217 +502,242 @@ __device__ __forceinline__ void eval_rows(const Feat &F, const GridP &g, TileSme
     }
 }
 
-// All regions of one band tile.  Warps take chunks of 32 regions from a shared counter and work on
-// them without block barriers: (1) one lane per region takes its box in the tile (packed in the
-// pair by the binning), its scan axis (the longest side), its row count and its span coefficients;
-// (2) a warp scan numbers the chunk's rows; (3) each lane takes one row, finds its region by a
-// shuffle search of the scan, and evaluates the span from the coefficients (Algorithm 2 on a grid
-// line); (4) non-empty rows wait in a per-warp queue until 32 are ready, then their points are
-// flattened over the lanes, evaluated and merged into the tile's keys with a shared-memory
-// atomicMin (Algorithm 1).
+// Set-up of one region of a band tile (pair q of the tile's list; none when q >= qend) into slot
+// `slot` of the tile's shared arrays: its scan axis (the longest side of its box in the tile), its
+// row count (returned) and its span coefficients (Algorithm 2's half-spaces as bounds linear in a
+// row's two indices, plus the quadratic bound of a vertex ball or an edge cylinder).
+template <int TY, int TZ>
+__device__ __forceinline__ int setup_region(const Feat &F, const GridP &g, const int2 *pairs, int64_t q, int64_t qend,
+                                            int x0, int y0, int z0, TileSmem<TY, TZ> &S, int slot) {
+    const float3 org = make_float3(g.ox, g.oy, g.oz);
+    int fid = 0, lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1}, type = FACE, id = 0;
+    if (q < qend) {
+        const int2 pr = __ldg(pairs + q);
+        fid = pr.x;
+        type = feat_type(F, fid);
+        id = feat_local(F, fid, type);
+        const unsigned bx = (unsigned)pr.y;
+        lo[0] = x0 + (int)(bx & 31u); hi[0] = x0 + (int)((bx >> 5) & 31u);
+        lo[1] = y0 + (int)((bx >> 10) & 15u); hi[1] = y0 + (int)((bx >> 14) & 15u);
+        lo[2] = z0 + (int)((bx >> 18) & 15u); hi[2] = z0 + (int)((bx >> 22) & 15u);
+    }
+    const int n0 = hi[0] - lo[0] + 1, n1 = hi[1] - lo[1] + 1, n2 = hi[2] - lo[2] + 1;
+    const int ax = (n0 >= n1 && n0 >= n2) ? 0 : (n1 >= n2 ? 1 : 2);
+    const int bx = ax == 0 ? 1 : 0, cx = ax == 2 ? 1 : 2;
+    const int nb = bx == 0 ? n0 : n1, nc = cx == 1 ? n1 : n2;
+    const int nrows = (n0 > 0 && n1 > 0 && n2 > 0) ? nb * nc : 0;
+    const int la = ax == 0 ? lo[0] : (ax == 1 ? lo[1] : lo[2]);
+    const int ha = ax == 0 ? hi[0] : (ax == 1 ? hi[1] : hi[2]);
+    const int lb = bx == 0 ? lo[0] : lo[1];
+    const int lc = cx == 1 ? lo[1] : lo[2];
+    S.fid[slot] = fid;
+    S.ax[slot] = (unsigned char)ax;
+    // tile-local starts: a row's points are (a, b, c) = (lo_a + j, lo_b + ib, lo_c + ic)
+    const int loa = la - (ax == 0 ? x0 : (ax == 1 ? y0 : z0));
+    const int lob = lb - (bx == 0 ? x0 : y0);
+    const int loc = lc - (cx == 1 ? y0 : z0);
+    const int nbc = max(nb, 1);
+    int nl = 0, nu = 0;
+    // quadratic row bound in index units: vertex (j_v, db0, dc0, R^2); edge (Qa, Qb, Qc, R^2),
+    // (t_a, t_b, t_c, -) with Q the edge point a seen from the row origin; faces none (their
+    // slab planes bound the distance)
+    float4 q0v = make_float4(0.f, 0.f, 0.f, 0.f), q1v = make_float4(0.f, 0.f, 0.f, Q_NONE);
+    if (nrows > 0) {
+        // whole-grid indices of the box's first row (z indices carry the slab's first layer)
+        const int la_g = la + (ax == 2 ? g.kofs : 0), lc_g = lc + (cx == 2 ? g.kofs : 0);
+        const float pb0 = fmaf((float)lb + 0.5f, g.h, comp3(org, bx));
+        const float pc0 = fmaf((float)lc_g + 0.5f, g.h, comp3(org, cx));
+        const float K = comp3(org, ax) * g.inv_h + 0.5f + (float)la_g;  // j = (p_a - o_a)/h - 1/2 - lo_a
+        float4 *E = S.coef[slot];  // written directly to shared memory
+        if (type == FACE) {
+            const float4 *r = F.face_rec + 4 * id;
+            const float4 n = __ldg(r);
+            add_coef(E, nl, nu, make_float4(n.x, n.y, n.z, n.w + g.W), ax, bx, cx, pb0, pc0, K, g);
+            add_coef(E, nl, nu, make_float4(-n.x, -n.y, -n.z, g.W - n.w), ax, bx, cx, pb0, pc0, K, g);
+            add_coef(E, nl, nu, __ldg(r + 1), ax, bx, cx, pb0, pc0, K, g);
+            add_coef(E, nl, nu, __ldg(r + 2), ax, bx, cx, pb0, pc0, K, g);
+            add_coef(E, nl, nu, __ldg(r + 3), ax, bx, cx, pb0, pc0, K, g);
+        } else if (type == EDGE) {
+            const float4 *r = F.edge_rec + 5 * id;
+            const float4 a = __ldg(r), tt = __ldg(r + 1);
+            add_coef(E, nl, nu, make_float4(tt.x, tt.y, tt.z, -tt.w), ax, bx, cx, pb0, pc0, K, g);
+            add_coef(E, nl, nu, make_float4(-tt.x, -tt.y, -tt.z, tt.w + a.w), ax, bx, cx, pb0, pc0, K, g);
+            add_coef(E, nl, nu, __ldg(r + 2), ax, bx, cx, pb0, pc0, K, g);
+            add_coef(E, nl, nu, __ldg(r + 3), ax, bx, cx, pb0, pc0, K, g);
+            // the wedge planes do not bound the distance to the edge line: add the cylinder
+            // |(p - a) x t| <= W (+ tolerance and a slack of 1/64 cell), which only removes
+            // points the merge would reject (d >= W)
+            const float3 av = f3(a), tv = f3(tt);
+            const float Rs = (g.W + g.eps) * g.inv_h + 1.f / 64.f;
+            q0v = make_float4((comp3(org, ax) - comp3(av, ax)) * g.inv_h + 0.5f + (float)la_g,
+                              (pb0 - comp3(av, bx)) * g.inv_h, (pc0 - comp3(av, cx)) * g.inv_h, Rs * Rs);
+            q1v = make_float4(comp3(tv, ax), comp3(tv, bx), comp3(tv, cx), Q_EDGE);
+        } else {
+            const float4 v = __ldg(F.vert_rec + 3 * id), nv = __ldg(F.vert_rec + 3 * id + 1);
+            const int s0 = __float_as_int(v.w), cnt = min(__float_as_int(nv.w), MAXVP);
+            for (int k = 0; k < cnt; k++)
+                add_coef(E, nl, nu, __ldg(F.vert_plane + s0 + k), ax, bx, cx, pb0, pc0, K, g);
+            const float3 vv = f3(v);
+            const float Rh = (g.W + g.eps) * g.inv_h;
+            q0v = make_float4((comp3(vv, ax) - comp3(org, ax)) * g.inv_h - 0.5f - (float)la_g,
+                              (pb0 - comp3(vv, bx)) * g.inv_h, (pc0 - comp3(vv, cx)) * g.inv_h, Rh * Rh);
+            q1v.w = Q_VERT;
+        }
+    }
+    for (int k = nl; k < KMAX - nu; k++) S.coef[slot][k] = make_float4(1e30f, 0.f, 0.f, 0.f);
+    S.quad[slot][0] = q0v;
+    S.quad[slot][1] = q1v;
+    S.qkind[slot] = (unsigned char)q1v.w;
+    // rinfo: x = nb | nl << 8 | span_hi << 12 | lo_a << 17 | lo_b << 22 | lo_c << 27 (tile-local,
+    // 5 bits each), y = 1 / nb
+    S.rinfo[slot] = make_uint2((unsigned)(nbc | (nl << 8) | (max(ha - la, 0) << 12) | (loa << 17) | (lob << 22) |
+                                       (loc << 27)),
+                            __float_as_uint(1.f / (float)nbc));
+    return nrows;
+}
+
+// The span of row `local` (in the region's row order) of the region in slot reg: its length (0 for
+// an empty row) and, in `packed`, its queue record slot | start along a << 8 | len << 13 |
+// b << 19 | c << 24 (tile-local).
+template <int TY, int TZ>
+__device__ __forceinline__ int row_span(const TileSmem<TY, TZ> &S, int reg, int local, int &packed) {
+    const uint2 ri = S.rinfo[reg];
+    const int nbv = (int)(ri.x & 255u), nl = (int)((ri.x >> 8) & 15u);
+    const int ic = (int)(((float)local + 0.5f) * __uint_as_float(ri.y));  // exact for these sizes
+    const int ib = local - ic * nbv;
+    const float fb = (float)ib, fc = (float)ic;
+    float lo_f = -1e30f, hi_f = 1e30f;
+    bool open = true;
+    const float4 *E = S.coef[reg];
+#pragma unroll
+    for (int k = 0; k < KMAX; k++) {
+        const float4 c = E[k];
+        const float v = fmaf(c.y, fb, fmaf(c.z, fc, c.x));
+        if (k < nl) lo_f = fmaxf(lo_f, v);
+        else hi_f = fminf(hi_f, v);
+    }
+    const int qk = S.qkind[reg];
+    if (qk == (int)Q_VERT) {  // ball around the vertex
+        const float4 bl = S.quad[reg][0];
+        const float db = bl.y + fb, dc = bl.z + fc;
+        const float q2 = bl.w - db * db - dc * dc;
+        if (q2 < 0.f) {
+            open = false;
+        } else {
+            const float sq = sqrtf(q2);
+            lo_f = fmaxf(lo_f, bl.x - sq);
+            hi_f = fminf(hi_f, bl.x + sq);
+        }
+    } else if (qk == (int)Q_EDGE && hi_f - lo_f > 2.f) {
+        // cylinder around the edge line, c2 j^2 + c1 j + c0 <= 0: only for spans of more than
+        // a few points (long spans come from wide wedges, whose planes leave the radius open)
+        const float4 cq = S.quad[reg][0], q1 = S.quad[reg][1];
+        const float ub = cq.y + fb, uc = cq.z + fc;
+        const float k0 = fmaf(q1.x, cq.x, fmaf(q1.y, ub, q1.z * uc));
+        const float c2 = fmaf(-q1.x, q1.x, 1.f);
+        const float c1 = 2.f * fmaf(-q1.x, k0, cq.x);
+        const float c0 = fmaf(cq.x, cq.x, fmaf(ub, ub, fmaf(uc, uc, fmaf(-k0, k0, -cq.w))));
+        if (c2 > 1e-6f) {
+            const float disc = fmaf(c1, c1, -4.f * c2 * c0);
+            if (disc < 0.f) {
+                open = false;
+            } else {  // roots by the cancellation-free form
+                const float qq = -0.5f * (c1 + copysignf(sqrtf(disc), c1));
+                const float r1 = qq / c2, r2 = qq != 0.f ? c0 / qq : r1;
+                lo_f = fmaxf(lo_f, fminf(r1, r2));
+                hi_f = fminf(hi_f, fmaxf(r1, r2));
+            }
+        } else if (c1 == 0.f || fabsf(c1) < 1e-6f) {  // the edge runs along the row
+            if (c0 > 0.f) open = false;
+        } else {  // linear: c1 j + c0 <= 0
+            const float r = -c0 / c1;
+            if (c1 > 0.f) hi_f = fminf(hi_f, r); else lo_f = fmaxf(lo_f, r);
+        }
+    }
+    const float sl = 1.f / 4096.f;
+    const float span_hi = (float)((ri.x >> 12) & 31u);
+    const float fa = fminf(fmaxf(lo_f - sl, 0.f), span_hi + 1.f);
+    const float fz = fmaxf(fminf(hi_f + sl, span_hi), -1.f);
+    const int ja = (int)ceilf(fa), jb = (int)floorf(fz);
+    const int len = open ? max(jb - ja + 1, 0) : 0;
+    packed = reg | ((int)((ri.x >> 17) & 31u) + ja) << 8 | (len << 13) |
+             (((int)((ri.x >> 22) & 31u) + ib) << 19) | (((int)(ri.x >> 27) + ic) << 24);
+    return len;
+}
+
+// Queue a row (len > 0) in the warp's ring; once 32 rows wait, evaluate their points.
+template <int TY, int TZ>
+__device__ __forceinline__ void queue_row(const Feat &F, const GridP &g, TileSmem<TY, TZ> &S, int len, int packed,
+                                          int &qh, int &qn, int x0, int y0, int z0, unsigned &cand) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned hit = __ballot_sync(FULL, len > 0);
+    if (len > 0) S.rowq[warp][(qh + qn + __popc(hit & ((1u << lane) - 1u))) & 63] = (unsigned)packed;
+    qn += __popc(hit);
+    __syncwarp();
+    if (qn >= 32) {
+        eval_rows<TY, TZ>(F, g, S, S.rowq[warp], qh, 32, x0, y0, z0, cand);
+        qh = (qh + 32) & 63;
+        qn -= 32;
+    }
+}
+// the rest of the warp's queue
+template <int TY, int TZ>
+__device__ __forceinline__ void flush_rows(const Feat &F, const GridP &g, TileSmem<TY, TZ> &S, int &qh, int &qn,
+                                           int x0, int y0, int z0, unsigned &cand) {
+    const int warp = threadIdx.x >> 5;
+    while (qn > 0) {
+        const int m = min(qn, 32);
+        eval_rows<TY, TZ>(F, g, S, S.rowq[warp], qh, m, x0, y0, z0, cand);
+        qh = (qh + m) & 63;
+        qn -= m;
+    }
+}
+
+// All regions of one band tile.  Per region: its box in the tile (packed in the pair by the
+// binning), its scan axis, its row count and its span coefficients (setup_region); per row: the
+// span (row_span, Algorithm 2 on a grid line); non-empty rows wait in a per-warp queue until 32
+// are ready, then their points are flattened over the lanes, evaluated and merged into the tile's
+// keys with a shared-memory atomicMin (Algorithm 1, eval_rows).  The warps take equal chunks of
+// at most 32 regions (a multiple of the warp count of them, so that a tile with few regions still
+// uses every warp) from a shared counter and work on them without block barriers: one lane per
+// region sets it up, a warp scan numbers the chunk's rows, and each lane takes one row, found by a
+// shuffle search of the scan.  (Handing out a tile's rows block-wide in batches of 32 was measured
+// slower on the knot tube and no faster on the torus.)
 template <int TY, int TZ>
 __device__ void process_band_tile(const Feat &F, const GridP &g, const int2 *pairs, int64_t q0, int64_t q3,
                                   int x0, int y0, int z0, TileSmem<TY, TZ> &S, unsigned &cand, unsigned &rows,
                                   unsigned &hits) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = threadIdx.x;
-    const float3 org = make_float3(g.ox, g.oy, g.oz);
-    // equal chunks of at most 32 regions, a multiple of the warp count of them, so that a tile with
-    // few regions still spreads its rows over every warp
     const int64_t npairs = q3 - q0;
     if (npairs <= 0) return;  // (after a pair-list overflow a band tile may have no stored pairs)
+    int qh = 0, qn = 0;       // head and length of this warp's row queue
     const int64_t nchunks = (NT / 32) * ((npairs + NT - 1) / NT);  // >= NT / 32
     const int cs = (int)((npairs + nchunks - 1) / nchunks);          // >= 1: every chunk advances
     for (;;) {
-        // this warp's next chunk of the tile's regions
-        int chunk = 0;
-        if (lane == 0) chunk = atomicAdd(&S.chunk_next, 1);
+        int chunk = 0;  // this warp's next chunk of the tile's regions
+        if (lane == 0) chunk = atomicAdd(&S.next, 1);
         chunk = __shfl_sync(FULL, chunk, 0);
         const int64_t base = q0 + (int64_t)cs * chunk;
         if (base >= q3) break;
-        const int64_t q = base + lane;
-        const int64_t qend = min(base + cs, q3);
-        int nrows = 0;
-        {
-            int fid = 0, lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1}, type = FACE, id = 0;
-            if (q < qend) {
-                const int2 pr = __ldg(pairs + q);
-                fid = pr.x;
-                type = feat_type(F, fid);
-                id = feat_local(F, fid, type);
-                const unsigned bx = (unsigned)pr.y;
-                lo[0] = x0 + (int)(bx & 31u); hi[0] = x0 + (int)((bx >> 5) & 31u);
-                lo[1] = y0 + (int)((bx >> 10) & 15u); hi[1] = y0 + (int)((bx >> 14) & 15u);
-                lo[2] = z0 + (int)((bx >> 18) & 15u); hi[2] = z0 + (int)((bx >> 22) & 15u);
-            }
-            const int n0 = hi[0] - lo[0] + 1, n1 = hi[1] - lo[1] + 1, n2 = hi[2] - lo[2] + 1;
-            const int ax = (n0 >= n1 && n0 >= n2) ? 0 : (n1 >= n2 ? 1 : 2);
-            const int bx = ax == 0 ? 1 : 0, cx = ax == 2 ? 1 : 2;
-            const int nb = bx == 0 ? n0 : n1, nc = cx == 1 ? n1 : n2;
-            nrows = (n0 > 0 && n1 > 0 && n2 > 0) ? nb * nc : 0;
-            const int la = ax == 0 ? lo[0] : (ax == 1 ? lo[1] : lo[2]);
-            const int ha = ax == 0 ? hi[0] : (ax == 1 ? hi[1] : hi[2]);
-            const int lb = bx == 0 ? lo[0] : lo[1];
-            const int lc = cx == 1 ? lo[1] : lo[2];
-            S.fid[t] = fid;
-            S.ax[t] = (unsigned char)ax;
-            // tile-local starts: a row's points are (a, b, c) = (lo_a + j, lo_b + ib, lo_c + ic)
-            const int loa = la - (ax == 0 ? x0 : (ax == 1 ? y0 : z0));
-            const int lob = lb - (bx == 0 ? x0 : y0);
-            const int loc = lc - (cx == 1 ? y0 : z0);
-            const int nbc = max(nb, 1);
-            int nl = 0, nu = 0;
-            // quadratic row bound in index units: vertex (j_v, db0, dc0, R^2); edge (Qa, Qb, Qc, R^2),
-            // (t_a, t_b, t_c, -) with Q the edge point a seen from the row origin; faces none (their
-            // slab planes bound the distance)
-            float4 q0v = make_float4(0.f, 0.f, 0.f, 0.f), q1v = make_float4(0.f, 0.f, 0.f, Q_NONE);
-            if (nrows > 0) {
-                // whole-grid indices of the box's first row (z indices carry the slab's first layer)
-                const int la_g = la + (ax == 2 ? g.kofs : 0), lc_g = lc + (cx == 2 ? g.kofs : 0);
-                const float pb0 = fmaf((float)lb + 0.5f, g.h, comp3(org, bx));
-                const float pc0 = fmaf((float)lc_g + 0.5f, g.h, comp3(org, cx));
-                const float K = comp3(org, ax) * g.inv_h + 0.5f + (float)la_g;  // j = (p_a - o_a)/h - 1/2 - lo_a
-                float4 *E = S.coef[t];  // written directly to shared memory
-                if (type == FACE) {
-                    const float4 *r = F.face_rec + 4 * id;
-                    const float4 n = __ldg(r);
-                    add_coef(E, nl, nu, make_float4(n.x, n.y, n.z, n.w + g.W), ax, bx, cx, pb0, pc0, K, g);
-                    add_coef(E, nl, nu, make_float4(-n.x, -n.y, -n.z, g.W - n.w), ax, bx, cx, pb0, pc0, K, g);
-                    add_coef(E, nl, nu, __ldg(r + 1), ax, bx, cx, pb0, pc0, K, g);
-                    add_coef(E, nl, nu, __ldg(r + 2), ax, bx, cx, pb0, pc0, K, g);
-                    add_coef(E, nl, nu, __ldg(r + 3), ax, bx, cx, pb0, pc0, K, g);
-                } else if (type == EDGE) {
-                    const float4 *r = F.edge_rec + 5 * id;
-                    const float4 a = __ldg(r), tt = __ldg(r + 1);
-                    add_coef(E, nl, nu, make_float4(tt.x, tt.y, tt.z, -tt.w), ax, bx, cx, pb0, pc0, K, g);
-                    add_coef(E, nl, nu, make_float4(-tt.x, -tt.y, -tt.z, tt.w + a.w), ax, bx, cx, pb0, pc0, K, g);
-                    add_coef(E, nl, nu, __ldg(r + 2), ax, bx, cx, pb0, pc0, K, g);
-                    add_coef(E, nl, nu, __ldg(r + 3), ax, bx, cx, pb0, pc0, K, g);
-                    // the wedge planes do not bound the distance to the edge line: add the cylinder
-                    // |(p - a) x t| <= W (+ tolerance and a slack of 1/64 cell), which only removes
-                    // points the merge would reject (d >= W)
-                    const float3 av = f3(a), tv = f3(tt);
-                    const float Rs = (g.W + g.eps) * g.inv_h + 1.f / 64.f;
-                    q0v = make_float4((comp3(org, ax) - comp3(av, ax)) * g.inv_h + 0.5f + (float)la_g,
-                                      (pb0 - comp3(av, bx)) * g.inv_h, (pc0 - comp3(av, cx)) * g.inv_h, Rs * Rs);
-                    q1v = make_float4(comp3(tv, ax), comp3(tv, bx), comp3(tv, cx), Q_EDGE);
-                } else {
-                    const float4 v = __ldg(F.vert_rec + 3 * id), nv = __ldg(F.vert_rec + 3 * id + 1);
-                    const int s0 = __float_as_int(v.w), cnt = min(__float_as_int(nv.w), MAXVP);
-                    for (int k = 0; k < cnt; k++)
-                        add_coef(E, nl, nu, __ldg(F.vert_plane + s0 + k), ax, bx, cx, pb0, pc0, K, g);
-                    const float3 vv = f3(v);
-                    const float Rh = (g.W + g.eps) * g.inv_h;
-                    q0v = make_float4((comp3(vv, ax) - comp3(org, ax)) * g.inv_h - 0.5f - (float)la_g,
-                                      (pb0 - comp3(vv, bx)) * g.inv_h, (pc0 - comp3(vv, cx)) * g.inv_h, Rh * Rh);
-                    q1v.w = Q_VERT;
-                }
-            }
-            for (int k = nl; k < KMAX - nu; k++) S.coef[t][k] = make_float4(1e30f, 0.f, 0.f, 0.f);
-            S.quad[t][0] = q0v;
-            S.quad[t][1] = q1v;
-            S.qkind[t] = (unsigned char)q1v.w;
-            // rinfo: x = nb | nl << 8 | span_hi << 12 | lo_a << 17 | lo_b << 22 | lo_c << 27 (tile-local,
-            // 5 bits each), y = 1 / nb
-            S.rinfo[t] = make_uint2((unsigned)(nbc | (nl << 8) | (max(ha - la, 0) << 12) | (loa << 17) | (lob << 22) |
-                                               (loc << 27)),
-                                    __float_as_uint(1.f / (float)nbc));
-        }
+        const int nrows = setup_region<TY, TZ>(F, g, pairs, base + lane, min(base + cs, q3), x0, y0, z0, S, t);
         // rows of the warp's regions, numbered by a warp scan
         const int incl = warp_incl_scan(nrows);
         const int R = __shfl_sync(FULL, incl, 31);
         __syncwarp();
-        int qh = 0, qn = 0;  // head and length of this warp's row queue
         for (int rbase = 0; rbase < R; rbase += 32) {
             const int r = rbase + lane;
             const int own = min(warp_owner(incl, r), 31);  // lane whose region holds row r
             const int r0 = __shfl_sync(FULL, incl - nrows, own);
-            const int reg = warp * 32 + own;
             int len = 0, packed = 0;
             if (r < R) {
-                const uint2 ri = S.rinfo[reg];
-                const int nbv = (int)(ri.x & 255u), nl = (int)((ri.x >> 8) & 15u);
-                const int local = r - r0;
-                const int ic = (int)(((float)local + 0.5f) * __uint_as_float(ri.y));  // exact for these sizes
-                const int ib = local - ic * nbv;
-                const float fb = (float)ib, fc = (float)ic;
-                float lo_f = -1e30f, hi_f = 1e30f;
-                bool open = true;
-                const float4 *E = S.coef[reg];
-#pragma unroll
-                for (int k = 0; k < KMAX; k++) {
-                    const float4 c = E[k];
-                    const float v = fmaf(c.y, fb, fmaf(c.z, fc, c.x));
-                    if (k < nl) lo_f = fmaxf(lo_f, v);
-                    else hi_f = fminf(hi_f, v);
-                }
-                const int qk = S.qkind[reg];
-                if (qk == (int)Q_VERT) {  // ball around the vertex
-                    const float4 bl = S.quad[reg][0];
-                    const float db = bl.y + fb, dc = bl.z + fc;
-                    const float q2 = bl.w - db * db - dc * dc;
-                    if (q2 < 0.f) {
-                        open = false;
-                    } else {
-                        const float sq = sqrtf(q2);
-                        lo_f = fmaxf(lo_f, bl.x - sq);
-                        hi_f = fminf(hi_f, bl.x + sq);
-                    }
-                } else if (qk == (int)Q_EDGE && hi_f - lo_f > 2.f) {
-                    // cylinder around the edge line, c2 j^2 + c1 j + c0 <= 0: only for spans of more than
-                    // a few points (long spans come from wide wedges, whose planes leave the radius open)
-                    const float4 cq = S.quad[reg][0], q1 = S.quad[reg][1];
-                    const float ub = cq.y + fb, uc = cq.z + fc;
-                    const float k0 = fmaf(q1.x, cq.x, fmaf(q1.y, ub, q1.z * uc));
-                    const float c2 = fmaf(-q1.x, q1.x, 1.f);
-                    const float c1 = 2.f * fmaf(-q1.x, k0, cq.x);
-                    const float c0 = fmaf(cq.x, cq.x, fmaf(ub, ub, fmaf(uc, uc, fmaf(-k0, k0, -cq.w))));
-                    if (c2 > 1e-6f) {
-                        const float disc = fmaf(c1, c1, -4.f * c2 * c0);
-                        if (disc < 0.f) {
-                            open = false;
-                        } else {  // roots by the cancellation-free form
-                            const float qq = -0.5f * (c1 + copysignf(sqrtf(disc), c1));
-                            const float r1 = qq / c2, r2 = qq != 0.f ? c0 / qq : r1;
-                            lo_f = fmaxf(lo_f, fminf(r1, r2));
-                            hi_f = fminf(hi_f, fmaxf(r1, r2));
-                        }
-                    } else if (c1 == 0.f || fabsf(c1) < 1e-6f) {  // the edge runs along the row
-                        if (c0 > 0.f) open = false;
-                    } else {  // linear: c1 j + c0 <= 0
-                        const float r = -c0 / c1;
-                        if (c1 > 0.f) hi_f = fminf(hi_f, r); else lo_f = fmaxf(lo_f, r);
-                    }
-                }
-                const float sl = 1.f / 4096.f;
-                const float span_hi = (float)((ri.x >> 12) & 31u);
-                const float fa = fminf(fmaxf(lo_f - sl, 0.f), span_hi + 1.f);
-                const float fz = fmaxf(fminf(hi_f + sl, span_hi), -1.f);
-                const int ja = (int)ceilf(fa), jb = (int)floorf(fz);
-                len = open ? max(jb - ja + 1, 0) : 0;
-                // row record: slot | start along a << 8 | len << 13 | b << 19 | c << 24 (tile-local)
-                packed = reg | ((int)((ri.x >> 17) & 31u) + ja) << 8 | (len << 13) |
-                         (((int)((ri.x >> 22) & 31u) + ib) << 19) | (((int)(ri.x >> 27) + ic) << 24);
+                len = row_span<TY, TZ>(S, warp * 32 + own, r - r0, packed);
                 rows++;
                 hits += len > 0;
             }
-            // queue the non-empty rows; evaluate their points once 32 rows are waiting
-            const unsigned hit = __ballot_sync(FULL, len > 0);
-            if (len > 0) S.rowq[warp][(qh + qn + __popc(hit & ((1u << lane) - 1u))) & 63] = (unsigned)packed;
-            qn += __popc(hit);
-            __syncwarp();
-            if (qn >= 32) {
-                eval_rows<TY, TZ>(F, g, S, S.rowq[warp], qh, 32, x0, y0, z0, cand);
-                qh = (qh + 32) & 63;
-                qn -= 32;
-            }
+            queue_row<TY, TZ>(F, g, S, len, packed, qh, qn, x0, y0, z0, cand);
         }
-        while (qn > 0) {  // the rest of this warp's queue (region slots are rewritten by the next pass)
-            const int m = min(qn, 32);
-            eval_rows<TY, TZ>(F, g, S, S.rowq[warp], qh, m, x0, y0, z0, cand);
-            qh = (qh + m) & 63;
-            qn -= m;
-        }
-        __syncwarp();  // this warp's region slots are rewritten by its next chunk
+        flush_rows<TY, TZ>(F, g, S, qh, qn, x0, y0, z0, cand);  // region slots are rewritten by the next chunk
+        __syncwarp();
     }
 }
 
@@ -971,7 +996,7 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
                 const uint32_t *st = o.bin_start + 3 * tile;
                 const int64_t q0 = min((int64_t)st[0], o.pair_cap), q3 = min((int64_t)st[3], o.pair_cap);
                 for (int e = threadIdx.x; e < TP; e += NT) S.key[e] = ~0ull;
-                if (threadIdx.x == 0) S.chunk_next = 0;
+                if (threadIdx.x == 0) S.next = 0;
                 __syncthreads();
                 process_band_tile<TY, TZ>(pr.F, g, o.pairs, q0, q3, x0, y0, z0, S, cand, rows, hits);
                 __syncthreads();  // every merge is in before the decode
