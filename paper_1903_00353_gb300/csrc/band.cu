@@ -438,10 +438,10 @@ constexpr float Q_NONE = 0.f, Q_EDGE = 1.f, Q_VERT = 2.f;  // kinds of quadratic
 
 template <int TY, int TZ>
 struct TileSmem {
-    unsigned long long key[TILE_X * TY * TZ];  // packed (|d| bits << 32 | id << 1 | sign) per tile point
+    unsigned long long key[TILE_X * TY * TZ];  // packed (|d| bits << 32 | id << 2 | unc << 1 | neg) per point
     float4 coef[NT][KMAX];             // span coefficients (A, B, C, -): nl lower bounds, then upper bounds
     float4 quad[NT][2];                // quadratic bound of a region's rows: vertex ball, edge cylinder
-    uint2 rinfo[NT];                   // row set-up of each region, packed (see process_band_tile)
+    uint2 rinfo[NT];                   // row set-up of each region, packed (see setup_region)
     int fid[NT];                       // regions of the current pass (global feature ids)
     unsigned char ax[NT];              // scan axis
     unsigned char qkind[NT];           // kind of quadratic row bound: Q_NONE, Q_EDGE or Q_VERT
