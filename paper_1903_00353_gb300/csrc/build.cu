@@ -447,6 +447,10 @@ __global__ void __launch_bounds__(BT) k_edge_records(const int4 *edge_vf, const 
     unsigned ncv = 0, ncc = 0;  // class counts of this thread's edges
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
         const int4 q = edge_vf[e];
+        if (q.x < 0 || q.y < 0 || q.z < 0 || q.w < 0) {  // not paired (a broken mesh, rejected by the build)
+            edge_class[e] = CLS_FLAT;
+            continue;
+        }
         const float3 a = load_vpos(vpos, q.x), b = load_vpos(vpos, q.y);
         const float3 n1 = f3(face_rec[4 * q.z]), n2 = f3(face_rec[4 * q.w]);
         const float3 ab = b - a;
@@ -878,6 +882,8 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     B_TRY(cudaGetLastError());
     B_TRY(scan_exclusive_u32(canon, head, n, true, scan_state, s, err));
     B_TRY(dalloc_s(&f->edge_vf, E, s));
+    // entries that no canonical edge writes (a broken mesh) stay -1 and are skipped by the records
+    B_TRY(cudaMemsetAsync(f->edge_vf, 0xff, sizeof(int4) * (size_t)E, s));
     k_edge_emit<<<nblk(n), BT, 0, s>>>(f->vert_corner, f->face_vid, twin, canon, head, n, f->edge_vf, f->face_edge);
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
@@ -889,16 +895,9 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     B_TRY(dalloc_s(&f->vert_rec, 3 * V, s));
     B_TRY(dalloc_s(&f->vert_plane, n, s));
     B_TRY(dalloc_s(&f->vert_class, V, s));
-    unsigned st = 0;
-    {
-        const HostRead rd[1] = {{&st, &f->ctr->status, sizeof(unsigned)}};
-        B_TRY(read_small(rd, 1, s));
-    }
-    if (st) {  // do not evaluate geometry on broken connectivity
-        tmp.release(s);
-        free_handle(f);
-        return status_to_code(st);
-    }
+    // The records are built without first reading the connectivity status (one host round trip
+    // fewer): on a broken mesh they only see valid indices (the weld's are valid by construction,
+    // unpaired edges are skipped) and the status read below rejects the handle.
     if (build_records(f, s) != SDF_OK) B_TRY(cudaErrorUnknown);
     DevCounters c;
     uint32_t n_canon = 0;
