@@ -19,6 +19,8 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <utility>
+#include <vector>
 
 #include "sdf_internal.cuh"
 
@@ -702,6 +704,15 @@ __global__ void __launch_bounds__(BT) k_vertex_records(const int32_t *vert_start
 
 inline unsigned nblk(int64_t n) { return (unsigned)((n + BT - 1) / BT); }
 
+// the build's small state: counters and scan state cleared, the bounding box at (+inf, -inf)
+__global__ void k_build_init(unsigned *ctr, int64_t ctr_words, float *bb, unsigned *n_long, unsigned *scan,
+                             int64_t scan_words) {
+    for (int64_t i = threadIdx.x; i < ctr_words; i += blockDim.x) ctr[i] = 0u;
+    for (int64_t i = threadIdx.x; i < scan_words; i += blockDim.x) scan[i] = 0u;
+    if (threadIdx.x < 6) bb[threadIdx.x] = threadIdx.x < 3 ? INFINITY : -INFINITY;
+    if (threadIdx.x == 0) *n_long = 0u;
+}
+
 // grid of a records kernel over n threads' worth of items: the blocks resident on the device at
 // once (a single wave of the grid-stride loop), fewer when the items need fewer
 template <class K> unsigned rec_grid(K kernel, int64_t n) {
@@ -750,10 +761,8 @@ static void free_handle(sdf_features_s *f) {
     if (!f) return;
     cudaDeviceSynchronize();  // no work may still use the handle's memory
     cudaStream_t s0 = 0;
-    void *ptrs[] = {f->soup_vid, f->face_soup, f->face_vid, f->face_edge, f->edge_vf, f->vert_start, f->vert_corner, f->vpos, f->face_rec,
-                    f->face_box, f->edge_rec, f->vert_rec, f->vert_plane, f->edge_class, f->vert_class, f->ctr};
-    for (void *p : ptrs)
-        if (p) pool_free(p, s0);
+    if (f->block) pool_free(f->block, s0);  // every array of the handle
+    if (f->ctr) pool_free(f->ctr, s0);
     sdf::plan_free(f->plan, s0);
     f->plan = nullptr;
     f->fwd_winner.release(s0);
@@ -765,6 +774,19 @@ static void free_handle(sdf_features_s *f) {
 template <class T> static cudaError_t dalloc_s(T **p, int64_t n, cudaStream_t s) {
     return pool_alloc(reinterpret_cast<void **>(p), sizeof(T) * (size_t)(n > 0 ? n : 1), s);
 }
+
+// Offsets of a handle's arrays within one allocation, each on a 256-byte boundary.
+struct HandleLayout {
+    size_t bytes = 0;
+    std::vector<std::pair<void **, size_t>> slots;
+    template <class T> void add(T *&p, int64_t n) {
+        slots.emplace_back(reinterpret_cast<void **>(&p), bytes);
+        bytes += (sizeof(T) * (size_t)(n > 0 ? n : 1) + 255) & ~(size_t)255;
+    }
+    void place(void *base) {
+        for (auto &sl : slots) *sl.first = static_cast<char *>(base) + sl.second;
+    }
+};
 
 #define B_TRY(expr)                                       \
     do {                                                  \
@@ -809,12 +831,11 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     void *scan_state = base + off_scan;
 
     B_TRY(dalloc_s(&f->ctr, 1, s));
-    B_TRY(cudaMemsetAsync(f->ctr, 0, sizeof(DevCounters), s));
     unsigned *const err = &f->ctr->status;  // a scan whose look-back ran out marks ST_TIMEOUT here
-    float bb_init[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-    B_TRY(cudaMemcpyAsync(bb, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
-    B_TRY(cudaMemsetAsync(n_long, 0, sizeof(unsigned), s));
-    B_TRY(cudaMemsetAsync(scan_state, 0, scan_bytes, s));
+    // counters, the bounding box, the long-run count and the scan state start cleared (one launch)
+    k_build_init<<<1, BT, 0, s>>>(reinterpret_cast<unsigned *>(f->ctr), sizeof(DevCounters) / sizeof(unsigned), bb,
+                                  n_long, reinterpret_cast<unsigned *>(scan_state), scan_bytes / sizeof(unsigned));
+    SDF_LAUNCHED(1);
     // about four corners per thread, at most four blocks per SM of this part
     k_soup_bounds<<<(unsigned)std::min<int64_t>((n + 4 * BT - 1) / (4 * BT), 4 * 152), BT, 0, s>>>(soup, n, bb, f->ctr);
     SDF_LAUNCHED(1);
@@ -844,13 +865,33 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     }
     const int64_t V = Vh;
     f->V = V;
-    B_TRY(dalloc_s(&f->soup_vid, n, s));
-    B_TRY(dalloc_s(&f->face_vid, n, s));
-    B_TRY(dalloc_s(&f->face_soup, T, s));
-    B_TRY(dalloc_s(&f->face_edge, n, s));
-    B_TRY(dalloc_s(&f->vert_start, V + 1, s));
-    B_TRY(dalloc_s(&f->vert_corner, n, s));
-    B_TRY(dalloc_s(&f->vpos, 3 * V, s));
+    if (n % 2) {  // a closed 2-manifold has 3T/2 edges
+        tmp.release(s);
+        free_handle(f);
+        return SDF_ERR_NONMANIFOLD;
+    }
+    const int64_t E = n / 2;
+    f->E = E;
+    {  // the handle's arrays, carved from one allocation (one pool call per build instead of 16)
+        HandleLayout L;
+        L.add(f->soup_vid, n);
+        L.add(f->face_vid, n);
+        L.add(f->face_soup, T);
+        L.add(f->face_edge, n);
+        L.add(f->vert_start, V + 1);
+        L.add(f->vert_corner, n);
+        L.add(f->vpos, 3 * V);
+        L.add(f->edge_vf, E);
+        L.add(f->face_rec, 4 * T);
+        L.add(f->face_box, 2 * T);
+        L.add(f->edge_rec, 5 * E);
+        L.add(f->edge_class, E);
+        L.add(f->vert_rec, 3 * V);
+        L.add(f->vert_plane, n);
+        L.add(f->vert_class, V);
+        B_TRY(pool_alloc(&f->block, L.bytes, s));
+        L.place(f->block);
+    }
     k_weld_scatter<<<nblk(n), BT, 0, s>>>(vals, head, keys, soup, n, f->soup_vid, f->vert_start, f->vert_corner,
                                           f->vpos);
     SDF_LAUNCHED(1);
@@ -868,33 +909,17 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
     // edge pairing through the vertex fans
-    if (n % 2) {
-        tmp.release(s);
-        free_handle(f);
-        return SDF_ERR_NONMANIFOLD;
-    }
-    const int64_t E = n / 2;
-    f->E = E;
     int32_t *twin = reinterpret_cast<int32_t *>(kalt);  // kalt is free again
     uint32_t *canon = valt;
     k_pair_fans<<<nblk(n), BT, 0, s>>>(f->vert_start, f->vert_corner, f->face_vid, n, twin, canon, f->ctr);
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
     B_TRY(scan_exclusive_u32(canon, head, n, true, scan_state, s, err));
-    B_TRY(dalloc_s(&f->edge_vf, E, s));
     // entries that no canonical edge writes (a broken mesh) stay -1 and are skipped by the records
     B_TRY(cudaMemsetAsync(f->edge_vf, 0xff, sizeof(int4) * (size_t)E, s));
     k_edge_emit<<<nblk(n), BT, 0, s>>>(f->vert_corner, f->face_vid, twin, canon, head, n, f->edge_vf, f->face_edge);
     SDF_LAUNCHED(1);
     B_TRY(cudaGetLastError());
-    // records
-    B_TRY(dalloc_s(&f->face_rec, 4 * T, s));
-    B_TRY(dalloc_s(&f->face_box, 2 * T, s));
-    B_TRY(dalloc_s(&f->edge_rec, 5 * E, s));
-    B_TRY(dalloc_s(&f->edge_class, E, s));
-    B_TRY(dalloc_s(&f->vert_rec, 3 * V, s));
-    B_TRY(dalloc_s(&f->vert_plane, n, s));
-    B_TRY(dalloc_s(&f->vert_class, V, s));
     // The records are built without first reading the connectivity status (one host round trip
     // fewer): on a broken mesh they only see valid indices (the weld's are valid by construction,
     // unpaired edges are skipped) and the status read below rejects the handle.
