@@ -168,6 +168,10 @@ struct Outputs {
     PatchEntry *patch;
     int64_t patch_cap;
     DevCounters *ctr;
+    // split tiles (see k_tile_lists): work items, per-slot merged keys and finished-item counts
+    const int2 *split_items = nullptr;
+    unsigned long long *split_keys = nullptr;
+    unsigned *split_done = nullptr;
 };
 
 // ----------------------------------------------------------------------------- boxes
@@ -849,20 +853,44 @@ __global__ void k_band_flags(const uint32_t *bin_start, int64_t n_tiles, uint32_
 // tiles, taken at the same time, share feature records in L2.  A tile's output depends on neither.
 constexpr int FILL_CHUNK = 32;
 
+//
+// A band tile with more than SPLIT_PAIRS pairs (a densely subdivided part of a mesh puts tens of
+// thousands of regions into a few tiles) is split: while slots last (split_cap), it takes a slot
+// and becomes S = min(ceil(np / SPLIT_PAIRS), SPLIT_MAX_ITEMS) work items, each a contiguous part
+// of its pairs, listed in split_items ahead of the band tiles; its own entry in band_list becomes
+// -1 (skipped).  An item packs (tile, slot | item << 12 | S << 20).
+constexpr int SPLIT_PAIRS = 2048, SPLIT_MAX_ITEMS = 64, SPLIT_SLOTS = 256;
+// the launch clears tile_hist, tile_cursor, n_split and n_split_items with one memset
+static_assert(offsetof(DevCounters, n_split_items) == offsetof(DevCounters, tile_hist) + 33 * sizeof(unsigned),
+              "the per-launch tile-list counters must be contiguous");
+
 __global__ void k_tile_lists(const uint32_t *bin_start, int64_t n_tiles, const uint32_t *band_pos,
-                             int32_t *band_list, int32_t *empty_list, DevCounters *ctr, int lpt) {
+                             int32_t *band_list, int32_t *empty_list, DevCounters *ctr, int lpt, int2 *split_items,
+                             int split_cap) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
     const uint32_t np = bin_start[3 * t + 3] - bin_start[3 * t];
-    if (np && !lpt) {
-        band_list[band_pos[t]] = (int32_t)t;
-    } else if (np) {
+    if (!np) {
+        empty_list[t - band_pos[t]] = (int32_t)t;
+        return;
+    }
+    int32_t entry = (int32_t)t;
+    if (np > (uint32_t)SPLIT_PAIRS && split_cap > 0) {
+        const unsigned slot = atomicAdd(&ctr->n_split, 1u);
+        if (slot < (unsigned)split_cap) {
+            const int S = (int)min((np + SPLIT_PAIRS - 1) / SPLIT_PAIRS, (uint32_t)SPLIT_MAX_ITEMS);
+            const unsigned base = atomicAdd(&ctr->n_split_items, (unsigned)S);  // < split_cap * SPLIT_MAX_ITEMS
+            for (int i = 0; i < S; i++) split_items[base + i] = make_int2((int)t, (int)(slot | i << 12 | S << 20));
+            entry = -1;
+        }
+    }
+    if (!lpt) {
+        band_list[band_pos[t]] = entry;
+    } else {
         const int c = tile_cost_class(np);
         uint32_t base = 0;
         for (int k = 0; k < c; k++) base += ctr->tile_hist[k];
-        band_list[base + atomicAdd(&ctr->tile_cursor[c], 1u)] = (int32_t)t;
-    } else {
-        empty_list[t - band_pos[t]] = (int32_t)t;
+        band_list[base + atomicAdd(&ctr->tile_cursor[c], 1u)] = entry;
     }
 }
 
@@ -939,11 +967,13 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
     extern __shared__ __align__(16) unsigned char tile_smem[];
     TileSmem<TY, TZ> &S = *reinterpret_cast<TileSmem<TY, TZ> *>(tile_smem);
     __shared__ unsigned s_cand, s_band, s_ovf, s_rows, s_hits, s_pairs;
-    __shared__ int s_kind;
+    __shared__ int s_kind, s_last;
     if (threadIdx.x == 0) { s_cand = 0; s_band = 0; s_ovf = 0; s_rows = 0; s_hits = 0; s_pairs = 0; }
     unsigned cand = 0, band = 0, rows = 0, hits = 0, pairs = 0;
     bool overflow = false, list_ovf = false;
     const int64_t n_band = *n_band_ptr, n_empty = n_tiles - n_band;
+    // the items of split tiles come first in the band queue (k_tile_lists)
+    const int64_t n_items = o.split_items ? min((int64_t)o.ctr->n_split_items, (int64_t)SPLIT_SLOTS * SPLIT_MAX_ITEMS) : 0;
     const int64_t n_chunks = dense ? (n_empty + FILL_CHUNK - 1) / FILL_CHUNK : 0;  // no field: no +inf fill
     for (;;) {
         if (threadIdx.x == 0) {
@@ -959,7 +989,7 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
             int kind = 0;
             for (int q = 0; q < 2 && w < 0; q++) {
                 const int k = (q == 0) == filler ? 1 : 0;  // 1: empty chunks, 0: band tiles
-                const long long lim = k ? n_chunks : n_band;
+                const long long lim = k ? n_chunks : n_items + n_band;
                 if ((long long)*(volatile unsigned long long *)(ticket + k) >= lim) continue;
                 const long long t = (long long)atomicAdd(ticket + k, 1ull);
                 if (t < lim) {
@@ -979,9 +1009,20 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
             fill_chunk<TY, TZ>(P, tile_base, n, empty_list, w * FILL_CHUNK, min((w + 1) * FILL_CHUNK, n_empty));
             continue;
         }
-        {  // a band tile
+        {  // a band tile, or an item of a split tile
             const bool is_band = true;
-            const int64_t tile = band_list[w];
+            int64_t tile;
+            int split_slot = -1, split_i = 0, split_n = 1;
+            if (w < n_items) {
+                const int2 it = o.split_items[w];
+                tile = it.x;
+                split_slot = it.y & 0xfff;
+                split_i = (it.y >> 12) & 0xff;
+                split_n = it.y >> 20;
+            } else {
+                tile = band_list[w - n_items];
+                if (tile < 0) continue;  // a split tile's own entry: its items do the work
+            }
             const int p = find_prob(tile_base, n, tile);
             const Prob &pr = P[p];
             const GridP &g = pr.g;
@@ -994,13 +1035,43 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
             int32_t *winner = pr.winner;
             if (is_band) {
                 const uint32_t *st = o.bin_start + 3 * tile;
-                const int64_t q0 = min((int64_t)st[0], o.pair_cap), q3 = min((int64_t)st[3], o.pair_cap);
+                int64_t q0 = min((int64_t)st[0], o.pair_cap), q3 = min((int64_t)st[3], o.pair_cap);
+                if (split_slot >= 0) {  // this item's contiguous part of the tile's pairs
+                    const int64_t np = q3 - q0;
+                    const int64_t qa = q0 + np * split_i / split_n, qb = q0 + np * (split_i + 1) / split_n;
+                    q0 = qa;
+                    q3 = qb;
+                }
                 for (int e = threadIdx.x; e < TP; e += NT) S.key[e] = ~0ull;
                 if (threadIdx.x == 0) S.next = 0;
                 __syncthreads();
                 process_band_tile<TY, TZ>(pr.F, g, o.pairs, q0, q3, x0, y0, z0, S, cand, rows, hits);
                 __syncthreads();  // every merge is in before the decode
                 if (threadIdx.x == 0) pairs += (unsigned)(q3 - q0);
+                if (split_slot >= 0) {
+                    // An item of a split tile: its keys go into the slot's keys in global memory
+                    // (atomicMin, the same minimum as in shared memory), and the CTA that finishes
+                    // the tile's last item decodes the merged keys (and clears the slot for the next
+                    // launch).  No CTA waits for another.
+                    unsigned long long *gk = o.split_keys + (size_t)split_slot * TP;
+                    for (int e = threadIdx.x; e < TP; e += NT) {
+                        const unsigned long long kv = S.key[e];
+                        if (kv != ~0ull) atomicMin(gk + e, kv);
+                    }
+                    __threadfence();
+                    __syncthreads();
+                    if (threadIdx.x == 0)
+                        s_last = atomicAdd(o.split_done + split_slot, 1u) == (unsigned)(split_n - 1) ? 1 : 0;
+                    __syncthreads();
+                    if (!s_last) continue;  // (uniform over the CTA)
+                    __threadfence();
+                    for (int e = threadIdx.x; e < TP; e += NT) {
+                        S.key[e] = __ldcg(gk + e);
+                        gk[e] = ~0ull;
+                    }
+                    if (threadIdx.x == 0) o.split_done[split_slot] = 0u;
+                    __syncthreads();
+                }
             }
             const bool list = LIST && is_band && pr.list != nullptr;
             const bool vec_rows = pr.vec && cx1 == x0 + TILE_X - 1;
@@ -1684,7 +1755,7 @@ struct Plan {
     int vmode = VM_EXACT;
     std::vector<long long> pbase;
     long long p_tot = 0;
-    DevBuf tables, bins, pairs, patch, scan_tmp, lists, rowsign, keys;
+    DevBuf tables, bins, pairs, patch, scan_tmp, lists, rowsign, keys, split;
     DevCounters *ctr = nullptr;
     bool own_ctr = false;
     int64_t pair_cap = 0, patch_cap = 0;
@@ -1740,6 +1811,7 @@ void plan_free(Plan *pl, cudaStream_t s) {
     pl->bins.release(s);
     pl->pairs.release(s);
     pl->patch.release(s);
+    pl->split.release(s);
     pl->scan_tmp.release(s);
     pl->lists.release(s);
     pl->rowsign.release(s);
@@ -1819,6 +1891,15 @@ static int plan_describe(Plan &pl, const sdf_features *feats, const sdf_grid *gr
     return SDF_OK;
 }
 
+// Layout of a plan's split-tile buffer: the keys of SPLIT_SLOTS tiles (sized for the largest tile
+// shape), the work items, the finished-item counts.
+static constexpr size_t SPLIT_TP_MAX = (size_t)TILE_X * 16 * 8;
+static constexpr size_t split_items_offset() { return sizeof(unsigned long long) * SPLIT_TP_MAX * SPLIT_SLOTS; }
+static constexpr size_t split_done_offset() {
+    return split_items_offset() + sizeof(int2) * (size_t)SPLIT_SLOTS * SPLIT_MAX_ITEMS;
+}
+static constexpr size_t split_bytes() { return split_done_offset() + sizeof(unsigned) * SPLIT_SLOTS; }
+
 // allocate scratch for the current capacities and upload the tables (not allowed while capturing)
 static int plan_reserve(Plan &pl, cudaStream_t s) {
     const int64_t n_bins = 3 * pl.n_tiles;
@@ -1828,6 +1909,15 @@ static int plan_reserve(Plan &pl, cudaStream_t s) {
     if (pl.fill) SDF_TRY(pl.rowsign.reserve((size_t)pl.r_tot + 64, s));
     if (pl.cell_loop) SDF_TRY(pl.keys.reserve(sizeof(unsigned long long) * (size_t)pl.p_tot, s));
     SDF_TRY(pl.bins.reserve(sizeof(uint32_t) * (size_t)(2 * n_bins + 64), s));
+    if (!pl.cell_loop) {  // split tiles: items, per-slot keys (kept at ~0 between launches) and counts
+        void *const before = pl.split.p;
+        SDF_TRY(pl.split.reserve(split_bytes(), s));
+        if (pl.split.p != before) {
+            SDF_TRY(cudaMemsetAsync(pl.split.p, 0xff, split_bytes(), s));
+            SDF_TRY(cudaMemsetAsync(static_cast<char *>(pl.split.p) + split_done_offset(), 0,
+                                    sizeof(unsigned) * SPLIT_SLOTS, s));
+        }
+    }
     {  // the scan state starts cleared whenever its memory is new (see scan_exclusive_u32)
         void *const before = pl.scan_tmp.p;
         SDF_TRY(pl.scan_tmp.reserve(scan_state_bytes(n_bins), s));
@@ -1911,6 +2001,10 @@ struct Scratch {  // device pointers used by one launch of the pipeline
     const long long *pbase = nullptr;
     long long p_tot = 0;
     unsigned long long *keys = nullptr;
+    // split tiles (null: not used, as in the allocation-free entry point)
+    unsigned long long *split_keys = nullptr;
+    int2 *split_items = nullptr;
+    unsigned *split_done = nullptr;
 };
 
 static Scratch plan_scratch(const Plan &pl) {
@@ -1952,6 +2046,12 @@ static Scratch plan_scratch(const Plan &pl) {
     sc.patch = pl.patch.as<PatchEntry>();
     sc.patch_cap = pl.patch_cap;
     sc.ctr = pl.ctr;
+    if (pl.split.p) {
+        char *b = static_cast<char *>(pl.split.p);
+        sc.split_keys = reinterpret_cast<unsigned long long *>(b);
+        sc.split_items = reinterpret_cast<int2 *>(b + split_items_offset());
+        sc.split_done = reinterpret_cast<unsigned *>(b + split_done_offset());
+    }
     return sc;
 }
 
@@ -1978,14 +2078,15 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
     SDF_TRY(cudaGetLastError());
     // band / empty tile lists for the persistent tile kernel (one scan of the band flags)
     uint32_t *flags = sc.cnt;  // the fill cursors are no longer needed
-    SDF_TRY(cudaMemsetAsync(sc.ctr->tile_hist, 0, 2 * N_COST_CLASSES * sizeof(unsigned), s));
+    // cost-class counts and cursors, and the split-tile counts (contiguous in DevCounters)
+    SDF_TRY(cudaMemsetAsync(sc.ctr->tile_hist, 0, (2 * N_COST_CLASSES + 2) * sizeof(unsigned), s));
     const int lpt = n > 1;  // largest-first order of the band tiles for batches
     k_band_flags<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, flags, sc.ctr, lpt);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
     SDF_TRY(scan_exclusive_u32(flags, sc.band_pos, n_tiles, true, sc.scan_tmp, s, &sc.ctr->nb_status));
     k_tile_lists<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, sc.band_pos, sc.band_list, sc.empty_list,
-                                                    sc.ctr, lpt);
+                                                    sc.ctr, lpt, sc.split_items, sc.split_items ? SPLIT_SLOTS : 0);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaMemsetAsync(sc.ticket, 0, 2 * sizeof(unsigned long long), s));  // band and fill tickets
     Outputs o;
@@ -1995,6 +2096,9 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
     o.patch = sc.patch;
     o.patch_cap = sc.patch_cap;
     o.ctr = sc.ctr;
+    o.split_items = sc.split_items;
+    o.split_keys = sc.split_keys;
+    o.split_done = sc.split_done;
     if (ev) SDF_TRY(record_event(ev[1], s));
     if (sc.any_list) {
         const int64_t ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm<TY, TZ, true>() * num_sms());

@@ -70,6 +70,8 @@ struct DevCounters {
     unsigned long long cls[8];         // classification counts
     unsigned tile_hist[16];            // band tiles per cost class (class 0: the most pairs)
     unsigned tile_cursor[16];          // fill cursors of the classes in the band tile list
+    unsigned n_split;                  // band tiles split over several CTAs (slots taken)
+    unsigned n_split_items;            // their work items
     // Precision terms of the current positions (FP32 bits of non-negative floats, so an unsigned
     // atomicMax takes their maximum), written by the records kernels: PREC_MESH_M the largest
     // vertex coordinate magnitude, PREC_TAU_A / PREC_TAU_B the shape term of the FP32 plane

@@ -277,3 +277,35 @@ def test_unsynchronised_call_on_a_fresh_handle_has_room(N):
         assert st["pairs"] > 8 * (feats.n_tri + feats.n_edge + feats.n_vert) + 4096
     ref = sdf.sdf_narrow_band(sdf.sdf_build_features(torch.from_numpy(soup).cuda()), grid, w)
     assert torch.equal(dist, ref)
+
+
+def test_split_tiles_agree_bitwise_with_unsplit_paths():
+    """A densely subdivided part puts about 250 k regions into a few tiles, which the tile kernel
+    splits over many CTAs (their keys merged with atomicMin in global memory, the last item decoding
+    the tile).  The merge is order-independent, so the field equals bit for bit the allocation-free
+    entry point's (which never splits), the band-list call's, and a batch's (split tiles listed in
+    largest-first order); the full-grid oracle comparison of the same mesh is
+    test_small_meshes_full_grid_dyadic[dense_cluster]."""
+    import ctypes
+    soup = TINY["dense_cluster"]().soup(seed=5)
+    grid, w = sdf.Grid.cube(96), 3 / 96
+    feats = sdf.sdf_build_features(torch.from_numpy(soup).cuda())
+    dist, win = sdf.sdf_narrow_band(feats, grid, w, winner=True)
+    st = feats.status()
+    assert st["pairs"] > 100_000
+    d_static = torch.empty_like(dist)
+    w_static = torch.empty_like(win)
+    L = sdf.load_library()
+    cg = grid.c()
+    assert L.sdf_narrow_band_static(feats.handle, ctypes.byref(cg), ctypes.c_float(w), d_static.data_ptr(),
+                                    w_static.data_ptr(), torch.cuda.current_stream().cuda_stream) == 0
+    assert torch.equal(dist, d_static) and torch.equal(win, w_static)
+    d_list, bl = sdf.sdf_narrow_band_list(feats, grid, w)
+    assert torch.equal(dist, d_list)
+    other = sdf.sdf_build_features(torch.from_numpy(meshgen.icosphere(6, radius=0.3).soup(seed=6)).cuda())
+    b = sdf.sdf_batch_create([other, feats], [sdf.Grid.cube(64), grid], [3 / 64, w])
+    b.run()
+    torch.cuda.synchronize()
+    assert torch.equal(b.outs[1], dist)
+    assert torch.equal(b.outs[0], sdf.sdf_narrow_band(other, sdf.Grid.cube(64), 3 / 64))
+    b.destroy()
