@@ -949,6 +949,33 @@ __device__ __forceinline__ void fill_chunk(const Prob *P, const long long *tile_
     }
 }
 
+// An item of a split tile: its keys go into the slot's keys in global memory (atomicMin, the same
+// minimum as in shared memory); the CTA that finishes the tile's last item takes the merged keys
+// back into shared memory (and clears the slot for the next launch) and returns true: it decodes
+// the tile.  No CTA waits for another.  Kept out of line, so that the band work of the tile kernel
+// compiles as without it (inlined, it cost the kernel about 12 %).
+template <int TP>
+__device__ __noinline__ bool split_merge(const Outputs &o, unsigned long long *key, int slot, int n_items, int &s_last) {
+    unsigned long long *gk = o.split_keys + (size_t)slot * TP;
+    for (int e = threadIdx.x; e < TP; e += NT) {
+        const unsigned long long kv = key[e];
+        if (kv != ~0ull) atomicMin(gk + e, kv);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(o.split_done + slot, 1u) == (unsigned)(n_items - 1) ? 1 : 0;
+    __syncthreads();
+    if (!s_last) return false;  // (uniform over the CTA)
+    __threadfence();
+    for (int e = threadIdx.x; e < TP; e += NT) {
+        key[e] = __ldcg(gk + e);
+        gk[e] = ~0ull;
+    }
+    if (threadIdx.x == 0) o.split_done[slot] = 0u;
+    __syncthreads();
+    return true;
+}
+
 // Persistent tile kernel over all tiles of all problems of a batch.  Two work queues, each with
 // its own atomic ticket: the band tiles (one per item, largest first for batches) and chunks of
 // FILL_CHUNK empty tiles.  The CTAs of a fifth of the SMs start on the empty chunks, the others on
@@ -957,8 +984,10 @@ __device__ __forceinline__ void fill_chunk(const Prob *P, const long long *tile_
 // (Algorithm 1's initial value).  The dense output goes out with streaming (evict-first) stores,
 // so that the write stream does not push the feature records that the band work reads out of
 // L2.  LIST: some problem of the launch writes a compact band list (compiled apart, so that the
-// plain kernel carries none of its code).
-template <int TY, int TZ, bool LIST>
+// plain kernel carries none of its code).  SPLIT: the launch that works on the items of split
+// tiles (k_tile_lists) alone, before the launch of the band tiles and the fill; compiled apart
+// too, since the split path in the same kernel cost the band work about 12 %.
+template <int TY, int TZ, bool LIST, bool SPLIT>
 __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *tile_base, int n, Outputs o,
                                                 int64_t n_tiles, const int32_t *band_list,
                                                 const int32_t *empty_list, const uint32_t *n_band_ptr,
@@ -972,9 +1001,10 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
     unsigned cand = 0, band = 0, rows = 0, hits = 0, pairs = 0;
     bool overflow = false, list_ovf = false;
     const int64_t n_band = *n_band_ptr, n_empty = n_tiles - n_band;
-    // the items of split tiles come first in the band queue (k_tile_lists)
-    const int64_t n_items = o.split_items ? min((int64_t)o.ctr->n_split_items, (int64_t)SPLIT_SLOTS * SPLIT_MAX_ITEMS) : 0;
-    const int64_t n_chunks = dense ? (n_empty + FILL_CHUNK - 1) / FILL_CHUNK : 0;  // no field: no +inf fill
+    // the items of split tiles (the SPLIT launch's only work; the other launch skips those tiles)
+    const int64_t n_items = SPLIT ? min((int64_t)o.ctr->n_split_items, (int64_t)SPLIT_SLOTS * SPLIT_MAX_ITEMS) : 0;
+    if (SPLIT) ticket += 2;  // its own ticket
+    const int64_t n_chunks = dense && !SPLIT ? (n_empty + FILL_CHUNK - 1) / FILL_CHUNK : 0;  // no field: no +inf fill
     for (;;) {
         if (threadIdx.x == 0) {
             // The CTAs of every fifth SM start on the fill queue, the others on the band tiles.  An
@@ -989,7 +1019,7 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
             int kind = 0;
             for (int q = 0; q < 2 && w < 0; q++) {
                 const int k = (q == 0) == filler ? 1 : 0;  // 1: empty chunks, 0: band tiles
-                const long long lim = k ? n_chunks : n_items + n_band;
+                const long long lim = k ? n_chunks : (SPLIT ? n_items : n_band);
                 if ((long long)*(volatile unsigned long long *)(ticket + k) >= lim) continue;
                 const long long t = (long long)atomicAdd(ticket + k, 1ull);
                 if (t < lim) {
@@ -1013,15 +1043,15 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
             const bool is_band = true;
             int64_t tile;
             int split_slot = -1, split_i = 0, split_n = 1;
-            if (w < n_items) {
+            if (SPLIT) {
                 const int2 it = o.split_items[w];
                 tile = it.x;
                 split_slot = it.y & 0xfff;
                 split_i = (it.y >> 12) & 0xff;
                 split_n = it.y >> 20;
             } else {
-                tile = band_list[w - n_items];
-                if (tile < 0) continue;  // a split tile's own entry: its items do the work
+                tile = band_list[w];
+                if (tile < 0) continue;  // a split tile's own entry: the SPLIT launch does its work
             }
             const int p = find_prob(tile_base, n, tile);
             const Prob &pr = P[p];
@@ -1036,7 +1066,7 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
             if (is_band) {
                 const uint32_t *st = o.bin_start + 3 * tile;
                 int64_t q0 = min((int64_t)st[0], o.pair_cap), q3 = min((int64_t)st[3], o.pair_cap);
-                if (split_slot >= 0) {  // this item's contiguous part of the tile's pairs
+                if (SPLIT) {  // this item's contiguous part of the tile's pairs
                     const int64_t np = q3 - q0;
                     const int64_t qa = q0 + np * split_i / split_n, qb = q0 + np * (split_i + 1) / split_n;
                     q0 = qa;
@@ -1048,30 +1078,7 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
                 process_band_tile<TY, TZ>(pr.F, g, o.pairs, q0, q3, x0, y0, z0, S, cand, rows, hits);
                 __syncthreads();  // every merge is in before the decode
                 if (threadIdx.x == 0) pairs += (unsigned)(q3 - q0);
-                if (split_slot >= 0) {
-                    // An item of a split tile: its keys go into the slot's keys in global memory
-                    // (atomicMin, the same minimum as in shared memory), and the CTA that finishes
-                    // the tile's last item decodes the merged keys (and clears the slot for the next
-                    // launch).  No CTA waits for another.
-                    unsigned long long *gk = o.split_keys + (size_t)split_slot * TP;
-                    for (int e = threadIdx.x; e < TP; e += NT) {
-                        const unsigned long long kv = S.key[e];
-                        if (kv != ~0ull) atomicMin(gk + e, kv);
-                    }
-                    __threadfence();
-                    __syncthreads();
-                    if (threadIdx.x == 0)
-                        s_last = atomicAdd(o.split_done + split_slot, 1u) == (unsigned)(split_n - 1) ? 1 : 0;
-                    __syncthreads();
-                    if (!s_last) continue;  // (uniform over the CTA)
-                    __threadfence();
-                    for (int e = threadIdx.x; e < TP; e += NT) {
-                        S.key[e] = __ldcg(gk + e);
-                        gk[e] = ~0ull;
-                    }
-                    if (threadIdx.x == 0) o.split_done[split_slot] = 0u;
-                    __syncthreads();
-                }
+                if (SPLIT && !split_merge<TP>(o, S.key, split_slot, split_n, s_last)) continue;
             }
             const bool list = LIST && is_band && pr.list != nullptr;
             const bool vec_rows = pr.vec && cx1 == x0 + TILE_X - 1;
@@ -1679,12 +1686,12 @@ static int num_sms() {
     return n;
 }
 
-template <int TY, int TZ, bool LIST> static int tile_blocks_per_sm() {
+template <int TY, int TZ, bool LIST, bool SPLIT = false> static int tile_blocks_per_sm() {
     static int b = 0;
     if (!b) {
-        cudaFuncSetAttribute(k_tile<TY, TZ, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_tile<TY, TZ, LIST, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(TileSmem<TY, TZ>));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tile<TY, TZ, LIST>, NT, sizeof(TileSmem<TY, TZ>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tile<TY, TZ, LIST, SPLIT>, NT, sizeof(TileSmem<TY, TZ>));
         if (b <= 0) b = 1;
     }
     return b;
@@ -1923,7 +1930,7 @@ static int plan_reserve(Plan &pl, cudaStream_t s) {
         SDF_TRY(pl.scan_tmp.reserve(scan_state_bytes(n_bins), s));
         if (pl.scan_tmp.p != before) SDF_TRY(cudaMemsetAsync(pl.scan_tmp.p, 0, pl.scan_tmp.bytes, s));
     }
-    SDF_TRY(pl.lists.reserve(16 + sizeof(uint32_t) * (size_t)(3 * pl.n_tiles + 256), s));
+    SDF_TRY(pl.lists.reserve(32 + sizeof(uint32_t) * (size_t)(3 * pl.n_tiles + 256), s));
     // room for the expected pairs (with a quarter to spare), and never less than 8 per feature;
     // a synchronising call grows it further when the binning finds more.  SDF_PAIR_CAPACITY, when
     // set, replaces the first capacity (to exercise that growth in tests).
@@ -2038,7 +2045,7 @@ static Scratch plan_scratch(const Plan &pl) {
     sc.start = sc.cnt + 3 * pl.n_tiles + 32;
     sc.scan_tmp = pl.scan_tmp.p;
     sc.ticket = pl.lists.as<unsigned long long>();  // 8-byte aligned (allocation start)
-    sc.band_pos = reinterpret_cast<uint32_t *>(sc.ticket + 2);
+    sc.band_pos = reinterpret_cast<uint32_t *>(sc.ticket + 4);  // tickets: band, fill, split items
     sc.band_list = reinterpret_cast<int32_t *>(sc.band_pos + pl.n_tiles + 32);
     sc.empty_list = sc.band_list + pl.n_tiles + 32;
     sc.pairs = pl.pairs.as<int2>();
@@ -2088,7 +2095,8 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
     k_tile_lists<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, sc.band_pos, sc.band_list, sc.empty_list,
                                                     sc.ctr, lpt, sc.split_items, sc.split_items ? SPLIT_SLOTS : 0);
     SDF_LAUNCHED(1);
-    SDF_TRY(cudaMemsetAsync(sc.ticket, 0, 2 * sizeof(unsigned long long), s));  // band and fill tickets
+    // band, fill and split-item tickets (the allocation-free entry point has the first two only)
+    SDF_TRY(cudaMemsetAsync(sc.ticket, 0, (sc.split_items ? 3 : 2) * sizeof(unsigned long long), s));
     Outputs o;
     o.pairs = sc.pairs;
     o.bin_start = sc.start;
@@ -2102,12 +2110,30 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
     if (ev) SDF_TRY(record_event(ev[1], s));
     if (sc.any_list) {
         const int64_t ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm<TY, TZ, true>() * num_sms());
-        k_tile<TY, TZ, true><<<(unsigned)ctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
+        if (sc.split_items) {  // the items of split tiles (none in most launches: the CTAs then return at once)
+            // one CTA per SM: a few tiles' items at most, and a cheap launch when there are none
+            tile_blocks_per_sm<TY, TZ, true, true>();  // (sets the kernel's shared-memory limit once)
+            const int64_t sctas = std::min<int64_t>(n_tiles, (int64_t)num_sms());
+            k_tile<TY, TZ, true, true><<<(unsigned)sctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
+                sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket,
+                sc.any_dense ? 1 : 0);
+            SDF_LAUNCHED(1);
+        }
+        k_tile<TY, TZ, true, false><<<(unsigned)ctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
             sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket,
             sc.any_dense ? 1 : 0);
     } else {
         const int64_t ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm<TY, TZ, false>() * num_sms());
-        k_tile<TY, TZ, false><<<(unsigned)ctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
+        if (sc.split_items) {
+            // one CTA per SM: a few tiles' items at most, and a cheap launch when there are none
+            tile_blocks_per_sm<TY, TZ, false, true>();  // (sets the kernel's shared-memory limit once)
+            const int64_t sctas = std::min<int64_t>(n_tiles, (int64_t)num_sms());
+            k_tile<TY, TZ, false, true><<<(unsigned)sctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
+                sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket,
+                sc.any_dense ? 1 : 0);
+            SDF_LAUNCHED(1);
+        }
+        k_tile<TY, TZ, false, false><<<(unsigned)ctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
             sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket,
             sc.any_dense ? 1 : 0);
     }
