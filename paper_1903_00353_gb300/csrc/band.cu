@@ -854,12 +854,14 @@ __global__ void k_band_flags(const uint32_t *bin_start, int64_t n_tiles, uint32_
 constexpr int FILL_CHUNK = 32;
 
 //
-// A band tile with more than SPLIT_PAIRS pairs (a densely subdivided part of a mesh puts tens of
+// A band tile with more than SPLIT_MIN pairs (a densely subdivided part of a mesh puts tens of
 // thousands of regions into a few tiles) is split: while slots last (split_cap), it takes a slot
 // and becomes S = min(ceil(np / SPLIT_PAIRS), SPLIT_MAX_ITEMS) work items, each a contiguous part
-// of its pairs, listed in split_items ahead of the band tiles; its own entry in band_list becomes
-// -1 (skipped).  An item packs (tile, slot | item << 12 | S << 20).
-constexpr int SPLIT_PAIRS = 2048, SPLIT_MAX_ITEMS = 64, SPLIT_SLOTS = 256;
+// of its pairs, listed in split_items for the SPLIT launch of the tile kernel; its own entry in
+// band_list becomes -1 (skipped).  An item packs (tile, slot | item << 12 | S << 20).  Tiles of a
+// few thousand pairs (the knot tube at 512^3 has some) stay whole: their split items, run in a
+// launch of their own, cost more than they gain.
+constexpr int SPLIT_MIN = 8192, SPLIT_PAIRS = 2048, SPLIT_MAX_ITEMS = 64, SPLIT_SLOTS = 256;
 // the launch clears tile_hist, tile_cursor, n_split and n_split_items with one memset
 static_assert(offsetof(DevCounters, n_split_items) == offsetof(DevCounters, tile_hist) + 33 * sizeof(unsigned),
               "the per-launch tile-list counters must be contiguous");
@@ -875,7 +877,7 @@ __global__ void k_tile_lists(const uint32_t *bin_start, int64_t n_tiles, const u
         return;
     }
     int32_t entry = (int32_t)t;
-    if (np > (uint32_t)SPLIT_PAIRS && split_cap > 0) {
+    if (np > (uint32_t)SPLIT_MIN && split_cap > 0) {
         const unsigned slot = atomicAdd(&ctr->n_split, 1u);
         if (slot < (unsigned)split_cap) {
             const int S = (int)min((np + SPLIT_PAIRS - 1) / SPLIT_PAIRS, (uint32_t)SPLIT_MAX_ITEMS);
