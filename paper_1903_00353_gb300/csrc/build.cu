@@ -763,7 +763,7 @@ static void free_handle(sdf_features_s *f) {
     cudaStream_t s0 = 0;
     if (f->block) pool_free(f->block, s0);  // every array of the handle
     if (f->ctr) pool_free(f->ctr, s0);
-    sdf::plan_free(f->plan, s0);
+    sdf::plan_park(f->plan, s0);
     f->plan = nullptr;
     f->fwd_winner.release(s0);
     for (cudaEvent_t e : f->ev)

@@ -89,6 +89,8 @@ constexpr float U32 = 5.9604644775390625e-8f;
 
 struct Plan;
 void plan_free(Plan *pl, cudaStream_t s);
+// keep a destroyed handle's plan (with its scratch) for the next handle on the device
+void plan_park(Plan *pl, cudaStream_t s);
 
 // compact band list of one problem (see sdf_narrow_band_list)
 struct ListOut {
