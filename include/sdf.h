@@ -464,7 +464,10 @@ int sdf_band_list_l2(sdf_features f, const sdf_grid *grid, const sdf_band_entry 
                      float *grad_vertices, double *loss_out, unsigned long long *band_out, uint32_t flags,
                      void *stream);
 
-/* Release the handle and its device memory (NULL is a no-op). */
+/* Release the handle and its device memory (NULL is a no-op).  Waits for the device.  The scratch
+ * of its narrow-band calls (pair list, bins, tile lists) is kept for the next handle's first call
+ * on the same device, at most two such sets per device: a loop that builds a handle per step then
+ * allocates nothing per step. */
 void sdf_features_destroy(sdf_features f);
 
 /* Static description of a status code. */
