@@ -57,7 +57,7 @@ typedef enum sdf_status {
     SDF_ERR_TOO_LARGE = 5,    /* sizes beyond the index ranges (2^31 features, 2^31 rows)  */
     SDF_ERR_OOM = 6,          /* device allocation failed                                 */
     SDF_ERR_CUDA = 7,         /* a CUDA runtime call failed                               */
-    SDF_ERR_TIMEOUT = 8,      /* a bounded device wait gave up (a scan's look-back)       */
+    SDF_ERR_TIMEOUT = 8,      /* a bounded device wait gave up (a look-back or a barrier) */
     SDF_ERR_LIST_OVERFLOW = 9 /* the caller's band list holds fewer entries than the band
                                  has points; its count holds the length needed             */
 } sdf_status;
@@ -131,9 +131,15 @@ typedef struct sdf_features_s *sdf_features;
  *   flags  0 or SDF_FLAG_DISABLE_SADDLE.
  *   out    host pointer receiving the new handle (NULL on error).
  *
- * Synchronises `stream` once (sizes and the status word).  Errors:
- * SDF_ERR_INVALID_ARG, SDF_ERR_NONFINITE, SDF_ERR_DEGENERATE,
- * SDF_ERR_NONMANIFOLD, SDF_ERR_TOO_LARGE, SDF_ERR_OOM, SDF_ERR_CUDA.
+ * Synchronises `stream` twice (the welded vertex count; the sizes and the
+ * status word at the end).  The two sorts (the weld's and the spatial face
+ * order) each run in one cooperative launch when their tiles fit on the
+ * device at once, else in three launches per 8-bit pass; the environment
+ * variable SDF_RADIX_ONE_LAUNCH=0 selects the latter always (both give the
+ * same result).  Errors: SDF_ERR_INVALID_ARG, SDF_ERR_NONFINITE,
+ * SDF_ERR_DEGENERATE, SDF_ERR_NONMANIFOLD, SDF_ERR_TOO_LARGE, SDF_ERR_OOM,
+ * SDF_ERR_CUDA, SDF_ERR_TIMEOUT (a bounded device wait of a scan or a sort
+ * ran out).
  */
 int sdf_build_features(const float *soup, int64_t n_tri, uint32_t flags, void *stream, sdf_features *out);
 

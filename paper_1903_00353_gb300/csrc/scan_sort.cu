@@ -5,9 +5,13 @@
 // hand-written stable radix sort of (64-bit key, 32-bit payload) pairs: 8-bit
 // digits, a per-tile histogram pass, a device-wide scan of the digit offsets and a
 // scatter pass that ranks keys inside each warp with __match_any_sync and stages
-// the tile in shared memory so global writes of one digit run are contiguous.
+// the tile in shared memory so global writes of one digit run are contiguous.  A
+// sort whose tiles all fit on the GPU at once runs every pass in one cooperative
+// launch instead.
+#include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -75,8 +79,8 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_apply(const uint32_t *in, u
 // its tile from a ticket, so it only ever waits for tiles whose CTAs have already started; it
 // publishes its tile's total (AGGREGATE), then sums its predecessors' words walking back 32 at a
 // time until one carries an inclusive prefix (PREFIX), and publishes its own inclusive prefix.
-// The state region: [0] ticket, [1] epoch, then one 64-bit word per tile, epoch << 34 | flag << 32 |
-// value.  Words of earlier scans carry an older epoch and count as not yet published.  The CTA
+// The state region: [0] ticket, [1] epoch, [2] and [3] the one-launch radix sort's grid barrier
+// (below; unused here), then one 64-bit word per tile, epoch << 34 | flag << 32 | value.  Words of earlier scans carry an older epoch and count as not yet published.  The CTA
 // that draws the last ticket puts the ticket back to 0, and the one holding the last tile
 // advances the epoch when it is done (by then every CTA has read it), so the region is ready for
 // the next scan issued after this one on the stream.  A wait that runs out of polls marks
@@ -293,6 +297,155 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *kin, 
     }
 }
 
+// ---------------------------------------------------------------------------- one-launch sort
+// A sort whose tiles can all be resident at once runs every pass in one cooperative launch, one
+// CTA per tile.  Per pass: (1) each CTA loads its tile's keys into registers, ranks them by digit
+// as the scatter pass above does, and writes its 256 digit counts (digit-major); grid barrier;
+// (2) the counts of each digit are scanned over the tiles, one CTA per digit, and the digit's
+// total is stored; grid barrier; (3) each CTA adds the digits' global starts to its own prefixes
+// and scatters its keys in place: every key of the pass is already in registers, so the pass
+// needs no second buffer; grid barrier (the next pass reads what the others wrote).  Data written
+// by other CTAs is read past L1 (ld.global.cg).  Against the three launches per pass above (a
+// histogram, a scan and a scatter) this makes 1 launch per sort.
+constexpr unsigned RS_POLL_LIMIT = 1u << 20;
+
+// Grid barrier of a cooperative launch on bar[0] (arrivals, 0 between barriers) and bar[1]
+// (generation): the last CTA to arrive clears the arrivals and advances the generation; the others
+// wait until it reaches `target`.  A wait that runs out of polls marks ST_TIMEOUT in *err and
+// returns false (the CTA then ends; the others run out at their next barrier).
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, unsigned *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();  // the CTA's writes (ordered before this thread by the block barrier) first
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned polls = 0;
+            while ((int)(*(volatile unsigned *)(bar + 1) - target) < 0) {
+                if (++polls > RS_POLL_LIMIT) {
+                    ok = 0;
+                    if (err) atomicOr(err, ST_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int ITEMS>
+constexpr size_t rs_one_smem() {
+    return (size_t)RS_THREADS * ITEMS * (sizeof(uint64_t) + sizeof(uint32_t)) +
+           (size_t)RS_WARPS * RADIX * sizeof(uint32_t) + 2 * RADIX * sizeof(uint32_t);
+}
+
+template <int ITEMS>
+__global__ void __launch_bounds__(RS_THREADS) k_rs_one(uint64_t *keys, uint32_t *vals, int64_t n, int passes,
+                                                       uint32_t *counts, uint32_t *totals, unsigned *bar,
+                                                       unsigned *err) {
+    constexpr int TILE = RS_THREADS * ITEMS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *skey = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *sval = reinterpret_cast<uint32_t *>(skey + TILE);
+    uint32_t *wcnt = sval + TILE;                // [RS_WARPS][RADIX]
+    uint32_t *bstart = wcnt + RS_WARPS * RADIX;  // [RADIX] start of each digit's run in the tile
+    uint32_t *gofs = bstart + RADIX;             // [RADIX] where that run goes in the output
+    __shared__ unsigned s_gen;
+    __shared__ uint32_t s_tot;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned nb = gridDim.x, t = blockIdx.x;
+    if (threadIdx.x == 0) s_gen = *(volatile unsigned *)(bar + 1);  // before the first arrival
+    __syncthreads();
+    unsigned target = s_gen;
+    const int64_t tile0 = (int64_t)t * TILE;
+    const int64_t wbase = tile0 + (int64_t)warp * (32 * ITEMS);
+    const int cnt = (int)(n - tile0 < (int64_t)TILE ? n - tile0 : (int64_t)TILE);
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t *mycnt = wcnt + warp * RADIX;
+    for (int p = 0; p < passes; p++) {
+        const int shift = 8 * p;
+        // (1) ranks within the tile: lanes in order within a warp, warps in order (stable)
+        for (int i = threadIdx.x; i < RS_WARPS * RADIX; i += RS_THREADS) wcnt[i] = 0;
+        __syncthreads();
+        uint64_t k[ITEMS];
+        uint32_t v[ITEMS], rank[ITEMS];
+#pragma unroll
+        for (int it = 0; it < ITEMS; it++) {
+            const int64_t idx = wbase + it * 32 + lane;
+            const bool valid = idx < n;
+            k[it] = valid ? __ldcg(keys + idx) : 0ull;
+            v[it] = valid ? __ldcg(vals + idx) : 0u;
+            const unsigned d = valid ? ((unsigned)(k[it] >> shift) & (RADIX - 1)) : (RADIX + lane);
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t before = valid ? mycnt[d] : 0u;
+            __syncwarp();
+            if (valid && (peers & lt_mask) == 0u) mycnt[d] = before + __popc(peers);
+            __syncwarp();
+            rank[it] = before + __popc(peers & lt_mask);
+        }
+        __syncthreads();
+        {  // thread d: prefix of digit d over the warps, the tile's count, its start in the tile
+            uint32_t run = 0;
+            for (int w = 0; w < RS_WARPS; w++) {
+                const uint32_t c = wcnt[w * RADIX + threadIdx.x];
+                wcnt[w * RADIX + threadIdx.x] = run;
+                run += c;
+            }
+            counts[(int64_t)threadIdx.x * nb + t] = run;
+            bstart[threadIdx.x] = block_excl_scan_u32(run, &s_tot);
+        }
+        if (!grid_barrier(bar, ++target, err)) return;
+        // (2) exclusive scan of digit d's counts over the tiles, in place, and the digit's total
+        for (unsigned d = t; d < (unsigned)RADIX; d += nb) {
+            uint32_t *row = counts + (int64_t)d * nb;
+            const unsigned per = (nb + RS_THREADS - 1) / RS_THREADS;
+            const unsigned j0 = min(threadIdx.x * per, nb), j1 = min(j0 + per, nb);
+            uint32_t s = 0;
+            for (unsigned j = j0; j < j1; j++) s += __ldcg(row + j);
+            uint32_t run = block_excl_scan_u32(s, &s_tot);
+            for (unsigned j = j0; j < j1; j++) {
+                const uint32_t c = __ldcg(row + j);
+                row[j] = run;
+                run += c;
+            }
+            if (threadIdx.x == 0) totals[d] = s_tot;
+        }
+        if (!grid_barrier(bar, ++target, err)) return;
+        // (3) global start of the tile's run of digit d: the totals of the smaller digits plus the
+        // counts of digit d in the tiles before this one
+        {
+            const uint32_t start = block_excl_scan_u32(__ldcg(totals + threadIdx.x), &s_tot);
+            gofs[threadIdx.x] = start + __ldcg(counts + (int64_t)threadIdx.x * nb + t);
+        }
+#pragma unroll
+        for (int it = 0; it < ITEMS; it++) {
+            const int64_t idx = wbase + it * 32 + lane;
+            if (idx < n) {
+                const unsigned d = (unsigned)(k[it] >> shift) & (RADIX - 1);
+                const uint32_t lp = bstart[d] + mycnt[d] + rank[it];
+                skey[lp] = k[it];
+                sval[lp] = v[it];
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += RS_THREADS) {
+            const uint64_t key = skey[i];
+            const unsigned d = (unsigned)(key >> shift) & (RADIX - 1);
+            const int64_t g = (int64_t)gofs[d] + (i - (int64_t)bstart[d]);
+            keys[g] = key;
+            vals[g] = sval[i];
+        }
+        if (p + 1 < passes && !grid_barrier(bar, ++target, err)) return;  // the kernel's end orders the last
+    }
+}
+
 // keys per thread: the largest of 8, 4, 2 that still gives at least one tile per SM (the SM
 // count of this part; the count only changes the choice, not the result).  16 keys per thread
 // would need 127 registers, two CTAs per SM: the 6.3 M-key sort of the knot tube ran its scatter
@@ -342,6 +495,56 @@ cudaError_t rs_passes(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     }
     return cudaSuccess;
 }
+
+// CTAs of k_rs_one<ITEMS> that the current device can hold at once (0 where it has no cooperative
+// launch), found once per device
+template <int ITEMS>
+cudaError_t rs_one_capacity(int64_t *cap) {
+    static std::atomic<int> known[64];  // static storage: starts at 0, "not yet known"
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    int c = known[dev].load(std::memory_order_relaxed);
+    if (c == 0) {
+        int per_sm = 0, n_sm = 0, coop = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rs_one<ITEMS>, RS_THREADS, rs_one_smem<ITEMS>());
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (e != cudaSuccess) return e;
+        c = coop && per_sm > 0 ? per_sm * n_sm : -1;
+        known[dev].store(c, std::memory_order_relaxed);
+    }
+    *cap = c > 0 ? c : 0;
+    return cudaSuccess;
+}
+
+// The one-launch sort when its tiles fit on the device at once (*ran set), else nothing.
+template <int ITEMS>
+cudaError_t rs_one(uint64_t *keys, uint32_t *vals, int64_t n, int bits, void *tmp, void *scan_state, cudaStream_t s,
+                   unsigned *err, bool *ran) {
+    *ran = false;
+    constexpr int TILE = RS_THREADS * ITEMS;
+    const int64_t nb = (n + TILE - 1) / TILE;
+    int64_t cap = 0;
+    cudaError_t e = rs_one_capacity<ITEMS>(&cap);
+    if (e != cudaSuccess || nb > cap) return e;
+    uint32_t *counts = reinterpret_cast<uint32_t *>(tmp);
+    uint32_t *totals = counts + nb * RADIX;
+    unsigned *bar = reinterpret_cast<unsigned *>(scan_state) + 2;  // words 2 and 3 of the scan state
+    int passes = (bits + 7) / 8;
+    void *args[] = {&keys, &vals, &n, &passes, &counts, &totals, &bar, &err};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_rs_one<ITEMS>), dim3((unsigned)nb),
+                                    dim3(RS_THREADS), args, rs_one_smem<ITEMS>(), s);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {  // not resident at once after all: the launches per pass
+        (void)cudaGetLastError();
+        return cudaSuccess;
+    }
+    if (e != cudaSuccess) return e;
+    SDF_LAUNCHED(1);
+    *ran = true;
+    return cudaSuccess;
+}
 }  // namespace
 
 // histograms of a sort of at most n keys: sized for the smallest tile (the most tiles), so that
@@ -349,7 +552,7 @@ cudaError_t rs_passes(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
 size_t radix_tmp_bytes(int64_t n) {
     const int64_t tile = (int64_t)RS_THREADS * 2;
     int64_t nb = (n + tile - 1) / tile;
-    return ((size_t)nb * RADIX + 64) * sizeof(uint32_t);
+    return ((size_t)nb * RADIX + RADIX + 64) * sizeof(uint32_t);  // + the one-launch sort's digit totals
 }
 
 // the scan state a sort of at most n keys needs (its digit histograms are scanned)
@@ -361,7 +564,18 @@ size_t radix_scan_state_bytes(int64_t n) {
 cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int64_t n,
                            int bits, void *tmp, void *scan_state, cudaStream_t s, unsigned *err) {
     if (n <= 1 || bits <= 0) return cudaSuccess;
-    switch (rs_items(n)) {
+    const int items = rs_items(n);
+    // SDF_RADIX_ONE_LAUNCH=0 keeps every sort on the launches per pass (the two give the same order)
+    const char *env = getenv("SDF_RADIX_ONE_LAUNCH");
+    if (!(env && env[0] == '0')) {
+        bool ran = false;
+        const cudaError_t e =
+            items == 8 ? rs_one<8>(keys, vals, n, bits, tmp, scan_state, s, err, &ran)
+                       : (items == 4 ? rs_one<4>(keys, vals, n, bits, tmp, scan_state, s, err, &ran)
+                                     : rs_one<2>(keys, vals, n, bits, tmp, scan_state, s, err, &ran));
+        if (e != cudaSuccess || ran) return e;
+    }
+    switch (items) {
     case 8: return rs_passes<8>(keys, vals, keys_alt, vals_alt, n, bits, tmp, scan_state, s, err);
     case 4: return rs_passes<4>(keys, vals, keys_alt, vals_alt, n, bits, tmp, scan_state, s, err);
     default: return rs_passes<2>(keys, vals, keys_alt, vals_alt, n, bits, tmp, scan_state, s, err);
@@ -371,7 +585,6 @@ cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, u
 }  // namespace sdf
 
 // ============================================================================= launch counter
-#include <atomic>
 namespace sdf {
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }

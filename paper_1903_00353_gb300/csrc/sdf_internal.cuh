@@ -167,7 +167,10 @@ cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, boo
                                cudaStream_t s, unsigned *err);
 // Stable LSD radix sort of (keys, vals) on bits [0, bits).  Buffers *_alt are ping-pong
 // scratch of the same size; the result ends in keys/vals.  tmp holds radix_tmp_bytes(n) bytes of
-// histograms; scan_state is a scan state (as above) of radix_scan_state_bytes(n) bytes.
+// histograms; scan_state is a scan state (as above) of radix_scan_state_bytes(n) bytes.  A sort
+// whose tiles fit on the device at once is one cooperative launch (its grid barrier uses words 2
+// and 3 of the scan state, which every completed sort leaves ready); a barrier wait that runs out
+// sets ST_TIMEOUT in *err.  Otherwise three launches per 8-bit pass.
 size_t radix_tmp_bytes(int64_t n);
 size_t radix_scan_state_bytes(int64_t n);
 cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int64_t n,
