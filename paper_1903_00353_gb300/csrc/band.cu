@@ -293,11 +293,14 @@ __device__ __forceinline__ int warp_owner(int incl, int r) {
 // Binning of the regions into tiles, one thread per feature, its (feature, tile) pairs flattened
 // over the warp: in each round every lane takes one pair, lanes whose pairs fall in the same bin
 // (neighbouring features share tiles: faces, edges and vertices are numbered in spatial order)
-// are grouped by __match_any_sync, and one atomicAdd per group takes their slots.  The count pass
-// (FILL false) and the fill pass walk the same pairs in the same order.
+// are grouped by __match_any_sync, and one atomic per group takes their slots.  The count pass
+// (FILL false) and the fill pass walk the same pairs; the fill pass takes each bin's slots by
+// counting its count back down to 0 (so the counts need no clearing in between, and end cleared).
 template <bool FILL, int TY, int TZ>
 __global__ void k_bin(const Prob *P, const long long *feat_base, const long long *tile_base, int n, long long f_tot,
                       uint32_t *cnt, const uint32_t *start, int2 *pairs, int64_t pair_cap, DevCounters *ctr) {
+    dep_wait();
+    dep_next();
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     int p = 0, type = 0, fid = 0, ntile = 0;
@@ -343,7 +346,10 @@ __global__ void k_bin(const Prob *P, const long long *feat_base, const long long
         const unsigned peers = __match_any_sync(FULL, bin);
         const int leader = __ffs(peers) - 1;
         unsigned base = 0;
-        if (has && lane == leader) base = atomicAdd(cnt + bin, (unsigned)__popc(peers));
+        if (has && lane == leader) {
+            const unsigned k = (unsigned)__popc(peers);
+            base = FILL ? atomicSub(cnt + bin, k) - k : atomicAdd(cnt + bin, k);
+        }
         base = __shfl_sync(FULL, base, leader);
         if (FILL && has) {
             const int64_t pos = (int64_t)start[bin] + base + __popc(peers & lt_mask);
@@ -838,6 +844,8 @@ constexpr int N_COST_CLASSES = 16;
 __device__ __forceinline__ int tile_cost_class(uint32_t np) { return N_COST_CLASSES - 1 - min(15, 31 - __clz(np)); }
 
 __global__ void k_band_flags(const uint32_t *bin_start, int64_t n_tiles, uint32_t *flag, DevCounters *ctr, int lpt) {
+    dep_wait();
+    dep_next();
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
     const uint32_t np = bin_start[3 * t + 3] - bin_start[3 * t];
@@ -869,6 +877,8 @@ static_assert(offsetof(DevCounters, n_split_items) == offsetof(DevCounters, tile
 __global__ void k_tile_lists(const uint32_t *bin_start, int64_t n_tiles, const uint32_t *band_pos,
                              int32_t *band_list, int32_t *empty_list, DevCounters *ctr, int lpt, int2 *split_items,
                              int split_cap) {
+    dep_wait();
+    dep_next();
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
     const uint32_t np = bin_start[3 * t + 3] - bin_start[3 * t];
@@ -994,6 +1004,8 @@ __global__ void __launch_bounds__(NT, 4) k_tile(const Prob *P, const long long *
                                                 int64_t n_tiles, const int32_t *band_list,
                                                 const int32_t *empty_list, const uint32_t *n_band_ptr,
                                                 unsigned long long *ticket, int dense) {
+    dep_wait();
+    dep_next();
     constexpr int TP = TILE_X * TY * TZ;
     extern __shared__ __align__(16) unsigned char tile_smem[];
     TileSmem<TY, TZ> &S = *reinterpret_cast<TileSmem<TY, TZ> *>(tile_smem);
@@ -1279,6 +1291,8 @@ __device__ __forceinline__ Cand64 vert_cand64(const Feat &F, double3 p, int v) {
 // of the feature holding the closest point q (face normal, n1 + n2, or N_alpha, Eq. 8).
 template <int TY, int TZ>
 __global__ void __launch_bounds__(256) k_patch(const Prob *P, const long long *tile_base, Outputs o) {
+    dep_wait();
+    dep_next();
     const int lane = threadIdx.x & 31;
     const int64_t wid0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1451,11 +1465,39 @@ __global__ void __launch_bounds__(256) k_patch(const Prob *P, const long long *t
 // The FP32 error windows of every problem of a launch, from its grid and the current precision
 // terms of its mesh (set_windows); the first kernel of every narrow-band launch.
 __global__ void k_windows(Prob *P, int n) {
+    dep_wait();
+    dep_next();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const unsigned *pr = P[p].F.prec;
     set_windows(P[p].g, __uint_as_float(pr[PREC_MESH_M]), __uint_as_float(pr[PREC_TAU_A]),
                 __uint_as_float(pr[PREC_TAU_B]), __uint_as_float(pr[PREC_TAU_V]));
+}
+
+// Start of a tile launch: the FP32 error windows of every problem (set_windows), and the launch's
+// bin counts, overflow status, statistics, cost-class counters and work tickets cleared, in one
+// launch instead of k_windows and five memsets (each an operation of its own on the stream).
+__global__ void k_front(Prob *P, int n, uint32_t *cnt, int64_t n_bins, DevCounters *ctr,
+                        unsigned long long *ticket, int n_tickets) {
+    dep_wait();
+    dep_next();
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (t < n) {
+        const unsigned *pr = P[t].F.prec;
+        set_windows(P[t].g, __uint_as_float(pr[PREC_MESH_M]), __uint_as_float(pr[PREC_TAU_A]),
+                    __uint_as_float(pr[PREC_TAU_B]), __uint_as_float(pr[PREC_TAU_V]));
+    }
+    if (t == 0) {
+        ctr->nb_status = 0;
+        unsigned long long *stats = &ctr->n_candidates;  // n_candidates .. n_rows_hit
+        for (int k = 0; k < 6; k++) stats[k] = 0;
+        for (int k = 0; k < 2 * N_COST_CLASSES + 2; k++) ctr->tile_hist[k] = 0;  // .. n_split_items
+        for (int k = 0; k < n_tickets; k++) ticket[k] = 0;
+    }
+    const int64_t n4 = n_bins / 4;  // cnt is 16-byte aligned
+    for (int64_t i = t; i < n4; i += stride) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
+    for (int64_t i = 4 * n4 + t; i < n_bins; i += stride) cnt[i] = 0;
 }
 
 inline unsigned nblk(int64_t n, int bt) { return (unsigned)((n + bt - 1) / bt); }
@@ -2122,35 +2164,25 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
                         cudaEvent_t *ev) {
     const int64_t n_bins = 3 * n_tiles;
     if (ev) SDF_TRY(record_event(ev[0], s));
-    k_windows<<<nblk(n, 64), 64, 0, s>>>(const_cast<Prob *>(sc.probs), n);
-    SDF_LAUNCHED(1);
-    SDF_TRY(cudaMemsetAsync(sc.cnt, 0, sizeof(uint32_t) * n_bins, s));
-    SDF_TRY(cudaMemsetAsync(&sc.ctr->nb_status, 0, sizeof(unsigned), s));
-    SDF_TRY(cudaMemsetAsync(&sc.ctr->n_candidates, 0, 6 * sizeof(unsigned long long), s));
-    k_bin<false, TY, TZ><<<nblk(f_tot, 256), 256, 0, s>>>(sc.probs, sc.fbase, sc.tbase, n, f_tot, sc.cnt, nullptr,
-                                                          nullptr, 0, sc.ctr);
-    SDF_LAUNCHED(1);
-    SDF_TRY(cudaGetLastError());
+    {  // windows, counters, tickets (band, fill and, where split tiles are possible, split items)
+        const unsigned blocks = std::max(nblk(n, 256), std::min(nblk(n_bins / 4, 256), (unsigned)(2 * num_sms())));
+        SDF_TRY(launch_dep(k_front, dim3(blocks), dim3(256), 0, s, const_cast<Prob *>(sc.probs), n, sc.cnt, n_bins,
+                           sc.ctr, sc.ticket, sc.split_items ? 3 : 2));
+    }
+    SDF_TRY(launch_dep(k_bin<false, TY, TZ>, dim3(nblk(f_tot, 256)), dim3(256), 0, s, sc.probs, sc.fbase, sc.tbase, n,
+                       f_tot, sc.cnt, (const uint32_t *)nullptr, (int2 *)nullptr, (int64_t)0, sc.ctr));
     SDF_TRY(scan_exclusive_u32(sc.cnt, sc.start, n_bins, true, sc.scan_tmp, s, &sc.ctr->nb_status));
-    SDF_TRY(cudaMemsetAsync(sc.cnt, 0, sizeof(uint32_t) * n_bins, s));
-    k_bin<true, TY, TZ><<<nblk(f_tot, 256), 256, 0, s>>>(sc.probs, sc.fbase, sc.tbase, n, f_tot, sc.cnt, sc.start,
-                                                         sc.pairs, sc.pair_cap, sc.ctr);
-    SDF_LAUNCHED(1);
-    SDF_TRY(cudaGetLastError());
+    SDF_TRY(launch_dep(k_bin<true, TY, TZ>, dim3(nblk(f_tot, 256)), dim3(256), 0, s, sc.probs, sc.fbase, sc.tbase, n,
+                       f_tot, sc.cnt, (const uint32_t *)sc.start, sc.pairs, sc.pair_cap, sc.ctr));
     // band / empty tile lists for the persistent tile kernel (one scan of the band flags)
     uint32_t *flags = sc.cnt;  // the fill cursors are no longer needed
-    // cost-class counts and cursors, and the split-tile counts (contiguous in DevCounters)
-    SDF_TRY(cudaMemsetAsync(sc.ctr->tile_hist, 0, (2 * N_COST_CLASSES + 2) * sizeof(unsigned), s));
     const int lpt = n > 1;  // largest-first order of the band tiles for batches
-    k_band_flags<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, flags, sc.ctr, lpt);
-    SDF_LAUNCHED(1);
-    SDF_TRY(cudaGetLastError());
+    SDF_TRY(launch_dep(k_band_flags, dim3(nblk(n_tiles, 256)), dim3(256), 0, s, (const uint32_t *)sc.start, n_tiles,
+                       flags, sc.ctr, lpt));
     SDF_TRY(scan_exclusive_u32(flags, sc.band_pos, n_tiles, true, sc.scan_tmp, s, &sc.ctr->nb_status));
-    k_tile_lists<<<nblk(n_tiles, 256), 256, 0, s>>>(sc.start, n_tiles, sc.band_pos, sc.band_list, sc.empty_list,
-                                                    sc.ctr, lpt, sc.split_items, sc.split_items ? SPLIT_SLOTS : 0);
-    SDF_LAUNCHED(1);
-    // band, fill and split-item tickets (the allocation-free entry point has the first two only)
-    SDF_TRY(cudaMemsetAsync(sc.ticket, 0, (sc.split_items ? 3 : 2) * sizeof(unsigned long long), s));
+    SDF_TRY(launch_dep(k_tile_lists, dim3(nblk(n_tiles, 256)), dim3(256), 0, s, (const uint32_t *)sc.start, n_tiles,
+                       (const uint32_t *)sc.band_pos, sc.band_list, sc.empty_list, sc.ctr, lpt, sc.split_items,
+                       sc.split_items ? SPLIT_SLOTS : 0));
     Outputs o;
     o.pairs = sc.pairs;
     o.bin_start = sc.start;
@@ -2168,35 +2200,31 @@ static int launch_shape(int n, long long f_tot, int64_t n_tiles, const Scratch &
             // one CTA per SM: a few tiles' items at most, and a cheap launch when there are none
             tile_blocks_per_sm<TY, TZ, true, true>();  // (sets the kernel's shared-memory limit once)
             const int64_t sctas = std::min<int64_t>(n_tiles, (int64_t)num_sms());
-            k_tile<TY, TZ, true, true><<<(unsigned)sctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
-                sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket,
-                sc.any_dense ? 1 : 0);
-            SDF_LAUNCHED(1);
+            SDF_TRY(launch_dep(k_tile<TY, TZ, true, true>, dim3((unsigned)sctas), dim3(NT),
+                               sizeof(TileSmem<TY, TZ>), s, sc.probs, sc.tbase, n, o, n_tiles,
+                               (const int32_t *)sc.band_list, (const int32_t *)sc.empty_list,
+                               sc.band_pos + n_tiles, sc.ticket, sc.any_dense ? 1 : 0));
         }
-        k_tile<TY, TZ, true, false><<<(unsigned)ctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
-            sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket,
-            sc.any_dense ? 1 : 0);
+        SDF_TRY(launch_dep(k_tile<TY, TZ, true, false>, dim3((unsigned)ctas), dim3(NT), sizeof(TileSmem<TY, TZ>), s,
+                           sc.probs, sc.tbase, n, o, n_tiles, (const int32_t *)sc.band_list,
+                           (const int32_t *)sc.empty_list, sc.band_pos + n_tiles, sc.ticket, sc.any_dense ? 1 : 0));
     } else {
         const int64_t ctas = std::min<int64_t>(n_tiles, (int64_t)tile_blocks_per_sm<TY, TZ, false>() * num_sms());
         if (sc.split_items) {
             // one CTA per SM: a few tiles' items at most, and a cheap launch when there are none
             tile_blocks_per_sm<TY, TZ, false, true>();  // (sets the kernel's shared-memory limit once)
             const int64_t sctas = std::min<int64_t>(n_tiles, (int64_t)num_sms());
-            k_tile<TY, TZ, false, true><<<(unsigned)sctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
-                sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket,
-                sc.any_dense ? 1 : 0);
-            SDF_LAUNCHED(1);
+            SDF_TRY(launch_dep(k_tile<TY, TZ, false, true>, dim3((unsigned)sctas), dim3(NT),
+                               sizeof(TileSmem<TY, TZ>), s, sc.probs, sc.tbase, n, o, n_tiles,
+                               (const int32_t *)sc.band_list, (const int32_t *)sc.empty_list,
+                               sc.band_pos + n_tiles, sc.ticket, sc.any_dense ? 1 : 0));
         }
-        k_tile<TY, TZ, false, false><<<(unsigned)ctas, NT, sizeof(TileSmem<TY, TZ>), s>>>(
-            sc.probs, sc.tbase, n, o, n_tiles, sc.band_list, sc.empty_list, sc.band_pos + n_tiles, sc.ticket,
-            sc.any_dense ? 1 : 0);
+        SDF_TRY(launch_dep(k_tile<TY, TZ, false, false>, dim3((unsigned)ctas), dim3(NT), sizeof(TileSmem<TY, TZ>), s,
+                           sc.probs, sc.tbase, n, o, n_tiles, (const int32_t *)sc.band_list,
+                           (const int32_t *)sc.empty_list, sc.band_pos + n_tiles, sc.ticket, sc.any_dense ? 1 : 0));
     }
-    SDF_LAUNCHED(1);
-    SDF_TRY(cudaGetLastError());
     if (ev) SDF_TRY(record_event(ev[2], s));
-    k_patch<TY, TZ><<<patch_blocks<TY, TZ>(), 256, 0, s>>>(sc.probs, sc.tbase, o);
-    SDF_LAUNCHED(1);
-    SDF_TRY(cudaGetLastError());
+    SDF_TRY(launch_dep(k_patch<TY, TZ>, dim3(patch_blocks<TY, TZ>()), dim3(256), 0, s, sc.probs, sc.tbase, o));
     if (sc.fprobs)
         SDF_TRY(fill_sign(sc.fprobs, sc.rbase, sc.zbase, sc.ybase, n, sc.r_tot, sc.z_tot, sc.y_tot, sc.rowsign,
                           num_sms(), s));

@@ -41,6 +41,8 @@ __device__ __forceinline__ float canon_zero(float x) { return x == 0.f ? 0.f : x
 
 // ----------------------------------------------------------------------------- soup bounds + finiteness
 __global__ void k_soup_bounds(const float *soup, int64_t n3, float *bb, DevCounters *ctr) {
+    dep_wait();
+    dep_next();
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     bool bad = false;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n3; s += (int64_t)gridDim.x * blockDim.x) {
@@ -97,6 +99,8 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {  // SplitMix64 finaliser
 }
 
 __global__ void k_weld_keys(const float *soup, int64_t n3, const float *bb, uint64_t *keys, uint32_t *vals) {
+    dep_wait();
+    dep_next();
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n3) return;
     float x = canon_zero(soup[3 * s]), y = canon_zero(soup[3 * s + 1]), z = canon_zero(soup[3 * s + 2]);
@@ -136,6 +140,8 @@ __device__ __forceinline__ bool less_xyz(const float *soup, uint32_t a, uint32_t
 constexpr int WELD_SHORT = 32, WELD_BLOCK_MAX = 2048;
 __global__ void k_weld_fix(const uint64_t *keys, uint32_t *vals, const float *soup, int64_t n, int2 *long_runs,
                            int64_t long_cap, unsigned *n_long) {
+    dep_wait();
+    dep_next();
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n || (i > 0 && keys[i] == keys[i - 1])) return;
     int64_t e = i + 1;
@@ -166,6 +172,8 @@ __global__ void k_weld_fix(const uint64_t *keys, uint32_t *vals, const float *so
 // coordinate bits makes equal vertices contiguous; -0 is read as +0.
 __global__ void __launch_bounds__(256) k_weld_sort_runs(const int2 *long_runs, const unsigned *n_long, int64_t long_cap,
                                                         uint32_t *vals, const float *soup) {
+    dep_wait();
+    dep_next();
     __shared__ uint4 rec[WELD_BLOCK_MAX];
     const int64_t nl = min((int64_t)*n_long, long_cap);
     for (int64_t r = blockIdx.x; r < nl; r += gridDim.x) {
@@ -206,6 +214,8 @@ __global__ void __launch_bounds__(256) k_weld_sort_runs(const int2 *long_runs, c
 
 __global__ void k_weld_heads(const uint64_t *keys, const uint32_t *vals, const float *soup, int64_t n,
                              uint32_t *head) {
+    dep_wait();
+    dep_next();
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     head[i] = (i == 0 || keys[i] != keys[i - 1] || !same_xyz(soup, vals[i], vals[i - 1])) ? 1u : 0u;
@@ -215,6 +225,8 @@ __global__ void k_weld_heads(const uint64_t *keys, const uint32_t *vals, const f
 __global__ void k_weld_scatter(const uint32_t *vals, const uint32_t *hscan, const uint64_t *keys, const float *soup,
                                int64_t n, int32_t *soup_vid, int32_t *vert_start, int32_t *vert_corner,
                                float *vpos) {
+    dep_wait();
+    dep_next();
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     bool is_head = hscan[i + 1] != hscan[i];
@@ -233,6 +245,8 @@ __global__ void k_weld_scatter(const uint32_t *vals, const uint32_t *hscan, cons
 // key of a face: its smallest welded vertex id (vertex ids follow the Morton order of the weld),
 // so faces that are close in space get close ids and their records share cache lines
 __global__ void k_face_keys(const int32_t *soup_vid, int64_t T, uint64_t *keys, uint32_t *vals) {
+    dep_wait();
+    dep_next();
     int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (f >= T) return;
     int32_t a = soup_vid[3 * f], b = soup_vid[3 * f + 1], c = soup_vid[3 * f + 2];
@@ -243,6 +257,8 @@ __global__ void k_face_keys(const int32_t *soup_vid, int64_t T, uint64_t *keys, 
 // face_soup[f] = soup triangle of library face f; face_vid in library order; inv: soup -> library
 __global__ void k_face_perm(const uint32_t *order, const int32_t *soup_vid, int64_t T, int32_t *face_soup,
                             int32_t *face_vid, uint32_t *inv) {
+    dep_wait();
+    dep_next();
     int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (f >= T) return;
     uint32_t sf = order[f];
@@ -252,6 +268,8 @@ __global__ void k_face_perm(const uint32_t *order, const int32_t *soup_vid, int6
 }
 
 __global__ void k_corner_remap(int32_t *vert_corner, const uint32_t *inv, int64_t n) {
+    dep_wait();
+    dep_next();
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t c = vert_corner[i];
@@ -266,6 +284,8 @@ __global__ void k_corner_remap(int32_t *vert_corner, const uint32_t *inv, int64_
 // order of their smaller end point's corners, which keeps them spatially ordered too.
 __global__ void k_pair_fans(const int32_t *vert_start, const int32_t *vert_corner, const int32_t *face_vid, int64_t n,
                             int32_t *twin, uint32_t *canon, DevCounters *ctr) {
+    dep_wait();
+    dep_next();
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int32_t h = vert_corner[i];
@@ -304,6 +324,8 @@ __global__ void k_pair_fans(const int32_t *vert_start, const int32_t *vert_corne
 __global__ void k_edge_emit(const int32_t *vert_corner, const int32_t *face_vid, const int32_t *twin,
                             const uint32_t *canon, const uint32_t *eid, int64_t n, int4 *edge_vf,
                             int32_t *face_edge) {
+    dep_wait();
+    dep_next();
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n || !canon[i]) return;
     const int32_t h = vert_corner[i];
@@ -393,6 +415,8 @@ __device__ __forceinline__ void block_sums_into(double *words, float (&v)[K]) {
 // narrow band adds tau_a + tau_b W to its FP32 error bound (the windows in band.cu).
 __global__ void __launch_bounds__(BT) k_face_records(const int32_t *face_vid, const float *vpos, int64_t T,
                                                      float4 *face_rec, float4 *face_box, DevCounters *ctr) {
+    dep_wait();
+    dep_next();
     float m_abs = 0.f, tau_a = 0.f;
     float mom[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     bool degenerate = false;
@@ -446,6 +470,8 @@ __device__ double3 face_normal_fp64(const int32_t *face_vid, const float *vpos, 
 __global__ void __launch_bounds__(BT) k_edge_records(const int4 *edge_vf, const int32_t *face_vid, const float *vpos,
                                                      const float4 *face_rec, int64_t E, float4 *edge_rec,
                                                      int8_t *edge_class, DevCounters *ctr) {
+    dep_wait();
+    dep_next();
     unsigned ncv = 0, ncc = 0;  // class counts of this thread's edges
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
         const int4 q = edge_vf[e];
@@ -522,6 +548,8 @@ __global__ void __launch_bounds__(BT) k_vertex_records(const int32_t *vert_start
                                                        const int32_t *face_vid, const float *vpos,
                                                        const float4 *face_rec, int64_t V, float4 *vert_rec,
                                                        float4 *vert_plane, int8_t *vert_class, DevCounters *ctr) {
+    dep_wait();
+    dep_next();
     // the planes and face normals of each group's fan, staged for the classification and the cone
     // search (fans of more than VMAXS corners read them from global memory and skip the search)
     __shared__ float4 s_plane[BT / VL][VMAXS];
@@ -707,6 +735,8 @@ inline unsigned nblk(int64_t n) { return (unsigned)((n + BT - 1) / BT); }
 // the build's small state: counters and scan state cleared, the bounding box at (+inf, -inf)
 __global__ void k_build_init(unsigned *ctr, int64_t ctr_words, float *bb, unsigned *n_long, unsigned *scan,
                              int64_t scan_words) {
+    dep_wait();
+    dep_next();
     for (int64_t i = threadIdx.x; i < ctr_words; i += blockDim.x) ctr[i] = 0u;
     for (int64_t i = threadIdx.x; i < scan_words; i += blockDim.x) scan[i] = 0u;
     if (threadIdx.x < 6) bb[threadIdx.x] = threadIdx.x < 3 ? INFINITY : -INFINITY;
@@ -731,14 +761,13 @@ template <class K> unsigned rec_grid(K kernel, int64_t n) {
 
 int build_records(sdf_features_s *f, cudaStream_t s) {
     if (f->T > 0) {
-        k_face_records<<<rec_grid(k_face_records, f->T), BT, 0, s>>>(f->face_vid, f->vpos, f->T, f->face_rec, f->face_box, f->ctr);
-        SDF_LAUNCHED(1);
-        k_edge_records<<<rec_grid(k_edge_records, f->E), BT, 0, s>>>(f->edge_vf, f->face_vid, f->vpos, f->face_rec, f->E, f->edge_rec,
-                                                f->edge_class, f->ctr);
-        SDF_LAUNCHED(1);
-        k_vertex_records<<<rec_grid(k_vertex_records, f->V * VL), BT, 0, s>>>(f->vert_start, f->vert_corner, f->face_vid, f->vpos, f->face_rec,
-                                                  f->V, f->vert_rec, f->vert_plane, f->vert_class, f->ctr);
-        SDF_LAUNCHED(1);
+        SDF_TRY(launch_dep(k_face_records, dim3(rec_grid(k_face_records, f->T)), dim3(BT), 0, s, f->face_vid, f->vpos,
+                           f->T, f->face_rec, f->face_box, f->ctr));
+        SDF_TRY(launch_dep(k_edge_records, dim3(rec_grid(k_edge_records, f->E)), dim3(BT), 0, s, f->edge_vf, f->face_vid,
+                           f->vpos, f->face_rec, f->E, f->edge_rec, f->edge_class, f->ctr));
+        SDF_TRY(launch_dep(k_vertex_records, dim3(rec_grid(k_vertex_records, f->V * VL)), dim3(BT), 0, s, f->vert_start,
+                           f->vert_corner, f->face_vid, f->vpos, f->face_rec, f->V, f->vert_rec, f->vert_plane,
+                           f->vert_class, f->ctr));
     }
     SDF_TRY(cudaGetLastError());
     return SDF_OK;
@@ -833,23 +862,17 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     B_TRY(dalloc_s(&f->ctr, 1, s));
     unsigned *const err = &f->ctr->status;  // a scan whose look-back ran out marks ST_TIMEOUT here
     // counters, the bounding box, the long-run count and the scan state start cleared (one launch)
-    k_build_init<<<1, BT, 0, s>>>(reinterpret_cast<unsigned *>(f->ctr), sizeof(DevCounters) / sizeof(unsigned), bb,
-                                  n_long, reinterpret_cast<unsigned *>(scan_state), scan_bytes / sizeof(unsigned));
-    SDF_LAUNCHED(1);
+    B_TRY(launch_dep(k_build_init, dim3(1), dim3(BT), 0, s, reinterpret_cast<unsigned *>(f->ctr),
+                     (int64_t)(sizeof(DevCounters) / sizeof(unsigned)), bb, n_long,
+                     reinterpret_cast<unsigned *>(scan_state), (int64_t)(scan_bytes / sizeof(unsigned))));
     // about four corners per thread, at most four blocks per SM of this part
-    k_soup_bounds<<<(unsigned)std::min<int64_t>((n + 4 * BT - 1) / (4 * BT), 4 * 152), BT, 0, s>>>(soup, n, bb, f->ctr);
-    SDF_LAUNCHED(1);
-    k_weld_keys<<<nblk(n), BT, 0, s>>>(soup, n, bb, keys, vals);
-    SDF_LAUNCHED(1);
-    B_TRY(cudaGetLastError());
+    B_TRY(launch_dep(k_soup_bounds, dim3((unsigned)std::min<int64_t>((n + 4 * BT - 1) / (4 * BT), 4 * 152)), dim3(BT),
+                     0, s, soup, n, bb, f->ctr));
+    B_TRY(launch_dep(k_weld_keys, dim3(nblk(n)), dim3(BT), 0, s, soup, n, bb, keys, vals));
     B_TRY(radix_sort_u64(keys, vals, kalt, valt, n, 40, rtmp, scan_state, s, err));
-    k_weld_fix<<<nblk(n), BT, 0, s>>>(keys, vals, soup, n, long_runs, long_cap, n_long);
-    SDF_LAUNCHED(1);
-    k_weld_sort_runs<<<2 * 152, 256, 0, s>>>(long_runs, n_long, long_cap, vals, soup);
-    SDF_LAUNCHED(1);
-    k_weld_heads<<<nblk(n), BT, 0, s>>>(keys, vals, soup, n, valt);
-    SDF_LAUNCHED(1);
-    B_TRY(cudaGetLastError());
+    B_TRY(launch_dep(k_weld_fix, dim3(nblk(n)), dim3(BT), 0, s, keys, vals, soup, n, long_runs, long_cap, n_long));
+    B_TRY(launch_dep(k_weld_sort_runs, dim3(2 * 152), dim3(256), 0, s, long_runs, n_long, long_cap, vals, soup));
+    B_TRY(launch_dep(k_weld_heads, dim3(nblk(n)), dim3(BT), 0, s, keys, vals, soup, n, valt));
     // head[i] = number of run heads before i, head[n] = V (so head[i+1] is the inclusive count at i)
     B_TRY(scan_exclusive_u32(valt, head, n, true, scan_state, s, err));
     uint32_t Vh = 0;
@@ -892,34 +915,26 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
         B_TRY(pool_alloc(&f->block, L.bytes, s));
         L.place(f->block);
     }
-    k_weld_scatter<<<nblk(n), BT, 0, s>>>(vals, head, keys, soup, n, f->soup_vid, f->vert_start, f->vert_corner,
-                                          f->vpos);
-    SDF_LAUNCHED(1);
-    B_TRY(cudaGetLastError());
+    B_TRY(launch_dep(k_weld_scatter, dim3(nblk(n)), dim3(BT), 0, s, vals, head, keys, soup, n, f->soup_vid,
+                     f->vert_start, f->vert_corner, f->vpos));
     // spatial face order: sort faces by their smallest (Morton-ordered) vertex id
     int nb = 1;
     while ((int64_t(1) << nb) < V) nb++;
-    k_face_keys<<<nblk(T), BT, 0, s>>>(f->soup_vid, T, keys, vals);
-    SDF_LAUNCHED(1);
-    B_TRY(cudaGetLastError());
+    B_TRY(launch_dep(k_face_keys, dim3(nblk(T)), dim3(BT), 0, s, f->soup_vid, T, keys, vals));
     B_TRY(radix_sort_u64(keys, vals, kalt, valt, T, nb, rtmp, scan_state, s, err));
-    k_face_perm<<<nblk(T), BT, 0, s>>>(vals, f->soup_vid, T, f->face_soup, f->face_vid, valt);
-    SDF_LAUNCHED(1);
-    k_corner_remap<<<nblk(n), BT, 0, s>>>(f->vert_corner, valt, n);
-    SDF_LAUNCHED(1);
-    B_TRY(cudaGetLastError());
+    B_TRY(launch_dep(k_face_perm, dim3(nblk(T)), dim3(BT), 0, s, vals, f->soup_vid, T, f->face_soup, f->face_vid,
+                     valt));
+    B_TRY(launch_dep(k_corner_remap, dim3(nblk(n)), dim3(BT), 0, s, f->vert_corner, valt, n));
     // edge pairing through the vertex fans
     int32_t *twin = reinterpret_cast<int32_t *>(kalt);  // kalt is free again
     uint32_t *canon = valt;
-    k_pair_fans<<<nblk(n), BT, 0, s>>>(f->vert_start, f->vert_corner, f->face_vid, n, twin, canon, f->ctr);
-    SDF_LAUNCHED(1);
-    B_TRY(cudaGetLastError());
+    B_TRY(launch_dep(k_pair_fans, dim3(nblk(n)), dim3(BT), 0, s, f->vert_start, f->vert_corner, f->face_vid, n, twin,
+                     canon, f->ctr));
     B_TRY(scan_exclusive_u32(canon, head, n, true, scan_state, s, err));
     // entries that no canonical edge writes (a broken mesh) stay -1 and are skipped by the records
     B_TRY(cudaMemsetAsync(f->edge_vf, 0xff, sizeof(int4) * (size_t)E, s));
-    k_edge_emit<<<nblk(n), BT, 0, s>>>(f->vert_corner, f->face_vid, twin, canon, head, n, f->edge_vf, f->face_edge);
-    SDF_LAUNCHED(1);
-    B_TRY(cudaGetLastError());
+    B_TRY(launch_dep(k_edge_emit, dim3(nblk(n)), dim3(BT), 0, s, f->vert_corner, f->face_vid, twin, canon, head, n,
+                     f->edge_vf, f->face_edge));
     // The records are built without first reading the connectivity status (one host round trip
     // fewer): on a broken mesh they only see valid indices (the weld's are valid by construction,
     // unpaired edges are skipped) and the status read below rejects the handle.

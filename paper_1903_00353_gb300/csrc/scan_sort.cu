@@ -56,6 +56,8 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *to
 // offset by offs[blockIdx.x] (nullable)
 __global__ void __launch_bounds__(SC_THREADS) k_scan_apply(const uint32_t *in, uint32_t *out, int64_t n,
                                                            const uint32_t *offs, uint32_t *total_out) {
+    dep_wait();
+    dep_next();
     int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
     uint32_t v[SC_ITEMS];
     uint32_t s = 0;
@@ -91,6 +93,8 @@ constexpr unsigned SCAN_POLL_LIMIT = 1u << 20;
 __global__ void __launch_bounds__(SC_THREADS) k_scan_chained(const uint32_t *in, uint32_t *out, int64_t n,
                                                              unsigned *hdr, unsigned long long *status,
                                                              uint32_t *total_out, unsigned *err) {
+    dep_wait();
+    dep_next();
     __shared__ unsigned s_tile, s_epoch;
     __shared__ uint32_t s_prefix, s_tot;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -177,16 +181,12 @@ cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, boo
         return cudaSuccess;
     }
     const int64_t nb = (n + SC_TILE - 1) / SC_TILE;
-    if (nb == 1) {
-        k_scan_apply<<<1, SC_THREADS, 0, s>>>(in, out, n, nullptr, write_total ? out + n : nullptr);
-    } else {
-        unsigned *hdr = reinterpret_cast<unsigned *>(state);
-        k_scan_chained<<<(unsigned)nb, SC_THREADS, 0, s>>>(in, out, n, hdr,
-                                                          reinterpret_cast<unsigned long long *>(hdr + 4),
-                                                          write_total ? out + n : nullptr, err);
-    }
-    SDF_LAUNCHED(1);
-    return cudaGetLastError();
+    uint32_t *total = write_total ? out + n : nullptr;
+    if (nb == 1)
+        return launch_dep(k_scan_apply, dim3(1), dim3(SC_THREADS), 0, s, in, out, n, (const uint32_t *)nullptr, total);
+    unsigned *hdr = reinterpret_cast<unsigned *>(state);
+    return launch_dep(k_scan_chained, dim3((unsigned)nb), dim3(SC_THREADS), 0, s, in, out, n, hdr,
+                      reinterpret_cast<unsigned long long *>(hdr + 4), total, err);
 }
 
 // ============================================================================= radix sort
@@ -207,6 +207,8 @@ constexpr size_t rs_smem() {
 template <int ITEMS>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *keys, int64_t n, int shift,
                                                         uint32_t *hist, int64_t nb) {
+    dep_wait();
+    dep_next();
     constexpr int TILE = RS_THREADS * ITEMS;
     __shared__ uint32_t h[RADIX];
     h[threadIdx.x] = 0;
@@ -224,6 +226,8 @@ template <int ITEMS>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *kin, const uint32_t *vin,
                                                            uint64_t *kout, uint32_t *vout, int64_t n, int shift,
                                                            const uint32_t *offs, int64_t nb) {
+    dep_wait();
+    dep_next();
     constexpr int TILE = RS_THREADS * ITEMS;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *skey = reinterpret_cast<uint64_t *>(smem);
@@ -474,15 +478,13 @@ cudaError_t rs_passes(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     uint32_t *vi = vals, *vo = vals_alt;
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
-        k_rs_hist<ITEMS><<<(unsigned)nb, RS_THREADS, 0, s>>>(ki, n, shift, hist, nb);
-        SDF_LAUNCHED(1);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_dep(k_rs_hist<ITEMS>, dim3((unsigned)nb), dim3(RS_THREADS), 0, s,
+                                   (const uint64_t *)ki, n, shift, hist, nb);
         if (e != cudaSuccess) return e;
         e = scan_exclusive_u32(hist, hist, nb * RADIX, false, scan_state, s, err);
         if (e != cudaSuccess) return e;
-        k_rs_scatter<ITEMS><<<(unsigned)nb, RS_THREADS, rs_smem<ITEMS>(), s>>>(ki, vi, ko, vo, n, shift, hist, nb);
-        SDF_LAUNCHED(1);
-        e = cudaGetLastError();
+        e = launch_dep(k_rs_scatter<ITEMS>, dim3((unsigned)nb), dim3(RS_THREADS), rs_smem<ITEMS>(), s,
+                       (const uint64_t *)ki, (const uint32_t *)vi, ko, vo, n, shift, (const uint32_t *)hist, nb);
         if (e != cudaSuccess) return e;
         uint64_t *tk = ki; ki = ko; ko = tk;
         uint32_t *tv = vi; vi = vo; vo = tv;
@@ -588,6 +590,13 @@ cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, u
 namespace sdf {
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char *e = getenv("SDF_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
 }  // namespace sdf
 extern "C" int64_t sdf_kernel_launches(void) { return sdf::g_launches.load(); }
 
@@ -668,6 +677,8 @@ struct SmallReads {
     int n;
 };
 __global__ void k_read_small(SmallReads r, unsigned char *out) {
+    dep_wait();
+    dep_next();
     for (int i = 0; i < r.n; i++)
         for (unsigned b = threadIdx.x; b < r.bytes[i]; b += blockDim.x) out[r.off[i] + b] = r.src[i][b];
 }
@@ -701,9 +712,8 @@ cudaError_t read_small(const HostRead *reads, int n, cudaStream_t s) {
         count_host_alloc();
     }
     if (e != cudaSuccess) return e;
-    k_read_small<<<1, 128, 0, s>>>(r, buf);  // pinned host memory is device-addressable (unified addressing)
-    count_launches(1);
-    e = cudaGetLastError();
+    // pinned host memory is device-addressable (unified addressing)
+    e = launch_dep(k_read_small, dim3(1), dim3(128), 0, s, r, buf);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess)
         for (int i = 0; i < n; i++) memcpy(reads[i].dst, buf + r.off[i], reads[i].bytes);

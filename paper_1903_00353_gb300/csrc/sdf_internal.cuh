@@ -156,6 +156,35 @@ namespace sdf {
 void count_launches(int64_t n);
 #define SDF_LAUNCHED(n) ::sdf::count_launches(n)
 
+// ----------------------------------------------------------------------------- dependent launches
+// The build and the scans are chains of short kernels on one stream, each waiting for the last.
+// They are launched with programmatic stream serialisation: a kernel may be scheduled while its
+// predecessor still runs and waits at its top (griddepcontrol.wait) until the predecessor has
+// finished and its writes are visible, so each launch's latency hides behind the kernel before it.
+// Every kernel launched by launch_dep calls dep_wait() before it touches memory, then dep_next()
+// to let its successor be scheduled (after the wait: at most one launch waits at a time).  Both are
+// no-ops in a kernel launched without the attribute.  SDF_PDL=0 in the environment launches every
+// kernel without it.
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dep_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+bool pdl_enabled();
+
+template <typename... P, typename... A>
+cudaError_t launch_dep(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    count_launches(1);
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ----------------------------------------------------------------------------- scans and sorts (scan_sort.cu)
 // Exclusive scan of n uint32 values (in may equal out); out[n] receives the total when
 // write_total is set.  One launch (decoupled look-back).  state holds scan_state_bytes(n) bytes,
