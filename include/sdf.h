@@ -472,8 +472,9 @@ int sdf_band_list_l2(sdf_features f, const sdf_grid *grid, const sdf_band_entry 
 
 /* Release the handle and its device memory (NULL is a no-op).  Waits for the device.  The scratch
  * of its narrow-band calls (pair list, bins, tile lists) is kept for the next handle's first call
- * on the same device, at most two such sets per device: a loop that builds a handle per step then
- * allocates nothing per step. */
+ * on the same device, at most two such sets per device, and its array block and counters for the
+ * next sdf_build_features on the device (with the builds' own scratch, at most four blocks per
+ * device): a loop that builds a handle per step then takes no memory from the pool per step. */
 void sdf_features_destroy(sdf_features f);
 
 /* Static description of a status code. */

@@ -136,6 +136,7 @@ struct sdf_features_s {
     int64_t counts[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     double box_mom[7] = {0, 0, 0, 0, 0, 0, 0};  // the build's face-box moments (DevCounters::box_mom)
     void *block = nullptr;           // one allocation holding every array above
+    size_t block_bytes = 0;
     sdf::DevCounters *ctr = nullptr; // device counters
     // narrow-band scratch of single-problem calls (problem table, bins, pairs), grown on demand
     sdf::Plan *plan = nullptr;
