@@ -29,6 +29,7 @@ struct AdjArgs {
     const float *grad;
     const int32_t *winner;
     float *gv;
+    float4 *g4;    // FP32 sums per vertex (the handle's grad4), added into gv by k_grad_out
     double *gv64;  // SDF_FLAG_GRAD_F64: the vertex gradient accumulated in FP64 instead
     const float4 *face_rec, *edge_rec, *vert_rec;
     const int32_t *face_vid;
@@ -117,6 +118,29 @@ __device__ __forceinline__ void warp_add(T *gv, int v, T gx, T gy, T gz, bool ac
     }
 }
 
+// The FP32 sums go to a float4 per vertex, one vector atomic (red.global.add.v4.f32) per run
+// instead of three scalar ones: on the 50 k-triangle torus the list adjoint took 0.118 instead of
+// 0.157 ms, close to the 0.113 ms of a copy with no atomics at all.  k_grad_out then adds the
+// float4 sums into the caller's float[V][3] gradient and clears them.
+__device__ __forceinline__ void warp_add4(float4 *g4, int v, float gx, float gy, float gz, bool active) {
+    const int lane = threadIdx.x & 31;
+    const int key = active ? v : -1;
+    const int prev = __shfl_up_sync(FULL, key, 1), next = __shfl_down_sync(FULL, key, 1);
+    const unsigned heads = __ballot_sync(FULL, lane == 0 || prev != key);
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // first lane of this run
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float tx = __shfl_up_sync(FULL, gx, o), ty = __shfl_up_sync(FULL, gy, o),
+                    tz = __shfl_up_sync(FULL, gz, o);
+        if (lane - o >= start) {
+            gx += tx;
+            gy += ty;
+            gz += tz;
+        }
+    }
+    if (active && (lane == 31 || next != key)) atomicAdd(g4 + v, make_float4(gx, gy, gz, 0.f));
+}
+
 // the contributions of one point (from point_adjoint) into the FP32 or FP64 vertex gradient
 template <bool F64>
 __device__ __forceinline__ void add_point(const AdjArgs &a, const int *vtx, const float (*c)[3], int nv) {
@@ -124,7 +148,22 @@ __device__ __forceinline__ void add_point(const AdjArgs &a, const int *vtx, cons
         if (F64)
             warp_add<double>(a.gv64, vtx[q], (double)c[q][0], (double)c[q][1], (double)c[q][2], q < nv);
         else
-            warp_add<float>(a.gv, vtx[q], c[q][0], c[q][1], c[q][2], q < nv);
+            warp_add4(a.g4, vtx[q], c[q][0], c[q][1], c[q][2], q < nv);
+    }
+}
+
+// adds the FP32 sums of an adjoint call into the caller's float[V][3] gradient and clears them
+__global__ void k_grad_out(float4 *g4, float *gv, int64_t V) {
+    dep_wait();
+    dep_next();
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const float4 t = g4[v];
+    if (t.x != 0.f || t.y != 0.f || t.z != 0.f) {
+        gv[3 * v] += t.x;
+        gv[3 * v + 1] += t.y;
+        gv[3 * v + 2] += t.z;
+        g4[v] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -396,6 +435,7 @@ AdjArgs make_adj_args(const sdf_features_s *f, const sdf_grid &gr) {
     a.grad = nullptr;
     a.winner = nullptr;
     a.gv = nullptr;
+    a.g4 = f->grad4;
     a.gv64 = nullptr;
     a.face_rec = f->face_rec; a.edge_rec = f->edge_rec; a.vert_rec = f->vert_rec;
     a.face_vid = f->face_vid; a.edge_vf = f->edge_vf; a.vpos = f->vpos;
@@ -441,6 +481,9 @@ int list_adjoint(sdf_features_s *f, const sdf_grid *grid, const sdf_band_entry *
                                                         (long long)list_cap, dist, target, loss_out, band_out);
     SDF_LAUNCHED(1);
     SDF_TRY(cudaGetLastError());
+    if (!f64)
+        SDF_TRY(launch_dep(k_grad_out, dim3((unsigned)((f->V + 255) / 256)), dim3(256), 0, s, f->grad4,
+                           grad_vertices, (int64_t)f->V));
     if (timing) {
         SDF_TRY(cudaEventRecord(f->ev[5], s));
         f->adj_pending = true;  // read later (resolve_timing)
@@ -517,6 +560,9 @@ extern "C" int sdf_narrow_band_backward(const sdf_features *feats, const sdf_gri
             k_adjoint<false><<<(unsigned)blocks, 256, 0, s>>>(a, vec);
         SDF_LAUNCHED(1);
         SDF_TRY(cudaGetLastError());
+        if (!f64)
+            SDF_TRY(launch_dep(k_grad_out, dim3((unsigned)((f->V + 255) / 256)), dim3(256), 0, s, f->grad4,
+                               grad_vertices[p], (int64_t)f->V));
         if (timing) {
             SDF_TRY(cudaEventRecord(f->ev[5], s));
             f->adj_pending = true;  // read later (resolve_timing)

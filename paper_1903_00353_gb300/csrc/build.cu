@@ -225,7 +225,7 @@ __global__ void k_weld_heads(const uint64_t *keys, const uint32_t *vals, const f
 // head[] holds the exclusive scan of the run heads; vid = that + is_head - 1
 __global__ void k_weld_scatter(const uint32_t *vals, const uint32_t *hscan, const uint64_t *keys, const float *soup,
                                int64_t n, int32_t *soup_vid, int32_t *vert_start, int32_t *vert_corner,
-                               float *vpos) {
+                               float *vpos, float4 *grad4) {
     dep_wait();
     dep_next();
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -238,6 +238,7 @@ __global__ void k_weld_scatter(const uint32_t *vals, const uint32_t *hscan, cons
     if (is_head) {
         vert_start[vid] = (int32_t)i;
         for (int j = 0; j < 3; j++) vpos[3 * vid + j] = canon_zero(soup[3 * (int64_t)s + j]);
+        grad4[vid] = make_float4(0.f, 0.f, 0.f, 0.f);  // the adjoints' sums start cleared
     }
     if (i == n - 1) vert_start[vid + 1] = (int32_t)n;
 }
@@ -978,11 +979,12 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
         L.add(f->vert_rec, 3 * V);
         L.add(f->vert_plane, n);
         L.add(f->vert_class, V);
+        L.add(f->grad4, V);
         B_TRY(take_block(L.bytes, &f->block, &f->block_bytes, s));
         L.place(f->block);
     }
     B_TRY(launch_dep(k_weld_scatter, dim3(nblk(n)), dim3(BT), 0, s, vals, head, keys, soup, n, f->soup_vid,
-                     f->vert_start, f->vert_corner, f->vpos));
+                     f->vert_start, f->vert_corner, f->vpos, f->grad4));
     // spatial face order: sort faces by their smallest (Morton-ordered) vertex id
     int nb = 1;
     while ((int64_t(1) << nb) < V) nb++;

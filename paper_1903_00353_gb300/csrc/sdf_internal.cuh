@@ -135,6 +135,8 @@ struct sdf_features_s {
     int8_t *vert_class = nullptr;   // [V]
     int64_t counts[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     double box_mom[7] = {0, 0, 0, 0, 0, 0, 0};  // the build's face-box moments (DevCounters::box_mom)
+    float4 *grad4 = nullptr;        // [V] FP32 vertex-gradient sums of an adjoint call (x, y, z, 0),
+                                    // zero between calls
     void *block = nullptr;           // one allocation holding every array above
     size_t block_bytes = 0;
     sdf::DevCounters *ctr = nullptr; // device counters
