@@ -24,6 +24,11 @@
  *   - Every call returns an sdf_status; no exception crosses the ABI.  On an
  *     error the outputs are unspecified.
  *   - Calls on one handle must not overlap in time (they share its scratch).
+ *   - The library's short kernels (the build, the scans, the narrow band's
+ *     set-up and FP64 re-decision) are launched as programmatic dependent
+ *     launches: each may be scheduled while its predecessor on `stream` runs
+ *     and waits on the device for it, so stream order is kept.  The
+ *     environment variable SDF_PDL=0 launches them plainly.
  *
  * Grid layout (Section 10, a row-major 1D float array): point (i,j,k) sits at
  * origin + ((i+1/2) h, (j+1/2) h, (k0+k+1/2) h) and is stored at
