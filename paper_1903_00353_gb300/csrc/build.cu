@@ -855,16 +855,21 @@ void keep_block(void *p, size_t bytes, cudaStream_t s) {
 // frees on the legacy default stream, after the caller's work on the handle has completed
 static void free_handle(sdf_features_s *f) {
     if (!f) return;
+    // on the handle's own device (the caller's current device may be another one), restored after
+    int cur = -1;
+    const bool other = f->dev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != f->dev &&
+                       cudaSetDevice(f->dev) == cudaSuccess;
     cudaDeviceSynchronize();  // no work may still use the handle's memory
     cudaStream_t s0 = 0;
     keep_block(f->block, f->block_bytes, s0);  // every array of the handle (kept for the next build)
-    keep_block(f->ctr, sizeof(DevCounters), s0);
+    keep_block(f->ctr, f->ctr_bytes, s0);
     sdf::plan_park(f->plan, s0);
     f->plan = nullptr;
     f->fwd_winner.release(s0);
     for (cudaEvent_t e : f->ev)
         if (e) cudaEventDestroy(e);
     delete f;
+    if (other) cudaSetDevice(cur);
 }
 
 
@@ -899,6 +904,10 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int64_t T = n_tri, n = 3 * T;
     sdf_features_s *f = new sdf_features_s();
+    if (cudaGetDevice(&f->dev) != cudaSuccess) {
+        delete f;
+        return SDF_ERR_CUDA;
+    }
     f->T = T;
     f->flags = flags;
     DevBuf tmp;
@@ -923,10 +932,7 @@ extern "C" int sdf_build_features(const float *soup, int64_t n_tri, uint32_t fla
     void *rtmp = base + off_rtmp;
     void *scan_state = base + off_scan;
 
-    {
-        size_t ctr_bytes = 0;
-        B_TRY(take_block(sizeof(DevCounters), reinterpret_cast<void **>(&f->ctr), &ctr_bytes, s));
-    }
+    B_TRY(take_block(sizeof(DevCounters), reinterpret_cast<void **>(&f->ctr), &f->ctr_bytes, s));
     unsigned *const err = &f->ctr->status;  // a scan whose look-back ran out marks ST_TIMEOUT here
     // counters, the bounding box, the long-run count and the scan state start cleared (one launch)
     B_TRY(launch_dep(k_build_init, dim3(1), dim3(BT), 0, s, reinterpret_cast<unsigned *>(f->ctr),

@@ -115,6 +115,7 @@ int resolve_timing(sdf_features_s *f);
 struct sdf_features_s {
     int64_t T = 0, V = 0, E = 0;
     uint32_t flags = 0;
+    int dev = -1;  // the device the handle was built on (its memory, kept blocks and plan belong to it)
     // connectivity (fixed after the build); faces are stored in a spatial order (by smallest
     // welded vertex id), face_soup maps them back to soup triangles
     int32_t *soup_vid = nullptr;    // [3T] welded vertex of each soup corner (soup order)
@@ -140,6 +141,7 @@ struct sdf_features_s {
     void *block = nullptr;           // one allocation holding every array above
     size_t block_bytes = 0;
     sdf::DevCounters *ctr = nullptr; // device counters
+    size_t ctr_bytes = 0;
     // narrow-band scratch of single-problem calls (problem table, bins, pairs), grown on demand
     sdf::Plan *plan = nullptr;
     sdf::DevBuf fwd_winner;  // winners recomputed by a backward call that was given none
